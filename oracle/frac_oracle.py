@@ -1,0 +1,525 @@
+"""FP64 CPU oracle: operator-factorization scheme for (-Delta)^{alpha/2} and its
+tempered form on uniform grids of (-1, 1)^d, d = 1, 2, 3.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): the product never
+imports this module.
+
+Notation follows Section 2 of the paper.  gamma = 2 (the splitting parameter
+used in all of Section 3), so zeta = floor(gamma / 2) = 1.  N intervals per
+axis, h = L / N, n = N - 1 interior points per axis; arrays of grid values
+have shape (n,) * d.  The operator is symmetric under permutations of the
+axes (the weights are, and so is every rule below), so the axis order of an
+array does not matter.
+
+Readings of the paper that this oracle takes (each pinned by a test):
+  * Appendix, p = 2: the even-k and k = N weight formulas carry index typos;
+    the oracle does not use the appendix for its weights at all (it
+    integrates Eq. (wi-1D) numerically); ``weights_1d_appendix`` restates
+    the appendix with xi_{k-3/2}, xi_{k+3/2} and xi_{N-3/2} in place of the
+    printed xi_{k-1/2}, xi_{k+1/2}, xi_{N-3/4}, and a test checks the two agree.
+  * Origin value Phi(x, xi_0) (Eq. (gamma1) and its 2D analogue): replaced by
+    (1/d) sum_i sum_j e_j Phi(x, j h e_i) with e = (1,) for p in {0, 1} and
+    e = (4/3, -1/3) for p = 2.  In 1D this is Eq. (gamma1) for p <= 1 and the
+    fourth-order difference for p = 2; in 2D with p = 1 it is the a_10 of
+    Eq. (2D-scheme) together with a_11 = omega_11 / |xi_11|^2 (no zeta term).
+    These reproduce Tables 3-2-1, 3-1-2, 3-1-3 and 3-2-2.
+  * 3D scheme (omitted by the paper, Sec. 2): the same rules with d = 3.
+  * Tempered kernel (Remark 2.2): mu -> |xi|^{2-d-alpha} exp(-lambda |xi|),
+    with the normalisation c_bar_{d,alpha} := c_{d,alpha} so that lambda = 0
+    is the fractional Laplacian (Example 3.2.2).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+import numpy as np
+from scipy import integrate, linalg, special
+
+ZETA = 1  # floor(gamma / 2) with gamma = 2
+
+
+# ---------------------------------------------------------------------------
+# Constants
+# ---------------------------------------------------------------------------
+
+def c_dalpha(d: int, alpha: float) -> float:
+    """c_{d,alpha} = 2^{alpha-1} alpha Gamma((d+alpha)/2) / (pi^{d/2} Gamma(1-alpha/2)),
+    the normalisation defined after Eq. (fL-nD)."""
+    return (2.0 ** (alpha - 1.0) * alpha * math.gamma((d + alpha) / 2.0)
+            / (math.pi ** (d / 2.0) * math.gamma(1.0 - alpha / 2.0)))
+
+
+def _radial_moment(a: float, lam_c, H: float):
+    """int_0^H r^{a-1} exp(-lam_c r) dr (a > 0), exactly, via the regularised
+    lower incomplete gamma function of scipy."""
+    lam_c = np.asarray(lam_c, dtype=np.float64)
+    if np.all(lam_c == 0.0):
+        return np.full(lam_c.shape, H ** a / a)
+    out = np.empty_like(lam_c)
+    zero = lam_c == 0.0
+    out[zero] = H ** a / a
+    lc = lam_c[~zero]
+    out[~zero] = special.gamma(a) * special.gammainc(a, lc * H) / lc ** a
+    return out
+
+
+def far_field(d: int, alpha: float, L: float, lam: float = 0.0) -> float:
+    """F_d = int over R_+^d minus [0, L]^d of |xi|^{-d-alpha} exp(-lambda |xi|) dxi,
+    the u(x) part of Eq. (L2) (1D: Eq. (L2h), 1/(alpha L^alpha) when lambda = 0).
+
+    The region is split by the coordinate that is largest: xi = rho (1, s),
+    rho > L, s in [0, 1]^{d-1}, Jacobian rho^{d-1}; the d pieces are equal.
+    """
+    def radial(cs: float) -> float:
+        # int_L^inf r^{-1-alpha} e^{-lambda c r} dr
+        if lam == 0.0:
+            return L ** (-alpha) / alpha
+        val, _ = integrate.quad(lambda r: r ** (-1.0 - alpha) * math.exp(-lam * cs * r),
+                                L, np.inf, epsabs=0.0, epsrel=1e-13, limit=200)
+        return val
+
+    if d == 1:
+        return radial(1.0)
+    xs, ws = special.roots_legendre(48)
+    s, w = 0.5 * (xs + 1.0), 0.5 * ws
+    total = 0.0
+    if d == 2:
+        for si, wi in zip(s, w):
+            cs = math.sqrt(1.0 + si * si)
+            total += wi * cs ** (-d - alpha) * radial(cs)
+    elif d == 3:
+        for si, wi in zip(s, w):
+            for sj, wj in zip(s, w):
+                cs = math.sqrt(1.0 + si * si + sj * sj)
+                total += wi * wj * cs ** (-d - alpha) * radial(cs)
+    else:
+        raise ValueError("d must be 1, 2 or 3")
+    return d * total
+
+
+# ---------------------------------------------------------------------------
+# Weight integrals omega_k^p  (Eq. (wi-1D), Eq. (2D-scheme0) and its 3D analogue)
+# ---------------------------------------------------------------------------
+
+def axis_elements(N: int, h: float, p: int):
+    """Elements of the 1D Lagrange basis of degree p on the nodes xi_k = k h,
+    k = 0..N, as used in Eq. (interpolation).
+
+    Returns a list of (lo, hi, [(node, roots, scale), ...]); on [lo, hi] the
+    basis function of ``node`` is scale * prod(xi - root for root in roots).
+      p = 0: indicator of [xi_{k-1/2}, xi_{k+1/2}] cut to [0, L];
+      p = 1: hat functions on the cells [j h, (j+1) h];
+      p = 2: quadratic Lagrange polynomials on [2m h, (2m+2) h] (N even).
+    """
+    L = N * h
+    els = []
+    if p == 0:
+        for k in range(N + 1):
+            els.append((max(0.0, (k - 0.5) * h), min(L, (k + 0.5) * h), [(k, (), 1.0)]))
+    elif p in (1, 2):
+        if p == 2 and N % 2:
+            raise ValueError("p = 2 needs an even number of intervals N")
+        for m in range(N // p):
+            pts = [(p * m + t) * h for t in range(p + 1)]
+            loc = []
+            for t in range(p + 1):
+                others = tuple(pts[s] for s in range(p + 1) if s != t)
+                scale = 1.0 / np.prod([pts[t] - o for o in others])
+                loc.append((p * m + t, others, scale))
+            els.append((pts[0], pts[-1], loc))
+    else:
+        raise ValueError("p must be 0, 1 or 2")
+    return els
+
+
+def _eval_local(loc, x):
+    """Values of the local basis functions ``loc`` at points x: shape (nloc,) + x.shape."""
+    out = []
+    for _, roots, scale in loc:
+        v = np.full(np.shape(x), scale)
+        for r in roots:
+            v = v * (x - r)
+        out.append(v)
+    return np.array(out)
+
+
+def _origin_block(d, alpha, lam, H, loc, qs=24):
+    """int over [0, H]^d of prod_i phi_{l_i}(xi_i) |xi|^{2-d-alpha} exp(-lambda |xi|),
+    for every choice (l_1..l_d) of local basis functions on the origin element.
+
+    Duffy split into the d pyramids {xi_i = max_j xi_j}: xi = r (s with s_i = 1),
+    Jacobian r^{d-1}, |xi| = r c(s), c = sqrt(1 + |s|^2); the radial factor is
+    r^{1-alpha} times a polynomial in r times exp(-lambda c r), integrated
+    exactly (incomplete gamma); the s-integral uses Gauss-Legendre.
+    """
+    nloc = len(loc)
+    polys = [scale * np.poly(np.array(roots, dtype=np.float64))[::-1] if roots else np.array([scale])
+             for _, roots, scale in loc]  # ascending monomial coefficients in xi
+    beta = d + alpha - 2.0
+    out = np.zeros((nloc,) * d)
+    if d == 1:
+        for l in range(nloc):
+            for m, cm in enumerate(polys[l]):
+                out[l] += cm * _radial_moment(2.0 - alpha + m, np.array([lam]), H)[0]
+        return out
+    xs, ws = special.roots_legendre(qs)
+    s1, w1 = 0.5 * (xs + 1.0), 0.5 * ws
+    grids = np.meshgrid(*([s1] * (d - 1)), indexing="ij")
+    S = np.stack([g.reshape(-1) for g in grids], axis=1)            # (Q, d-1)
+    Wq = np.prod(np.meshgrid(*([w1] * (d - 1)), indexing="ij"), axis=0).reshape(-1)
+    cs = np.sqrt(1.0 + np.sum(S * S, axis=1))
+    maxdeg = sum(len(pl) - 1 for pl in polys[:1]) * d
+    R = np.stack([_radial_moment(2.0 - alpha + m, lam * cs, H) for m in range(maxdeg + 1)], axis=1)
+    base = Wq * cs ** (-beta)                                          # (Q,)
+    for i in range(d):                                                 # pyramid: axis i is the largest
+        coords = []
+        col = 0
+        for j in range(d):
+            if j == i:
+                coords.append(np.ones_like(cs))
+            else:
+                coords.append(S[:, col])
+                col += 1
+        for ls in itertools.product(range(nloc), repeat=d):
+            # polynomial in r: prod_j phi_{l_j}(r s_j) = prod_j sum_m c_m s_j^m r^m
+            P = np.ones((len(cs), 1))
+            for j, l in enumerate(ls):
+                pj = polys[l][None, :] * coords[j][:, None] ** np.arange(len(polys[l]))[None, :]
+                prod = np.zeros((len(cs), P.shape[1] + pj.shape[1] - 1))
+                for m1 in range(P.shape[1]):
+                    for m2 in range(pj.shape[1]):
+                        prod[:, m1 + m2] += P[:, m1] * pj[:, m2]
+                P = prod
+            out[ls] += np.sum(base * np.sum(P * R[:, :P.shape[1]], axis=1))
+    return out
+
+
+def _gauss_points(lo, hi, q):
+    xs, ws = special.roots_legendre(q)
+    return 0.5 * (hi - lo) * xs + 0.5 * (hi + lo), 0.5 * (hi - lo) * ws
+
+
+def weights(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0, q: int = 20) -> np.ndarray:
+    """omega_k^p for every k in {0..N}^d (Eq. (wi-1D); Eq. (2D-scheme0); Remark 2.2 for lambda > 0).
+
+    omega_k = int over [0, L]^d of prod_i phi_{k_i}(xi_i) mu(xi) dxi with
+    mu(xi) = |xi|^{2-d-alpha} exp(-lambda |xi|), summed element by element:
+    the origin element by ``_origin_block``; every other element, where the
+    integrand is smooth, by a q^d-point tensor Gauss-Legendre rule.
+    """
+    els = axis_elements(N, h, p)
+    ne = len(els)
+    nloc = len(els[0][2])
+    H0 = els[0][1]
+    X = np.empty((ne, q))
+    W = np.empty((ne, q))
+    B = np.empty((ne, nloc, q))
+    nodes = np.empty((ne, nloc), dtype=np.int64)
+    for e, (lo, hi, loc) in enumerate(els):
+        X[e], W[e] = _gauss_points(lo, hi, q)
+        B[e] = _eval_local(loc, X[e])
+        nodes[e] = [nd for nd, _, _ in loc]
+    WB = W[:, None, :] * B                                          # (ne, nloc, q)
+    omega = np.zeros((N + 1,) * d)
+    letters = "abc"[: d - 1]
+    qlet = "pqr"[: d - 1]
+    spec = ",".join(f"{letters[i]}{qlet[i]}" for i in range(d - 1))
+    spec = (spec + "," if spec else "") + "elz," + "e" + "".join(qlet) + "z->e" + letters + "l"
+    for outer in itertools.product(range(ne), repeat=d - 1):
+        r2 = np.zeros((ne,) + (q,) * d)
+        for i, e in enumerate(outer):
+            shape = [1] * (d + 1)
+            shape[1 + i] = q
+            r2 = r2 + (X[e] ** 2).reshape(shape)
+        shape = [ne] + [1] * (d - 1) + [q]
+        r2 = r2 + (X ** 2).reshape(shape)
+        r = np.sqrt(r2)
+        Mu = r ** (2.0 - d - alpha) * np.exp(-lam * r)
+        ops = [WB[e] for e in outer] + [WB, Mu]
+        C = np.einsum(spec, *ops)                                     # (ne, nloc.., nloc)
+        if all(e == 0 for e in outer):
+            C[0] = _origin_block(d, alpha, lam, H0, els[0][2])
+        idx = []
+        for i, e in enumerate(outer):
+            shape = [1] * (d + 1)
+            shape[1 + i] = nloc
+            idx.append(nodes[e].reshape(shape))
+        shape = [ne] + [1] * (d - 1) + [nloc]
+        idx.append(nodes.reshape(shape))
+        idx = np.broadcast_arrays(*idx)
+        np.add.at(omega, tuple(idx), C)
+    return omega
+
+
+def weights_1d_appendix(N: int, h: float, alpha: float, p: int) -> np.ndarray:
+    """Closed forms of the Appendix for omega_k^p, 1D, lambda = 0, gamma = 2.
+
+    p = 2, even 0 < k < N and k = N: uses xi_{k-3/2}, xi_{k+3/2} and
+    xi_{N-3/2} where the paper prints xi_{k-1/2}, xi_{k+1/2}, xi_{N-3/4}
+    (the printed forms disagree with Eq. (wi-1D); the corrected ones agree).
+    """
+    s0 = 2.0 - alpha
+    s1, s2 = s0 + 1.0, s0 + 2.0
+    xi = lambda t: t * h  # noqa: E731
+    w = np.zeros(N + 1)
+    if p == 0:
+        w[0] = xi(0.5) ** s0
+        w[N] = xi(N) ** s0 - xi(N - 0.5) ** s0
+        for k in range(1, N):
+            w[k] = xi(k + 0.5) ** s0 - xi(k - 0.5) ** s0
+        return w / s0
+    if p == 1:
+        w[0] = h ** s1
+        w[N] = xi(N - 1) ** s1 - xi(N) ** s1 + s1 * h * xi(N) ** s0
+        for k in range(1, N):
+            w[k] = xi(k + 1) ** s1 + xi(k - 1) ** s1 - 2.0 * xi(k) ** s1
+        return w / (h * s1 * s0)
+    if p == 2:
+        if N % 2:
+            raise ValueError("p = 2 needs even N")
+        w[0] = xi(2) ** s2 / s2 - xi(3) * xi(2) ** s1 / s1 + 2 * h * h * xi(2) ** s0 / s0
+        w[N] = ((xi(N) ** s2 - xi(N - 2) ** s2) / s2
+                - 2 * xi(N - 1.5) * (xi(N) ** s1 - xi(N - 2) ** s1) / s1
+                + xi(N - 1) * xi(N - 2) * (xi(N) ** s0 - xi(N - 2) ** s0) / s0)
+        for k in range(1, N):
+            if k % 2:
+                w[k] = (-2 * (xi(k + 1) ** s2 - xi(k - 1) ** s2) / s2
+                        + 4 * xi(k) * (xi(k + 1) ** s1 - xi(k - 1) ** s1) / s1
+                        - 2 * xi(k + 1) * xi(k - 1) * (xi(k + 1) ** s0 - xi(k - 1) ** s0) / s0)
+            else:
+                w[k] = ((xi(k + 2) ** s2 - xi(k - 2) ** s2) / s2
+                        - 2.0 / s1 * (xi(k - 1.5) * (xi(k) ** s1 - xi(k - 2) ** s1)
+                                      + xi(k + 1.5) * (xi(k + 2) ** s1 - xi(k) ** s1))
+                        + 1.0 / s0 * (xi(k - 2) * xi(k - 1) * (xi(k) ** s0 - xi(k - 2) ** s0)
+                                      + xi(k + 2) * xi(k + 1) * (xi(k + 2) ** s0 - xi(k) ** s0)))
+        return w / (2 * h * h)
+    raise ValueError("p must be 0, 1 or 2")
+
+
+# ---------------------------------------------------------------------------
+# Stencil a_k and the multilevel Toeplitz operator  (Eq. (1D-scheme), Eq. (2D-scheme))
+# ---------------------------------------------------------------------------
+
+ORIGIN_RULE = {0: (1.0,), 1: (1.0,), 2: (4.0 / 3.0, -1.0 / 3.0)}
+
+
+def stencil(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0,
+            omega: np.ndarray | None = None, q: int = 20) -> np.ndarray:
+    """Generator a_k, k in {0..N}^d, of the scheme; a[(0,)*d] holds a_0.
+
+    * k != 0: a_k = 2^{z(k)} omega_k / |xi_k|^2, z(k) = number of zero entries
+      of k (each distinct neighbour x + s o xi_k appears 2^{z(k)} times in the
+      sum over m in varkappa_1 of Eq. (eq0)).
+    * origin term: zeta omega_0 Phi(x, xi_0) ~ zeta omega_0 (1/d) sum_i sum_j
+      e_j Phi(x, j h e_i), which adds 2^{d-1} zeta e_j omega_0 / (d (j h)^2)
+      to a_{j e_i}.
+    * a_0 = -sum_{k != 0} 2^{d-z(k)} a_k - 2^d F_d  (Eq. (1D-scheme): a_0;
+      Eq. (2D-scheme): a_00).
+    """
+    if omega is None:
+        omega = weights(d, N, h, alpha, p, lam, q=q)
+    K = np.indices((N + 1,) * d)
+    k2 = np.sum(K * K, axis=0)
+    z = np.sum(K == 0, axis=0)
+    nz = k2 > 0
+    a = np.zeros_like(omega)
+    a[nz] = 2.0 ** z[nz] * omega[nz] / (h * h * k2[nz])
+    o0 = omega[(0,) * d]
+    for i in range(d):
+        for j, ej in enumerate(ORIGIN_RULE[p], start=1):
+            idx = [0] * d
+            idx[i] = j
+            a[tuple(idx)] += 2.0 ** (d - 1) * ZETA * ej * o0 / (d * (j * h) ** 2)
+    mult = 2.0 ** (d - z)
+    a[(0,) * d] = -math.fsum((mult * a)[nz].ravel()) - 2.0 ** d * far_field(d, alpha, N * h, lam)
+    return a
+
+
+def toeplitz_matrix(a: np.ndarray, n: int) -> np.ndarray:
+    """Dense symmetric multilevel Toeplitz matrix T with T[i, j] = a[|i - j|]
+    (componentwise), rows/columns in C order of the (n,)*d grid
+    (A^{(1)} after Eq. (1D-scheme); A^{(2)} after Eq. (2D-scheme))."""
+    d = a.ndim
+    I = np.indices((n,) * d).reshape(d, -1)
+    D = tuple(np.abs(I[i][:, None] - I[i][None, :]) for i in range(d))
+    return a[D]
+
+
+def operator_matrix(a: np.ndarray, c: float, n: int) -> np.ndarray:
+    """A = -c_{d,alpha} T(a)."""
+    return -c * toeplitz_matrix(a, n)
+
+
+def apply_dense(a: np.ndarray, c: float, u: np.ndarray) -> np.ndarray:
+    """y = A u with A = -c T(a), by the dense sum of the scheme (all rows)."""
+    n = u.shape[0]
+    return (operator_matrix(a, c, n) @ u.reshape(-1)).reshape(u.shape)
+
+
+def apply_rows(a: np.ndarray, c: float, u: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """(A u)_i = -c sum_j a[|i - j|] u_j for the multi-indices i in ``rows`` (R, d)."""
+    d = u.ndim
+    n = u.shape[0]
+    J = np.indices((n,) * d).reshape(d, -1)
+    uf = u.reshape(-1)
+    out = np.empty(len(rows))
+    for t, r in enumerate(np.asarray(rows)):
+        D = tuple(np.abs(J[i] - r[i]) for i in range(d))
+        out[t] = -c * math.fsum(a[D] * uf)
+    return out
+
+
+def norm_bound(a: np.ndarray, c: float, n: int) -> float:
+    """c * sum over the offsets o in (-(n-1)..n-1)^d of |a_{|o|}|: the largest
+    absolute row sum bound, hence an upper bound of ||A||_2 for the (n,)*d grid;
+    used to normalise apply errors."""
+    d = a.ndim
+    sub = a[(slice(0, n),) * d]
+    K = np.indices(sub.shape)
+    mult = 2.0 ** np.sum(K > 0, axis=0)
+    return c * float(np.sum(mult * np.abs(sub)))
+
+
+# ---------------------------------------------------------------------------
+# Boundary vector b  (Eq. (1D-scheme): b_i; Eq. (2D-scheme): b_ij)
+# ---------------------------------------------------------------------------
+
+def boundary_vector(d: int, N: int, h: float, alpha: float, a: np.ndarray, c: float, g,
+                    lam: float = 0.0, lo: float = -1.0, nq: int = 96) -> np.ndarray:
+    """-c b_i for every interior point: b_i is the near-field sum of a_{|o|} g
+    over the exterior grid points x_i + o h (o in [-N, N]^d) plus the far field
+    sum_{m in varkappa_1} int over Upsilon_+^c of g(x_i + (-1)^m o xi)
+    |xi|^{-d-alpha} exp(-lambda |xi|) dxi  (Eq. (L2)).
+
+    ``g`` maps an array (..., d) of points to values.  The far-field integral
+    uses xi = rho (1, s) with rho = L / t: rho^{-1-alpha} d rho = L^{-alpha}
+    t^{alpha-1} dt, integrated by Gauss-Jacobi in t and Gauss-Legendre in s.
+    """
+    n = N - 1
+    L = N * h
+    # near field over exterior points, index range [1-N, 2N-1] per axis (paper indexing)
+    ext = np.arange(1 - N, 2 * N)
+    grids = np.meshgrid(*([lo + ext * h] * d), indexing="ij")
+    P = np.stack(grids, axis=-1)
+    G = g(P)
+    inside = np.ones(G.shape, dtype=bool)
+    for i in range(d):
+        shape = [1] * d
+        shape[i] = len(ext)
+        inside = inside & ((ext >= 1) & (ext <= N - 1)).reshape(shape)
+    G = np.where(inside, 0.0, G)
+    near = np.zeros((n,) * d)
+    for o in itertools.product(range(-N, N + 1), repeat=d):
+        coef = a[tuple(abs(t) for t in o)]
+        sl = tuple(slice(N + t, N + t + n) for t in o)   # interior index i+1 -> ext offset (i+1)-(1-N)
+        near += coef * G[sl]
+    # far field
+    xt, wt = special.roots_jacobi(nq, 0.0, alpha - 1.0)     # weight (1+x)^{alpha-1} on [-1, 1]
+    t = 0.5 * (xt + 1.0)
+    wt = wt * 0.5 ** alpha                                   # int_0^1 t^{alpha-1} f(t) dt
+    rho = L / t
+    interior = lo + (np.arange(n) + 1) * h
+    X = np.stack(np.meshgrid(*([interior] * d), indexing="ij"), axis=-1)  # (n,)*d + (d,)
+    far = np.zeros((n,) * d)
+    if d == 1:
+        for sgn in (-1.0, 1.0):
+            vals = g(X[..., None, :] + sgn * rho[:, None])          # (n, nq)
+            far += L ** (-alpha) * np.sum(wt * np.exp(-lam * rho) * vals, axis=-1)
+    else:
+        xs, ws = special.roots_legendre(nq // 2)
+        s1, w1 = 0.5 * (xs + 1.0), 0.5 * ws
+        S = np.stack([g_.reshape(-1) for g_ in np.meshgrid(*([s1] * (d - 1)), indexing="ij")], axis=1)
+        WS = np.prod(np.meshgrid(*([w1] * (d - 1)), indexing="ij"), axis=0).reshape(-1)
+        cs = np.sqrt(1.0 + np.sum(S * S, axis=1))
+        for i in range(d):
+            dirs = np.ones((len(cs), d))
+            dirs[:, [j for j in range(d) if j != i]] = S
+            for m in itertools.product((-1.0, 1.0), repeat=d):
+                sd = dirs * np.array(m)                              # (Q, d)
+                for ti in range(nq):
+                    pts = X[..., None, :] + rho[ti] * sd            # (n..,Q,d)
+                    wq = WS * cs ** (-d - alpha) * np.exp(-lam * rho[ti] * cs)
+                    far += L ** (-alpha) * wt[ti] * np.sum(wq * g(pts), axis=-1)
+    return -c * (near + far)
+
+
+# ---------------------------------------------------------------------------
+# Solves
+# ---------------------------------------------------------------------------
+
+def solve_dense(a: np.ndarray, c: float, rhs: np.ndarray) -> np.ndarray:
+    """Solve A u = rhs by dense Cholesky (A is symmetric positive definite)."""
+    n = rhs.shape[0]
+    A = operator_matrix(a, c, n)
+    cf = linalg.cho_factor(A, lower=True)
+    return linalg.cho_solve(cf, rhs.reshape(-1)).reshape(rhs.shape)
+
+
+def solve_cg(a: np.ndarray, c: float, rhs: np.ndarray, rtol: float = 1e-12, maxiter: int = 100000):
+    """Plain conjugate gradients with the dense apply; returns (u, iterations)."""
+    n = rhs.shape[0]
+    A = operator_matrix(a, c, n)
+    b = rhs.reshape(-1)
+    x = np.zeros_like(b)
+    r = b.copy()
+    pvec = r.copy()
+    rr = r @ r
+    bn = math.sqrt(b @ b)
+    it = 0
+    while math.sqrt(rr) > rtol * bn and it < maxiter:
+        q = A @ pvec
+        alpha_k = rr / (pvec @ q)
+        x += alpha_k * pvec
+        r -= alpha_k * q
+        rr_new = r @ r
+        pvec = r + (rr_new / rr) * pvec
+        rr = rr_new
+        it += 1
+    return x.reshape(rhs.shape), it
+
+
+# ---------------------------------------------------------------------------
+# Grids and closed-form references
+# ---------------------------------------------------------------------------
+
+def interior_points(N: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """x_i = a + i h, i = 1..N-1 (Sec. 2.1)."""
+    h = (hi - lo) / N
+    return lo + h * np.arange(1, N)
+
+
+def radius2(N: int, d: int) -> np.ndarray:
+    """|x|^2 on the interior grid of (-1, 1)^d, shape (N-1,)*d."""
+    x = interior_points(N)
+    grids = np.meshgrid(*([x] * d), indexing="ij")
+    return sum(g * g for g in grids)
+
+
+def fl_ball_power(d: int, alpha: float, s: float, r2) -> np.ndarray:
+    """(-Delta)^{alpha/2} (1 - |x|^2)_+^s for |x| < 1:
+    2^alpha Gamma(1+s) Gamma((d+alpha)/2) / (Gamma(d/2) Gamma(1+s-alpha/2))
+    * 2F1((d+alpha)/2, alpha/2 - s; d/2; |x|^2)  (Eq. (fun0) for d = 1)."""
+    pref = (2.0 ** alpha * math.gamma(1 + s) * math.gamma((d + alpha) / 2)
+            / (math.gamma(d / 2) * math.gamma(1 + s - alpha / 2)))
+    return pref * special.hyp2f1((d + alpha) / 2, alpha / 2 - s, d / 2, np.asarray(r2))
+
+
+def fl_lorentzian_1d(alpha: float, x) -> np.ndarray:
+    """(-Delta)^{alpha/2} 1/(1+x^2) = Gamma(1+alpha) cos((1+alpha) arctan x) / (1+x^2)^{(1+alpha)/2},
+    from the pseudo-differential definition Eq. (pseudo) (Fourier transform pi e^{-|k|})."""
+    x = np.asarray(x)
+    return math.gamma(1 + alpha) * np.cos((1 + alpha) * np.arctan(x)) / (1 + x * x) ** ((1 + alpha) / 2)
+
+
+def fl_gaussian(d: int, alpha: float, r2) -> np.ndarray:
+    """(-Delta)^{alpha/2} exp(-|x|^2) = 2^alpha Gamma((d+alpha)/2)/Gamma(d/2) 1F1((d+alpha)/2; d/2; -|x|^2)
+    (Example 3.2.3 states the d = 2 case)."""
+    return (2.0 ** alpha * math.gamma((d + alpha) / 2) / math.gamma(d / 2)
+            * special.hyp1f1((d + alpha) / 2, d / 2, -np.asarray(r2)))
+
+
+def build_operator(d: int, N: int, alpha: float, p: int, lam: float = 0.0, L: float = 2.0, q: int = 20):
+    """Convenience: (a, c, h) for the scheme on (-1, 1)^d with N intervals."""
+    h = L / N
+    return stencil(d, N, h, alpha, p, lam, q=q), c_dalpha(d, alpha), h
