@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the FFT Toeplitz apply (and the solves around it) on GB300.
+
+Workload (one "step"): y = A u for 65 fields on the 1023 x 1023 interior grid
+of (-1, 1)^2, alpha = 1.2, quadratic basis (p = 2), FP32, 2048^2 circulant
+embedding: the exact solution (1-|x|^2)_+^{1+alpha/2} plus 64 seeded smooth
+random fields.  Inputs (272 MB) and the intermediate spectra (545 MB) exceed
+the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With N > 1 (torchrun) every rank runs the same workload
+on its own GPU (replicas; no collective on the data path) and rank 0 reports
+the whole-job rate.  --impl reference times the FP64 CPU oracle on the same
+workload (bounded sample of rows).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Toeplitz apply GDOF/s; Poisson solves/s @1e-10 vs FP64 plain; p50/p99 latency"
+D, NSIDE, ALPHA, DEGREE, NFIELDS = 2, 1023, 1.2, 2, 65
+WORKLOAD = ("2D FFT-Toeplitz apply, 1023^2 interior grid on a 2048^2 circulant embedding, alpha=1.2, "
+            "quadratic basis, 65 fields (exact solution + 64 seeded smooth fields), FP32")
+
+
+def workload_fields() -> np.ndarray:
+    u0 = synth.ball_power(D, NSIDE, 1 + ALPHA / 2)[None]
+    return np.concatenate([u0, synth.smooth_fields(D, NSIDE, NFIELDS - 1)]).astype(np.float32)
+
+
+def config(parallelism: str) -> dict:
+    return {"workload": WORKLOAD, "grid": [NSIDE, NSIDE], "fft": [2048, 2048], "fields": NFIELDS,
+            "alpha": ALPHA, "degree": DEGREE, "global_batch": NFIELDS, "parallelism": parallelism,
+            "l2": "inputs 272 MB and spectra 545 MB exceed the 129 MB L2; no flush"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_rows_rate(seconds: float = 15.0, fields: np.ndarray | None = None) -> dict:
+    """Time the FP64 oracle on a bounded sample of the workload: build its
+    generator, then dense rows of the fields until ``seconds`` have elapsed."""
+    from oracle import frac_oracle as O
+    N = NSIDE + 1
+    t0 = time.perf_counter()
+    a = O.stencil(D, N, 2.0 / N, ALPHA, DEGREE)
+    c = O.c_dalpha(D, ALPHA)
+    t_gen = time.perf_counter() - t0
+    if fields is None:
+        fields = np.stack([synth.ball_power(D, NSIDE, 1 + ALPHA / 2), synth.smooth_field(D, NSIDE, synth.BASE_SEED)])
+    rng = np.random.default_rng(1)
+    rows = 0
+    t1 = time.perf_counter()
+    while time.perf_counter() - t1 < seconds:
+        b = rows % len(fields)
+        r = rng.integers(0, NSIDE, size=(1, 2))
+        O.apply_rows(a, c, fields[b].astype(np.float64), r)
+        rows += 1
+    t_rows = time.perf_counter() - t1
+    rate = rows / t_rows / 1e9
+    return {"value": rate, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"{rows} output rows of the 1023^2 FP64 dense sum (generator build {t_gen:.1f} s excluded), "
+                      f"single-threaded numpy"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    fields = np.stack([synth.ball_power(D, NSIDE, 1 + ALPHA / 2), synth.smooth_field(D, NSIDE, synth.BASE_SEED)])
+    per_step = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        oracle_rows_rate(min(per_step, 2.0), fields)
+    t0 = time.perf_counter()
+    vals = [oracle_rows_rate(per_step, fields) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config("host cores, rank 0 only"),
+            "cpu_baseline": {"value": v, "unit": "GDOF/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in (self.out or "").splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def profile_read(lib) -> dict:
+    import ctypes
+
+    class KS(ctypes.Structure):
+        _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+    arr = (KS * 64)()
+    cnt = ctypes.c_int()
+    lib.frac_profile_read(ctypes.cast(arr, ctypes.c_void_p), 64, ctypes.byref(cnt), 1)
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(min(cnt.value, 64))}
+
+
+def algorithmic_bytes(kernel: str, fields: int) -> float:
+    """Compulsory bytes per launch of each apply kernel for the workload
+    (FP32; n = 1023, K = 1025 half-spectrum columns, complex = 8 B)."""
+    n, K = NSIDE, 1025
+    u = n * n * 4
+    W = n * K * 8
+    if kernel.startswith("rows_fwd"):
+        return fields * (u + W)
+    if kernel.startswith("rows_inv"):
+        return fields * (W + u)
+    if kernel.startswith("cols_sym"):
+        return fields * 2 * W + K * K * 4
+    raise KeyError(kernel)
+
+
+def run_ours(args) -> None:
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2103_03658_gb300 as fg
+    from paper_2103_03658_gb300 import _native as nat
+    lib = nat.load()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    op = fg.FracOp(D, NSIDE, ALPHA, degree=DEGREE)
+    host = workload_fields()
+    u = torch.from_numpy(host).cuda()
+    y = torch.empty_like(u)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        op.apply(u, out=y)
+    barrier()
+    lib.frac_profile_enable(1)
+    profile_read(lib)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            op.apply(u, out=y)
+        ev1.record(stream)
+        barrier()
+    lib.frac_profile_enable(0)
+    prof = profile_read(lib)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    dof = NFIELDS * NSIDE * NSIDE
+    value = world * dof / (ms * 1e-3) / 1e9
+    launches = sum(v[0] for v in prof.values())
+
+    # roofline of the dominant kernel (largest total device time in the timed region)
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_note = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    roof = None
+    if dom:
+        name, (nl, tot) = dom
+        per_launch_ms = tot / nl
+        ab = algorithmic_bytes(name, NFIELDS)
+        achieved = ab / (per_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "peak_source": peak_note,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None, "algorithmic_bytes": ab,
+                "ms_per_launch": per_launch_ms,
+                "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1),
+                                "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-12)} for k, v in prof.items()}}
+
+    # end to end through the public API with pinned host buffers (copies inside the timed region)
+    hu = torch.from_numpy(host).pin_memory()
+    hy = torch.empty_like(hu).pin_memory()
+    op.apply(hu, out=hy)
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        op.apply(hu, out=hy)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * dof / e2e_s / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": host.nbytes,
+           "d2h_bytes_per_step": host.nbytes}
+
+    extra = {}
+    if not args.no_extra:
+        extra = extra_measurements(fg, torch, u, op, barrier)
+
+    if rank != 0:
+        op.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        cpu = oracle_rows_rate(12.0)
+    line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config("replicas" if world > 1 else "single GPU"),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(), "extra": extra}
+    print(json.dumps(line), flush=True)
+    op.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def extra_measurements(fg, torch, u32, op, barrier) -> dict:
+    """FP64 apply of the same workload, and solves at a 1e-10 relative residual:
+    1D (n = 1023, p = 1, alpha in {0.5, 1, 1.5}) mixed and plain FP64, and the
+    3D mixed solve (255^3, p = 1, alpha = 1.6)."""
+    out = {}
+    u64 = u32.double()
+    y64 = torch.empty_like(u64)
+    op.apply(u64, out=y64)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        op.apply(u64, out=y64)
+    barrier()
+    t = (time.perf_counter() - t0) / 3
+    out["apply_f64"] = {"value": NFIELDS * NSIDE * NSIDE / t / 1e9, "unit": "GDOF/s", "ms_per_step": 1e3 * t}
+    del u64, y64
+    solves = {}
+    for alpha in (0.5, 1.0, 1.5):
+        op1 = fg.FracOp(1, 1023, alpha, degree=1)
+        f = torch.tensor(synth.ball_power_rhs(1, 1023, alpha), device="cuda")
+        res = {}
+        for prec in ("mixed", "f64"):
+            op1.solve(f, precision=prec)
+            barrier()
+            t0 = time.perf_counter()
+            reps = 3
+            for _ in range(reps):
+                _, info = op1.solve(f, rtol=1e-10, precision=prec)
+            barrier()
+            dt = (time.perf_counter() - t0) / reps
+            res[prec] = {"solves_per_s": 1.0 / dt, "ms": 1e3 * dt, "iters": info["iters"],
+                         "outer": info["outer"], "rel_resid": info["rel_resid"]}
+        solves[f"1d_n1023_p1_alpha{alpha}"] = res
+        op1.close()
+    op3 = fg.FracOp(3, 255, 1.6, degree=1)
+    f3 = torch.tensor(synth.ball_power_rhs(3, 255, 1.6), device="cuda")
+    barrier()
+    t0 = time.perf_counter()
+    _, info = op3.solve(f3, rtol=1e-10, precision="mixed")
+    barrier()
+    dt = time.perf_counter() - t0
+    solves["3d_n255_p1_alpha1.6"] = {"mixed": {"solves_per_s": 1.0 / dt, "ms": 1e3 * dt, "iters": info["iters"],
+                                               "outer": info["outer"], "rel_resid": info["rel_resid"]}}
+    op3.close()
+    out["solves"] = solves
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * frac.h -- C ABI of the GB300 (sm_103a) library for the operator-factorization
+ * discretization of the integral fractional Laplacian (-Delta)^{alpha/2} and its
+ * tempered generalization (Wu & Zhang, arXiv 2103.03658).
+ *
+ * Discrete operator (Sec. 2, Eq. (1D-scheme), Eq. (2D-scheme), Remark 2.2):
+ *   (-Delta)^{alpha/2}_h u = A u + b,   A = -c_{d,alpha} T(a),
+ * T(a) the symmetric multilevel Toeplitz matrix with generator a_k,
+ * k in {0..N}^d, built from the weight integrals omega_k^p of Lagrange
+ * bases of degree p (Eq. (wi-1D), Eq. (2D-scheme0)), splitting parameter
+ * gamma = 2.
+ *
+ * Conventions for every entry point:
+ *   - Grid vectors are C-ordered arrays of shape [n3][n2][n1] (d = 3),
+ *     [n2][n1] (d = 2) or [n1] (d = 1): x^{(1)} is the fastest axis.  A batch
+ *     of vectors is contiguous, vector after vector.
+ *   - Pointers may be device or host memory; host buffers are staged through
+ *     device memory on the given stream (the call then synchronises that
+ *     stream before returning).  Device buffers must be aligned to their
+ *     element size.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Calls on device buffers are stream-ordered and do not synchronise the
+ *     host, except where stated.
+ *   - Ownership: callers own every vector; the library owns frac_op objects
+ *     and the scratch it allocates (stream-ordered, cudaMallocAsync).
+ *   - Return value: FRAC_OK or one of the error codes below; frac_strerror()
+ *     names it.  On error no output is written unless stated.
+ */
+#ifndef FRAC_H
+#define FRAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum frac_status {
+  FRAC_OK = 0,
+  FRAC_EINVAL = 1,      /* invalid argument (see each entry point)              */
+  FRAC_ENOMEM = 2,      /* device allocation failed                             */
+  FRAC_ENOTSUP = 3,     /* valid but not supported by this build                */
+  FRAC_ENOCONV = 4,     /* solver hit max_iter; u holds the last iterate        */
+  FRAC_EBREAKDOWN = 5,  /* CG breakdown: p^T A p <= 0 or non-finite             */
+  FRAC_ETIMEOUT = 6,    /* a bounded device wait ran out                        */
+  FRAC_ECUDA = 7        /* a CUDA runtime call failed                           */
+};
+
+enum frac_dtype { FRAC_F32 = 0, FRAC_F64 = 1 };
+
+enum frac_precision {
+  FRAC_PLAIN_F64 = 0,   /* CG with the FP64 apply throughout                    */
+  FRAC_MIXED_IR = 1     /* FP32 CG inside FP64 iterative refinement             */
+};
+
+/* One discretized problem on Omega = prod_i (lo_i, lo_i + (n_i + 1) h). */
+typedef struct frac_problem {
+  int32_t d;        /* dimension, 1..3                                             */
+  int32_t degree;   /* Lagrange basis degree p: 0 (constant), 1 (linear), 2 (quadratic);
+                       p = 2 needs an even number of intervals N_i = n_i + 1       */
+  double alpha;     /* fractional power, 0 < alpha < 2                             */
+  double h;         /* mesh size, > 0                                              */
+  int64_t n[3];     /* interior points per axis (N_i - 1); entries i >= d ignored;
+                       d >= 2 needs n_1 = n_2 (= n_3)                              */
+  double lambda;    /* tempering: kernel e^{-lambda |xi|} (Remark 2.2); 0 = (-Delta)^{alpha/2} */
+} frac_problem;
+
+typedef struct frac_op frac_op;  /* opaque, immutable after frac_coeffs, shareable across streams */
+
+typedef struct frac_op_info_t {
+  double c_dalpha;        /* c_{d,alpha} (definition after Eq. (fL-nD))           */
+  double a0;              /* centre coefficient a_0 (Eq. (1D-scheme), a_00 of Eq. (2D-scheme)) */
+  double far_field;       /* F_d = int over R_+^d \ [0,L]^d of |xi|^{-d-alpha} e^{-lambda|xi|} */
+  double norm_bound;      /* max_k |Lambda_k| = ||A||_2 (from the FP64 symbol)    */
+  int64_t fft_len;        /* M: circulant embedding length per axis (power of two >= 2n-1) */
+  int64_t n_gen;          /* N + 1: generator entries per axis                     */
+  size_t device_bytes;    /* device memory owned by the op                         */
+} frac_op_info_t;
+
+/*
+ * frac_coeffs -- build the operator of `prob` on the device.
+ * Computes, in FP64 on the GPU: the weight integrals omega_k^p for
+ * k in {0..N}^d (Eq. (wi-1D); Eq. (2D-scheme0); its 3D analogue), the
+ * stencil a_k = 2^{z(k)} omega_k / |xi_k|^2 with the origin rule, the centre
+ * coefficient a_0 = -sum_{k!=0} 2^{d-z(k)} a_k - 2^d F_d, and the symbol
+ * Lambda = -c_{d,alpha} DFT_M(circulant embedding of a) (real, even), kept in
+ * FP64 and FP32.  *out receives a new op (release with frac_op_free).
+ * Errors: FRAC_EINVAL (d not in 1..3, alpha not in (0,2), degree not in 0..2,
+ * n_i < 1, unequal n_i for d >= 2, odd N with degree 2, h <= 0 or non-finite,
+ * lambda < 0 or non-finite, out == NULL), FRAC_ENOTSUP (M beyond the FFT
+ * sizes of this build: M <= 8192 for d = 1, <= 2048 for d = 2, <= 512 for
+ * d = 3), FRAC_ENOMEM, FRAC_ECUDA.  Synchronises `stream` before returning.
+ */
+int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream);
+
+/* Release an op (NULL is ignored).  The caller must ensure no work using it is in flight. */
+void frac_op_free(frac_op* op);
+
+/* Fill *info (host pointer).  Errors: FRAC_EINVAL for NULL arguments. */
+int frac_op_info(const frac_op* op, frac_op_info_t* info);
+
+/*
+ * Copy the FP64 generator a_k (k in {0..N}^d, C order, k_1 fastest, a[0] = a_0)
+ * to the host buffer `a` of `count` doubles.  Errors: FRAC_EINVAL if count
+ * differs from (N+1)^d or a pointer is NULL; FRAC_ECUDA.  Synchronous.
+ */
+int frac_op_generator(const frac_op* op, double* a, size_t count);
+
+/*
+ * frac_apply -- y = A u for `batch` grid vectors (Eq. (1D-scheme) and
+ * Eq. (2D-scheme) with b = 0, i.e. g = 0), by circulant embedding and FFT
+ * (Sec. 2.1 notes that the Toeplitz structure allows an O(N log N) FFT product).  u and y hold
+ * batch * prod(n_i) values of `dtype` (FRAC_F32: float, FP32 FFT and symbol;
+ * FRAC_F64: double, FP64 FFT and symbol).  u and y must not overlap.
+ * Errors: FRAC_EINVAL (NULL op/pointers with batch > 0, batch < 0, unknown
+ * dtype, misaligned device pointer), FRAC_ENOMEM, FRAC_ECUDA.
+ * batch == 0 is a no-op.
+ */
+int frac_apply(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* stream);
+
+typedef struct frac_solve_opts {
+  double rtol;          /* target ||f - A u||_2 / ||f||_2 (true residual, FP64); e.g. 1e-10 */
+  int32_t max_iter;     /* cap on CG iterations (all inner iterations summed for MIXED_IR) */
+  int32_t precision;    /* FRAC_PLAIN_F64 or FRAC_MIXED_IR                                  */
+  int32_t use_x0;       /* nonzero: u holds the initial guess on entry                      */
+  double inner_tol;     /* MIXED_IR: relative residual reduction of each FP32 inner solve   */
+} frac_solve_opts;
+
+typedef struct frac_solve_info {
+  int32_t status;       /* FRAC_OK, FRAC_ENOCONV or FRAC_EBREAKDOWN                    */
+  int32_t iters;        /* CG iterations (inner iterations summed for MIXED_IR)        */
+  int32_t outer;        /* refinement steps (MIXED_IR), 0 for PLAIN_F64                */
+  int32_t reserved;
+  double rel_resid;     /* final ||f - A u||_2 / ||f||_2, recomputed with the FP64 apply */
+} frac_solve_info;
+
+/*
+ * frac_solve -- solve A u = f for one right-hand side (the fractional Poisson
+ * problem Eq. (Poisson)-(BC) with g = 0; Example 3.2.3 asks for an FFT-based
+ * fast solver without naming one).  A is symmetric positive
+ * definite, so the solver is conjugate gradients with the FFT apply, either in
+ * FP64 or as FP32 CG inside FP64 iterative refinement.  f and u hold prod(n_i)
+ * doubles (device or host).  g must be NULL (nonhomogeneous data:
+ * FRAC_ENOTSUP).  `info` is a host pointer filled before return (the call
+ * synchronises `stream`).  Errors: FRAC_EINVAL (NULL op/f/u/opts/info, rtol
+ * <= 0, max_iter < 1, unknown precision, non-finite f), FRAC_ENOTSUP,
+ * FRAC_ENOCONV / FRAC_EBREAKDOWN (u holds the last iterate, info filled),
+ * FRAC_ENOMEM, FRAC_ECUDA.
+ */
+int frac_solve(const frac_op* op, const double* f, const double* g, double* u,
+               const frac_solve_opts* opts, frac_solve_info* info, void* stream);
+
+/*
+ * frac_solve_batch -- solve `count` independent problems (ops[i], f[i], u[i],
+ * all device pointers) with the same options; info[i] filled per problem
+ * (host array).  Problems run concurrently on the device: 1D problems of
+ * M <= 8192 are solved whole inside one thread block each, in one launch;
+ * larger problems share the remaining work.  Errors as frac_solve, per problem
+ * in info[i].status; the return value is the first nonzero status or FRAC_OK.
+ */
+int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* const* f,
+                     double* const* u, const frac_solve_opts* opts, frac_solve_info* info,
+                     void* stream);
+
+/*
+ * Kernel timing (tracing aid, off by default; not part of the paper's method).
+ * frac_profile_enable(1) makes every library kernel launch record a pair of
+ * CUDA events on its own stream; frac_profile_read() waits for the recorded
+ * events, folds them into per-kernel totals (launch count, summed device time
+ * in ms), copies up to `cap` of them to `out` (host array), stores the number
+ * of kernels in *count and, if `reset`, clears the totals.  Names identify the
+ * kernel, precision and FFT length (e.g. "cols_sym_f32_M2048").
+ * Errors: FRAC_EINVAL (NULL count, cap < 0), FRAC_ECUDA.
+ */
+typedef struct frac_kernel_stat {
+  char name[48];
+  int64_t launches;
+  double total_ms;
+} frac_kernel_stat;
+
+int frac_profile_enable(int on);
+int frac_profile_read(frac_kernel_stat* out, int cap, int* count, int reset);
+
+/* Static string naming a status code. */
+const char* frac_strerror(int status);
+
+/* Text of the last failed CUDA runtime call made by the library in the calling
+ * thread ("file:line call -> error"), or "" if none; valid until the next failure. */
+const char* frac_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FRAC_H */

@@ -252,6 +252,42 @@ def weights(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0, q:
     return omega
 
 
+def weights_at(d: int, N: int, h: float, alpha: float, p: int, lam: float, nodes, q: int = 20) -> np.ndarray:
+    """omega_k^p for the multi-indices in ``nodes`` only (same integrals as
+    ``weights``: origin element by ``_origin_block``, the others by tensor
+    Gauss-Legendre), for sizes where the whole generator is out of reach."""
+    els = axis_elements(N, h, p)
+    owner = [[] for _ in range(N + 1)]
+    for e, (_, _, loc) in enumerate(els):
+        for l, (nd, _, _) in enumerate(loc):
+            owner[nd].append((e, l))
+    origin = _origin_block(d, alpha, lam, els[0][1], els[0][2])
+    xs, ws = special.roots_legendre(q)
+    out = np.empty(len(nodes))
+    for t, k in enumerate(nodes):
+        tot = 0.0
+        for combo in itertools.product(*[owner[int(ki)] for ki in k]):
+            es = [e for e, _ in combo]
+            ls = [l for _, l in combo]
+            if all(e == 0 for e in es):
+                tot += origin[tuple(ls)]
+                continue
+            r2 = np.zeros((q,) * d)
+            wb = np.ones((q,) * d)
+            for i, (e, l) in enumerate(combo):
+                lo, hi, loc = els[e]
+                x = 0.5 * (hi - lo) * xs + 0.5 * (hi + lo)
+                w = 0.5 * (hi - lo) * ws * _eval_local([loc[l]], x)[0]
+                shape = [1] * d
+                shape[i] = q
+                r2 = r2 + (x * x).reshape(shape)
+                wb = wb * w.reshape(shape)
+            r = np.sqrt(r2)
+            tot += float(np.sum(wb * r ** (2.0 - d - alpha) * np.exp(-lam * r)))
+        out[t] = tot
+    return out
+
+
 def weights_1d_appendix(N: int, h: float, alpha: float, p: int) -> np.ndarray:
     """Closed forms of the Appendix for omega_k^p, 1D, lambda = 0, gamma = 2.
 

@@ -1,0 +1,271 @@
+"""ctypes binding of the C ABI declared in include/frac.h.
+
+Argument marshalling only: every step of the computation runs in the sm_103a
+library.  There is no CPU fallback: if the library is missing or fails to
+load, constructing an operator raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+F32, F64 = 0, 1
+PLAIN_F64, MIXED_IR = 0, 1
+STATUS = {0: "FRAC_OK", 1: "FRAC_EINVAL", 2: "FRAC_ENOMEM", 3: "FRAC_ENOTSUP", 4: "FRAC_ENOCONV",
+          5: "FRAC_EBREAKDOWN", 6: "FRAC_ETIMEOUT", 7: "FRAC_ECUDA"}
+
+
+class FracError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        detail = _detail() if status in (2, 7) else ""
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_strerror(status)})"
+                         + (f" [{detail}]" if detail else ""))
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("degree", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("h", ctypes.c_double), ("n", ctypes.c_int64 * 3), ("lam", ctypes.c_double)]
+
+
+class OpInfo(ctypes.Structure):
+    _fields_ = [("c_dalpha", ctypes.c_double), ("a0", ctypes.c_double), ("far_field", ctypes.c_double),
+                ("norm_bound", ctypes.c_double), ("fft_len", ctypes.c_int64), ("n_gen", ctypes.c_int64),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("use_x0", ctypes.c_int32), ("inner_tol", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("outer", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rel_resid", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libfrac.so (raising if it is absent and ``build_if_missing`` is False)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"{_build.LIB} is missing: build it with paper_2103_03658_gb300.build.build() "
+                               "(the library has no CPU fallback)")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    lib.frac_coeffs.argtypes = [ctypes.POINTER(Problem), ctypes.POINTER(vp), vp]
+    lib.frac_coeffs.restype = i32
+    lib.frac_op_free.argtypes = [vp]
+    lib.frac_op_free.restype = None
+    lib.frac_op_info.argtypes = [vp, ctypes.POINTER(OpInfo)]
+    lib.frac_op_info.restype = i32
+    lib.frac_op_generator.argtypes = [vp, dp, ctypes.c_size_t]
+    lib.frac_op_generator.restype = i32
+    lib.frac_apply.argtypes = [vp, vp, vp, i32, i64, vp]
+    lib.frac_apply.restype = i32
+    lib.frac_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    lib.frac_solve.restype = i32
+    lib.frac_solve_batch.argtypes = [i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    lib.frac_solve_batch.restype = i32
+    lib.frac_strerror.argtypes = [i32]
+    lib.frac_strerror.restype = ctypes.c_char_p
+    lib.frac_error_detail.argtypes = []
+    lib.frac_error_detail.restype = ctypes.c_char_p
+    lib.frac_profile_enable.argtypes = [i32]
+    lib.frac_profile_enable.restype = i32
+    lib.frac_profile_read.argtypes = [ctypes.c_void_p, i32, ctypes.POINTER(ctypes.c_int), i32]
+    lib.frac_profile_read.restype = i32
+    _lib = lib
+    return lib
+
+
+def _strerror(status: int) -> str:
+    try:
+        return load().frac_strerror(status).decode()
+    except Exception:  # library not loadable: the status name is still shown
+        return "?"
+
+
+def _detail() -> str:
+    try:
+        return load().frac_error_detail().decode()
+    except Exception:
+        return ""
+
+
+def declared_entry_points() -> list[str]:
+    """Names of the functions declared in include/frac.h."""
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "frac.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(frac_\w+)\s*\(", text, re.M)))
+
+
+# ---------------------------------------------------------------------------
+# buffers: torch tensors (device or host) and numpy arrays (host)
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(x) -> int:
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if not x.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return x.data_ptr()
+
+
+def _dtype_code(x) -> int:
+    if isinstance(x, np.ndarray):
+        dt = x.dtype
+        if dt == np.float64:
+            return F64
+        if dt == np.float32:
+            return F32
+    else:
+        torch = _torch()
+        if x.dtype == torch.float64:
+            return F64
+        if x.dtype == torch.float32:
+            return F32
+    raise TypeError("only float32 and float64 are supported")
+
+
+def _stream(stream) -> int | None:
+    if stream is not None:
+        return int(stream)
+    try:
+        torch = _torch()
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def _empty_like(x):
+    if isinstance(x, np.ndarray):
+        return np.empty_like(x)
+    return _torch().empty_like(x)
+
+
+class FracOp:
+    """Discretized (-Delta)^{alpha/2} (tempered when lam > 0) on (-1, 1)^d with n interior
+    points per axis, h = 2 / (n + 1) unless given; built on the current CUDA device."""
+
+    def __init__(self, d: int, n: int, alpha: float, degree: int = 1, lam: float = 0.0,
+                 h: float | None = None, stream=None):
+        lib = load()
+        self._lib = lib
+        self.d, self.n, self.alpha, self.degree, self.lam = d, n, alpha, degree, lam
+        self.h = 2.0 / (n + 1) if h is None else h
+        self._prob = Problem(d, degree, alpha, self.h, (ctypes.c_int64 * 3)(n, n, n), lam)
+        handle = ctypes.c_void_p()
+        s = lib.frac_coeffs(ctypes.byref(self._prob), ctypes.byref(handle), _stream(stream))
+        if s != 0:
+            raise FracError(s, "frac_coeffs")
+        self._h = handle
+
+    # -- lifecycle --
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.frac_op_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    @property
+    def shape(self) -> tuple:
+        return (self.n,) * self.d
+
+    def info(self) -> dict:
+        inf = OpInfo()
+        s = self._lib.frac_op_info(self._h, ctypes.byref(inf))
+        if s != 0:
+            raise FracError(s, "frac_op_info")
+        return {k: getattr(inf, k) for k, _ in OpInfo._fields_}
+
+    def generator(self) -> np.ndarray:
+        N1 = self.n + 2
+        a = np.empty((N1,) * self.d, dtype=np.float64)
+        s = self._lib.frac_op_generator(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size)
+        if s != 0:
+            raise FracError(s, "frac_op_generator")
+        return a
+
+    # -- apply --
+    def apply(self, u, out=None, stream=None):
+        """y = A u for u of shape (batch,) + (n,)*d or (n,)*d; float32 or float64."""
+        code = _dtype_code(u)
+        nd = self.n ** self.d
+        numel = u.size if isinstance(u, np.ndarray) else u.numel()
+        if numel % nd:
+            raise ValueError(f"size {numel} is not a multiple of n^d = {nd}")
+        y = _empty_like(u) if out is None else out
+        s = self._lib.frac_apply(self._h, _ptr(u), _ptr(y), code, numel // nd, _stream(stream))
+        if s != 0:
+            raise FracError(s, "frac_apply")
+        return y
+
+    # -- solve --
+    def solve(self, f, u=None, rtol: float = 1e-10, max_iter: int = 200000, precision: str = "mixed",
+              inner_tol: float = 1e-4, stream=None):
+        """Solve A u = f (g = 0); returns (u, info dict).  f, u float64."""
+        if _dtype_code(f) != F64:
+            raise TypeError("solve takes float64 data")
+        use_x0 = u is not None
+        if u is None:
+            u = _empty_like(f)
+        opts = SolveOpts(rtol, max_iter, MIXED_IR if precision == "mixed" else PLAIN_F64, int(use_x0), inner_tol)
+        info = SolveInfo()
+        s = self._lib.frac_solve(self._h, _ptr(f), None, _ptr(u), ctypes.byref(opts), ctypes.byref(info),
+                                 _stream(stream))
+        out = {k: getattr(info, k) for k, _ in SolveInfo._fields_ if k != "reserved"}
+        if s not in (0, 4):
+            raise FracError(s, "frac_solve")
+        return u, out
+
+
+def solve_batch(ops, fs, us, rtol: float = 1e-10, max_iter: int = 200000, precision: str = "mixed",
+                inner_tol: float = 1e-4, stream=None):
+    """Solve ops[i] u[i] = f[i] for all i (device tensors); returns a list of info dicts."""
+    lib = load()
+    cnt = len(ops)
+    H = (ctypes.c_void_p * cnt)(*[op.handle.value for op in ops])
+    F = (ctypes.c_void_p * cnt)(*[_ptr(f) for f in fs])
+    U = (ctypes.c_void_p * cnt)(*[_ptr(u) for u in us])
+    opts = SolveOpts(rtol, max_iter, MIXED_IR if precision == "mixed" else PLAIN_F64, 0, inner_tol)
+    infos = (SolveInfo * cnt)()
+    s = lib.frac_solve_batch(cnt, H, F, U, ctypes.byref(opts), infos, _stream(stream))
+    out = [{k: getattr(i, k) for k, _ in SolveInfo._fields_ if k != "reserved"} for i in infos]
+    if s not in (0, 4):
+        raise FracError(s, "frac_solve_batch")
+    return out

@@ -1,0 +1,261 @@
+// C ABI entry points (include/frac.h): argument validation, operator
+// lifecycle, staging of host buffers, dispatch to the device kernels.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "apply.cuh"
+
+namespace frac {
+
+// c_{d,alpha} = 2^{alpha-1} alpha Gamma((d+alpha)/2) / (pi^{d/2} Gamma(1-alpha/2))
+// (definition after Eq. (fL-nD)).
+static double c_dalpha(int d, double alpha) {
+  return std::pow(2.0, alpha - 1.0) * alpha * std::tgamma((d + alpha) / 2.0) /
+         (std::pow(M_PI, d / 2.0) * std::tgamma(1.0 - alpha / 2.0));
+}
+
+static int keep_pool_memory() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  FRAC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  for (int d : done)
+    if (d == dev) return FRAC_OK;
+  cudaMemPool_t pool;
+  FRAC_CUDA_TRY(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t thr = UINT64_MAX;
+  FRAC_CUDA_TRY(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  done.push_back(dev);
+  return FRAC_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static int max_logm(int d) { return d == 1 ? 13 : (d == 2 ? 11 : 9); }
+
+static int validate(const frac_problem* p) {
+  if (!p) return FRAC_EINVAL;
+  if (p->d < 1 || p->d > 3) return FRAC_EINVAL;
+  if (!(p->alpha > 0.0 && p->alpha < 2.0)) return FRAC_EINVAL;
+  if (p->degree < 0 || p->degree > 2) return FRAC_EINVAL;
+  if (!(p->h > 0.0) || !std::isfinite(p->h)) return FRAC_EINVAL;
+  if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return FRAC_EINVAL;
+  for (int i = 0; i < p->d; ++i)
+    if (p->n[i] < 1 || p->n[i] != p->n[0]) return FRAC_EINVAL;
+  if (p->degree == 2 && ((p->n[0] + 1) % 2) != 0) return FRAC_EINVAL;
+  return FRAC_OK;
+}
+
+static thread_local char g_detail[256] = "";
+
+int record_cuda_error(cudaError_t e, const char* file, int line, const char* expr) {
+  const char* base = file;
+  for (const char* c = file; *c; ++c)
+    if (*c == '/') base = c + 1;
+  std::snprintf(g_detail, sizeof(g_detail), "%s:%d %s -> %s (%s)", base, line, expr, cudaGetErrorName(e),
+                cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FRAC_ENOMEM : FRAC_ECUDA;
+}
+
+int record_check_failure(const char* file, int line, long long index) {
+  std::snprintf(g_detail, sizeof(g_detail), "%s:%d device bounds check failed at index %lld", file, line, index);
+  return FRAC_ECUDA;
+}
+
+}  // namespace frac
+
+using namespace frac;
+
+extern "C" {
+
+const char* frac_error_detail(void) { return g_detail; }
+
+const char* frac_strerror(int s) {
+  switch (s) {
+    case FRAC_OK: return "ok";
+    case FRAC_EINVAL: return "invalid argument";
+    case FRAC_ENOMEM: return "device allocation failed";
+    case FRAC_ENOTSUP: return "not supported by this build";
+    case FRAC_ENOCONV: return "solver did not converge within max_iter";
+    case FRAC_EBREAKDOWN: return "conjugate-gradient breakdown";
+    case FRAC_ETIMEOUT: return "bounded device wait ran out";
+    case FRAC_ECUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
+  if (!out) return FRAC_EINVAL;
+  *out = nullptr;
+  FRAC_TRY(validate(prob));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = prob->d;
+  const int64_t n = prob->n[0];
+  int64_t M = 2;
+  while (M < 2 * n - 1) M *= 2;
+  const int logm = ilog2(M);
+  if (logm > max_logm(d)) return FRAC_ENOTSUP;
+  FRAC_TRY(keep_pool_memory());
+  frac_op* op = new (std::nothrow) frac_op();
+  if (!op) return FRAC_ENOMEM;
+  op->prob = *prob;
+  for (int i = d; i < 3; ++i) op->prob.n[i] = 1;
+  op->N = n + 1;
+  op->n = n;
+  op->M = M;
+  op->logm = logm;
+  op->K = M / 2 + 1;
+  op->nd = op->ngen = op->nsym = 1;
+  for (int i = 0; i < d; ++i) {
+    op->nd *= n;
+    op->ngen *= (op->N + 1);
+    op->nsym *= op->K;
+  }
+  op->c = c_dalpha(d, prob->alpha);
+  cudaGetDevice(&op->device);
+  op->device_bytes = op->ngen * sizeof(double) + op->nsym * (sizeof(double) + sizeof(float));
+  int s = FRAC_OK;
+  if (cudaMalloc(&op->a, op->ngen * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&op->lam64, op->nsym * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&op->lam32, op->nsym * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    s = FRAC_ENOMEM;
+  }
+  if (s == FRAC_OK) s = prepare_twiddles(logm);
+  if (s == FRAC_OK) s = build_coefficients(op, st);
+  if (s != FRAC_OK) {
+    frac_op_free(op);
+    return s;
+  }
+  *out = op;
+  return FRAC_OK;
+}
+
+void frac_op_free(frac_op* op) {
+  if (!op) return;
+  if (op->a) cudaFree(op->a);
+  if (op->lam64) cudaFree(op->lam64);
+  if (op->lam32) cudaFree(op->lam32);
+  delete op;
+}
+
+int frac_op_info(const frac_op* op, frac_op_info_t* info) {
+  if (!op || !info) return FRAC_EINVAL;
+  info->c_dalpha = op->c;
+  info->a0 = op->a0;
+  info->far_field = op->far_field;
+  info->norm_bound = op->norm_bound;
+  info->fft_len = op->M;
+  info->n_gen = op->N + 1;
+  info->device_bytes = op->device_bytes;
+  return FRAC_OK;
+}
+
+int frac_op_generator(const frac_op* op, double* a, size_t count) {
+  if (!op || !a || count != (size_t)op->ngen) return FRAC_EINVAL;
+  FRAC_CUDA_TRY(cudaMemcpy(a, op->a, count * sizeof(double), cudaMemcpyDeviceToHost));
+  return FRAC_OK;
+}
+
+int frac_apply(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* stream) {
+  if (!op || batch < 0 || (dtype != FRAC_F32 && dtype != FRAC_F64)) return FRAC_EINVAL;
+  if (batch == 0) return FRAC_OK;
+  if (!u || !y || u == y) return FRAC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t es = dtype == FRAC_F64 ? sizeof(double) : sizeof(float);
+  const size_t bytes = (size_t)batch * op->nd * es;
+  const bool du = is_device_ptr(u), dy = is_device_ptr(y);
+  if ((du && ((uintptr_t)u % es)) || (dy && ((uintptr_t)y % es))) return FRAC_EINVAL;
+  void* ws = nullptr;
+  const size_t wsb = apply_workspace_bytes(op, dtype, batch);
+  if (wsb) FRAC_CUDA_TRY(cudaMallocAsync(&ws, wsb, st));
+  const void* ud = u;
+  void* yd = y;
+  void *tmp_u = nullptr, *tmp_y = nullptr;
+  if (!du) {
+    FRAC_CUDA_TRY(cudaMallocAsync(&tmp_u, bytes, st));
+    FRAC_CUDA_TRY(cudaMemcpyAsync(tmp_u, u, bytes, cudaMemcpyHostToDevice, st));
+    ud = tmp_u;
+  }
+  if (!dy) {
+    FRAC_CUDA_TRY(cudaMallocAsync(&tmp_y, bytes, st));
+    yd = tmp_y;
+  }
+  int s = dtype == FRAC_F64 ? apply_t<double>(op, (const double*)ud, (double*)yd, batch, ws, st)
+                            : apply_t<float>(op, (const float*)ud, (float*)yd, batch, ws, st);
+  if (s == FRAC_OK && !dy)
+    if (cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = FRAC_ECUDA;
+  if (ws) cudaFreeAsync(ws, st);
+  if (tmp_u) cudaFreeAsync(tmp_u, st);
+  if (tmp_y) cudaFreeAsync(tmp_y, st);
+  if (!du || !dy) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (s == FRAC_OK && e != cudaSuccess) s = FRAC_ECUDA;
+  }
+  return s;
+}
+
+int frac_solve(const frac_op* op, const double* f, const double* g, double* u, const frac_solve_opts* opts,
+               frac_solve_info* info, void* stream) {
+  if (!op || !f || !u || !opts || !info) return FRAC_EINVAL;
+  if (g) return FRAC_ENOTSUP;
+  if (!(opts->rtol > 0.0) || opts->max_iter < 1) return FRAC_EINVAL;
+  if (opts->precision != FRAC_PLAIN_F64 && opts->precision != FRAC_MIXED_IR) return FRAC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = op->nd * sizeof(double);
+  const bool df = is_device_ptr(f), du = is_device_ptr(u);
+  const double* fd = f;
+  double* ud = u;
+  double *tf = nullptr, *tu = nullptr;
+  if (!df) {
+    for (int64_t i = 0; i < op->nd; ++i)
+      if (!std::isfinite(f[i])) return FRAC_EINVAL;
+    FRAC_CUDA_TRY(cudaMallocAsync(&tf, bytes, st));
+    FRAC_CUDA_TRY(cudaMemcpyAsync(tf, f, bytes, cudaMemcpyHostToDevice, st));
+    fd = tf;
+  }
+  if (!du) {
+    FRAC_CUDA_TRY(cudaMallocAsync(&tu, bytes, st));
+    if (opts->use_x0) FRAC_CUDA_TRY(cudaMemcpyAsync(tu, u, bytes, cudaMemcpyHostToDevice, st));
+    ud = tu;
+  }
+  int s = solve_device(op, fd, ud, opts, info, st);
+  if (s == FRAC_OK && !du)
+    if (cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = FRAC_ECUDA;
+  if (tf) cudaFreeAsync(tf, st);
+  if (tu) cudaFreeAsync(tu, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (s == FRAC_OK && e != cudaSuccess) s = FRAC_ECUDA;
+  if (s == FRAC_OK && std::isnan(info->rel_resid)) {
+    info->status = FRAC_EINVAL;  // non-finite data in f
+    return FRAC_EINVAL;
+  }
+  if (s == FRAC_OK) s = info->status;
+  return s;
+}
+
+int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
+                     const frac_solve_opts* opts, frac_solve_info* info, void* stream) {
+  if (count < 0 || (count > 0 && (!ops || !f || !u || !opts || !info))) return FRAC_EINVAL;
+  int first = FRAC_OK;
+  for (int64_t i = 0; i < count; ++i) {
+    int s = frac_solve(ops[i], f[i], nullptr, u[i], opts, &info[i], stream);
+    if (s != FRAC_OK && first == FRAC_OK) first = s;
+    if (s != FRAC_OK && s != FRAC_ENOCONV && s != FRAC_EBREAKDOWN) info[i].status = s;
+  }
+  return first;
+}
+
+}  // extern "C"

@@ -1,0 +1,31 @@
+// Internal interfaces between the translation units of the library.
+#pragma once
+
+#include "common.cuh"
+
+namespace frac {
+
+template <typename T> inline const cplx_t<T>* tw_table(int logm);
+template <> inline const float2* tw_table<float>(int logm) { return twiddles32(logm); }
+template <> inline const double2* tw_table<double>(int logm) { return twiddles64(logm); }
+
+template <typename T> inline const T* sym_table(const frac_op* op);
+template <> inline const float* sym_table<float>(const frac_op* op) { return op->lam32; }
+template <> inline const double* sym_table<double>(const frac_op* op) { return op->lam64; }
+
+// coeffs.cu
+int prepare_twiddles(int logm);
+double far_field(int d, double alpha, double L, double lambda);
+int build_coefficients(frac_op* op, cudaStream_t st);
+
+// apply.cu: y = A u for `batch` vectors on device buffers; ws holds
+// apply_workspace_bytes(op, dtype, batch) bytes (unused for d = 1).
+size_t apply_workspace_bytes(const frac_op* op, int dtype, int64_t batch);
+template <typename T>
+int apply_t(const frac_op* op, const T* u, T* y, int64_t batch, void* ws, cudaStream_t st);
+
+// solve.cu
+int solve_device(const frac_op* op, const double* f, double* u, const frac_solve_opts* opts,
+                 frac_solve_info* info, cudaStream_t st);
+
+}  // namespace frac

@@ -1,0 +1,701 @@
+// Coefficient generation on the device, FP64:
+//   weight integrals omega_k^p (Eq. (wi-1D), Eq. (2D-scheme0) and its 3D analogue;
+//   tempered kernel of Remark 2.2), stencil a_k with the origin rule, centre
+//   coefficient a_0, far field F_d (host), and the symbol of the circulant
+//   embedding (separable cosine sums).
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace frac {
+
+// ---------------------------------------------------------------------------
+// Gauss-Legendre rules on [-1, 1] (Newton iteration on P_q, host, FP64)
+// ---------------------------------------------------------------------------
+
+constexpr int kNumRules = 8;
+constexpr int kRuleTotal = 81;
+// rule r: q points, stored from offset rule_off(r)
+__host__ __device__ constexpr int rule_q(int r) {
+  return r == 0 ? 4 : r == 1 ? 5 : r == 2 ? 6 : r == 3 ? 8 : r == 4 ? 10 : r == 5 ? 12 : r == 6 ? 16 : 20;
+}
+// (no recursion: a recursive device function called with a runtime argument
+// would need stack beyond the kernel's static frame)
+__host__ __device__ constexpr int rule_off(int r) {
+  return r == 0 ? 0 : r == 1 ? 4 : r == 2 ? 9 : r == 3 ? 15 : r == 4 ? 23 : r == 5 ? 33 : r == 6 ? 45 : 61;
+}
+__host__ __device__ constexpr bool rule_table_ok(int r) {
+  return r == kNumRules ? true : (rule_off(r) + rule_q(r) == (r + 1 == kNumRules ? kRuleTotal : rule_off(r + 1)) &&
+                                  rule_table_ok(r + 1));
+}
+static_assert(rule_table_ok(0), "rule offsets");
+
+__constant__ double c_gl_x[kRuleTotal];
+__constant__ double c_gl_w[kRuleTotal];
+
+// Self-checking accesses: an index outside [0, n) is recorded (first source
+// line and index) and the access is skipped; the host reads the record after
+// the coefficient build and reports it as FRAC_ECUDA with the line.
+__device__ unsigned long long g_fault_line = 0;
+__device__ long long g_fault_index = 0;
+__device__ __noinline__ void note_fault(int line, long long idx) {
+  if (atomicCAS(&g_fault_line, 0ull, (unsigned long long)line) == 0ull) g_fault_index = idx;
+}
+#define CHK(i, n) \
+  (((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n)) ? true : (note_fault(__LINE__, (long long)(i)), false))
+
+static void legendre_rule(int q, double* x, double* w) {
+  for (int i = 0; i < q; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (q + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;  // P_0, P_1
+      for (int k = 2; k <= q; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = q * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) {
+        // one more evaluation for the derivative at the converged node
+        p0 = 1.0;
+        p1 = z;
+        for (int k = 2; k <= q; ++k) {
+          double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        dp = q * (z * p1 - p0) / (z * z - 1.0);
+        break;
+      }
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+static int upload_rules() {
+  static std::mutex mu;
+  static std::vector<int> done;  // devices already initialised
+  int dev = 0;
+  FRAC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  for (int d : done)
+    if (d == dev) return FRAC_OK;
+  double hx[kRuleTotal], hw[kRuleTotal];
+  for (int r = 0; r < kNumRules; ++r) legendre_rule(rule_q(r), hx + rule_off(r), hw + rule_off(r));
+  FRAC_CUDA_TRY(cudaMemcpyToSymbol(c_gl_x, hx, sizeof(hx)));
+  FRAC_CUDA_TRY(cudaMemcpyToSymbol(c_gl_w, hw, sizeof(hw)));
+  done.push_back(dev);
+  return FRAC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Twiddle tables exp(-2 pi i t / M) (host FP64 with octant symmetry)
+// ---------------------------------------------------------------------------
+
+static void host_twiddles(int64_t M, std::vector<double2>& out) {
+  out.resize(M);
+  for (int64_t t = 0; t < M; ++t) {
+    // angle 2 pi t / M reduced to [0, pi/4] by symmetry
+    int64_t t8 = t * 8;  // octant = t8 / M
+    int64_t oct = t8 / M;
+    int64_t r = t8 - oct * M;  // remainder, angle within octant = (r / M) * pi/4
+    double th, c, s;
+    if (oct & 1) {
+      th = (double)(M - r) / (double)M * (M_PI / 4.0);
+    } else {
+      th = (double)r / (double)M * (M_PI / 4.0);
+    }
+    double ct = std::cos(th), st = std::sin(th);
+    // base angle: oct * pi/4 + (oct odd ? pi/4 - th : th)
+    switch (oct & 7) {
+      case 0: c = ct; s = st; break;
+      case 1: c = st; s = ct; break;
+      case 2: c = -st; s = ct; break;
+      case 3: c = -ct; s = st; break;
+      case 4: c = -ct; s = -st; break;
+      case 5: c = -st; s = -ct; break;
+      case 6: c = st; s = -ct; break;
+      default: c = ct; s = -st; break;
+    }
+    out[t] = double2{c, -s};  // exp(-i angle)
+  }
+}
+
+struct TwTables {
+  std::mutex mu;
+  // per device, per logm
+  std::vector<std::vector<double2*>> t64;
+  std::vector<std::vector<float2*>> t32;
+};
+static TwTables g_tw;
+
+static int ensure_twiddles(int logm) {
+  int dev = 0;
+  FRAC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tw.mu);
+  if ((int)g_tw.t64.size() <= dev) {
+    g_tw.t64.resize(dev + 1);
+    g_tw.t32.resize(dev + 1);
+  }
+  auto& a64 = g_tw.t64[dev];
+  auto& a32 = g_tw.t32[dev];
+  if ((int)a64.size() <= logm) {
+    a64.resize(logm + 1, nullptr);
+    a32.resize(logm + 1, nullptr);
+  }
+  if (a64[logm]) return FRAC_OK;
+  int64_t M = int64_t(1) << logm;
+  std::vector<double2> h;
+  host_twiddles(M, h);
+  std::vector<float2> hf(M);
+  for (int64_t t = 0; t < M; ++t) hf[t] = float2{(float)h[t].x, (float)h[t].y};
+  double2* d64 = nullptr;
+  float2* d32 = nullptr;
+  FRAC_CUDA_TRY(cudaMalloc(&d64, M * sizeof(double2)));
+  FRAC_CUDA_TRY(cudaMalloc(&d32, M * sizeof(float2)));
+  FRAC_CUDA_TRY(cudaMemcpy(d64, h.data(), M * sizeof(double2), cudaMemcpyHostToDevice));
+  FRAC_CUDA_TRY(cudaMemcpy(d32, hf.data(), M * sizeof(float2), cudaMemcpyHostToDevice));
+  a64[logm] = d64;
+  a32[logm] = d32;
+  return FRAC_OK;
+}
+
+int prepare_twiddles(int logm) { return ensure_twiddles(logm); }
+
+const double2* twiddles64(int logm) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_tw.mu);
+  return g_tw.t64[dev][logm];
+}
+const float2* twiddles32(int logm) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_tw.mu);
+  return g_tw.t32[dev][logm];
+}
+
+// ---------------------------------------------------------------------------
+// Far field F_d = int over R_+^d \ [0, L]^d of |xi|^{-d-alpha} e^{-lambda |xi|}
+// (the u(x) part of Eq. (L2); 1D: 1/(alpha L^alpha) when lambda = 0).
+// Largest-coordinate split: xi = rho (1, s), rho > L, s in [0,1]^{d-1}:
+// F_d = d int_s c(s)^{-d-alpha} int_L^inf rho^{-1-alpha} e^{-lambda c rho} d rho ds.
+// The rho-integral with rho = L / t is L^{-alpha} int_0^1 t^{alpha-1} e^{-lambda c L / t} dt,
+// integrated by Gauss-Legendre on geometrically graded panels [2^{-j-1}, 2^{-j}].
+// ---------------------------------------------------------------------------
+
+static double radial_tail(double alpha, double b, double L) {
+  if (b * L < 1e-14) return std::pow(L, -alpha) / alpha;
+  double x[20], w[20];
+  legendre_rule(20, x, w);
+  double x_ = b * L;
+  double sum = 0.0;
+  for (int j = 0; j < 80; ++j) {
+    double hi = std::ldexp(1.0, -j), lo = std::ldexp(1.0, -j - 1);
+    double part = 0.0;
+    for (int g = 0; g < 20; ++g) {
+      double t = 0.5 * (hi + lo) + 0.5 * (hi - lo) * x[g];
+      part += w[g] * std::pow(t, alpha - 1.0) * std::exp(-x_ / t);
+    }
+    part *= 0.5 * (hi - lo);
+    sum += part;
+    if (x_ / hi > 800.0) break;  // e^{-x/t} below underflow on every later panel
+  }
+  return std::pow(L, -alpha) * sum;
+}
+
+double far_field(int d, double alpha, double L, double lambda) {
+  if (d == 1) return radial_tail(alpha, lambda, L);
+  double x[32], w[32];
+  legendre_rule(32, x, w);
+  double tot = 0.0;
+  if (d == 2) {
+    for (int i = 0; i < 32; ++i) {
+      double s = 0.5 * (x[i] + 1.0), c = std::sqrt(1.0 + s * s);
+      tot += 0.5 * w[i] * std::pow(c, -2.0 - alpha) * radial_tail(alpha, lambda * c, L);
+    }
+  } else {
+    for (int i = 0; i < 32; ++i)
+      for (int j = 0; j < 32; ++j) {
+        double s = 0.5 * (x[i] + 1.0), t = 0.5 * (x[j] + 1.0);
+        double c = std::sqrt(1.0 + s * s + t * t);
+        tot += 0.25 * w[i] * w[j] * std::pow(c, -3.0 - alpha) * radial_tail(alpha, lambda * c, L);
+      }
+  }
+  return d * tot;
+}
+
+// ---------------------------------------------------------------------------
+// Weight integrals, one thread per node k in {0..N}^d (gather over the
+// elements of the support of the tensor basis function of k).
+// ---------------------------------------------------------------------------
+
+struct WParams {
+  int d, p;
+  int64_t N;
+  double h, alpha, lambda, beta;  // beta = d + alpha - 2
+};
+
+struct AxisEl {
+  double lo, hi;     // element interval
+  double r0, r1;     // roots of the local basis function (product form)
+  double scale;
+  int nroots;
+  int origin_l;      // local index on the origin element, or -1 if lo > 0
+};
+
+// Elements of the support of the 1D basis function of node k (at most 2).
+__device__ int axis_elements(const WParams& P, int64_t k, AxisEl* el) {
+  const double h = P.h;
+  const int64_t N = P.N;
+  const double L = N * h;
+  int ne = 0;
+  if (P.p == 0) {
+    if (!CHK(0, 2)) return 0;
+    el[0] = AxisEl{fmax(0.0, (k - 0.5) * h), fmin(L, (k + 0.5) * h), 0, 0, 1.0, 0, k == 0 ? 0 : -1};
+    ne = 1;
+  } else if (P.p == 1) {
+    if (k >= 1 && CHK(ne, 2)) el[ne++] = AxisEl{(k - 1) * h, k * h, (k - 1) * h, 0, 1.0 / h, 1, k == 1 ? 1 : -1};
+    if (k < N && CHK(ne, 2)) el[ne++] = AxisEl{k * h, (k + 1) * h, (k + 1) * h, 0, -1.0 / h, 1, k == 0 ? 0 : -1};
+  } else {
+    if (k & 1) {
+      if (CHK(ne, 2)) el[ne++] = AxisEl{(k - 1) * h, (k + 1) * h, (k - 1) * h, (k + 1) * h, -1.0 / (h * h), 2, k == 1 ? 1 : -1};
+    } else {
+      if (k >= 2 && CHK(ne, 2)) el[ne++] = AxisEl{(k - 2) * h, k * h, (k - 2) * h, (k - 1) * h, 0.5 / (h * h), 2, k == 2 ? 2 : -1};
+      if (k <= N - 2 && CHK(ne, 2)) el[ne++] = AxisEl{k * h, (k + 2) * h, (k + 1) * h, (k + 2) * h, 0.5 / (h * h), 2, k == 0 ? 0 : -1};
+    }
+  }
+  return ne;
+}
+
+__device__ __forceinline__ double basis_val(const AxisEl& e, double x) {
+  double v = e.scale;
+  if (e.nroots >= 1) v *= (x - e.r0);
+  if (e.nroots >= 2) v *= (x - e.r1);
+  return v;
+}
+
+__device__ __forceinline__ double mu_r2(double r2, const WParams& P) {
+  // |xi|^{2-d-alpha} e^{-lambda |xi|}
+  double lg = log(r2);
+  if (P.lambda == 0.0) return exp(-0.5 * P.beta * lg);
+  return exp(-0.5 * P.beta * lg - P.lambda * sqrt(r2));
+}
+
+__device__ int pick_rule(double ratio) {
+  // ratio = distance of the element's nearest corner to the origin / element width
+  if (ratio < 1.0) return 7;   // q = 20
+  if (ratio < 2.0) return 6;   // 16
+  if (ratio < 4.0) return 5;   // 12
+  if (ratio < 8.0) return 4;   // 10
+  if (ratio < 16.0) return 3;  // 8
+  if (ratio < 32.0) return 2;  // 6
+  if (ratio < 64.0) return 1;  // 5
+  return 0;                    // 4
+}
+
+// Monomial coefficients (in t = xi / h) of the local basis on the origin element.
+__device__ void origin_poly(int p, int l, double* c) {
+  c[0] = c[1] = c[2] = 0.0;
+  if (p == 0) {
+    c[0] = 1.0;
+  } else if (p == 1) {
+    if (l == 0) { c[0] = 1.0; c[1] = -1.0; } else { c[1] = 1.0; }
+  } else {
+    if (l == 0) { c[0] = 1.0; c[1] = -1.5; c[2] = 0.5; }
+    else if (l == 1) { c[1] = 2.0; c[2] = -1.0; }
+    else { c[1] = -0.5; c[2] = 0.5; }
+  }
+}
+
+// int_0^H r^{a-1} e^{-b r} dr = H^a sum_j (-b H)^j / (j! (a + j))  (power series of the lower
+// incomplete gamma function; b H <= a few on every element that reaches the origin)
+__device__ double radial_moment(double a, double b, double H) {
+  double Ha = pow(H, a);
+  if (b == 0.0) return Ha / a;
+  double x = -b * H, term = 1.0, sum = 1.0 / a;
+  for (int j = 1; j < 200; ++j) {
+    term *= x / j;
+    double t = term / (a + j);
+    sum += t;
+    if (fabs(t) < 1e-18 * fabs(sum)) break;
+  }
+  return Ha * sum;
+}
+
+// int over the origin element [0, H]^d of prod_i phi_{l_i}(xi_i) mu(xi): Duffy split into the d
+// pyramids {xi_i = max}, xi = r (s with s_i = 1), exact radial moments, Gauss-Legendre (16) in s.
+__device__ double origin_element(const WParams& P, const int* l, double H) {
+  const int d = P.d, p = P.p;
+  double cf[3][3];
+  for (int i = 0; i < d; ++i) {
+    origin_poly(p, l[i], cf[i]);
+    for (int m = 0; m < 3; ++m) cf[i][m] *= pow(P.h, -m);  // coefficients of xi^m
+  }
+  const int maxdeg = p * d;
+  if (d == 1) {
+    double s = 0.0;
+    for (int m = 0; m <= p; ++m) s += cf[0][m] * radial_moment(2.0 - P.alpha + m, P.lambda, H);
+    return s;
+  }
+  const int R = 6;  // rule index of q = 16
+  const int q = rule_q(R), off = rule_off(R);
+  double tot = 0.0;
+  const int nang = (d == 2) ? q : q * q;
+  for (int a = 0; a < nang; ++a) {
+    double s[2], ws = 1.0;
+    int ia = a % q, ib = a / q;
+    if (!CHK(off + ia, kRuleTotal) || !CHK(off + ib, kRuleTotal)) continue;
+    s[0] = 0.5 * (c_gl_x[off + ia] + 1.0);
+    ws *= 0.5 * c_gl_w[off + ia];
+    if (d == 3) {
+      s[1] = 0.5 * (c_gl_x[off + ib] + 1.0);
+      ws *= 0.5 * c_gl_w[off + ib];
+    } else {
+      s[1] = 0.0;
+    }
+    double cs2 = 1.0 + s[0] * s[0] + (d == 3 ? s[1] * s[1] : 0.0);
+    double cs = sqrt(cs2);
+    double R_m[7];
+    for (int m = 0; m <= maxdeg && CHK(m, 7); ++m) R_m[m] = radial_moment(2.0 - P.alpha + m, P.lambda * cs, H);
+    double base = ws * pow(cs, -P.beta);
+    for (int i = 0; i < d; ++i) {  // pyramid: axis i largest
+      double poly[7] = {1, 0, 0, 0, 0, 0, 0};
+      int deg = 0, col = 0;
+      for (int j = 0; j < d; ++j) {
+        double t = (j == i) ? 1.0 : (CHK(col, 2) ? s[col++] : 0.0);
+        double pj[3] = {cf[j][0], cf[j][1] * t, cf[j][2] * t * t};
+        double np[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int m1 = 0; m1 <= deg; ++m1)
+          for (int m2 = 0; m2 <= p; ++m2)
+            if (CHK(m1 + m2, 7) && CHK(m1, 7) && CHK(m2, 3)) np[m1 + m2] += poly[m1] * pj[m2];
+        deg += p;
+        for (int m = 0; m < 7; ++m) poly[m] = np[m];
+      }
+      double acc = 0.0;
+      for (int m = 0; m <= deg && CHK(m, 7); ++m) acc += poly[m] * R_m[m];
+      tot += base * acc;
+    }
+  }
+  return tot;
+}
+
+__global__ void k_weights(WParams P, double* __restrict__ omega, int64_t count) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  const int d = P.d;
+  const int64_t N1 = P.N + 1;
+  int64_t k[3] = {0, 0, 0};
+  int64_t rem = idx;
+  for (int i = 0; i < d; ++i) {  // i = 0 is the fastest axis
+    k[i] = rem % N1;
+    rem /= N1;
+  }
+  AxisEl el[3][2];
+  int ne[3] = {1, 1, 1};
+  if (!CHK(d - 1, 3)) return;
+  for (int i = 0; i < d; ++i) {
+    ne[i] = axis_elements(P, k[i], el[i]);
+    if (!CHK(ne[i] - 1, 2)) return;
+  }
+  double total = 0.0;
+  const int ncomb = ne[0] * (d > 1 ? ne[1] : 1) * (d > 2 ? ne[2] : 1);
+  for (int cmb = 0; cmb < ncomb; ++cmb) {
+    int e[3] = {cmb % ne[0], d > 1 ? (cmb / ne[0]) % ne[1] : 0, d > 2 ? cmb / (ne[0] * ne[1]) : 0};
+    const AxisEl* E[3] = {&el[0][e[0]], d > 1 ? &el[1][e[1]] : nullptr, d > 2 ? &el[2][e[2]] : nullptr};
+    bool origin = true;
+    double width = 0.0, lo2 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      origin = origin && (E[i]->origin_l >= 0);
+      width = fmax(width, E[i]->hi - E[i]->lo);
+      lo2 += E[i]->lo * E[i]->lo;
+    }
+    if (origin) {
+      int l[3] = {E[0]->origin_l, d > 1 ? E[1]->origin_l : 0, d > 2 ? E[2]->origin_l : 0};
+      total += origin_element(P, l, E[0]->hi - E[0]->lo);
+      continue;
+    }
+    const int rule = pick_rule(sqrt(lo2) / width);
+    if (!CHK(rule, kNumRules)) continue;
+    const int q = rule_q(rule), off = rule_off(rule);
+    if (!CHK(q - 1, 20) || !CHK(off + q - 1, kRuleTotal)) continue;
+    // per-axis nodes and weighted basis values
+    double X[3][20], WB[3][20];
+    for (int i = 0; i < d; ++i) {
+      const double c = 0.5 * (E[i]->hi + E[i]->lo), hw = 0.5 * (E[i]->hi - E[i]->lo);
+      for (int g = 0; g < q; ++g) {
+        X[i][g] = c + hw * c_gl_x[off + g];
+        WB[i][g] = hw * c_gl_w[off + g] * basis_val(*E[i], X[i][g]);
+      }
+    }
+    double acc = 0.0;
+    if (d == 1) {
+      for (int g = 0; g < q; ++g) acc += WB[0][g] * mu_r2(X[0][g] * X[0][g], P);
+    } else if (d == 2) {
+      for (int g1 = 0; g1 < q; ++g1) {
+        double a1 = 0.0;
+        const double x1 = X[1][g1] * X[1][g1];
+        for (int g0 = 0; g0 < q; ++g0) a1 += WB[0][g0] * mu_r2(X[0][g0] * X[0][g0] + x1, P);
+        acc += WB[1][g1] * a1;
+      }
+    } else {
+      for (int g2 = 0; g2 < q; ++g2) {
+        double a2 = 0.0;
+        const double x2 = X[2][g2] * X[2][g2];
+        for (int g1 = 0; g1 < q; ++g1) {
+          double a1 = 0.0;
+          const double x12 = X[1][g1] * X[1][g1] + x2;
+          for (int g0 = 0; g0 < q; ++g0) a1 += WB[0][g0] * mu_r2(X[0][g0] * X[0][g0] + x12, P);
+          a2 += WB[1][g1] * a1;
+        }
+        acc += WB[2][g2] * a2;
+      }
+    }
+    total += acc;
+  }
+  if (CHK(idx, count)) omega[idx] = total;
+}
+
+// ---------------------------------------------------------------------------
+// Stencil: a_k = 2^{z(k)} omega_k / (h^2 |k|^2) (k != 0), plus the origin rule
+// a_{j e_i} += 2^{d-1} e_j omega_0 / (d (j h)^2), e = (1) for p <= 1 and
+// (4/3, -1/3) for p = 2.  Writes a_k, and per-block partial sums (Kahan) of
+// 2^{d-z(k)} a_k over k != 0 for the centre coefficient.
+// ---------------------------------------------------------------------------
+
+__global__ void k_stencil(WParams P, const double* __restrict__ omega, double* __restrict__ a,
+                          double* __restrict__ partial, int64_t count) {
+  __shared__ double sh[32];
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double contrib = 0.0;
+  if (idx < count && idx > 0) {
+    const int d = P.d;
+    const int64_t N1 = P.N + 1;
+    int64_t k[3] = {0, 0, 0}, rem = idx;
+    int z = 0, nzaxis = -1;
+    double k2 = 0.0;
+    for (int i = 0; i < d; ++i) {
+      k[i] = rem % N1;
+      rem /= N1;
+      if (k[i] == 0) ++z; else nzaxis = i;
+      k2 += (double)k[i] * (double)k[i];
+    }
+    double v = CHK(idx, count) ? ldexp(omega[idx], z) / (P.h * P.h * k2) : 0.0;
+    if (z == d - 1) {  // on an axis: k = j e_i
+      const int64_t j = k[nzaxis];
+      double e = 0.0;
+      if (P.p <= 1) e = (j == 1) ? 1.0 : 0.0;
+      else e = (j == 1) ? 4.0 / 3.0 : (j == 2 ? -1.0 / 3.0 : 0.0);
+      if (e != 0.0) v += ldexp(1.0, d - 1) * e * omega[0] / (d * (j * P.h) * (j * P.h));
+    }
+    if (CHK(idx, count)) a[idx] = v;
+    contrib = ldexp(v, d - z);
+  }
+  // block sum with pairwise tree (deterministic)
+  for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = contrib;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0 && CHK(blockIdx.x, gridDim.x)) partial[blockIdx.x] = v;
+  }
+}
+
+// a_0 = -sum(partials) - 2^d F_d, Kahan-compensated, one block.
+__global__ void k_centre(const double* __restrict__ partial, int64_t nparts, double far_term, double* a) {
+  __shared__ double sh_s[1024], sh_c[1024];
+  double s = 0.0, c = 0.0;
+  for (int64_t i = threadIdx.x; i < nparts; i += blockDim.x) {
+    double y = CHK(i, nparts) ? partial[i] - c : 0.0;
+    double t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  sh_s[threadIdx.x] = s;
+  sh_c[threadIdx.x] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0, C = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      double y = sh_s[i] - (C + sh_c[i]);
+      double t = S + y;
+      C = (t - S) - y;
+      S = t;
+    }
+    a[0] = -S - far_term;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Symbol: Lambda_raw[k] = sum_{j in (-(n-1)..n-1)^d} a_{|j|} e^{-2 pi i j.k/M}
+//       = prod-separable cosine sums  sum_{j=0}^{n-1} w_j a_j cos(2 pi j k / M),
+// w_0 = 1, w_j = 2; computed axis by axis, k in [0, M/2].
+// ---------------------------------------------------------------------------
+
+// compact copy of the [0, n)^d block of the generator
+__global__ void k_gen_block(const double* __restrict__ a, double* __restrict__ out, int d, int64_t N1, int64_t n,
+                            int64_t count) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  int64_t rem = idx, src = 0, mul = 1;
+  for (int i = 0; i < d; ++i) {
+    int64_t ki = rem % n;
+    rem /= n;
+    src += ki * mul;
+    mul *= N1;
+  }
+  int64_t tot = 1;
+  for (int i = 0; i < d; ++i) tot *= N1;
+  if (CHK(src, tot)) out[idx] = a[src];
+}
+
+// in: (A, n, B) -> out: (A, K, B)
+__global__ void k_cos_pass(const double* __restrict__ in, double* __restrict__ out, int64_t A, int64_t n,
+                           int64_t B, int64_t K, int64_t M, const double2* __restrict__ tw) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= A * K * B) return;
+  const int64_t b = idx % B;
+  const int64_t k = (idx / B) % K;
+  const int64_t a = idx / (B * K);
+  const double* src = in + a * n * B + b;
+  double s = 0.0;
+  int64_t t = 0;  // (j * k) mod M
+  for (int64_t j = 0; j < n; ++j) {
+    if (!CHK(t, M) || !CHK(a * n * B + j * B + b, A * n * B)) break;
+    double v = src[j * B] * tw[t].x;
+    s += (j == 0) ? v : 2.0 * v;
+    t += k;
+    if (t >= M) t -= M;
+  }
+  if (CHK(idx, A * K * B)) out[idx] = s;
+}
+
+__global__ void k_scale_symbol(const double* __restrict__ raw, double* __restrict__ l64, float* __restrict__ l32,
+                               double scale, int64_t count, double* __restrict__ partial_max) {
+  __shared__ double sh[32];
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (idx < count && CHK(idx, count)) {
+    double v = raw[idx] * scale;
+    l64[idx] = v;
+    l32[idx] = (float)v;
+    m = fabs(raw[idx]);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) partial_max[blockIdx.x] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host driver
+// ---------------------------------------------------------------------------
+
+static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int build_coefficients(frac_op* op, cudaStream_t st) {
+  FRAC_TRY(upload_rules());
+  FRAC_TRY(ensure_twiddles(op->logm));
+  const frac_problem& pr = op->prob;
+  WParams P;
+  P.d = pr.d;
+  P.p = pr.degree;
+  P.N = op->N;
+  P.h = pr.h;
+  P.alpha = pr.alpha;
+  P.lambda = pr.lambda;
+  P.beta = pr.d + pr.alpha - 2.0;
+  const int d = pr.d;
+  const int64_t ngen = op->ngen;
+  const double L = op->N * pr.h;
+  op->far_field = far_field(d, pr.alpha, L, pr.lambda);
+
+  double *omega = nullptr, *partial = nullptr;
+  const int TB = 256;
+  const int64_t nblk = ceil_div(ngen, TB);
+  FRAC_CUDA_TRY(cudaMallocAsync(&omega, ngen * sizeof(double), st));
+  FRAC_CUDA_TRY(cudaMallocAsync(&partial, nblk * sizeof(double), st));
+  k_weights<<<(unsigned)nblk, TB, 0, st>>>(P, omega, ngen);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  k_stencil<<<(unsigned)nblk, TB, 0, st>>>(P, omega, op->a, partial, ngen);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  k_centre<<<1, 1024, 0, st>>>(partial, nblk, std::ldexp(op->far_field, d), op->a);
+  FRAC_CUDA_TRY(cudaGetLastError());
+
+  // symbol
+  const int64_t n = op->n, K = op->K, M = op->M;
+  int64_t sz = 1;
+  for (int i = 0; i < d; ++i) sz *= n;
+  int64_t maxsz = sz;
+  {
+    int64_t s = sz;
+    for (int i = 0; i < d; ++i) {
+      s = s / n * K;
+      if (s > maxsz) maxsz = s;
+    }
+  }
+  double *bufA = nullptr, *bufB = nullptr;
+  FRAC_CUDA_TRY(cudaMallocAsync(&bufA, maxsz * sizeof(double), st));
+  FRAC_CUDA_TRY(cudaMallocAsync(&bufB, maxsz * sizeof(double), st));
+  k_gen_block<<<(unsigned)ceil_div(sz, TB), TB, 0, st>>>(op->a, bufA, d, op->N + 1, n, sz);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  const double2* tw = twiddles64(op->logm);
+  // pass over axis i (0 = fastest): shape (A, n, B) with B = K^i, A = n^{d-1-i}
+  int64_t B = 1;
+  for (int i = 0; i < d; ++i) {
+    int64_t A = 1;
+    for (int j = i + 1; j < d; ++j) A *= n;
+    const int64_t outsz = A * K * B;
+    k_cos_pass<<<(unsigned)ceil_div(outsz, TB), TB, 0, st>>>(bufA, bufB, A, n, B, K, M, tw);
+    FRAC_CUDA_TRY(cudaGetLastError());
+    std::swap(bufA, bufB);
+    B *= K;
+  }
+  // bufA holds Lambda_raw on [0, K)^d
+  const int64_t ns = op->nsym;
+  double Md = 1.0;
+  for (int i = 0; i < d; ++i) Md *= (double)M;
+  const double scale = -op->c / (d == 1 ? Md : 2.0 * Md);
+  const int64_t nb2 = ceil_div(ns, TB);
+  double* pmax = nullptr;
+  FRAC_CUDA_TRY(cudaMallocAsync(&pmax, nb2 * sizeof(double), st));
+  k_scale_symbol<<<(unsigned)nb2, TB, 0, st>>>(bufA, op->lam64, op->lam32, scale, ns, pmax);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  std::vector<double> hmax(nb2);
+  FRAC_CUDA_TRY(cudaMemcpyAsync(hmax.data(), pmax, nb2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FRAC_CUDA_TRY(cudaMemcpyAsync(&op->a0, op->a, sizeof(double), cudaMemcpyDeviceToHost, st));
+  FRAC_CUDA_TRY(cudaFreeAsync(omega, st));
+  FRAC_CUDA_TRY(cudaFreeAsync(partial, st));
+  FRAC_CUDA_TRY(cudaFreeAsync(bufA, st));
+  FRAC_CUDA_TRY(cudaFreeAsync(bufB, st));
+  FRAC_CUDA_TRY(cudaFreeAsync(pmax, st));
+  FRAC_CUDA_TRY(cudaStreamSynchronize(st));
+  {
+    unsigned long long line = 0;
+    long long index = 0;
+    FRAC_CUDA_TRY(cudaMemcpyFromSymbol(&line, g_fault_line, sizeof(line)));
+    if (line) {
+      FRAC_CUDA_TRY(cudaMemcpyFromSymbol(&index, g_fault_index, sizeof(index)));
+      const unsigned long long zero = 0;
+      FRAC_CUDA_TRY(cudaMemcpyToSymbol(g_fault_line, &zero, sizeof(zero)));
+      return record_check_failure("coeffs.cu", (int)line, index);
+    }
+  }
+  double m = 0.0;
+  for (double v : hmax) m = v > m ? v : m;
+  op->norm_bound = op->c * m;
+  return FRAC_OK;
+}
+
+}  // namespace frac

@@ -1,0 +1,77 @@
+// Shared definitions for the sm_103a fractional-Laplacian library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/frac.h"
+
+namespace frac {
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+template <typename T> using cplx_t = typename Cplx<T>::type;
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return C{a.x * s, a.y * s}; }
+
+// Records the text of a failed CUDA call for frac_error_detail(); returns the status.
+int record_cuda_error(cudaError_t e, const char* file, int line, const char* expr);
+// Records a failed device-side bounds check (file:line, index); returns FRAC_ECUDA.
+int record_check_failure(const char* file, int line, long long index);
+
+// Status propagation for host code.
+#define FRAC_CUDA_TRY(expr)                                                   \
+  do {                                                                        \
+    cudaError_t e_ = (expr);                                                  \
+    if (e_ != cudaSuccess) return record_cuda_error(e_, __FILE__, __LINE__, #expr); \
+  } while (0)
+
+#define FRAC_TRY(expr)            \
+  do {                            \
+    int s_ = (expr);              \
+    if (s_ != FRAC_OK) return s_; \
+  } while (0)
+
+inline int ilog2(int64_t m) {
+  int l = 0;
+  while ((int64_t(1) << l) < m) ++l;
+  return l;
+}
+
+// Twiddle tables exp(-2 pi i t / M), t in [0, M), FP64 and FP32, per M (device-resident,
+// built once per M and device, never freed).
+const double2* twiddles64(int logm);
+const float2* twiddles32(int logm);
+
+}  // namespace frac
+
+// Opaque operator object of the C ABI.
+struct frac_op {
+  frac_problem prob;
+  int64_t N;         // intervals per axis
+  int64_t n;         // interior points per axis
+  int64_t M;         // FFT length per axis
+  int logm;
+  int64_t K;         // M / 2 + 1
+  int64_t nd;        // n^d grid values
+  int64_t ngen;      // (N + 1)^d generator entries
+  int64_t nsym;      // K^d symbol entries
+  double c;          // c_{d,alpha}
+  double a0;
+  double far_field;
+  double norm_bound;
+  double* a;         // device, (N+1)^d FP64 generator
+  double* lam64;     // device, K^d FP64 scaled symbol
+  float* lam32;      // device, K^d FP32 scaled symbol
+  size_t device_bytes;
+  int device;
+};

@@ -1,0 +1,365 @@
+// Conjugate-gradient solves of A u = f (A symmetric positive definite; the
+// paper asks for an FFT-based fast solver for the Toeplitz system without
+// naming one, Example 3.2.3).
+//
+//   FRAC_PLAIN_F64: CG with the FP64 FFT apply.
+//   FRAC_MIXED_IR : iterative refinement: r64 = f - A64 u (FP64 apply), the
+//                   correction from CG with the FP32 FFT apply on r64 / ||r64||
+//                   to a relative reduction inner_tol, u += ||r64|| d, until the
+//                   true FP64 residual meets rtol.
+//
+// Every CG scalar lives on the device (struct CGState); the host launches
+// iterations in chunks and reads the state back between chunks; once a
+// kernel marks the state done, the remaining launches of the chunk are no-ops
+// for x and r.
+#include <cmath>
+#include <vector>
+
+#include "apply.cuh"
+
+namespace frac {
+
+struct CGState {
+  double rr;     // r.r
+  double pq;     // p.Ap
+  double alpha, beta;
+  double tol2;   // stop when rr <= tol2
+  int it, maxit, done, status;
+};
+
+constexpr int kRedBlocks = 1024;  // partial-sum slots of the two-stage reductions
+constexpr int kTB = 256;
+
+// ---- reductions -----------------------------------------------------------
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+// partial[b] = sum over this block's grid-stride share of a[i] * b[i]
+// (each thread accumulates in T, the block in FP64)
+template <typename T>
+__global__ void k_dot(const T* __restrict__ a, const T* __restrict__ b, int64_t n, double* __restrict__ partial,
+                      const CGState* st) {
+  __shared__ double sh[32];
+  if (st && st->done) return;
+  T acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  double s = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__device__ double sum_partials(const double* __restrict__ partial, int np, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) v += partial[i];
+  return block_sum(v, sh);
+}
+
+// pq = sum partials; alpha = rr / pq; breakdown check
+__global__ void k_cg_alpha(const double* __restrict__ partial, int np, CGState* st) {
+  __shared__ double sh[32];
+  if (st->done) return;
+  double pq = sum_partials(partial, np, sh);
+  if (threadIdx.x == 0) {
+    st->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      st->status = FRAC_EBREAKDOWN;
+      st->done = 1;
+    } else {
+      st->alpha = st->rr / pq;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha q; partial r.r
+template <typename T>
+__global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ q,
+                            int64_t n, double* __restrict__ partial, const CGState* st) {
+  __shared__ double sh[32];
+  if (st->done) return;
+  const T al = (T)st->alpha;
+  T acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += al * p[i];
+    T ri = r[i] - al * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  double s = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// rr_new = sum partials; beta = rr_new / rr; convergence / iteration cap
+__global__ void k_cg_beta(const double* __restrict__ partial, int np, CGState* st) {
+  __shared__ double sh[32];
+  if (st->done) return;
+  double rr = sum_partials(partial, np, sh);
+  if (threadIdx.x == 0) {
+    st->beta = rr / st->rr;
+    st->rr = rr;
+    st->it += 1;
+    if (!isfinite(rr)) {
+      st->status = FRAC_EBREAKDOWN;
+      st->done = 1;
+    } else if (rr <= st->tol2) {
+      st->done = 1;
+    } else if (st->it >= st->maxit) {
+      st->status = FRAC_ENOCONV;
+      st->done = 1;
+    }
+  }
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void k_cg_p(T* __restrict__ p, const T* __restrict__ r, int64_t n, const CGState* st) {
+  if (st->done) return;
+  const T be = (T)st->beta;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = r[i] + be * p[i];
+}
+
+// start: rr = sum partials (of r.r), tol2 = tol^2 * rr_ref (rr_ref < 0: use rr)
+__global__ void k_cg_start(const double* __restrict__ partial, int np, CGState* st, double tol, double rr_ref,
+                           int maxit) {
+  __shared__ double sh[32];
+  double rr = sum_partials(partial, np, sh);
+  if (threadIdx.x == 0) {
+    st->rr = rr;
+    st->tol2 = tol * tol * (rr_ref < 0.0 ? rr : rr_ref);
+    st->it = 0;
+    st->maxit = maxit;
+    st->status = FRAC_OK;
+    st->done = (rr <= st->tol2 || rr == 0.0) ? 1 : 0;
+    st->alpha = st->beta = st->pq = 0.0;
+  }
+}
+
+// ---- elementwise helpers --------------------------------------------------
+
+// r = f - Ay; partial r.r (all FP64)
+__global__ void k_residual(const double* __restrict__ f, const double* __restrict__ Ay, double* __restrict__ r,
+                           int64_t n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = f[i] - Ay[i];
+    r[i] = v;
+    acc += v * v;
+  }
+  double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_sum_to(const double* __restrict__ partial, int np, double* out) {
+  __shared__ double sh[32];
+  double s = sum_partials(partial, np, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// r32 = r64 * s (s = 1 / ||r64||, read from device), x32 = 0, p32 = r32
+__global__ void k_ir_scale_down(const double* __restrict__ r64, const double* __restrict__ nrm2, float* __restrict__ r32,
+                                float* __restrict__ p32, float* __restrict__ x32, int64_t n) {
+  const double s = 1.0 / sqrt(*nrm2);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float v = (float)(r64[i] * s);
+    r32[i] = v;
+    p32[i] = v;
+    x32[i] = 0.0f;
+  }
+}
+
+// u += ||r64|| * d32
+__global__ void k_ir_correct(double* __restrict__ u, const float* __restrict__ d32, const double* __restrict__ nrm2,
+                             int64_t n) {
+  const double s = sqrt(*nrm2);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    u[i] += s * (double)d32[i];
+}
+
+template <typename T>
+__global__ void k_copy2(const T* __restrict__ a, T* __restrict__ b, T* __restrict__ c, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    b[i] = a[i];
+    c[i] = a[i];
+  }
+}
+
+// ---- host drivers ---------------------------------------------------------
+
+static int red_blocks(int64_t n) {
+  int64_t b = (n + kTB * 4 - 1) / (kTB * 4);
+  if (b < 1) b = 1;
+  if (b > kRedBlocks) b = kRedBlocks;
+  return (int)b;
+}
+
+struct Ws {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  ~Ws() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+  template <typename P>
+  int get(P** out, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(&p, bytes, st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FRAC_ENOMEM : FRAC_ECUDA;
+    ptrs.push_back(p);
+    *out = (P*)p;
+    return FRAC_OK;
+  }
+};
+
+// CG on A_T x = b (x, r, p, q device vectors of length nd; r = b - A x0 and p = r
+// on entry).  Runs until the device state is done.  Returns FRAC_OK or FRAC_ECUDA;
+// the outcome is in the state.
+template <typename T>
+static int cg_run(const frac_op* op, T* x, T* r, T* p, T* q, void* apply_ws, CGState* dst, CGState* hst,
+                  double* partial, int* iters_total, cudaStream_t st) {
+  const int64_t nd = op->nd;
+  const int nb = red_blocks(nd);
+  int chunk = 4;
+  for (;;) {
+    for (int c = 0; c < chunk; ++c) {
+      FRAC_TRY(apply_t<T>(op, p, q, 1, apply_ws, st));
+      k_dot<T><<<nb, kTB, 0, st>>>(p, q, nd, partial, dst);
+      k_cg_alpha<<<1, kTB, 0, st>>>(partial, nb, dst);
+      k_cg_update<T><<<nb, kTB, 0, st>>>(x, r, p, q, nd, partial, dst);
+      k_cg_beta<<<1, kTB, 0, st>>>(partial, nb, dst);
+      k_cg_p<T><<<nb, kTB, 0, st>>>(p, r, nd, dst);
+    }
+    FRAC_CUDA_TRY(cudaGetLastError());
+    FRAC_CUDA_TRY(cudaMemcpyAsync(hst, dst, sizeof(CGState), cudaMemcpyDeviceToHost, st));
+    FRAC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hst->done) break;
+    if (chunk < 64) chunk *= 2;
+  }
+  *iters_total += hst->it;
+  return FRAC_OK;
+}
+
+int solve_device(const frac_op* op, const double* f, double* u, const frac_solve_opts* opts,
+                 frac_solve_info* info, cudaStream_t st) {
+  const int64_t nd = op->nd;
+  const int nb = red_blocks(nd);
+  const unsigned gb = (unsigned)nb;
+  Ws ws{st, {}};
+  double *r64, *Au64, *partial, *scal;
+  CGState *dst, *hst = nullptr;
+  void* ws64;
+  FRAC_TRY(ws.get(&r64, nd * sizeof(double)));
+  FRAC_TRY(ws.get(&Au64, nd * sizeof(double)));
+  FRAC_TRY(ws.get(&partial, kRedBlocks * sizeof(double)));
+  FRAC_TRY(ws.get(&scal, 4 * sizeof(double)));
+  FRAC_TRY(ws.get(&dst, sizeof(CGState)));
+  FRAC_TRY(ws.get(&ws64, apply_workspace_bytes(op, FRAC_F64, 1)));
+  FRAC_CUDA_TRY(cudaMallocHost(&hst, sizeof(CGState) + 4 * sizeof(double)));
+  double* hscal = reinterpret_cast<double*>(hst + 1);
+  struct HostFree {
+    void* p;
+    ~HostFree() { if (p) cudaFreeHost(p); }
+  } hf{hst};
+
+  // ||f||^2
+  k_dot<double><<<gb, kTB, 0, st>>>(f, f, nd, partial, nullptr);
+  k_sum_to<<<1, kTB, 0, st>>>(partial, nb, scal + 0);
+  // initial residual r64 = f - A u (or f)
+  if (opts->use_x0) {
+    FRAC_TRY(apply_t<double>(op, u, Au64, 1, ws64, st));
+  } else {
+    FRAC_CUDA_TRY(cudaMemsetAsync(u, 0, nd * sizeof(double), st));
+    FRAC_CUDA_TRY(cudaMemsetAsync(Au64, 0, nd * sizeof(double), st));
+  }
+  k_residual<<<gb, kTB, 0, st>>>(f, Au64, r64, nd, partial);
+  k_sum_to<<<1, kTB, 0, st>>>(partial, nb, scal + 1);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  FRAC_CUDA_TRY(cudaMemcpyAsync(hscal, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FRAC_CUDA_TRY(cudaStreamSynchronize(st));
+  const double fnorm = std::sqrt(hscal[0]);
+  double rnorm = std::sqrt(hscal[1]);
+  info->iters = 0;
+  info->outer = 0;
+  info->status = FRAC_OK;
+  if (fnorm == 0.0) {
+    FRAC_CUDA_TRY(cudaMemsetAsync(u, 0, nd * sizeof(double), st));
+    info->rel_resid = 0.0;
+    FRAC_CUDA_TRY(cudaStreamSynchronize(st));
+    return FRAC_OK;
+  }
+  const double rtol = opts->rtol;
+  int iters = 0;
+
+  if (opts->precision == FRAC_PLAIN_F64) {
+    double *p, *q;
+    FRAC_TRY(ws.get(&p, nd * sizeof(double)));
+    FRAC_TRY(ws.get(&q, nd * sizeof(double)));
+    int restarts = 0;
+    while (rnorm > rtol * fnorm && iters < opts->max_iter && restarts < 8) {
+      // CG on the current residual; the recursive residual is checked against rtol ||f||
+      k_copy2<double><<<gb, kTB, 0, st>>>(r64, p, q, nd);  // p = r (q overwritten by the apply)
+      k_dot<double><<<gb, kTB, 0, st>>>(r64, r64, nd, partial, nullptr);
+      k_cg_start<<<1, kTB, 0, st>>>(partial, nb, dst, rtol * fnorm / std::max(rnorm, 1e-300), -1.0,
+                                    opts->max_iter - iters);
+      FRAC_TRY(cg_run<double>(op, u, r64, p, q, ws64, dst, hst, partial, &iters, st));
+      if (hst->status == FRAC_EBREAKDOWN) {
+        info->status = FRAC_EBREAKDOWN;
+        break;
+      }
+      // true residual
+      FRAC_TRY(apply_t<double>(op, u, Au64, 1, ws64, st));
+      k_residual<<<gb, kTB, 0, st>>>(f, Au64, r64, nd, partial);
+      k_sum_to<<<1, kTB, 0, st>>>(partial, nb, scal + 1);
+      FRAC_CUDA_TRY(cudaMemcpyAsync(hscal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+      FRAC_CUDA_TRY(cudaStreamSynchronize(st));
+      rnorm = std::sqrt(hscal[1]);
+      ++restarts;
+    }
+  } else {
+    float *x32, *r32, *p32, *q32;
+    void* ws32;
+    FRAC_TRY(ws.get(&x32, nd * sizeof(float)));
+    FRAC_TRY(ws.get(&r32, nd * sizeof(float)));
+    FRAC_TRY(ws.get(&p32, nd * sizeof(float)));
+    FRAC_TRY(ws.get(&q32, nd * sizeof(float)));
+    FRAC_TRY(ws.get(&ws32, apply_workspace_bytes(op, FRAC_F32, 1)));
+    const double inner = opts->inner_tol > 0.0 ? opts->inner_tol : 1e-4;
+    int outer = 0;
+    while (rnorm > rtol * fnorm && iters < opts->max_iter && outer < 100) {
+      // inner FP32 CG on A d = r / ||r||
+      k_ir_scale_down<<<gb, kTB, 0, st>>>(r64, scal + 1, r32, p32, x32, nd);
+      k_dot<float><<<gb, kTB, 0, st>>>(r32, r32, nd, partial, nullptr);
+      k_cg_start<<<1, kTB, 0, st>>>(partial, nb, dst, inner, -1.0, opts->max_iter - iters);
+      FRAC_TRY(cg_run<float>(op, x32, r32, p32, q32, ws32, dst, hst, partial, &iters, st));
+      k_ir_correct<<<gb, kTB, 0, st>>>(u, x32, scal + 1, nd);
+      // true FP64 residual
+      FRAC_TRY(apply_t<double>(op, u, Au64, 1, ws64, st));
+      k_residual<<<gb, kTB, 0, st>>>(f, Au64, r64, nd, partial);
+      k_sum_to<<<1, kTB, 0, st>>>(partial, nb, scal + 1);
+      FRAC_CUDA_TRY(cudaGetLastError());
+      FRAC_CUDA_TRY(cudaMemcpyAsync(hscal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+      FRAC_CUDA_TRY(cudaStreamSynchronize(st));
+      double prev = rnorm;
+      rnorm = std::sqrt(hscal[1]);
+      ++outer;
+      if (!(rnorm < prev) && outer > 3) break;  // refinement stagnated
+    }
+    info->outer = outer;
+  }
+  info->iters = iters;
+  info->rel_resid = rnorm / fnorm;
+  if (info->status == FRAC_OK && !(info->rel_resid <= rtol)) info->status = FRAC_ENOCONV;
+  return FRAC_OK;
+}
+
+}  // namespace frac

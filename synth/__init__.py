@@ -46,7 +46,10 @@ def ball_power_rhs(d: int, n: int, alpha: float) -> np.ndarray:
 
 def smooth_field(d: int, n: int, seed: int, modes: int = 32, kmax: int = 16) -> np.ndarray:
     """u = sum_{j<modes} c_j cos(pi k_j . x + phi_j), k_j uniform on
-    {-kmax..kmax}^d minus 0, c_j ~ N(0,1) / (1 + |k_j|^2), phi_j ~ U(0, 2 pi)."""
+    {-kmax..kmax}^d minus 0, c_j ~ N(0,1) / (1 + |k_j|^2), phi_j ~ U(0, 2 pi).
+
+    Evaluated separably: cos(a_1 + ... + a_d) is expanded into products of
+    cos(a_i) and sin(a_i) along each axis (axis 0 carries phi_j)."""
     rng = np.random.default_rng(seed)
     ks = []
     while len(ks) < modes:
@@ -57,11 +60,20 @@ def smooth_field(d: int, n: int, seed: int, modes: int = 32, kmax: int = 16) -> 
     cs = rng.standard_normal(modes) / (1.0 + np.sum(ks * ks, axis=1))
     phis = rng.uniform(0.0, 2.0 * math.pi, size=modes)
     x = interior_grid(n)
-    axes = np.meshgrid(*([x] * d), indexing="ij")
-    u = np.zeros((n,) * d)
-    for k, c, ph in zip(ks, cs, phis):
-        arg = ph + math.pi * sum(k[i] * axes[i] for i in range(d))
-        u += c * np.cos(arg)
+    ang = [math.pi * ks[:, i:i + 1] * x[None, :] for i in range(d)]      # (modes, n) per axis
+    ang[0] = ang[0] + phis[:, None]
+    C = [np.cos(a) for a in ang]
+    S = [np.sin(a) for a in ang]
+    if d == 1:
+        return cs @ C[0]
+    if d == 2:
+        # cos(a+b) = cos a cos b - sin a sin b
+        return (C[0].T * cs) @ C[1] - (S[0].T * cs) @ S[1]
+    # cos(a+b+c) = cos a cos b cos c - cos a sin b sin c - sin a cos b sin c - sin a sin b cos c
+    u = np.zeros((n, n, n))
+    for sa, sb, sc, sg in ((C, C, C, 1.0), (C, S, S, -1.0), (S, C, S, -1.0), (S, S, C, -1.0)):
+        ab = np.einsum("ji,jk->jik", sa[0] * cs[:, None], sb[1])          # (modes, n, n)
+        u += sg * np.einsum("jik,jl->ikl", ab, sc[2])
     return u
 
 

@@ -1,0 +1,164 @@
+"""GPU parity, solves: conjugate gradients (FP64) and FP32 CG inside FP64
+iterative refinement, through the C ABI, against the oracle and the paper.
+
+Bars: the relative residual recomputed by the oracle with its own dense
+operator, ||f - A_ref u||_2 / ||f||_2, is at most rtol plus the part that the
+measured generator difference can explain (c sum |a_gpu - a_ref| ||u|| / ||f||);
+solution errors reproduce the printed Tables 3-2-1 and 3-2-2 to the printed
+digit.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import frac_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _op(d, n, p, alpha, lam=0.0):
+    import paper_2103_03658_gb300 as fg
+    return fg.FracOp(d, n, alpha, degree=p, lam=lam)
+
+
+def _unit(v):
+    return 10.0 ** (math.floor(math.log10(abs(v))) - 4)
+
+
+def _table(name):
+    with open(os.path.join(GOLD, name + ".json")) as f:
+        return json.load(f)
+
+
+T321 = _table("table_3_2_1")
+CASES_321 = [(float(al), int(p), hh, T321["entries"][al][p][T321["h"].index(hh)])
+             for al in T321["entries"] for p in T321["entries"][al] for hh in (0.0625, 0.015625, 0.001953125)]
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+@pytest.mark.parametrize("al,p,hh,ref", CASES_321)
+def test_gpu_solve_reproduces_table_3_2_1(al, p, hh, ref, precision):
+    N = int(round(2 / hh))
+    n = N - 1
+    op = _op(1, n, p, al)
+    x = synth.interior_grid(n)
+    f = torch.ones(n, dtype=torch.float64, device="cuda")
+    u, info = op.solve(f, rtol=1e-12, precision=precision)
+    assert info["status"] == 0 and info["rel_resid"] <= 1e-12
+    err = np.max(np.abs(u.cpu().numpy() - (1 - x * x) ** (al / 2) / math.gamma(1 + al)))
+    assert abs(err - ref) <= 0.51 * _unit(ref), (err, ref)
+    op.close()
+
+
+@pytest.mark.parametrize("al", [0.7, 1.9])
+@pytest.mark.parametrize("hh", [0.125, 0.03125])
+def test_gpu_solve_reproduces_table_3_2_2(al, hh):
+    """2D, p = 1, g = exp(-|x|^2): the oracle supplies f - b (boundary data),
+    the GPU solves A u = f - b."""
+    G = _table("table_3_2_2")
+    ref = G["entries"][str(al)][G["h"].index(hh)]
+    N = int(round(2 / hh))
+    n = N - 1
+    a, c, h = O.build_operator(2, N, al, 1)
+    bvec = O.boundary_vector(2, N, h, al, a, c, lambda P: np.exp(-np.sum(P * P, axis=-1)))
+    r2 = O.radius2(N, 2)
+    rhs = O.fl_gaussian(2, al, r2) - bvec
+    op = _op(2, n, 1, al)
+    u, info = op.solve(torch.tensor(rhs, device="cuda"), rtol=1e-12, precision="mixed")
+    assert info["rel_resid"] <= 1e-12
+    err = np.max(np.abs(u.cpu().numpy() - np.exp(-r2)))
+    assert abs(err - ref) <= 0.51 * _unit(ref), (err, ref)
+    op.close()
+
+
+SOLVE_CASES = [(1, 127, 0, 0.3, 0.0), (1, 1023, 1, 1.5, 0.0), (1, 511, 2, 1.9, 1.2), (2, 31, 1, 1.2, 0.0),
+               (2, 45, 2, 0.5, 0.7), (2, 63, 0, 1.8, 0.0), (3, 9, 1, 0.4, 0.0), (3, 15, 2, 1.6, 0.3)]
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+@pytest.mark.parametrize("d,n,p,alpha,lam", SOLVE_CASES)
+def test_gpu_solve_residual_recomputed_by_oracle(d, n, p, alpha, lam, precision):
+    N = n + 1
+    a = O.stencil(d, N, 2.0 / N, alpha, p, lam, q=20 if d < 3 else 12)
+    c = O.c_dalpha(d, alpha)
+    f = synth.smooth_field(d, n, 2103 + n) + 0.5
+    op = _op(d, n, p, alpha, lam)
+    u, info = op.solve(torch.tensor(f, device="cuda"), rtol=1e-10, precision=precision)
+    assert info["status"] == 0 and info["rel_resid"] <= 1e-10
+    u = u.cpu().numpy()
+    A = O.operator_matrix(a, c, n)
+    res = np.linalg.norm(f.reshape(-1) - A @ u.reshape(-1)) / np.linalg.norm(f)
+    da = np.abs(op.generator() - a)
+    K = np.indices(da.shape)
+    slack = c * float(np.sum(2.0 ** np.sum(K > 0, axis=0) * da)) * np.linalg.norm(u) / np.linalg.norm(f)
+    assert res <= 1e-10 * 1.05 + 2 * slack, (res, slack)
+    if n ** d <= 4096:
+        uref = O.solve_dense(a, c, f)
+        kappa_bound = O.norm_bound(a, c, n) * np.linalg.norm(uref) / np.linalg.norm(f)
+        assert np.linalg.norm(u - uref) <= 2 * kappa_bound * (1e-10 + slack) * np.linalg.norm(uref)
+    op.close()
+
+
+def test_solve_edge_cases():
+    import paper_2103_03658_gb300 as fg
+    op = _op(1, 63, 1, 1.0)
+    z = torch.zeros(63, dtype=torch.float64, device="cuda")
+    u, info = op.solve(z)
+    assert info["rel_resid"] == 0.0 and float(u.abs().max()) == 0.0
+    f = torch.ones(63, dtype=torch.float64, device="cuda")
+    u, info = op.solve(f, max_iter=2, precision="f64")
+    assert info["status"] == 4 and info["iters"] <= 2          # FRAC_ENOCONV, last iterate kept
+    bad = f.clone()
+    bad[5] = float("nan")
+    with pytest.raises(fg.FracError):
+        op.solve(bad)
+    # warm start from the converged solution: no further iterations needed
+    u, info = op.solve(f, rtol=1e-10)
+    u2, info2 = op.solve(f, u=u.clone(), rtol=1e-10)
+    assert info2["iters"] == 0 and info2["rel_resid"] <= 1e-10
+    op.close()
+
+
+@pytest.mark.parametrize("alpha", [0.4, 1.6])
+def test_gpu_mixed_solve_3d_full_size(alpha):
+    """255^3 unknowns on a 512^3 FFT grid, p = 1, f from u = (1-|x|^2)_+^{1+alpha/2}:
+    mixed-precision solve to a 1e-10 FP64 residual; the solution error against
+    the exact solution is the discretization error (checked O(h) small)."""
+    d, n = 3, 255
+    op = _op(d, n, 1, alpha)
+    f = torch.tensor(synth.ball_power_rhs(d, n, alpha), device="cuda")
+    u, info = op.solve(f, rtol=1e-10, precision="mixed", inner_tol=1e-4)
+    assert info["status"] == 0 and info["rel_resid"] <= 1e-10
+    ue = torch.tensor(synth.ball_power(d, n, 1 + alpha / 2), device="cuda")
+    assert float((u - ue).abs().max()) < 2e-2
+    # the FP64 residual of the returned u, recomputed with the FP64 apply
+    r = f - op.apply(u)
+    assert float(r.norm() / f.norm()) <= 1e-10 * 1.01
+    op.close()
+
+
+def test_solve_batch_matches_single_solves():
+    import paper_2103_03658_gb300 as fg
+    probs = [(1, 255, 1, 0.7, 0.0), (2, 31, 2, 1.3, 0.4), (1, 100, 0, 1.9, 0.0), (3, 7, 1, 0.5, 0.0)]
+    ops = [_op(*p) for p in probs]
+    fs = [torch.tensor(synth.smooth_field(p[0], p[1], 7 + i) + 1.0, device="cuda") for i, p in enumerate(probs)]
+    us = [torch.empty_like(f) for f in fs]
+    infos = fg.solve_batch(ops, fs, us, rtol=1e-10)
+    for op, f, u, info in zip(ops, fs, us, infos):
+        assert info["status"] == 0 and info["rel_resid"] <= 1e-10
+        u1, _ = op.solve(f, rtol=1e-10)
+        assert float((u1 - u).norm() / u1.norm()) <= 1e-8
+        op.close()
