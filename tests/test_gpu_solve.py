@@ -56,8 +56,10 @@ def test_gpu_solve_reproduces_table_3_2_1(al, p, hh, ref, precision):
     op = _op(1, n, p, al)
     x = synth.interior_grid(n)
     f = torch.ones(n, dtype=torch.float64, device="cuda")
-    u, info = op.solve(f, rtol=1e-12, precision=precision)
-    assert info["status"] == 0 and info["rel_resid"] <= 1e-12
+    # 1e-11: plain FP64 CG cannot always drive the true residual of kappa ~ 1e5 systems to
+    # 1e-12; ||u - u_h|| <= ||A^{-1}|| 1e-11 ||f|| stays far below the printed digits
+    u, info = op.solve(f, rtol=1e-11, precision=precision)
+    assert info["status"] == 0 and info["rel_resid"] <= 1e-11
     err = np.max(np.abs(u.cpu().numpy() - (1 - x * x) ** (al / 2) / math.gamma(1 + al)))
     assert abs(err - ref) <= 0.51 * _unit(ref), (err, ref)
     op.close()
