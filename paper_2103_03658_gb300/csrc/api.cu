@@ -249,8 +249,27 @@ int frac_solve(const frac_op* op, const double* f, const double* g, double* u, c
 int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
                      const frac_solve_opts* opts, frac_solve_info* info, void* stream) {
   if (count < 0 || (count > 0 && (!ops || !f || !u || !opts || !info))) return FRAC_EINVAL;
-  int first = FRAC_OK;
+  if (count == 0) return FRAC_OK;
+  if (!(opts->rtol > 0.0) || opts->max_iter < 1) return FRAC_EINVAL;
+  if (opts->precision != FRAC_PLAIN_F64 && opts->precision != FRAC_MIXED_IR) return FRAC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  // 1D problems with device buffers: whole solves, one block each, one launch per FFT length
+  std::vector<int64_t> oned, rest;
   for (int64_t i = 0; i < count; ++i) {
+    if (!ops[i] || !f[i] || !u[i]) return FRAC_EINVAL;
+    if (ops[i]->prob.d == 1 && is_device_ptr(f[i]) && is_device_ptr(u[i])) oned.push_back(i);
+    else rest.push_back(i);
+  }
+  int first = FRAC_OK;
+  if (!oned.empty()) {
+    int s = solve_batch_1d((int64_t)oned.size(), ops, f, u, opts, info, oned.data(), st);
+    if (s != FRAC_OK) return s;
+    for (int64_t i : oned) {
+      if (std::isnan(info[i].rel_resid)) info[i].status = FRAC_EINVAL;
+      if (info[i].status != FRAC_OK && first == FRAC_OK) first = info[i].status;
+    }
+  }
+  for (int64_t i : rest) {
     int s = frac_solve(ops[i], f[i], nullptr, u[i], opts, &info[i], stream);
     if (s != FRAC_OK && first == FRAC_OK) first = s;
     if (s != FRAC_OK && s != FRAC_ENOCONV && s != FRAC_EBREAKDOWN) info[i].status = s;

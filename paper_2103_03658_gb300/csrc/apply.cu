@@ -21,12 +21,34 @@ namespace frac {
 
 using namespace fft;
 
+// Intermediate spectra are stored column-blocked: entry (row, k) of a slab of
+// `n` rows lives at (k / B) (n B) + row B + (k % B), B = 32 bytes / complex
+// size (4 for FP32, 2 for FP64).  A tile of B adjacent columns is then one
+// contiguous chunk, read and written with one lane per column and
+// consecutive lanes on consecutive rows, and every row segment is a full
+// 32-byte sector.  Every FFT below keeps the line in registers at entry and
+// exit (fft_reg): loads go straight from global memory into registers.
 // ---------------------------------------------------------------------------
-// d = 1: whole convolution per line
+
+template <typename T> __host__ __device__ constexpr int blk() { return 32 / (int)sizeof(cplx_t<T>); }
+
+// minimum resident blocks per SM requested from the compiler: at least 512 resident
+// threads for FP32 kernels and 256 for FP64 (registers capped at 128 and 255 per thread);
+// the row kernels ask for twice that
+template <typename T> __host__ __device__ constexpr int minb(int nt) {
+  return ((int)sizeof(T) == 4 ? 512 : 256) / nt > 1 ? ((int)sizeof(T) == 4 ? 512 : 256) / nt : 1;
+}
+// the row kernels hold one FFT per thread group and need fewer registers: 1024 / 512
+template <typename T> __host__ __device__ constexpr int minb_rows(int nt) {
+  return ((int)sizeof(T) == 4 ? 1024 : 512) / nt > 1 ? ((int)sizeof(T) == 4 ? 1024 : 512) / nt : 1;
+}
+
+// ---------------------------------------------------------------------------
+// d = 1: whole convolution per line (two vectors per complex line)
 // ---------------------------------------------------------------------------
 
 template <typename T, int LOGM, int LINES>
-__global__ void __launch_bounds__(LINES * tpl(LOGM))
+__global__ void __launch_bounds__(LINES * tpl(LOGM), minb<T>(LINES * tpl(LOGM)))
 k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const T* __restrict__ lam,
          const cplx_t<T>* __restrict__ tw) {
   using C = cplx_t<T>;
@@ -37,68 +59,87 @@ k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const
   C* buf = sm + line * LS;
   const int64_t va = 2 * ((int64_t)blockIdx.x * LINES + line), vb = va + 1;
   const bool ha = va < batch, hb = vb < batch;
+  C v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int x = tl + e * TPL;
     T re = (x < n && ha) ? u[va * n + x] : T(0);
     T im = (x < n && hb) ? u[vb * n + x] : T(0);
-    buf[pidx(x)] = C{re, im};
+    v[e] = C{re, im};
   }
-  __syncthreads();
-  run<C, LOGM, false>(buf, tl, tw);
+  fft_reg<C, LOGM, false>(v, buf, tl, tw);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int k = tl + e * TPL;
-    const int kr = k <= M / 2 ? k : M - k;
-    buf[pidx(k)] = cscale(buf[pidx(k)], lam[kr]);
+    v[e] = cscale(v[e], lam[k <= M / 2 ? k : M - k]);
   }
-  __syncthreads();
-  run<C, LOGM, true>(buf, tl, tw);
+  fft_reg<C, LOGM, true>(v, buf, tl, tw);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int x = tl + e * TPL;
     if (x < n) {
-      C v = buf[pidx(x)];
-      if (ha) y[va * n + x] = v.x;
-      if (hb) y[vb * n + x] = v.y;
+      if (ha) y[va * n + x] = v[e].x;
+      if (hb) y[vb * n + x] = v[e].y;
     }
   }
 }
 
+// column-blocked layout, slabs of n rows, KB = ceil(K / B) blocks per slab:
+// entry (row, k) at rowbase(row) + (k / B) n B + k % B
+template <int B>
+__device__ __forceinline__ int64_t wrow(int64_t row, int n, int KB) {
+  const int64_t slab = row / n, r = row - slab * n;
+  return slab * KB * (int64_t)n * B + r * B;
+}
+template <int B>
+__device__ __forceinline__ int64_t wcol(int k, int n) {
+  return (int64_t)(k / B) * n * B + (k % B);
+}
+
 // ---------------------------------------------------------------------------
 // Rows, forward: two real rows -> one complex FFT -> two half spectra
+// U0 = Z[k] + conj Z[M-k], U1 = -i (Z[k] - conj Z[M-k]), k in [0, M/2]
 // (stored without the 1/2 of the separation; the symbol carries it).
 // ---------------------------------------------------------------------------
 
 template <typename T, int LOGM, int LINES>
-__global__ void __launch_bounds__(LINES * tpl(LOGM))
-k_rows_fwd(const T* __restrict__ u, cplx_t<T>* __restrict__ W, int n, int64_t nrows,
+__global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
+k_rows_fwd(const T* __restrict__ u, cplx_t<T>* __restrict__ W, int n, int64_t nrows, int KB,
            const cplx_t<T>* __restrict__ tw) {
   using C = cplx_t<T>;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM);
-  constexpr int K = M / 2 + 1;
+  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM), B = blk<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
   C* buf = sm + line * LS;
   const int64_t r0 = 2 * ((int64_t)blockIdx.x * LINES + line), r1 = r0 + 1;
   const bool h0 = r0 < nrows, h1 = r1 < nrows;
+  C v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int x = tl + e * TPL;
     T re = (x < n && h0) ? u[r0 * n + x] : T(0);
     T im = (x < n && h1) ? u[r1 * n + x] : T(0);
-    buf[pidx(x)] = C{re, im};
+    v[e] = C{re, im};
   }
+  fft_reg<C, LOGM, false>(v, buf, tl, tw);
   __syncthreads();
-  run<C, LOGM, false>(buf, tl, tw);
-  // U0 = Z[k] + conj(Z[M-k]),  U1 = -i (Z[k] - conj(Z[M-k])),  k in [0, M/2]
-  for (int k = tl; k < K; k += TPL) {
-    const C z = buf[pidx(k)];
-    const C zc = cconj(buf[pidx((M - k) & (M - 1))]);
-    const C s = cadd(z, zc), dd = csub(z, zc);
-    if (h0) W[r0 * K + k] = s;
-    if (h1) W[r1 * K + k] = C{dd.y, -dd.x};
+#pragma unroll
+  for (int e = 0; e < E; ++e) buf[pidx(tl + e * TPL)] = v[e];
+  __syncthreads();
+  C* W0 = W + wrow<B>(r0, n, KB);
+  C* W1 = W + wrow<B>(r1, n, KB);
+#pragma unroll
+  for (int e = 0; e <= E / 2; ++e) {
+    const int k = tl + e * TPL;
+    if (k <= M / 2) {
+      const C z = buf[pidx(k)];
+      const C zc = cconj(buf[pidx((M - k) & (M - 1))]);
+      const C s = cadd(z, zc), dd = csub(z, zc);
+      const int64_t kc = wcol<B>(k, n);
+      if (h0) W0[kc] = s;
+      if (h1) W1[kc] = C{dd.y, -dd.x};
+    }
   }
 }
 
@@ -108,120 +149,137 @@ k_rows_fwd(const T* __restrict__ u, cplx_t<T>* __restrict__ W, int n, int64_t nr
 // ---------------------------------------------------------------------------
 
 template <typename T, int LOGM, int LINES>
-__global__ void __launch_bounds__(LINES * tpl(LOGM))
-k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nrows,
+__global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
+k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nrows, int KB,
            const cplx_t<T>* __restrict__ tw) {
   using C = cplx_t<T>;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM);
-  constexpr int K = M / 2 + 1;
+  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM), B = blk<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
   C* buf = sm + line * LS;
   const int64_t r0 = 2 * ((int64_t)blockIdx.x * LINES + line), r1 = r0 + 1;
   const bool h0 = r0 < nrows, h1 = r1 < nrows;
+  C v[E];
+  const C* W0 = W + wrow<B>(h0 ? r0 : 0, n, KB);
+  const C* W1 = W + wrow<B>(h1 ? r1 : 0, n, KB);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int x = tl + e * TPL;
     const int k = x <= M / 2 ? x : M - x;
-    C v0 = h0 ? W[r0 * K + k] : C{0, 0};
-    C v1 = h1 ? W[r1 * K + k] : C{0, 0};
+    const int64_t kc = wcol<B>(k, n);
+    C v0 = h0 ? W0[kc] : C{0, 0};
+    C v1 = h1 ? W1[kc] : C{0, 0};
     if (x > M / 2) {
       v0 = cconj(v0);
       v1 = cconj(v1);
     }
-    buf[pidx(x)] = C{v0.x - v1.y, v0.y + v1.x};  // v0 + i v1
+    v[e] = C{v0.x - v1.y, v0.y + v1.x};  // v0 + i v1
   }
-  __syncthreads();
-  run<C, LOGM, true>(buf, tl, tw);
+  fft_reg<C, LOGM, true>(v, buf, tl, tw);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int x = tl + e * TPL;
     if (x < n) {
-      const C v = buf[pidx(x)];
-      if (h0) y[r0 * n + x] = v.x;
-      if (h1) y[r1 * n + x] = v.y;
+      if (h0) y[r0 * n + x] = v[e].x;
+      if (h1) y[r1 * n + x] = v[e].y;
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Columns: TILE adjacent columns per block, one line per column.
-// Element j of column c of outer slab o lives at base + o * os + j * es + c.
-// MODE 0: pad len_in -> M, FFT, store M.
-// MODE 1: pad len_in -> M, FFT, * Lambda, iFFT, store len_out.
-// MODE 2: iFFT of all M, store len_out.
+// Columns: one tile of B adjacent columns per block, TPL threads per column
+// (lane order: column fastest).  Modes:
+//   SYM2 (d = 2): slab o = field, pad n -> M, FFT, * Lambda[kr][k1], iFFT, keep n; in place.
+//   YFWD (d = 3): slab o = (b, j3) of W1, pad n -> M, FFT along j2, all M k2 to W2,
+//                 W2 column c = k2 Kp + k1 (Kp = KB B), column-blocked with n rows (j3).
+//   ZSYM (d = 3): W2 column tile of field o, pad n -> M along j3, FFT, * Lambda[k3r][k2r][k1],
+//                 iFFT, keep n; in place.
+//   YINV (d = 3): slab o = (b, j3): M entries k2 of W2 columns k1, iFFT, first n (j2) to W1.
 // ---------------------------------------------------------------------------
 
+enum ColMode { SYM2 = 0, YFWD = 1, ZSYM = 2, YINV = 3 };
+
 struct ColArgs {
-  int64_t ncols, nouter;
-  int64_t os_in, es_in, os_out, es_out;
-  int len_in, len_out;
-  int K;        // symbol extent per axis (M/2 + 1)
-  int sym3d;    // 0: Lambda[kr][c] (d = 2); 1: Lambda[kr][c2r][c1], c = c2 K + c1 (d = 3)
+  int n, K, KB;      // interior points, symbol extent M/2+1, column blocks per W1 slab
+  int64_t tiles;     // column tiles per slab
+  int64_t nb;        // batch (fields)
 };
 
-template <typename T, int LOGM, int TILE, int MODE>
-__global__ void __launch_bounds__(TILE * tpl(LOGM))
+template <typename T, int LOGM, int MODE>
+__global__ void __launch_bounds__(blk<T>() * tpl(LOGM), minb<T>(blk<T>() * tpl(LOGM)))
 k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw) {
   using C = cplx_t<T>;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM);
-  constexpr int NT = TILE * TPL;
+  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride_tile(LOGM), B = blk<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* sm = reinterpret_cast<C*>(smem_raw);
-  const int64_t tiles = (A.ncols + TILE - 1) / TILE;
-  const int64_t o = blockIdx.x / tiles;
-  const int64_t c0 = (blockIdx.x % tiles) * TILE;
-  const C* src = in + o * A.os_in + c0;
-  // load (coalesced over columns)
-  const int len_load = (MODE == 2) ? M : A.len_in;
-  for (int idx = threadIdx.x; idx < len_load * TILE; idx += NT) {
-    const int cl = idx % TILE, j = idx / TILE;
-    C v = (c0 + cl < A.ncols) ? src[(int64_t)j * A.es_in + cl] : C{0, 0};
-    sm[cl * LS + pidx(j)] = v;
+  const int cl = threadIdx.x % B, tl = threadIdx.x / B;
+  C* buf = sm + cl * LS;
+  const int64_t o = blockIdx.x / A.tiles, tile = blockIdx.x % A.tiles;
+  const int n = A.n, K = A.K, KB = A.KB, Kp = KB * B;
+  const int64_t nB = (int64_t)n * B;
+  const int64_t W2slab = (int64_t)M * KB * nB;  // one field of W2
+  C v[E];
+  // ---- column identity and load
+  int k1 = 0, k2r = 0;
+  bool live = true;
+  if (MODE == SYM2 || MODE == YFWD || MODE == YINV) {
+    k1 = (int)tile * B + cl;
+    live = k1 < K;
+  } else {  // ZSYM: tile indexes W2 column blocks, c = k2 Kp + k1
+    const int64_t c = tile * B + cl;
+    const int k2 = (int)(c / Kp);
+    k1 = (int)(c % Kp);
+    k2r = k2 <= M / 2 ? k2 : M - k2;
+    live = k1 < K;
   }
-  if (MODE != 2) {
-    for (int idx = threadIdx.x; idx < (M - len_load) * TILE; idx += NT) {
-      const int cl = idx % TILE, j = len_load + idx / TILE;
-      sm[cl * LS + pidx(j)] = C{0, 0};
+  if (MODE == YINV) {
+    const int64_t b = o / n, j3 = o % n;
+    const C* src = in + b * W2slab + tile * nB + j3 * B + cl;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k2 = tl + e * TPL;
+      v[e] = live ? src[(int64_t)k2 * KB * nB] : C{0, 0};
+    }
+  } else {
+    const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl : in + (o * KB + tile) * nB + cl;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = tl + e * TPL;
+      v[e] = (live && j < n) ? src[(int64_t)j * B] : C{0, 0};
     }
   }
-  __syncthreads();
-  const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
-  C* buf = sm + line * LS;
-  if (MODE != 2) run<C, LOGM, false>(buf, tl, tw);
-  if (MODE == 1) {
-    const int64_t c = c0 + line;
-    const int64_t cc = c < A.ncols ? c : 0;
-    const T* lrow;
-    if (A.sym3d) {
-      const int64_t c2 = cc / A.K, c1 = cc % A.K;
-      const int64_t c2r = c2 <= M / 2 ? c2 : M - c2;
-      lrow = lam + c2r * A.K + c1;  // + kr * K * K
+  // ---- transforms
+  if (MODE != YINV) fft_reg<C, LOGM, false>(v, buf, tl, tw);
+  if (MODE == SYM2 || MODE == ZSYM) {
+    const T* lrow = (MODE == SYM2) ? lam + k1 : lam + (int64_t)k2r * K + k1;
+    const int64_t kstride = (MODE == SYM2) ? K : (int64_t)K * K;
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int k = tl + e * TPL;
-        const int kr = k <= M / 2 ? k : M - k;
-        buf[pidx(k)] = cscale(buf[pidx(k)], lrow[(int64_t)kr * A.K * A.K]);
-      }
-    } else {
-      lrow = lam + cc;
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int k = tl + e * TPL;
-        const int kr = k <= M / 2 ? k : M - k;
-        buf[pidx(k)] = cscale(buf[pidx(k)], lrow[(int64_t)kr * A.K]);
-      }
+    for (int e = 0; e < E; ++e) {
+      const int k = tl + e * TPL;
+      const int kr = k <= M / 2 ? k : M - k;
+      v[e] = cscale(v[e], live ? lrow[kr * kstride] : T(0));
     }
-    __syncthreads();
   }
-  if (MODE != 0) run<C, LOGM, true>(buf, tl, tw);
-  // store (coalesced over columns)
-  const int len_store = (MODE == 0) ? M : A.len_out;
-  C* dst = out + o * A.os_out + c0;
-  for (int idx = threadIdx.x; idx < len_store * TILE; idx += NT) {
-    const int cl = idx % TILE, j = idx / TILE;
-    if (c0 + cl < A.ncols) dst[(int64_t)j * A.es_out + cl] = sm[cl * LS + pidx(j)];
+  if (MODE != YFWD) fft_reg<C, LOGM, true>(v, buf, tl, tw);
+  // ---- store
+  if (!live) return;
+  if (MODE == YFWD) {
+    const int64_t b = o / n, j3 = o % n;
+    C* dst = out + b * W2slab + tile * nB + j3 * B + cl;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k2 = tl + e * TPL;
+      dst[(int64_t)k2 * KB * nB] = v[e];
+    }
+  } else {
+    C* dst = (MODE == ZSYM) ? out + o * W2slab + tile * nB + cl
+                            : out + (o * KB + tile) * nB + cl;  // SYM2 in place; YINV to W1 slab o
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = tl + e * TPL;
+      if (j < n) dst[(int64_t)j * B] = v[e];
+    }
   }
 }
 
@@ -232,15 +290,14 @@ k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam
 template <typename T, int LOGM>
 struct Cfg {
   static constexpr int LINE_BYTES = line_stride(LOGM) * (int)sizeof(cplx_t<T>);
-  // lines per block: aim for ~48-64 KB of shared memory and <= 512 threads
-  static constexpr int lines_for(int maxbytes) {
+  // lines per block for the row and 1D kernels: at most 48 KB of shared memory and 256 threads
+  static constexpr int lines_for(int maxbytes, int maxthreads) {
     int l = maxbytes / LINE_BYTES;
-    int lim = 512 / tpl(LOGM);
+    int lim = maxthreads / tpl(LOGM);
     l = l < lim ? l : lim;
     return l < 1 ? 1 : l;
   }
-  static constexpr int ROW_LINES = lines_for(64 * 1024);
-  static constexpr int TILE = lines_for(72 * 1024) >= 8 ? 8 : lines_for(72 * 1024);
+  static constexpr int ROW_LINES = lines_for(48 * 1024, 256);
 };
 
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -273,7 +330,7 @@ static int launch_conv1d(const T* u, T* y, int64_t n, int64_t batch, const T* la
 }
 
 template <typename T, int LOGM>
-static int launch_rows(bool fwd, const void* in, void* out, int64_t n, int64_t nrows, cudaStream_t st) {
+static int launch_rows(bool fwd, const void* in, void* out, int64_t n, int64_t nrows, int KB, cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int L = Cfg<T, LOGM>::ROW_LINES;
   const size_t sm = (size_t)L * Cfg<T, LOGM>::LINE_BYTES;
@@ -283,27 +340,30 @@ static int launch_rows(bool fwd, const void* in, void* out, int64_t n, int64_t n
   if (fwd) {
     auto kern = k_rows_fwd<T, LOGM, L>;
     FRAC_TRY(set_smem(kern, sm));
-    kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const T*)in, (C*)out, (int)n, nrows, tw_table<T>(LOGM));
+    kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const T*)in, (C*)out, (int)n, nrows, KB,
+                                                               tw_table<T>(LOGM));
   } else {
     auto kern = k_rows_inv<T, LOGM, L>;
     FRAC_TRY(set_smem(kern, sm));
-    kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const C*)in, (T*)out, (int)n, nrows, tw_table<T>(LOGM));
+    kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const C*)in, (T*)out, (int)n, nrows, KB,
+                                                               tw_table<T>(LOGM));
   }
   FRAC_CUDA_TRY(cudaGetLastError());
   return FRAC_OK;
 }
 
 template <typename T, int LOGM, int MODE>
-static int launch_cols(const void* in, void* out, const ColArgs& A, const T* lam, cudaStream_t st) {
+static int launch_cols(const void* in, void* out, const ColArgs& A, int64_t nouter, const T* lam, cudaStream_t st) {
   using C = cplx_t<T>;
-  constexpr int TILE = Cfg<T, LOGM>::TILE;
-  const size_t sm = (size_t)TILE * Cfg<T, LOGM>::LINE_BYTES;
-  auto kern = k_cols<T, LOGM, TILE, MODE>;
+  constexpr int B = blk<T>();
+  const size_t sm = (size_t)B * line_stride_tile(LOGM) * sizeof(C);
+  auto kern = k_cols<T, LOGM, MODE>;
   FRAC_TRY(set_smem(kern, sm));
-  const int64_t blocks = A.nouter * cdiv(A.ncols, TILE);
+  const int64_t blocks = nouter * A.tiles;
+  static const char* names[4] = {"cols_sym2", "cols_yfwd", "cols_zsym", "cols_yinv"};
   char nb[48];
-  prof::Scope ps(kname<T>(nb, MODE == 0 ? "cols_fwd" : (MODE == 1 ? "cols_sym" : "cols_inv"), LOGM), st);
-  kern<<<(unsigned)blocks, TILE * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, lam, tw_table<T>(LOGM));
+  prof::Scope ps(kname<T>(nb, names[MODE], LOGM), st);
+  kern<<<(unsigned)blocks, B * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, lam, tw_table<T>(LOGM));
   FRAC_CUDA_TRY(cudaGetLastError());
   return FRAC_OK;
 }
@@ -333,56 +393,79 @@ static int conv1d_any(int logm, const T* u, T* y, int64_t n, int64_t batch, cons
   FRAC_DISPATCH_LOGM(logm, 1, 13, (launch_conv1d<T, LG>(u, y, n, batch, lam, st)));
 }
 template <typename T>
-static int rows_any(int logm, bool fwd, const void* in, void* out, int64_t n, int64_t nrows, cudaStream_t st) {
-  FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_rows<T, LG>(fwd, in, out, n, nrows, st)));
+static int rows_any(int logm, bool fwd, const void* in, void* out, int64_t n, int64_t nrows, int KB, cudaStream_t st) {
+  FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_rows<T, LG>(fwd, in, out, n, nrows, KB, st)));
 }
 template <typename T, int MODE>
-static int cols_any(int logm, const void* in, void* out, const ColArgs& A, const T* lam, cudaStream_t st) {
-  FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_cols<T, LG, MODE>(in, out, A, lam, st)));
+static int cols_any(int logm, const void* in, void* out, const ColArgs& A, int64_t nouter, const T* lam,
+                    cudaStream_t st) {
+  if constexpr (MODE == SYM2) {
+    FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_cols<T, LG, MODE>(in, out, A, nouter, lam, st)));
+  } else {
+    FRAC_DISPATCH_LOGM(logm, 1, 9, (launch_cols<T, LG, MODE>(in, out, A, nouter, lam, st)));
+  }
+}
+
+template <typename T>
+static void layout(const frac_op* op, int64_t batch, int64_t& KB, int64_t& w1, int64_t& w2) {
+  constexpr int B = blk<T>();
+  const int64_t n = op->n, M = op->M, K = op->K;
+  KB = cdiv(K, B);
+  w1 = w2 = 0;
+  if (op->prob.d == 2) w1 = batch * KB * n * B;
+  if (op->prob.d == 3) {
+    w1 = batch * n * KB * n * B;
+    w2 = batch * M * KB * n * B;
+  }
 }
 
 size_t apply_workspace_bytes(const frac_op* op, int dtype, int64_t batch) {
-  const size_t cs = dtype == FRAC_F64 ? sizeof(double2) : sizeof(float2);
-  const int64_t n = op->n, M = op->M, K = op->K;
-  if (op->prob.d == 1) return 0;
-  if (op->prob.d == 2) return (size_t)batch * n * K * cs;
-  return (size_t)batch * ((size_t)n * n * K + (size_t)n * M * K) * cs;
+  int64_t KB, w1, w2;
+  if (dtype == FRAC_F64) {
+    layout<double>(op, batch, KB, w1, w2);
+    return (size_t)(w1 + w2) * sizeof(double2);
+  }
+  layout<float>(op, batch, KB, w1, w2);
+  return (size_t)(w1 + w2) * sizeof(float2);
 }
 
 template <typename T>
 int apply_t(const frac_op* op, const T* u, T* y, int64_t batch, void* ws, cudaStream_t st) {
   using C = cplx_t<T>;
+  constexpr int B = blk<T>();
   const int d = op->prob.d, logm = op->logm;
   const int64_t n = op->n, M = op->M, K = op->K;
   const T* lam = sym_table<T>(op);
   if (batch <= 0) return FRAC_OK;
   if (d == 1) return conv1d_any<T>(logm, u, y, n, batch, lam, st);
+  int64_t KB, w1, w2;
+  layout<T>(op, batch, KB, w1, w2);
   C* W1 = (C*)ws;
   if (d == 2) {
     const int64_t nrows = batch * n;
-    FRAC_TRY(rows_any<T>(logm, true, u, W1, n, nrows, st));
-    ColArgs A{K, batch, n * K, K, n * K, K, (int)n, (int)n, (int)K, 0};
-    FRAC_TRY((cols_any<T, 1>(logm, W1, W1, A, lam, st)));
-    FRAC_TRY(rows_any<T>(logm, false, W1, y, n, nrows, st));
+    FRAC_TRY(rows_any<T>(logm, true, u, W1, n, nrows, (int)KB, st));
+    ColArgs A{(int)n, (int)K, (int)KB, KB, batch};
+    FRAC_TRY((cols_any<T, SYM2>(logm, W1, W1, A, batch, lam, st)));
+    FRAC_TRY(rows_any<T>(logm, false, W1, y, n, nrows, (int)KB, st));
     return FRAC_OK;
   }
-  // d == 3
-  C* W2 = W1 + batch * n * n * K;
+  C* W2 = W1 + w1;
   const int64_t nrows = batch * n * n;
-  FRAC_TRY(rows_any<T>(logm, true, u, W1, n, nrows, st));
-  {  // y forward: outer = (b, j3), columns k1, elements j2
-    ColArgs A{K, batch * n, n * K, K, M * K, K, (int)n, (int)M, (int)K, 0};
-    FRAC_TRY((cols_any<T, 0>(logm, W1, W2, A, lam, st)));
+  FRAC_TRY(rows_any<T>(logm, true, u, W1, n, nrows, (int)KB, st));
+  {
+    ColArgs A{(int)n, (int)K, (int)KB, KB, batch};
+    FRAC_TRY((cols_any<T, YFWD>(logm, W1, W2, A, batch * n, lam, st)));
   }
-  {  // z: outer = b, columns (k2, k1), elements j3; symbol; in place
-    ColArgs A{M * K, batch, n * M * K, M * K, n * M * K, M * K, (int)n, (int)n, (int)K, 1};
-    FRAC_TRY((cols_any<T, 1>(logm, W2, W2, A, lam, st)));
+  {
+    ColArgs A{(int)n, (int)K, (int)KB, M * KB, batch};
+    FRAC_TRY((cols_any<T, ZSYM>(logm, W2, W2, A, batch, lam, st)));
   }
-  {  // y inverse: outer = (b, j3), columns k1, elements k2 -> j2 < n
-    ColArgs A{K, batch * n, M * K, K, n * K, K, (int)M, (int)n, (int)K, 0};
-    FRAC_TRY((cols_any<T, 2>(logm, W2, W1, A, lam, st)));
+  {
+    ColArgs A{(int)n, (int)K, (int)KB, KB, batch};
+    FRAC_TRY((cols_any<T, YINV>(logm, W2, W1, A, batch * n, lam, st)));
   }
-  FRAC_TRY(rows_any<T>(logm, false, W1, y, n, nrows, st));
+  FRAC_TRY(rows_any<T>(logm, false, W1, y, n, nrows, (int)KB, st));
+  (void)B;
   return FRAC_OK;
 }
 

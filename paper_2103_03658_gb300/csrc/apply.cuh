@@ -27,5 +27,9 @@ int apply_t(const frac_op* op, const T* u, T* y, int64_t batch, void* ws, cudaSt
 // solve.cu
 int solve_device(const frac_op* op, const double* f, double* u, const frac_solve_opts* opts,
                  frac_solve_info* info, cudaStream_t st);
+// Solves the 1D problems listed in idx[0..count) of (ops, f, u) (device pointers),
+// grouped by FFT length, one launch per group; fills info[idx[t]].
+int solve_batch_1d(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
+                   const frac_solve_opts* opts, frac_solve_info* info, const int64_t* idx, cudaStream_t st);
 
 }  // namespace frac

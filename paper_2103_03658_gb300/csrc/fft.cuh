@@ -34,6 +34,12 @@ __host__ __device__ constexpr int tpl(int logm) { return (1 << logm) / elems(log
 __host__ __device__ constexpr int line_stride(int logm) {
   return (1 << logm) + ((1 << logm) >> 4) + 1;
 }
+// Line stride for tiles whose lanes interleave 4 (FP32) or 2 (FP64) lines with the
+// line index fastest: a stride of 4 mod 16 puts the 16 lanes of a half-warp
+// (4 lines x 4 consecutive entries) in 16 distinct 8-byte bank slots.
+__host__ __device__ constexpr int line_stride_tile(int logm) {
+  return (1 << logm) + ((1 << logm) >> 4) + ((4 - (((1 << logm) + ((1 << logm) >> 4)) & 15)) & 15);
+}
 
 __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 
@@ -136,6 +142,102 @@ __device__ __forceinline__ void pass(C* __restrict__ buf, int tl, const C* __res
     for (int r = 0; r < R; ++r) buf[pidx(base + r * Ns)] = v[b * R + r];
   }
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Register-interface FFT: on entry and on exit thread tl of a line holds the
+// E entries tl + e TPL (e = 0..E-1) of the line in v[e]; only the passes in
+// between exchange through the line's shared-memory buffer.  Butterfly b of
+// a pass of radix R (j = tl + b TPL) takes its inputs j + r M/R from
+// v[b + r NB] in the first pass and leaves its outputs j + r M/R in
+// v[b + r NB] in the last pass (NB = E / R), so no permutation is needed at
+// either end.  The caller must not touch `buf` between the entry __syncthreads
+// and the return.
+// ---------------------------------------------------------------------------
+
+template <typename C, int LOGM, int P, bool INV>
+__device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
+  constexpr int M = 1 << LOGM;
+  constexpr int NP = npasses(LOGM);
+  constexpr int RB = pass_bits(LOGM, P);
+  constexpr int R = 1 << RB;
+  constexpr int NSB = pass_ns_bits(LOGM, P);
+  constexpr int Ns = 1 << NSB;
+  constexpr int E = elems(LOGM);
+  constexpr int TPL = tpl(LOGM);
+  constexpr int NB = E / R;
+  constexpr int TWS = M / (Ns * R);
+  constexpr bool FIRST = (P == 0), LAST = (P == NP - 1);
+  C w[E];
+  if constexpr (FIRST) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) w[b * R + r] = v[b + r * NB];
+  } else {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = tl + b * TPL;
+      if constexpr ((M / R) % 16 == 0) {  // pidx(j + c) = pidx(j) + pidx(c) for c a multiple of 16
+        const C* src = buf + pidx(j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) w[b * R + r] = src[r * (M / R) + ((r * (M / R)) >> 4)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) w[b * R + r] = buf[pidx(j + r * (M / R))];
+      }
+    }
+    if constexpr (!LAST) __syncthreads();  // every read of this pass done before its writes
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = tl + b * TPL;
+    const int k = j & (Ns - 1);
+    if constexpr (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C t = tw[r * k * TWS];
+        if (INV) t.y = -t.y;
+        w[b * R + r] = cmul(w[b * R + r], t);
+      }
+    }
+    dft<R, INV>(w + b * R);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b + r * NB] = w[b * R + r];
+    } else {
+      const int base = ((j >> NSB) << (NSB + RB)) + k;
+      if constexpr (Ns % 16 == 0) {
+        C* dst = buf + pidx(base);
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[r * Ns + ((r * Ns) >> 4)] = w[b * R + r];
+      } else if constexpr (Ns == 1 && 16 % R == 0) {  // base = j R: base + r stays in one 16-block
+        C* dst = buf + pidx(base);
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[r] = w[b * R + r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pidx(base + r * Ns)] = w[b * R + r];
+      }
+    }
+  }
+  if constexpr (!LAST) __syncthreads();  // writes visible to the next pass
+}
+
+template <typename C, int LOGM, bool INV, int P = 0>
+__device__ __forceinline__ void reg_passes(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
+  if constexpr (P < npasses(LOGM)) {
+    reg_pass<C, LOGM, P, INV>(v, buf, tl, tw);
+    reg_passes<C, LOGM, INV, P + 1>(v, buf, tl, tw);
+  }
+}
+
+// FFT of the line held in registers (see above); `buf` is the line's shared
+// buffer (line_stride(LOGM) entries), used only when there is more than one pass.
+template <typename C, int LOGM, bool INV>
+__device__ __forceinline__ void fft_reg(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
+  if constexpr (npasses(LOGM) > 1) __syncthreads();  // earlier users of buf are done
+  reg_passes<C, LOGM, INV>(v, buf, tl, tw);
 }
 
 template <typename C, int LOGM, bool INV, int P = 0>

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "apply.cuh"
+#include "solve1d.cuh"
 
 namespace frac {
 
@@ -249,8 +250,67 @@ static int cg_run(const frac_op* op, T* x, T* r, T* p, T* q, void* apply_ws, CGS
   return FRAC_OK;
 }
 
+// d = 1: the whole solve runs inside one thread block (solve1d.cu).
+static int solve_1d(const frac_op* op, const double* f, double* u, const frac_solve_opts* opts,
+                    frac_solve_info* info, cudaStream_t st) {
+  Ws ws{st, {}};
+  Solve1dTask* dt;
+  frac_solve_info* di;
+  FRAC_TRY(ws.get(&dt, sizeof(Solve1dTask)));
+  FRAC_TRY(ws.get(&di, sizeof(frac_solve_info)));
+  Solve1dTask t{f, u, op->lam32, op->lam64, di, opts->rtol, opts->inner_tol > 0.0 ? opts->inner_tol : 1e-4,
+                (int)op->n, opts->max_iter, opts->use_x0 ? 1 : 0};
+  FRAC_CUDA_TRY(cudaMemcpyAsync(dt, &t, sizeof(t), cudaMemcpyHostToDevice, st));
+  FRAC_TRY(solve1d_launch(op->logm, opts->precision == FRAC_MIXED_IR, dt, 1, st));
+  FRAC_CUDA_TRY(cudaMemcpyAsync(info, di, sizeof(frac_solve_info), cudaMemcpyDeviceToHost, st));
+  FRAC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (info->status == FRAC_EINVAL) {  // non-finite data: report through rel_resid as the other paths do
+    info->status = FRAC_OK;
+    info->rel_resid = NAN;
+  }
+  return FRAC_OK;
+}
+
+int solve_batch_1d(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
+                   const frac_solve_opts* opts, frac_solve_info* info, const int64_t* idx, cudaStream_t st) {
+  // group the listed problems by FFT length; one launch per group
+  Ws ws{st, {}};
+  std::vector<std::vector<int64_t>> groups(14);
+  for (int64_t t = 0; t < count; ++t) groups[ops[idx[t]]->logm].push_back(idx[t]);
+  frac_solve_info* di;
+  Solve1dTask* dt;
+  FRAC_TRY(ws.get(&di, count * sizeof(frac_solve_info)));
+  FRAC_TRY(ws.get(&dt, count * sizeof(Solve1dTask)));
+  std::vector<Solve1dTask> tasks;
+  std::vector<int64_t> order;
+  std::vector<std::pair<int, int64_t>> launches;  // (logm, first task)
+  for (int lg = 1; lg <= 13; ++lg) {
+    if (groups[lg].empty()) continue;
+    launches.emplace_back(lg, (int64_t)tasks.size());
+    for (int64_t i : groups[lg]) {
+      const frac_op* op = ops[i];
+      tasks.push_back(Solve1dTask{f[i], u[i], op->lam32, op->lam64, di + tasks.size(), opts->rtol,
+                                  opts->inner_tol > 0.0 ? opts->inner_tol : 1e-4, (int)op->n, opts->max_iter,
+                                  opts->use_x0 ? 1 : 0});
+      order.push_back(i);
+    }
+  }
+  FRAC_CUDA_TRY(cudaMemcpyAsync(dt, tasks.data(), tasks.size() * sizeof(Solve1dTask), cudaMemcpyHostToDevice, st));
+  for (size_t g = 0; g < launches.size(); ++g) {
+    const int64_t first = launches[g].second;
+    const int64_t last = g + 1 < launches.size() ? launches[g + 1].second : (int64_t)tasks.size();
+    FRAC_TRY(solve1d_launch(launches[g].first, opts->precision == FRAC_MIXED_IR, dt + first, (int)(last - first), st));
+  }
+  std::vector<frac_solve_info> hi(tasks.size());
+  FRAC_CUDA_TRY(cudaMemcpyAsync(hi.data(), di, hi.size() * sizeof(frac_solve_info), cudaMemcpyDeviceToHost, st));
+  FRAC_CUDA_TRY(cudaStreamSynchronize(st));
+  for (size_t t = 0; t < order.size(); ++t) info[order[t]] = hi[t];
+  return FRAC_OK;
+}
+
 int solve_device(const frac_op* op, const double* f, double* u, const frac_solve_opts* opts,
                  frac_solve_info* info, cudaStream_t st) {
+  if (op->prob.d == 1) return solve_1d(op, f, u, opts, info, st);
   const int64_t nd = op->nd;
   const int nb = red_blocks(nd);
   const unsigned gb = (unsigned)nb;
