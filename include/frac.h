@@ -119,6 +119,28 @@ int frac_op_generator(const frac_op* op, double* a, size_t count);
  */
 int frac_apply(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* stream);
 
+/*
+ * frac_apply_static -- the same y = A u as frac_apply, for callers that cannot
+ * allocate device memory when they apply the operator (a fixed memory budget
+ * reserved up front, a host framework that forbids device allocations after
+ * start-up, or a latency-critical loop that cannot let an allocation stall or
+ * fail mid-step).  This entry point has no counterpart in the paper.
+ * Its spectral scratch is one fixed 64 MiB device array inside the library,
+ * reserved on every GPU that loads the library and held until the process
+ * exits; it calls no cudaMalloc, cudaFree or other allocating routine.  The
+ * first call on a device looks up that array's device address (with the
+ * device current), so make that first call before any stream capture.
+ * u and y must be device buffers (host buffers would need staging memory).
+ * Every call shares the one array: calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race on it and must be
+ * serialised by the caller; nothing needs clearing between calls, because
+ * every scratch entry an apply reads is written earlier in the same apply.
+ * Errors: as frac_apply, plus FRAC_EINVAL for host buffers or for a batch
+ * whose scratch exceeds 64 MiB (frac_error_detail() gives the sizes; split
+ * the batch or call frac_apply).  d = 1 applies need no scratch at all.
+ */
+int frac_apply_static(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* stream);
+
 typedef struct frac_solve_opts {
   double rtol;          /* target ||f - A u||_2 / ||f||_2 (true residual, FP64); e.g. 1e-10 */
   int32_t max_iter;     /* cap on CG iterations (all inner iterations summed for MIXED_IR) */

@@ -78,6 +78,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.frac_op_generator.restype = i32
     lib.frac_apply.argtypes = [vp, vp, vp, i32, i64, vp]
     lib.frac_apply.restype = i32
+    lib.frac_apply_static.argtypes = [vp, vp, vp, i32, i64, vp]
+    lib.frac_apply_static.restype = i32
     lib.frac_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.frac_solve.restype = i32
     lib.frac_solve_batch.argtypes = [i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),

@@ -1,6 +1,7 @@
 // C ABI entry points (include/frac.h): argument validation, operator
 // lifecycle, staging of host buffers, dispatch to the device kernels.
 #include <cmath>
+#include <cstdarg>
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
@@ -67,6 +68,13 @@ int record_cuda_error(cudaError_t e, const char* file, int line, const char* exp
   std::snprintf(g_detail, sizeof(g_detail), "%s:%d %s -> %s (%s)", base, line, expr, cudaGetErrorName(e),
                 cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? FRAC_ENOMEM : FRAC_ECUDA;
+}
+
+void record_detail(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(g_detail, sizeof(g_detail), fmt, ap);
+  va_end(ap);
 }
 
 int record_check_failure(const char* file, int line, long long index) {

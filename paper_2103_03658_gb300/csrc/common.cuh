@@ -27,6 +27,8 @@ template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) 
 int record_cuda_error(cudaError_t e, const char* file, int line, const char* expr);
 // Records a failed device-side bounds check (file:line, index); returns FRAC_ECUDA.
 int record_check_failure(const char* file, int line, long long index);
+// Sets the text returned by frac_error_detail() (printf format).
+void record_detail(const char* fmt, ...);
 
 // Status propagation for host code.
 #define FRAC_CUDA_TRY(expr)                                                   \
