@@ -96,31 +96,90 @@ __device__ __forceinline__ int64_t wcol(int k, int n) {
   return (int64_t)(k / B) * n * B + (k % B);
 }
 
+// Block sum of a per-thread value (FP64), valid in every thread; red needs 32 doubles.
+__device__ __forceinline__ double block_sum_all(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// Every block stores its total in partials[blockIdx.x]; the last block to
+// arrive (counter) sums all of them in index order and calls fin(sum) in
+// thread 0, then resets the counter for the next use.
+template <typename F>
+__device__ __forceinline__ void last_block_reduce(double total, double* partials, unsigned int* counter, double* red,
+                                                  F fin) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = total;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) s += __ldcg(partials + i);
+  s = block_sum_all(s, red);
+  if (threadIdx.x == 0) {
+    fin(s);
+    *counter = 0;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Rows, forward: two real rows -> one complex FFT -> two half spectra
 // U0 = Z[k] + conj Z[M-k], U1 = -i (Z[k] - conj Z[M-k]), k in [0, M/2]
 // (stored without the 1/2 of the separation; the symbol carries it).
 // ---------------------------------------------------------------------------
 
-template <typename T, int LOGM, int LINES>
+// CG = true: the input is p = r + beta p (beta from st), written back to u (= p)
+// on the way in; the block returns at once when st->done is set.
+template <typename T, int LOGM, int LINES, bool CG>
 __global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
-k_rows_fwd(const T* __restrict__ u, cplx_t<T>* __restrict__ W, int n, int64_t nrows, int KB,
-           const cplx_t<T>* __restrict__ tw) {
+k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int64_t nrows, int KB,
+           const cplx_t<T>* __restrict__ tw, const T* __restrict__ r, const CGState* st) {
   using C = cplx_t<T>;
   constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM), B = blk<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (CG && st->done) return;
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
   C* buf = sm + line * LS;
   const int64_t r0 = 2 * ((int64_t)blockIdx.x * LINES + line), r1 = r0 + 1;
   const bool h0 = r0 < nrows, h1 = r1 < nrows;
   C v[E];
+  if constexpr (CG) {
+    const T be = (T)st->beta;
+    T* p = const_cast<T*>(u);
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int x = tl + e * TPL;
-    T re = (x < n && h0) ? u[r0 * n + x] : T(0);
-    T im = (x < n && h1) ? u[r1 * n + x] : T(0);
-    v[e] = C{re, im};
+    for (int e = 0; e < E; ++e) {
+      const int x = tl + e * TPL;
+      T re = T(0), im = T(0);
+      if (x < n && h0) {
+        re = r[r0 * n + x] + be * p[r0 * n + x];
+        p[r0 * n + x] = re;
+      }
+      if (x < n && h1) {
+        im = r[r1 * n + x] + be * p[r1 * n + x];
+        p[r1 * n + x] = im;
+      }
+      v[e] = C{re, im};
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int x = tl + e * TPL;
+      T re = (x < n && h0) ? u[r0 * n + x] : T(0);
+      T im = (x < n && h1) ? u[r1 * n + x] : T(0);
+      v[e] = C{re, im};
+    }
   }
   fft_reg<C, LOGM, false>(v, buf, tl, tw);
   __syncthreads();
@@ -148,13 +207,17 @@ k_rows_fwd(const T* __restrict__ u, cplx_t<T>* __restrict__ W, int n, int64_t nr
 // -> iFFT -> two real rows (first n entries).
 // ---------------------------------------------------------------------------
 
-template <typename T, int LOGM, int LINES>
+// CG = true: also per-block partial sums of p.y (p at the same points) into
+// partials[blockIdx.x]; the last block to finish sums them in index order and
+// sets st->pq, st->alpha (or flags a breakdown).  Returns at once when st->done.
+template <typename T, int LOGM, int LINES, bool CG>
 __global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
 k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nrows, int KB,
-           const cplx_t<T>* __restrict__ tw) {
+           const cplx_t<T>* __restrict__ tw, const T* __restrict__ p, CGState* st, double* partials) {
   using C = cplx_t<T>;
   constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM), B = blk<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (CG && st->done) return;
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
   C* buf = sm + line * LS;
@@ -177,13 +240,33 @@ k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nr
     v[e] = C{v0.x - v1.y, v0.y + v1.x};  // v0 + i v1
   }
   fft_reg<C, LOGM, true>(v, buf, tl, tw);
+  T dot = T(0);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int x = tl + e * TPL;
     if (x < n) {
-      if (h0) y[r0 * n + x] = v[e].x;
-      if (h1) y[r1 * n + x] = v[e].y;
+      if (h0) {
+        y[r0 * n + x] = v[e].x;
+        if (CG) dot += v[e].x * p[r0 * n + x];
+      }
+      if (h1) {
+        y[r1 * n + x] = v[e].y;
+        if (CG) dot += v[e].y * p[r1 * n + x];
+      }
     }
+  }
+  if constexpr (CG) {
+    double* red = reinterpret_cast<double*>(smem_raw);  // the FFT lines are no longer needed
+    const double total = block_sum_all(dot, red);
+    last_block_reduce(total, partials, &st->count_pq, red, [&](double pq) {
+      st->pq = pq;
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        st->status = FRAC_EBREAKDOWN;
+        st->done = 1;
+      } else {
+        st->alpha = st->rr / pq;
+      }
+    });
   }
 }
 
@@ -208,10 +291,12 @@ struct ColArgs {
 
 template <typename T, int LOGM, int MODE>
 __global__ void __launch_bounds__(blk<T>() * tpl(LOGM), minb<T>(blk<T>() * tpl(LOGM)))
-k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw) {
+k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw,
+       const CGState* st) {
   using C = cplx_t<T>;
   constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride_tile(LOGM), B = blk<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (st && st->done) return;
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int cl = threadIdx.x % B, tl = threadIdx.x / B;
   C* buf = sm + cl * LS;
@@ -329,31 +414,45 @@ static int launch_conv1d(const T* u, T* y, int64_t n, int64_t batch, const T* la
   return FRAC_OK;
 }
 
-template <typename T, int LOGM>
-static int launch_rows(bool fwd, const void* in, void* out, int64_t n, int64_t nrows, int KB, cudaStream_t st) {
+struct CgArgs {
+  const void* r = nullptr;   // rows_fwd: r of p = r + beta p
+  const void* p = nullptr;   // rows_inv: p of the p.q partials
+  CGState* st = nullptr;
+  double* partials = nullptr;
+};
+
+template <typename T, int LOGM, bool CG>
+static int launch_rows(bool fwd, const void* in, void* out, int64_t n, int64_t nrows, int KB, const CgArgs& cg,
+                       cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int L = Cfg<T, LOGM>::ROW_LINES;
   const size_t sm = (size_t)L * Cfg<T, LOGM>::LINE_BYTES;
   const int64_t pairs = cdiv(nrows, 2);
   char nb[48];
-  prof::Scope ps(kname<T>(nb, fwd ? "rows_fwd" : "rows_inv", LOGM), st);
+  prof::Scope ps(kname<T>(nb, fwd ? (CG ? "rows_fwd_cg" : "rows_fwd") : (CG ? "rows_inv_cg" : "rows_inv"), LOGM), st);
   if (fwd) {
-    auto kern = k_rows_fwd<T, LOGM, L>;
+    auto kern = k_rows_fwd<T, LOGM, L, CG>;
     FRAC_TRY(set_smem(kern, sm));
     kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const T*)in, (C*)out, (int)n, nrows, KB,
-                                                               tw_table<T>(LOGM));
+                                                               tw_table<T>(LOGM), (const T*)cg.r, cg.st);
   } else {
-    auto kern = k_rows_inv<T, LOGM, L>;
+    auto kern = k_rows_inv<T, LOGM, L, CG>;
     FRAC_TRY(set_smem(kern, sm));
     kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const C*)in, (T*)out, (int)n, nrows, KB,
-                                                               tw_table<T>(LOGM));
+                                                               tw_table<T>(LOGM), (const T*)cg.p, cg.st, cg.partials);
   }
   FRAC_CUDA_TRY(cudaGetLastError());
   return FRAC_OK;
 }
 
+template <typename T, int LOGM>
+static int64_t rows_grid(int64_t nrows) {
+  return cdiv(cdiv(nrows, 2), Cfg<T, LOGM>::ROW_LINES);
+}
+
 template <typename T, int LOGM, int MODE>
-static int launch_cols(const void* in, void* out, const ColArgs& A, int64_t nouter, const T* lam, cudaStream_t st) {
+static int launch_cols(const void* in, void* out, const ColArgs& A, int64_t nouter, const T* lam, const CGState* cgst,
+                       cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int B = blk<T>();
   const size_t sm = (size_t)B * line_stride_tile(LOGM) * sizeof(C);
@@ -363,7 +462,7 @@ static int launch_cols(const void* in, void* out, const ColArgs& A, int64_t nout
   static const char* names[4] = {"cols_sym2", "cols_yfwd", "cols_zsym", "cols_yinv"};
   char nb[48];
   prof::Scope ps(kname<T>(nb, names[MODE], LOGM), st);
-  kern<<<(unsigned)blocks, B * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, lam, tw_table<T>(LOGM));
+  kern<<<(unsigned)blocks, B * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, lam, tw_table<T>(LOGM), cgst);
   FRAC_CUDA_TRY(cudaGetLastError());
   return FRAC_OK;
 }
@@ -392,17 +491,35 @@ template <typename T>
 static int conv1d_any(int logm, const T* u, T* y, int64_t n, int64_t batch, const T* lam, cudaStream_t st) {
   FRAC_DISPATCH_LOGM(logm, 1, 13, (launch_conv1d<T, LG>(u, y, n, batch, lam, st)));
 }
+template <typename T, bool CG = false>
+static int rows_any(int logm, bool fwd, const void* in, void* out, int64_t n, int64_t nrows, int KB, cudaStream_t st,
+                    const CgArgs& cg = CgArgs{}) {
+  FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_rows<T, LG, CG>(fwd, in, out, n, nrows, KB, cg, st)));
+}
 template <typename T>
-static int rows_any(int logm, bool fwd, const void* in, void* out, int64_t n, int64_t nrows, int KB, cudaStream_t st) {
-  FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_rows<T, LG>(fwd, in, out, n, nrows, KB, st)));
+static int64_t rows_grid_any(int logm, int64_t nrows) {
+  switch (logm) {
+    case 1: return rows_grid<T, 1>(nrows);
+    case 2: return rows_grid<T, 2>(nrows);
+    case 3: return rows_grid<T, 3>(nrows);
+    case 4: return rows_grid<T, 4>(nrows);
+    case 5: return rows_grid<T, 5>(nrows);
+    case 6: return rows_grid<T, 6>(nrows);
+    case 7: return rows_grid<T, 7>(nrows);
+    case 8: return rows_grid<T, 8>(nrows);
+    case 9: return rows_grid<T, 9>(nrows);
+    case 10: return rows_grid<T, 10>(nrows);
+    case 11: return rows_grid<T, 11>(nrows);
+    default: return 0;
+  }
 }
 template <typename T, int MODE>
 static int cols_any(int logm, const void* in, void* out, const ColArgs& A, int64_t nouter, const T* lam,
-                    cudaStream_t st) {
+                    cudaStream_t st, const CGState* cgst = nullptr) {
   if constexpr (MODE == SYM2) {
-    FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_cols<T, LG, MODE>(in, out, A, nouter, lam, st)));
+    FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_cols<T, LG, MODE>(in, out, A, nouter, lam, cgst, st)));
   } else {
-    FRAC_DISPATCH_LOGM(logm, 1, 9, (launch_cols<T, LG, MODE>(in, out, A, nouter, lam, st)));
+    FRAC_DISPATCH_LOGM(logm, 1, 9, (launch_cols<T, LG, MODE>(in, out, A, nouter, lam, cgst, st)));
   }
 }
 
@@ -471,5 +588,50 @@ int apply_t(const frac_op* op, const T* u, T* y, int64_t batch, void* ws, cudaSt
 
 template int apply_t<float>(const frac_op*, const float*, float*, int64_t, void*, cudaStream_t);
 template int apply_t<double>(const frac_op*, const double*, double*, int64_t, void*, cudaStream_t);
+
+size_t apply_cg_partials(const frac_op* op) {
+  int64_t nrows = op->n;
+  for (int i = 2; i < op->prob.d; ++i) nrows *= op->n;
+  const int64_t a = rows_grid_any<float>(op->logm, nrows), b = rows_grid_any<double>(op->logm, nrows);
+  return (size_t)(a > b ? a : b);
+}
+
+template <typename T>
+int apply_cg_t(const frac_op* op, T* p, const T* r, T* q, void* ws, CGState* cgst, double* partials, cudaStream_t st) {
+  using C = cplx_t<T>;
+  const int d = op->prob.d, logm = op->logm;
+  const int64_t n = op->n, M = op->M, K = op->K;
+  const T* lam = sym_table<T>(op);
+  if (d < 2) return FRAC_ENOTSUP;
+  int64_t KB, w1, w2;
+  layout<T>(op, 1, KB, w1, w2);
+  C* W1 = (C*)ws;
+  CgArgs fwd, inv;
+  fwd.r = r;
+  fwd.st = cgst;
+  inv.p = p;
+  inv.st = cgst;
+  inv.partials = partials;
+  if (d == 2) {
+    FRAC_TRY((rows_any<T, true>(logm, true, p, W1, n, n, (int)KB, st, fwd)));
+    ColArgs A{(int)n, (int)K, (int)KB, KB, 1};
+    FRAC_TRY((cols_any<T, SYM2>(logm, W1, W1, A, 1, lam, st, cgst)));
+    FRAC_TRY((rows_any<T, true>(logm, false, W1, q, n, n, (int)KB, st, inv)));
+    return FRAC_OK;
+  }
+  C* W2 = W1 + w1;
+  const int64_t nrows = n * n;
+  FRAC_TRY((rows_any<T, true>(logm, true, p, W1, n, nrows, (int)KB, st, fwd)));
+  ColArgs Ay{(int)n, (int)K, (int)KB, KB, 1};
+  FRAC_TRY((cols_any<T, YFWD>(logm, W1, W2, Ay, n, lam, st, cgst)));
+  ColArgs Az{(int)n, (int)K, (int)KB, M * KB, 1};
+  FRAC_TRY((cols_any<T, ZSYM>(logm, W2, W2, Az, 1, lam, st, cgst)));
+  FRAC_TRY((cols_any<T, YINV>(logm, W2, W1, Ay, n, lam, st, cgst)));
+  FRAC_TRY((rows_any<T, true>(logm, false, W1, q, n, nrows, (int)KB, st, inv)));
+  return FRAC_OK;
+}
+
+template int apply_cg_t<float>(const frac_op*, float*, const float*, float*, void*, CGState*, double*, cudaStream_t);
+template int apply_cg_t<double>(const frac_op*, double*, const double*, double*, void*, CGState*, double*, cudaStream_t);
 
 }  // namespace frac

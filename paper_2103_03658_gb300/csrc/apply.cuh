@@ -13,6 +13,16 @@ template <typename T> inline const T* sym_table(const frac_op* op);
 template <> inline const float* sym_table<float>(const frac_op* op) { return op->lam32; }
 template <> inline const double* sym_table<double>(const frac_op* op) { return op->lam64; }
 
+// Device-resident conjugate-gradient state (solve.cu, fused apply kernels).
+struct CGState {
+  double rr;      // r.r
+  double pq;      // p.Ap
+  double alpha, beta;
+  double tol2;    // stop when rr <= tol2
+  int it, maxit, done, status;
+  unsigned int count_pq, count_rr;  // arrival counters of the last-block reductions
+};
+
 // coeffs.cu
 int prepare_twiddles(int logm);
 double far_field(int d, double alpha, double L, double lambda);
@@ -23,6 +33,16 @@ int build_coefficients(frac_op* op, cudaStream_t st);
 size_t apply_workspace_bytes(const frac_op* op, int dtype, int64_t batch);
 template <typename T>
 int apply_t(const frac_op* op, const T* u, T* y, int64_t batch, void* ws, cudaStream_t st);
+
+// One CG apply for d >= 2 with the vector work fused into the FFT passes:
+// p = r + beta p (beta from st) on the way into the forward row pass, q = A p
+// stored by the inverse row pass together with per-block partials of p.q;
+// the last block of that pass sums the partials in index order and sets
+// st->pq and st->alpha (or flags a breakdown).  Every kernel returns at once
+// when st->done is set.  `partials` holds apply_cg_partials(op) doubles.
+size_t apply_cg_partials(const frac_op* op);
+template <typename T>
+int apply_cg_t(const frac_op* op, T* p, const T* r, T* q, void* ws, CGState* st, double* partials, cudaStream_t s);
 
 // solve.cu
 int solve_device(const frac_op* op, const double* f, double* u, const frac_solve_opts* opts,

@@ -32,6 +32,11 @@ bool enabled() { return g_on.load(std::memory_order_relaxed); }
 
 Scope::Scope(const char* name, cudaStream_t st) : st_(st) {
   if (!enabled()) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;  // no timing events inside a graph capture
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t a, b;
   if (!g_pool.empty()) {

@@ -13,6 +13,7 @@
 // kernel marks the state done, the remaining launches of the chunk are no-ops
 // for x and r.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "apply.cuh"
@@ -20,13 +21,6 @@
 
 namespace frac {
 
-struct CGState {
-  double rr;     // r.r
-  double pq;     // p.Ap
-  double alpha, beta;
-  double tol2;   // stop when rr <= tol2
-  int it, maxit, done, status;
-};
 
 constexpr int kRedBlocks = 1024;  // partial-sum slots of the two-stage reductions
 constexpr int kTB = 256;
@@ -142,6 +136,54 @@ __global__ void k_cg_start(const double* __restrict__ partial, int np, CGState* 
     st->status = FRAC_OK;
     st->done = (rr <= st->tol2 || rr == 0.0) ? 1 : 0;
     st->alpha = st->beta = st->pq = 0.0;
+    st->count_pq = st->count_rr = 0;
+  }
+}
+
+// Fused update (d >= 2): x += alpha p, r -= alpha q, per-block r.r partials;
+// the last block sums them in index order and sets rr, beta, the iteration
+// count and the stop flag.
+template <typename T>
+__global__ void k_cg_update_fused(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                  const T* __restrict__ q, int64_t n, double* __restrict__ partial, CGState* st) {
+  __shared__ double red[32];
+  __shared__ bool last;
+  if (st->done) return;
+  const T al = (T)st->alpha;
+  T acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += al * p[i];
+    T ri = r[i] - al * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  double tot = block_sum((double)acc, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = tot;
+    __threadfence();
+    last = atomicAdd(&st->count_rr, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double sacc = 0.0;
+  for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) sacc += __ldcg(partial + i);
+  __syncthreads();
+  const double rr = block_sum(sacc, red);
+  if (threadIdx.x == 0) {
+    st->count_rr = 0;
+    st->beta = rr / st->rr;
+    st->rr = rr;
+    st->it += 1;
+    if (!isfinite(rr)) {
+      st->status = FRAC_EBREAKDOWN;
+      st->done = 1;
+    } else if (rr <= st->tol2) {
+      st->done = 1;
+    } else if (st->it >= st->maxit) {
+      st->status = FRAC_ENOCONV;
+      st->done = 1;
+    }
   }
 }
 
@@ -222,30 +264,71 @@ struct Ws {
   }
 };
 
-// CG on A_T x = b (x, r, p, q device vectors of length nd; r = b - A x0 and p = r
-// on entry).  Runs until the device state is done.  Returns FRAC_OK or FRAC_ECUDA;
-// the outcome is in the state.
+// Library stream used for graph replay (the caller's stream may be the legacy
+// default stream, which cannot be captured); fenced to the caller's stream with events.
+static cudaStream_t graph_stream() {
+  static std::mutex mu;
+  static std::vector<cudaStream_t> per_dev;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1, nullptr);
+  if (!per_dev[dev]) cudaStreamCreateWithFlags(&per_dev[dev], cudaStreamNonBlocking);
+  return per_dev[dev];
+}
+
+// CG iterations on A_T x = b for d >= 2, fused kernels, replayed as a CUDA graph
+// of kChunk iterations (captured on first use, kept in *exec for later calls with
+// the same buffers).  On entry r = b - A x, p holds any finite values and the
+// state was set by k_cg_start (beta = 0).  Runs until the device state is done.
+constexpr int kChunk = 16;
+
 template <typename T>
-static int cg_run(const frac_op* op, T* x, T* r, T* p, T* q, void* apply_ws, CGState* dst, CGState* hst,
-                  double* partial, int* iters_total, cudaStream_t st) {
+static int cg_run_fused(const frac_op* op, T* x, T* r, T* p, T* q, void* apply_ws, CGState* dst, CGState* hst,
+                        double* part_inv, double* part_upd, cudaGraphExec_t* exec, int* iters_total,
+                        cudaStream_t caller) {
   const int64_t nd = op->nd;
   const int nb = red_blocks(nd);
-  int chunk = 4;
-  for (;;) {
-    for (int c = 0; c < chunk; ++c) {
-      FRAC_TRY(apply_t<T>(op, p, q, 1, apply_ws, st));
-      k_dot<T><<<nb, kTB, 0, st>>>(p, q, nd, partial, dst);
-      k_cg_alpha<<<1, kTB, 0, st>>>(partial, nb, dst);
-      k_cg_update<T><<<nb, kTB, 0, st>>>(x, r, p, q, nd, partial, dst);
-      k_cg_beta<<<1, kTB, 0, st>>>(partial, nb, dst);
-      k_cg_p<T><<<nb, kTB, 0, st>>>(p, r, nd, dst);
-    }
+  cudaStream_t gs = graph_stream();
+  if (!gs) return FRAC_ECUDA;
+  cudaEvent_t ev;
+  FRAC_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  struct EvFree {
+    cudaEvent_t e;
+    ~EvFree() { cudaEventDestroy(e); }
+  } evf{ev};
+  FRAC_CUDA_TRY(cudaEventRecord(ev, caller));
+  FRAC_CUDA_TRY(cudaStreamWaitEvent(gs, ev, 0));
+  if (!*exec) {
+    // one plain iteration first: sets kernel attributes outside the capture
+    FRAC_TRY(apply_cg_t<T>(op, p, r, q, apply_ws, dst, part_inv, gs));
+    k_cg_update_fused<T><<<nb, kTB, 0, gs>>>(x, r, p, q, nd, part_upd, dst);
     FRAC_CUDA_TRY(cudaGetLastError());
-    FRAC_CUDA_TRY(cudaMemcpyAsync(hst, dst, sizeof(CGState), cudaMemcpyDeviceToHost, st));
-    FRAC_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hst->done) break;
-    if (chunk < 64) chunk *= 2;
+    cudaGraph_t g;
+    FRAC_CUDA_TRY(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    int s = FRAC_OK;
+    for (int c = 0; c < kChunk && s == FRAC_OK; ++c) {
+      s = apply_cg_t<T>(op, p, r, q, apply_ws, dst, part_inv, gs);
+      if (s == FRAC_OK) {
+        k_cg_update_fused<T><<<nb, kTB, 0, gs>>>(x, r, p, q, nd, part_upd, dst);
+        if (cudaGetLastError() != cudaSuccess) s = FRAC_ECUDA;
+      }
+    }
+    cudaError_t e = cudaStreamEndCapture(gs, &g);
+    if (s != FRAC_OK) return s;
+    FRAC_CUDA_TRY(e);
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    FRAC_CUDA_TRY(e);
   }
+  for (;;) {
+    FRAC_CUDA_TRY(cudaMemcpyAsync(hst, dst, sizeof(CGState), cudaMemcpyDeviceToHost, gs));
+    FRAC_CUDA_TRY(cudaStreamSynchronize(gs));
+    if (hst->done) break;
+    FRAC_CUDA_TRY(cudaGraphLaunch(*exec, gs));
+  }
+  FRAC_CUDA_TRY(cudaEventRecord(ev, gs));
+  FRAC_CUDA_TRY(cudaStreamWaitEvent(caller, ev, 0));
   *iters_total += hst->it;
   return FRAC_OK;
 }
@@ -315,12 +398,18 @@ int solve_device(const frac_op* op, const double* f, double* u, const frac_solve
   const int nb = red_blocks(nd);
   const unsigned gb = (unsigned)nb;
   Ws ws{st, {}};
-  double *r64, *Au64, *partial, *scal;
+  double *r64, *Au64, *partial, *scal, *part_inv;
   CGState *dst, *hst = nullptr;
   void* ws64;
+  cudaGraphExec_t exec = nullptr;
+  struct ExecFree {
+    cudaGraphExec_t* e;
+    ~ExecFree() { if (*e) cudaGraphExecDestroy(*e); }
+  } exf{&exec};
   FRAC_TRY(ws.get(&r64, nd * sizeof(double)));
   FRAC_TRY(ws.get(&Au64, nd * sizeof(double)));
   FRAC_TRY(ws.get(&partial, kRedBlocks * sizeof(double)));
+  FRAC_TRY(ws.get(&part_inv, apply_cg_partials(op) * sizeof(double)));
   FRAC_TRY(ws.get(&scal, 4 * sizeof(double)));
   FRAC_TRY(ws.get(&dst, sizeof(CGState)));
   FRAC_TRY(ws.get(&ws64, apply_workspace_bytes(op, FRAC_F64, 1)));
@@ -371,7 +460,7 @@ int solve_device(const frac_op* op, const double* f, double* u, const frac_solve
       k_dot<double><<<gb, kTB, 0, st>>>(r64, r64, nd, partial, nullptr);
       k_cg_start<<<1, kTB, 0, st>>>(partial, nb, dst, rtol * fnorm / std::max(rnorm, 1e-300), -1.0,
                                     opts->max_iter - iters);
-      FRAC_TRY(cg_run<double>(op, u, r64, p, q, ws64, dst, hst, partial, &iters, st));
+      FRAC_TRY(cg_run_fused<double>(op, u, r64, p, q, ws64, dst, hst, part_inv, partial, &exec, &iters, st));
       if (hst->status == FRAC_EBREAKDOWN) {
         info->status = FRAC_EBREAKDOWN;
         break;
@@ -400,7 +489,7 @@ int solve_device(const frac_op* op, const double* f, double* u, const frac_solve
       k_ir_scale_down<<<gb, kTB, 0, st>>>(r64, scal + 1, r32, p32, x32, nd);
       k_dot<float><<<gb, kTB, 0, st>>>(r32, r32, nd, partial, nullptr);
       k_cg_start<<<1, kTB, 0, st>>>(partial, nb, dst, inner, -1.0, opts->max_iter - iters);
-      FRAC_TRY(cg_run<float>(op, x32, r32, p32, q32, ws32, dst, hst, partial, &iters, st));
+      FRAC_TRY(cg_run_fused<float>(op, x32, r32, p32, q32, ws32, dst, hst, part_inv, partial, &exec, &iters, st));
       k_ir_correct<<<gb, kTB, 0, st>>>(u, x32, scal + 1, nd);
       // true FP64 residual
       FRAC_TRY(apply_t<double>(op, u, Au64, 1, ws64, st));

@@ -127,7 +127,7 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
         conv_line<double, LOGM>(buf64, n, T.lam64, tw64, [&](int e, int) { return p[e]; });
         double pq = 0.0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) pq += p[e] * buf64[pidx(tl + e * TPL)].x;
+        for (int e = 0; e < E; ++e) pq += p[e] * buf64[pidx(tl + e * TPL)].x;  // p = 0 beyond n
         pq = block_allsum<TPL>(pq, red);
         if (!(pq > 0.0) || !isfinite(pq)) {
           status = FRAC_EBREAKDOWN;
@@ -138,8 +138,10 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int x = tl + e * TPL;
-          if (x < n) U[x] += al * p[e];
-          r[e] -= al * buf64[pidx(x)].x;
+          if (x < n) {  // the convolution is nonzero beyond n; r and p stay zero there
+            U[x] += al * p[e];
+            r[e] -= al * buf64[pidx(x)].x;
+          }
           rr1 += r[e] * r[e];
         }
         rr1 = block_allsum<TPL>(rr1, red);
@@ -188,8 +190,10 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
         float rr1f = 0.0f;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          x[e] += al * p[e];
-          r[e] -= al * buf32[pidx(tl + e * TPL)].x;
+          if (tl + e * TPL < n) {  // r and p stay zero beyond n
+            x[e] += al * p[e];
+            r[e] -= al * buf32[pidx(tl + e * TPL)].x;
+          }
           rr1f += r[e] * r[e];
         }
         const double rr1 = block_allsum<TPL>((double)rr1f, red);
@@ -216,7 +220,7 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
     out.iters = iters;
     out.outer = outer;
     out.reserved = 0;
-    out.rel_resid = fn2 > 0.0 ? sqrt(rn2 / fn2) : 0.0;
+    out.rel_resid = fn2 > 0.0 ? sqrt(rn2 / fn2) : (fn2 == 0.0 ? 0.0 : NAN);  // NaN: non-finite f
     if (status == FRAC_OK && !(out.rel_resid <= T.rtol)) status = FRAC_ENOCONV;
     if (!isfinite(out.rel_resid)) status = FRAC_EINVAL;
     out.status = status;

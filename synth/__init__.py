@@ -37,11 +37,67 @@ def ball_power(d: int, n: int, s: float) -> np.ndarray:
 
 
 def ball_power_rhs(d: int, n: int, alpha: float) -> np.ndarray:
-    """Right-hand side f whose exact solution is u = (1 - |x|^2)_+^{1+alpha/2}
-    (g = 0): 2^alpha Gamma(2+alpha/2) Gamma((d+alpha)/2) / Gamma(d/2)
-    * (1 - (1 + alpha/d) |x|^2), the s = 1 + alpha/2 case of Eq. (fun0)."""
+    """Right-hand side f = (-Delta)^{alpha/2} u of u = (1 - |x|^2)_+^{1+alpha/2}
+    on the interior grid of (-1, 1)^d (data of the continuous problem, g = 0).
+
+    Inside the unit ball: 2^alpha Gamma(2+alpha/2) Gamma((d+alpha)/2) / Gamma(d/2)
+    * (1 - (1 + alpha/d) |x|^2), the s = 1 + alpha/2 case of Eq. (fun0).
+    At the corners of the cube (|x| > 1, d >= 2), where u = 0, the definition
+    Eq. (fL-nD) gives f(x) = -c_{d,alpha} int_{|y|<1} u(y) |x - y|^{-d-alpha} dy;
+    it is radial, reduced to a 1D integral over rho = |y| (closed-form angular
+    integral) and tabulated in r = |x| (see ``_outside_ball``)."""
     pref = 2.0 ** alpha * math.gamma(2 + alpha / 2) * math.gamma((d + alpha) / 2) / math.gamma(d / 2)
-    return pref * (1.0 - (1.0 + alpha / d) * radius2(d, n))
+    r2 = radius2(d, n)
+    f = pref * (1.0 - (1.0 + alpha / d) * r2)
+    if d >= 2:
+        out = r2 > 1.0
+        if np.any(out):
+            f[out] = _outside_ball(d, alpha, 1.0 + alpha / 2)(np.sqrt(r2[out]))
+    return f
+
+
+_OUT_CACHE: dict = {}
+
+
+def _outside_ball(d: int, alpha: float, s: float):
+    """r -> -c_{d,alpha} int_{|y|<1} (1-|y|^2)^s |x-y|^{-d-alpha} dy for |x| = r in (1, sqrt(d)].
+
+    Angular integrals in closed form: d = 3, int_{S^2} |x - rho w|^{-3-alpha} dw
+    = 2 pi ((r - rho)^{-1-alpha} - (r + rho)^{-1-alpha}) / ((1 + alpha) r rho);
+    d = 2, int_0^{2 pi} (a - b cos phi)^{-nu} dphi = 2 pi a^{-nu} 2F1(nu/2, (nu+1)/2; 1; (b/a)^2)
+    with a = r^2 + rho^2, b = 2 r rho, nu = 1 + alpha/2.  The rho-integral is
+    done by adaptive quadrature on 500 points t = sqrt(r - 1) and interpolated
+    by a cubic spline in t."""
+    key = (d, round(alpha, 15), round(s, 15))
+    if key in _OUT_CACHE:
+        return _OUT_CACHE[key]
+    from scipy import integrate, interpolate, special
+    c = 2.0 ** (alpha - 1) * alpha * math.gamma((d + alpha) / 2) / (math.pi ** (d / 2) * math.gamma(1 - alpha / 2))
+
+    def value(r: float) -> float:
+        if d == 3:
+            g = lambda rho: rho * (1 - rho * rho) ** s * ((r - rho) ** (-1 - alpha) - (r + rho) ** (-1 - alpha))  # noqa: E731
+            v = integrate.quad(g, 0.0, 1.0, epsabs=0.0, epsrel=1e-11, limit=400)[0]
+            return -c * 2.0 * math.pi / (r * (1.0 + alpha)) * v
+        nu = 1.0 + alpha / 2.0
+
+        def g(rho):
+            a = r * r + rho * rho
+            return rho * (1 - rho * rho) ** s * 2.0 * math.pi * a ** (-nu) * special.hyp2f1(
+                nu / 2, (nu + 1) / 2, 1.0, (2.0 * r * rho / a) ** 2)
+        v = integrate.quad(g, 0.0, 1.0, epsabs=0.0, epsrel=1e-11, limit=400)[0]
+        return -c * v
+
+    import warnings
+    t = np.linspace(1e-3, math.sqrt(math.sqrt(d) - 1.0) + 1e-3, 500)
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        vals = np.array([value(1.0 + ti * ti) for ti in t])
+    spline = interpolate.CubicSpline(t, vals)
+    fn = lambda r: spline(np.sqrt(np.maximum(np.asarray(r) - 1.0, 0.0)))  # noqa: E731
+    fn.value = value
+    _OUT_CACHE[key] = fn
+    return fn
 
 
 def smooth_field(d: int, n: int, seed: int, modes: int = 32, kmax: int = 16) -> np.ndarray:

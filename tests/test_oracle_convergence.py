@@ -100,3 +100,22 @@ def test_synth_rhs_matches_oracle_closed_form():
             f = synth.ball_power_rhs(d, n, alpha)
             ref = O.fl_ball_power(d, alpha, 1 + alpha / 2, synth.radius2(d, n))
             assert np.allclose(f, ref, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("d,alpha", [(2, 0.7), (3, 0.7), (3, 1.6)])
+def test_synth_rhs_outside_ball_matches_definition(d, alpha):
+    """At the cube corners (|x| > 1, where u = 0) the workload right-hand side
+    must equal -c int_{|y|<1} u(y) |x-y|^{-d-alpha} dy (Eq. (fL-nD)); brute-force
+    cubature over the ball in polar / spherical coordinates here."""
+    import synth
+    s = 1 + alpha / 2
+    c = O.c_dalpha(d, alpha)
+    fn = synth._outside_ball(d, alpha, s)
+    for r in (1.05, 1.3):
+        if d == 2:
+            g = lambda ph, rho: rho * (1 - rho * rho) ** s * (r * r + rho * rho - 2 * r * rho * math.cos(ph)) ** (-(2 + alpha) / 2)  # noqa: E731
+            ref = -c * integrate.dblquad(g, 0, 1, 0, 2 * math.pi, epsabs=0, epsrel=1e-9)[0]
+        else:
+            g = lambda th, rho: 2 * math.pi * rho * rho * math.sin(th) * (1 - rho * rho) ** s * (r * r + rho * rho - 2 * r * rho * math.cos(th)) ** (-(3 + alpha) / 2)  # noqa: E731
+            ref = -c * integrate.dblquad(g, 0, 1, 0, math.pi, epsabs=0, epsrel=1e-9)[0]
+        assert abs(float(fn(r)) - ref) <= 1e-5 * abs(ref), (r, float(fn(r)), ref)
