@@ -341,7 +341,70 @@ def extra_measurements(fg, torch, u32, op, barrier) -> dict:
                                                "outer": info["outer"], "rel_resid": info["rel_resid"]}}
     op3.close()
     out["solves"] = solves
+    out["batch"] = batch_measurement(fg, torch, barrier)
+    out["served"] = served_measurement(fg, torch, barrier)
     return out
+
+
+def batch_measurement(fg, torch, barrier) -> dict:
+    """256 mixed problems (d in {1, 2}, 1D n in [63, 4095], 2D side in [63, 511],
+    alpha ~ U(0.1, 1.9), p in {0, 1, 2}, lambda ~ U(0, 2), smooth random right-hand
+    sides) solved by one frac_solve_batch call, FP32 CG in FP64 refinement to 1e-10."""
+    probs = synth.batch_problems(256)
+    t0 = time.perf_counter()
+    ops = [fg.FracOp(p.d, p.n, p.alpha, degree=p.degree, lam=p.lam) for p in probs]
+    barrier()
+    t_coeff = time.perf_counter() - t0
+    fs = [torch.tensor(synth.smooth_field(p.d, p.n, p.seed) + 0.25, device="cuda") for p in probs]
+    us = [torch.empty_like(f) for f in fs]
+    fg.solve_batch(ops[:4], fs[:4], us[:4])                 # warm-up of the kernels
+    barrier()
+    t0 = time.perf_counter()
+    infos = fg.solve_batch(ops, fs, us, rtol=1e-10, precision="mixed")
+    barrier()
+    dt = time.perf_counter() - t0
+    dof = sum(p.n ** p.d for p in probs)
+    ok = sum(1 for i in infos if i["status"] == 0 and i["rel_resid"] <= 1e-10)
+    for op in ops:
+        op.close()
+    return {"problems": len(probs), "converged": ok, "solves_per_s": len(probs) / dt, "ms": 1e3 * dt,
+            "dof_total": dof, "iters_total": int(sum(i["iters"] for i in infos)),
+            "coefficient_build_ms_all_ops": 1e3 * t_coeff}
+
+
+def served_measurement(fg, torch, barrier, seconds: float = 3.0) -> dict:
+    """Poisson arrivals at 200 req/s for `seconds`: d in {1, 2, 3} (0.4/0.4/0.2),
+    1D/2D sizes as in the batch mix, 3D side in {63, 127, 255}, alpha ~ U(0.1, 1.9),
+    lambda ~ U(0, 2), p in {0, 1, 2}; right-hand sides drawn from a seeded pool of
+    two smooth fields per grid; 150 GB admission budget; latency from arrival to
+    the solution on the host."""
+    from paper_2103_03658_gb300 import serve
+    arr = synth.arrival_times(rate=200.0, duration=seconds)
+    probs = synth.served_problems(len(arr))
+    pool = {}
+    reqs = []
+    for i, (pb, t) in enumerate(zip(probs, arr)):
+        key = (pb.d, pb.n, i % 2)
+        if key not in pool:
+            pool[key] = synth.smooth_field(pb.d, pb.n, 7000 + len(pool)) + 0.25
+        reqs.append(serve.Request(i, pb.d, pb.n, pb.alpha, pb.degree, pb.lam, pool[key], float(t)))
+    srv = serve.Server(hbm_budget=150e9, nstreams=16)
+    barrier()
+    t0 = time.perf_counter()
+    res = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = [r.latency_s for r in res]
+    ok = sum(1 for r in res if r.info["status"] == 0 and r.info["rel_resid"] <= 1e-10)
+    by_d = {}
+    for r, q in zip(res, reqs):
+        by_d.setdefault(q.d, []).append(r.latency_s)
+    return {"requests": len(reqs), "window_s": seconds, "rate_per_s": 200.0, "converged": ok,
+            "solves_per_s": len(res) / wall, "wall_s": wall,
+            "p50_ms": 1e3 * serve.percentile(lat, 50), "p99_ms": 1e3 * serve.percentile(lat, 99),
+            "p50_ms_by_d": {str(d): 1e3 * serve.percentile(v, 50) for d, v in sorted(by_d.items())},
+            "p99_ms_by_d": {str(d): 1e3 * serve.percentile(v, 99) for d, v in sorted(by_d.items())},
+            "op_cache_hits": srv.cache.hits, "op_cache_misses": srv.cache.misses}
 
 
 def main():

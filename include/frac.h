@@ -204,6 +204,43 @@ typedef struct frac_kernel_stat {
 int frac_profile_enable(int on);
 int frac_profile_read(frac_kernel_stat* out, int cap, int* count, int reset);
 
+/*
+ * Solve engine: many solves in flight at once (continuous batching).  Each
+ * submitted job advances through its own stream from a fixed pool: d = 1 as
+ * one whole-solve block, d >= 2 as FP32 CG chunks (replayed CUDA graphs) and
+ * FP64 refinement steps (or FP64 CG chunks for FRAC_PLAIN_F64), exactly the
+ * computation of frac_solve.  Jobs submitted while others run start at once;
+ * their kernels overlap on the device.  Not thread safe: one host thread
+ * drives an engine.
+ *
+ * frac_engine_create: `nstreams` >= 1 streams (non-blocking, created on the
+ *   current device).  Errors: FRAC_EINVAL (nstreams < 1, out NULL), FRAC_ECUDA.
+ * frac_engine_submit: queue A u = f with `opts`; f and u are device or host
+ *   buffers of prod(n_i) doubles that must stay valid until the job is
+ *   returned by frac_engine_poll (host buffers are staged on the job's
+ *   stream).  *job receives an id > 0.  Errors: as frac_solve's argument checks,
+ *   FRAC_ENOMEM.  The op must outlive the job.
+ * frac_engine_poll: advance every job whose pending device work finished;
+ *   copy up to `cap` finished jobs to out (host array), *count = how many.
+ *   With block != 0 it waits until at least one job finishes (returns at once
+ *   when none is in flight).
+ * frac_engine_stats: jobs in flight and device bytes they hold (host pointers).
+ * frac_engine_destroy: waits for all work, releases every job and stream.
+ */
+typedef struct frac_engine frac_engine;
+typedef struct frac_job_result {
+  int64_t job;
+  frac_solve_info info;
+  double submit_to_done_ms;  /* host wall time from submit to completion seen by poll */
+} frac_job_result;
+
+int frac_engine_create(int nstreams, frac_engine** out);
+int frac_engine_submit(frac_engine* e, const frac_op* op, const double* f, double* u, const frac_solve_opts* opts,
+                       int64_t* job);
+int frac_engine_poll(frac_engine* e, int block, frac_job_result* out, int cap, int* count);
+int frac_engine_stats(const frac_engine* e, int64_t* active, size_t* device_bytes);
+void frac_engine_destroy(frac_engine* e);
+
 /* Static string naming a status code. */
 const char* frac_strerror(int status);
 

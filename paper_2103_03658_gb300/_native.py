@@ -49,6 +49,10 @@ class SolveInfo(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("rel_resid", ctypes.c_double)]
 
 
+class JobResult(ctypes.Structure):
+    _fields_ = [("job", ctypes.c_int64), ("info", SolveInfo), ("submit_to_done_ms", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -85,6 +89,16 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.frac_solve_batch.argtypes = [i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.frac_solve_batch.restype = i32
+    lib.frac_engine_create.argtypes = [i32, ctypes.POINTER(vp)]
+    lib.frac_engine_create.restype = i32
+    lib.frac_engine_submit.argtypes = [vp, vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(ctypes.c_int64)]
+    lib.frac_engine_submit.restype = i32
+    lib.frac_engine_poll.argtypes = [vp, i32, ctypes.POINTER(JobResult), i32, ctypes.POINTER(ctypes.c_int)]
+    lib.frac_engine_poll.restype = i32
+    lib.frac_engine_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t)]
+    lib.frac_engine_stats.restype = i32
+    lib.frac_engine_destroy.argtypes = [vp]
+    lib.frac_engine_destroy.restype = None
     lib.frac_strerror.argtypes = [i32]
     lib.frac_strerror.restype = ctypes.c_char_p
     lib.frac_error_detail.argtypes = []
@@ -271,3 +285,71 @@ def solve_batch(ops, fs, us, rtol: float = 1e-10, max_iter: int = 200000, precis
     if s not in (0, 4):
         raise FracError(s, "frac_solve_batch")
     return out
+
+
+def _info(si: SolveInfo) -> dict:
+    return {k: getattr(si, k) for k, _ in SolveInfo._fields_ if k != "reserved"}
+
+
+class Engine:
+    """Many solves in flight at once (frac_engine_* of include/frac.h): jobs
+    advance on a pool of `nstreams` streams; poll() advances them and returns
+    the finished ones.  The buffers of a job are kept alive until it finishes."""
+
+    def __init__(self, nstreams: int = 16):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        s = self._lib.frac_engine_create(nstreams, ctypes.byref(h))
+        if s != 0:
+            raise FracError(s, "frac_engine_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, op: "FracOp", f, u=None, rtol: float = 1e-10, max_iter: int = 200000,
+               precision: str = "mixed", inner_tol: float = 1e-4, use_x0: bool = False) -> tuple:
+        """Queue op u = f; the solution goes to `u` (a new buffer if None), whose
+        contents are the initial guess only when use_x0 is set.  Returns (job id, u)."""
+        if _dtype_code(f) != F64:
+            raise TypeError("solve takes float64 data")
+        if u is None:
+            u = _empty_like(f)
+            use_x0 = False
+        opts = SolveOpts(rtol, max_iter, MIXED_IR if precision == "mixed" else PLAIN_F64, int(use_x0), inner_tol)
+        job = ctypes.c_int64()
+        s = self._lib.frac_engine_submit(self._h, op.handle, _ptr(f), _ptr(u), ctypes.byref(opts), ctypes.byref(job))
+        if s != 0:
+            raise FracError(s, "frac_engine_submit")
+        self._keep[job.value] = (op, f, u)
+        return job.value, u
+
+    def poll(self, block: bool = False, cap: int = 256) -> list:
+        """Advance all jobs; list of (job, info dict, submit-to-done ms, u) for the finished ones."""
+        arr = (JobResult * cap)()
+        cnt = ctypes.c_int()
+        s = self._lib.frac_engine_poll(self._h, int(block), arr, cap, ctypes.byref(cnt))
+        out = []
+        for i in range(cnt.value):
+            r = arr[i]
+            op, f, u = self._keep.pop(r.job, (None, None, None))
+            out.append((r.job, _info(r.info), r.submit_to_done_ms, u))
+        if s != 0 and not out:
+            raise FracError(s, "frac_engine_poll")
+        return out
+
+    def stats(self) -> tuple:
+        a = ctypes.c_int64()
+        b = ctypes.c_size_t()
+        self._lib.frac_engine_stats(self._h, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.frac_engine_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

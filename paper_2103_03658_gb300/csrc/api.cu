@@ -1,5 +1,6 @@
 // C ABI entry points (include/frac.h): argument validation, operator
 // lifecycle, staging of host buffers, dispatch to the device kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -277,10 +278,38 @@ int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* con
       if (info[i].status != FRAC_OK && first == FRAC_OK) first = info[i].status;
     }
   }
-  for (int64_t i : rest) {
-    int s = frac_solve(ops[i], f[i], nullptr, u[i], opts, &info[i], stream);
-    if (s != FRAC_OK && first == FRAC_OK) first = s;
-    if (s != FRAC_OK && s != FRAC_ENOCONV && s != FRAC_EBREAKDOWN) info[i].status = s;
+  if (!rest.empty()) {
+    // the other problems progress together through a solve engine (their kernels overlap)
+    frac_engine* e = nullptr;
+    const int ns = (int)std::min<size_t>(8, rest.size());
+    FRAC_TRY(frac_engine_create(ns, &e));
+    int s = engine_wait_for(e, st);
+    std::vector<std::pair<int64_t, int64_t>> ids;  // (job, index)
+    for (int64_t i : rest) {
+      int64_t job = 0;
+      int r = s == FRAC_OK ? frac_engine_submit(e, ops[i], f[i], u[i], opts, &job) : s;
+      if (r != FRAC_OK) {
+        info[i] = frac_solve_info{r, 0, 0, 0, NAN};
+        if (first == FRAC_OK) first = r;
+      } else {
+        ids.emplace_back(job, i);
+      }
+    }
+    std::vector<frac_job_result> done(ids.size() + 1);
+    size_t got = 0;
+    while (got < ids.size()) {
+      int cnt = 0;
+      int r = frac_engine_poll(e, 1, done.data(), (int)done.size(), &cnt);
+      if (r != FRAC_OK && first == FRAC_OK) first = r;
+      if (cnt == 0 && r != FRAC_OK) break;
+      for (int k = 0; k < cnt; ++k)
+        for (auto& pr : ids)
+          if (pr.first == done[k].job) info[pr.second] = done[k].info;
+      got += cnt;
+    }
+    frac_engine_destroy(e);
+    for (int64_t i : rest)
+      if (info[i].status != FRAC_OK && first == FRAC_OK) first = info[i].status;
   }
   return first;
 }

@@ -47,6 +47,9 @@ int apply_cg_t(const frac_op* op, T* p, const T* r, T* q, void* ws, CGState* st,
 // solve.cu
 int solve_device(const frac_op* op, const double* f, double* u, const frac_solve_opts* opts,
                  frac_solve_info* info, cudaStream_t st);
+// Makes every stream of engine e wait for the work already queued on `caller`.
+int engine_wait_for(frac_engine* e, cudaStream_t caller);
+
 // Solves the 1D problems listed in idx[0..count) of (ops, f, u) (device pointers),
 // grouped by FFT length, one launch per group; fills info[idx[t]].
 int solve_batch_1d(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,

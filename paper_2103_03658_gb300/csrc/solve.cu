@@ -12,8 +12,12 @@
 // iterations in chunks and reads the state back between chunks; once a
 // kernel marks the state done, the remaining launches of the chunk are no-ops
 // for x and r.
+#include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <mutex>
+#include <new>
+#include <thread>
 #include <vector>
 
 #include "apply.cuh"
@@ -511,4 +515,469 @@ int solve_device(const frac_op* op, const double* f, double* u, const frac_solve
   return FRAC_OK;
 }
 
+}  // namespace frac
+
+// ===========================================================================
+// Solve engine (frac_engine_*): the computation of solve_device as an
+// asynchronous state machine per job, so that many jobs progress at once on
+// a pool of streams.  poll() advances every job whose last device step has
+// finished (cudaEventQuery) by issuing its next step.
+// ===========================================================================
+
+namespace frac {
+namespace {
+
+enum Phase { PH_WHOLE1D, PH_NORM, PH_INNER, PH_REFINE, PH_COPYOUT, PH_DONE };
+
+struct Mirror {  // pinned host copies of the small device results
+  CGState st;
+  double scal[4];
+  frac_solve_info info;
+  Solve1dTask task;
+};
+
+struct Job {
+  int64_t id = 0;
+  const frac_op* op = nullptr;
+  frac_solve_opts opts{};
+  double* u_user = nullptr;
+  bool host_u = false;
+  const double* f = nullptr;  // device
+  double* u = nullptr;        // device
+  cudaStream_t s = nullptr;
+  Mirror* hm = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<void*> bufs;
+  size_t bytes = 0;
+  // device buffers (d >= 2)
+  double *r64 = nullptr, *Au64 = nullptr, *partial = nullptr, *part_inv = nullptr, *scal = nullptr;
+  CGState* st = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  double *p64 = nullptr, *q64 = nullptr;
+  void *ws32 = nullptr, *ws64 = nullptr;
+  frac_solve_info* dinfo = nullptr;
+  Solve1dTask* dtask = nullptr;
+  Phase phase = PH_NORM;
+  int iters = 0, outer = 0, restarts = 0, status = FRAC_OK;
+  double fnorm = 0.0, rnorm = 0.0, prev = INFINITY;
+  std::chrono::steady_clock::time_point t0;
+  frac_solve_info result{};
+};
+
+bool dev_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+}  // namespace frac
+
+struct frac_engine {
+  int device = 0;
+  std::vector<cudaStream_t> streams;
+  size_t next_stream = 0;
+  std::vector<frac::Job*> jobs;  // in flight
+  std::vector<frac_job_result> finished;
+  int64_t next_id = 1;
+  size_t bytes = 0;
+  std::vector<frac::Mirror*> free_mirrors;
+  std::vector<frac::Mirror*> mirror_blocks;
+};
+
+namespace frac {
+namespace {
+
+template <typename P>
+int jalloc(Job* j, P** out, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, j->s);
+  if (e != cudaSuccess) return record_cuda_error(e, __FILE__, __LINE__, "cudaMallocAsync");
+  j->bufs.push_back(p);
+  j->bytes += bytes;
+  *out = (P*)p;
+  return FRAC_OK;
+}
+
+Mirror* get_mirror(frac_engine* e) {
+  if (e->free_mirrors.empty()) {
+    Mirror* blk = nullptr;
+    if (cudaMallocHost(&blk, 64 * sizeof(Mirror)) != cudaSuccess) return nullptr;
+    e->mirror_blocks.push_back(blk);
+    for (int i = 0; i < 64; ++i) e->free_mirrors.push_back(blk + i);
+  }
+  Mirror* m = e->free_mirrors.back();
+  e->free_mirrors.pop_back();
+  return m;
+}
+
+// Launch the next chunk of the current inner/plain CG and the state read-back.
+template <typename T>
+int launch_chunk(Job* j, T* x, T* r, T* p, T* q, void* ws) {
+  const int64_t nd = j->op->nd;
+  const int nb = red_blocks(nd);
+  if (!j->exec) {
+    FRAC_TRY(apply_cg_t<T>(j->op, p, r, q, ws, j->st, j->part_inv, j->s));
+    k_cg_update_fused<T><<<nb, kTB, 0, j->s>>>(x, r, p, q, nd, j->partial, j->st);
+    FRAC_CUDA_TRY(cudaGetLastError());
+    cudaGraph_t g;
+    FRAC_CUDA_TRY(cudaStreamBeginCapture(j->s, cudaStreamCaptureModeThreadLocal));
+    int s = FRAC_OK;
+    for (int c = 0; c < kChunk && s == FRAC_OK; ++c) {
+      s = apply_cg_t<T>(j->op, p, r, q, ws, j->st, j->part_inv, j->s);
+      if (s == FRAC_OK) {
+        k_cg_update_fused<T><<<nb, kTB, 0, j->s>>>(x, r, p, q, nd, j->partial, j->st);
+        if (cudaGetLastError() != cudaSuccess) s = FRAC_ECUDA;
+      }
+    }
+    cudaError_t e = cudaStreamEndCapture(j->s, &g);
+    if (s != FRAC_OK) return s;
+    FRAC_CUDA_TRY(e);
+    e = cudaGraphInstantiate(&j->exec, g, 0);
+    cudaGraphDestroy(g);
+    FRAC_CUDA_TRY(e);
+  } else {
+    FRAC_CUDA_TRY(cudaGraphLaunch(j->exec, j->s));
+  }
+  FRAC_CUDA_TRY(cudaMemcpyAsync(&j->hm->st, j->st, sizeof(CGState), cudaMemcpyDeviceToHost, j->s));
+  FRAC_CUDA_TRY(cudaEventRecord(j->ev, j->s));
+  return FRAC_OK;
+}
+
+int launch_chunk_resume(Job* j);
+
+// Start an inner (mixed) or plain CG run from the current residual r64.
+int start_cg(Job* j) {
+  const int64_t nd = j->op->nd;
+  const int nb = red_blocks(nd);
+  const unsigned gb = (unsigned)nb;
+  const int left = j->opts.max_iter - j->iters;
+  if (j->opts.precision == FRAC_MIXED_IR) {
+    const double inner = j->opts.inner_tol > 0.0 ? j->opts.inner_tol : 1e-4;
+    k_ir_scale_down<<<gb, kTB, 0, j->s>>>(j->r64, j->scal + 1, j->r32, j->p32, j->x32, nd);
+    k_dot<float><<<gb, kTB, 0, j->s>>>(j->r32, j->r32, nd, j->partial, nullptr);
+    k_cg_start<<<1, kTB, 0, j->s>>>(j->partial, nb, j->st, inner, -1.0, left);
+    FRAC_CUDA_TRY(cudaGetLastError());
+    j->phase = PH_INNER;
+    return launch_chunk<float>(j, j->x32, j->r32, j->p32, j->q32, j->ws32);
+  }
+  k_copy2<double><<<gb, kTB, 0, j->s>>>(j->r64, j->p64, j->q64, nd);
+  k_dot<double><<<gb, kTB, 0, j->s>>>(j->r64, j->r64, nd, j->partial, nullptr);
+  k_cg_start<<<1, kTB, 0, j->s>>>(j->partial, nb, j->st, j->opts.rtol * j->fnorm / std::max(j->rnorm, 1e-300), -1.0,
+                                  left);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  j->phase = PH_INNER;
+  return launch_chunk<double>(j, j->u, j->r64, j->p64, j->q64, j->ws64);
+}
+
+// r64 = f - A64 u, ||r64||^2 -> scal[1] -> host; phase REFINE
+int start_residual(Job* j) {
+  const int64_t nd = j->op->nd;
+  const int nb = red_blocks(nd);
+  FRAC_TRY(apply_t<double>(j->op, j->u, j->Au64, 1, j->ws64, j->s));
+  k_residual<<<(unsigned)nb, kTB, 0, j->s>>>(j->f, j->Au64, j->r64, nd, j->partial);
+  k_sum_to<<<1, kTB, 0, j->s>>>(j->partial, nb, j->scal + 1);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  FRAC_CUDA_TRY(cudaMemcpyAsync(j->hm->scal, j->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, j->s));
+  FRAC_CUDA_TRY(cudaEventRecord(j->ev, j->s));
+  j->phase = PH_REFINE;
+  return FRAC_OK;
+}
+
+int finish(Job* j) {
+  frac_solve_info& r = j->result;
+  r.iters = j->iters;
+  r.outer = j->outer;
+  r.reserved = 0;
+  if (j->op->prob.d == 1) {
+    r = j->hm->info;
+    if (r.status == FRAC_EINVAL || std::isnan(r.rel_resid)) r.status = FRAC_EINVAL;
+  } else {
+    r.rel_resid = j->fnorm > 0.0 ? j->rnorm / j->fnorm : (j->fnorm == 0.0 ? 0.0 : NAN);
+    if (std::isnan(r.rel_resid)) j->status = FRAC_EINVAL;
+    if (j->status == FRAC_OK && !(r.rel_resid <= j->opts.rtol)) j->status = FRAC_ENOCONV;
+    r.status = j->status;
+  }
+  if (j->host_u) {
+    FRAC_CUDA_TRY(cudaMemcpyAsync(j->u_user, j->u, j->op->nd * sizeof(double), cudaMemcpyDeviceToHost, j->s));
+    FRAC_CUDA_TRY(cudaEventRecord(j->ev, j->s));
+    j->phase = PH_COPYOUT;
+  } else {
+    j->phase = PH_DONE;
+  }
+  return FRAC_OK;
+}
+
+// One step of job j whose last device work has completed.
+int advance(Job* j) {
+  switch (j->phase) {
+    case PH_WHOLE1D:
+      return finish(j);
+    case PH_NORM:
+      j->fnorm = std::sqrt(j->hm->scal[0]);
+      j->rnorm = std::sqrt(j->hm->scal[1]);
+      if (!(j->fnorm > 0.0) || j->rnorm <= j->opts.rtol * j->fnorm) {
+        if (j->fnorm == 0.0) {
+          FRAC_CUDA_TRY(cudaMemsetAsync(j->u, 0, j->op->nd * sizeof(double), j->s));
+          j->rnorm = 0.0;
+        }
+        return finish(j);
+      }
+      return start_cg(j);
+    case PH_INNER: {
+      const CGState& st = j->hm->st;
+      if (!st.done) return launch_chunk_resume(j);
+      j->iters += st.it;
+      if (j->opts.precision == FRAC_MIXED_IR) {
+        k_ir_correct<<<(unsigned)red_blocks(j->op->nd), kTB, 0, j->s>>>(j->u, j->x32, j->scal + 1, j->op->nd);
+        FRAC_CUDA_TRY(cudaGetLastError());
+      } else if (st.status == FRAC_EBREAKDOWN) {
+        j->status = FRAC_EBREAKDOWN;
+      }
+      return start_residual(j);
+    }
+    case PH_REFINE: {
+      const double rn = std::sqrt(j->hm->scal[1]);
+      j->rnorm = rn;
+      ++j->outer;
+      if (j->opts.precision != FRAC_MIXED_IR) ++j->restarts;
+      const bool converged = rn <= j->opts.rtol * j->fnorm;
+      const bool stagnated = j->opts.precision == FRAC_MIXED_IR ? (!(rn < j->prev) && j->outer > 3) : j->restarts >= 8;
+      j->prev = rn;
+      if (converged || stagnated || j->status != FRAC_OK || j->iters >= j->opts.max_iter || j->outer >= 100 ||
+          !std::isfinite(rn))
+        return finish(j);
+      return start_cg(j);
+    }
+    case PH_COPYOUT:
+      j->phase = PH_DONE;
+      return FRAC_OK;
+    default:
+      return FRAC_OK;
+  }
+}
+
+}  // namespace
+}  // namespace frac
+
+namespace frac {
+namespace {
+int launch_chunk_resume(Job* j) {
+  if (j->opts.precision == FRAC_MIXED_IR) return launch_chunk<float>(j, j->x32, j->r32, j->p32, j->q32, j->ws32);
+  return launch_chunk<double>(j, j->u, j->r64, j->p64, j->q64, j->ws64);
+}
+}  // namespace
+}  // namespace frac
+
+using namespace frac;
+
+extern "C" int frac_engine_create(int nstreams, frac_engine** out) {
+  if (!out || nstreams < 1) return FRAC_EINVAL;
+  *out = nullptr;
+  frac_engine* e = new (std::nothrow) frac_engine();
+  if (!e) return FRAC_ENOMEM;
+  cudaGetDevice(&e->device);
+  for (int i = 0; i < nstreams; ++i) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      frac_engine_destroy(e);
+      return FRAC_ECUDA;
+    }
+    e->streams.push_back(s);
+  }
+  *out = e;
+  return FRAC_OK;
+}
+
+static void release_job(frac_engine* e, Job* j) {
+  for (void* p : j->bufs) cudaFreeAsync(p, j->s);
+  if (j->exec) cudaGraphExecDestroy(j->exec);
+  if (j->ev) cudaEventDestroy(j->ev);
+  if (j->hm) e->free_mirrors.push_back(j->hm);
+  e->bytes -= j->bytes;
+  delete j;
+}
+
+static int submit_impl(frac_engine* e, Job* j, const double* f, double* u) {
+  const frac_op* op = j->op;
+  const int64_t nd = op->nd;
+  FRAC_CUDA_TRY(cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming));
+  j->hm = get_mirror(e);
+  if (!j->hm) return FRAC_ENOMEM;
+  const bool df = dev_ptr(f);
+  j->host_u = !dev_ptr(u);
+  j->u_user = u;
+  if (df) {
+    j->f = f;
+  } else {
+    for (int64_t i = 0; i < nd; ++i)
+      if (!std::isfinite(f[i])) return FRAC_EINVAL;
+    double* fd;
+    FRAC_TRY(jalloc(j, &fd, nd * sizeof(double)));
+    FRAC_CUDA_TRY(cudaMemcpyAsync(fd, f, nd * sizeof(double), cudaMemcpyHostToDevice, j->s));
+    j->f = fd;
+  }
+  if (!j->host_u) {
+    j->u = u;
+  } else {
+    FRAC_TRY(jalloc(j, &j->u, nd * sizeof(double)));
+    if (j->opts.use_x0) FRAC_CUDA_TRY(cudaMemcpyAsync(j->u, u, nd * sizeof(double), cudaMemcpyHostToDevice, j->s));
+  }
+  if (op->prob.d == 1) {
+    FRAC_TRY(jalloc(j, &j->dinfo, sizeof(frac_solve_info)));
+    FRAC_TRY(jalloc(j, &j->dtask, sizeof(Solve1dTask)));
+    j->hm->task = Solve1dTask{j->f, j->u, op->lam32, op->lam64, j->dinfo, j->opts.rtol,
+                              j->opts.inner_tol > 0.0 ? j->opts.inner_tol : 1e-4, (int)op->n, j->opts.max_iter,
+                              j->opts.use_x0 ? 1 : 0};
+    FRAC_CUDA_TRY(cudaMemcpyAsync(j->dtask, &j->hm->task, sizeof(Solve1dTask), cudaMemcpyHostToDevice, j->s));
+    FRAC_TRY(solve1d_launch(op->logm, j->opts.precision == FRAC_MIXED_IR, j->dtask, 1, j->s));
+    FRAC_CUDA_TRY(cudaMemcpyAsync(&j->hm->info, j->dinfo, sizeof(frac_solve_info), cudaMemcpyDeviceToHost, j->s));
+    FRAC_CUDA_TRY(cudaEventRecord(j->ev, j->s));
+    j->phase = PH_WHOLE1D;
+    return FRAC_OK;
+  }
+  const int nb = red_blocks(nd);
+  FRAC_TRY(jalloc(j, &j->r64, nd * sizeof(double)));
+  FRAC_TRY(jalloc(j, &j->Au64, nd * sizeof(double)));
+  FRAC_TRY(jalloc(j, &j->partial, kRedBlocks * sizeof(double)));
+  FRAC_TRY(jalloc(j, &j->part_inv, apply_cg_partials(op) * sizeof(double)));
+  FRAC_TRY(jalloc(j, &j->scal, 4 * sizeof(double)));
+  FRAC_TRY(jalloc(j, &j->st, sizeof(CGState)));
+  FRAC_TRY(jalloc(j, &j->ws64, apply_workspace_bytes(op, FRAC_F64, 1)));
+  if (j->opts.precision == FRAC_MIXED_IR) {
+    FRAC_TRY(jalloc(j, &j->x32, nd * sizeof(float)));
+    FRAC_TRY(jalloc(j, &j->r32, nd * sizeof(float)));
+    FRAC_TRY(jalloc(j, &j->p32, nd * sizeof(float)));
+    FRAC_TRY(jalloc(j, &j->q32, nd * sizeof(float)));
+    FRAC_TRY(jalloc(j, &j->ws32, apply_workspace_bytes(op, FRAC_F32, 1)));
+  } else {
+    FRAC_TRY(jalloc(j, &j->p64, nd * sizeof(double)));
+    FRAC_TRY(jalloc(j, &j->q64, nd * sizeof(double)));
+  }
+  k_dot<double><<<(unsigned)nb, kTB, 0, j->s>>>(j->f, j->f, nd, j->partial, nullptr);
+  k_sum_to<<<1, kTB, 0, j->s>>>(j->partial, nb, j->scal + 0);
+  if (j->opts.use_x0) {
+    FRAC_TRY(apply_t<double>(op, j->u, j->Au64, 1, j->ws64, j->s));
+  } else {
+    FRAC_CUDA_TRY(cudaMemsetAsync(j->u, 0, nd * sizeof(double), j->s));
+    FRAC_CUDA_TRY(cudaMemsetAsync(j->Au64, 0, nd * sizeof(double), j->s));
+  }
+  k_residual<<<(unsigned)nb, kTB, 0, j->s>>>(j->f, j->Au64, j->r64, nd, j->partial);
+  k_sum_to<<<1, kTB, 0, j->s>>>(j->partial, nb, j->scal + 1);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  FRAC_CUDA_TRY(cudaMemcpyAsync(j->hm->scal, j->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, j->s));
+  FRAC_CUDA_TRY(cudaEventRecord(j->ev, j->s));
+  j->phase = PH_NORM;
+  return FRAC_OK;
+}
+
+extern "C" int frac_engine_submit(frac_engine* e, const frac_op* op, const double* f, double* u,
+                                  const frac_solve_opts* opts, int64_t* job) {
+  if (!e || !op || !f || !u || !opts || !job) return FRAC_EINVAL;
+  if (!(opts->rtol > 0.0) || opts->max_iter < 1) return FRAC_EINVAL;
+  if (opts->precision != FRAC_PLAIN_F64 && opts->precision != FRAC_MIXED_IR) return FRAC_EINVAL;
+  Job* j = new (std::nothrow) Job();
+  if (!j) return FRAC_ENOMEM;
+  j->id = e->next_id++;
+  j->op = op;
+  j->opts = *opts;
+  j->s = e->streams[e->next_stream++ % e->streams.size()];
+  j->t0 = std::chrono::steady_clock::now();
+  const int s = submit_impl(e, j, f, u);
+  e->bytes += j->bytes;
+  if (s != FRAC_OK) {
+    cudaStreamSynchronize(j->s);
+    release_job(e, j);
+    return s;
+  }
+  e->jobs.push_back(j);
+  *job = j->id;
+  return FRAC_OK;
+}
+
+extern "C" int frac_engine_poll(frac_engine* e, int block, frac_job_result* out, int cap, int* count) {
+  if (!e || !count || cap < 0 || (cap > 0 && !out)) return FRAC_EINVAL;
+  int first_err = FRAC_OK;
+  for (;;) {
+    for (size_t i = 0; i < e->jobs.size();) {
+      Job* j = e->jobs[i];
+      cudaError_t q = cudaEventQuery(j->ev);
+      if (q == cudaErrorNotReady) {
+        ++i;
+        continue;
+      }
+      int s = (q == cudaSuccess) ? FRAC_OK : record_cuda_error(q, __FILE__, __LINE__, "cudaEventQuery");
+      if (s == FRAC_OK) {
+        const size_t before = j->bytes;
+        s = advance(j);
+        e->bytes += j->bytes - before;
+      }
+      if (s != FRAC_OK) {
+        j->result.status = s;
+        j->phase = PH_DONE;
+        if (first_err == FRAC_OK) first_err = s;
+        cudaStreamSynchronize(j->s);
+      }
+      if (j->phase == PH_DONE) {
+        frac_job_result r;
+        r.job = j->id;
+        r.info = j->result;
+        r.submit_to_done_ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - j->t0).count();
+        e->finished.push_back(r);
+        release_job(e, j);
+        e->jobs.erase(e->jobs.begin() + i);
+      } else {
+        ++i;
+      }
+    }
+    if (!block || !e->finished.empty() || e->jobs.empty()) break;
+    std::this_thread::yield();
+  }
+  const int n = (int)std::min<size_t>((size_t)cap, e->finished.size());
+  for (int i = 0; i < n; ++i) out[i] = e->finished[i];
+  e->finished.erase(e->finished.begin(), e->finished.begin() + n);
+  *count = n;
+  return first_err;
+}
+
+extern "C" int frac_engine_stats(const frac_engine* e, int64_t* active, size_t* device_bytes) {
+  if (!e) return FRAC_EINVAL;
+  if (active) *active = (int64_t)e->jobs.size();
+  if (device_bytes) *device_bytes = e->bytes;
+  return FRAC_OK;
+}
+
+extern "C" void frac_engine_destroy(frac_engine* e) {
+  if (!e) return;
+  for (cudaStream_t s : e->streams) cudaStreamSynchronize(s);
+  for (Job* j : e->jobs) release_job(e, j);
+  e->jobs.clear();
+  for (cudaStream_t s : e->streams) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (Mirror* m : e->mirror_blocks) cudaFreeHost(m);
+  delete e;
+}
+
+namespace frac {
+// Make every engine stream wait for the work already queued on `caller`.
+int engine_wait_for(frac_engine* e, cudaStream_t caller) {
+  cudaEvent_t ev;
+  FRAC_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t r = cudaEventRecord(ev, caller);
+  for (cudaStream_t s : e->streams)
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(s, ev, 0);
+  cudaEventDestroy(ev);
+  FRAC_CUDA_TRY(r);
+  return FRAC_OK;
+}
 }  // namespace frac

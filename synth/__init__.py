@@ -199,3 +199,20 @@ def served_problems(count: int, seed: int = BASE_SEED, sides3d=(63, 127, 255)) -
             n += 1
         out.append(Problem(d, n, alpha, degree, lam, seed * 7919 + j))
     return out
+
+
+def served_problems_repeat(count: int, seed: int = BASE_SEED, fixed: int = 16, share: float = 0.8,
+                           sides3d=(63, 127, 255)) -> list[Problem]:
+    """The served mix with repeats: a share ``share`` of the requests are drawn
+    from ``fixed`` fixed problems (d, n, alpha, degree, lambda), the rest fresh."""
+    base = served_problems(fixed, seed=seed + 17, sides3d=sides3d)
+    fresh = served_problems(count, seed=seed, sides3d=sides3d)
+    rng = np.random.default_rng(seed + 23)
+    out = []
+    for j in range(count):
+        if rng.random() < share:
+            b = base[int(rng.integers(0, fixed))]
+            out.append(Problem(b.d, b.n, b.alpha, b.degree, b.lam, seed * 104729 + j))
+        else:
+            out.append(fresh[j])
+    return out
