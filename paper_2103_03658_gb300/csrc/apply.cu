@@ -35,12 +35,19 @@ template <typename T> __host__ __device__ constexpr int blk() { return 32 / (int
 // minimum resident blocks per SM requested from the compiler: at least 512 resident
 // threads for FP32 kernels and 256 for FP64 (registers capped at 128 and 255 per thread);
 // the row kernels ask for twice that
+// (clamped to the 32 resident blocks an SM can hold)
+__host__ __device__ constexpr int clamp_blocks(int b) { return b < 1 ? 1 : (b > 32 ? 32 : b); }
 template <typename T> __host__ __device__ constexpr int minb(int nt) {
-  return ((int)sizeof(T) == 4 ? 512 : 256) / nt > 1 ? ((int)sizeof(T) == 4 ? 512 : 256) / nt : 1;
+  return clamp_blocks(((int)sizeof(T) == 4 ? 512 : 256) / nt);
 }
 // the row kernels hold one FFT per thread group and need fewer registers: 1024 / 512
 template <typename T> __host__ __device__ constexpr int minb_rows(int nt) {
-  return ((int)sizeof(T) == 4 ? 1024 : 512) / nt > 1 ? ((int)sizeof(T) == 4 ? 1024 : 512) / nt : 1;
+  return clamp_blocks(((int)sizeof(T) == 4 ? 1024 : 512) / nt);
+}
+// the column kernels: FP32 fits 64 registers without spills (two 512-thread
+// blocks per SM); FP64 needs more than 128 and keeps one block
+template <typename T> __host__ __device__ constexpr int minb_cols(int nt) {
+  return sizeof(T) == 4 ? minb_rows<T>(nt) : minb<T>(nt);
 }
 
 // ---------------------------------------------------------------------------
@@ -59,23 +66,25 @@ k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const
   C* buf = sm + line * LS;
   const int64_t va = 2 * ((int64_t)blockIdx.x * LINES + line), vb = va + 1;
   const bool ha = va < batch, hb = vb < batch;
+  // n <= M/2: entries e >= E/2 (x >= M/2) are zero padding, and only
+  // outputs x < n are kept, so both transforms are half-pruned
   C v[E];
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
+  for (int e = 0; e < E / 2; ++e) {
     const int x = tl + e * TPL;
     T re = (x < n && ha) ? u[va * n + x] : T(0);
     T im = (x < n && hb) ? u[vb * n + x] : T(0);
     v[e] = C{re, im};
   }
-  fft_reg<C, LOGM, false>(v, buf, tl, tw);
+  fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int k = tl + e * TPL;
     v[e] = cscale(v[e], lam[k <= M / 2 ? k : M - k]);
   }
-  fft_reg<C, LOGM, true>(v, buf, tl, tw);
+  fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
+  for (int e = 0; e < E / 2; ++e) {
     const int x = tl + e * TPL;
     if (x < n) {
       if (ha) y[va * n + x] = v[e].x;
@@ -159,7 +168,7 @@ k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int64_t nrows, int KB,
     const T be = (T)st->beta;
     T* p = const_cast<T*>(u);
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
+    for (int e = 0; e < E / 2; ++e) {  // x < n <= M/2: e < E/2
       const int x = tl + e * TPL;
       T re = T(0), im = T(0);
       if (x < n && h0) {
@@ -174,14 +183,14 @@ k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int64_t nrows, int KB,
     }
   } else {
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
+    for (int e = 0; e < E / 2; ++e) {
       const int x = tl + e * TPL;
       T re = (x < n && h0) ? u[r0 * n + x] : T(0);
       T im = (x < n && h1) ? u[r1 * n + x] : T(0);
       v[e] = C{re, im};
     }
   }
-  fft_reg<C, LOGM, false>(v, buf, tl, tw);
+  fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);  // upper half is zero padding
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < E; ++e) buf[pidx(tl + e * TPL)] = v[e];
@@ -239,10 +248,10 @@ k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nr
     }
     v[e] = C{v0.x - v1.y, v0.y + v1.x};  // v0 + i v1
   }
-  fft_reg<C, LOGM, true>(v, buf, tl, tw);
+  fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // only x < n <= M/2 is kept
   T dot = T(0);
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
+  for (int e = 0; e < E / 2; ++e) {
     const int x = tl + e * TPL;
     if (x < n) {
       if (h0) {
@@ -290,7 +299,7 @@ struct ColArgs {
 };
 
 template <typename T, int LOGM, int MODE>
-__global__ void __launch_bounds__(blk<T>() * tpl(LOGM), minb<T>(blk<T>() * tpl(LOGM)))
+__global__ void __launch_bounds__(blk<T>() * tpl(LOGM), minb_cols<T>(blk<T>() * tpl(LOGM)))
 k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw,
        const CGState* st) {
   using C = cplx_t<T>;
@@ -329,13 +338,13 @@ k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam
   } else {
     const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl : in + (o * KB + tile) * nB + cl;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
+    for (int e = 0; e < E / 2; ++e) {  // j < n <= M/2; the rest is zero padding
       const int j = tl + e * TPL;
       v[e] = (live && j < n) ? src[(int64_t)j * B] : C{0, 0};
     }
   }
   // ---- transforms
-  if (MODE != YINV) fft_reg<C, LOGM, false>(v, buf, tl, tw);
+  if (MODE != YINV) fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);
   if (MODE == SYM2 || MODE == ZSYM) {
     const T* lrow = (MODE == SYM2) ? lam + k1 : lam + (int64_t)k2r * K + k1;
     const int64_t kstride = (MODE == SYM2) ? K : (int64_t)K * K;
@@ -346,7 +355,7 @@ k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam
       v[e] = cscale(v[e], live ? lrow[kr * kstride] : T(0));
     }
   }
-  if (MODE != YFWD) fft_reg<C, LOGM, true>(v, buf, tl, tw);
+  if (MODE != YFWD) fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // keeps j < n only
   // ---- store
   if (!live) return;
   if (MODE == YFWD) {
@@ -361,7 +370,7 @@ k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam
     C* dst = (MODE == ZSYM) ? out + o * W2slab + tile * nB + cl
                             : out + (o * KB + tile) * nB + cl;  // SYM2 in place; YINV to W1 slab o
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
+    for (int e = 0; e < E / 2; ++e) {
       const int j = tl + e * TPL;
       if (j < n) dst[(int64_t)j * B] = v[e];
     }

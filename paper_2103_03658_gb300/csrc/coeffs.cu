@@ -15,16 +15,16 @@ namespace frac {
 // Gauss-Legendre rules on [-1, 1] (Newton iteration on P_q, host, FP64)
 // ---------------------------------------------------------------------------
 
-constexpr int kNumRules = 8;
-constexpr int kRuleTotal = 81;
+constexpr int kNumRules = 9;
+constexpr int kRuleTotal = 84;
 // rule r: q points, stored from offset rule_off(r)
 __host__ __device__ constexpr int rule_q(int r) {
-  return r == 0 ? 4 : r == 1 ? 5 : r == 2 ? 6 : r == 3 ? 8 : r == 4 ? 10 : r == 5 ? 12 : r == 6 ? 16 : 20;
+  return r == 0 ? 4 : r == 1 ? 5 : r == 2 ? 6 : r == 3 ? 8 : r == 4 ? 10 : r == 5 ? 12 : r == 6 ? 16 : r == 7 ? 20 : 3;
 }
 // (no recursion: a recursive device function called with a runtime argument
 // would need stack beyond the kernel's static frame)
 __host__ __device__ constexpr int rule_off(int r) {
-  return r == 0 ? 0 : r == 1 ? 4 : r == 2 ? 9 : r == 3 ? 15 : r == 4 ? 23 : r == 5 ? 33 : r == 6 ? 45 : 61;
+  return r == 0 ? 0 : r == 1 ? 4 : r == 2 ? 9 : r == 3 ? 15 : r == 4 ? 23 : r == 5 ? 33 : r == 6 ? 45 : r == 7 ? 61 : 81;
 }
 __host__ __device__ constexpr bool rule_table_ok(int r) {
   return r == kNumRules ? true : (rule_off(r) + rule_q(r) == (r + 1 == kNumRules ? kRuleTotal : rule_off(r + 1)) &&
@@ -297,7 +297,8 @@ __device__ int pick_rule(double ratio) {
   if (ratio < 16.0) return 3;  // 8
   if (ratio < 32.0) return 2;  // 6
   if (ratio < 64.0) return 1;  // 5
-  return 0;                    // 4
+  if (ratio < 128.0) return 0; // 4
+  return 8;                    // 3: error ~ (1 / (2 ratio))^6 < 4e-15 relative
 }
 
 // Monomial coefficients (in t = xi / h) of the local basis on the origin element.
@@ -460,6 +461,161 @@ __global__ void k_weights(WParams P, double* __restrict__ omega, int64_t count) 
     total += acc;
   }
   if (CHK(idx, count)) omega[idx] = total;
+}
+
+// ---------------------------------------------------------------------------
+// Tiled weights (d >= 2): one block per tile of T^d nodes.  Phase 1 computes,
+// once, the integrals of every local basis product over every element that
+// touches the tile (the element is shared by up to 2^d nodes of the tile) and
+// keeps them in shared memory; phase 2 lets each node sum its contributions
+// in a fixed order.  Elements per axis: p = 0: e = k (one node); p = 1:
+// [e h, (e+1) h], nodes e, e+1; p = 2: [2e h, (2e+2) h], nodes 2e, 2e+1, 2e+2.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int elem_first_node(int p, int e) { return p == 2 ? 2 * e : e; }
+
+// 1D element e of degree p: interval and the local basis function l (product form)
+__device__ AxisEl elem_axis(const WParams& P, int e, int l) {
+  const double h = P.h, L = P.N * h;
+  if (P.p == 0) return AxisEl{fmax(0.0, (e - 0.5) * h), fmin(L, (e + 0.5) * h), 0, 0, 1.0, 0, e == 0 ? 0 : -1};
+  if (P.p == 1) {
+    const double a = e * h;
+    if (l == 0) return AxisEl{a, a + h, a + h, 0, -1.0 / h, 1, e == 0 ? 0 : -1};
+    return AxisEl{a, a + h, a, 0, 1.0 / h, 1, e == 0 ? 1 : -1};
+  }
+  const double a = 2 * e * h;
+  if (l == 0) return AxisEl{a, a + 2 * h, a + h, a + 2 * h, 0.5 / (h * h), 2, e == 0 ? 0 : -1};
+  if (l == 1) return AxisEl{a, a + 2 * h, a, a + 2 * h, -1.0 / (h * h), 2, e == 0 ? 1 : -1};
+  return AxisEl{a, a + 2 * h, a, a + h, 0.5 / (h * h), 2, e == 0 ? 2 : -1};
+}
+
+template <int D, int T>
+__global__ void __launch_bounds__(256) k_weights_tiled(WParams P, double* __restrict__ omega) {
+  constexpr int NL = 27;                       // max local basis products per element ((p+1)^d)
+  extern __shared__ __align__(16) double eint[];
+  const int p = P.p;
+  const int nloc1 = p + 1, nloc = (D == 2) ? nloc1 * nloc1 : nloc1 * nloc1 * nloc1;
+  const int64_t N1 = P.N + 1;
+  const int ne_axis = (p == 0) ? (int)N1 : (p == 1 ? (int)P.N : (int)(P.N / 2));
+  // tile origin (node indices) from the block index
+  int64_t bid = blockIdx.x;
+  const int64_t tiles_axis = (N1 + T - 1) / T;
+  int k0[3] = {0, 0, 0};
+  for (int i = 0; i < D; ++i) {
+    k0[i] = (int)(bid % tiles_axis) * T;
+    bid /= tiles_axis;
+  }
+  // element range per axis touching nodes [k0, k0 + T)
+  int e0[3], ecount[3];
+  for (int i = 0; i < D; ++i) {
+    const int lo_node = k0[i], hi_node = min((int)N1, k0[i] + T) - 1;
+    int ea, eb;
+    if (p == 0) { ea = lo_node; eb = hi_node; }
+    else if (p == 1) { ea = max(0, lo_node - 1); eb = min(ne_axis - 1, hi_node); }
+    else { ea = max(0, (lo_node - 1) / 2); eb = min(ne_axis - 1, hi_node / 2); }
+    e0[i] = ea;
+    ecount[i] = eb - ea + 1;
+  }
+  const int nelem = ecount[0] * ecount[1] * (D == 3 ? ecount[2] : 1);
+  // ---- phase 1: element integrals
+  for (int t = threadIdx.x; t < nelem; t += blockDim.x) {
+    int el[3] = {t % ecount[0] + e0[0], (t / ecount[0]) % ecount[1] + e0[1], D == 3 ? t / (ecount[0] * ecount[1]) + e0[2] : 0};
+    double acc[NL];
+    for (int c = 0; c < NL; ++c) acc[c] = 0.0;
+    bool origin = true;
+    double lo2 = 0.0, width = 0.0;
+    AxisEl ax[3][3];
+    for (int i = 0; i < D; ++i)
+      for (int l = 0; l < nloc1; ++l) ax[i][l] = elem_axis(P, el[i], l);
+    for (int i = 0; i < D; ++i) {
+      origin = origin && el[i] == 0;
+      lo2 += ax[i][0].lo * ax[i][0].lo;
+      width = fmax(width, ax[i][0].hi - ax[i][0].lo);
+    }
+    if (origin) {
+      for (int c = 0; c < nloc; ++c) {
+        int l[3] = {c % nloc1, (c / nloc1) % nloc1, D == 3 ? c / (nloc1 * nloc1) : 0};
+        acc[c] = origin_element(P, l, ax[0][0].hi - ax[0][0].lo);
+      }
+    } else {
+      const int rule = pick_rule(sqrt(lo2) / width);
+      const int q = rule_q(rule), off = rule_off(rule);
+      double X[3][20], Wb[3][3][20];
+      for (int i = 0; i < D; ++i) {
+        const double c = 0.5 * (ax[i][0].hi + ax[i][0].lo), hw = 0.5 * (ax[i][0].hi - ax[i][0].lo);
+        for (int g = 0; g < q; ++g) {
+          X[i][g] = c + hw * c_gl_x[off + g];
+          const double w = hw * c_gl_w[off + g];
+          for (int l = 0; l < nloc1; ++l) Wb[i][l][g] = w * basis_val(ax[i][l], X[i][g]);
+        }
+      }
+      if (D == 2) {
+        for (int g1 = 0; g1 < q; ++g1) {
+          const double x1 = X[1][g1] * X[1][g1];
+          for (int g0 = 0; g0 < q; ++g0) {
+            const double m = mu_r2(X[0][g0] * X[0][g0] + x1, P);
+            for (int l1 = 0; l1 < nloc1; ++l1) {
+              const double m1 = m * Wb[1][l1][g1];
+              for (int l0 = 0; l0 < nloc1; ++l0) acc[l1 * nloc1 + l0] += m1 * Wb[0][l0][g0];
+            }
+          }
+        }
+      } else {
+        for (int g2 = 0; g2 < q; ++g2) {
+          const double x2 = X[2][g2] * X[2][g2];
+          for (int g1 = 0; g1 < q; ++g1) {
+            const double x12 = X[1][g1] * X[1][g1] + x2;
+            for (int g0 = 0; g0 < q; ++g0) {
+              const double m = mu_r2(X[0][g0] * X[0][g0] + x12, P);
+              for (int l2 = 0; l2 < nloc1; ++l2) {
+                const double m2 = m * Wb[2][l2][g2];
+                for (int l1 = 0; l1 < nloc1; ++l1) {
+                  const double m1 = m2 * Wb[1][l1][g1];
+                  for (int l0 = 0; l0 < nloc1; ++l0) acc[(l2 * nloc1 + l1) * nloc1 + l0] += m1 * Wb[0][l0][g0];
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    for (int c = 0; c < nloc; ++c) eint[(int64_t)t * nloc + c] = acc[c];
+  }
+  __syncthreads();
+  // ---- phase 2: nodes of the tile sum their element contributions
+  const int tnodes = (D == 2) ? T * T : T * T * T;
+  for (int t = threadIdx.x; t < tnodes; t += blockDim.x) {
+    int k[3] = {k0[0] + t % T, k0[1] + (t / T) % T, D == 3 ? k0[2] + t / (T * T) : 0};
+    bool inside = true;
+    for (int i = 0; i < D; ++i) inside = inside && k[i] < N1;
+    if (!inside) continue;
+    // per axis: elements containing node k and the local index of k in them
+    int ee[3][2], ll[3][2], ne[3] = {1, 1, 1};
+    for (int i = 0; i < D; ++i) {
+      ne[i] = 0;
+      if (p == 0) { ee[i][0] = k[i]; ll[i][0] = 0; ne[i] = 1; }
+      else if (p == 1) {
+        if (k[i] >= 1) { ee[i][ne[i]] = k[i] - 1; ll[i][ne[i]++] = 1; }
+        if (k[i] < P.N) { ee[i][ne[i]] = k[i]; ll[i][ne[i]++] = 0; }
+      } else {
+        if (k[i] & 1) { ee[i][0] = k[i] / 2; ll[i][0] = 1; ne[i] = 1; }
+        else {
+          if (k[i] >= 2) { ee[i][ne[i]] = k[i] / 2 - 1; ll[i][ne[i]++] = 2; }
+          if (k[i] <= P.N - 2) { ee[i][ne[i]] = k[i] / 2; ll[i][ne[i]++] = 0; }
+        }
+      }
+    }
+    double tot = 0.0;
+    for (int a = 0; a < ne[0]; ++a)
+      for (int b = 0; b < ne[1]; ++b)
+        for (int cc = 0; cc < (D == 3 ? ne[2] : 1); ++cc) {
+          const int le = (ee[0][a] - e0[0]) + ecount[0] * ((ee[1][b] - e0[1]) + (D == 3 ? ecount[1] * (ee[2][cc] - e0[2]) : 0));
+          const int lc = ll[0][a] + nloc1 * (ll[1][b] + (D == 3 ? nloc1 * ll[2][cc] : 0));
+          if (CHK(le, nelem) && CHK(lc, nloc)) tot += eint[(int64_t)le * nloc + lc];
+        }
+    int64_t idx = k[0] + N1 * (k[1] + (D == 3 ? N1 * k[2] : 0));
+    omega[idx] = tot;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -626,7 +782,26 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   const int64_t nblk = ceil_div(ngen, TB);
   FRAC_CUDA_TRY(cudaMallocAsync(&omega, ngen * sizeof(double), st));
   FRAC_CUDA_TRY(cudaMallocAsync(&partial, nblk * sizeof(double), st));
-  k_weights<<<(unsigned)nblk, TB, 0, st>>>(P, omega, ngen);
+  if (d == 1) {
+    k_weights<<<(unsigned)nblk, TB, 0, st>>>(P, omega, ngen);
+  } else {
+    // tiles of 16^2 / 8^3 nodes; shared memory = elements per tile x local products
+    const int T = d == 2 ? 16 : 8;
+    const int64_t tiles_axis = ceil_div(op->N + 1, T);
+    int64_t tiles = 1;
+    for (int i = 0; i < d; ++i) tiles *= tiles_axis;
+    const int ea = (pr.degree == 0) ? T : (pr.degree == 1 ? T + 1 : T / 2 + 2);
+    const int nl1 = pr.degree + 1;
+    size_t sm = sizeof(double);
+    for (int i = 0; i < d; ++i) sm *= (size_t)ea * nl1;
+    if (d == 2) {
+      FRAC_CUDA_TRY(cudaFuncSetAttribute(k_weights_tiled<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_weights_tiled<2, 16><<<(unsigned)tiles, 256, sm, st>>>(P, omega);
+    } else {
+      FRAC_CUDA_TRY(cudaFuncSetAttribute(k_weights_tiled<3, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_weights_tiled<3, 8><<<(unsigned)tiles, 256, sm, st>>>(P, omega);
+    }
+  }
   FRAC_CUDA_TRY(cudaGetLastError());
   k_stencil<<<(unsigned)nblk, TB, 0, st>>>(P, omega, op->a, partial, ngen);
   FRAC_CUDA_TRY(cudaGetLastError());

@@ -104,6 +104,34 @@ __device__ __forceinline__ void dft(C* x) {
   }
 }
 
+template <int R, bool INV, typename C, int... Is>
+__device__ __forceinline__ void split_half(const C* x, C* a, C* b, std::integer_sequence<int, Is...>) {
+  ((a[Is] = x[Is]), ...);
+  ((b[Is] = mul_w16<Is * (16 / R), INV>(x[Is])), ...);
+}
+
+// R-point DFT of a vector whose upper half x[R/2 .. R-1] is zero (those
+// entries are not read).  Decimation in frequency: with the upper half zero,
+// the even outputs are the R/2-point DFT of x[0 .. R/2-1] and the odd outputs
+// that of x[i] w_R^i.
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void dft_zin(C* x) {
+  if constexpr (R == 2) {
+    x[1] = x[0];
+  } else if constexpr (R > 2) {
+    constexpr int H = R / 2;
+    C a[H], b[H];
+    split_half<R, INV>(x, a, b, std::make_integer_sequence<int, H>{});
+    dft<H, INV>(a);
+    dft<H, INV>(b);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      x[2 * k] = a[k];
+      x[2 * k + 1] = b[k];
+    }
+  }
+}
+
 // One Stockham pass on this thread's line; tl = thread index within the line.
 template <typename C, int LOGM, int P, bool INV>
 __device__ __forceinline__ void pass(C* __restrict__ buf, int tl, const C* __restrict__ tw) {
@@ -153,9 +181,15 @@ __device__ __forceinline__ void pass(C* __restrict__ buf, int tl, const C* __res
 // v[b + r NB] in the last pass (NB = E / R), so no permutation is needed at
 // either end.  The caller must not touch `buf` between the entry __syncthreads
 // and the return.
+//
+// Zero-padded transforms: ZIN states that entries M/2 .. M-1 of the input are
+// zero (v[e] for e >= E/2 is not read); ZOUT that only outputs 0 .. M/2-1 are
+// wanted (v[e] for e >= E/2 is left undefined).  A convolution of n <= M/2
+// points embedded in length M meets both, and the first and last passes then
+// skip the butterflies' dead halves.
 // ---------------------------------------------------------------------------
 
-template <typename C, int LOGM, int P, bool INV>
+template <typename C, int LOGM, int P, bool INV, bool ZIN, bool ZOUT>
 __device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
   constexpr int M = 1 << LOGM;
   constexpr int NP = npasses(LOGM);
@@ -170,10 +204,11 @@ __device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ bu
   constexpr bool FIRST = (P == 0), LAST = (P == NP - 1);
   C w[E];
   if constexpr (FIRST) {
+    // butterfly j < M/R reads j + r M/R, which lies in the zero half iff r >= R/2
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
-      for (int r = 0; r < R; ++r) w[b * R + r] = v[b + r * NB];
+      for (int r = 0; r < (ZIN ? R / 2 : R); ++r) w[b * R + r] = v[b + r * NB];
   } else {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -194,17 +229,32 @@ __device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ bu
     const int j = tl + b * TPL;
     const int k = j & (Ns - 1);
     if constexpr (Ns > 1) {
+      if constexpr (sizeof(decltype(w[0].x)) == 4) {
+        // FP32: one table load, the other powers by binary splitting
+        // (w^r = w^{r/2} w^{r - r/2}, at most four products deep)
+        C wp[R];
+        wp[1] = tw[k * TWS];
+        if (INV) wp[1].y = -wp[1].y;
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        C t = tw[r * k * TWS];
-        if (INV) t.y = -t.y;
-        w[b * R + r] = cmul(w[b * R + r], t);
+        for (int r = 2; r < R; ++r) wp[r] = cmul(wp[r >> 1], wp[r - (r >> 1)]);
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[b * R + r] = cmul(w[b * R + r], wp[r]);
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C t = tw[r * k * TWS];
+          if (INV) t.y = -t.y;
+          w[b * R + r] = cmul(w[b * R + r], t);
+        }
       }
     }
-    dft<R, INV>(w + b * R);
+    if constexpr (FIRST && ZIN)
+      dft_zin<R, INV>(w + b * R);
+    else
+      dft<R, INV>(w + b * R);
     if constexpr (LAST) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b + r * NB] = w[b * R + r];
+      for (int r = 0; r < (ZOUT ? R / 2 : R); ++r) v[b + r * NB] = w[b * R + r];
     } else {
       const int base = ((j >> NSB) << (NSB + RB)) + k;
       if constexpr (Ns % 16 == 0) {
@@ -224,20 +274,20 @@ __device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ bu
   if constexpr (!LAST) __syncthreads();  // writes visible to the next pass
 }
 
-template <typename C, int LOGM, bool INV, int P = 0>
+template <typename C, int LOGM, bool INV, bool ZIN, bool ZOUT, int P = 0>
 __device__ __forceinline__ void reg_passes(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
   if constexpr (P < npasses(LOGM)) {
-    reg_pass<C, LOGM, P, INV>(v, buf, tl, tw);
-    reg_passes<C, LOGM, INV, P + 1>(v, buf, tl, tw);
+    reg_pass<C, LOGM, P, INV, ZIN, ZOUT>(v, buf, tl, tw);
+    reg_passes<C, LOGM, INV, ZIN, ZOUT, P + 1>(v, buf, tl, tw);
   }
 }
 
 // FFT of the line held in registers (see above); `buf` is the line's shared
 // buffer (line_stride(LOGM) entries), used only when there is more than one pass.
-template <typename C, int LOGM, bool INV>
+template <typename C, int LOGM, bool INV, bool ZIN = false, bool ZOUT = false>
 __device__ __forceinline__ void fft_reg(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
   if constexpr (npasses(LOGM) > 1) __syncthreads();  // earlier users of buf are done
-  reg_passes<C, LOGM, INV>(v, buf, tl, tw);
+  reg_passes<C, LOGM, INV, ZIN, ZOUT>(v, buf, tl, tw);
 }
 
 template <typename C, int LOGM, bool INV, int P = 0>
