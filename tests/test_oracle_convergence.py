@@ -91,15 +91,19 @@ def test_tempered_lambda_zero_is_fractional_laplacian():
 
 
 def test_synth_rhs_matches_oracle_closed_form():
-    """The workload right-hand side (polynomial, s = 1 + alpha/2) equals the
-    oracle's 2F1 closed form."""
+    """Inside the unit ball the workload right-hand side (polynomial, s = 1 +
+    alpha/2) equals the oracle's 2F1 closed form, which holds for |x| < 1 only;
+    the cube corners outside the ball are checked against the definition below."""
     import synth
     for d in (1, 2, 3):
         for alpha in (0.4, 1.6):
             n = 15
             f = synth.ball_power_rhs(d, n, alpha)
-            ref = O.fl_ball_power(d, alpha, 1 + alpha / 2, synth.radius2(d, n))
-            assert np.allclose(f, ref, rtol=1e-13, atol=1e-13)
+            r2 = synth.radius2(d, n)
+            inside = r2 < 1.0
+            assert inside.sum() > n ** d // 2
+            ref = O.fl_ball_power(d, alpha, 1 + alpha / 2, r2[inside])
+            assert np.allclose(f[inside], ref, rtol=1e-13, atol=1e-13)
 
 
 @pytest.mark.parametrize("d,alpha", [(2, 0.7), (3, 0.7), (3, 1.6)])
