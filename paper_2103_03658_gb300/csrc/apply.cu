@@ -191,24 +191,27 @@ k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int64_t nrows, int KB,
     }
   }
   fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);  // upper half is zero padding
+  // separation needs Z[k] and Z[M-k] for k in [0, M/2]: each thread keeps its
+  // lower-half Z[k] in registers and reads the mirror from the upper half,
+  // which alone goes through the line buffer
   __syncthreads();
 #pragma unroll
-  for (int e = 0; e < E; ++e) buf[pidx(tl + e * TPL)] = v[e];
+  for (int e = E / 2; e < E; ++e) buf[pidx(tl + e * TPL)] = v[e];
   __syncthreads();
   C* W0 = W + wrow<B>(r0, n, KB);
   C* W1 = W + wrow<B>(r1, n, KB);
+  auto emit = [&](int k, C z, C zc) {
+    const C s = cadd(z, zc), dd = csub(z, zc);
+    const int64_t kc = wcol<B>(k, n);
+    if (h0) W0[kc] = s;
+    if (h1) W1[kc] = C{dd.y, -dd.x};
+  };
 #pragma unroll
-  for (int e = 0; e <= E / 2; ++e) {
-    const int k = tl + e * TPL;
-    if (k <= M / 2) {
-      const C z = buf[pidx(k)];
-      const C zc = cconj(buf[pidx((M - k) & (M - 1))]);
-      const C s = cadd(z, zc), dd = csub(z, zc);
-      const int64_t kc = wcol<B>(k, n);
-      if (h0) W0[kc] = s;
-      if (h1) W1[kc] = C{dd.y, -dd.x};
-    }
+  for (int e = 0; e < E / 2; ++e) {
+    const int k = tl + e * TPL;  // k < M/2; M - k is in the upper half unless k = 0
+    emit(k, v[e], cconj(k == 0 ? v[e] : buf[pidx(M - k)]));
   }
+  if (tl == 0) emit(M / 2, v[E / 2], cconj(v[E / 2]));
 }
 
 // ---------------------------------------------------------------------------
@@ -235,19 +238,32 @@ k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nr
   C v[E];
   const C* W0 = W + wrow<B>(h0 ? r0 : 0, n, KB);
   const C* W1 = W + wrow<B>(h1 ? r1 : 0, n, KB);
+  // line z = W0 + i W1 extended Hermitian-wise: z[x] = W0[x] + i W1[x] and
+  // z[M-x] = conj(W0[x]) + i conj(W1[x]) for x in [0, M/2], so each half
+  // spectrum entry is read once; the thread that reads W[x] leaves z[M-x] in
+  // the line buffer for its owner
+  auto load = [&](int x, C& lo, C& hi) {
+    const int64_t kc = wcol<B>(x, n);
+    const C v0 = h0 ? W0[kc] : C{0, 0};
+    const C v1 = h1 ? W1[kc] : C{0, 0};
+    lo = C{v0.x - v1.y, v0.y + v1.x};   // v0 + i v1
+    hi = C{v0.x + v1.y, v1.x - v0.y};   // conj(v0) + i conj(v1)
+  };
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int x = tl + e * TPL;
-    const int k = x <= M / 2 ? x : M - x;
-    const int64_t kc = wcol<B>(k, n);
-    C v0 = h0 ? W0[kc] : C{0, 0};
-    C v1 = h1 ? W1[kc] : C{0, 0};
-    if (x > M / 2) {
-      v0 = cconj(v0);
-      v1 = cconj(v1);
-    }
-    v[e] = C{v0.x - v1.y, v0.y + v1.x};  // v0 + i v1
+  for (int e = 0; e < E / 2; ++e) {
+    const int x = tl + e * TPL;  // x < M/2
+    C hi;
+    load(x, v[e], hi);
+    if (x > 0) buf[pidx(M - x)] = hi;
   }
+  if (tl == 0) {
+    C lo, hi;
+    load(M / 2, lo, hi);
+    buf[pidx(M / 2)] = lo;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = E / 2; e < E; ++e) v[e] = buf[pidx(tl + e * TPL)];
   fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // only x < n <= M/2 is kept
   T dot = T(0);
 #pragma unroll
