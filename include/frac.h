@@ -176,14 +176,50 @@ int frac_solve(const frac_op* op, const double* f, const double* g, double* u,
 /*
  * frac_solve_batch -- solve `count` independent problems (ops[i], f[i], u[i],
  * all device pointers) with the same options; info[i] filled per problem
- * (host array).  Problems run concurrently on the device: 1D problems of
- * M <= 8192 are solved whole inside one thread block each, in one launch;
- * larger problems share the remaining work.  Errors as frac_solve, per problem
- * in info[i].status; the return value is the first nonzero status or FRAC_OK.
+ * (host array).  Problems run concurrently on the device:
+ *   - 1D problems of M <= 8192: solved whole inside one thread block each,
+ *     one launch per FFT length;
+ *   - 2D problems of M in [32, 1024] with FRAC_MIXED_IR: one persistent launch
+ *     of thread-block clusters takes them from work queues, largest first; the
+ *     larger FFT lengths are solved by a whole cluster each, the smaller by one
+ *     block each, as chosen by an autotuner that times each FFT length once
+ *     per device (the first batch with a new length pays for that timing);
+ *   - the others share a solve engine (frac_engine_*) on several streams.
+ * Errors as frac_solve, per problem in info[i].status; the return value is the
+ * first nonzero status or FRAC_OK.  Synchronizes `stream` before returning.
  */
 int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* const* f,
                      double* const* u, const frac_solve_opts* opts, frac_solve_info* info,
                      void* stream);
+
+/*
+ * frac_batch_last_plan -- the plan of the calling thread's last
+ * frac_solve_batch call that used the persistent 2D launch: cluster size,
+ * resident clusters launched, the smallest FFT length (log2) solved
+ * cluster-wide (11 = none), problems in each queue and the autotuner's
+ * predicted makespan in ms (its cost model is relative: compare plans, not
+ * times).  Errors: FRAC_EINVAL (NULL out, or no such call on this thread).
+ */
+typedef struct frac_batch_plan {
+  int32_t cluster_size;
+  int32_t clusters;
+  int32_t first_cluster_logm;
+  int32_t cluster_problems;
+  int32_t local_problems;
+  double predicted_ms;
+} frac_batch_plan;
+int frac_batch_last_plan(frac_batch_plan* out);
+
+/*
+ * frac_batch_pin_plan -- pin the persistent 2D launch of the calling thread's
+ * later frac_solve_batch calls: clusters of `cluster_size` CTAs (1, 2, 4, 8 or
+ * 16), with FFT lengths >= 2^first_cluster_logm solved cluster-wide (11: none,
+ * every problem on one block); cluster_size 0 returns to the autotuner.  The
+ * solutions do not depend on the plan beyond rounding.  Errors: FRAC_EINVAL
+ * (another size, or first_cluster_logm outside [5, 11]); a pinned size that the
+ * device cannot launch makes frac_solve_batch return FRAC_ENOTSUP.
+ */
+int frac_batch_pin_plan(int32_t cluster_size, int32_t first_cluster_logm);
 
 /*
  * Kernel timing (tracing aid, off by default; not part of the paper's method).

@@ -3,5 +3,5 @@ the integral fractional Laplacian and its tempered form (Wu & Zhang,
 arXiv 2103.03658): coefficients, FFT Toeplitz apply and CG / mixed-precision
 iterative-refinement solves, behind the C ABI of include/frac.h.
 """
-from ._native import (F32, F64, MIXED_IR, PLAIN_F64, Engine, FracError, FracOp, declared_entry_points,  # noqa: F401
-                      library_path, load, solve_batch)
+from ._native import (F32, F64, MIXED_IR, PLAIN_F64, Engine, FracError, FracOp, batch_last_plan,  # noqa: F401
+                      batch_pin_plan, declared_entry_points, library_path, load, solve_batch)

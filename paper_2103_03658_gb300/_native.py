@@ -49,6 +49,12 @@ class SolveInfo(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("rel_resid", ctypes.c_double)]
 
 
+class BatchPlan(ctypes.Structure):
+    _fields_ = [("cluster_size", ctypes.c_int32), ("clusters", ctypes.c_int32),
+                ("first_cluster_logm", ctypes.c_int32), ("cluster_problems", ctypes.c_int32),
+                ("local_problems", ctypes.c_int32), ("predicted_ms", ctypes.c_double)]
+
+
 class JobResult(ctypes.Structure):
     _fields_ = [("job", ctypes.c_int64), ("info", SolveInfo), ("submit_to_done_ms", ctypes.c_double)]
 
@@ -89,6 +95,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.frac_solve_batch.argtypes = [i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.frac_solve_batch.restype = i32
+    lib.frac_batch_last_plan.argtypes = [ctypes.POINTER(BatchPlan)]
+    lib.frac_batch_last_plan.restype = i32
+    lib.frac_batch_pin_plan.argtypes = [i32, i32]
+    lib.frac_batch_pin_plan.restype = i32
     lib.frac_engine_create.argtypes = [i32, ctypes.POINTER(vp)]
     lib.frac_engine_create.restype = i32
     lib.frac_engine_submit.argtypes = [vp, vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(ctypes.c_int64)]
@@ -285,6 +295,22 @@ def solve_batch(ops, fs, us, rtol: float = 1e-10, max_iter: int = 200000, precis
     if s not in (0, 4):
         raise FracError(s, "frac_solve_batch")
     return out
+
+
+def batch_last_plan() -> dict:
+    """Plan of this thread's last frac_solve_batch call with a persistent 2D launch."""
+    p = BatchPlan()
+    s = load().frac_batch_last_plan(ctypes.byref(p))
+    if s != 0:
+        raise FracError(s, "frac_batch_last_plan")
+    return {k: getattr(p, k) for k, _ in BatchPlan._fields_}
+
+
+def batch_pin_plan(cluster_size: int, first_cluster_logm: int = 11) -> None:
+    """Pin the persistent 2D launch of this thread's later batches (cluster_size 0: autotune)."""
+    s = load().frac_batch_pin_plan(cluster_size, first_cluster_logm)
+    if s != 0:
+        raise FracError(s, "frac_batch_pin_plan")
 
 
 def _info(si: SolveInfo) -> dict:

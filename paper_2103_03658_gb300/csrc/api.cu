@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "apply.cuh"
+#include "batch2d.cuh"
 
 namespace frac {
 
@@ -61,6 +62,9 @@ static int validate(const frac_problem* p) {
 }
 
 static thread_local char g_detail[256] = "";
+static thread_local frac_batch_plan g_last_plan;  // last persistent 2D batch of this thread
+static thread_local bool g_have_plan = false;
+static thread_local int g_pin_size = 0, g_pin_cut = 11;  // frac_batch_pin_plan
 
 int record_cuda_error(cudaError_t e, const char* file, int line, const char* expr) {
   const char* base = file;
@@ -255,6 +259,25 @@ int frac_solve(const frac_op* op, const double* f, const double* g, double* u, c
   return s;
 }
 
+int frac_batch_pin_plan(int32_t cluster_size, int32_t first_cluster_logm) {
+  if (cluster_size == 0) {
+    g_pin_size = 0;
+    return FRAC_OK;
+  }
+  if (cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 && cluster_size != 16)
+    return FRAC_EINVAL;
+  if (first_cluster_logm < kBatch2dMinLog || first_cluster_logm > kBatch2dMaxLog + 1) return FRAC_EINVAL;
+  g_pin_size = cluster_size;
+  g_pin_cut = cluster_size == 1 ? kBatch2dMaxLog + 1 : first_cluster_logm;
+  return FRAC_OK;
+}
+
+int frac_batch_last_plan(frac_batch_plan* out) {
+  if (!out || !g_have_plan) return FRAC_EINVAL;
+  *out = g_last_plan;
+  return FRAC_OK;
+}
+
 int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
                      const frac_solve_opts* opts, frac_solve_info* info, void* stream) {
   if (count < 0 || (count > 0 && (!ops || !f || !u || !opts || !info))) return FRAC_EINVAL;
@@ -274,6 +297,25 @@ int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* con
     int s = solve_batch_1d((int64_t)oned.size(), ops, f, u, opts, info, oned.data(), st);
     if (s != FRAC_OK) return s;
     for (int64_t i : oned) {
+      if (std::isnan(info[i].rel_resid)) info[i].status = FRAC_EINVAL;
+      if (info[i].status != FRAC_OK && first == FRAC_OK) first = info[i].status;
+    }
+  }
+  // 2D problems of the persistent kernel's FFT lengths: one launch
+  std::vector<int64_t> wide, others;
+  for (int64_t i : rest) {
+    if (batch2d_eligible(ops[i], opts) && is_device_ptr(f[i]) && is_device_ptr(u[i])) wide.push_back(i);
+    else others.push_back(i);
+  }
+  rest.swap(others);
+  if (!wide.empty()) {
+    frac_batch_plan plan{};
+    int s = solve_batch_2d((int64_t)wide.size(), ops, f, u, opts, info, wide.data(), st, &plan, g_pin_size,
+                           g_pin_cut);
+    if (s != FRAC_OK) return s;
+    g_last_plan = plan;
+    g_have_plan = true;
+    for (int64_t i : wide) {
       if (std::isnan(info[i].rel_resid)) info[i].status = FRAC_EINVAL;
       if (info[i].status != FRAC_OK && first == FRAC_OK) first = info[i].status;
     }

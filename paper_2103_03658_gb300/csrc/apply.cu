@@ -15,22 +15,12 @@
 
 #include "apply.cuh"
 #include "fft.cuh"
+#include "passes.cuh"
 #include "prof.cuh"
 
 namespace frac {
 
 using namespace fft;
-
-// Intermediate spectra are stored column-blocked: entry (row, k) of a slab of
-// `n` rows lives at (k / B) (n B) + row B + (k % B), B = 32 bytes / complex
-// size (4 for FP32, 2 for FP64).  A tile of B adjacent columns is then one
-// contiguous chunk, read and written with one lane per column and
-// consecutive lanes on consecutive rows, and every row segment is a full
-// 32-byte sector.  Every FFT below keeps the line in registers at entry and
-// exit (fft_reg): loads go straight from global memory into registers.
-// ---------------------------------------------------------------------------
-
-template <typename T> __host__ __device__ constexpr int blk() { return 32 / (int)sizeof(cplx_t<T>); }
 
 // minimum resident blocks per SM requested from the compiler: at least 512 resident
 // threads for FP32 kernels and 256 for FP64 (registers capped at 128 and 255 per thread);
@@ -93,31 +83,6 @@ k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const
   }
 }
 
-// column-blocked layout, slabs of n rows, KB = ceil(K / B) blocks per slab:
-// entry (row, k) at rowbase(row) + (k / B) n B + k % B
-template <int B>
-__device__ __forceinline__ int64_t wrow(int64_t row, int n, int KB) {
-  const int64_t slab = row / n, r = row - slab * n;
-  return slab * KB * (int64_t)n * B + r * B;
-}
-template <int B>
-__device__ __forceinline__ int64_t wcol(int k, int n) {
-  return (int64_t)(k / B) * n * B + (k % B);
-}
-
-// Block sum of a per-thread value (FP64), valid in every thread; red needs 32 doubles.
-__device__ __forceinline__ double block_sum_all(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  const int nw = (blockDim.x + 31) >> 5;
-  for (int i = 0; i < nw; ++i) s += red[i];
-  __syncthreads();
-  return s;
-}
-
 // Every block stores its total in partials[blockIdx.x]; the last block to
 // arrive (counter) sums all of them in index order and calls fin(sum) in
 // thread 0, then resets the counter for the next use.
@@ -143,143 +108,60 @@ __device__ __forceinline__ void last_block_reduce(double total, double* partials
 }
 
 // ---------------------------------------------------------------------------
-// Rows, forward: two real rows -> one complex FFT -> two half spectra
-// U0 = Z[k] + conj Z[M-k], U1 = -i (Z[k] - conj Z[M-k]), k in [0, M/2]
-// (stored without the 1/2 of the separation; the symbol carries it).
+// Grid kernels over the passes of passes.cuh: one unit (row pair or column
+// tile) per thread group.
 // ---------------------------------------------------------------------------
 
-// CG = true: the input is p = r + beta p (beta from st), written back to u (= p)
-// on the way in; the block returns at once when st->done is set.
+// Forward rows, LINES row pairs per block.  CG = true: the input is p = r +
+// beta p (beta from st), written back to u (= p) on the way in; the block
+// returns at once when st->done is set.
 template <typename T, int LOGM, int LINES, bool CG>
 __global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
 k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int64_t nrows, int KB,
            const cplx_t<T>* __restrict__ tw, const T* __restrict__ r, const CGState* st) {
   using C = cplx_t<T>;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM), B = blk<T>();
+  constexpr int TPL = tpl(LOGM), LS = line_stride(LOGM);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (CG && st->done) return;
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
-  C* buf = sm + line * LS;
-  const int64_t r0 = 2 * ((int64_t)blockIdx.x * LINES + line), r1 = r0 + 1;
-  const bool h0 = r0 < nrows, h1 = r1 < nrows;
-  C v[E];
+  const int64_t pair = (int64_t)blockIdx.x * LINES + line;
   if constexpr (CG) {
     const T be = (T)st->beta;
     T* p = const_cast<T*>(u);
-#pragma unroll
-    for (int e = 0; e < E / 2; ++e) {  // x < n <= M/2: e < E/2
-      const int x = tl + e * TPL;
-      T re = T(0), im = T(0);
-      if (x < n && h0) {
-        re = r[r0 * n + x] + be * p[r0 * n + x];
-        p[r0 * n + x] = re;
-      }
-      if (x < n && h1) {
-        im = r[r1 * n + x] + be * p[r1 * n + x];
-        p[r1 * n + x] = im;
-      }
-      v[e] = C{re, im};
-    }
+    row_fwd_pair<T, LOGM>(
+        [&](int64_t row, int x) {
+          const T v = r[row * n + x] + be * p[row * n + x];
+          p[row * n + x] = v;
+          return v;
+        },
+        W, n, nrows, KB, tw, pair, sm + line * LS, tl);
   } else {
-#pragma unroll
-    for (int e = 0; e < E / 2; ++e) {
-      const int x = tl + e * TPL;
-      T re = (x < n && h0) ? u[r0 * n + x] : T(0);
-      T im = (x < n && h1) ? u[r1 * n + x] : T(0);
-      v[e] = C{re, im};
-    }
+    row_fwd_pair<T, LOGM>([&](int64_t row, int x) { return u[row * n + x]; }, W, n, nrows, KB, tw, pair,
+                          sm + line * LS, tl);
   }
-  fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);  // upper half is zero padding
-  // separation needs Z[k] and Z[M-k] for k in [0, M/2]: each thread keeps its
-  // lower-half Z[k] in registers and reads the mirror from the upper half,
-  // which alone goes through the line buffer
-  __syncthreads();
-#pragma unroll
-  for (int e = E / 2; e < E; ++e) buf[pidx(tl + e * TPL)] = v[e];
-  __syncthreads();
-  C* W0 = W + wrow<B>(r0, n, KB);
-  C* W1 = W + wrow<B>(r1, n, KB);
-  auto emit = [&](int k, C z, C zc) {
-    const C s = cadd(z, zc), dd = csub(z, zc);
-    const int64_t kc = wcol<B>(k, n);
-    if (h0) W0[kc] = s;
-    if (h1) W1[kc] = C{dd.y, -dd.x};
-  };
-#pragma unroll
-  for (int e = 0; e < E / 2; ++e) {
-    const int k = tl + e * TPL;  // k < M/2; M - k is in the upper half unless k = 0
-    emit(k, v[e], cconj(k == 0 ? v[e] : buf[pidx(M - k)]));
-  }
-  if (tl == 0) emit(M / 2, v[E / 2], cconj(v[E / 2]));
 }
 
-// ---------------------------------------------------------------------------
-// Rows, inverse: two half spectra -> one complex line (Hermitian extension)
-// -> iFFT -> two real rows (first n entries).
-// ---------------------------------------------------------------------------
-
-// CG = true: also per-block partial sums of p.y (p at the same points) into
-// partials[blockIdx.x]; the last block to finish sums them in index order and
-// sets st->pq, st->alpha (or flags a breakdown).  Returns at once when st->done.
+// Inverse rows.  CG = true: also per-block partial sums of p.y (p at the same
+// points) into partials[blockIdx.x]; the last block to finish sums them in
+// index order and sets st->pq, st->alpha (or flags a breakdown).  Returns at
+// once when st->done.
 template <typename T, int LOGM, int LINES, bool CG>
 __global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
 k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nrows, int KB,
            const cplx_t<T>* __restrict__ tw, const T* __restrict__ p, CGState* st, double* partials) {
   using C = cplx_t<T>;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM), B = blk<T>();
+  constexpr int TPL = tpl(LOGM), LS = line_stride(LOGM);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (CG && st->done) return;
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
-  C* buf = sm + line * LS;
-  const int64_t r0 = 2 * ((int64_t)blockIdx.x * LINES + line), r1 = r0 + 1;
-  const bool h0 = r0 < nrows, h1 = r1 < nrows;
-  C v[E];
-  const C* W0 = W + wrow<B>(h0 ? r0 : 0, n, KB);
-  const C* W1 = W + wrow<B>(h1 ? r1 : 0, n, KB);
-  // line z = W0 + i W1 extended Hermitian-wise: z[x] = W0[x] + i W1[x] and
-  // z[M-x] = conj(W0[x]) + i conj(W1[x]) for x in [0, M/2], so each half
-  // spectrum entry is read once; the thread that reads W[x] leaves z[M-x] in
-  // the line buffer for its owner
-  auto load = [&](int x, C& lo, C& hi) {
-    const int64_t kc = wcol<B>(x, n);
-    const C v0 = h0 ? W0[kc] : C{0, 0};
-    const C v1 = h1 ? W1[kc] : C{0, 0};
-    lo = C{v0.x - v1.y, v0.y + v1.x};   // v0 + i v1
-    hi = C{v0.x + v1.y, v1.x - v0.y};   // conj(v0) + i conj(v1)
-  };
-#pragma unroll
-  for (int e = 0; e < E / 2; ++e) {
-    const int x = tl + e * TPL;  // x < M/2
-    C hi;
-    load(x, v[e], hi);
-    if (x > 0) buf[pidx(M - x)] = hi;
-  }
-  if (tl == 0) {
-    C lo, hi;
-    load(M / 2, lo, hi);
-    buf[pidx(M / 2)] = lo;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int e = E / 2; e < E; ++e) v[e] = buf[pidx(tl + e * TPL)];
-  fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // only x < n <= M/2 is kept
+  const int64_t pair = (int64_t)blockIdx.x * LINES + line;
   T dot = T(0);
-#pragma unroll
-  for (int e = 0; e < E / 2; ++e) {
-    const int x = tl + e * TPL;
-    if (x < n) {
-      if (h0) {
-        y[r0 * n + x] = v[e].x;
-        if (CG) dot += v[e].x * p[r0 * n + x];
-      }
-      if (h1) {
-        y[r1 * n + x] = v[e].y;
-        if (CG) dot += v[e].y * p[r1 * n + x];
-      }
-    }
-  }
+  row_inv_pair<T, LOGM>(W, n, nrows, KB, tw, pair, sm + line * LS, tl, [&](int64_t row, int x, T v) {
+    y[row * n + x] = v;
+    if (CG) dot += v * p[row * n + x];
+  });
   if constexpr (CG) {
     double* red = reinterpret_cast<double*>(smem_raw);  // the FFT lines are no longer needed
     const double total = block_sum_all(dot, red);
@@ -295,102 +177,18 @@ k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nr
   }
 }
 
-// ---------------------------------------------------------------------------
-// Columns: one tile of B adjacent columns per block, TPL threads per column
-// (lane order: column fastest).  Modes:
-//   SYM2 (d = 2): slab o = field, pad n -> M, FFT, * Lambda[kr][k1], iFFT, keep n; in place.
-//   YFWD (d = 3): slab o = (b, j3) of W1, pad n -> M, FFT along j2, all M k2 to W2,
-//                 W2 column c = k2 Kp + k1 (Kp = KB B), column-blocked with n rows (j3).
-//   ZSYM (d = 3): W2 column tile of field o, pad n -> M along j3, FFT, * Lambda[k3r][k2r][k1],
-//                 iFFT, keep n; in place.
-//   YINV (d = 3): slab o = (b, j3): M entries k2 of W2 columns k1, iFFT, first n (j2) to W1.
-// ---------------------------------------------------------------------------
-
-enum ColMode { SYM2 = 0, YFWD = 1, ZSYM = 2, YINV = 3 };
-
-struct ColArgs {
-  int n, K, KB;      // interior points, symbol extent M/2+1, column blocks per W1 slab
-  int64_t tiles;     // column tiles per slab
-  int64_t nb;        // batch (fields)
-};
-
+// Columns: one tile of B adjacent columns per block (see col_tile).
 template <typename T, int LOGM, int MODE>
 __global__ void __launch_bounds__(blk<T>() * tpl(LOGM), minb_cols<T>(blk<T>() * tpl(LOGM)))
 k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw,
        const CGState* st) {
   using C = cplx_t<T>;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride_tile(LOGM), B = blk<T>();
+  constexpr int B = blk<T>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (st && st->done) return;
-  C* sm = reinterpret_cast<C*>(smem_raw);
   const int cl = threadIdx.x % B, tl = threadIdx.x / B;
-  C* buf = sm + cl * LS;
   const int64_t o = blockIdx.x / A.tiles, tile = blockIdx.x % A.tiles;
-  const int n = A.n, K = A.K, KB = A.KB, Kp = KB * B;
-  const int64_t nB = (int64_t)n * B;
-  const int64_t W2slab = (int64_t)M * KB * nB;  // one field of W2
-  C v[E];
-  // ---- column identity and load
-  int k1 = 0, k2r = 0;
-  bool live = true;
-  if (MODE == SYM2 || MODE == YFWD || MODE == YINV) {
-    k1 = (int)tile * B + cl;
-    live = k1 < K;
-  } else {  // ZSYM: tile indexes W2 column blocks, c = k2 Kp + k1
-    const int64_t c = tile * B + cl;
-    const int k2 = (int)(c / Kp);
-    k1 = (int)(c % Kp);
-    k2r = k2 <= M / 2 ? k2 : M - k2;
-    live = k1 < K;
-  }
-  if (MODE == YINV) {
-    const int64_t b = o / n, j3 = o % n;
-    const C* src = in + b * W2slab + tile * nB + j3 * B + cl;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int k2 = tl + e * TPL;
-      v[e] = live ? src[(int64_t)k2 * KB * nB] : C{0, 0};
-    }
-  } else {
-    const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl : in + (o * KB + tile) * nB + cl;
-#pragma unroll
-    for (int e = 0; e < E / 2; ++e) {  // j < n <= M/2; the rest is zero padding
-      const int j = tl + e * TPL;
-      v[e] = (live && j < n) ? src[(int64_t)j * B] : C{0, 0};
-    }
-  }
-  // ---- transforms
-  if (MODE != YINV) fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);
-  if (MODE == SYM2 || MODE == ZSYM) {
-    const T* lrow = (MODE == SYM2) ? lam + k1 : lam + (int64_t)k2r * K + k1;
-    const int64_t kstride = (MODE == SYM2) ? K : (int64_t)K * K;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int k = tl + e * TPL;
-      const int kr = k <= M / 2 ? k : M - k;
-      v[e] = cscale(v[e], live ? lrow[kr * kstride] : T(0));
-    }
-  }
-  if (MODE != YFWD) fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // keeps j < n only
-  // ---- store
-  if (!live) return;
-  if (MODE == YFWD) {
-    const int64_t b = o / n, j3 = o % n;
-    C* dst = out + b * W2slab + tile * nB + j3 * B + cl;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const int k2 = tl + e * TPL;
-      dst[(int64_t)k2 * KB * nB] = v[e];
-    }
-  } else {
-    C* dst = (MODE == ZSYM) ? out + o * W2slab + tile * nB + cl
-                            : out + (o * KB + tile) * nB + cl;  // SYM2 in place; YINV to W1 slab o
-#pragma unroll
-    for (int e = 0; e < E / 2; ++e) {
-      const int j = tl + e * TPL;
-      if (j < n) dst[(int64_t)j * B] = v[e];
-    }
-  }
+  col_tile<T, LOGM, MODE>(in, out, A, lam, tw, o, tile, reinterpret_cast<C*>(smem_raw), cl, tl);
 }
 
 // ---------------------------------------------------------------------------

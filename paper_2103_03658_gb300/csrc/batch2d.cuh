@@ -1,0 +1,23 @@
+// Persistent batched 2D solver (batch2d.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace frac {
+
+// FFT lengths handled by the persistent kernel: 2^5 .. 2^10 (n = 9 .. 511).
+constexpr int kBatch2dMinLog = 5, kBatch2dMaxLog = 10;
+
+// True when a problem can go to the persistent kernel (d = 2, mixed precision,
+// FFT length in range); f and u must also be device pointers.
+bool batch2d_eligible(const frac_op* op, const frac_solve_opts* opts);
+
+// Solves the problems idx[0..count) of (ops, f, u) in one persistent launch;
+// fills info[idx[t]] and, when plan is not null, the plan used.  pin_size > 0
+// fixes the cluster size (and pin_cut the first cluster-wide log2 FFT length)
+// instead of the autotuner's choice.
+int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
+                   const frac_solve_opts* opts, frac_solve_info* info, const int64_t* idx, cudaStream_t st,
+                   frac_batch_plan* plan, int pin_size, int pin_cut);
+
+}  // namespace frac

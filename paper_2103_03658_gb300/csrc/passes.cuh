@@ -1,0 +1,256 @@
+// The three passes of the d >= 2 FFT apply (Sec. 2.1: the Toeplitz product by
+// circulant embedding and FFT), as device functions over one unit of work: a
+// pair of rows (forward and inverse row passes) or a tile of B adjacent
+// columns (column passes).  The grid kernels of apply.cu run one unit per
+// thread group; the persistent batched solver (batch2d.cu) loops over units.
+//
+// Every function calls __syncthreads(): all threads of the block must call it
+// together, with units out of range passed in as empty ones (they load zeros
+// and store nothing).  The spectrum pointers are deliberately not __restrict__:
+// in the persistent solver other threads of the same launch write a spectrum
+// that these functions then read after a barrier, and a const __restrict__
+// pointer would let the compiler read it through the non-coherent path or
+// move those reads ahead of the barrier.  The grid kernels declare their own
+// parameters __restrict__ where the data is written by an earlier launch.
+//
+// Intermediate spectra are stored column-blocked: entry (row, k) of a slab of
+// `n` rows lives at (k / B) (n B) + row B + (k % B), B = 32 bytes / complex
+// size (4 for FP32, 2 for FP64).  A tile of B adjacent columns is then one
+// contiguous chunk, read and written with one lane per column and
+// consecutive lanes on consecutive rows, and every row segment is a full
+// 32-byte sector.  Every FFT keeps the line in registers at entry and exit
+// (fft_reg): loads go straight from global memory into registers.
+#pragma once
+
+#include "fft.cuh"
+
+namespace frac {
+
+template <typename T> __host__ __device__ constexpr int blk() { return 32 / (int)sizeof(cplx_t<T>); }
+
+// column-blocked layout, slabs of n rows, KB = ceil(K / B) blocks per slab:
+// entry (row, k) at rowbase(row) + (k / B) n B + k % B
+template <int B>
+__device__ __forceinline__ int64_t wrow(int64_t row, int n, int KB) {
+  const int64_t slab = row / n, r = row - slab * n;
+  return slab * KB * (int64_t)n * B + r * B;
+}
+template <int B>
+__device__ __forceinline__ int64_t wcol(int k, int n) {
+  return (int64_t)(k / B) * n * B + (k % B);
+}
+
+// Block sum of a per-thread value (FP64), valid in every thread; red needs 32 doubles.
+__device__ __forceinline__ double block_sum_all(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = (blockDim.x + 31) >> 5;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Rows, forward: two real rows r0 = 2 pair, r1 = r0 + 1 (of nrows) -> one
+// complex FFT -> two half spectra U0 = Z[k] + conj Z[M-k], U1 = -i (Z[k] -
+// conj Z[M-k]), k in [0, M/2] (stored without the 1/2 of the separation; the
+// symbol carries it).  in(row, x) gives the real input at x < n of a row < nrows
+// (called once per such point).  buf: this group's line buffer
+// (line_stride(LOGM) entries); tl: thread index within the group of tpl(LOGM).
+// ---------------------------------------------------------------------------
+template <typename T, int LOGM, typename In>
+__device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t nrows, int KB,
+                                             const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
+                                             int tl) {
+  using C = cplx_t<T>;
+  using namespace fft;
+  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), B = blk<T>();
+  const int64_t r0 = 2 * pair, r1 = r0 + 1;
+  const bool h0 = r0 < nrows, h1 = r1 < nrows;
+  C v[E];
+#pragma unroll
+  for (int e = 0; e < E / 2; ++e) {  // x < n <= M/2: e < E/2
+    const int x = tl + e * TPL;
+    const T re = (x < n && h0) ? in(r0, x) : T(0);
+    const T im = (x < n && h1) ? in(r1, x) : T(0);
+    v[e] = C{re, im};
+  }
+  fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);  // upper half is zero padding
+  // separation needs Z[k] and Z[M-k] for k in [0, M/2]: each thread keeps its
+  // lower-half Z[k] in registers and reads the mirror from the upper half,
+  // which alone goes through the line buffer
+  __syncthreads();
+#pragma unroll
+  for (int e = E / 2; e < E; ++e) buf[pidx(tl + e * TPL)] = v[e];
+  __syncthreads();
+  C* W0 = W + wrow<B>(h0 ? r0 : 0, n, KB);
+  C* W1 = W + wrow<B>(h1 ? r1 : 0, n, KB);
+  auto emit = [&](int k, C z, C zc) {
+    const C s = cadd(z, zc), dd = csub(z, zc);
+    const int64_t kc = wcol<B>(k, n);
+    if (h0) W0[kc] = s;
+    if (h1) W1[kc] = C{dd.y, -dd.x};
+  };
+#pragma unroll
+  for (int e = 0; e < E / 2; ++e) {
+    const int k = tl + e * TPL;  // k < M/2; M - k is in the upper half unless k = 0
+    emit(k, v[e], cconj(k == 0 ? v[e] : buf[pidx(M - k)]));
+  }
+  if (tl == 0) emit(M / 2, v[E / 2], cconj(v[E / 2]));
+}
+
+// ---------------------------------------------------------------------------
+// Rows, inverse: two half spectra -> one complex line (Hermitian extension)
+// -> iFFT -> two real rows; out(row, x, value) receives the first n entries
+// of each row < nrows.
+// ---------------------------------------------------------------------------
+template <typename T, int LOGM, typename Out>
+__device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t nrows, int KB,
+                                             const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
+                                             int tl, Out out) {
+  using C = cplx_t<T>;
+  using namespace fft;
+  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), B = blk<T>();
+  const int64_t r0 = 2 * pair, r1 = r0 + 1;
+  const bool h0 = r0 < nrows, h1 = r1 < nrows;
+  C v[E];
+  const C* W0 = W + wrow<B>(h0 ? r0 : 0, n, KB);
+  const C* W1 = W + wrow<B>(h1 ? r1 : 0, n, KB);
+  // line z = W0 + i W1 extended Hermitian-wise: z[x] = W0[x] + i W1[x] and
+  // z[M-x] = conj(W0[x]) + i conj(W1[x]) for x in [0, M/2], so each half
+  // spectrum entry is read once; the thread that reads W[x] leaves z[M-x] in
+  // the line buffer for its owner
+  auto load = [&](int x, C& lo, C& hi) {
+    const int64_t kc = wcol<B>(x, n);
+    const C v0 = h0 ? W0[kc] : C{0, 0};
+    const C v1 = h1 ? W1[kc] : C{0, 0};
+    lo = C{v0.x - v1.y, v0.y + v1.x};  // v0 + i v1
+    hi = C{v0.x + v1.y, v1.x - v0.y};  // conj(v0) + i conj(v1)
+  };
+  __syncthreads();  // earlier users of buf are done
+#pragma unroll
+  for (int e = 0; e < E / 2; ++e) {
+    const int x = tl + e * TPL;  // x < M/2
+    C hi;
+    load(x, v[e], hi);
+    if (x > 0) buf[pidx(M - x)] = hi;
+  }
+  if (tl == 0) {
+    C lo, hi;
+    load(M / 2, lo, hi);
+    buf[pidx(M / 2)] = lo;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = E / 2; e < E; ++e) v[e] = buf[pidx(tl + e * TPL)];
+  fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // only x < n <= M/2 is kept
+#pragma unroll
+  for (int e = 0; e < E / 2; ++e) {
+    const int x = tl + e * TPL;
+    if (x < n) {
+      if (h0) out(r0, x, v[e].x);
+      if (h1) out(r1, x, v[e].y);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Columns: one tile of B adjacent columns, TPL threads per column (lane order:
+// column fastest, cl = column in the tile, tl = thread in the column).  Modes:
+//   SYM2 (d = 2): slab o = field, pad n -> M, FFT, * Lambda[kr][k1], iFFT, keep n; in place.
+//   YFWD (d = 3): slab o = (b, j3) of W1, pad n -> M, FFT along j2, all M k2 to W2,
+//                 W2 column c = k2 Kp + k1 (Kp = KB B), column-blocked with n rows (j3).
+//   ZSYM (d = 3): W2 column tile of field o, pad n -> M along j3, FFT, * Lambda[k3r][k2r][k1],
+//                 iFFT, keep n; in place.
+//   YINV (d = 3): slab o = (b, j3): M entries k2 of W2 columns k1, iFFT, first n (j2) to W1.
+// A tile whose column k1 >= K is empty.  sm: the tile's B line buffers of
+// line_stride_tile(LOGM) entries each.
+// ---------------------------------------------------------------------------
+
+enum ColMode { SYM2 = 0, YFWD = 1, ZSYM = 2, YINV = 3 };
+
+struct ColArgs {
+  int n, K, KB;      // interior points, symbol extent M/2+1, column blocks per W1 slab
+  int64_t tiles;     // column tiles per slab
+  int64_t nb;        // batch (fields)
+};
+
+template <typename T, int LOGM, int MODE>
+__device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, const ColArgs& A,
+                                         const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, int64_t o,
+                                         int64_t tile, cplx_t<T>* sm, int cl, int tl) {
+  using C = cplx_t<T>;
+  using namespace fft;
+  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride_tile(LOGM), B = blk<T>();
+  C* buf = sm + cl * LS;
+  const int n = A.n, K = A.K, KB = A.KB, Kp = KB * B;
+  const int64_t nB = (int64_t)n * B;
+  const int64_t W2slab = (int64_t)M * KB * nB;  // one field of W2
+  C v[E];
+  // ---- column identity and load
+  int k1 = 0, k2r = 0;
+  bool live = true;
+  if (MODE == SYM2 || MODE == YFWD || MODE == YINV) {
+    k1 = (int)tile * B + cl;
+    live = k1 < K;
+  } else {  // ZSYM: tile indexes W2 column blocks, c = k2 Kp + k1
+    const int64_t c = tile * B + cl;
+    const int k2 = (int)(c / Kp);
+    k1 = (int)(c % Kp);
+    k2r = k2 <= M / 2 ? k2 : M - k2;
+    live = k1 < K;
+  }
+  if (MODE == YINV) {
+    const int64_t b = o / n, j3 = o % n;
+    const C* src = in + b * W2slab + tile * nB + j3 * B + cl;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k2 = tl + e * TPL;
+      v[e] = live ? src[(int64_t)k2 * KB * nB] : C{0, 0};
+    }
+  } else {
+    const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl : in + (o * KB + tile) * nB + cl;
+#pragma unroll
+    for (int e = 0; e < E / 2; ++e) {  // j < n <= M/2; the rest is zero padding
+      const int j = tl + e * TPL;
+      v[e] = (live && j < n) ? src[(int64_t)j * B] : C{0, 0};
+    }
+  }
+  // ---- transforms
+  if (MODE != YINV) fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);
+  if (MODE == SYM2 || MODE == ZSYM) {
+    const T* lrow = (MODE == SYM2) ? lam + k1 : lam + (int64_t)k2r * K + k1;
+    const int64_t kstride = (MODE == SYM2) ? K : (int64_t)K * K;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = tl + e * TPL;
+      const int kr = k <= M / 2 ? k : M - k;
+      v[e] = cscale(v[e], live ? lrow[kr * kstride] : T(0));
+    }
+  }
+  if (MODE != YFWD) fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // keeps j < n only
+  // ---- store
+  if (!live) return;
+  if (MODE == YFWD) {
+    const int64_t b = o / n, j3 = o % n;
+    C* dst = out + b * W2slab + tile * nB + j3 * B + cl;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k2 = tl + e * TPL;
+      dst[(int64_t)k2 * KB * nB] = v[e];
+    }
+  } else {
+    C* dst = (MODE == ZSYM) ? out + o * W2slab + tile * nB + cl
+                            : out + (o * KB + tile) * nB + cl;  // SYM2 in place; YINV to W1 slab o
+#pragma unroll
+    for (int e = 0; e < E / 2; ++e) {
+      const int j = tl + e * TPL;
+      if (j < n) dst[(int64_t)j * B] = v[e];
+    }
+  }
+}
+
+}  // namespace frac
