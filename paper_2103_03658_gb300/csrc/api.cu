@@ -37,6 +37,19 @@ static int keep_pool_memory() {
   return FRAC_OK;
 }
 
+// A non-blocking library stream per device for work that runs beside the caller's stream.
+static int side_stream(cudaStream_t* out) {
+  static std::mutex mu;
+  static std::vector<cudaStream_t> per_dev;
+  int dev = 0;
+  FRAC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1, nullptr);
+  if (!per_dev[dev]) FRAC_CUDA_TRY(cudaStreamCreateWithFlags(&per_dev[dev], cudaStreamNonBlocking));
+  *out = per_dev[dev];
+  return FRAC_OK;
+}
+
 static bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -293,14 +306,6 @@ int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* con
     else rest.push_back(i);
   }
   int first = FRAC_OK;
-  if (!oned.empty()) {
-    int s = solve_batch_1d((int64_t)oned.size(), ops, f, u, opts, info, oned.data(), st);
-    if (s != FRAC_OK) return s;
-    for (int64_t i : oned) {
-      if (std::isnan(info[i].rel_resid)) info[i].status = FRAC_EINVAL;
-      if (info[i].status != FRAC_OK && first == FRAC_OK) first = info[i].status;
-    }
-  }
   // 2D problems of the persistent kernel's FFT lengths: one launch
   std::vector<int64_t> wide, others;
   for (int64_t i : rest) {
@@ -308,18 +313,45 @@ int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* con
     else others.push_back(i);
   }
   rest.swap(others);
+  // the 1D launches run on a side stream next to the persistent 2D launch: fork
+  // here, before anything of this call is queued on st
+  cudaStream_t s1 = st;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if (!oned.empty() && !wide.empty()) {
+    FRAC_TRY(side_stream(&s1));
+    FRAC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    FRAC_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    FRAC_CUDA_TRY(cudaEventRecord(fork, st));
+    FRAC_CUDA_TRY(cudaStreamWaitEvent(s1, fork, 0));
+  }
+  struct EvFree {
+    cudaEvent_t* a;
+    cudaEvent_t* b;
+    ~EvFree() {
+      if (*a) cudaEventDestroy(*a);
+      if (*b) cudaEventDestroy(*b);
+    }
+  } evf{&fork, &join};
+  BatchPending p2, p1;
   if (!wide.empty()) {
     frac_batch_plan plan{};
-    int s = solve_batch_2d((int64_t)wide.size(), ops, f, u, opts, info, wide.data(), st, &plan, g_pin_size,
-                           g_pin_cut);
-    if (s != FRAC_OK) return s;
+    FRAC_TRY(solve_batch_2d((int64_t)wide.size(), ops, f, u, opts, wide.data(), st, &plan, g_pin_size, g_pin_cut,
+                            &p2));
     g_last_plan = plan;
     g_have_plan = true;
-    for (int64_t i : wide) {
+  }
+  if (!oned.empty()) FRAC_TRY(solve_batch_1d((int64_t)oned.size(), ops, f, u, opts, oned.data(), s1, &p1));
+  if (!wide.empty()) FRAC_TRY(p2.collect(info));
+  if (!oned.empty()) FRAC_TRY(p1.collect(info));
+  if (join) {  // later work on st is ordered after the side stream's
+    FRAC_CUDA_TRY(cudaEventRecord(join, s1));
+    FRAC_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
+  }
+  for (const std::vector<int64_t>* v : {&oned, &wide})
+    for (int64_t i : *v) {
       if (std::isnan(info[i].rel_resid)) info[i].status = FRAC_EINVAL;
       if (info[i].status != FRAC_OK && first == FRAC_OK) first = info[i].status;
     }
-  }
   if (!rest.empty()) {
     // the other problems progress together through a solve engine (their kernels overlap)
     frac_engine* e = nullptr;

@@ -1,6 +1,8 @@
 // Internal interfaces between the translation units of the library.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace frac {
@@ -50,9 +52,33 @@ int solve_device(const frac_op* op, const double* f, double* u, const frac_solve
 // Makes every stream of engine e wait for the work already queued on `caller`.
 int engine_wait_for(frac_engine* e, cudaStream_t caller);
 
-// Solves the 1D problems listed in idx[0..count) of (ops, f, u) (device pointers),
-// grouped by FFT length, one launch per group; fills info[idx[t]].
+// Batched work launched on a stream whose per-problem results are still on the
+// device: collect() waits for the stream, copies the results to
+// info[order[t]] and frees the device buffers (stream ordered); the
+// destructor frees them if collect() was never called.
+struct BatchPending {
+  cudaStream_t st = nullptr;
+  std::vector<void*> bufs;
+  frac_solve_info* dinfo = nullptr;
+  std::vector<int64_t> order;
+  template <typename P>
+  int alloc(P** out, size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FRAC_ENOMEM : FRAC_ECUDA;
+    bufs.push_back(p);
+    *out = static_cast<P*>(p);
+    return FRAC_OK;
+  }
+  void* pinned = nullptr;  // host staging of the launch records, freed once st is done
+  int collect(frac_solve_info* info);
+  ~BatchPending();
+};
+
+// Launches the 1D problems listed in idx[0..count) of (ops, f, u) (device
+// pointers), grouped by FFT length, one launch per group, on st; the results
+// arrive through pend->collect().
 int solve_batch_1d(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
-                   const frac_solve_opts* opts, frac_solve_info* info, const int64_t* idx, cudaStream_t st);
+                   const frac_solve_opts* opts, const int64_t* idx, cudaStream_t st, BatchPending* pend);
 
 }  // namespace frac

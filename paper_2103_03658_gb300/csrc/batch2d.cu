@@ -24,6 +24,7 @@
 // cluster barriers, reached the same number of times by every CTA.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -98,43 +99,44 @@ __device__ double group_sum(double v, const Group& g, double* red, double* slots
   return t;
 }
 
-// Not inlined into the kernel: inlined, the 2^5-point instantiation computed a
-// wrong inverse row pass (the same source as a separate function, or in a
-// separate kernel, is exact), so each FFT length keeps its own function body.
+// One problem on one group (cluster or CTA).  The three steps of the
+// refinement are separate (non-inlined) functions, so the FP32 CG loop gets
+// its own register allocation instead of sharing one with the FP64 passes;
+// and inlined into the kernel, the 2^5-point instantiation computed a wrong
+// inverse row pass (the same source as a separate function, or in a separate
+// kernel, is exact), so nothing of it is inlined there.
+struct Ctx {
+  const B2Prob* P;
+  const B2Slot* S;
+  Group g;
+  const float2* tw32;
+  const double2* tw64;
+  unsigned char* smem;
+  double* red;
+  double* slots;
+  int parity;
+};
+
 template <int LOGM>
-__device__ __noinline__ void solve_problem(const B2Prob& P, frac_solve_info* info, const B2Slot& S, const Group g,
-                              const float2* __restrict__ tw32, const double2* __restrict__ tw64,
-                              unsigned char* smem, double* red, double* slots) {
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LINES = kThreads / TPL;
-  constexpr int LS = line_stride(LOGM), LST = line_stride_tile(LOGM);
-  constexpr int K = M / 2 + 1, KB32 = (K + 3) / 4, KB64 = (K + 1) / 2;
-  constexpr int TPR32 = kThreads / (4 * TPL), TPR64 = kThreads / (2 * TPL);  // column tiles per CTA round
-  const int n = P.n, tid = threadIdx.x;
-  const int line = tid / TPL, tl = tid % TPL;
-  const int npairs = (n + 1) / 2;
-  const int rrounds = (npairs + g.G * LINES - 1) / (g.G * LINES);
-  const int crounds32 = (KB32 + g.G * TPR32 - 1) / (g.G * TPR32);
-  const int crounds64 = (KB64 + g.G * TPR64 - 1) / (g.G * TPR64);
-  const ColArgs A32{n, K, KB32, KB32, 1}, A64{n, K, KB64, KB64, 1};
-  float2* W32 = static_cast<float2*>(S.W);
-  double2* W64 = static_cast<double2*>(S.W);
-  float2* rb32 = reinterpret_cast<float2*>(smem) + line * LS;
-  double2* rb64 = reinterpret_cast<double2*>(smem) + line * LS;
-  // plain pointers: everything here is written and read within the launch
-  const double* F = P.f;
-  double* U = P.u;
-  float* X = S.x;
-  float* R = S.r;
-  float* Pv = S.p;
-  float* Q = S.q;
-  double* R64 = S.r64;
-  int parity = 0;
-  auto gsum = [&](double v) { return group_sum(v, g, red, slots, parity); };
-  auto pair_of = [&](int i) -> int64_t { return ((int64_t)i * g.G + g.rank) * LINES + line; };
+struct Solver {
+  static constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LINES = kThreads / TPL;
+  static constexpr int LS = line_stride(LOGM), LST = line_stride_tile(LOGM);
+  static constexpr int K = M / 2 + 1, KB32 = (K + 3) / 4, KB64 = (K + 1) / 2;
+  static constexpr int TPR32 = kThreads / (4 * TPL), TPR64 = kThreads / (2 * TPL);  // column tiles per CTA round
+
+  static __device__ __forceinline__ int rrounds(const Ctx& c) {
+    const int npairs = (c.P->n + 1) / 2;
+    return (npairs + c.g.G * LINES - 1) / (c.g.G * LINES);
+  }
+  static __device__ __forceinline__ int64_t pair_of(const Ctx& c, int i) {
+    return ((int64_t)i * c.g.G + c.g.rank) * LINES + threadIdx.x / TPL;
+  }
   // the points of this thread: those its row passes read and write
-  auto for_own = [&](auto&& fn) {
-    for (int i = 0; i < rrounds; ++i) {
-      const int64_t r0 = 2 * pair_of(i);
+  template <typename Fn>
+  static __device__ __forceinline__ void for_own(const Ctx& c, Fn fn) {
+    const int n = c.P->n, tl = threadIdx.x % TPL, rr = rrounds(c);
+    for (int i = 0; i < rr; ++i) {
+      const int64_t r0 = 2 * pair_of(c, i);
 #pragma unroll
       for (int e = 0; e < E / 2; ++e) {
         const int x = tl + e * TPL;
@@ -144,129 +146,169 @@ __device__ __noinline__ void solve_problem(const B2Prob& P, frac_solve_info* inf
         }
       }
     }
-  };
-  auto cols32 = [&]() {
-    const int ts = tid / (4 * TPL), w = tid % (4 * TPL);
-    for (int i = 0; i < crounds32; ++i)
-      col_tile<float, LOGM, SYM2>(W32, W32, A32, P.lam32, tw32, 0, ((int64_t)i * g.G + g.rank) * TPR32 + ts,
-                                  reinterpret_cast<float2*>(smem) + ts * 4 * LST, w % 4, w / 4);
-  };
-  auto cols64 = [&]() {
-    const int ts = tid / (2 * TPL), w = tid % (2 * TPL);
-    for (int i = 0; i < crounds64; ++i)
-      col_tile<double, LOGM, SYM2>(W64, W64, A64, P.lam64, tw64, 0, ((int64_t)i * g.G + g.rank) * TPR64 + ts,
-                                   reinterpret_cast<double2*>(smem) + ts * 2 * LST, w % 2, w / 2);
-  };
-  // R64 = F - A64 U; returns ||R64||^2
-  auto residual = [&]() -> double {
-    for (int i = 0; i < rrounds; ++i)
-      row_fwd_pair<double, LOGM>([&](int64_t row, int x) { return U[row * n + x]; }, W64, n, n, KB64, tw64,
-                                 pair_of(i), rb64, tl);
-    g.sync();
-    cols64();
-    g.sync();
+  }
+  static __device__ __forceinline__ double gsum(Ctx& c, double v) {
+    return group_sum(v, c.g, c.red, c.slots, c.parity);
+  }
+
+  // ||f||^2, and u = 0 unless it is the initial guess
+  static __device__ __noinline__ double start(Ctx& c) {
+    const double* F = c.P->f;
+    double* U = c.P->u;
+    const bool zero = !c.P->use_x0;
+    double ff = 0.0;
+    for_own(c, [&](int64_t k) {
+      const double fv = F[k];
+      ff += fv * fv;
+      if (zero) U[k] = 0.0;
+    });
+    return gsum(c, ff);
+  }
+
+  // R64 = F - A64 U (FP64 passes); returns ||R64||^2
+  static __device__ __noinline__ double residual(Ctx& c) {
+    const int n = c.P->n, tid = threadIdx.x, tl = tid % TPL, rr = rrounds(c);
+    const double* F = c.P->f;
+    const double* U = c.P->u;
+    double* R64 = c.S->r64;
+    double2* W = static_cast<double2*>(c.S->W);
+    double2* rb = reinterpret_cast<double2*>(c.smem) + (tid / TPL) * LS;
+    for (int i = 0; i < rr; ++i)
+      row_fwd_pair<double, LOGM>([&](int64_t row, int x) { return U[row * n + x]; }, W, n, n, KB64, c.tw64,
+                                 pair_of(c, i), rb, tl);
+    c.g.sync();
+    {
+      const ColArgs A{n, K, KB64, KB64, 1};
+      const int ts = tid / (2 * TPL), w = tid % (2 * TPL);
+      const int cr = (KB64 + c.g.G * TPR64 - 1) / (c.g.G * TPR64);
+      for (int i = 0; i < cr; ++i)
+        col_tile<double, LOGM, SYM2>(W, W, A, c.P->lam64, c.tw64, 0, ((int64_t)i * c.g.G + c.g.rank) * TPR64 + ts,
+                                     reinterpret_cast<double2*>(c.smem) + ts * 2 * LST, w % 2, w / 2);
+    }
+    c.g.sync();
     double part = 0.0;
-    for (int i = 0; i < rrounds; ++i)
-      row_inv_pair<double, LOGM>(W64, n, n, KB64, tw64, pair_of(i), rb64, tl, [&](int64_t row, int x, double v) {
+    for (int i = 0; i < rr; ++i)
+      row_inv_pair<double, LOGM>(W, n, n, KB64, c.tw64, pair_of(c, i), rb, tl, [&](int64_t row, int x, double v) {
         const double rv = F[row * n + x] - v;
         R64[row * n + x] = rv;
         part += rv * rv;
       });
-    return gsum(part);
-  };
+    return gsum(c, part);
+  }
 
-  // ||f||^2 and the start
-  double ff = 0.0;
-  for_own([&](int64_t k) {
-    const double fv = F[k];
-    ff += fv * fv;
-    if (!P.use_x0) U[k] = 0.0;
-  });
-  const double fn2 = gsum(ff);
-  const double tol2 = P.rtol * P.rtol * fn2, inner2 = P.inner_tol * P.inner_tol;
-  int iters = 0, outer = 0, status = FRAC_OK;
-  double rn2 = 0.0;
-  if (fn2 != 0.0) {
-    rn2 = residual();
-    double prev = INFINITY;
-    while (rn2 > tol2 && iters < P.max_iter && outer < 100) {
-      // FP32 CG on A d = R64 / ||R64||, d in X
-      const double sc = 1.0 / sqrt(rn2);
-      float rf = 0.0f;
-      for_own([&](int64_t k) {
-        const float rv = (float)(R64[k] * sc);
-        R[k] = rv;
-        X[k] = 0.0f;
-        rf += rv * rv;
-      });
-      double rr = gsum(rf);
-      const double stop = inner2 * rr;
-      bool first = true;
-      float be = 0.0f;
-      while (rr > stop && iters < P.max_iter) {
-        for (int i = 0; i < rrounds; ++i)
-          row_fwd_pair<float, LOGM>(
-              [&](int64_t row, int x) {
-                const int64_t k = row * n + x;
-                const float v = first ? R[k] : R[k] + be * Pv[k];
-                Pv[k] = v;
-                return v;
-              },
-              W32, n, n, KB32, tw32, pair_of(i), rb32, tl);
-        g.sync();
-        cols32();
-        g.sync();
-        float pqf = 0.0f;
-        for (int i = 0; i < rrounds; ++i)
-          row_inv_pair<float, LOGM>(W32, n, n, KB32, tw32, pair_of(i), rb32, tl, [&](int64_t row, int x, float v) {
-            const int64_t k = row * n + x;
-            Q[k] = v;
-            pqf += v * Pv[k];
-          });
-        const double pq = gsum(pqf);
-        if (!(pq > 0.0) || !isfinite(pq)) break;  // inner breakdown: refine from here
-        const float al = (float)(rr / pq);
-        float rf1 = 0.0f;
-        for_own([&](int64_t k) {
-          X[k] += al * Pv[k];
-          const float rv = R[k] - al * Q[k];
-          R[k] = rv;
-          rf1 += rv * rv;
+  // FP32 CG on A d = R64 / ||R64|| (||R64||^2 = rn2) to a relative reduction
+  // inner_tol, then U += ||R64|| d.  Returns the iteration count after it.
+  static __device__ __noinline__ int inner(Ctx& c, double rn2, int iters) {
+    const int n = c.P->n, tid = threadIdx.x, tl = tid % TPL, rr = rrounds(c), max_iter = c.P->max_iter;
+    const double* R64 = c.S->r64;
+    double* U = c.P->u;
+    float* X = c.S->x;
+    float* R = c.S->r;
+    float* Pv = c.S->p;
+    float* Q = c.S->q;
+    float2* W = static_cast<float2*>(c.S->W);
+    float2* rb = reinterpret_cast<float2*>(c.smem) + (tid / TPL) * LS;
+    const ColArgs A{n, K, KB32, KB32, 1};
+    const int ts = tid / (4 * TPL), w = tid % (4 * TPL);
+    const int cr = (KB32 + c.g.G * TPR32 - 1) / (c.g.G * TPR32);
+    const double sc = 1.0 / sqrt(rn2);
+    float rf = 0.0f;
+    for_own(c, [&](int64_t k) {
+      const float rv = (float)(R64[k] * sc);
+      R[k] = rv;
+      X[k] = 0.0f;
+      rf += rv * rv;
+    });
+    double rrv = gsum(c, rf);
+    const double stop = c.P->inner_tol * c.P->inner_tol * rrv;
+    bool first = true;
+    float be = 0.0f;
+    while (rrv > stop && iters < max_iter) {
+      for (int i = 0; i < rr; ++i)
+        row_fwd_pair<float, LOGM>(
+            [&](int64_t row, int x) {
+              const int64_t k = row * n + x;
+              const float v = first ? R[k] : R[k] + be * Pv[k];
+              Pv[k] = v;
+              return v;
+            },
+            W, n, n, KB32, c.tw32, pair_of(c, i), rb, tl);
+      c.g.sync();
+      for (int i = 0; i < cr; ++i)
+        col_tile<float, LOGM, SYM2>(W, W, A, c.P->lam32, c.tw32, 0, ((int64_t)i * c.g.G + c.g.rank) * TPR32 + ts,
+                                    reinterpret_cast<float2*>(c.smem) + ts * 4 * LST, w % 4, w / 4);
+      c.g.sync();
+      float pqf = 0.0f;
+      for (int i = 0; i < rr; ++i)
+        row_inv_pair<float, LOGM>(W, n, n, KB32, c.tw32, pair_of(c, i), rb, tl, [&](int64_t row, int x, float v) {
+          const int64_t k = row * n + x;
+          Q[k] = v;
+          pqf += v * Pv[k];
         });
-        const double rr1 = gsum(rf1);
-        be = (float)(rr1 / rr);
-        rr = rr1;
-        first = false;
-        ++iters;
+      const double pq = gsum(c, pqf);
+      if (!(pq > 0.0) || !isfinite(pq)) break;  // inner breakdown: refine from here
+      const float al = (float)(rrv / pq);
+      float rf1 = 0.0f;
+      for_own(c, [&](int64_t k) {
+        X[k] += al * Pv[k];
+        const float rv = R[k] - al * Q[k];
+        R[k] = rv;
+        rf1 += rv * rv;
+      });
+      const double rr1 = gsum(c, rf1);
+      be = (float)(rr1 / rrv);
+      rrv = rr1;
+      first = false;
+      ++iters;
+    }
+    const double s = sqrt(rn2);
+    for_own(c, [&](int64_t k) { U[k] += s * (double)X[k]; });
+    return iters;
+  }
+
+  // mixed-precision refinement to ||f - A u|| <= rtol ||f||
+  static __device__ __noinline__ void solve(Ctx& c, frac_solve_info* info) {
+    const double fn2 = start(c);
+    const double tol2 = c.P->rtol * c.P->rtol * fn2;
+    int iters = 0, outer = 0, status = FRAC_OK;
+    double rn2 = 0.0;
+    if (fn2 != 0.0) {
+      rn2 = residual(c);
+      double prev = INFINITY;
+      while (rn2 > tol2 && iters < c.P->max_iter && outer < 100) {
+        iters = inner(c, rn2, iters);
+        rn2 = residual(c);
+        ++outer;
+        if (!(rn2 < prev) && outer > 3) break;  // refinement stagnated
+        prev = rn2;
       }
-      const double s = sqrt(rn2);
-      for_own([&](int64_t k) { U[k] += s * (double)X[k]; });
-      rn2 = residual();
-      ++outer;
-      if (!(rn2 < prev) && outer > 3) break;  // refinement stagnated
-      prev = rn2;
+    }
+    if (c.g.rank == 0 && threadIdx.x == 0) {
+      frac_solve_info out;
+      out.iters = iters;
+      out.outer = outer;
+      out.reserved = 0;
+      out.rel_resid = fn2 > 0.0 ? sqrt(rn2 / fn2) : (fn2 == 0.0 ? 0.0 : NAN);  // NaN: non-finite f
+      if (status == FRAC_OK && !(out.rel_resid <= c.P->rtol)) status = FRAC_ENOCONV;
+      if (!isfinite(out.rel_resid)) status = FRAC_EINVAL;
+      out.status = status;
+      *info = out;
     }
   }
-  if (g.rank == 0 && tid == 0) {
-    frac_solve_info out;
-    out.iters = iters;
-    out.outer = outer;
-    out.reserved = 0;
-    out.rel_resid = fn2 > 0.0 ? sqrt(rn2 / fn2) : (fn2 == 0.0 ? 0.0 : NAN);  // NaN: non-finite f
-    if (status == FRAC_OK && !(out.rel_resid <= P.rtol)) status = FRAC_ENOCONV;
-    if (!isfinite(out.rel_resid)) status = FRAC_EINVAL;
-    out.status = status;
-    *info = out;
-  }
-}
+};
 
 __device__ void solve_any(const B2Args& A, int item, const B2Slot& S, const Group g, unsigned char* smem,
                           double* red, double* slots) {
   const B2Prob& P = A.probs[item];
   frac_solve_info* info = A.info + item;
+  Ctx c{&P, &S, g, nullptr, nullptr, smem, red, slots, 0};
   switch (P.logm) {  // uniform over the group
-#define FRAC_B2_CASE(L) \
-  case L: solve_problem<L>(P, info, S, g, A.tw32[L], A.tw64[L], smem, red, slots); break;
+#define FRAC_B2_CASE(L)       \
+  case L:                     \
+    c.tw32 = A.tw32[L];       \
+    c.tw64 = A.tw64[L];       \
+    Solver<L>::solve(c, info); \
+    break;
     FRAC_B2_CASE(5)
     FRAC_B2_CASE(6)
     FRAC_B2_CASE(7)
@@ -570,8 +612,8 @@ bool batch2d_eligible(const frac_op* op, const frac_solve_opts* opts) {
 }
 
 int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
-                   const frac_solve_opts* opts, frac_solve_info* info, const int64_t* idx, cudaStream_t st,
-                   frac_batch_plan* plan_out, int pin_size, int pin_cut) {
+                   const frac_solve_opts* opts, const int64_t* idx, cudaStream_t st, frac_batch_plan* plan_out,
+                   int pin_size, int pin_cut, BatchPending* pend) {
   if (count <= 0) return FRAC_OK;
   FRAC_TRY(configure_kernel());
   int dev = 0;
@@ -651,53 +693,51 @@ int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const
     if (it->n > nlo_max) nlo_max = it->n, llo = it->logm;
   const size_t cslot = cl.empty() ? 0 : slot_bytes(ncl_max, lcl), lslot = lo.empty() ? 0 : slot_bytes(nlo_max, llo);
   const int n_cslots = cl.empty() ? 0 : best_ncl, n_lslots = lo.empty() ? 0 : grid;
-  DevBuf b{st, {}};
+  pend->st = st;
   B2Prob* dp;
   B2Slot* ds;
-  frac_solve_info* di;
   unsigned int* next;
   unsigned char* scratch;
-  FRAC_TRY(b.get(&dp, count * sizeof(B2Prob)));
-  FRAC_TRY(b.get(&ds, (size_t)(n_cslots + n_lslots + 1) * sizeof(B2Slot)));
-  FRAC_TRY(b.get(&di, count * sizeof(frac_solve_info)));
-  FRAC_TRY(b.get(&next, 2 * sizeof(unsigned int)));
-  FRAC_TRY(b.get(&scratch, (size_t)n_cslots * cslot + (size_t)n_lslots * lslot));
+  FRAC_TRY(pend->alloc(&dp, count * sizeof(B2Prob)));
+  FRAC_TRY(pend->alloc(&ds, (size_t)(n_cslots + n_lslots + 1) * sizeof(B2Slot)));
+  FRAC_TRY(pend->alloc(&pend->dinfo, count * sizeof(frac_solve_info)));
+  FRAC_TRY(pend->alloc(&next, 2 * sizeof(unsigned int)));
+  FRAC_TRY(pend->alloc(&scratch, (size_t)n_cslots * cslot + (size_t)n_lslots * lslot));
   std::vector<B2Prob> hp;
-  std::vector<int64_t> order;
   for (const Item* it : cl) {
     hp.push_back(make_prob(ops[it->idx], f[it->idx], u[it->idx], opts));
-    order.push_back(it->idx);
+    pend->order.push_back(it->idx);
   }
   for (const Item* it : lo) {
     hp.push_back(make_prob(ops[it->idx], f[it->idx], u[it->idx], opts));
-    order.push_back(it->idx);
+    pend->order.push_back(it->idx);
   }
   std::vector<B2Slot> hs;
   for (int i = 0; i < n_cslots; ++i) hs.push_back(carve(scratch + (size_t)i * cslot, ncl_max, lcl));
   for (int i = 0; i < n_lslots; ++i)
     hs.push_back(carve(scratch + (size_t)n_cslots * cslot + (size_t)i * lslot, nlo_max, llo));
   if (hs.empty()) hs.push_back(B2Slot{});
-  FRAC_CUDA_TRY(cudaMemcpyAsync(dp, hp.data(), hp.size() * sizeof(B2Prob), cudaMemcpyHostToDevice, st));
-  FRAC_CUDA_TRY(cudaMemcpyAsync(ds, hs.data(), hs.size() * sizeof(B2Slot), cudaMemcpyHostToDevice, st));
+  // pinned staging kept until collect(), so the uploads do not wait for the stream
+  const size_t hb = hp.size() * sizeof(B2Prob), sb = hs.size() * sizeof(B2Slot);
+  unsigned char* stage = nullptr;
+  FRAC_CUDA_TRY(cudaMallocHost(&stage, hb + sb));
+  pend->pinned = stage;
+  std::memcpy(stage, hp.data(), hb);
+  std::memcpy(stage + hb, hs.data(), sb);
+  FRAC_CUDA_TRY(cudaMemcpyAsync(dp, stage, hb, cudaMemcpyHostToDevice, st));
+  FRAC_CUDA_TRY(cudaMemcpyAsync(ds, stage + hb, sb, cudaMemcpyHostToDevice, st));
   FRAC_CUDA_TRY(cudaMemsetAsync(next, 0, 2 * sizeof(unsigned int), st));
   B2Args a = {};
   a.probs = dp;
-  a.info = di;
+  a.info = pend->dinfo;
   a.n_cluster = (int)cl.size();
   a.n_local = (int)lo.size();
   a.next = next;
   a.cslots = ds;
   a.lslots = ds + n_cslots;
   fill_twiddles(a);
-  {
-    prof::Scope ps("batch2d", st);
-    FRAC_TRY(launch(a, C, grid, smem, st));
-  }
-  std::vector<frac_solve_info> hi(count);
-  FRAC_CUDA_TRY(cudaMemcpyAsync(hi.data(), di, count * sizeof(frac_solve_info), cudaMemcpyDeviceToHost, st));
-  FRAC_CUDA_TRY(cudaStreamSynchronize(st));
-  for (size_t t = 0; t < order.size(); ++t) info[order[t]] = hi[t];
-  return FRAC_OK;
+  prof::Scope ps("batch2d", st);
+  return launch(a, C, grid, smem, st);
 }
 
 }  // namespace frac

@@ -1,7 +1,7 @@
 // Persistent batched 2D solver (batch2d.cu).
 #pragma once
 
-#include "common.cuh"
+#include "apply.cuh"
 
 namespace frac {
 
@@ -12,12 +12,13 @@ constexpr int kBatch2dMinLog = 5, kBatch2dMaxLog = 10;
 // FFT length in range); f and u must also be device pointers.
 bool batch2d_eligible(const frac_op* op, const frac_solve_opts* opts);
 
-// Solves the problems idx[0..count) of (ops, f, u) in one persistent launch;
-// fills info[idx[t]] and, when plan is not null, the plan used.  pin_size > 0
-// fixes the cluster size (and pin_cut the first cluster-wide log2 FFT length)
-// instead of the autotuner's choice.
+// Launches the problems idx[0..count) of (ops, f, u) in one persistent launch
+// on st (the autotuner's first timings of a new FFT length run, and wait,
+// before it); the results arrive through pend->collect().  Fills the plan used
+// when plan is not null.  pin_size > 0 fixes the cluster size (and pin_cut the
+// first cluster-wide log2 FFT length) instead of the autotuner's choice.
 int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
-                   const frac_solve_opts* opts, frac_solve_info* info, const int64_t* idx, cudaStream_t st,
-                   frac_batch_plan* plan, int pin_size, int pin_cut);
+                   const frac_solve_opts* opts, const int64_t* idx, cudaStream_t st, frac_batch_plan* plan,
+                   int pin_size, int pin_cut, BatchPending* pend);
 
 }  // namespace frac

@@ -358,40 +358,65 @@ static int solve_1d(const frac_op* op, const double* f, double* u, const frac_so
   return FRAC_OK;
 }
 
+int BatchPending::collect(frac_solve_info* info) {
+  std::vector<frac_solve_info> hi(order.size());
+  if (!order.empty()) {
+    FRAC_CUDA_TRY(cudaMemcpyAsync(hi.data(), dinfo, hi.size() * sizeof(frac_solve_info), cudaMemcpyDeviceToHost, st));
+    FRAC_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  else if (pinned) {
+    FRAC_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  for (size_t t = 0; t < order.size(); ++t) info[order[t]] = hi[t];
+  for (void* p : bufs) cudaFreeAsync(p, st);
+  bufs.clear();
+  order.clear();
+  if (pinned) cudaFreeHost(pinned);
+  pinned = nullptr;
+  return FRAC_OK;
+}
+
+BatchPending::~BatchPending() {
+  if (pinned) {
+    cudaStreamSynchronize(st);
+    cudaFreeHost(pinned);
+  }
+  for (void* p : bufs) cudaFreeAsync(p, st);
+}
+
 int solve_batch_1d(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
-                   const frac_solve_opts* opts, frac_solve_info* info, const int64_t* idx, cudaStream_t st) {
-  // group the listed problems by FFT length; one launch per group
-  Ws ws{st, {}};
+                   const frac_solve_opts* opts, const int64_t* idx, cudaStream_t st, BatchPending* pend) {
+  // group the listed problems by FFT length; one launch per group, largest first
+  pend->st = st;
   std::vector<std::vector<int64_t>> groups(14);
   for (int64_t t = 0; t < count; ++t) groups[ops[idx[t]]->logm].push_back(idx[t]);
-  frac_solve_info* di;
   Solve1dTask* dt;
-  FRAC_TRY(ws.get(&di, count * sizeof(frac_solve_info)));
-  FRAC_TRY(ws.get(&dt, count * sizeof(Solve1dTask)));
+  FRAC_TRY(pend->alloc(&pend->dinfo, count * sizeof(frac_solve_info)));
+  FRAC_TRY(pend->alloc(&dt, count * sizeof(Solve1dTask)));
   std::vector<Solve1dTask> tasks;
-  std::vector<int64_t> order;
   std::vector<std::pair<int, int64_t>> launches;  // (logm, first task)
-  for (int lg = 1; lg <= 13; ++lg) {
+  for (int lg = 13; lg >= 1; --lg) {
     if (groups[lg].empty()) continue;
     launches.emplace_back(lg, (int64_t)tasks.size());
     for (int64_t i : groups[lg]) {
       const frac_op* op = ops[i];
-      tasks.push_back(Solve1dTask{f[i], u[i], op->lam32, op->lam64, di + tasks.size(), opts->rtol,
+      tasks.push_back(Solve1dTask{f[i], u[i], op->lam32, op->lam64, pend->dinfo + tasks.size(), opts->rtol,
                                   opts->inner_tol > 0.0 ? opts->inner_tol : 1e-4, (int)op->n, opts->max_iter,
                                   opts->use_x0 ? 1 : 0});
-      order.push_back(i);
+      pend->order.push_back(i);
     }
   }
-  FRAC_CUDA_TRY(cudaMemcpyAsync(dt, tasks.data(), tasks.size() * sizeof(Solve1dTask), cudaMemcpyHostToDevice, st));
+  // pinned staging, kept until collect(), so the upload does not wait for the stream
+  Solve1dTask* ht = nullptr;
+  FRAC_CUDA_TRY(cudaMallocHost(&ht, tasks.size() * sizeof(Solve1dTask)));
+  pend->pinned = ht;
+  std::copy(tasks.begin(), tasks.end(), ht);
+  FRAC_CUDA_TRY(cudaMemcpyAsync(dt, ht, tasks.size() * sizeof(Solve1dTask), cudaMemcpyHostToDevice, st));
   for (size_t g = 0; g < launches.size(); ++g) {
     const int64_t first = launches[g].second;
     const int64_t last = g + 1 < launches.size() ? launches[g + 1].second : (int64_t)tasks.size();
     FRAC_TRY(solve1d_launch(launches[g].first, opts->precision == FRAC_MIXED_IR, dt + first, (int)(last - first), st));
   }
-  std::vector<frac_solve_info> hi(tasks.size());
-  FRAC_CUDA_TRY(cudaMemcpyAsync(hi.data(), di, hi.size() * sizeof(frac_solve_info), cudaMemcpyDeviceToHost, st));
-  FRAC_CUDA_TRY(cudaStreamSynchronize(st));
-  for (size_t t = 0; t < order.size(); ++t) info[order[t]] = hi[t];
   return FRAC_OK;
 }
 
