@@ -516,6 +516,108 @@ def solve_cg(a: np.ndarray, c: float, rhs: np.ndarray, rtol: float = 1e-12, maxi
 
 
 # ---------------------------------------------------------------------------
+# tau preconditioner (the paper names no solver; this is the preconditioned CG
+# the library offers).  The tau matrix of a symmetric Toeplitz matrix T_m with
+# first column t_0..t_{m-1} is tau(T_m) = T_m - H_m, H_m the Hankel matrix with
+# H_ij = t_{i+j+2} (i + j <= m - 3) and t_{2m-i-j} (i + j >= m + 1), 0-based;
+# it is diagonalised by the sine transform S_jk = sqrt(2/(m+1)) sin(pi j k/(m+1)),
+# j, k = 1..m, with eigenvalues the symbol t_0 + 2 sum_j t_j cos(pi j k/(m+1)).
+# Multilevel: tensor products over the axes.  For n interior points the
+# preconditioner is the tau matrix of size m = M/2 - 1 >= n (M the FFT length
+# of the apply) of the Toeplitz matrix whose generator is a zero beyond n - 1,
+# restricted to the leading n^d block: P = R tau(T_m)^{-1} R^T.  PARITY
+# UNPINNED against the paper (it has no solver); pinned to the definition of
+# the tau algebra by the Hankel identity in tests.
+# ---------------------------------------------------------------------------
+
+def fft_len(n: int) -> int:
+    """FFT length of the circulant embedding: max(2, 2^ceil(log2(2n - 1)))."""
+    M = 2
+    while M < 2 * n - 1:
+        M *= 2
+    return M
+
+
+def sine_matrix(m: int) -> np.ndarray:
+    """Orthogonal, symmetric DST-I matrix of size m."""
+    j = np.arange(1, m + 1)
+    return math.sqrt(2.0 / (m + 1)) * np.sin(np.pi * np.outer(j, j) / (m + 1))
+
+
+def tau_hankel_1d(t: np.ndarray) -> np.ndarray:
+    """H_m of tau(T_m) = T_m - H_m for the symmetric Toeplitz column t (length m)."""
+    m = len(t)
+    H = np.zeros((m, m))
+    for i in range(m):
+        for j in range(m):
+            s = i + j
+            if s <= m - 3:
+                H[i, j] = t[s + 2]
+            elif s >= m + 1:
+                H[i, j] = t[2 * m - s]
+    return H
+
+
+def tau_symbol(a: np.ndarray, c: float, n: int, m: int) -> np.ndarray:
+    """Eigenvalues of -c tau(T_m) on k in [1..m]^d: the symbol of the generator
+    a (entries |j| <= n - 1 per axis, zero beyond) at theta_k = pi k / (m + 1)."""
+    d = a.ndim
+    k = np.arange(1, m + 1)
+    j = np.arange(0, n)
+    Cm = np.cos(np.pi * np.outer(k, j) / (m + 1))   # (m, n)
+    Cm[:, 1:] *= 2.0                                   # +-j folded
+    out = a[tuple(slice(0, n) for _ in range(d))].copy()
+    for ax in range(d):
+        out = np.moveaxis(np.tensordot(Cm, np.moveaxis(out, ax, 0), axes=(1, 0)), 0, ax)
+    return -c * out
+
+
+def tau_precond(a: np.ndarray, c: float, v: np.ndarray, m: int | None = None) -> np.ndarray:
+    """P v = R tau(T_m)^{-1} R^T v with m = M/2 - 1 (default), v of shape (n,)*d."""
+    n = v.shape[0]
+    d = v.ndim
+    if m is None:
+        m = fft_len(n) // 2 - 1
+    if m < n:
+        raise ValueError("tau system smaller than the problem (n is a power of two)")
+    S = sine_matrix(m)
+    w = np.zeros((m,) * d)
+    w[tuple(slice(0, n) for _ in range(d))] = v
+    for ax in range(d):
+        w = np.moveaxis(np.tensordot(S, np.moveaxis(w, ax, 0), axes=(1, 0)), 0, ax)
+    w = w / tau_symbol(a, c, n, m)
+    for ax in range(d):
+        w = np.moveaxis(np.tensordot(S, np.moveaxis(w, ax, 0), axes=(1, 0)), 0, ax)
+    return w[tuple(slice(0, n) for _ in range(d))]
+
+
+def solve_pcg(a: np.ndarray, c: float, rhs: np.ndarray, rtol: float = 1e-12, maxiter: int = 100000):
+    """Conjugate gradients preconditioned by tau_precond; stops on the true
+    residual ||r|| <= rtol ||rhs||; returns (u, iterations)."""
+    n = rhs.shape[0]
+    A = operator_matrix(a, c, n)
+    b = rhs.reshape(-1)
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = tau_precond(a, c, r.reshape(rhs.shape)).reshape(-1)
+    pvec = z.copy()
+    rz = r @ z
+    bn = math.sqrt(b @ b)
+    it = 0
+    while math.sqrt(r @ r) > rtol * bn and it < maxiter:
+        q = A @ pvec
+        alpha_k = rz / (pvec @ q)
+        x += alpha_k * pvec
+        r -= alpha_k * q
+        z = tau_precond(a, c, r.reshape(rhs.shape)).reshape(-1)
+        rz_new = r @ z
+        pvec = z + (rz_new / rz) * pvec
+        rz = rz_new
+        it += 1
+    return x.reshape(rhs.shape), it
+
+
+# ---------------------------------------------------------------------------
 # Grids and closed-form references
 # ---------------------------------------------------------------------------
 
