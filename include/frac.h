@@ -76,6 +76,7 @@ typedef struct frac_op_info_t {
   int64_t fft_len;        /* M: circulant embedding length per axis (power of two >= 2n-1) */
   int64_t n_gen;          /* N + 1: generator entries per axis                     */
   size_t device_bytes;    /* device memory owned by the op                         */
+  int32_t precond_ok;     /* 1: the tau preconditioner applies (n <= M/2 - 1, positive symbol) */
 } frac_op_info_t;
 
 /*
@@ -141,11 +142,35 @@ int frac_apply(const frac_op* op, const void* u, void* y, int dtype, int64_t bat
  */
 int frac_apply_static(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* stream);
 
+/*
+ * frac_precond -- z = P r, the tau preconditioner of the CG solves (the paper
+ * names no solver; this is the library's).  With m = M/2 - 1 >= n per axis,
+ * P = R tau(T_m)^{-1} R^T: T_m is the Toeplitz matrix of the generator a
+ * zero-extended to size m (T_n is its leading block, R the restriction to it)
+ * and tau(T_m) = T_m - H_m (H_m the Hankel correction, levelwise in d >= 2) is
+ * diagonalised by the sine transform of size m with the circulant-embedding
+ * eigenvalues of A as its eigenvalues; P is symmetric positive definite.
+ * Computed as the FFT pipeline of frac_apply on the odd extension of r with the
+ * reciprocal symbol.  Layout, dtype, batch, buffers (device or host) and
+ * stream as frac_apply; r and z must not overlap.
+ * Errors: as frac_apply, plus FRAC_ENOTSUP when the preconditioner does not
+ * apply to op (n a power of two, so that M/2 - 1 < n, or a symbol that is not
+ * positive; frac_op_info reports precond_ok).
+ */
+int frac_precond(const frac_op* op, const void* r, void* z, int dtype, int64_t batch, void* stream);
+
+/* Preconditioner of the CG iterations (frac_solve_opts.precond). */
+enum {
+  FRAC_PRECOND_TAU = 0,   /* the tau preconditioner (see frac_precond); plain CG where it does not apply */
+  FRAC_PRECOND_NONE = 1   /* plain CG */
+};
+
 typedef struct frac_solve_opts {
   double rtol;          /* target ||f - A u||_2 / ||f||_2 (true residual, FP64); e.g. 1e-10 */
   int32_t max_iter;     /* cap on CG iterations (all inner iterations summed for MIXED_IR) */
   int32_t precision;    /* FRAC_PLAIN_F64 or FRAC_MIXED_IR                                  */
   int32_t use_x0;       /* nonzero: u holds the initial guess on entry                      */
+  int32_t precond;      /* FRAC_PRECOND_TAU (0, the default) or FRAC_PRECOND_NONE           */
   double inner_tol;     /* MIXED_IR: relative residual reduction of each FP32 inner solve   */
 } frac_solve_opts;
 
@@ -153,7 +178,7 @@ typedef struct frac_solve_info {
   int32_t status;       /* FRAC_OK, FRAC_ENOCONV or FRAC_EBREAKDOWN                    */
   int32_t iters;        /* CG iterations (inner iterations summed for MIXED_IR)        */
   int32_t outer;        /* refinement steps (MIXED_IR), 0 for PLAIN_F64                */
-  int32_t reserved;
+  int32_t precond;      /* 1: the tau preconditioner was used, 0: plain CG               */
   double rel_resid;     /* final ||f - A u||_2 / ||f||_2, recomputed with the FP64 apply */
 } frac_solve_info;
 

@@ -36,17 +36,17 @@ class Problem(ctypes.Structure):
 class OpInfo(ctypes.Structure):
     _fields_ = [("c_dalpha", ctypes.c_double), ("a0", ctypes.c_double), ("far_field", ctypes.c_double),
                 ("norm_bound", ctypes.c_double), ("fft_len", ctypes.c_int64), ("n_gen", ctypes.c_int64),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("precond_ok", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("use_x0", ctypes.c_int32), ("inner_tol", ctypes.c_double)]
+                ("use_x0", ctypes.c_int32), ("precond", ctypes.c_int32), ("inner_tol", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("outer", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("rel_resid", ctypes.c_double)]
+                ("precond", ctypes.c_int32), ("rel_resid", ctypes.c_double)]
 
 
 class BatchPlan(ctypes.Structure):
@@ -90,6 +90,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.frac_apply.restype = i32
     lib.frac_apply_static.argtypes = [vp, vp, vp, i32, i64, vp]
     lib.frac_apply_static.restype = i32
+    lib.frac_precond.argtypes = [vp, vp, vp, i32, i64, vp]
+    lib.frac_precond.restype = i32
     lib.frac_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.frac_solve.restype = i32
     lib.frac_solve_batch.argtypes = [i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -261,37 +263,62 @@ class FracOp:
             raise FracError(s, "frac_apply")
         return y
 
+    def precond(self, r, out=None, stream=None):
+        """z = P r with the tau preconditioner (frac_precond); shapes and dtypes as apply."""
+        code = _dtype_code(r)
+        nd = self.n ** self.d
+        numel = r.size if isinstance(r, np.ndarray) else r.numel()
+        if numel % nd:
+            raise ValueError(f"size {numel} is not a multiple of n^d = {nd}")
+        z = _empty_like(r) if out is None else out
+        s = self._lib.frac_precond(self._h, _ptr(r), _ptr(z), code, numel // nd, _stream(stream))
+        if s != 0:
+            raise FracError(s, "frac_precond")
+        return z
+
     # -- solve --
     def solve(self, f, u=None, rtol: float = 1e-10, max_iter: int = 200000, precision: str = "mixed",
-              inner_tol: float = 1e-4, stream=None):
+              inner_tol: float = 1e-4, stream=None, precond: str = "tau"):
         """Solve A u = f (g = 0); returns (u, info dict).  f, u float64."""
         if _dtype_code(f) != F64:
             raise TypeError("solve takes float64 data")
         use_x0 = u is not None
         if u is None:
             u = _empty_like(f)
-        opts = SolveOpts(rtol, max_iter, MIXED_IR if precision == "mixed" else PLAIN_F64, int(use_x0), inner_tol)
+        opts = _opts(rtol, max_iter, precision, use_x0, inner_tol, precond)
         info = SolveInfo()
         s = self._lib.frac_solve(self._h, _ptr(f), None, _ptr(u), ctypes.byref(opts), ctypes.byref(info),
                                  _stream(stream))
-        out = {k: getattr(info, k) for k, _ in SolveInfo._fields_ if k != "reserved"}
+        out = {k: getattr(info, k) for k, _ in SolveInfo._fields_}
         if s not in (0, 4):
             raise FracError(s, "frac_solve")
         return u, out
 
 
+PRECOND_TAU, PRECOND_NONE = 0, 1
+
+
+def _opts(rtol, max_iter, precision, use_x0, inner_tol, precond) -> "SolveOpts":
+    if precision not in ("mixed", "f64"):
+        raise ValueError("precision is 'mixed' or 'f64'")
+    if precond not in ("tau", "none"):
+        raise ValueError("precond is 'tau' or 'none'")
+    return SolveOpts(rtol, max_iter, MIXED_IR if precision == "mixed" else PLAIN_F64, int(use_x0),
+                     PRECOND_TAU if precond == "tau" else PRECOND_NONE, inner_tol)
+
+
 def solve_batch(ops, fs, us, rtol: float = 1e-10, max_iter: int = 200000, precision: str = "mixed",
-                inner_tol: float = 1e-4, stream=None):
+                inner_tol: float = 1e-4, stream=None, precond: str = "tau"):
     """Solve ops[i] u[i] = f[i] for all i (device tensors); returns a list of info dicts."""
     lib = load()
     cnt = len(ops)
     H = (ctypes.c_void_p * cnt)(*[op.handle.value for op in ops])
     F = (ctypes.c_void_p * cnt)(*[_ptr(f) for f in fs])
     U = (ctypes.c_void_p * cnt)(*[_ptr(u) for u in us])
-    opts = SolveOpts(rtol, max_iter, MIXED_IR if precision == "mixed" else PLAIN_F64, 0, inner_tol)
+    opts = _opts(rtol, max_iter, precision, False, inner_tol, precond)
     infos = (SolveInfo * cnt)()
     s = lib.frac_solve_batch(cnt, H, F, U, ctypes.byref(opts), infos, _stream(stream))
-    out = [{k: getattr(i, k) for k, _ in SolveInfo._fields_ if k != "reserved"} for i in infos]
+    out = [{k: getattr(i, k) for k, _ in SolveInfo._fields_} for i in infos]
     if s not in (0, 4):
         raise FracError(s, "frac_solve_batch")
     return out
@@ -314,7 +341,7 @@ def batch_pin_plan(cluster_size: int, first_cluster_logm: int = 11) -> None:
 
 
 def _info(si: SolveInfo) -> dict:
-    return {k: getattr(si, k) for k, _ in SolveInfo._fields_ if k != "reserved"}
+    return {k: getattr(si, k) for k, _ in SolveInfo._fields_}
 
 
 class Engine:
@@ -332,7 +359,8 @@ class Engine:
         self._keep = {}
 
     def submit(self, op: "FracOp", f, u=None, rtol: float = 1e-10, max_iter: int = 200000,
-               precision: str = "mixed", inner_tol: float = 1e-4, use_x0: bool = False) -> tuple:
+               precision: str = "mixed", inner_tol: float = 1e-4, use_x0: bool = False,
+               precond: str = "tau") -> tuple:
         """Queue op u = f; the solution goes to `u` (a new buffer if None), whose
         contents are the initial guess only when use_x0 is set.  Returns (job id, u)."""
         if _dtype_code(f) != F64:
@@ -340,7 +368,7 @@ class Engine:
         if u is None:
             u = _empty_like(f)
             use_x0 = False
-        opts = SolveOpts(rtol, max_iter, MIXED_IR if precision == "mixed" else PLAIN_F64, int(use_x0), inner_tol)
+        opts = _opts(rtol, max_iter, precision, use_x0, inner_tol, precond)
         job = ctypes.c_int64()
         s = self._lib.frac_engine_submit(self._h, op.handle, _ptr(f), _ptr(u), ctypes.byref(opts), ctypes.byref(job))
         if s != 0:

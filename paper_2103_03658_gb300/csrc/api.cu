@@ -151,11 +151,13 @@ int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
   }
   op->c = c_dalpha(d, prob->alpha);
   cudaGetDevice(&op->device);
-  op->device_bytes = op->ngen * sizeof(double) + op->nsym * (sizeof(double) + sizeof(float));
+  op->device_bytes = op->ngen * sizeof(double) + 2 * op->nsym * (sizeof(double) + sizeof(float));
   int s = FRAC_OK;
   if (cudaMalloc(&op->a, op->ngen * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&op->lam64, op->nsym * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&op->lam32, op->nsym * sizeof(float)) != cudaSuccess) {
+      cudaMalloc(&op->lam32, op->nsym * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&op->pinv64, op->nsym * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&op->pinv32, op->nsym * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     s = FRAC_ENOMEM;
   }
@@ -174,6 +176,8 @@ void frac_op_free(frac_op* op) {
   if (op->a) cudaFree(op->a);
   if (op->lam64) cudaFree(op->lam64);
   if (op->lam32) cudaFree(op->lam32);
+  if (op->pinv64) cudaFree(op->pinv64);
+  if (op->pinv32) cudaFree(op->pinv32);
   delete op;
 }
 
@@ -186,6 +190,7 @@ int frac_op_info(const frac_op* op, frac_op_info_t* info) {
   info->fft_len = op->M;
   info->n_gen = op->N + 1;
   info->device_bytes = op->device_bytes;
+  info->precond_ok = op->precond_ok;
   return FRAC_OK;
 }
 
@@ -195,8 +200,13 @@ int frac_op_generator(const frac_op* op, double* a, size_t count) {
   return FRAC_OK;
 }
 
-int frac_apply(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* stream) {
+}  // extern "C"
+
+// frac_apply (precond = false) and frac_precond (precond = true): device or host buffers.
+static int apply_entry(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* stream,
+                       bool precond) {
   if (!op || batch < 0 || (dtype != FRAC_F32 && dtype != FRAC_F64)) return FRAC_EINVAL;
+  if (precond && !op->precond_ok) return FRAC_ENOTSUP;
   if (batch == 0) return FRAC_OK;
   if (!u || !y || u == y) return FRAC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -219,8 +229,13 @@ int frac_apply(const frac_op* op, const void* u, void* y, int dtype, int64_t bat
     FRAC_CUDA_TRY(cudaMallocAsync(&tmp_y, bytes, st));
     yd = tmp_y;
   }
-  int s = dtype == FRAC_F64 ? apply_t<double>(op, (const double*)ud, (double*)yd, batch, ws, st)
-                            : apply_t<float>(op, (const float*)ud, (float*)yd, batch, ws, st);
+  int s;
+  if (precond)
+    s = dtype == FRAC_F64 ? precond_t<double>(op, (const double*)ud, (double*)yd, batch, ws, st)
+                          : precond_t<float>(op, (const float*)ud, (float*)yd, batch, ws, st);
+  else
+    s = dtype == FRAC_F64 ? apply_t<double>(op, (const double*)ud, (double*)yd, batch, ws, st)
+                          : apply_t<float>(op, (const float*)ud, (float*)yd, batch, ws, st);
   if (s == FRAC_OK && !dy)
     if (cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = FRAC_ECUDA;
   if (ws) cudaFreeAsync(ws, st);
@@ -231,6 +246,16 @@ int frac_apply(const frac_op* op, const void* u, void* y, int dtype, int64_t bat
     if (s == FRAC_OK && e != cudaSuccess) s = FRAC_ECUDA;
   }
   return s;
+}
+
+extern "C" {
+
+int frac_apply(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* stream) {
+  return apply_entry(op, u, y, dtype, batch, stream, false);
+}
+
+int frac_precond(const frac_op* op, const void* r, void* z, int dtype, int64_t batch, void* stream) {
+  return apply_entry(op, r, z, dtype, batch, stream, true);
 }
 
 int frac_solve(const frac_op* op, const double* f, const double* g, double* u, const frac_solve_opts* opts,

@@ -1,363 +1,8 @@
-// y = A u by circulant embedding and FFT (Sec. 2.1: the Toeplitz structure
-// allows an O(N log N) product), A = -c_{d,alpha} T(a).  The scaled symbol Lambda (real, even,
-// stored on [0, M/2]^d) already carries -c / M (d = 1) or -c / (2 M^d)
-// (d >= 2, the 2 from the two-rows-per-complex packing below).
-//
-// d = 1: one kernel; two vectors share one complex line (z = u_a + i u_b,
-//        A is real so Re and Im stay separate); pad, FFT, * Lambda, iFFT,
-//        extract, all in shared memory.
-// d = 2: rows (R2C, two rows per complex line, spectra separated in the
-//        epilogue) -> columns (pad, FFT, * Lambda, iFFT, extract; in place)
-//        -> rows (C2R, two rows per line).
-// d = 3: rows -> y-columns (pad, FFT) -> z-columns (pad, FFT, * Lambda, iFFT,
-//        extract; in place) -> y-columns (iFFT, extract) -> rows.
-#include <cstdio>
-
-#include "apply.cuh"
-#include "fft.cuh"
-#include "passes.cuh"
-#include "prof.cuh"
+// y = A u by circulant embedding and FFT (Sec. 2.1): the operator apply and
+// the fused CG apply; kernels and launch helpers in apply_kernels.cuh.
+#include "apply_kernels.cuh"
 
 namespace frac {
-
-using namespace fft;
-
-// minimum resident blocks per SM requested from the compiler: at least 512 resident
-// threads for FP32 kernels and 256 for FP64 (registers capped at 128 and 255 per thread);
-// the row kernels ask for twice that
-// (clamped to the 32 resident blocks an SM can hold)
-__host__ __device__ constexpr int clamp_blocks(int b) { return b < 1 ? 1 : (b > 32 ? 32 : b); }
-template <typename T> __host__ __device__ constexpr int minb(int nt) {
-  return clamp_blocks(((int)sizeof(T) == 4 ? 512 : 256) / nt);
-}
-// the row kernels hold one FFT per thread group and need fewer registers: 1024 / 512
-template <typename T> __host__ __device__ constexpr int minb_rows(int nt) {
-  return clamp_blocks(((int)sizeof(T) == 4 ? 1024 : 512) / nt);
-}
-// the column kernels: FP32 fits 64 registers without spills (two 512-thread
-// blocks per SM); FP64 needs more than 128 and keeps one block
-template <typename T> __host__ __device__ constexpr int minb_cols(int nt) {
-  return sizeof(T) == 4 ? minb_rows<T>(nt) : minb<T>(nt);
-}
-
-// ---------------------------------------------------------------------------
-// d = 1: whole convolution per line (two vectors per complex line)
-// ---------------------------------------------------------------------------
-
-template <typename T, int LOGM, int LINES>
-__global__ void __launch_bounds__(LINES * tpl(LOGM), minb<T>(LINES * tpl(LOGM)))
-k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const T* __restrict__ lam,
-         const cplx_t<T>* __restrict__ tw) {
-  using C = cplx_t<T>;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
-  C* buf = sm + line * LS;
-  const int64_t va = 2 * ((int64_t)blockIdx.x * LINES + line), vb = va + 1;
-  const bool ha = va < batch, hb = vb < batch;
-  // n <= M/2: entries e >= E/2 (x >= M/2) are zero padding, and only
-  // outputs x < n are kept, so both transforms are half-pruned
-  C v[E];
-#pragma unroll
-  for (int e = 0; e < E / 2; ++e) {
-    const int x = tl + e * TPL;
-    T re = (x < n && ha) ? u[va * n + x] : T(0);
-    T im = (x < n && hb) ? u[vb * n + x] : T(0);
-    v[e] = C{re, im};
-  }
-  fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int k = tl + e * TPL;
-    v[e] = cscale(v[e], lam[k <= M / 2 ? k : M - k]);
-  }
-  fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);
-#pragma unroll
-  for (int e = 0; e < E / 2; ++e) {
-    const int x = tl + e * TPL;
-    if (x < n) {
-      if (ha) y[va * n + x] = v[e].x;
-      if (hb) y[vb * n + x] = v[e].y;
-    }
-  }
-}
-
-// Every block stores its total in partials[blockIdx.x]; the last block to
-// arrive (counter) sums all of them in index order and calls fin(sum) in
-// thread 0, then resets the counter for the next use.
-template <typename F>
-__device__ __forceinline__ void last_block_reduce(double total, double* partials, unsigned int* counter, double* red,
-                                                  F fin) {
-  __shared__ bool last;
-  if (threadIdx.x == 0) {
-    partials[blockIdx.x] = total;
-    __threadfence();
-    last = atomicAdd(counter, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double s = 0.0;
-  for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) s += __ldcg(partials + i);
-  s = block_sum_all(s, red);
-  if (threadIdx.x == 0) {
-    fin(s);
-    *counter = 0;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Grid kernels over the passes of passes.cuh: one unit (row pair or column
-// tile) per thread group.
-// ---------------------------------------------------------------------------
-
-// Forward rows, LINES row pairs per block.  CG = true: the input is p = r +
-// beta p (beta from st), written back to u (= p) on the way in; the block
-// returns at once when st->done is set.
-template <typename T, int LOGM, int LINES, bool CG>
-__global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
-k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int64_t nrows, int KB,
-           const cplx_t<T>* __restrict__ tw, const T* __restrict__ r, const CGState* st) {
-  using C = cplx_t<T>;
-  constexpr int TPL = tpl(LOGM), LS = line_stride(LOGM);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (CG && st->done) return;
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
-  const int64_t pair = (int64_t)blockIdx.x * LINES + line;
-  if constexpr (CG) {
-    const T be = (T)st->beta;
-    T* p = const_cast<T*>(u);
-    row_fwd_pair<T, LOGM>(
-        [&](int64_t row, int x) {
-          const T v = r[row * n + x] + be * p[row * n + x];
-          p[row * n + x] = v;
-          return v;
-        },
-        W, n, nrows, KB, tw, pair, sm + line * LS, tl);
-  } else {
-    row_fwd_pair<T, LOGM>([&](int64_t row, int x) { return u[row * n + x]; }, W, n, nrows, KB, tw, pair,
-                          sm + line * LS, tl);
-  }
-}
-
-// Inverse rows.  CG = true: also per-block partial sums of p.y (p at the same
-// points) into partials[blockIdx.x]; the last block to finish sums them in
-// index order and sets st->pq, st->alpha (or flags a breakdown).  Returns at
-// once when st->done.
-template <typename T, int LOGM, int LINES, bool CG>
-__global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
-k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nrows, int KB,
-           const cplx_t<T>* __restrict__ tw, const T* __restrict__ p, CGState* st, double* partials) {
-  using C = cplx_t<T>;
-  constexpr int TPL = tpl(LOGM), LS = line_stride(LOGM);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (CG && st->done) return;
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
-  const int64_t pair = (int64_t)blockIdx.x * LINES + line;
-  T dot = T(0);
-  row_inv_pair<T, LOGM>(W, n, nrows, KB, tw, pair, sm + line * LS, tl, [&](int64_t row, int x, T v) {
-    y[row * n + x] = v;
-    if (CG) dot += v * p[row * n + x];
-  });
-  if constexpr (CG) {
-    double* red = reinterpret_cast<double*>(smem_raw);  // the FFT lines are no longer needed
-    const double total = block_sum_all(dot, red);
-    last_block_reduce(total, partials, &st->count_pq, red, [&](double pq) {
-      st->pq = pq;
-      if (!(pq > 0.0) || !isfinite(pq)) {
-        st->status = FRAC_EBREAKDOWN;
-        st->done = 1;
-      } else {
-        st->alpha = st->rr / pq;
-      }
-    });
-  }
-}
-
-// Columns: one tile of B adjacent columns per block (see col_tile).
-template <typename T, int LOGM, int MODE>
-__global__ void __launch_bounds__(blk<T>() * tpl(LOGM), minb_cols<T>(blk<T>() * tpl(LOGM)))
-k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw,
-       const CGState* st) {
-  using C = cplx_t<T>;
-  constexpr int B = blk<T>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (st && st->done) return;
-  const int cl = threadIdx.x % B, tl = threadIdx.x / B;
-  const int64_t o = blockIdx.x / A.tiles, tile = blockIdx.x % A.tiles;
-  col_tile<T, LOGM, MODE>(in, out, A, lam, tw, o, tile, reinterpret_cast<C*>(smem_raw), cl, tl);
-}
-
-// ---------------------------------------------------------------------------
-// Launch helpers
-// ---------------------------------------------------------------------------
-
-template <typename T, int LOGM>
-struct Cfg {
-  static constexpr int LINE_BYTES = line_stride(LOGM) * (int)sizeof(cplx_t<T>);
-  // lines per block for the row and 1D kernels: at most 48 KB of shared memory and 256 threads
-  static constexpr int lines_for(int maxbytes, int maxthreads) {
-    int l = maxbytes / LINE_BYTES;
-    int lim = maxthreads / tpl(LOGM);
-    l = l < lim ? l : lim;
-    return l < 1 ? 1 : l;
-  }
-  static constexpr int ROW_LINES = lines_for(48 * 1024, 256);
-};
-
-static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
-
-template <typename T>
-static const char* kname(char* buf, const char* what, int logm) {
-  std::snprintf(buf, 48, "%s_%s_M%d", what, sizeof(T) == 8 ? "f64" : "f32", 1 << logm);
-  return buf;
-}
-
-template <typename K>
-static int set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024)
-    FRAC_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  return FRAC_OK;
-}
-
-template <typename T, int LOGM>
-static int launch_conv1d(const T* u, T* y, int64_t n, int64_t batch, const T* lam, cudaStream_t st) {
-  constexpr int L = Cfg<T, LOGM>::ROW_LINES;
-  const size_t sm = (size_t)L * Cfg<T, LOGM>::LINE_BYTES;
-  auto kern = k_conv1d<T, LOGM, L>;
-  FRAC_TRY(set_smem(kern, sm));
-  const int64_t pairs = cdiv(batch, 2);
-  char nb[48];
-  prof::Scope ps(kname<T>(nb, "conv1d", LOGM), st);
-  kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>(u, y, (int)n, batch, lam, tw_table<T>(LOGM));
-  FRAC_CUDA_TRY(cudaGetLastError());
-  return FRAC_OK;
-}
-
-struct CgArgs {
-  const void* r = nullptr;   // rows_fwd: r of p = r + beta p
-  const void* p = nullptr;   // rows_inv: p of the p.q partials
-  CGState* st = nullptr;
-  double* partials = nullptr;
-};
-
-template <typename T, int LOGM, bool CG>
-static int launch_rows(bool fwd, const void* in, void* out, int64_t n, int64_t nrows, int KB, const CgArgs& cg,
-                       cudaStream_t st) {
-  using C = cplx_t<T>;
-  constexpr int L = Cfg<T, LOGM>::ROW_LINES;
-  const size_t sm = (size_t)L * Cfg<T, LOGM>::LINE_BYTES;
-  const int64_t pairs = cdiv(nrows, 2);
-  char nb[48];
-  prof::Scope ps(kname<T>(nb, fwd ? (CG ? "rows_fwd_cg" : "rows_fwd") : (CG ? "rows_inv_cg" : "rows_inv"), LOGM), st);
-  if (fwd) {
-    auto kern = k_rows_fwd<T, LOGM, L, CG>;
-    FRAC_TRY(set_smem(kern, sm));
-    kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const T*)in, (C*)out, (int)n, nrows, KB,
-                                                               tw_table<T>(LOGM), (const T*)cg.r, cg.st);
-  } else {
-    auto kern = k_rows_inv<T, LOGM, L, CG>;
-    FRAC_TRY(set_smem(kern, sm));
-    kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const C*)in, (T*)out, (int)n, nrows, KB,
-                                                               tw_table<T>(LOGM), (const T*)cg.p, cg.st, cg.partials);
-  }
-  FRAC_CUDA_TRY(cudaGetLastError());
-  return FRAC_OK;
-}
-
-template <typename T, int LOGM>
-static int64_t rows_grid(int64_t nrows) {
-  return cdiv(cdiv(nrows, 2), Cfg<T, LOGM>::ROW_LINES);
-}
-
-template <typename T, int LOGM, int MODE>
-static int launch_cols(const void* in, void* out, const ColArgs& A, int64_t nouter, const T* lam, const CGState* cgst,
-                       cudaStream_t st) {
-  using C = cplx_t<T>;
-  constexpr int B = blk<T>();
-  const size_t sm = (size_t)B * line_stride_tile(LOGM) * sizeof(C);
-  auto kern = k_cols<T, LOGM, MODE>;
-  FRAC_TRY(set_smem(kern, sm));
-  const int64_t blocks = nouter * A.tiles;
-  static const char* names[4] = {"cols_sym2", "cols_yfwd", "cols_zsym", "cols_yinv"};
-  char nb[48];
-  prof::Scope ps(kname<T>(nb, names[MODE], LOGM), st);
-  kern<<<(unsigned)blocks, B * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, lam, tw_table<T>(LOGM), cgst);
-  FRAC_CUDA_TRY(cudaGetLastError());
-  return FRAC_OK;
-}
-
-// Size dispatch (LOGM is a template parameter of every kernel).
-#define FRAC_DISPATCH_LOGM(logm, LO, HI, CALL)                                 \
-  switch (logm) {                                                             \
-    case 1: if constexpr (1 >= LO && 1 <= HI) { constexpr int LG = 1; return CALL; } break;   \
-    case 2: if constexpr (2 >= LO && 2 <= HI) { constexpr int LG = 2; return CALL; } break;   \
-    case 3: if constexpr (3 >= LO && 3 <= HI) { constexpr int LG = 3; return CALL; } break;   \
-    case 4: if constexpr (4 >= LO && 4 <= HI) { constexpr int LG = 4; return CALL; } break;   \
-    case 5: if constexpr (5 >= LO && 5 <= HI) { constexpr int LG = 5; return CALL; } break;   \
-    case 6: if constexpr (6 >= LO && 6 <= HI) { constexpr int LG = 6; return CALL; } break;   \
-    case 7: if constexpr (7 >= LO && 7 <= HI) { constexpr int LG = 7; return CALL; } break;   \
-    case 8: if constexpr (8 >= LO && 8 <= HI) { constexpr int LG = 8; return CALL; } break;   \
-    case 9: if constexpr (9 >= LO && 9 <= HI) { constexpr int LG = 9; return CALL; } break;   \
-    case 10: if constexpr (10 >= LO && 10 <= HI) { constexpr int LG = 10; return CALL; } break; \
-    case 11: if constexpr (11 >= LO && 11 <= HI) { constexpr int LG = 11; return CALL; } break; \
-    case 12: if constexpr (12 >= LO && 12 <= HI) { constexpr int LG = 12; return CALL; } break; \
-    case 13: if constexpr (13 >= LO && 13 <= HI) { constexpr int LG = 13; return CALL; } break; \
-    default: break;                                                           \
-  }                                                                           \
-  return FRAC_ENOTSUP;
-
-template <typename T>
-static int conv1d_any(int logm, const T* u, T* y, int64_t n, int64_t batch, const T* lam, cudaStream_t st) {
-  FRAC_DISPATCH_LOGM(logm, 1, 13, (launch_conv1d<T, LG>(u, y, n, batch, lam, st)));
-}
-template <typename T, bool CG = false>
-static int rows_any(int logm, bool fwd, const void* in, void* out, int64_t n, int64_t nrows, int KB, cudaStream_t st,
-                    const CgArgs& cg = CgArgs{}) {
-  FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_rows<T, LG, CG>(fwd, in, out, n, nrows, KB, cg, st)));
-}
-template <typename T>
-static int64_t rows_grid_any(int logm, int64_t nrows) {
-  switch (logm) {
-    case 1: return rows_grid<T, 1>(nrows);
-    case 2: return rows_grid<T, 2>(nrows);
-    case 3: return rows_grid<T, 3>(nrows);
-    case 4: return rows_grid<T, 4>(nrows);
-    case 5: return rows_grid<T, 5>(nrows);
-    case 6: return rows_grid<T, 6>(nrows);
-    case 7: return rows_grid<T, 7>(nrows);
-    case 8: return rows_grid<T, 8>(nrows);
-    case 9: return rows_grid<T, 9>(nrows);
-    case 10: return rows_grid<T, 10>(nrows);
-    case 11: return rows_grid<T, 11>(nrows);
-    default: return 0;
-  }
-}
-template <typename T, int MODE>
-static int cols_any(int logm, const void* in, void* out, const ColArgs& A, int64_t nouter, const T* lam,
-                    cudaStream_t st, const CGState* cgst = nullptr) {
-  if constexpr (MODE == SYM2) {
-    FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_cols<T, LG, MODE>(in, out, A, nouter, lam, cgst, st)));
-  } else {
-    FRAC_DISPATCH_LOGM(logm, 1, 9, (launch_cols<T, LG, MODE>(in, out, A, nouter, lam, cgst, st)));
-  }
-}
-
-template <typename T>
-static void layout(const frac_op* op, int64_t batch, int64_t& KB, int64_t& w1, int64_t& w2) {
-  constexpr int B = blk<T>();
-  const int64_t n = op->n, M = op->M, K = op->K;
-  KB = cdiv(K, B);
-  w1 = w2 = 0;
-  if (op->prob.d == 2) w1 = batch * KB * n * B;
-  if (op->prob.d == 3) {
-    w1 = batch * n * KB * n * B;
-    w2 = batch * M * KB * n * B;
-  }
-}
 
 size_t apply_workspace_bytes(const frac_op* op, int dtype, int64_t batch) {
   int64_t KB, w1, w2;
@@ -371,42 +16,10 @@ size_t apply_workspace_bytes(const frac_op* op, int dtype, int64_t batch) {
 
 template <typename T>
 int apply_t(const frac_op* op, const T* u, T* y, int64_t batch, void* ws, cudaStream_t st) {
-  using C = cplx_t<T>;
-  constexpr int B = blk<T>();
-  const int d = op->prob.d, logm = op->logm;
-  const int64_t n = op->n, M = op->M, K = op->K;
-  const T* lam = sym_table<T>(op);
   if (batch <= 0) return FRAC_OK;
-  if (d == 1) return conv1d_any<T>(logm, u, y, n, batch, lam, st);
-  int64_t KB, w1, w2;
-  layout<T>(op, batch, KB, w1, w2);
-  C* W1 = (C*)ws;
-  if (d == 2) {
-    const int64_t nrows = batch * n;
-    FRAC_TRY(rows_any<T>(logm, true, u, W1, n, nrows, (int)KB, st));
-    ColArgs A{(int)n, (int)K, (int)KB, KB, batch};
-    FRAC_TRY((cols_any<T, SYM2>(logm, W1, W1, A, batch, lam, st)));
-    FRAC_TRY(rows_any<T>(logm, false, W1, y, n, nrows, (int)KB, st));
-    return FRAC_OK;
-  }
-  C* W2 = W1 + w1;
-  const int64_t nrows = batch * n * n;
-  FRAC_TRY(rows_any<T>(logm, true, u, W1, n, nrows, (int)KB, st));
-  {
-    ColArgs A{(int)n, (int)K, (int)KB, KB, batch};
-    FRAC_TRY((cols_any<T, YFWD>(logm, W1, W2, A, batch * n, lam, st)));
-  }
-  {
-    ColArgs A{(int)n, (int)K, (int)KB, M * KB, batch};
-    FRAC_TRY((cols_any<T, ZSYM>(logm, W2, W2, A, batch, lam, st)));
-  }
-  {
-    ColArgs A{(int)n, (int)K, (int)KB, KB, batch};
-    FRAC_TRY((cols_any<T, YINV>(logm, W2, W1, A, batch * n, lam, st)));
-  }
-  FRAC_TRY(rows_any<T>(logm, false, W1, y, n, nrows, (int)KB, st));
-  (void)B;
-  return FRAC_OK;
+  if (op->prob.d == 1) return conv1d_any<T, false>(op->logm, u, y, op->n, batch, sym_table<T>(op), st);
+  return pipeline<T, RF_PLAIN, RI_PLAIN, false>(op, sym_table<T>(op), u, y, batch, ws, CgArgs{}, CgArgs{}, nullptr,
+                                                st);
 }
 
 template int apply_t<float>(const frac_op*, const float*, float*, int64_t, void*, cudaStream_t);
@@ -421,37 +34,14 @@ size_t apply_cg_partials(const frac_op* op) {
 
 template <typename T>
 int apply_cg_t(const frac_op* op, T* p, const T* r, T* q, void* ws, CGState* cgst, double* partials, cudaStream_t st) {
-  using C = cplx_t<T>;
-  const int d = op->prob.d, logm = op->logm;
-  const int64_t n = op->n, M = op->M, K = op->K;
-  const T* lam = sym_table<T>(op);
-  if (d < 2) return FRAC_ENOTSUP;
-  int64_t KB, w1, w2;
-  layout<T>(op, 1, KB, w1, w2);
-  C* W1 = (C*)ws;
+  if (op->prob.d < 2) return FRAC_ENOTSUP;
   CgArgs fwd, inv;
   fwd.r = r;
   fwd.st = cgst;
   inv.p = p;
   inv.st = cgst;
   inv.partials = partials;
-  if (d == 2) {
-    FRAC_TRY((rows_any<T, true>(logm, true, p, W1, n, n, (int)KB, st, fwd)));
-    ColArgs A{(int)n, (int)K, (int)KB, KB, 1};
-    FRAC_TRY((cols_any<T, SYM2>(logm, W1, W1, A, 1, lam, st, cgst)));
-    FRAC_TRY((rows_any<T, true>(logm, false, W1, q, n, n, (int)KB, st, inv)));
-    return FRAC_OK;
-  }
-  C* W2 = W1 + w1;
-  const int64_t nrows = n * n;
-  FRAC_TRY((rows_any<T, true>(logm, true, p, W1, n, nrows, (int)KB, st, fwd)));
-  ColArgs Ay{(int)n, (int)K, (int)KB, KB, 1};
-  FRAC_TRY((cols_any<T, YFWD>(logm, W1, W2, Ay, n, lam, st, cgst)));
-  ColArgs Az{(int)n, (int)K, (int)KB, M * KB, 1};
-  FRAC_TRY((cols_any<T, ZSYM>(logm, W2, W2, Az, 1, lam, st, cgst)));
-  FRAC_TRY((cols_any<T, YINV>(logm, W2, W1, Ay, n, lam, st, cgst)));
-  FRAC_TRY((rows_any<T, true>(logm, false, W1, q, n, nrows, (int)KB, st, inv)));
-  return FRAC_OK;
+  return pipeline<T, RF_CG, RI_CG, false>(op, sym_table<T>(op), p, q, 1, ws, fwd, inv, cgst, st);
 }
 
 template int apply_cg_t<float>(const frac_op*, float*, const float*, float*, void*, CGState*, double*, cudaStream_t);

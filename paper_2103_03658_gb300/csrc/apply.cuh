@@ -16,13 +16,16 @@ template <> inline const float* sym_table<float>(const frac_op* op) { return op-
 template <> inline const double* sym_table<double>(const frac_op* op) { return op->lam64; }
 
 // Device-resident conjugate-gradient state (solve.cu, fused apply kernels).
+// Plain CG keeps rz = rr; preconditioned CG (pcg = 1) sets rz = r.z and beta
+// in the preconditioner pass (z = P r) that follows each update.
 struct CGState {
   double rr;      // r.r
   double pq;      // p.Ap
   double alpha, beta;
   double tol2;    // stop when rr <= tol2
-  int it, maxit, done, status;
-  unsigned int count_pq, count_rr;  // arrival counters of the last-block reductions
+  double rz;      // r.z (= rr without preconditioner); alpha = rz / pq
+  int it, maxit, done, status, pcg;
+  unsigned int count_pq, count_rr, count_rz;  // arrival counters of the last-block reductions
 };
 
 // coeffs.cu
@@ -45,6 +48,17 @@ int apply_t(const frac_op* op, const T* u, T* y, int64_t batch, void* ws, cudaSt
 size_t apply_cg_partials(const frac_op* op);
 template <typename T>
 int apply_cg_t(const frac_op* op, T* p, const T* r, T* q, void* ws, CGState* st, double* partials, cudaStream_t s);
+
+// z = P r with the tau preconditioner (op->precond_ok required) for `batch`
+// vectors on device buffers; ws as for apply_t.
+template <typename T>
+int precond_t(const frac_op* op, const T* r, T* z, int64_t batch, void* ws, cudaStream_t st);
+// The preconditioner pass of preconditioned CG (d >= 2): z = P r together with
+// per-block partials of r.z; the last block sets st->beta = r.z / st->rz
+// (0 when st->rz is 0, the first pass) and st->rz = r.z.  Returns at once when
+// st->done.  partials as for apply_cg_t.
+template <typename T>
+int precond_cg_t(const frac_op* op, const T* r, T* z, void* ws, CGState* st, double* partials, cudaStream_t s);
 
 // solve.cu
 int solve_device(const frac_op* op, const double* f, double* u, const frac_solve_opts* opts,

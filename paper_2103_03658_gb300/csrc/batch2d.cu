@@ -47,7 +47,8 @@ struct B2Prob {
   double* u;
   const float* lam32;
   const double* lam64;
-  int n, logm, max_iter, use_x0;
+  const float* pinv32;  // tau preconditioner symbol (pcg)
+  int n, logm, max_iter, use_x0, pcg;
   double rtol, inner_tol;
 };
 
@@ -196,8 +197,42 @@ struct Solver {
     return gsum(c, part);
   }
 
-  // FP32 CG on A d = R64 / ||R64|| (||R64||^2 = rn2) to a relative reduction
-  // inner_tol, then U += ||R64|| d.  Returns the iteration count after it.
+  // Z = P R (tau preconditioner, FP32 passes on the odd extension; Z in the
+  // storage of Q, which is dead once R is updated); returns the group sum of
+  // R.Z.  The odd passes read entries that other threads of the CTA own; the
+  // block barriers of the group sums before and after order those accesses.
+  static __device__ __forceinline__ double precond(Ctx& c) {
+    const int n = c.P->n, tid = threadIdx.x, tl = tid % TPL, rr = rrounds(c);
+    const float* R = c.S->r;
+    float* Z = c.S->q;
+    float2* W = static_cast<float2*>(c.S->W);
+    float2* rb = reinterpret_cast<float2*>(c.smem) + (tid / TPL) * LS;
+    for (int i = 0; i < rr; ++i)
+      row_fwd_pair<float, LOGM, true>([&](int64_t row, int x) { return R[row * n + x]; }, W, n, n, KB32, c.tw32,
+                                      pair_of(c, i), rb, tl);
+    c.g.sync();
+    {
+      const ColArgs A{n, K, KB32, KB32, 1};
+      const int ts = tid / (4 * TPL), w = tid % (4 * TPL);
+      const int cr = (KB32 + c.g.G * TPR32 - 1) / (c.g.G * TPR32);
+      for (int i = 0; i < cr; ++i)
+        col_tile<float, LOGM, SYM2, true>(W, W, A, c.P->pinv32, c.tw32, 0,
+                                          ((int64_t)i * c.g.G + c.g.rank) * TPR32 + ts,
+                                          reinterpret_cast<float2*>(c.smem) + ts * 4 * LST, w % 4, w / 4);
+    }
+    c.g.sync();
+    float s = 0.0f;
+    for (int i = 0; i < rr; ++i)
+      row_inv_pair<float, LOGM, true>(W, n, n, KB32, c.tw32, pair_of(c, i), rb, tl, [&](int64_t row, int x, float v) {
+        Z[row * n + x] = v;
+        s += v * R[row * n + x];
+      });
+    return gsum(c, s);
+  }
+
+  // FP32 CG (preconditioned when pcg) on A d = R64 / ||R64|| (||R64||^2 = rn2)
+  // to a relative reduction inner_tol, then U += ||R64|| d.  Returns the
+  // iteration count after it.
   static __device__ __noinline__ int inner(Ctx& c, double rn2, int iters) {
     const int n = c.P->n, tid = threadIdx.x, tl = tid % TPL, rr = rrounds(c), max_iter = c.P->max_iter;
     const double* R64 = c.S->r64;
@@ -221,6 +256,9 @@ struct Solver {
     });
     double rrv = gsum(c, rf);
     const double stop = c.P->inner_tol * c.P->inner_tol * rrv;
+    const bool pcg = c.P->pcg;
+    const float* Zs = pcg ? Q : R;  // the vector the direction is built from
+    double rz = (pcg && rrv > stop) ? precond(c) : rrv;
     bool first = true;
     float be = 0.0f;
     while (rrv > stop && iters < max_iter) {
@@ -228,7 +266,7 @@ struct Solver {
         row_fwd_pair<float, LOGM>(
             [&](int64_t row, int x) {
               const int64_t k = row * n + x;
-              const float v = first ? R[k] : R[k] + be * Pv[k];
+              const float v = first ? Zs[k] : Zs[k] + be * Pv[k];
               Pv[k] = v;
               return v;
             },
@@ -247,7 +285,7 @@ struct Solver {
         });
       const double pq = gsum(c, pqf);
       if (!(pq > 0.0) || !isfinite(pq)) break;  // inner breakdown: refine from here
-      const float al = (float)(rrv / pq);
+      const float al = (float)(rz / pq);
       float rf1 = 0.0f;
       for_own(c, [&](int64_t k) {
         X[k] += al * Pv[k];
@@ -255,11 +293,13 @@ struct Solver {
         R[k] = rv;
         rf1 += rv * rv;
       });
-      const double rr1 = gsum(c, rf1);
-      be = (float)(rr1 / rrv);
-      rrv = rr1;
+      rrv = gsum(c, rf1);
       first = false;
       ++iters;
+      if (!(rrv > stop)) break;
+      const double rz1 = pcg ? precond(c) : rrv;
+      be = (float)(rz1 / rz);
+      rz = rz1;
     }
     const double s = sqrt(rn2);
     for_own(c, [&](int64_t k) { U[k] += s * (double)X[k]; });
@@ -287,7 +327,7 @@ struct Solver {
       frac_solve_info out;
       out.iters = iters;
       out.outer = outer;
-      out.reserved = 0;
+      out.precond = c.P->pcg;
       out.rel_resid = fn2 > 0.0 ? sqrt(rn2 / fn2) : (fn2 == 0.0 ? 0.0 : NAN);  // NaN: non-finite f
       if (status == FRAC_OK && !(out.rel_resid <= c.P->rtol)) status = FRAC_ENOCONV;
       if (!isfinite(out.rel_resid)) status = FRAC_EINVAL;
@@ -480,6 +520,8 @@ B2Prob make_prob(const frac_op* op, const double* f, double* u, const frac_solve
   p.u = u;
   p.lam32 = op->lam32;
   p.lam64 = op->lam64;
+  p.pinv32 = op->pinv32;
+  p.pcg = (o->precond == FRAC_PRECOND_TAU && op->precond_ok) ? 1 : 0;
   p.n = (int)op->n;
   p.logm = op->logm;
   p.max_iter = o->max_iter;
@@ -507,7 +549,7 @@ int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming
   FRAC_TRY(b.get(&di, sizeof(frac_solve_info)));
   FRAC_TRY(b.get(&next, 2 * sizeof(unsigned int)));
   FRAC_TRY(b.get(&scratch, slot_bytes(n, logm)));
-  frac_solve_opts o{0.0, kProbeIters, FRAC_MIXED_IR, 0, 1e-30};  // exactly kProbeIters CG iterations
+  frac_solve_opts o{0.0, kProbeIters, FRAC_MIXED_IR, 0, FRAC_PRECOND_TAU, 1e-30};  // exactly kProbeIters iterations
   B2Prob hp = make_prob(op, f, u, &o);
   B2Slot hs = carve(scratch, n, logm);
   FRAC_CUDA_TRY(cudaMemcpyAsync(dp, &hp, sizeof(hp), cudaMemcpyHostToDevice, st));
@@ -553,15 +595,19 @@ int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming
   return rc;
 }
 
-// Relative cost model of one problem: CG iterations ~ n^(alpha/2) (condition
-// number ~ n^alpha), per-iteration time of its class measured at n_probe,
-// half of it proportional to the number of rows.
-double est_iters(int n, double alpha) { return 20.0 + 6.0 * std::pow((double)n, 0.5 * alpha); }
+// Relative cost model of one problem: plain CG iterations ~ n^(alpha/2)
+// (condition number ~ n^alpha); with the tau preconditioner they hardly grow
+// (about 5-15 to 1e-10 in 2D); per-iteration time of its class measured at
+// n_probe, half of it proportional to the number of rows.
+double est_iters(int n, double alpha, bool pcg) {
+  return pcg ? 10.0 + std::log2((double)n) : 20.0 + 6.0 * std::pow((double)n, 0.5 * alpha);
+}
 
 struct Item {
   int64_t idx;  // problem index in the caller's arrays
   int logm, n;
   double alpha;
+  bool pcg;
 };
 
 // Makespan of the two queues on `ncl` clusters of C CTAs, classes with logm >= cut cluster-wide.
@@ -574,7 +620,7 @@ double simulate(const std::vector<Item>& items, const std::map<int, ClassTiming>
     const double scale = 0.5 + 0.5 * (double)it.n / t.n_probe;
     const bool wide = C > 1 && it.logm >= cut && t.t[si] > 0;
     const double per = wide ? t.t[si] : t.t[0];
-    (wide ? cl : lo).emplace_back(est_iters(it.n, it.alpha) * per * scale, &it);
+    (wide ? cl : lo).emplace_back(est_iters(it.n, it.alpha, it.pcg) * per * scale, &it);
   }
   auto desc = [](const std::pair<double, const Item*>& a, const std::pair<double, const Item*>& b) {
     return a.first > b.first;
@@ -622,7 +668,8 @@ int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const
   std::map<int, int64_t> rep;  // logm -> largest problem of that class
   for (int64_t t = 0; t < count; ++t) {
     const frac_op* op = ops[idx[t]];
-    items.push_back(Item{idx[t], op->logm, (int)op->n, op->prob.alpha});
+    items.push_back(Item{idx[t], op->logm, (int)op->n, op->prob.alpha,
+                         opts->precond == FRAC_PRECOND_TAU && op->precond_ok != 0});
     auto it = rep.find(op->logm);
     if (it == rep.end() || ops[it->second]->n < op->n) rep[op->logm] = idx[t];
   }

@@ -754,6 +754,47 @@ __global__ void k_scale_symbol(const double* __restrict__ raw, double* __restric
   }
 }
 
+// Symbol of the tau preconditioner: the sine transform of size M/2 - 1 per axis
+// diagonalises the tau matrix of the (zero-extended) Toeplitz operator with the
+// circulant-embedding eigenvalues mu at k in [1, M/2 - 1]^d as its eigenvalues, so
+// tau^{-1} is the same FFT pipeline on the odd extension with 1/mu.  The stored
+// symbol is scale * mu (scale = 1/M for d = 1, 1/(2 M^d) otherwise, the
+// normalisation of the FFT pipeline), so 1/mu in that normalisation is
+// 1 / (stored * s2) with s2 = M^2 (d = 1) or (2 M^d)^2.  Zero where some k_i is
+// 0 or M/2 (the odd extension has no spectrum there); per-block minimum of the
+// stored symbol over the other entries for the positivity check.
+__global__ void k_precond_symbol(const double* __restrict__ l64, double* __restrict__ p64, float* __restrict__ p32,
+                                 int64_t K, int d, double s2, int64_t count, double* __restrict__ partial_min) {
+  __shared__ double sh[32];
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double m = INFINITY;
+  if (idx < count) {
+    int64_t r = idx;
+    bool edge = false;
+    for (int i = 0; i < d; ++i) {
+      const int64_t k = r % K;
+      r /= K;
+      edge = edge || k == 0 || k == K - 1;
+    }
+    double v = 0.0;
+    if (!edge) {
+      const double mu = l64[idx];
+      m = mu;
+      v = mu > 0.0 ? 1.0 / (mu * s2) : 0.0;
+    }
+    p64[idx] = v;
+    p32[idx] = (float)v;
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : INFINITY;
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) partial_min[blockIdx.x] = v;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host driver
 // ---------------------------------------------------------------------------
@@ -849,6 +890,14 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   FRAC_CUDA_TRY(cudaGetLastError());
   std::vector<double> hmax(nb2);
   FRAC_CUDA_TRY(cudaMemcpyAsync(hmax.data(), pmax, nb2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double* pmin = nullptr;
+  FRAC_CUDA_TRY(cudaMallocAsync(&pmin, nb2 * sizeof(double), st));
+  const double s2 = d == 1 ? (double)M * (double)M : (2.0 * Md) * (2.0 * Md);
+  k_precond_symbol<<<(unsigned)nb2, TB, 0, st>>>(op->lam64, op->pinv64, op->pinv32, K, d, s2, ns, pmin);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  std::vector<double> hmin(nb2);
+  FRAC_CUDA_TRY(cudaMemcpyAsync(hmin.data(), pmin, nb2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FRAC_CUDA_TRY(cudaFreeAsync(pmin, st));
   FRAC_CUDA_TRY(cudaMemcpyAsync(&op->a0, op->a, sizeof(double), cudaMemcpyDeviceToHost, st));
   FRAC_CUDA_TRY(cudaFreeAsync(omega, st));
   FRAC_CUDA_TRY(cudaFreeAsync(partial, st));
@@ -870,6 +919,9 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   double m = 0.0;
   for (double v : hmax) m = v > m ? v : m;
   op->norm_bound = op->c * m;
+  double mn = INFINITY;
+  for (double v : hmin) mn = v < mn ? v : mn;
+  op->precond_ok = (n <= M / 2 - 1) && mn > 0.0 ? 1 : 0;
   return FRAC_OK;
 }
 

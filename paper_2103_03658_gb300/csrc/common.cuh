@@ -74,6 +74,9 @@ struct frac_op {
   double* a;         // device, (N+1)^d FP64 generator
   double* lam64;     // device, K^d FP64 scaled symbol
   float* lam32;      // device, K^d FP32 scaled symbol
+  double* pinv64;    // device, K^d FP64 symbol of the tau preconditioner (0 where k_i is 0 or M/2)
+  float* pinv32;     // device, K^d FP32 copy
+  int precond_ok;    // n <= M/2 - 1 and the symbol is positive: the tau preconditioner applies
   size_t device_bytes;
   int device;
 };

@@ -61,7 +61,7 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
 // (called once per such point).  buf: this group's line buffer
 // (line_stride(LOGM) entries); tl: thread index within the group of tpl(LOGM).
 // ---------------------------------------------------------------------------
-template <typename T, int LOGM, typename In>
+template <typename T, int LOGM, bool ODD = false, typename In>
 __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t nrows, int KB,
                                              const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
                                              int tl) {
@@ -71,14 +71,33 @@ __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t
   const int64_t r0 = 2 * pair, r1 = r0 + 1;
   const bool h0 = r0 < nrows, h1 = r1 < nrows;
   C v[E];
+  if constexpr (!ODD) {
 #pragma unroll
-  for (int e = 0; e < E / 2; ++e) {  // x < n <= M/2: e < E/2
-    const int x = tl + e * TPL;
-    const T re = (x < n && h0) ? in(r0, x) : T(0);
-    const T im = (x < n && h1) ? in(r1, x) : T(0);
-    v[e] = C{re, im};
+    for (int e = 0; e < E / 2; ++e) {  // x < n <= M/2: e < E/2
+      const int x = tl + e * TPL;
+      const T re = (x < n && h0) ? in(r0, x) : T(0);
+      const T im = (x < n && h1) ? in(r1, x) : T(0);
+      v[e] = C{re, im};
+    }
+    fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);  // upper half is zero padding
+  } else {
+    // odd extension (n <= M/2 - 1): entry j at x = j + 1, -entry j at x = M - 1 - j,
+    // zero at x = 0, M/2 and between; in() is called twice per point here
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int x = tl + e * TPL;
+      T re = T(0), im = T(0);
+      if (x >= 1 && x <= n) {
+        if (h0) re = in(r0, x - 1);
+        if (h1) im = in(r1, x - 1);
+      } else if (x >= M - n) {
+        if (h0) re = -in(r0, M - 1 - x);
+        if (h1) im = -in(r1, M - 1 - x);
+      }
+      v[e] = C{re, im};
+    }
+    fft_reg<C, LOGM, false, false, false>(v, buf, tl, tw);
   }
-  fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);  // upper half is zero padding
   // separation needs Z[k] and Z[M-k] for k in [0, M/2]: each thread keeps its
   // lower-half Z[k] in registers and reads the mirror from the upper half,
   // which alone goes through the line buffer
@@ -105,9 +124,9 @@ __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t
 // ---------------------------------------------------------------------------
 // Rows, inverse: two half spectra -> one complex line (Hermitian extension)
 // -> iFFT -> two real rows; out(row, x, value) receives the first n entries
-// of each row < nrows.
+// of each row < nrows (ODD: entries 1..n, as x = 0..n-1).
 // ---------------------------------------------------------------------------
-template <typename T, int LOGM, typename Out>
+template <typename T, int LOGM, bool ODD = false, typename Out>
 __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t nrows, int KB,
                                              const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
                                              int tl, Out out) {
@@ -146,13 +165,25 @@ __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t 
   __syncthreads();
 #pragma unroll
   for (int e = E / 2; e < E; ++e) v[e] = buf[pidx(tl + e * TPL)];
-  fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // only x < n <= M/2 is kept
+  if constexpr (!ODD) {
+    fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // only x < n <= M/2 is kept
 #pragma unroll
-  for (int e = 0; e < E / 2; ++e) {
-    const int x = tl + e * TPL;
-    if (x < n) {
-      if (h0) out(r0, x, v[e].x);
-      if (h1) out(r1, x, v[e].y);
+    for (int e = 0; e < E / 2; ++e) {
+      const int x = tl + e * TPL;
+      if (x < n) {
+        if (h0) out(r0, x, v[e].x);
+        if (h1) out(r1, x, v[e].y);
+      }
+    }
+  } else {
+    fft_reg<C, LOGM, true, false, false>(v, buf, tl, tw);  // odd extension: entries 1..n are kept
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int x = tl + e * TPL;
+      if (x >= 1 && x <= n) {
+        if (h0) out(r0, x - 1, v[e].x);
+        if (h1) out(r1, x - 1, v[e].y);
+      }
     }
   }
 }
@@ -167,7 +198,9 @@ __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t 
 //                 iFFT, keep n; in place.
 //   YINV (d = 3): slab o = (b, j3): M entries k2 of W2 columns k1, iFFT, first n (j2) to W1.
 // A tile whose column k1 >= K is empty.  sm: the tile's B line buffers of
-// line_stride_tile(LOGM) entries each.
+// line_stride_tile(LOGM) entries each.  ODD: the odd extension of the n
+// entries (the sine-transform embedding of the tau preconditioner) instead of
+// zero padding, and entries 1..n kept.
 // ---------------------------------------------------------------------------
 
 enum ColMode { SYM2 = 0, YFWD = 1, ZSYM = 2, YINV = 3 };
@@ -178,7 +211,7 @@ struct ColArgs {
   int64_t nb;        // batch (fields)
 };
 
-template <typename T, int LOGM, int MODE>
+template <typename T, int LOGM, int MODE, bool ODD = false>
 __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, const ColArgs& A,
                                          const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, int64_t o,
                                          int64_t tile, cplx_t<T>* sm, int cl, int tl) {
@@ -211,16 +244,30 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
       const int k2 = tl + e * TPL;
       v[e] = live ? src[(int64_t)k2 * KB * nB] : C{0, 0};
     }
-  } else {
+  } else if constexpr (!ODD) {
     const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl : in + (o * KB + tile) * nB + cl;
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {  // j < n <= M/2; the rest is zero padding
       const int j = tl + e * TPL;
       v[e] = (live && j < n) ? src[(int64_t)j * B] : C{0, 0};
     }
+  } else {  // odd extension: row j at j + 1, its negative at M - 1 - j
+    const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl : in + (o * KB + tile) * nB + cl;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = tl + e * TPL;
+      C w = C{0, 0};
+      if (live && j >= 1 && j <= n) {
+        w = src[(int64_t)(j - 1) * B];
+      } else if (live && j >= M - n) {
+        w = src[(int64_t)(M - 1 - j) * B];
+        w = C{-w.x, -w.y};
+      }
+      v[e] = w;
+    }
   }
   // ---- transforms
-  if (MODE != YINV) fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);
+  if (MODE != YINV) fft_reg<C, LOGM, false, !ODD, false>(v, buf, tl, tw);
   if (MODE == SYM2 || MODE == ZSYM) {
     const T* lrow = (MODE == SYM2) ? lam + k1 : lam + (int64_t)k2r * K + k1;
     const int64_t kstride = (MODE == SYM2) ? K : (int64_t)K * K;
@@ -231,7 +278,7 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
       v[e] = cscale(v[e], live ? lrow[kr * kstride] : T(0));
     }
   }
-  if (MODE != YFWD) fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // keeps j < n only
+  if (MODE != YFWD) fft_reg<C, LOGM, true, false, !ODD>(v, buf, tl, tw);  // keeps j < n (ODD: 1..n) only
   // ---- store
   if (!live) return;
   if (MODE == YFWD) {
@@ -245,10 +292,18 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
   } else {
     C* dst = (MODE == ZSYM) ? out + o * W2slab + tile * nB + cl
                             : out + (o * KB + tile) * nB + cl;  // SYM2 in place; YINV to W1 slab o
+    if constexpr (!ODD) {
 #pragma unroll
-    for (int e = 0; e < E / 2; ++e) {
-      const int j = tl + e * TPL;
-      if (j < n) dst[(int64_t)j * B] = v[e];
+      for (int e = 0; e < E / 2; ++e) {
+        const int j = tl + e * TPL;
+        if (j < n) dst[(int64_t)j * B] = v[e];
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int j = tl + e * TPL;
+        if (j >= 1 && j <= n) dst[(int64_t)(j - 1) * B] = v[e];
+      }
     }
   }
 }

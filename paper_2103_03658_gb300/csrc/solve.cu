@@ -63,90 +63,30 @@ __device__ double sum_partials(const double* __restrict__ partial, int np, doubl
   return block_sum(v, sh);
 }
 
-// pq = sum partials; alpha = rr / pq; breakdown check
-__global__ void k_cg_alpha(const double* __restrict__ partial, int np, CGState* st) {
-  __shared__ double sh[32];
-  if (st->done) return;
-  double pq = sum_partials(partial, np, sh);
-  if (threadIdx.x == 0) {
-    st->pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      st->status = FRAC_EBREAKDOWN;
-      st->done = 1;
-    } else {
-      st->alpha = st->rr / pq;
-    }
-  }
-}
-
-// x += alpha p; r -= alpha q; partial r.r
-template <typename T>
-__global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ q,
-                            int64_t n, double* __restrict__ partial, const CGState* st) {
-  __shared__ double sh[32];
-  if (st->done) return;
-  const T al = (T)st->alpha;
-  T acc = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += al * p[i];
-    T ri = r[i] - al * q[i];
-    r[i] = ri;
-    acc += ri * ri;
-  }
-  double s = block_sum((double)acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-// rr_new = sum partials; beta = rr_new / rr; convergence / iteration cap
-__global__ void k_cg_beta(const double* __restrict__ partial, int np, CGState* st) {
-  __shared__ double sh[32];
-  if (st->done) return;
-  double rr = sum_partials(partial, np, sh);
-  if (threadIdx.x == 0) {
-    st->beta = rr / st->rr;
-    st->rr = rr;
-    st->it += 1;
-    if (!isfinite(rr)) {
-      st->status = FRAC_EBREAKDOWN;
-      st->done = 1;
-    } else if (rr <= st->tol2) {
-      st->done = 1;
-    } else if (st->it >= st->maxit) {
-      st->status = FRAC_ENOCONV;
-      st->done = 1;
-    }
-  }
-}
-
-// p = r + beta p
-template <typename T>
-__global__ void k_cg_p(T* __restrict__ p, const T* __restrict__ r, int64_t n, const CGState* st) {
-  if (st->done) return;
-  const T be = (T)st->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = r[i] + be * p[i];
-}
-
-// start: rr = sum partials (of r.r), tol2 = tol^2 * rr_ref (rr_ref < 0: use rr)
+// start: rr = sum partials (of r.r), tol2 = tol^2 * rr_ref (rr_ref < 0: use rr);
+// pcg: preconditioned (rz and beta come from the preconditioner pass that
+// follows), else rz = rr
 __global__ void k_cg_start(const double* __restrict__ partial, int np, CGState* st, double tol, double rr_ref,
-                           int maxit) {
+                           int maxit, int pcg) {
   __shared__ double sh[32];
   double rr = sum_partials(partial, np, sh);
   if (threadIdx.x == 0) {
     st->rr = rr;
+    st->rz = pcg ? 0.0 : rr;
+    st->pcg = pcg;
     st->tol2 = tol * tol * (rr_ref < 0.0 ? rr : rr_ref);
     st->it = 0;
     st->maxit = maxit;
     st->status = FRAC_OK;
     st->done = (rr <= st->tol2 || rr == 0.0) ? 1 : 0;
     st->alpha = st->beta = st->pq = 0.0;
-    st->count_pq = st->count_rr = 0;
+    st->count_pq = st->count_rr = st->count_rz = 0;
   }
 }
 
 // Fused update (d >= 2): x += alpha p, r -= alpha q, per-block r.r partials;
-// the last block sums them in index order and sets rr, beta, the iteration
-// count and the stop flag.
+// the last block sums them in index order and sets rr, the iteration count,
+// the stop flag and (plain CG) beta and rz = rr.
 template <typename T>
 __global__ void k_cg_update_fused(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                   const T* __restrict__ q, int64_t n, double* __restrict__ partial, CGState* st) {
@@ -176,7 +116,10 @@ __global__ void k_cg_update_fused(T* __restrict__ x, T* __restrict__ r, const T*
   const double rr = block_sum(sacc, red);
   if (threadIdx.x == 0) {
     st->count_rr = 0;
-    st->beta = rr / st->rr;
+    if (!st->pcg) {
+      st->beta = rr / st->rr;
+      st->rz = rr;
+    }
     st->rr = rr;
     st->it += 1;
     if (!isfinite(rr)) {
@@ -284,15 +227,35 @@ static cudaStream_t graph_stream() {
 // CG iterations on A_T x = b for d >= 2, fused kernels, replayed as a CUDA graph
 // of kChunk iterations (captured on first use, kept in *exec for later calls with
 // the same buffers).  On entry r = b - A x, p holds any finite values and the
-// state was set by k_cg_start (beta = 0).  Runs until the device state is done.
+// state was set by k_cg_start (beta = 0) and, preconditioned (z != nullptr), by
+// cg_precond_start.  Runs until the device state is done.
 constexpr int kChunk = 16;
 
+// One (P)CG iteration: q = A p with p = (z or r) + beta p fused in, the x/r
+// update, and (z != nullptr) the preconditioner pass z = P r that sets beta.
 template <typename T>
-static int cg_run_fused(const frac_op* op, T* x, T* r, T* p, T* q, void* apply_ws, CGState* dst, CGState* hst,
+static int cg_iteration(const frac_op* op, T* x, T* r, T* p, T* q, T* z, void* apply_ws, CGState* dst,
+                        double* part_inv, double* part_upd, cudaStream_t s) {
+  const int64_t nd = op->nd;
+  FRAC_TRY(apply_cg_t<T>(op, p, z ? z : r, q, apply_ws, dst, part_inv, s));
+  k_cg_update_fused<T><<<red_blocks(nd), kTB, 0, s>>>(x, r, p, q, nd, part_upd, dst);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  if (z) FRAC_TRY(precond_cg_t<T>(op, r, z, apply_ws, dst, part_inv, s));
+  return FRAC_OK;
+}
+
+// After k_cg_start(pcg = 1): p = 0 and the first z = P r (rz, beta = 0).
+template <typename T>
+static int cg_precond_start(const frac_op* op, T* r, T* p, T* z, void* apply_ws, CGState* dst, double* part_inv,
+                            cudaStream_t s) {
+  FRAC_CUDA_TRY(cudaMemsetAsync(p, 0, op->nd * sizeof(T), s));
+  return precond_cg_t<T>(op, r, z, apply_ws, dst, part_inv, s);
+}
+
+template <typename T>
+static int cg_run_fused(const frac_op* op, T* x, T* r, T* p, T* q, T* z, void* apply_ws, CGState* dst, CGState* hst,
                         double* part_inv, double* part_upd, cudaGraphExec_t* exec, int* iters_total,
                         cudaStream_t caller) {
-  const int64_t nd = op->nd;
-  const int nb = red_blocks(nd);
   cudaStream_t gs = graph_stream();
   if (!gs) return FRAC_ECUDA;
   cudaEvent_t ev;
@@ -305,19 +268,12 @@ static int cg_run_fused(const frac_op* op, T* x, T* r, T* p, T* q, void* apply_w
   FRAC_CUDA_TRY(cudaStreamWaitEvent(gs, ev, 0));
   if (!*exec) {
     // one plain iteration first: sets kernel attributes outside the capture
-    FRAC_TRY(apply_cg_t<T>(op, p, r, q, apply_ws, dst, part_inv, gs));
-    k_cg_update_fused<T><<<nb, kTB, 0, gs>>>(x, r, p, q, nd, part_upd, dst);
-    FRAC_CUDA_TRY(cudaGetLastError());
+    FRAC_TRY(cg_iteration<T>(op, x, r, p, q, z, apply_ws, dst, part_inv, part_upd, gs));
     cudaGraph_t g;
     FRAC_CUDA_TRY(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
     int s = FRAC_OK;
-    for (int c = 0; c < kChunk && s == FRAC_OK; ++c) {
-      s = apply_cg_t<T>(op, p, r, q, apply_ws, dst, part_inv, gs);
-      if (s == FRAC_OK) {
-        k_cg_update_fused<T><<<nb, kTB, 0, gs>>>(x, r, p, q, nd, part_upd, dst);
-        if (cudaGetLastError() != cudaSuccess) s = FRAC_ECUDA;
-      }
-    }
+    for (int c = 0; c < kChunk && s == FRAC_OK; ++c) s = cg_iteration<T>(op, x, r, p, q, z, apply_ws, dst, part_inv,
+                                                                         part_upd, gs);
     cudaError_t e = cudaStreamEndCapture(gs, &g);
     if (s != FRAC_OK) return s;
     FRAC_CUDA_TRY(e);
@@ -345,8 +301,7 @@ static int solve_1d(const frac_op* op, const double* f, double* u, const frac_so
   frac_solve_info* di;
   FRAC_TRY(ws.get(&dt, sizeof(Solve1dTask)));
   FRAC_TRY(ws.get(&di, sizeof(frac_solve_info)));
-  Solve1dTask t{f, u, op->lam32, op->lam64, di, opts->rtol, opts->inner_tol > 0.0 ? opts->inner_tol : 1e-4,
-                (int)op->n, opts->max_iter, opts->use_x0 ? 1 : 0};
+  Solve1dTask t = make_task1d(op, f, u, di, opts);
   FRAC_CUDA_TRY(cudaMemcpyAsync(dt, &t, sizeof(t), cudaMemcpyHostToDevice, st));
   FRAC_TRY(solve1d_launch(op->logm, opts->precision == FRAC_MIXED_IR, dt, 1, st));
   FRAC_CUDA_TRY(cudaMemcpyAsync(info, di, sizeof(frac_solve_info), cudaMemcpyDeviceToHost, st));
@@ -400,9 +355,7 @@ int solve_batch_1d(int64_t count, const frac_op* const* ops, const double* const
     launches.emplace_back(lg, (int64_t)tasks.size());
     for (int64_t i : groups[lg]) {
       const frac_op* op = ops[i];
-      tasks.push_back(Solve1dTask{f[i], u[i], op->lam32, op->lam64, pend->dinfo + tasks.size(), opts->rtol,
-                                  opts->inner_tol > 0.0 ? opts->inner_tol : 1e-4, (int)op->n, opts->max_iter,
-                                  opts->use_x0 ? 1 : 0});
+      tasks.push_back(make_task1d(op, f[i], u[i], pend->dinfo + tasks.size(), opts));
       pend->order.push_back(i);
     }
   }
@@ -477,19 +430,23 @@ int solve_device(const frac_op* op, const double* f, double* u, const frac_solve
   }
   const double rtol = opts->rtol;
   int iters = 0;
+  const bool pcg = opts->precond == FRAC_PRECOND_TAU && op->precond_ok;
+  info->precond = pcg ? 1 : 0;
 
   if (opts->precision == FRAC_PLAIN_F64) {
-    double *p, *q;
+    double *p, *q, *z = nullptr;
     FRAC_TRY(ws.get(&p, nd * sizeof(double)));
     FRAC_TRY(ws.get(&q, nd * sizeof(double)));
+    if (pcg) FRAC_TRY(ws.get(&z, nd * sizeof(double)));
     int restarts = 0;
     while (rnorm > rtol * fnorm && iters < opts->max_iter && restarts < 8) {
       // CG on the current residual; the recursive residual is checked against rtol ||f||
       k_copy2<double><<<gb, kTB, 0, st>>>(r64, p, q, nd);  // p = r (q overwritten by the apply)
       k_dot<double><<<gb, kTB, 0, st>>>(r64, r64, nd, partial, nullptr);
       k_cg_start<<<1, kTB, 0, st>>>(partial, nb, dst, rtol * fnorm / std::max(rnorm, 1e-300), -1.0,
-                                    opts->max_iter - iters);
-      FRAC_TRY(cg_run_fused<double>(op, u, r64, p, q, ws64, dst, hst, part_inv, partial, &exec, &iters, st));
+                                    opts->max_iter - iters, pcg ? 1 : 0);
+      if (pcg) FRAC_TRY(cg_precond_start<double>(op, r64, p, z, ws64, dst, part_inv, st));
+      FRAC_TRY(cg_run_fused<double>(op, u, r64, p, q, z, ws64, dst, hst, part_inv, partial, &exec, &iters, st));
       if (hst->status == FRAC_EBREAKDOWN) {
         info->status = FRAC_EBREAKDOWN;
         break;
@@ -504,12 +461,13 @@ int solve_device(const frac_op* op, const double* f, double* u, const frac_solve
       ++restarts;
     }
   } else {
-    float *x32, *r32, *p32, *q32;
+    float *x32, *r32, *p32, *q32, *z32 = nullptr;
     void* ws32;
     FRAC_TRY(ws.get(&x32, nd * sizeof(float)));
     FRAC_TRY(ws.get(&r32, nd * sizeof(float)));
     FRAC_TRY(ws.get(&p32, nd * sizeof(float)));
     FRAC_TRY(ws.get(&q32, nd * sizeof(float)));
+    if (pcg) FRAC_TRY(ws.get(&z32, nd * sizeof(float)));
     FRAC_TRY(ws.get(&ws32, apply_workspace_bytes(op, FRAC_F32, 1)));
     const double inner = opts->inner_tol > 0.0 ? opts->inner_tol : 1e-4;
     int outer = 0;
@@ -517,8 +475,10 @@ int solve_device(const frac_op* op, const double* f, double* u, const frac_solve
       // inner FP32 CG on A d = r / ||r||
       k_ir_scale_down<<<gb, kTB, 0, st>>>(r64, scal + 1, r32, p32, x32, nd);
       k_dot<float><<<gb, kTB, 0, st>>>(r32, r32, nd, partial, nullptr);
-      k_cg_start<<<1, kTB, 0, st>>>(partial, nb, dst, inner, -1.0, opts->max_iter - iters);
-      FRAC_TRY(cg_run_fused<float>(op, x32, r32, p32, q32, ws32, dst, hst, part_inv, partial, &exec, &iters, st));
+      k_cg_start<<<1, kTB, 0, st>>>(partial, nb, dst, inner, -1.0, opts->max_iter - iters, pcg ? 1 : 0);
+      if (pcg) FRAC_TRY(cg_precond_start<float>(op, r32, p32, z32, ws32, dst, part_inv, st));
+      FRAC_TRY(cg_run_fused<float>(op, x32, r32, p32, q32, z32, ws32, dst, hst, part_inv, partial, &exec, &iters,
+                                   st));
       k_ir_correct<<<gb, kTB, 0, st>>>(u, x32, scal + 1, nd);
       // true FP64 residual
       FRAC_TRY(apply_t<double>(op, u, Au64, 1, ws64, st));
@@ -578,8 +538,9 @@ struct Job {
   // device buffers (d >= 2)
   double *r64 = nullptr, *Au64 = nullptr, *partial = nullptr, *part_inv = nullptr, *scal = nullptr;
   CGState* st = nullptr;
-  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr;
-  double *p64 = nullptr, *q64 = nullptr;
+  float *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *z32 = nullptr;
+  double *p64 = nullptr, *q64 = nullptr, *z64 = nullptr;
+  bool pcg = false;
   void *ws32 = nullptr, *ws64 = nullptr;
   frac_solve_info* dinfo = nullptr;
   Solve1dTask* dtask = nullptr;
@@ -644,23 +605,14 @@ Mirror* get_mirror(frac_engine* e) {
 
 // Launch the next chunk of the current inner/plain CG and the state read-back.
 template <typename T>
-int launch_chunk(Job* j, T* x, T* r, T* p, T* q, void* ws) {
-  const int64_t nd = j->op->nd;
-  const int nb = red_blocks(nd);
+int launch_chunk(Job* j, T* x, T* r, T* p, T* q, T* z, void* ws) {
   if (!j->exec) {
-    FRAC_TRY(apply_cg_t<T>(j->op, p, r, q, ws, j->st, j->part_inv, j->s));
-    k_cg_update_fused<T><<<nb, kTB, 0, j->s>>>(x, r, p, q, nd, j->partial, j->st);
-    FRAC_CUDA_TRY(cudaGetLastError());
+    FRAC_TRY(cg_iteration<T>(j->op, x, r, p, q, z, ws, j->st, j->part_inv, j->partial, j->s));
     cudaGraph_t g;
     FRAC_CUDA_TRY(cudaStreamBeginCapture(j->s, cudaStreamCaptureModeThreadLocal));
     int s = FRAC_OK;
-    for (int c = 0; c < kChunk && s == FRAC_OK; ++c) {
-      s = apply_cg_t<T>(j->op, p, r, q, ws, j->st, j->part_inv, j->s);
-      if (s == FRAC_OK) {
-        k_cg_update_fused<T><<<nb, kTB, 0, j->s>>>(x, r, p, q, nd, j->partial, j->st);
-        if (cudaGetLastError() != cudaSuccess) s = FRAC_ECUDA;
-      }
-    }
+    for (int c = 0; c < kChunk && s == FRAC_OK; ++c)
+      s = cg_iteration<T>(j->op, x, r, p, q, z, ws, j->st, j->part_inv, j->partial, j->s);
     cudaError_t e = cudaStreamEndCapture(j->s, &g);
     if (s != FRAC_OK) return s;
     FRAC_CUDA_TRY(e);
@@ -687,18 +639,20 @@ int start_cg(Job* j) {
     const double inner = j->opts.inner_tol > 0.0 ? j->opts.inner_tol : 1e-4;
     k_ir_scale_down<<<gb, kTB, 0, j->s>>>(j->r64, j->scal + 1, j->r32, j->p32, j->x32, nd);
     k_dot<float><<<gb, kTB, 0, j->s>>>(j->r32, j->r32, nd, j->partial, nullptr);
-    k_cg_start<<<1, kTB, 0, j->s>>>(j->partial, nb, j->st, inner, -1.0, left);
+    k_cg_start<<<1, kTB, 0, j->s>>>(j->partial, nb, j->st, inner, -1.0, left, j->pcg ? 1 : 0);
     FRAC_CUDA_TRY(cudaGetLastError());
+    if (j->pcg) FRAC_TRY(cg_precond_start<float>(j->op, j->r32, j->p32, j->z32, j->ws32, j->st, j->part_inv, j->s));
     j->phase = PH_INNER;
-    return launch_chunk<float>(j, j->x32, j->r32, j->p32, j->q32, j->ws32);
+    return launch_chunk<float>(j, j->x32, j->r32, j->p32, j->q32, j->z32, j->ws32);
   }
   k_copy2<double><<<gb, kTB, 0, j->s>>>(j->r64, j->p64, j->q64, nd);
   k_dot<double><<<gb, kTB, 0, j->s>>>(j->r64, j->r64, nd, j->partial, nullptr);
   k_cg_start<<<1, kTB, 0, j->s>>>(j->partial, nb, j->st, j->opts.rtol * j->fnorm / std::max(j->rnorm, 1e-300), -1.0,
-                                  left);
+                                  left, j->pcg ? 1 : 0);
   FRAC_CUDA_TRY(cudaGetLastError());
+  if (j->pcg) FRAC_TRY(cg_precond_start<double>(j->op, j->r64, j->p64, j->z64, j->ws64, j->st, j->part_inv, j->s));
   j->phase = PH_INNER;
-  return launch_chunk<double>(j, j->u, j->r64, j->p64, j->q64, j->ws64);
+  return launch_chunk<double>(j, j->u, j->r64, j->p64, j->q64, j->z64, j->ws64);
 }
 
 // r64 = f - A64 u, ||r64||^2 -> scal[1] -> host; phase REFINE
@@ -719,7 +673,7 @@ int finish(Job* j) {
   frac_solve_info& r = j->result;
   r.iters = j->iters;
   r.outer = j->outer;
-  r.reserved = 0;
+  r.precond = j->pcg ? 1 : 0;
   if (j->op->prob.d == 1) {
     r = j->hm->info;
     if (r.status == FRAC_EINVAL || std::isnan(r.rel_resid)) r.status = FRAC_EINVAL;
@@ -794,8 +748,9 @@ int advance(Job* j) {
 namespace frac {
 namespace {
 int launch_chunk_resume(Job* j) {
-  if (j->opts.precision == FRAC_MIXED_IR) return launch_chunk<float>(j, j->x32, j->r32, j->p32, j->q32, j->ws32);
-  return launch_chunk<double>(j, j->u, j->r64, j->p64, j->q64, j->ws64);
+  if (j->opts.precision == FRAC_MIXED_IR)
+    return launch_chunk<float>(j, j->x32, j->r32, j->p32, j->q32, j->z32, j->ws32);
+  return launch_chunk<double>(j, j->u, j->r64, j->p64, j->q64, j->z64, j->ws64);
 }
 }  // namespace
 }  // namespace frac
@@ -858,9 +813,7 @@ static int submit_impl(frac_engine* e, Job* j, const double* f, double* u) {
   if (op->prob.d == 1) {
     FRAC_TRY(jalloc(j, &j->dinfo, sizeof(frac_solve_info)));
     FRAC_TRY(jalloc(j, &j->dtask, sizeof(Solve1dTask)));
-    j->hm->task = Solve1dTask{j->f, j->u, op->lam32, op->lam64, j->dinfo, j->opts.rtol,
-                              j->opts.inner_tol > 0.0 ? j->opts.inner_tol : 1e-4, (int)op->n, j->opts.max_iter,
-                              j->opts.use_x0 ? 1 : 0};
+    j->hm->task = make_task1d(op, j->f, j->u, j->dinfo, &j->opts);
     FRAC_CUDA_TRY(cudaMemcpyAsync(j->dtask, &j->hm->task, sizeof(Solve1dTask), cudaMemcpyHostToDevice, j->s));
     FRAC_TRY(solve1d_launch(op->logm, j->opts.precision == FRAC_MIXED_IR, j->dtask, 1, j->s));
     FRAC_CUDA_TRY(cudaMemcpyAsync(&j->hm->info, j->dinfo, sizeof(frac_solve_info), cudaMemcpyDeviceToHost, j->s));
@@ -876,15 +829,18 @@ static int submit_impl(frac_engine* e, Job* j, const double* f, double* u) {
   FRAC_TRY(jalloc(j, &j->scal, 4 * sizeof(double)));
   FRAC_TRY(jalloc(j, &j->st, sizeof(CGState)));
   FRAC_TRY(jalloc(j, &j->ws64, apply_workspace_bytes(op, FRAC_F64, 1)));
+  j->pcg = j->opts.precond == FRAC_PRECOND_TAU && op->precond_ok;
   if (j->opts.precision == FRAC_MIXED_IR) {
     FRAC_TRY(jalloc(j, &j->x32, nd * sizeof(float)));
     FRAC_TRY(jalloc(j, &j->r32, nd * sizeof(float)));
     FRAC_TRY(jalloc(j, &j->p32, nd * sizeof(float)));
     FRAC_TRY(jalloc(j, &j->q32, nd * sizeof(float)));
+    if (j->pcg) FRAC_TRY(jalloc(j, &j->z32, nd * sizeof(float)));
     FRAC_TRY(jalloc(j, &j->ws32, apply_workspace_bytes(op, FRAC_F32, 1)));
   } else {
     FRAC_TRY(jalloc(j, &j->p64, nd * sizeof(double)));
     FRAC_TRY(jalloc(j, &j->q64, nd * sizeof(double)));
+    if (j->pcg) FRAC_TRY(jalloc(j, &j->z64, nd * sizeof(double)));
   }
   k_dot<double><<<(unsigned)nb, kTB, 0, j->s>>>(j->f, j->f, nd, j->partial, nullptr);
   k_sum_to<<<1, kTB, 0, j->s>>>(j->partial, nb, j->scal + 0);

@@ -64,6 +64,40 @@ __device__ __forceinline__ void conv_line(cplx_t<T>* buf, int n, const T* __rest
   run<C, LOGM, true>(buf, tl, tw);
 }
 
+// z = P r with the tau preconditioner on the line `buf`: the odd extension of
+// the vector (entry x at x + 1, its negative at M - 1 - x), FFT, * pinv, iFFT;
+// z at entry x is left in buf[pidx(x + 1)].x.
+template <typename T, int LOGM, typename Load>
+__device__ __forceinline__ void precond_line(cplx_t<T>* buf, int n, const T* __restrict__ pinv,
+                                             const cplx_t<T>* __restrict__ tw, Load load) {
+  using C = cplx_t<T>;
+  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM);
+  const int tl = threadIdx.x;
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) buf[pidx(tl + e * TPL)] = C{T(0), T(0)};
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int x = tl + e * TPL;
+    if (x < n) {  // n <= M/2 - 1: the two images never meet
+      const T v = load(e, x);
+      buf[pidx(x + 1)] = C{v, T(0)};
+      buf[pidx(M - 1 - x)] = C{-v, T(0)};
+    }
+  }
+  __syncthreads();
+  run<C, LOGM, false>(buf, tl, tw);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = tl + e * TPL;
+    const int kr = k <= M / 2 ? k : M - k;
+    buf[pidx(k)] = cscale(buf[pidx(k)], pinv[kr]);
+  }
+  __syncthreads();
+  run<C, LOGM, true>(buf, tl, tw);
+}
+
 }  // namespace
 
 template <int LOGM, bool MIXED>
@@ -116,12 +150,28 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
   if (fn2 == 0.0) {
     rn2 = 0.0;
   } else if constexpr (!MIXED) {
-    // plain FP64 CG, restarted from the true residual if the recursive one drifts
+    // FP64 CG (preconditioned when T.pcg), restarted from the true residual if
+    // the recursive one drifts
     double r[E], p[E];
     rn2 = residual(r);
-    for (int restart = 0; restart < 8 && rn2 > tol2 && iters < T.max_iter; ++restart) {
+    // rz = r.z with z = P r (pcg) or z = r; the new direction p = z + beta p
+    auto precond_rz = [&]() -> double {
+      precond_line<double, LOGM>(buf64, n, T.pinv64, tw64, [&](int e, int) { return r[e]; });
+      double s = 0.0;
 #pragma unroll
-      for (int e = 0; e < E; ++e) p[e] = r[e];
+      for (int e = 0; e < E; ++e) {
+        const int x = tl + e * TPL;
+        if (x < n) s += r[e] * buf64[pidx(x + 1)].x;
+      }
+      return block_allsum<TPL>(s, red);
+    };
+    for (int restart = 0; restart < 8 && rn2 > tol2 && iters < T.max_iter; ++restart) {
+      double rz = T.pcg ? precond_rz() : rn2;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int x = tl + e * TPL;
+        p[e] = T.pcg ? (x < n ? buf64[pidx(x + 1)].x : 0.0) : r[e];
+      }
       double rr = rn2;
       while (rr > tol2 && iters < T.max_iter) {
         conv_line<double, LOGM>(buf64, n, T.lam64, tw64, [&](int e, int) { return p[e]; });
@@ -133,7 +183,7 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
           status = FRAC_EBREAKDOWN;
           break;
         }
-        const double al = rr / pq;
+        const double al = rz / pq;
         double rr1 = 0.0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -145,11 +195,18 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
           rr1 += r[e] * r[e];
         }
         rr1 = block_allsum<TPL>(rr1, red);
-        const double be = rr1 / rr;
         rr = rr1;
-#pragma unroll
-        for (int e = 0; e < E; ++e) p[e] = r[e] + be * p[e];
         ++iters;
+        if (!(rr > tol2)) break;
+        const double rz1 = T.pcg ? precond_rz() : rr1;
+        const double be = rz1 / rz;
+        rz = rz1;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int x = tl + e * TPL;
+          const double z = T.pcg ? (x < n ? buf64[pidx(x + 1)].x : 0.0) : r[e];
+          p[e] = z + be * p[e];
+        }
       }
       if (status != FRAC_OK) break;
       rn2 = residual(r);
@@ -169,15 +226,30 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
     };
     rn2 = refresh();
     double prev = INFINITY;
+    auto precond_rz = [&]() -> double {
+      precond_line<float, LOGM>(buf32, n, T.pinv32, tw32, [&](int e, int) { return r[e]; });
+      float s = 0.0f;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int xx = tl + e * TPL;
+        if (xx < n) s += r[e] * buf32[pidx(xx + 1)].x;
+      }
+      return block_allsum<TPL>((double)s, red);
+    };
     while (rn2 > tol2 && iters < T.max_iter && outer < 100) {
       double rr = 0.0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        p[e] = r[e];
         x[e] = 0.0f;
         rr += (double)r[e] * r[e];
       }
       rr = block_allsum<TPL>(rr, red);
+      double rz = T.pcg ? precond_rz() : rr;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int xx = tl + e * TPL;
+        p[e] = T.pcg ? (xx < n ? buf32[pidx(xx + 1)].x : 0.0f) : r[e];
+      }
       const double stop = inner2 * rr;
       while (rr > stop && iters < T.max_iter) {
         conv_line<float, LOGM>(buf32, n, T.lam32, tw32, [&](int e, int) { return p[e]; });
@@ -186,7 +258,7 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
         for (int e = 0; e < E; ++e) pqf += p[e] * buf32[pidx(tl + e * TPL)].x;
         const double pq = block_allsum<TPL>((double)pqf, red);
         if (!(pq > 0.0) || !isfinite(pq)) break;  // inner breakdown: refine from here
-        const float al = (float)(rr / pq);
+        const float al = (float)(rz / pq);
         float rr1f = 0.0f;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -197,11 +269,18 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
           rr1f += r[e] * r[e];
         }
         const double rr1 = block_allsum<TPL>((double)rr1f, red);
-        const float be = (float)(rr1 / rr);
         rr = rr1;
-#pragma unroll
-        for (int e = 0; e < E; ++e) p[e] = r[e] + be * p[e];
         ++iters;
+        if (!(rr > stop)) break;
+        const double rz1 = T.pcg ? precond_rz() : rr1;
+        const float be = (float)(rz1 / rz);
+        rz = rz1;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int xx = tl + e * TPL;
+          const float z = T.pcg ? (xx < n ? buf32[pidx(xx + 1)].x : 0.0f) : r[e];
+          p[e] = z + be * p[e];
+        }
       }
       const double sc = sqrt(rn2);
 #pragma unroll
@@ -219,7 +298,7 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
     frac_solve_info out;
     out.iters = iters;
     out.outer = outer;
-    out.reserved = 0;
+    out.precond = T.pcg;
     out.rel_resid = fn2 > 0.0 ? sqrt(rn2 / fn2) : (fn2 == 0.0 ? 0.0 : NAN);  // NaN: non-finite f
     if (status == FRAC_OK && !(out.rel_resid <= T.rtol)) status = FRAC_ENOCONV;
     if (!isfinite(out.rel_resid)) status = FRAC_EINVAL;

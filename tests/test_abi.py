@@ -49,7 +49,7 @@ def test_null_arguments(lib):
     assert lib.frac_apply(None, None, None, 0, 1, None) == 1
     assert lib.frac_op_info(None, None) == 1
     lib.frac_op_free(None)
-    opts = nat.SolveOpts(1e-10, 10, 0, 0, 1e-4)
+    opts = nat.SolveOpts(1e-10, 10, 0, 0, 0, 1e-4)
     info = nat.SolveInfo()
     assert lib.frac_solve(None, None, None, None, ctypes.byref(opts), ctypes.byref(info), None) == 1
     assert lib.frac_solve_batch(-1, None, None, None, None, None, None) == 1
