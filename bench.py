@@ -44,7 +44,9 @@ def workload_fields() -> np.ndarray:
 
 
 def config(parallelism: str) -> dict:
-    return {"workload": WORKLOAD, "grid": [NSIDE, NSIDE], "fft": [2048, 2048], "fields": NFIELDS,
+    wl = WORKLOAD if NFIELDS == 65 else WORKLOAD.replace("65 fields (exact solution + 64 seeded smooth fields)",
+                                                         f"{NFIELDS} fields (profiling case)")
+    return {"workload": wl, "grid": [NSIDE, NSIDE], "fft": [2048, 2048], "fields": NFIELDS,
             "alpha": ALPHA, "degree": DEGREE, "global_batch": NFIELDS, "parallelism": parallelism,
             "l2": "inputs 272 MB and spectra 545 MB exceed the 129 MB L2; no flush"}
 
@@ -210,11 +212,17 @@ def apply_model_bytes(fields: int) -> float:
 # FP32 FMA peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# kernels as they stand, from the capture summarised in
-# profiles/apply2d_1023_ncu_full.md (20 fields, scaled to 65 by the fields
-# processed); None where the kernel changed after the capture.
-DRAM_TRAFFIC_PER_FIELD = {}
+# DRAM bytes per field (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch / fields in it) of the kernels as they stand, from one ncu --set full
+# capture of a 20-field apply, scaled to a launch by the fields it processes.
+# With 20 fields part of the 168 MB half spectrum is still in the 129 MB L2 when
+# the next pass reads it, so at 65 fields the traffic per field is somewhat
+# higher.  Remove an entry when its kernel changes.
+DRAM_TRAFFIC_PER_FIELD = {
+    "cols_sym2_f32_M2048": (172.527360e6 + 110.699264e6) / 20,
+    "rows_fwd_f32_M2048": (84.182528e6 + 114.387200e6) / 20,
+    "rows_inv_f32_M2048": (168.299008e6 + 54.121216e6) / 20,
+}
 
 
 def run_ours(args) -> None:
@@ -393,8 +401,29 @@ def extra_measurements(fg, torch, u32, op, barrier) -> dict:
         solves[f"3d_n255_p1_alpha{alpha}"] = res
         op3.close()
     out["solves"] = solves
+    out["operator_builds"] = build_measurement(fg, barrier)
     out["batch"] = batch_measurement(fg, torch, barrier)
     out["served"] = served_measurement(fg, torch, barrier)
+    return out
+
+
+def build_measurement(fg, barrier) -> dict:
+    """Operator build (frac_coeffs: weights, stencil, centre, symbol, tau symbol;
+    synchronous) for the sizes of the served stream, alpha = 1.3, lambda in {0, 1}:
+    ms of the second of two builds, host clock around the call."""
+    out = {}
+    for d, n, p in ((3, 63, 1), (3, 127, 1), (3, 255, 0), (3, 255, 1), (3, 255, 2), (2, 511, 2), (2, 1023, 2),
+                    (1, 4095, 2)):
+        for lam in (0.0, 1.0):
+            ms = 0.0
+            for _ in range(2):
+                barrier()
+                t0 = time.perf_counter()
+                op = fg.FracOp(d, n, 1.3, degree=p, lam=lam)
+                barrier()
+                ms = 1e3 * (time.perf_counter() - t0)
+                op.close()
+            out[f"{d}d_n{n}_p{p}_lam{lam:g}"] = ms
     return out
 
 
@@ -506,7 +535,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fields", type=int, default=65,
+                    help="fields per apply (65 = the benchmark workload; fewer only for profiler captures)")
     args = ap.parse_args()
+    global NFIELDS
+    NFIELDS = args.fields
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -2,7 +2,7 @@
 //   weight integrals omega_k^p (Eq. (wi-1D), Eq. (2D-scheme0) and its 3D analogue;
 //   tempered kernel of Remark 2.2), stencil a_k with the origin rule, centre
 //   coefficient a_0, far field F_d (host), and the symbol of the circulant
-//   embedding (separable cosine sums).
+//   embedding (separable cosine sums, each axis by an FP64 FFT).
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -232,8 +232,10 @@ double far_field(int d, double alpha, double L, double lambda) {
 }
 
 // ---------------------------------------------------------------------------
-// Weight integrals, one thread per node k in {0..N}^d (gather over the
-// elements of the support of the tensor basis function of k).
+// Weight integrals omega_k = int phi_k(xi) mu(xi) dxi (Eq. (wi-1D), Eq. (2D-scheme0)): per
+// element a Gauss-Legendre rule of q points per axis, q chosen by the
+// element's distance to the origin; the origin element by exact radial
+// moments (1D) or a Duffy split (d >= 2).
 // ---------------------------------------------------------------------------
 
 struct WParams {
@@ -330,133 +332,98 @@ __device__ double radial_moment(double a, double b, double H) {
   return Ha * sum;
 }
 
-// int over the origin element [0, H]^d of prod_i phi_{l_i}(xi_i) mu(xi): Duffy split into the d
-// pyramids {xi_i = max}, xi = r (s with s_i = 1), exact radial moments, Gauss-Legendre (16) in s.
-__device__ double origin_element(const WParams& P, const int* l, double H) {
-  const int d = P.d, p = P.p;
-  double cf[3][3];
-  for (int i = 0; i < d; ++i) {
-    origin_poly(p, l[i], cf[i]);
-    for (int m = 0; m < 3; ++m) cf[i][m] *= pow(P.h, -m);  // coefficients of xi^m
-  }
-  const int maxdeg = p * d;
-  if (d == 1) {
-    double s = 0.0;
-    for (int m = 0; m <= p; ++m) s += cf[0][m] * radial_moment(2.0 - P.alpha + m, P.lambda, H);
-    return s;
-  }
-  const int R = 6;  // rule index of q = 16
-  const int q = rule_q(R), off = rule_off(R);
-  double tot = 0.0;
-  const int nang = (d == 2) ? q : q * q;
-  for (int a = 0; a < nang; ++a) {
-    double s[2], ws = 1.0;
-    int ia = a % q, ib = a / q;
-    if (!CHK(off + ia, kRuleTotal) || !CHK(off + ib, kRuleTotal)) continue;
-    s[0] = 0.5 * (c_gl_x[off + ia] + 1.0);
-    ws *= 0.5 * c_gl_w[off + ia];
-    if (d == 3) {
-      s[1] = 0.5 * (c_gl_x[off + ib] + 1.0);
-      ws *= 0.5 * c_gl_w[off + ib];
-    } else {
-      s[1] = 0.0;
-    }
-    double cs2 = 1.0 + s[0] * s[0] + (d == 3 ? s[1] * s[1] : 0.0);
-    double cs = sqrt(cs2);
-    double R_m[7];
-    for (int m = 0; m <= maxdeg && CHK(m, 7); ++m) R_m[m] = radial_moment(2.0 - P.alpha + m, P.lambda * cs, H);
-    double base = ws * pow(cs, -P.beta);
-    for (int i = 0; i < d; ++i) {  // pyramid: axis i largest
-      double poly[7] = {1, 0, 0, 0, 0, 0, 0};
-      int deg = 0, col = 0;
-      for (int j = 0; j < d; ++j) {
-        double t = (j == i) ? 1.0 : (CHK(col, 2) ? s[col++] : 0.0);
-        double pj[3] = {cf[j][0], cf[j][1] * t, cf[j][2] * t * t};
-        double np[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int m1 = 0; m1 <= deg; ++m1)
-          for (int m2 = 0; m2 <= p; ++m2)
-            if (CHK(m1 + m2, 7) && CHK(m1, 7) && CHK(m2, 3)) np[m1 + m2] += poly[m1] * pj[m2];
-        deg += p;
-        for (int m = 0; m < 7; ++m) poly[m] = np[m];
-      }
-      double acc = 0.0;
-      for (int m = 0; m <= deg && CHK(m, 7); ++m) acc += poly[m] * R_m[m];
-      tot += base * acc;
-    }
-  }
-  return tot;
+// int_0^H phi_l(xi) mu(xi) dxi on the 1D origin element: exact radial moments of the
+// monomials of the local basis.
+__device__ double origin_element_1d(const WParams& P, int l, double H) {
+  double cf[3];
+  origin_poly(P.p, l, cf);
+  const double ih = 1.0 / P.h;
+  double s = 0.0, scale = 1.0;
+  for (int m = 0; m <= P.p; ++m, scale *= ih) s += cf[m] * scale * radial_moment(2.0 - P.alpha + m, P.lambda, H);
+  return s;
 }
 
-__global__ void k_weights(WParams P, double* __restrict__ omega, int64_t count) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= count) return;
-  const int d = P.d;
-  const int64_t N1 = P.N + 1;
-  int64_t k[3] = {0, 0, 0};
-  int64_t rem = idx;
-  for (int i = 0; i < d; ++i) {  // i = 0 is the fastest axis
-    k[i] = rem % N1;
-    rem /= N1;
+// Origin element [0, H]^d (d >= 2) of prod_i phi_{l_i}(xi_i) mu(xi): Duffy split into the d
+// pyramids {xi_i = max}, xi = r (s with s_i = 1), exact radial moments in r, tensor
+// Gauss-Legendre (16 points per angular coordinate) in s.  duffy_angle evaluates what angle
+// a shares across all basis products (direction, weight x |s|^{-beta}, radial moments);
+// duffy_product the sum over the pyramids for one product l.
+constexpr int kDuffyRule = 6;  // rule index of q = 16
+struct DuffyAngle {
+  double s[2];
+  double base;
+  double R[7];
+};
+
+__device__ void duffy_angle(const WParams& P, int a, double H, DuffyAngle& A) {
+  const int d = P.d, q = rule_q(kDuffyRule), off = rule_off(kDuffyRule);
+  const int ia = a % q, ib = a / q;
+  double ws = 1.0;
+  A.s[0] = A.s[1] = 0.0;
+  if (CHK(off + ia, kRuleTotal)) {
+    A.s[0] = 0.5 * (c_gl_x[off + ia] + 1.0);
+    ws *= 0.5 * c_gl_w[off + ia];
   }
-  AxisEl el[3][2];
-  int ne[3] = {1, 1, 1};
-  if (!CHK(d - 1, 3)) return;
-  for (int i = 0; i < d; ++i) {
-    ne[i] = axis_elements(P, k[i], el[i]);
-    if (!CHK(ne[i] - 1, 2)) return;
+  if (d == 3 && CHK(off + ib, kRuleTotal)) {
+    A.s[1] = 0.5 * (c_gl_x[off + ib] + 1.0);
+    ws *= 0.5 * c_gl_w[off + ib];
   }
-  double total = 0.0;
-  const int ncomb = ne[0] * (d > 1 ? ne[1] : 1) * (d > 2 ? ne[2] : 1);
-  for (int cmb = 0; cmb < ncomb; ++cmb) {
-    int e[3] = {cmb % ne[0], d > 1 ? (cmb / ne[0]) % ne[1] : 0, d > 2 ? cmb / (ne[0] * ne[1]) : 0};
-    const AxisEl* E[3] = {&el[0][e[0]], d > 1 ? &el[1][e[1]] : nullptr, d > 2 ? &el[2][e[2]] : nullptr};
-    bool origin = true;
-    double width = 0.0, lo2 = 0.0;
-    for (int i = 0; i < d; ++i) {
-      origin = origin && (E[i]->origin_l >= 0);
-      width = fmax(width, E[i]->hi - E[i]->lo);
-      lo2 += E[i]->lo * E[i]->lo;
-    }
-    if (origin) {
-      int l[3] = {E[0]->origin_l, d > 1 ? E[1]->origin_l : 0, d > 2 ? E[2]->origin_l : 0};
-      total += origin_element(P, l, E[0]->hi - E[0]->lo);
-      continue;
-    }
-    const int rule = pick_rule(sqrt(lo2) / width);
-    if (!CHK(rule, kNumRules)) continue;
-    const int q = rule_q(rule), off = rule_off(rule);
-    if (!CHK(q - 1, 20) || !CHK(off + q - 1, kRuleTotal)) continue;
-    // per-axis nodes and weighted basis values
-    double X[3][20], WB[3][20];
-    for (int i = 0; i < d; ++i) {
-      const double c = 0.5 * (E[i]->hi + E[i]->lo), hw = 0.5 * (E[i]->hi - E[i]->lo);
-      for (int g = 0; g < q; ++g) {
-        X[i][g] = c + hw * c_gl_x[off + g];
-        WB[i][g] = hw * c_gl_w[off + g] * basis_val(*E[i], X[i][g]);
-      }
+  const double cs = sqrt(1.0 + A.s[0] * A.s[0] + A.s[1] * A.s[1]);
+  for (int m = 0; m <= P.p * d && CHK(m, 7); ++m) A.R[m] = radial_moment(2.0 - P.alpha + m, P.lambda * cs, H);
+  A.base = ws * pow(cs, -P.beta);
+}
+
+__device__ double duffy_product(const WParams& P, const int* l, const DuffyAngle& A) {
+  const int d = P.d, p = P.p;
+  const double ih = 1.0 / P.h;
+  double cf[3][3];
+  for (int i = 0; i < d && CHK(i, 3); ++i) {
+    origin_poly(p, l[i], cf[i]);
+    cf[i][1] *= ih;  // coefficients of xi^m
+    cf[i][2] *= ih * ih;
+  }
+  double tot = 0.0;
+  for (int i = 0; i < d; ++i) {  // pyramid: axis i largest
+    double poly[7] = {1, 0, 0, 0, 0, 0, 0};
+    int deg = 0, col = 0;
+    for (int j = 0; j < d && CHK(j, 3); ++j) {
+      const double t = (j == i) ? 1.0 : (CHK(col, 2) ? A.s[col++] : 0.0);
+      const double pj[3] = {cf[j][0], cf[j][1] * t, cf[j][2] * t * t};
+      double np[7] = {0, 0, 0, 0, 0, 0, 0};
+      for (int m1 = 0; m1 <= deg; ++m1)
+        for (int m2 = 0; m2 <= p; ++m2)
+          if (CHK(m1 + m2, 7) && CHK(m1, 7) && CHK(m2, 3)) np[m1 + m2] += poly[m1] * pj[m2];
+      deg += p;
+      for (int m = 0; m < 7; ++m) poly[m] = np[m];
     }
     double acc = 0.0;
-    if (d == 1) {
-      for (int g = 0; g < q; ++g) acc += WB[0][g] * mu_r2(X[0][g] * X[0][g], P);
-    } else if (d == 2) {
-      for (int g1 = 0; g1 < q; ++g1) {
-        double a1 = 0.0;
-        const double x1 = X[1][g1] * X[1][g1];
-        for (int g0 = 0; g0 < q; ++g0) a1 += WB[0][g0] * mu_r2(X[0][g0] * X[0][g0] + x1, P);
-        acc += WB[1][g1] * a1;
-      }
-    } else {
-      for (int g2 = 0; g2 < q; ++g2) {
-        double a2 = 0.0;
-        const double x2 = X[2][g2] * X[2][g2];
-        for (int g1 = 0; g1 < q; ++g1) {
-          double a1 = 0.0;
-          const double x12 = X[1][g1] * X[1][g1] + x2;
-          for (int g0 = 0; g0 < q; ++g0) a1 += WB[0][g0] * mu_r2(X[0][g0] * X[0][g0] + x12, P);
-          a2 += WB[1][g1] * a1;
-        }
-        acc += WB[2][g2] * a2;
-      }
+    for (int m = 0; m <= deg && CHK(m, 7); ++m) acc += poly[m] * A.R[m];
+    tot += acc;
+  }
+  return A.base * tot;
+}
+
+__global__ void k_weights_1d(WParams P, double* __restrict__ omega, int64_t count) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  AxisEl el[2];
+  const int ne = axis_elements(P, idx, el);
+  double total = 0.0;
+  for (int e = 0; e < ne && CHK(e, 2); ++e) {
+    const AxisEl& E = el[e];
+    if (E.origin_l >= 0) {
+      total += origin_element_1d(P, E.origin_l, E.hi - E.lo);
+      continue;
+    }
+    const int rule = pick_rule(sqrt(E.lo * E.lo) / (E.hi - E.lo));
+    if (!CHK(rule, kNumRules)) continue;
+    const int q = rule_q(rule), off = rule_off(rule);
+    if (!CHK(off + q - 1, kRuleTotal)) continue;
+    const double c = 0.5 * (E.hi + E.lo), hw = 0.5 * (E.hi - E.lo);
+    double acc = 0.0;
+    for (int g = 0; g < q; ++g) {
+      const double x = c + hw * c_gl_x[off + g];
+      acc += hw * c_gl_w[off + g] * basis_val(E, x) * mu_r2(x * x, P);
     }
     total += acc;
   }
@@ -489,8 +456,105 @@ __device__ AxisEl elem_axis(const WParams& P, int e, int l) {
   return AxisEl{a, a + 2 * h, a, a + h, 0.5 / (h * h), 2, e == 0 ? 2 : -1};
 }
 
+// ---------------------------------------------------------------------------
+// Near-origin elements (d >= 2): the elements e in [0, E)^d carry the densest
+// rules (q up to 20 per axis, the Duffy-split origin element), so they are
+// integrated up front with kNearSplit blocks each: block s takes every
+// kNearSplit-th quadrature point (or, on the origin element, every
+// kNearSplit-th (angle, product group) pair), and writes per-product partial
+// sums tab[(element * kNearSplit + s) * nloc + c]; the tiled kernel adds the
+// kNearSplit partials in order.  Deterministic: fixed split, fixed reduction tree.
+// ---------------------------------------------------------------------------
+
+constexpr int kNearSplit = 8;
+constexpr int kNearGroups = 8;   // product groups per Duffy angle
+constexpr int kNearE[4] = {0, 0, 16, 8};
+
+template <int D, int PD>
+__global__ void __launch_bounds__(256) k_near_elements(WParams P, int E, double* __restrict__ tab) {
+  constexpr int N1 = PD + 1, NL = (D == 2) ? N1 * N1 : N1 * N1 * N1;
+  __shared__ double red[8][NL];
+  const int eidx = blockIdx.x / kNearSplit, sp = blockIdx.x % kNearSplit;
+  const int el[3] = {eidx % E, (eidx / E) % E, D == 3 ? eidx / (E * E) : 0};
+  double acc[NL];
+#pragma unroll
+  for (int c = 0; c < NL; ++c) acc[c] = 0.0;
+  AxisEl ax[3][N1];
+  bool origin = true;
+  double lo2 = 0.0, width = 0.0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int l = 0; l < N1; ++l) ax[i][l] = elem_axis(P, el[i], l);
+    origin = origin && el[i] == 0;
+    lo2 += ax[i][0].lo * ax[i][0].lo;
+    width = fmax(width, ax[i][0].hi - ax[i][0].lo);
+  }
+  const int stride = kNearSplit * blockDim.x;
+  if (origin) {
+    const int q = rule_q(kDuffyRule), nang = (D == 2) ? q : q * q;
+    const double H = ax[0][0].hi - ax[0][0].lo;
+    for (int u = sp + kNearSplit * threadIdx.x; u < nang * kNearGroups; u += stride) {
+      const int a = u % nang, g = u / nang;
+      DuffyAngle A;
+      duffy_angle(P, a, H, A);
+#pragma unroll
+      for (int c = 0; c < NL; ++c) {
+        if (c % kNearGroups != g) continue;
+        const int l[3] = {c % N1, (c / N1) % N1, D == 3 ? c / (N1 * N1) : 0};
+        acc[c] += duffy_product(P, l, A);
+      }
+    }
+  } else {
+    const int rule = pick_rule(sqrt(lo2) / width);
+    const int q = rule_q(rule), off = rule_off(rule);
+    const int npts = (D == 2) ? q * q : q * q * q;
+    double cen[3], hw[3];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      cen[i] = 0.5 * (ax[i][0].hi + ax[i][0].lo);
+      hw[i] = 0.5 * (ax[i][0].hi - ax[i][0].lo);
+    }
+    for (int j = sp + kNearSplit * threadIdx.x; j < npts; j += stride) {
+      const int g[3] = {j % q, (j / q) % q, D == 3 ? j / (q * q) : 0};
+      double wb[3][N1], r2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const int gi = CHK(off + g[i], kRuleTotal) ? off + g[i] : off;
+        const double x = cen[i] + hw[i] * c_gl_x[gi];
+        const double w = hw[i] * c_gl_w[gi];
+        r2 += x * x;
+#pragma unroll
+        for (int l = 0; l < N1; ++l) wb[i][l] = w * basis_val(ax[i][l], x);
+      }
+      const double m = mu_r2(r2, P);
+#pragma unroll
+      for (int c = 0; c < NL; ++c) {
+        double v = m * wb[0][c % N1] * wb[1][(c / N1) % N1];
+        if (D == 3) v *= wb[2][c / (N1 * N1)];
+        acc[c] += v;
+      }
+    }
+  }
+  // block sum per product: warps by shuffles, then the 8 warp sums in order
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < NL; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0 && CHK(warp, 8)) red[warp][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NL) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5) && w < 8; ++w) t += red[w][threadIdx.x];
+    tab[((int64_t)eidx * kNearSplit + sp) * NL + threadIdx.x] = t;
+  }
+}
+
 template <int D, int T>
-__global__ void __launch_bounds__(256) k_weights_tiled(WParams P, double* __restrict__ omega) {
+__global__ void __launch_bounds__(256) k_weights_tiled(WParams P, const double* __restrict__ near, int E,
+                                                       double* __restrict__ omega) {
   constexpr int NL = 27;                       // max local basis products per element ((p+1)^d)
   extern __shared__ __align__(16) double eint[];
   const int p = P.p;
@@ -532,11 +596,17 @@ __global__ void __launch_bounds__(256) k_weights_tiled(WParams P, double* __rest
       lo2 += ax[i][0].lo * ax[i][0].lo;
       width = fmax(width, ax[i][0].hi - ax[i][0].lo);
     }
-    if (origin) {
+    bool in_near = true;
+    for (int i = 0; i < D; ++i) in_near = in_near && el[i] < E;
+    if (in_near) {
+      const int64_t ne = el[0] + E * (el[1] + (D == 3 ? E * el[2] : 0));
       for (int c = 0; c < nloc; ++c) {
-        int l[3] = {c % nloc1, (c / nloc1) % nloc1, D == 3 ? c / (nloc1 * nloc1) : 0};
-        acc[c] = origin_element(P, l, ax[0][0].hi - ax[0][0].lo);
+        double v = 0.0;
+        for (int sp = 0; sp < kNearSplit; ++sp) v += near[(ne * kNearSplit + sp) * nloc + c];
+        acc[c] = v;
       }
+    } else if (origin) {
+      (void)CHK(-1, 1);  // the origin element is always in the near block
     } else {
       const int rule = pick_rule(sqrt(lo2) / width);
       const int q = rule_q(rule), off = rule_off(rule);
@@ -712,25 +782,60 @@ __global__ void k_gen_block(const double* __restrict__ a, double* __restrict__ o
   if (CHK(src, tot)) out[idx] = a[src];
 }
 
-// in: (A, n, B) -> out: (A, K, B)
-__global__ void k_cos_pass(const double* __restrict__ in, double* __restrict__ out, int64_t A, int64_t n,
-                           int64_t B, int64_t K, int64_t M, const double2* __restrict__ tw) {
-  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= A * K * B) return;
-  const int64_t b = idx % B;
-  const int64_t k = (idx / B) % K;
-  const int64_t a = idx / (B * K);
-  const double* src = in + a * n * B + b;
-  double s = 0.0;
-  int64_t t = 0;  // (j * k) mod M
-  for (int64_t j = 0; j < n; ++j) {
-    if (!CHK(t, M) || !CHK(a * n * B + j * B + b, A * n * B)) break;
-    double v = src[j * B] * tw[t].x;
-    s += (j == 0) ? v : 2.0 * v;
-    t += k;
-    if (t >= M) t -= M;
+// One axis of the symbol by FFT, in: (A, n, B) -> out: (A, K, B).  Line (a, b) is
+// even-extended to length M (x_j = a_{min(j, M - j)} when that index is below n,
+// else 0; n <= M/2 so the two halves never overlap), whose DFT is the cosine sum
+// sum_j w_j a_j cos(2 pi j k / M) above.  The DFT of a real even sequence is real, so
+// two lines share one complex transform (one as the real part, one as the imaginary
+// part).  A block takes 2 LB consecutive lines (consecutive b: coalesced when B > 1,
+// along the line when B = 1), loads them in bit-reversed order into shared memory
+// (M x LB complex slots), runs log2 M in-place radix-2 stages with the FP64 twiddle
+// table tw[t] = e^{-2 pi i t / M}, and writes k in [0, K).
+__global__ void __launch_bounds__(256) k_sym_fft(const double* __restrict__ in, double* __restrict__ out, int64_t A,
+                                                 int64_t n, int64_t B, int64_t K, int logm, int LB,
+                                                 const double2* __restrict__ tw) {
+  extern __shared__ __align__(16) double2 sx[];
+  const int64_t M = (int64_t)1 << logm, lines = A * B, L0 = (int64_t)blockIdx.x * 2 * LB;
+  const int64_t nl = 2 * LB;
+  const int64_t nsh = M * LB;
+  for (int64_t idx = threadIdx.x; idx < nl * M; idx += blockDim.x) {
+    const int64_t l = (B == 1) ? idx / M : idx % nl, j = (B == 1) ? idx % M : idx / nl;
+    const int64_t L = L0 + l, jj = j <= M - j ? j : M - j;
+    double v = 0.0;
+    if (L < lines && jj < n) {
+      const int64_t a = L / B, b = L % B, src = (a * n + jj) * B + b;
+      if (CHK(src, lines * n)) v = in[src];
+    }
+    const int64_t pos = (int64_t)(__brev((unsigned)j) >> (32 - logm));
+    const int64_t slot = pos * LB + (l % LB);
+    if (CHK(slot, nsh)) {
+      if (l < LB) sx[slot].x = v;
+      else sx[slot].y = v;
+    }
   }
-  if (CHK(idx, A * K * B)) out[idx] = s;
+  __syncthreads();
+  for (int s = 0; s < logm; ++s) {
+    const int64_t half = (int64_t)1 << s;
+    for (int64_t t = threadIdx.x; t < (M / 2) * LB; t += blockDim.x) {
+      const int64_t i = t % LB, bf = t / LB, k = bf & (half - 1);
+      const int64_t p0 = ((bf >> s) << (s + 1)) + k, p1 = p0 + half;
+      const int64_t ti = k << (logm - 1 - s);
+      if (!CHK(p1 * LB + i, nsh) || !CHK(ti, M)) continue;
+      const double2 w = tw[ti], x0 = sx[p0 * LB + i], y = sx[p1 * LB + i];
+      const double2 x1 = make_double2(y.x * w.x - y.y * w.y, y.x * w.y + y.y * w.x);
+      sx[p0 * LB + i] = make_double2(x0.x + x1.x, x0.y + x1.y);
+      sx[p1 * LB + i] = make_double2(x0.x - x1.x, x0.y - x1.y);
+    }
+    __syncthreads();
+  }
+  for (int64_t idx = threadIdx.x; idx < nl * K; idx += blockDim.x) {
+    const int64_t l = (B == 1) ? idx / K : idx % nl, k = (B == 1) ? idx % K : idx / nl;
+    const int64_t L = L0 + l;
+    if (L >= lines || !CHK(k * LB + (l % LB), nsh)) continue;
+    const double2 v = sx[k * LB + (l % LB)];
+    const int64_t a = L / B, b = L % B, dst = (a * K + k) * B + b;
+    if (CHK(dst, lines * K)) out[dst] = l < LB ? v.x : v.y;
+  }
 }
 
 __global__ void k_scale_symbol(const double* __restrict__ raw, double* __restrict__ l64, float* __restrict__ l32,
@@ -818,13 +923,13 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   const double L = op->N * pr.h;
   op->far_field = far_field(d, pr.alpha, L, pr.lambda);
 
-  double *omega = nullptr, *partial = nullptr;
+  double *omega = nullptr, *partial = nullptr, *near = nullptr;
   const int TB = 256;
   const int64_t nblk = ceil_div(ngen, TB);
   FRAC_CUDA_TRY(cudaMallocAsync(&omega, ngen * sizeof(double), st));
   FRAC_CUDA_TRY(cudaMallocAsync(&partial, nblk * sizeof(double), st));
   if (d == 1) {
-    k_weights<<<(unsigned)nblk, TB, 0, st>>>(P, omega, ngen);
+    k_weights_1d<<<(unsigned)nblk, TB, 0, st>>>(P, omega, ngen);
   } else {
     // tiles of 16^2 / 8^3 nodes; shared memory = elements per tile x local products
     const int T = d == 2 ? 16 : 8;
@@ -835,12 +940,28 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
     const int nl1 = pr.degree + 1;
     size_t sm = sizeof(double);
     for (int i = 0; i < d; ++i) sm *= (size_t)ea * nl1;
+    // near-origin elements [0, E)^d first, spread over kNearSplit blocks each
+    const int64_t ne_axis = pr.degree == 0 ? op->N + 1 : (pr.degree == 1 ? op->N : op->N / 2);
+    const int E = (int)std::min<int64_t>(kNearE[d], ne_axis);
+    int64_t nnear = 1;
+    for (int i = 0; i < d; ++i) nnear *= E;
+    FRAC_CUDA_TRY(cudaMallocAsync(&near, (size_t)nnear * kNearSplit * 27 * sizeof(double), st));
+    const unsigned nb = (unsigned)(nnear * kNearSplit);
+    switch (d * 3 + pr.degree) {
+      case 6: k_near_elements<2, 0><<<nb, 256, 0, st>>>(P, E, near); break;
+      case 7: k_near_elements<2, 1><<<nb, 256, 0, st>>>(P, E, near); break;
+      case 8: k_near_elements<2, 2><<<nb, 256, 0, st>>>(P, E, near); break;
+      case 9: k_near_elements<3, 0><<<nb, 256, 0, st>>>(P, E, near); break;
+      case 10: k_near_elements<3, 1><<<nb, 256, 0, st>>>(P, E, near); break;
+      default: k_near_elements<3, 2><<<nb, 256, 0, st>>>(P, E, near); break;
+    }
+    FRAC_CUDA_TRY(cudaGetLastError());
     if (d == 2) {
       FRAC_CUDA_TRY(cudaFuncSetAttribute(k_weights_tiled<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_weights_tiled<2, 16><<<(unsigned)tiles, 256, sm, st>>>(P, omega);
+      k_weights_tiled<2, 16><<<(unsigned)tiles, 256, sm, st>>>(P, near, E, omega);
     } else {
       FRAC_CUDA_TRY(cudaFuncSetAttribute(k_weights_tiled<3, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_weights_tiled<3, 8><<<(unsigned)tiles, 256, sm, st>>>(P, omega);
+      k_weights_tiled<3, 8><<<(unsigned)tiles, 256, sm, st>>>(P, near, E, omega);
     }
   }
   FRAC_CUDA_TRY(cudaGetLastError());
@@ -867,13 +988,16 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   k_gen_block<<<(unsigned)ceil_div(sz, TB), TB, 0, st>>>(op->a, bufA, d, op->N + 1, n, sz);
   FRAC_CUDA_TRY(cudaGetLastError());
   const double2* tw = twiddles64(op->logm);
-  // pass over axis i (0 = fastest): shape (A, n, B) with B = K^i, A = n^{d-1-i}
+  // pass over axis i (0 = fastest): shape (A, n, B) with B = K^i, A = n^{d-1-i};
+  // 2 LB lines per block, M x LB complex slots (64 KB; one 128 KB line at M = 8192)
+  const int LB = (int)std::max<int64_t>(1, std::min<int64_t>(8, 4096 / M));
+  const size_t fsm = (size_t)M * LB * sizeof(double2);
+  FRAC_CUDA_TRY(cudaFuncSetAttribute(k_sym_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
   int64_t B = 1;
   for (int i = 0; i < d; ++i) {
     int64_t A = 1;
     for (int j = i + 1; j < d; ++j) A *= n;
-    const int64_t outsz = A * K * B;
-    k_cos_pass<<<(unsigned)ceil_div(outsz, TB), TB, 0, st>>>(bufA, bufB, A, n, B, K, M, tw);
+    k_sym_fft<<<(unsigned)ceil_div(A * B, 2 * LB), 256, fsm, st>>>(bufA, bufB, A, n, B, K, op->logm, LB, tw);
     FRAC_CUDA_TRY(cudaGetLastError());
     std::swap(bufA, bufB);
     B *= K;
@@ -900,6 +1024,7 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   FRAC_CUDA_TRY(cudaFreeAsync(pmin, st));
   FRAC_CUDA_TRY(cudaMemcpyAsync(&op->a0, op->a, sizeof(double), cudaMemcpyDeviceToHost, st));
   FRAC_CUDA_TRY(cudaFreeAsync(omega, st));
+  if (near) FRAC_CUDA_TRY(cudaFreeAsync(near, st));
   FRAC_CUDA_TRY(cudaFreeAsync(partial, st));
   FRAC_CUDA_TRY(cudaFreeAsync(bufA, st));
   FRAC_CUDA_TRY(cudaFreeAsync(bufB, st));
