@@ -174,9 +174,10 @@ def profile_read(lib) -> dict:
     return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(min(cnt.value, 64))}
 
 
-def algorithmic_bytes(kernel: str, fields: int) -> float:
-    """Compulsory bytes per launch of each apply kernel for the workload
-    (FP32; n = 1023, K = 1025 half-spectrum columns, complex = 8 B)."""
+def algorithmic_bytes(kernel: str, fields: float, launches: float = 1.0) -> float:
+    """Compulsory bytes of each apply kernel over `fields` fields processed in
+    `launches` launches (FP32; n = 1023, K = 1025 half-spectrum columns, complex
+    = 8 B; the symbol pass reads the K^2 FP32 symbol once per launch)."""
     n, K = NSIDE, 1025
     u = n * n * 4
     W = n * K * 8
@@ -185,7 +186,7 @@ def algorithmic_bytes(kernel: str, fields: int) -> float:
     if kernel.startswith("rows_inv"):
         return fields * (W + u)
     if kernel.startswith("cols_sym"):
-        return fields * 2 * W + K * K * 4
+        return fields * 2 * W + launches * K * K * 4
     raise KeyError(kernel)
 
 
@@ -283,12 +284,18 @@ def run_ours(args) -> None:
     roof = None
     if dom:
         name, (nl, tot) = dom
+        # the 2D apply runs its passes on chunks of fields (one launch per pass and
+        # chunk): per-launch figures are the step's totals over its launches
+        lps = nl / args.steps
         per_launch_ms = tot / nl
-        ab = algorithmic_bytes(name, NFIELDS)
-        fl = nominal_flops(name, NFIELDS)
+        step_ms = tot / args.steps
+        ab = algorithmic_bytes(name, NFIELDS, lps) / lps
+        fl = nominal_flops(name, NFIELDS) / lps
         hbm = ab / (per_launch_ms * 1e-3) / 1e9
         alu = fl / (per_launch_ms * 1e-3) / 1e12
         tr = DRAM_TRAFFIC_PER_FIELD.get(name)
+        if tr is not None:
+            tr = tr * NFIELDS / lps
         bm = apply_model_bytes(NFIELDS)
         # the symbol pass is issue bound (FP32 FFT arithmetic, DRAM well below
         # peak in the capture); the row passes are closer to the HBM bound
@@ -300,8 +307,9 @@ def run_ours(args) -> None:
                 "frac": (alu / FP32_PEAK_TFLOPS) if alu_bound else (hbm / peak),
                 "peak_source": ("FP32 FMA peak from unit counts and clocks (152 SMs x 128 lanes x 2 x 2.07 GHz)"
                                 if alu_bound else peak_note),
-                "traffic": None if tr is None else tr * NFIELDS,
+                "traffic": tr,
                 "algorithmic_bytes": ab, "nominal_flops": fl, "ms_per_launch": per_launch_ms,
+                "launches_per_step": lps, "fields_per_launch": NFIELDS / lps, "kernel_ms_per_step": step_ms,
                 "hbm_view": {"achieved_gbs": hbm, "peak_gbs": peak, "frac": hbm / peak, "peak_source": peak_note},
                 "alu_view": {"achieved_tflops": alu, "peak_tflops": FP32_PEAK_TFLOPS, "frac": alu / FP32_PEAK_TFLOPS},
                 "apply_model": {"bytes": bm, "ms": ms, "achieved_gbs": bm / (ms * 1e-3) / 1e9,

@@ -30,7 +30,6 @@ struct CGState {
 
 // coeffs.cu
 int prepare_twiddles(int logm);
-double far_field(int d, double alpha, double L, double lambda);
 int build_coefficients(frac_op* op, cudaStream_t st);
 
 // apply.cu: y = A u for `batch` vectors on device buffers; ws holds

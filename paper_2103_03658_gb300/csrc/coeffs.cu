@@ -34,6 +34,8 @@ static_assert(rule_table_ok(0), "rule offsets");
 
 __constant__ double c_gl_x[kRuleTotal];
 __constant__ double c_gl_w[kRuleTotal];
+__constant__ double c_gl32_x[32];  // angular rule of the far field
+__constant__ double c_gl32_w[32];
 
 // Self-checking accesses: an index outside [0, n) is recorded (first source
 // line and index) and the access is skipped; the host reads the record after
@@ -90,6 +92,10 @@ static int upload_rules() {
   for (int r = 0; r < kNumRules; ++r) legendre_rule(rule_q(r), hx + rule_off(r), hw + rule_off(r));
   FRAC_CUDA_TRY(cudaMemcpyToSymbol(c_gl_x, hx, sizeof(hx)));
   FRAC_CUDA_TRY(cudaMemcpyToSymbol(c_gl_w, hw, sizeof(hw)));
+  double x32[32], w32[32];
+  legendre_rule(32, x32, w32);
+  FRAC_CUDA_TRY(cudaMemcpyToSymbol(c_gl32_x, x32, sizeof(x32)));
+  FRAC_CUDA_TRY(cudaMemcpyToSymbol(c_gl32_w, w32, sizeof(w32)));
   done.push_back(dev);
   return FRAC_OK;
 }
@@ -185,50 +191,46 @@ const float2* twiddles32(int logm) {
 // Far field F_d = int over R_+^d \ [0, L]^d of |xi|^{-d-alpha} e^{-lambda |xi|}
 // (the u(x) part of Eq. (L2); 1D: 1/(alpha L^alpha) when lambda = 0).
 // Largest-coordinate split: xi = rho (1, s), rho > L, s in [0,1]^{d-1}:
-// F_d = d int_s c(s)^{-d-alpha} int_L^inf rho^{-1-alpha} e^{-lambda c rho} d rho ds.
-// The rho-integral with rho = L / t is L^{-alpha} int_0^1 t^{alpha-1} e^{-lambda c L / t} dt,
-// integrated by Gauss-Legendre on geometrically graded panels [2^{-j-1}, 2^{-j}].
+// F_d = d int_s c(s)^{-d-alpha} int_L^inf rho^{-1-alpha} e^{-lambda c rho} d rho ds,
+// s by a 32-point Gauss-Legendre rule per coordinate.  The rho-integral with
+// rho = L / t is L^{-alpha} int_0^1 t^{alpha-1} e^{-lambda c L / t} dt, integrated
+// by a 20-point Gauss-Legendre rule on the graded panels [2^{-j-1}, 2^{-j}]
+// until e^{-lambda c L / t} underflows (closed form L^{-alpha} / alpha when
+// lambda c L is negligible).  k_far_terms writes one term per (angle, panel);
+// k_centre sums them.
 // ---------------------------------------------------------------------------
 
-static double radial_tail(double alpha, double b, double L) {
-  if (b * L < 1e-14) return std::pow(L, -alpha) / alpha;
-  double x[20], w[20];
-  legendre_rule(20, x, w);
-  double x_ = b * L;
-  double sum = 0.0;
-  for (int j = 0; j < 80; ++j) {
-    double hi = std::ldexp(1.0, -j), lo = std::ldexp(1.0, -j - 1);
-    double part = 0.0;
-    for (int g = 0; g < 20; ++g) {
-      double t = 0.5 * (hi + lo) + 0.5 * (hi - lo) * x[g];
-      part += w[g] * std::pow(t, alpha - 1.0) * std::exp(-x_ / t);
-    }
-    part *= 0.5 * (hi - lo);
-    sum += part;
-    if (x_ / hi > 800.0) break;  // e^{-x/t} below underflow on every later panel
-  }
-  return std::pow(L, -alpha) * sum;
-}
+constexpr int kFarPanels = 80;
 
-double far_field(int d, double alpha, double L, double lambda) {
-  if (d == 1) return radial_tail(alpha, lambda, L);
-  double x[32], w[32];
-  legendre_rule(32, x, w);
-  double tot = 0.0;
-  if (d == 2) {
-    for (int i = 0; i < 32; ++i) {
-      double s = 0.5 * (x[i] + 1.0), c = std::sqrt(1.0 + s * s);
-      tot += 0.5 * w[i] * std::pow(c, -2.0 - alpha) * radial_tail(alpha, lambda * c, L);
-    }
-  } else {
-    for (int i = 0; i < 32; ++i)
-      for (int j = 0; j < 32; ++j) {
-        double s = 0.5 * (x[i] + 1.0), t = 0.5 * (x[j] + 1.0);
-        double c = std::sqrt(1.0 + s * s + t * t);
-        tot += 0.25 * w[i] * w[j] * std::pow(c, -3.0 - alpha) * radial_tail(alpha, lambda * c, L);
-      }
+__device__ __forceinline__ int far_angles(int d) { return d == 1 ? 1 : (d == 2 ? 32 : 32 * 32); }
+
+__global__ void k_far_terms(int d, double alpha, double lambda, double L, double* __restrict__ terms, int64_t count) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  const int a = (int)(idx / kFarPanels), j = (int)(idx % kFarPanels);
+  double c = 1.0, wa = 1.0;
+  if (d >= 2) {
+    const int i0 = a % 32, i1 = a / 32;
+    const double s0 = 0.5 * (c_gl32_x[i0] + 1.0);
+    const double s1 = d == 3 && i1 < 32 ? 0.5 * (c_gl32_x[i1] + 1.0) : 0.0;
+    c = sqrt(1.0 + s0 * s0 + s1 * s1);
+    wa = d * 0.5 * c_gl32_w[i0] * (d == 3 && i1 < 32 ? 0.5 * c_gl32_w[i1] : 1.0) * pow(c, -(double)d - alpha);
   }
-  return d * tot;
+  const double x = lambda * c * L;
+  double v = 0.0;
+  if (x < 1e-14) {
+    if (j == 0) v = pow(L, -alpha) / alpha;
+  } else if (j == 0 || ldexp(x, j - 1) <= 800.0) {  // panel j follows one that did not underflow
+    const double hi = ldexp(1.0, -j), lo = ldexp(1.0, -j - 1);
+    const int off = rule_off(7), q = rule_q(7);
+    double part = 0.0;
+    for (int g = 0; g < q && CHK(off + g, kRuleTotal); ++g) {
+      const double t = 0.5 * (hi + lo) + 0.5 * (hi - lo) * c_gl_x[off + g];
+      part += c_gl_w[off + g] * pow(t, alpha - 1.0) * exp(-x / t);
+    }
+    v = pow(L, -alpha) * part * 0.5 * (hi - lo);
+  }
+  terms[idx] = wa * v;
 }
 
 // ---------------------------------------------------------------------------
@@ -431,15 +433,17 @@ __global__ void k_weights_1d(WParams P, double* __restrict__ omega, int64_t coun
 }
 
 // ---------------------------------------------------------------------------
-// Tiled weights (d >= 2): one block per tile of T^d nodes.  Phase 1 computes,
-// once, the integrals of every local basis product over every element that
-// touches the tile (the element is shared by up to 2^d nodes of the tile) and
-// keeps them in shared memory; phase 2 lets each node sum its contributions
-// in a fixed order.  Elements per axis: p = 0: e = k (one node); p = 1:
-// [e h, (e+1) h], nodes e, e+1; p = 2: [2e h, (2e+2) h], nodes 2e, 2e+1, 2e+2.
+// Weights for d >= 2 in three steps, each element integrated once:
+//   k_near_elements: the elements near the origin (densest rules, Duffy-split
+//     origin element), spread over several blocks each;
+//   k_elements: one thread per element, the integrals of all its local basis
+//     products (tensor Gauss-Legendre, q per axis from the distance to the
+//     origin), eint[e * NL + c];
+//   k_gather: one thread per node, the sum of its elements' contributions in a
+//     fixed order.
+// Elements per axis: p = 0: e = k (one node); p = 1: [e h, (e+1) h], nodes e,
+// e+1; p = 2: [2e h, (2e+2) h], nodes 2e, 2e+1, 2e+2.
 // ---------------------------------------------------------------------------
-
-__device__ __forceinline__ int elem_first_node(int p, int e) { return p == 2 ? 2 * e : e; }
 
 // 1D element e of degree p: interval and the local basis function l (product form)
 __device__ AxisEl elem_axis(const WParams& P, int e, int l) {
@@ -552,140 +556,121 @@ __global__ void __launch_bounds__(256) k_near_elements(WParams P, int E, double*
   }
 }
 
-template <int D, int T>
-__global__ void __launch_bounds__(256) k_weights_tiled(WParams P, const double* __restrict__ near, int E,
-                                                       double* __restrict__ omega) {
-  constexpr int NL = 27;                       // max local basis products per element ((p+1)^d)
-  extern __shared__ __align__(16) double eint[];
-  const int p = P.p;
-  const int nloc1 = p + 1, nloc = (D == 2) ? nloc1 * nloc1 : nloc1 * nloc1 * nloc1;
-  const int64_t N1 = P.N + 1;
-  const int ne_axis = (p == 0) ? (int)N1 : (p == 1 ? (int)P.N : (int)(P.N / 2));
-  // tile origin (node indices) from the block index
-  int64_t bid = blockIdx.x;
-  const int64_t tiles_axis = (N1 + T - 1) / T;
-  int k0[3] = {0, 0, 0};
-  for (int i = 0; i < D; ++i) {
-    k0[i] = (int)(bid % tiles_axis) * T;
-    bid /= tiles_axis;
-  }
-  // element range per axis touching nodes [k0, k0 + T)
-  int e0[3], ecount[3];
-  for (int i = 0; i < D; ++i) {
-    const int lo_node = k0[i], hi_node = min((int)N1, k0[i] + T) - 1;
-    int ea, eb;
-    if (p == 0) { ea = lo_node; eb = hi_node; }
-    else if (p == 1) { ea = max(0, lo_node - 1); eb = min(ne_axis - 1, hi_node); }
-    else { ea = max(0, (lo_node - 1) / 2); eb = min(ne_axis - 1, hi_node / 2); }
-    e0[i] = ea;
-    ecount[i] = eb - ea + 1;
-  }
-  const int nelem = ecount[0] * ecount[1] * (D == 3 ? ecount[2] : 1);
-  // ---- phase 1: element integrals
-  for (int t = threadIdx.x; t < nelem; t += blockDim.x) {
-    int el[3] = {t % ecount[0] + e0[0], (t / ecount[0]) % ecount[1] + e0[1], D == 3 ? t / (ecount[0] * ecount[1]) + e0[2] : 0};
-    double acc[NL];
-    for (int c = 0; c < NL; ++c) acc[c] = 0.0;
-    bool origin = true;
+template <int D, int PD>
+__global__ void __launch_bounds__(256) k_elements(WParams P, int64_t ne, const double* __restrict__ near, int E,
+                                                  double* __restrict__ eint) {
+  constexpr int N1 = PD + 1, NL = (D == 2) ? N1 * N1 : N1 * N1 * N1, NW = (D == 2) ? N1 : N1 * N1;
+  const int64_t total = (D == 2) ? ne * ne : ne * ne * ne;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int el[3] = {(int)(t % ne), (int)((t / ne) % ne), D == 3 ? (int)(t / (ne * ne)) : 0};
+  double acc[NL];
+#pragma unroll
+  for (int c = 0; c < NL; ++c) acc[c] = 0.0;
+  bool in_near = true;
+#pragma unroll
+  for (int i = 0; i < D; ++i) in_near = in_near && el[i] < E;
+  if (in_near) {
+    const int64_t nidx = el[0] + E * (el[1] + (D == 3 ? E * el[2] : 0));
+#pragma unroll
+    for (int c = 0; c < NL; ++c)
+      for (int sp = 0; sp < kNearSplit; ++sp) acc[c] += near[(nidx * kNearSplit + sp) * NL + c];
+  } else {
+    AxisEl ax[3][N1];
     double lo2 = 0.0, width = 0.0;
-    AxisEl ax[3][3];
-    for (int i = 0; i < D; ++i)
-      for (int l = 0; l < nloc1; ++l) ax[i][l] = elem_axis(P, el[i], l);
+#pragma unroll
     for (int i = 0; i < D; ++i) {
-      origin = origin && el[i] == 0;
+#pragma unroll
+      for (int l = 0; l < N1; ++l) ax[i][l] = elem_axis(P, el[i], l);
       lo2 += ax[i][0].lo * ax[i][0].lo;
       width = fmax(width, ax[i][0].hi - ax[i][0].lo);
     }
-    bool in_near = true;
-    for (int i = 0; i < D; ++i) in_near = in_near && el[i] < E;
-    if (in_near) {
-      const int64_t ne = el[0] + E * (el[1] + (D == 3 ? E * el[2] : 0));
-      for (int c = 0; c < nloc; ++c) {
-        double v = 0.0;
-        for (int sp = 0; sp < kNearSplit; ++sp) v += near[(ne * kNearSplit + sp) * nloc + c];
-        acc[c] = v;
-      }
-    } else if (origin) {
-      (void)CHK(-1, 1);  // the origin element is always in the near block
-    } else {
-      const int rule = pick_rule(sqrt(lo2) / width);
-      const int q = rule_q(rule), off = rule_off(rule);
-      double X[3][20], Wb[3][3][20];
+    const int rule = pick_rule(sqrt(lo2) / width);
+    const int q = rule_q(rule), off = rule_off(rule);
+    if (CHK(q - 1, 20) && CHK(off + q - 1, kRuleTotal)) {
+      double cen[3], hw[3];
+#pragma unroll
       for (int i = 0; i < D; ++i) {
-        const double c = 0.5 * (ax[i][0].hi + ax[i][0].lo), hw = 0.5 * (ax[i][0].hi - ax[i][0].lo);
-        for (int g = 0; g < q; ++g) {
-          X[i][g] = c + hw * c_gl_x[off + g];
-          const double w = hw * c_gl_w[off + g];
-          for (int l = 0; l < nloc1; ++l) Wb[i][l][g] = w * basis_val(ax[i][l], X[i][g]);
-        }
+        cen[i] = 0.5 * (ax[i][0].hi + ax[i][0].lo);
+        hw[i] = 0.5 * (ax[i][0].hi - ax[i][0].lo);
       }
-      if (D == 2) {
+      // axis 0 (innermost): squared nodes and weighted basis values
+      double X0[20], W0[N1][20];
+      for (int g = 0; g < q; ++g) {
+        const double x = cen[0] + hw[0] * c_gl_x[off + g], w = hw[0] * c_gl_w[off + g];
+        X0[g] = x * x;
+#pragma unroll
+        for (int l = 0; l < N1; ++l) W0[l][g] = w * basis_val(ax[0][l], x);
+      }
+      for (int g2 = 0; g2 < (D == 3 ? q : 1); ++g2) {
+        double x2s = 0.0, wb2[N1];
+#pragma unroll
+        for (int l = 0; l < N1; ++l) wb2[l] = 1.0;
+        if (D == 3) {
+          const double x = cen[2] + hw[2] * c_gl_x[off + g2], w = hw[2] * c_gl_w[off + g2];
+          x2s = x * x;
+#pragma unroll
+          for (int l = 0; l < N1; ++l) wb2[l] = w * basis_val(ax[2][l], x);
+        }
         for (int g1 = 0; g1 < q; ++g1) {
-          const double x1 = X[1][g1] * X[1][g1];
+          const double x = cen[1] + hw[1] * c_gl_x[off + g1], w = hw[1] * c_gl_w[off + g1];
+          const double r12 = x * x + x2s;
+          double w21[NW];  // products of the outer axes' weighted basis values, (l2, l1) with l1 fastest
+#pragma unroll
+          for (int j = 0; j < NW; ++j) w21[j] = w * basis_val(ax[1][j % N1], x) * wb2[j / N1];
           for (int g0 = 0; g0 < q; ++g0) {
-            const double m = mu_r2(X[0][g0] * X[0][g0] + x1, P);
-            for (int l1 = 0; l1 < nloc1; ++l1) {
-              const double m1 = m * Wb[1][l1][g1];
-              for (int l0 = 0; l0 < nloc1; ++l0) acc[l1 * nloc1 + l0] += m1 * Wb[0][l0][g0];
-            }
-          }
-        }
-      } else {
-        for (int g2 = 0; g2 < q; ++g2) {
-          const double x2 = X[2][g2] * X[2][g2];
-          for (int g1 = 0; g1 < q; ++g1) {
-            const double x12 = X[1][g1] * X[1][g1] + x2;
-            for (int g0 = 0; g0 < q; ++g0) {
-              const double m = mu_r2(X[0][g0] * X[0][g0] + x12, P);
-              for (int l2 = 0; l2 < nloc1; ++l2) {
-                const double m2 = m * Wb[2][l2][g2];
-                for (int l1 = 0; l1 < nloc1; ++l1) {
-                  const double m1 = m2 * Wb[1][l1][g1];
-                  for (int l0 = 0; l0 < nloc1; ++l0) acc[(l2 * nloc1 + l1) * nloc1 + l0] += m1 * Wb[0][l0][g0];
-                }
-              }
+            const double m = mu_r2(X0[g0] + r12, P);
+#pragma unroll
+            for (int l0 = 0; l0 < N1; ++l0) {
+              const double ml = m * W0[l0][g0];
+#pragma unroll
+              for (int j = 0; j < NW; ++j) acc[j * N1 + l0] += ml * w21[j];
             }
           }
         }
       }
     }
-    for (int c = 0; c < nloc; ++c) eint[(int64_t)t * nloc + c] = acc[c];
   }
-  __syncthreads();
-  // ---- phase 2: nodes of the tile sum their element contributions
-  const int tnodes = (D == 2) ? T * T : T * T * T;
-  for (int t = threadIdx.x; t < tnodes; t += blockDim.x) {
-    int k[3] = {k0[0] + t % T, k0[1] + (t / T) % T, D == 3 ? k0[2] + t / (T * T) : 0};
-    bool inside = true;
-    for (int i = 0; i < D; ++i) inside = inside && k[i] < N1;
-    if (!inside) continue;
-    // per axis: elements containing node k and the local index of k in them
-    int ee[3][2], ll[3][2], ne[3] = {1, 1, 1};
-    for (int i = 0; i < D; ++i) {
-      ne[i] = 0;
-      if (p == 0) { ee[i][0] = k[i]; ll[i][0] = 0; ne[i] = 1; }
-      else if (p == 1) {
-        if (k[i] >= 1) { ee[i][ne[i]] = k[i] - 1; ll[i][ne[i]++] = 1; }
-        if (k[i] < P.N) { ee[i][ne[i]] = k[i]; ll[i][ne[i]++] = 0; }
-      } else {
-        if (k[i] & 1) { ee[i][0] = k[i] / 2; ll[i][0] = 1; ne[i] = 1; }
-        else {
-          if (k[i] >= 2) { ee[i][ne[i]] = k[i] / 2 - 1; ll[i][ne[i]++] = 2; }
-          if (k[i] <= P.N - 2) { ee[i][ne[i]] = k[i] / 2; ll[i][ne[i]++] = 0; }
-        }
+#pragma unroll
+  for (int c = 0; c < NL; ++c) eint[t * NL + c] = acc[c];
+}
+
+// omega_k = sum over the elements containing node k of the integral of k's local basis product
+template <int D>
+__global__ void k_gather(WParams P, int64_t ne, const double* __restrict__ eint, double* __restrict__ omega,
+                         int64_t count) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= count) return;
+  const int p = P.p, nl1 = p + 1, nloc = (D == 2) ? nl1 * nl1 : nl1 * nl1 * nl1;
+  const int64_t N1 = P.N + 1;
+  int64_t k[3] = {idx % N1, (idx / N1) % N1, D == 3 ? idx / (N1 * N1) : 0};
+  // per axis: elements containing node k and the local index of k in them
+  int64_t ee[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  int ll[3][2] = {{0, 0}, {0, 0}, {0, 0}}, nc[3] = {1, 1, 1};
+  for (int i = 0; i < D; ++i) {
+    nc[i] = 0;
+    if (p == 0) { ee[i][0] = k[i]; ll[i][0] = 0; nc[i] = 1; }
+    else if (p == 1) {
+      if (k[i] >= 1) { ee[i][nc[i]] = k[i] - 1; ll[i][nc[i]++] = 1; }
+      if (k[i] < P.N) { ee[i][nc[i]] = k[i]; ll[i][nc[i]++] = 0; }
+    } else {
+      if (k[i] & 1) { ee[i][0] = k[i] / 2; ll[i][0] = 1; nc[i] = 1; }
+      else {
+        if (k[i] >= 2) { ee[i][nc[i]] = k[i] / 2 - 1; ll[i][nc[i]++] = 2; }
+        if (k[i] <= P.N - 2) { ee[i][nc[i]] = k[i] / 2; ll[i][nc[i]++] = 0; }
       }
     }
-    double tot = 0.0;
-    for (int a = 0; a < ne[0]; ++a)
-      for (int b = 0; b < ne[1]; ++b)
-        for (int cc = 0; cc < (D == 3 ? ne[2] : 1); ++cc) {
-          const int le = (ee[0][a] - e0[0]) + ecount[0] * ((ee[1][b] - e0[1]) + (D == 3 ? ecount[1] * (ee[2][cc] - e0[2]) : 0));
-          const int lc = ll[0][a] + nloc1 * (ll[1][b] + (D == 3 ? nloc1 * ll[2][cc] : 0));
-          if (CHK(le, nelem) && CHK(lc, nloc)) tot += eint[(int64_t)le * nloc + lc];
-        }
-    int64_t idx = k[0] + N1 * (k[1] + (D == 3 ? N1 * k[2] : 0));
-    omega[idx] = tot;
   }
+  const int64_t total = (D == 2) ? ne * ne : ne * ne * ne;
+  double tot = 0.0;
+  for (int a = 0; a < nc[0]; ++a)
+    for (int b = 0; b < nc[1]; ++b)
+      for (int cc = 0; cc < (D == 3 ? nc[2] : 1); ++cc) {
+        const int64_t e = ee[0][a] + ne * (ee[1][b] + (D == 3 ? ne * ee[2][cc] : 0));
+        const int lc = ll[0][a] + nl1 * (ll[1][b] + (D == 3 ? nl1 * ll[2][cc] : 0));
+        if (CHK(e, total) && CHK(lc, nloc)) tot += eint[e * nloc + lc];
+      }
+  omega[idx] = tot;
 }
 
 // ---------------------------------------------------------------------------
@@ -735,27 +720,44 @@ __global__ void k_stencil(WParams P, const double* __restrict__ omega, double* _
 }
 
 // a_0 = -sum(partials) - 2^d F_d, Kahan-compensated, one block.
-__global__ void k_centre(const double* __restrict__ partial, int64_t nparts, double far_term, double* a) {
-  __shared__ double sh_s[1024], sh_c[1024];
-  double s = 0.0, c = 0.0;
-  for (int64_t i = threadIdx.x; i < nparts; i += blockDim.x) {
-    double y = CHK(i, nparts) ? partial[i] - c : 0.0;
-    double t = s + y;
+// Compensated sum of x[0..n) by the block (1024 threads): each thread a strided
+// Kahan sum, then the (sum, compensation) pairs merged in a fixed binary tree
+// (TwoSum of the sums, the compensations added).  Result in thread 0.
+__device__ double block_sum_compensated(const double* __restrict__ x, int64_t n, double* sh_s, double* sh_c) {
+  double s = 0.0, c = 0.0;  // value s - c
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double y = (CHK(i, n) ? x[i] : 0.0) - c;
+    const double t = s + y;
     c = (t - s) - y;
     s = t;
   }
   sh_s[threadIdx.x] = s;
   sh_c[threadIdx.x] = c;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double S = 0.0, C = 0.0;
-    for (int i = 0; i < (int)blockDim.x; ++i) {
-      double y = sh_s[i] - (C + sh_c[i]);
-      double t = S + y;
-      C = (t - S) - y;
-      S = t;
+  for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
+    if ((int)threadIdx.x < stride) {
+      const double a = sh_s[threadIdx.x], b = sh_s[threadIdx.x + stride];
+      const double t = a + b, bb = t - a, e = (a - (t - bb)) + (b - bb);  // t + e = a + b exactly
+      sh_s[threadIdx.x] = t;
+      sh_c[threadIdx.x] = sh_c[threadIdx.x] + sh_c[threadIdx.x + stride] - e;
     }
-    a[0] = -S - far_term;
+    __syncthreads();
+  }
+  const double r = sh_s[0] - sh_c[0];
+  __syncthreads();
+  return r;
+}
+
+// a_0 = -sum(partials) - 2^d F_d, F_d = sum of the far-field terms (also stored in far_out)
+__global__ void __launch_bounds__(1024) k_centre(const double* __restrict__ partial, int64_t nparts,
+                                                 const double* __restrict__ terms, int64_t nterms, int d, double* a,
+                                                 double* far_out) {
+  __shared__ double sh_s[1024], sh_c[1024];
+  const double S = block_sum_compensated(partial, nparts, sh_s, sh_c);
+  const double F = block_sum_compensated(terms, nterms, sh_s, sh_c);
+  if (threadIdx.x == 0) {
+    a[0] = -S - ldexp(F, d);
+    far_out[0] = F;
   }
 }
 
@@ -791,6 +793,8 @@ __global__ void k_gen_block(const double* __restrict__ a, double* __restrict__ o
 // along the line when B = 1), loads them in bit-reversed order into shared memory
 // (M x LB complex slots), runs log2 M in-place radix-2 stages with the FP64 twiddle
 // table tw[t] = e^{-2 pi i t / M}, and writes k in [0, K).
+constexpr int kSymFftMaxSmem = 8192 * (int)sizeof(double2);  // M x LB <= 8192 slots
+
 __global__ void __launch_bounds__(256) k_sym_fft(const double* __restrict__ in, double* __restrict__ out, int64_t A,
                                                  int64_t n, int64_t B, int64_t K, int logm, int LB,
                                                  const double2* __restrict__ tw) {
@@ -921,9 +925,8 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   const int d = pr.d;
   const int64_t ngen = op->ngen;
   const double L = op->N * pr.h;
-  op->far_field = far_field(d, pr.alpha, L, pr.lambda);
 
-  double *omega = nullptr, *partial = nullptr, *near = nullptr;
+  double *omega = nullptr, *partial = nullptr, *near = nullptr, *eint = nullptr;
   const int TB = 256;
   const int64_t nblk = ceil_div(ngen, TB);
   FRAC_CUDA_TRY(cudaMallocAsync(&omega, ngen * sizeof(double), st));
@@ -931,43 +934,59 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   if (d == 1) {
     k_weights_1d<<<(unsigned)nblk, TB, 0, st>>>(P, omega, ngen);
   } else {
-    // tiles of 16^2 / 8^3 nodes; shared memory = elements per tile x local products
-    const int T = d == 2 ? 16 : 8;
-    const int64_t tiles_axis = ceil_div(op->N + 1, T);
-    int64_t tiles = 1;
-    for (int i = 0; i < d; ++i) tiles *= tiles_axis;
-    const int ea = (pr.degree == 0) ? T : (pr.degree == 1 ? T + 1 : T / 2 + 2);
-    const int nl1 = pr.degree + 1;
-    size_t sm = sizeof(double);
-    for (int i = 0; i < d; ++i) sm *= (size_t)ea * nl1;
     // near-origin elements [0, E)^d first, spread over kNearSplit blocks each
     const int64_t ne_axis = pr.degree == 0 ? op->N + 1 : (pr.degree == 1 ? op->N : op->N / 2);
     const int E = (int)std::min<int64_t>(kNearE[d], ne_axis);
-    int64_t nnear = 1;
-    for (int i = 0; i < d; ++i) nnear *= E;
-    FRAC_CUDA_TRY(cudaMallocAsync(&near, (size_t)nnear * kNearSplit * 27 * sizeof(double), st));
-    const unsigned nb = (unsigned)(nnear * kNearSplit);
+    int64_t nnear = 1, nel = 1;
+    for (int i = 0; i < d; ++i) {
+      nnear *= E;
+      nel *= ne_axis;
+    }
+    const int nl1 = pr.degree + 1;
+    const int nloc = d == 2 ? nl1 * nl1 : nl1 * nl1 * nl1;
+    FRAC_CUDA_TRY(cudaMallocAsync(&near, (size_t)nnear * kNearSplit * nloc * sizeof(double), st));
+    FRAC_CUDA_TRY(cudaMallocAsync(&eint, (size_t)nel * nloc * sizeof(double), st));
+    const unsigned nb = (unsigned)(nnear * kNearSplit), eb = (unsigned)ceil_div(nel, 256);
     switch (d * 3 + pr.degree) {
-      case 6: k_near_elements<2, 0><<<nb, 256, 0, st>>>(P, E, near); break;
-      case 7: k_near_elements<2, 1><<<nb, 256, 0, st>>>(P, E, near); break;
-      case 8: k_near_elements<2, 2><<<nb, 256, 0, st>>>(P, E, near); break;
-      case 9: k_near_elements<3, 0><<<nb, 256, 0, st>>>(P, E, near); break;
-      case 10: k_near_elements<3, 1><<<nb, 256, 0, st>>>(P, E, near); break;
-      default: k_near_elements<3, 2><<<nb, 256, 0, st>>>(P, E, near); break;
+      case 6:
+        k_near_elements<2, 0><<<nb, 256, 0, st>>>(P, E, near);
+        k_elements<2, 0><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
+        break;
+      case 7:
+        k_near_elements<2, 1><<<nb, 256, 0, st>>>(P, E, near);
+        k_elements<2, 1><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
+        break;
+      case 8:
+        k_near_elements<2, 2><<<nb, 256, 0, st>>>(P, E, near);
+        k_elements<2, 2><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
+        break;
+      case 9:
+        k_near_elements<3, 0><<<nb, 256, 0, st>>>(P, E, near);
+        k_elements<3, 0><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
+        break;
+      case 10:
+        k_near_elements<3, 1><<<nb, 256, 0, st>>>(P, E, near);
+        k_elements<3, 1><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
+        break;
+      default:
+        k_near_elements<3, 2><<<nb, 256, 0, st>>>(P, E, near);
+        k_elements<3, 2><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
+        break;
     }
     FRAC_CUDA_TRY(cudaGetLastError());
-    if (d == 2) {
-      FRAC_CUDA_TRY(cudaFuncSetAttribute(k_weights_tiled<2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_weights_tiled<2, 16><<<(unsigned)tiles, 256, sm, st>>>(P, near, E, omega);
-    } else {
-      FRAC_CUDA_TRY(cudaFuncSetAttribute(k_weights_tiled<3, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-      k_weights_tiled<3, 8><<<(unsigned)tiles, 256, sm, st>>>(P, near, E, omega);
-    }
+    if (d == 2) k_gather<2><<<(unsigned)nblk, TB, 0, st>>>(P, ne_axis, eint, omega, ngen);
+    else k_gather<3><<<(unsigned)nblk, TB, 0, st>>>(P, ne_axis, eint, omega, ngen);
   }
   FRAC_CUDA_TRY(cudaGetLastError());
   k_stencil<<<(unsigned)nblk, TB, 0, st>>>(P, omega, op->a, partial, ngen);
   FRAC_CUDA_TRY(cudaGetLastError());
-  k_centre<<<1, 1024, 0, st>>>(partial, nblk, std::ldexp(op->far_field, d), op->a);
+  const int64_t nterms = (int64_t)(d == 1 ? 1 : (d == 2 ? 32 : 1024)) * kFarPanels;
+  double *terms = nullptr, *far_dev = nullptr;
+  FRAC_CUDA_TRY(cudaMallocAsync(&terms, (nterms + 1) * sizeof(double), st));
+  far_dev = terms + nterms;
+  k_far_terms<<<(unsigned)ceil_div(nterms, TB), TB, 0, st>>>(d, pr.alpha, pr.lambda, L, terms, nterms);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  k_centre<<<1, 1024, 0, st>>>(partial, nblk, terms, nterms, d, op->a, far_dev);
   FRAC_CUDA_TRY(cudaGetLastError());
 
   // symbol
@@ -992,7 +1011,8 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   // 2 LB lines per block, M x LB complex slots (64 KB; one 128 KB line at M = 8192)
   const int LB = (int)std::max<int64_t>(1, std::min<int64_t>(8, 4096 / M));
   const size_t fsm = (size_t)M * LB * sizeof(double2);
-  FRAC_CUDA_TRY(cudaFuncSetAttribute(k_sym_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+  // one value for every build (builds on several host threads must not lower it under one another)
+  FRAC_CUDA_TRY(cudaFuncSetAttribute(k_sym_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymFftMaxSmem));
   int64_t B = 1;
   for (int i = 0; i < d; ++i) {
     int64_t A = 1;
@@ -1023,8 +1043,11 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   FRAC_CUDA_TRY(cudaMemcpyAsync(hmin.data(), pmin, nb2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   FRAC_CUDA_TRY(cudaFreeAsync(pmin, st));
   FRAC_CUDA_TRY(cudaMemcpyAsync(&op->a0, op->a, sizeof(double), cudaMemcpyDeviceToHost, st));
+  FRAC_CUDA_TRY(cudaMemcpyAsync(&op->far_field, far_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
   FRAC_CUDA_TRY(cudaFreeAsync(omega, st));
   if (near) FRAC_CUDA_TRY(cudaFreeAsync(near, st));
+  if (eint) FRAC_CUDA_TRY(cudaFreeAsync(eint, st));
+  FRAC_CUDA_TRY(cudaFreeAsync(terms, st));
   FRAC_CUDA_TRY(cudaFreeAsync(partial, st));
   FRAC_CUDA_TRY(cudaFreeAsync(bufA, st));
   FRAC_CUDA_TRY(cudaFreeAsync(bufB, st));
