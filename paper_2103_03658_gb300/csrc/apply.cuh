@@ -26,6 +26,7 @@ struct CGState {
   double rz;      // r.z (= rr without preconditioner); alpha = rz / pq
   int it, maxit, done, status, pcg;
   unsigned int count_pq, count_rr, count_rz;  // arrival counters of the last-block reductions
+  int trips;      // loop-body executions in the current launch of a CG graph (reset by the host)
 };
 
 // coeffs.cu

@@ -224,12 +224,20 @@ static cudaStream_t graph_stream() {
   return per_dev[dev];
 }
 
-// CG iterations on A_T x = b for d >= 2, fused kernels, replayed as a CUDA graph
-// of kChunk iterations (captured on first use, kept in *exec for later calls with
-// the same buffers).  On entry r = b - A x, p holds any finite values and the
-// state was set by k_cg_start (beta = 0) and, preconditioned (z != nullptr), by
-// cg_precond_start.  Runs until the device state is done.
-constexpr int kChunk = 16;
+// CG iterations on A_T x = b for d >= 2, fused kernels, run as a CUDA graph whose
+// body (one iteration) sits in a device-side WHILE node: the loop guard kernel at
+// the end of the body keeps it going while the state is not done, for at most
+// kLoopTrips iterations per graph launch (so every launch ends by construction;
+// the host relaunches while the state is not done).  Captured on first use, kept
+// in *exec for later calls with the same buffers.  On entry r = b - A x, p holds
+// any finite values and the state was set by k_cg_start (beta = 0) and,
+// preconditioned (z != nullptr), by cg_precond_start.
+constexpr int kLoopTrips = 256;
+
+__global__ void k_loop_guard(CGState* st, cudaGraphConditionalHandle h) {
+  const int t = ++st->trips;
+  cudaGraphSetConditional(h, (!st->done && t < kLoopTrips) ? 1u : 0u);
+}
 
 // One (P)CG iteration: q = A p with p = (z or r) + beta p fused in, the x/r
 // update, and (z != nullptr) the preconditioner pass z = P r that sets beta.
@@ -252,6 +260,47 @@ static int cg_precond_start(const frac_op* op, T* r, T* p, T* z, void* apply_ws,
   return precond_cg_t<T>(op, r, z, apply_ws, dst, part_inv, s);
 }
 
+// Build the looping CG graph: [WHILE (condition set by k_loop_guard) { one iteration; k_loop_guard }].
+template <typename T>
+static int capture_cg_loop(const frac_op* op, T* x, T* r, T* p, T* q, T* z, void* apply_ws, CGState* dst,
+                           double* part_inv, double* part_upd, cudaStream_t s, cudaGraphExec_t* exec) {
+  cudaGraph_t g = nullptr;
+  FRAC_CUDA_TRY(cudaGraphCreate(&g, 0));
+  struct GFree {
+    cudaGraph_t g;
+    ~GFree() { cudaGraphDestroy(g); }
+  } gf{g};
+  cudaGraphConditionalHandle h;
+  FRAC_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  FRAC_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  FRAC_CUDA_TRY(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int st = cg_iteration<T>(op, x, r, p, q, z, apply_ws, dst, part_inv, part_upd, s);
+  if (st == FRAC_OK) {
+    k_loop_guard<<<1, 1, 0, s>>>(dst, h);
+    if (cudaPeekAtLastError() != cudaSuccess) st = FRAC_ECUDA;
+  }
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &captured);
+  if (st != FRAC_OK) return st;
+  FRAC_CUDA_TRY(e);
+  FRAC_CUDA_TRY(cudaGraphInstantiate(exec, g, 0));
+  return FRAC_OK;
+}
+
+// One launch of the looping CG graph (at most kLoopTrips iterations).
+static int launch_cg_loop(cudaGraphExec_t exec, CGState* dst, cudaStream_t s) {
+  FRAC_CUDA_TRY(cudaMemsetAsync(&dst->trips, 0, sizeof(int), s));
+  FRAC_CUDA_TRY(cudaGraphLaunch(exec, s));
+  return FRAC_OK;
+}
+
 template <typename T>
 static int cg_run_fused(const frac_op* op, T* x, T* r, T* p, T* q, T* z, void* apply_ws, CGState* dst, CGState* hst,
                         double* part_inv, double* part_upd, cudaGraphExec_t* exec, int* iters_total,
@@ -269,23 +318,13 @@ static int cg_run_fused(const frac_op* op, T* x, T* r, T* p, T* q, T* z, void* a
   if (!*exec) {
     // one plain iteration first: sets kernel attributes outside the capture
     FRAC_TRY(cg_iteration<T>(op, x, r, p, q, z, apply_ws, dst, part_inv, part_upd, gs));
-    cudaGraph_t g;
-    FRAC_CUDA_TRY(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
-    int s = FRAC_OK;
-    for (int c = 0; c < kChunk && s == FRAC_OK; ++c) s = cg_iteration<T>(op, x, r, p, q, z, apply_ws, dst, part_inv,
-                                                                         part_upd, gs);
-    cudaError_t e = cudaStreamEndCapture(gs, &g);
-    if (s != FRAC_OK) return s;
-    FRAC_CUDA_TRY(e);
-    e = cudaGraphInstantiate(exec, g, 0);
-    cudaGraphDestroy(g);
-    FRAC_CUDA_TRY(e);
+    FRAC_TRY(capture_cg_loop<T>(op, x, r, p, q, z, apply_ws, dst, part_inv, part_upd, gs, exec));
   }
   for (;;) {
     FRAC_CUDA_TRY(cudaMemcpyAsync(hst, dst, sizeof(CGState), cudaMemcpyDeviceToHost, gs));
     FRAC_CUDA_TRY(cudaStreamSynchronize(gs));
     if (hst->done) break;
-    FRAC_CUDA_TRY(cudaGraphLaunch(*exec, gs));
+    FRAC_TRY(launch_cg_loop(*exec, dst, gs));
   }
   FRAC_CUDA_TRY(cudaEventRecord(ev, gs));
   FRAC_CUDA_TRY(cudaStreamWaitEvent(caller, ev, 0));
@@ -608,19 +647,9 @@ template <typename T>
 int launch_chunk(Job* j, T* x, T* r, T* p, T* q, T* z, void* ws) {
   if (!j->exec) {
     FRAC_TRY(cg_iteration<T>(j->op, x, r, p, q, z, ws, j->st, j->part_inv, j->partial, j->s));
-    cudaGraph_t g;
-    FRAC_CUDA_TRY(cudaStreamBeginCapture(j->s, cudaStreamCaptureModeThreadLocal));
-    int s = FRAC_OK;
-    for (int c = 0; c < kChunk && s == FRAC_OK; ++c)
-      s = cg_iteration<T>(j->op, x, r, p, q, z, ws, j->st, j->part_inv, j->partial, j->s);
-    cudaError_t e = cudaStreamEndCapture(j->s, &g);
-    if (s != FRAC_OK) return s;
-    FRAC_CUDA_TRY(e);
-    e = cudaGraphInstantiate(&j->exec, g, 0);
-    cudaGraphDestroy(g);
-    FRAC_CUDA_TRY(e);
+    FRAC_TRY(capture_cg_loop<T>(j->op, x, r, p, q, z, ws, j->st, j->part_inv, j->partial, j->s, &j->exec));
   } else {
-    FRAC_CUDA_TRY(cudaGraphLaunch(j->exec, j->s));
+    FRAC_TRY(launch_cg_loop(j->exec, j->st, j->s));
   }
   FRAC_CUDA_TRY(cudaMemcpyAsync(&j->hm->st, j->st, sizeof(CGState), cudaMemcpyDeviceToHost, j->s));
   FRAC_CUDA_TRY(cudaEventRecord(j->ev, j->s));
