@@ -61,8 +61,9 @@ typedef struct frac_problem {
                        p = 2 needs an even number of intervals N_i = n_i + 1       */
   double alpha;     /* fractional power, 0 < alpha < 2                             */
   double h;         /* mesh size, > 0                                              */
-  int64_t n[3];     /* interior points per axis (N_i - 1); entries i >= d ignored;
-                       d >= 2 needs n_1 = n_2 (= n_3)                              */
+  int64_t n[3];     /* interior points per axis (N_i - 1); entries i >= d ignored.
+                       Unequal extents (a rectangular domain, Sec. 2.2) are allowed:
+                       the generator covers [0, L]^d with L = max_i N_i h        */
   double lambda;    /* tempering: kernel e^{-lambda |xi|} (Remark 2.2); 0 = (-Delta)^{alpha/2} */
 } frac_problem;
 
@@ -73,10 +74,12 @@ typedef struct frac_op_info_t {
   double a0;              /* centre coefficient a_0 (Eq. (1D-scheme), a_00 of Eq. (2D-scheme)) */
   double far_field;       /* F_d = int over R_+^d \ [0,L]^d of |xi|^{-d-alpha} e^{-lambda|xi|} */
   double norm_bound;      /* max_k |Lambda_k| = ||A||_2 (from the FP64 symbol)    */
-  int64_t fft_len;        /* M: circulant embedding length per axis (power of two >= 2n-1) */
-  int64_t n_gen;          /* N + 1: generator entries per axis                     */
+  int64_t fft_len;        /* M_1: circulant embedding length of axis 1 (power of two >= 2 n_1 - 1) */
+  int64_t n_gen;          /* N + 1: generator entries per axis, N = the largest N_i */
   size_t device_bytes;    /* device memory owned by the op                         */
-  int32_t precond_ok;     /* 1: the tau preconditioner applies (n <= M/2 - 1, positive symbol) */
+  int32_t precond_ok;     /* 1: the tau preconditioner applies (n_i <= M_i/2 - 1, positive symbol) */
+  int64_t n[3];           /* interior points per axis (1 for axes >= d)            */
+  int64_t fft_lens[3];    /* M_i per axis (1 for axes >= d)                        */
 } frac_op_info_t;
 
 /*
@@ -88,10 +91,10 @@ typedef struct frac_op_info_t {
  * Lambda = -c_{d,alpha} DFT_M(circulant embedding of a) (real, even), kept in
  * FP64 and FP32.  *out receives a new op (release with frac_op_free).
  * Errors: FRAC_EINVAL (d not in 1..3, alpha not in (0,2), degree not in 0..2,
- * n_i < 1, unequal n_i for d >= 2, odd N with degree 2, h <= 0 or non-finite,
+ * n_i < 1, an odd N_i with degree 2, h <= 0 or non-finite,
  * lambda < 0 or non-finite, out == NULL), FRAC_ENOTSUP (M beyond the FFT
- * sizes of this build: M <= 8192 for d = 1, <= 2048 for d = 2, <= 512 for
- * d = 3), FRAC_ENOMEM, FRAC_ECUDA.  Synchronises `stream` before returning.
+ * sizes of this build, per axis: M_i <= 8192 for d = 1, <= 2048 for d = 2,
+ * <= 512 for d = 3), FRAC_ENOMEM, FRAC_ECUDA.  Synchronises `stream` before returning.
  */
 int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream);
 

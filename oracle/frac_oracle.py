@@ -372,32 +372,37 @@ def stencil(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0,
     return a
 
 
-def toeplitz_matrix(a: np.ndarray, n: int) -> np.ndarray:
+def grid_shape(a: np.ndarray, n) -> tuple:
+    """The grid's array shape: (n,)*d for an int n, else the given shape (one extent per
+    array axis, C order; a rectangular grid of Sec. 2.2 with N_2 < N_1)."""
+    return (int(n),) * a.ndim if np.isscalar(n) else tuple(int(v) for v in n)
+
+
+def toeplitz_matrix(a: np.ndarray, n) -> np.ndarray:
     """Dense symmetric multilevel Toeplitz matrix T with T[i, j] = a[|i - j|]
-    (componentwise), rows/columns in C order of the (n,)*d grid
-    (A^{(1)} after Eq. (1D-scheme); A^{(2)} after Eq. (2D-scheme))."""
+    (componentwise), rows/columns in C order of the grid of shape grid_shape(a, n)
+    (A^{(1)} after Eq. (1D-scheme); A^{(2)} after Eq. (2D-scheme), block Toeplitz with
+    Toeplitz blocks also when N_2 < N_1)."""
     d = a.ndim
-    I = np.indices((n,) * d).reshape(d, -1)
+    I = np.indices(grid_shape(a, n)).reshape(d, -1)
     D = tuple(np.abs(I[i][:, None] - I[i][None, :]) for i in range(d))
     return a[D]
 
 
-def operator_matrix(a: np.ndarray, c: float, n: int) -> np.ndarray:
+def operator_matrix(a: np.ndarray, c: float, n) -> np.ndarray:
     """A = -c_{d,alpha} T(a)."""
     return -c * toeplitz_matrix(a, n)
 
 
 def apply_dense(a: np.ndarray, c: float, u: np.ndarray) -> np.ndarray:
     """y = A u with A = -c T(a), by the dense sum of the scheme (all rows)."""
-    n = u.shape[0]
-    return (operator_matrix(a, c, n) @ u.reshape(-1)).reshape(u.shape)
+    return (operator_matrix(a, c, u.shape) @ u.reshape(-1)).reshape(u.shape)
 
 
 def apply_rows(a: np.ndarray, c: float, u: np.ndarray, rows: np.ndarray) -> np.ndarray:
     """(A u)_i = -c sum_j a[|i - j|] u_j for the multi-indices i in ``rows`` (R, d)."""
     d = u.ndim
-    n = u.shape[0]
-    J = np.indices((n,) * d).reshape(d, -1)
+    J = np.indices(u.shape).reshape(d, -1)
     uf = u.reshape(-1)
     out = np.empty(len(rows))
     for t, r in enumerate(np.asarray(rows)):
@@ -406,12 +411,11 @@ def apply_rows(a: np.ndarray, c: float, u: np.ndarray, rows: np.ndarray) -> np.n
     return out
 
 
-def norm_bound(a: np.ndarray, c: float, n: int) -> float:
-    """c * sum over the offsets o in (-(n-1)..n-1)^d of |a_{|o|}|: the largest
-    absolute row sum bound, hence an upper bound of ||A||_2 for the (n,)*d grid;
-    used to normalise apply errors."""
-    d = a.ndim
-    sub = a[(slice(0, n),) * d]
+def norm_bound(a: np.ndarray, c: float, n) -> float:
+    """c * sum over the offsets o in (-(n_i-1)..n_i-1) per axis of |a_{|o|}|: the largest
+    absolute row sum bound, hence an upper bound of ||A||_2 for the grid of shape
+    grid_shape(a, n); used to normalise apply errors."""
+    sub = a[tuple(slice(0, v) for v in grid_shape(a, n))]
     K = np.indices(sub.shape)
     mult = 2.0 ** np.sum(K > 0, axis=0)
     return c * float(np.sum(mult * np.abs(sub)))
@@ -486,16 +490,14 @@ def boundary_vector(d: int, N: int, h: float, alpha: float, a: np.ndarray, c: fl
 
 def solve_dense(a: np.ndarray, c: float, rhs: np.ndarray) -> np.ndarray:
     """Solve A u = rhs by dense Cholesky (A is symmetric positive definite)."""
-    n = rhs.shape[0]
-    A = operator_matrix(a, c, n)
+    A = operator_matrix(a, c, rhs.shape)
     cf = linalg.cho_factor(A, lower=True)
     return linalg.cho_solve(cf, rhs.reshape(-1)).reshape(rhs.shape)
 
 
 def solve_cg(a: np.ndarray, c: float, rhs: np.ndarray, rtol: float = 1e-12, maxiter: int = 100000):
     """Plain conjugate gradients with the dense apply; returns (u, iterations)."""
-    n = rhs.shape[0]
-    A = operator_matrix(a, c, n)
+    A = operator_matrix(a, c, rhs.shape)
     b = rhs.reshape(-1)
     x = np.zeros_like(b)
     r = b.copy()
@@ -558,44 +560,46 @@ def tau_hankel_1d(t: np.ndarray) -> np.ndarray:
     return H
 
 
-def tau_symbol(a: np.ndarray, c: float, n: int, m: int) -> np.ndarray:
-    """Eigenvalues of -c tau(T_m) on k in [1..m]^d: the symbol of the generator
-    a (entries |j| <= n - 1 per axis, zero beyond) at theta_k = pi k / (m + 1)."""
+def tau_symbol(a: np.ndarray, c: float, n, m) -> np.ndarray:
+    """Eigenvalues of -c tau(T_m) on k in [1..m_i] per axis: the symbol of the generator
+    a (entries |j| <= n_i - 1 along axis i, zero beyond) at theta_k = pi k / (m_i + 1).
+    n, m: ints (every axis) or one extent per array axis."""
     d = a.ndim
-    k = np.arange(1, m + 1)
-    j = np.arange(0, n)
-    Cm = np.cos(np.pi * np.outer(k, j) / (m + 1))   # (m, n)
-    Cm[:, 1:] *= 2.0                                   # +-j folded
-    out = a[tuple(slice(0, n) for _ in range(d))].copy()
+    ns = grid_shape(a, n)
+    ms = grid_shape(a, m)
+    out = a[tuple(slice(0, v) for v in ns)].copy()
     for ax in range(d):
+        k = np.arange(1, ms[ax] + 1)
+        j = np.arange(0, ns[ax])
+        Cm = np.cos(np.pi * np.outer(k, j) / (ms[ax] + 1))   # (m_i, n_i)
+        Cm[:, 1:] *= 2.0                                       # +-j folded
         out = np.moveaxis(np.tensordot(Cm, np.moveaxis(out, ax, 0), axes=(1, 0)), 0, ax)
     return -c * out
 
 
-def tau_precond(a: np.ndarray, c: float, v: np.ndarray, m: int | None = None) -> np.ndarray:
-    """P v = R tau(T_m)^{-1} R^T v with m = M/2 - 1 (default), v of shape (n,)*d."""
-    n = v.shape[0]
+def tau_precond(a: np.ndarray, c: float, v: np.ndarray, m=None) -> np.ndarray:
+    """P v = R tau(T_m)^{-1} R^T v with m_i = M_i/2 - 1 per axis (default), v of the grid's shape."""
     d = v.ndim
-    if m is None:
-        m = fft_len(n) // 2 - 1
-    if m < n:
-        raise ValueError("tau system smaller than the problem (n is a power of two)")
-    S = sine_matrix(m)
-    w = np.zeros((m,) * d)
-    w[tuple(slice(0, n) for _ in range(d))] = v
+    ns = v.shape
+    ms = tuple(fft_len(x) // 2 - 1 for x in ns) if m is None else grid_shape(a, m)
+    if any(mi < ni for mi, ni in zip(ms, ns)):
+        raise ValueError("tau system smaller than the problem (an n_i is a power of two)")
+    w = np.zeros(ms)
+    w[tuple(slice(0, x) for x in ns)] = v
     for ax in range(d):
+        S = sine_matrix(ms[ax])
         w = np.moveaxis(np.tensordot(S, np.moveaxis(w, ax, 0), axes=(1, 0)), 0, ax)
-    w = w / tau_symbol(a, c, n, m)
+    w = w / tau_symbol(a, c, ns, ms)
     for ax in range(d):
+        S = sine_matrix(ms[ax])
         w = np.moveaxis(np.tensordot(S, np.moveaxis(w, ax, 0), axes=(1, 0)), 0, ax)
-    return w[tuple(slice(0, n) for _ in range(d))]
+    return w[tuple(slice(0, x) for x in ns)]
 
 
 def solve_pcg(a: np.ndarray, c: float, rhs: np.ndarray, rtol: float = 1e-12, maxiter: int = 100000):
     """Conjugate gradients preconditioned by tau_precond; stops on the true
     residual ||r|| <= rtol ||rhs||; returns (u, iterations)."""
-    n = rhs.shape[0]
-    A = operator_matrix(a, c, n)
+    A = operator_matrix(a, c, rhs.shape)
     b = rhs.reshape(-1)
     x = np.zeros_like(b)
     r = b.copy()

@@ -36,7 +36,8 @@ class Problem(ctypes.Structure):
 class OpInfo(ctypes.Structure):
     _fields_ = [("c_dalpha", ctypes.c_double), ("a0", ctypes.c_double), ("far_field", ctypes.c_double),
                 ("norm_bound", ctypes.c_double), ("fft_len", ctypes.c_int64), ("n_gen", ctypes.c_int64),
-                ("device_bytes", ctypes.c_size_t), ("precond_ok", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_size_t), ("precond_ok", ctypes.c_int32),
+                ("n", ctypes.c_int64 * 3), ("fft_lens", ctypes.c_int64 * 3)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -198,16 +199,24 @@ def _empty_like(x):
 
 
 class FracOp:
-    """Discretized (-Delta)^{alpha/2} (tempered when lam > 0) on (-1, 1)^d with n interior
-    points per axis, h = 2 / (n + 1) unless given; built on the current CUDA device."""
+    """Discretized (-Delta)^{alpha/2} (tempered when lam > 0) on a box with n interior points
+    per axis: n an int (the cube (-1, 1)^d) or a sequence (n_1, .., n_d) of per-axis counts,
+    axis 1 = x^(1) the fastest-varying (arrays have shape (n_d, .., n_1)).  h = 2 / (max n_i + 1)
+    unless given (the longest axis spans (-1, 1)); built on the current CUDA device."""
 
-    def __init__(self, d: int, n: int, alpha: float, degree: int = 1, lam: float = 0.0,
+    def __init__(self, d: int, n, alpha: float, degree: int = 1, lam: float = 0.0,
                  h: float | None = None, stream=None):
         lib = load()
         self._lib = lib
-        self.d, self.n, self.alpha, self.degree, self.lam = d, n, alpha, degree, lam
-        self.h = 2.0 / (n + 1) if h is None else h
-        self._prob = Problem(d, degree, alpha, self.h, (ctypes.c_int64 * 3)(n, n, n), lam)
+        ns = tuple(int(v) for v in n) if isinstance(n, (tuple, list)) else (int(n),) * d
+        if len(ns) != d:
+            raise ValueError(f"n has {len(ns)} entries for d = {d}")
+        self.d, self.alpha, self.degree, self.lam = d, alpha, degree, lam
+        self.n = ns[0] if len(set(ns)) == 1 else ns
+        self.ns = ns
+        self.nd = int(np.prod(ns))
+        self.h = 2.0 / (max(ns) + 1) if h is None else h
+        self._prob = Problem(d, degree, alpha, self.h, (ctypes.c_int64 * 3)(*(ns + (1,) * (3 - d))), lam)
         handle = ctypes.c_void_p()
         s = lib.frac_coeffs(ctypes.byref(self._prob), ctypes.byref(handle), _stream(stream))
         if s != 0:
@@ -232,17 +241,20 @@ class FracOp:
 
     @property
     def shape(self) -> tuple:
-        return (self.n,) * self.d
+        return tuple(reversed(self.ns))
 
     def info(self) -> dict:
         inf = OpInfo()
         s = self._lib.frac_op_info(self._h, ctypes.byref(inf))
         if s != 0:
             raise FracError(s, "frac_op_info")
-        return {k: getattr(inf, k) for k, _ in OpInfo._fields_}
+        out = {k: getattr(inf, k) for k, _ in OpInfo._fields_}
+        out["n"] = tuple(out["n"])[: self.d]
+        out["fft_lens"] = tuple(out["fft_lens"])[: self.d]
+        return out
 
     def generator(self) -> np.ndarray:
-        N1 = self.n + 2
+        N1 = max(self.ns) + 2
         a = np.empty((N1,) * self.d, dtype=np.float64)
         s = self._lib.frac_op_generator(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size)
         if s != 0:
@@ -251,12 +263,12 @@ class FracOp:
 
     # -- apply --
     def apply(self, u, out=None, stream=None):
-        """y = A u for u of shape (batch,) + (n,)*d or (n,)*d; float32 or float64."""
+        """y = A u for u of shape (batch,) + shape or shape; float32 or float64."""
         code = _dtype_code(u)
-        nd = self.n ** self.d
+        nd = self.nd
         numel = u.size if isinstance(u, np.ndarray) else u.numel()
         if numel % nd:
-            raise ValueError(f"size {numel} is not a multiple of n^d = {nd}")
+            raise ValueError(f"size {numel} is not a multiple of prod(n_i) = {nd}")
         y = _empty_like(u) if out is None else out
         s = self._lib.frac_apply(self._h, _ptr(u), _ptr(y), code, numel // nd, _stream(stream))
         if s != 0:
@@ -266,10 +278,10 @@ class FracOp:
     def precond(self, r, out=None, stream=None):
         """z = P r with the tau preconditioner (frac_precond); shapes and dtypes as apply."""
         code = _dtype_code(r)
-        nd = self.n ** self.d
+        nd = self.nd
         numel = r.size if isinstance(r, np.ndarray) else r.numel()
         if numel % nd:
-            raise ValueError(f"size {numel} is not a multiple of n^d = {nd}")
+            raise ValueError(f"size {numel} is not a multiple of prod(n_i) = {nd}")
         z = _empty_like(r) if out is None else out
         s = self._lib.frac_precond(self._h, _ptr(r), _ptr(z), code, numel // nd, _stream(stream))
         if s != 0:

@@ -68,9 +68,10 @@ static int validate(const frac_problem* p) {
   if (p->degree < 0 || p->degree > 2) return FRAC_EINVAL;
   if (!(p->h > 0.0) || !std::isfinite(p->h)) return FRAC_EINVAL;
   if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return FRAC_EINVAL;
-  for (int i = 0; i < p->d; ++i)
-    if (p->n[i] < 1 || p->n[i] != p->n[0]) return FRAC_EINVAL;
-  if (p->degree == 2 && ((p->n[0] + 1) % 2) != 0) return FRAC_EINVAL;
+  for (int i = 0; i < p->d; ++i) {
+    if (p->n[i] < 1) return FRAC_EINVAL;
+    if (p->degree == 2 && ((p->n[i] + 1) % 2) != 0) return FRAC_EINVAL;
+  }
   return FRAC_OK;
 }
 
@@ -128,26 +129,37 @@ int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
   FRAC_TRY(validate(prob));
   cudaStream_t st = (cudaStream_t)stream;
   const int d = prob->d;
-  const int64_t n = prob->n[0];
-  int64_t M = 2;
-  while (M < 2 * n - 1) M *= 2;
-  const int logm = ilog2(M);
-  if (logm > max_logm(d)) return FRAC_ENOTSUP;
+  int64_t Ma[3] = {1, 1, 1}, nmax = 0;
+  for (int i = 0; i < d; ++i) {
+    int64_t M = 2;
+    while (M < 2 * prob->n[i] - 1) M *= 2;
+    if (ilog2(M) > max_logm(d)) return FRAC_ENOTSUP;
+    Ma[i] = M;
+    nmax = std::max<int64_t>(nmax, prob->n[i]);
+  }
   FRAC_TRY(keep_pool_memory());
   frac_op* op = new (std::nothrow) frac_op();
   if (!op) return FRAC_ENOMEM;
   op->prob = *prob;
   for (int i = d; i < 3; ++i) op->prob.n[i] = 1;
-  op->N = n + 1;
-  op->n = n;
-  op->M = M;
-  op->logm = logm;
-  op->K = M / 2 + 1;
+  op->square = 1;
+  for (int i = 0; i < 3; ++i) {
+    op->na[i] = i < d ? prob->n[i] : 1;
+    op->Ma[i] = Ma[i];
+    op->Ka[i] = i < d ? Ma[i] / 2 + 1 : 1;
+    op->logma[i] = i < d ? ilog2(Ma[i]) : 0;
+    if (i < d && prob->n[i] != prob->n[0]) op->square = 0;
+  }
+  op->N = nmax + 1;  // the generator covers [0, L]^d with L the largest extent
+  op->n = op->na[0];
+  op->M = op->Ma[0];
+  op->logm = op->logma[0];
+  op->K = op->Ka[0];
   op->nd = op->ngen = op->nsym = 1;
   for (int i = 0; i < d; ++i) {
-    op->nd *= n;
+    op->nd *= op->na[i];
     op->ngen *= (op->N + 1);
-    op->nsym *= op->K;
+    op->nsym *= op->Ka[i];
   }
   op->c = c_dalpha(d, prob->alpha);
   cudaGetDevice(&op->device);
@@ -161,7 +173,7 @@ int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
     cudaGetLastError();
     s = FRAC_ENOMEM;
   }
-  if (s == FRAC_OK) s = prepare_twiddles(logm);
+  for (int i = 0; i < d && s == FRAC_OK; ++i) s = prepare_twiddles(op->logma[i]);
   if (s == FRAC_OK) s = build_coefficients(op, st);
   if (s != FRAC_OK) {
     frac_op_free(op);
@@ -191,6 +203,10 @@ int frac_op_info(const frac_op* op, frac_op_info_t* info) {
   info->n_gen = op->N + 1;
   info->device_bytes = op->device_bytes;
   info->precond_ok = op->precond_ok;
+  for (int i = 0; i < 3; ++i) {
+    info->n[i] = op->na[i];
+    info->fft_lens[i] = op->Ma[i];
+  }
   return FRAC_OK;
 }
 

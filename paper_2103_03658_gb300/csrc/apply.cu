@@ -26,8 +26,8 @@ template int apply_t<float>(const frac_op*, const float*, float*, int64_t, void*
 template int apply_t<double>(const frac_op*, const double*, double*, int64_t, void*, cudaStream_t);
 
 size_t apply_cg_partials(const frac_op* op) {
-  int64_t nrows = op->n;
-  for (int i = 2; i < op->prob.d; ++i) nrows *= op->n;
+  int64_t nrows = 1;  // rows of one field: the extents of the axes after the row axis
+  for (int i = 1; i < op->prob.d; ++i) nrows *= op->na[i];
   const int64_t a = rows_grid_any<float>(op->logm, nrows), b = rows_grid_any<double>(op->logm, nrows);
   return (size_t)(a > b ? a : b);
 }

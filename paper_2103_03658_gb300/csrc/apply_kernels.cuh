@@ -157,7 +157,7 @@ enum RowKind { RF_PLAIN = 0, RF_CG = 1, RF_ODD = 2, RI_PLAIN = 0, RI_CG = 1, RI_
 
 template <typename T, int LOGM, int LINES, int KIND>
 __global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
-k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int64_t nrows, int KB,
+k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int ns, int64_t nrows, int KB,
            const cplx_t<T>* __restrict__ tw, const T* __restrict__ r, const CGState* st) {
   using C = cplx_t<T>;
   constexpr int TPL = tpl(LOGM), LS = line_stride(LOGM);
@@ -175,16 +175,16 @@ k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int64_t nrows, int KB,
           p[row * n + x] = v;
           return v;
         },
-        W, n, nrows, KB, tw, pair, sm + line * LS, tl);
+        W, n, nrows, KB, tw, pair, sm + line * LS, tl, ns);
   } else {
     row_fwd_pair<T, LOGM, KIND == RF_ODD>([&](int64_t row, int x) { return u[row * n + x]; }, W, n, nrows, KB, tw,
-                                          pair, sm + line * LS, tl);
+                                          pair, sm + line * LS, tl, ns);
   }
 }
 
 template <typename T, int LOGM, int LINES, int KIND>
 __global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
-k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nrows, int KB,
+k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int ns, int64_t nrows, int KB,
            const cplx_t<T>* __restrict__ tw, const T* __restrict__ p, CGState* st, double* partials) {
   using C = cplx_t<T>;
   constexpr int TPL = tpl(LOGM), LS = line_stride(LOGM);
@@ -199,7 +199,7 @@ k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int64_t nr
   row_inv_pair<T, LOGM, ODD>(W, n, nrows, KB, tw, pair, sm + line * LS, tl, [&](int64_t row, int x, T v) {
     y[row * n + x] = v;
     if (CG) dot += v * p[row * n + x];
-  });
+  }, ns);
   if constexpr (KIND == RI_CG) {
     double* red = reinterpret_cast<double*>(smem_raw);  // the FFT lines are no longer needed
     const double total = block_sum_all(dot, red);
@@ -295,7 +295,7 @@ struct CgArgs {
 };
 
 template <typename T, int LOGM, int KIND>
-static int launch_rows_fwd(const void* in, void* out, int64_t n, int64_t nrows, int KB, const CgArgs& cg,
+static int launch_rows_fwd(const void* in, void* out, int64_t n, int64_t ns, int64_t nrows, int KB, const CgArgs& cg,
                            cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int L = Cfg<T, LOGM>::ROW_LINES;
@@ -306,14 +306,14 @@ static int launch_rows_fwd(const void* in, void* out, int64_t n, int64_t nrows, 
   prof::Scope ps(kname<T>(nb, names[KIND], LOGM), st);
   auto kern = k_rows_fwd<T, LOGM, L, KIND>;
   FRAC_TRY(set_smem(kern, sm));
-  kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const T*)in, (C*)out, (int)n, nrows, KB,
+  kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const T*)in, (C*)out, (int)n, (int)ns, nrows, KB,
                                                              tw_table<T>(LOGM), (const T*)cg.r, cg.st);
   FRAC_CUDA_TRY(cudaGetLastError());
   return FRAC_OK;
 }
 
 template <typename T, int LOGM, int KIND>
-static int launch_rows_inv(const void* in, void* out, int64_t n, int64_t nrows, int KB, const CgArgs& cg,
+static int launch_rows_inv(const void* in, void* out, int64_t n, int64_t ns, int64_t nrows, int KB, const CgArgs& cg,
                            cudaStream_t st) {
   using C = cplx_t<T>;
   constexpr int L = Cfg<T, LOGM>::ROW_LINES;
@@ -324,7 +324,7 @@ static int launch_rows_inv(const void* in, void* out, int64_t n, int64_t nrows, 
   prof::Scope ps(kname<T>(nb, names[KIND], LOGM), st);
   auto kern = k_rows_inv<T, LOGM, L, KIND>;
   FRAC_TRY(set_smem(kern, sm));
-  kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const C*)in, (T*)out, (int)n, nrows, KB,
+  kern<<<(unsigned)cdiv(pairs, L), L * tpl(LOGM), sm, st>>>((const C*)in, (T*)out, (int)n, (int)ns, nrows, KB,
                                                              tw_table<T>(LOGM), (const T*)cg.p, cg.st, cg.partials);
   FRAC_CUDA_TRY(cudaGetLastError());
   return FRAC_OK;
@@ -378,14 +378,14 @@ static int conv1d_any(int logm, const T* u, T* y, int64_t n, int64_t batch, cons
   FRAC_DISPATCH_LOGM(logm, 1, 13, (launch_conv1d<T, LG, ODD>(u, y, n, batch, lam, st)));
 }
 template <typename T, int KIND>
-static int rows_fwd_any(int logm, const void* in, void* out, int64_t n, int64_t nrows, int KB, cudaStream_t st,
-                        const CgArgs& cg) {
-  FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_rows_fwd<T, LG, KIND>(in, out, n, nrows, KB, cg, st)));
+static int rows_fwd_any(int logm, const void* in, void* out, int64_t n, int64_t ns, int64_t nrows, int KB,
+                        cudaStream_t st, const CgArgs& cg) {
+  FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_rows_fwd<T, LG, KIND>(in, out, n, ns, nrows, KB, cg, st)));
 }
 template <typename T, int KIND>
-static int rows_inv_any(int logm, const void* in, void* out, int64_t n, int64_t nrows, int KB, cudaStream_t st,
-                        const CgArgs& cg) {
-  FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_rows_inv<T, LG, KIND>(in, out, n, nrows, KB, cg, st)));
+static int rows_inv_any(int logm, const void* in, void* out, int64_t n, int64_t ns, int64_t nrows, int KB,
+                        cudaStream_t st, const CgArgs& cg) {
+  FRAC_DISPATCH_LOGM(logm, 1, 11, (launch_rows_inv<T, LG, KIND>(in, out, n, ns, nrows, KB, cg, st)));
 }
 template <typename T>
 static int64_t rows_grid_any(int logm, int64_t nrows) {
@@ -414,16 +414,19 @@ static int cols_any(int logm, const void* in, void* out, const ColArgs& A, int64
   }
 }
 
+// Spectrum layout for d >= 2 (axis i: n_i points, FFT length M_i, K_i = M_i/2 + 1;
+// axis 0 = x^(1) is the row axis): W1 holds the rows' half spectra column-blocked,
+// slabs of n_2 rows (KB = ceil(K_1 / B) blocks); d = 3: W2 holds the y transform,
+// per field M_2 x KB column blocks of n_3 rows.
 template <typename T>
 static void layout(const frac_op* op, int64_t batch, int64_t& KB, int64_t& w1, int64_t& w2) {
   constexpr int B = blk<T>();
-  const int64_t n = op->n, M = op->M, K = op->K;
-  KB = cdiv(K, B);
+  KB = cdiv(op->Ka[0], B);
   w1 = w2 = 0;
-  if (op->prob.d == 2) w1 = batch * KB * n * B;
+  if (op->prob.d == 2) w1 = batch * KB * op->na[1] * B;
   if (op->prob.d == 3) {
-    w1 = batch * n * KB * n * B;
-    w2 = batch * M * KB * n * B;
+    w1 = batch * op->na[2] * KB * op->na[1] * B;
+    w2 = batch * op->Ma[1] * KB * op->na[2] * B;
   }
 }
 
@@ -433,28 +436,28 @@ template <typename T, int FK, int IK, bool ODD>
 static int pipeline(const frac_op* op, const T* lam, const void* in, void* out, int64_t batch, void* ws,
                     const CgArgs& fwd, const CgArgs& inv, const CGState* cgst, cudaStream_t st) {
   using C = cplx_t<T>;
-  const int d = op->prob.d, logm = op->logm;
-  const int64_t n = op->n, M = op->M, K = op->K;
+  const int d = op->prob.d;
+  const int64_t n1 = op->na[0], n2 = op->na[1], n3 = op->na[2], K1 = op->Ka[0];
   int64_t KB, w1, w2;
   layout<T>(op, batch, KB, w1, w2);
   C* W1 = (C*)ws;
   if (d == 2) {
-    const int64_t nrows = batch * n;
-    FRAC_TRY((rows_fwd_any<T, FK>(logm, in, W1, n, nrows, (int)KB, st, fwd)));
-    ColArgs A{(int)n, (int)K, (int)KB, KB, batch};
-    FRAC_TRY((cols_any<T, SYM2, ODD>(logm, W1, W1, A, batch, lam, st, cgst)));
-    FRAC_TRY((rows_inv_any<T, IK>(logm, W1, out, n, nrows, (int)KB, st, inv)));
+    const int64_t nrows = batch * n2;
+    FRAC_TRY((rows_fwd_any<T, FK>(op->logma[0], in, W1, n1, n2, nrows, (int)KB, st, fwd)));
+    ColArgs A{(int)n2, (int)K1, (int)KB, KB, batch};
+    FRAC_TRY((cols_any<T, SYM2, ODD>(op->logma[1], W1, W1, A, batch, lam, st, cgst)));
+    FRAC_TRY((rows_inv_any<T, IK>(op->logma[0], W1, out, n1, n2, nrows, (int)KB, st, inv)));
     return FRAC_OK;
   }
   C* W2 = W1 + w1;
-  const int64_t nrows = batch * n * n;
-  FRAC_TRY((rows_fwd_any<T, FK>(logm, in, W1, n, nrows, (int)KB, st, fwd)));
-  ColArgs Ay{(int)n, (int)K, (int)KB, KB, batch};
-  FRAC_TRY((cols_any<T, YFWD, ODD>(logm, W1, W2, Ay, batch * n, lam, st, cgst)));
-  ColArgs Az{(int)n, (int)K, (int)KB, M * KB, batch};
-  FRAC_TRY((cols_any<T, ZSYM, ODD>(logm, W2, W2, Az, batch, lam, st, cgst)));
-  FRAC_TRY((cols_any<T, YINV, ODD>(logm, W2, W1, Ay, batch * n, lam, st, cgst)));
-  FRAC_TRY((rows_inv_any<T, IK>(logm, W1, out, n, nrows, (int)KB, st, inv)));
+  const int64_t nrows = batch * n3 * n2;
+  FRAC_TRY((rows_fwd_any<T, FK>(op->logma[0], in, W1, n1, n2, nrows, (int)KB, st, fwd)));
+  ColArgs Ay{(int)n2, (int)K1, (int)KB, KB, batch, (int)n3, (int)op->Ma[1], (int)op->Ka[1]};
+  FRAC_TRY((cols_any<T, YFWD, ODD>(op->logma[1], W1, W2, Ay, batch * n3, lam, st, cgst)));
+  ColArgs Az{(int)n3, (int)K1, (int)KB, op->Ma[1] * KB, batch, (int)n3, (int)op->Ma[1], (int)op->Ka[1]};
+  FRAC_TRY((cols_any<T, ZSYM, ODD>(op->logma[2], W2, W2, Az, batch, lam, st, cgst)));
+  FRAC_TRY((cols_any<T, YINV, ODD>(op->logma[1], W2, W1, Ay, batch * n3, lam, st, cgst)));
+  FRAC_TRY((rows_inv_any<T, IK>(op->logma[0], W1, out, n1, n2, nrows, (int)KB, st, inv)));
   return FRAC_OK;
 }
 

@@ -653,7 +653,7 @@ double simulate(const std::vector<Item>& items, const std::map<int, ClassTiming>
 }  // namespace
 
 bool batch2d_eligible(const frac_op* op, const frac_solve_opts* opts) {
-  return op->prob.d == 2 && opts->precision == FRAC_MIXED_IR && op->logm >= kBatch2dMinLog &&
+  return op->prob.d == 2 && op->square && opts->precision == FRAC_MIXED_IR && op->logm >= kBatch2dMinLog &&
          op->logm <= kBatch2dMaxLog;
 }
 

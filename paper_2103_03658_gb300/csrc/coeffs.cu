@@ -767,15 +767,16 @@ __global__ void __launch_bounds__(1024) k_centre(const double* __restrict__ part
 // w_0 = 1, w_j = 2; computed axis by axis, k in [0, M/2].
 // ---------------------------------------------------------------------------
 
-// compact copy of the [0, n)^d block of the generator
-__global__ void k_gen_block(const double* __restrict__ a, double* __restrict__ out, int d, int64_t N1, int64_t n,
-                            int64_t count) {
+// compact copy of the [0, n_1) x .. x [0, n_d) block of the generator
+__global__ void k_gen_block(const double* __restrict__ a, double* __restrict__ out, int d, int64_t N1, int64_t n0,
+                            int64_t n1, int64_t n2, int64_t count) {
   int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= count) return;
   int64_t rem = idx, src = 0, mul = 1;
   for (int i = 0; i < d; ++i) {
-    int64_t ki = rem % n;
-    rem /= n;
+    const int64_t ni = i == 0 ? n0 : (i == 1 ? n1 : n2);
+    const int64_t ki = rem % ni;
+    rem /= ni;
     src += ki * mul;
     mul *= N1;
   }
@@ -873,7 +874,8 @@ __global__ void k_scale_symbol(const double* __restrict__ raw, double* __restric
 // 0 or M/2 (the odd extension has no spectrum there); per-block minimum of the
 // stored symbol over the other entries for the positivity check.
 __global__ void k_precond_symbol(const double* __restrict__ l64, double* __restrict__ p64, float* __restrict__ p32,
-                                 int64_t K, int d, double s2, int64_t count, double* __restrict__ partial_min) {
+                                 int64_t K0, int64_t K1, int64_t K2, int d, double s2, int64_t count,
+                                 double* __restrict__ partial_min) {
   __shared__ double sh[32];
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double m = INFINITY;
@@ -881,6 +883,7 @@ __global__ void k_precond_symbol(const double* __restrict__ l64, double* __restr
     int64_t r = idx;
     bool edge = false;
     for (int i = 0; i < d; ++i) {
+      const int64_t K = i == 0 ? K0 : (i == 1 ? K1 : K2);
       const int64_t k = r % K;
       r /= K;
       edge = edge || k == 0 || k == K - 1;
@@ -912,7 +915,7 @@ static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int build_coefficients(frac_op* op, cudaStream_t st) {
   FRAC_TRY(upload_rules());
-  FRAC_TRY(ensure_twiddles(op->logm));
+  for (int i = 0; i < op->prob.d; ++i) FRAC_TRY(ensure_twiddles(op->logma[i]));
   const frac_problem& pr = op->prob;
   WParams P;
   P.d = pr.d;
@@ -989,43 +992,43 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   k_centre<<<1, 1024, 0, st>>>(partial, nblk, terms, nterms, d, op->a, far_dev);
   FRAC_CUDA_TRY(cudaGetLastError());
 
-  // symbol
-  const int64_t n = op->n, K = op->K, M = op->M;
+  // symbol: axis by axis, shape (A, n_i, B) -> (A, K_i, B) with A = prod_{j > i} n_j, B = prod_{j < i} K_j
   int64_t sz = 1;
-  for (int i = 0; i < d; ++i) sz *= n;
+  for (int i = 0; i < d; ++i) sz *= op->na[i];
   int64_t maxsz = sz;
   {
     int64_t s = sz;
     for (int i = 0; i < d; ++i) {
-      s = s / n * K;
+      s = s / op->na[i] * op->Ka[i];
       if (s > maxsz) maxsz = s;
     }
   }
   double *bufA = nullptr, *bufB = nullptr;
   FRAC_CUDA_TRY(cudaMallocAsync(&bufA, maxsz * sizeof(double), st));
   FRAC_CUDA_TRY(cudaMallocAsync(&bufB, maxsz * sizeof(double), st));
-  k_gen_block<<<(unsigned)ceil_div(sz, TB), TB, 0, st>>>(op->a, bufA, d, op->N + 1, n, sz);
+  k_gen_block<<<(unsigned)ceil_div(sz, TB), TB, 0, st>>>(op->a, bufA, d, op->N + 1, op->na[0], op->na[1], op->na[2],
+                                                          sz);
   FRAC_CUDA_TRY(cudaGetLastError());
-  const double2* tw = twiddles64(op->logm);
-  // pass over axis i (0 = fastest): shape (A, n, B) with B = K^i, A = n^{d-1-i};
-  // 2 LB lines per block, M x LB complex slots (64 KB; one 128 KB line at M = 8192)
-  const int LB = (int)std::max<int64_t>(1, std::min<int64_t>(8, 4096 / M));
-  const size_t fsm = (size_t)M * LB * sizeof(double2);
   // one value for every build (builds on several host threads must not lower it under one another)
   FRAC_CUDA_TRY(cudaFuncSetAttribute(k_sym_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymFftMaxSmem));
   int64_t B = 1;
   for (int i = 0; i < d; ++i) {
     int64_t A = 1;
-    for (int j = i + 1; j < d; ++j) A *= n;
-    k_sym_fft<<<(unsigned)ceil_div(A * B, 2 * LB), 256, fsm, st>>>(bufA, bufB, A, n, B, K, op->logm, LB, tw);
+    for (int j = i + 1; j < d; ++j) A *= op->na[j];
+    const int64_t Mi = op->Ma[i];
+    // 2 LB lines per block, M x LB complex slots (64 KB; one 128 KB line at M = 8192)
+    const int LB = (int)std::max<int64_t>(1, std::min<int64_t>(8, 4096 / Mi));
+    const size_t fsm = (size_t)Mi * LB * sizeof(double2);
+    k_sym_fft<<<(unsigned)ceil_div(A * B, 2 * LB), 256, fsm, st>>>(bufA, bufB, A, op->na[i], B, op->Ka[i],
+                                                                     op->logma[i], LB, twiddles64(op->logma[i]));
     FRAC_CUDA_TRY(cudaGetLastError());
     std::swap(bufA, bufB);
-    B *= K;
+    B *= op->Ka[i];
   }
   // bufA holds Lambda_raw on [0, K)^d
   const int64_t ns = op->nsym;
   double Md = 1.0;
-  for (int i = 0; i < d; ++i) Md *= (double)M;
+  for (int i = 0; i < d; ++i) Md *= (double)op->Ma[i];
   const double scale = -op->c / (d == 1 ? Md : 2.0 * Md);
   const int64_t nb2 = ceil_div(ns, TB);
   double* pmax = nullptr;
@@ -1036,8 +1039,9 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   FRAC_CUDA_TRY(cudaMemcpyAsync(hmax.data(), pmax, nb2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   double* pmin = nullptr;
   FRAC_CUDA_TRY(cudaMallocAsync(&pmin, nb2 * sizeof(double), st));
-  const double s2 = d == 1 ? (double)M * (double)M : (2.0 * Md) * (2.0 * Md);
-  k_precond_symbol<<<(unsigned)nb2, TB, 0, st>>>(op->lam64, op->pinv64, op->pinv32, K, d, s2, ns, pmin);
+  const double s2 = d == 1 ? Md * Md : (2.0 * Md) * (2.0 * Md);
+  k_precond_symbol<<<(unsigned)nb2, TB, 0, st>>>(op->lam64, op->pinv64, op->pinv32, op->Ka[0], op->Ka[1], op->Ka[2], d,
+                                                 s2, ns, pmin);
   FRAC_CUDA_TRY(cudaGetLastError());
   std::vector<double> hmin(nb2);
   FRAC_CUDA_TRY(cudaMemcpyAsync(hmin.data(), pmin, nb2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1069,7 +1073,9 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   op->norm_bound = op->c * m;
   double mn = INFINITY;
   for (double v : hmin) mn = v < mn ? v : mn;
-  op->precond_ok = (n <= M / 2 - 1) && mn > 0.0 ? 1 : 0;
+  bool fits = true;
+  for (int i = 0; i < d; ++i) fits = fits && op->na[i] <= op->Ma[i] / 2 - 1;
+  op->precond_ok = fits && mn > 0.0 ? 1 : 0;
   return FRAC_OK;
 }
 

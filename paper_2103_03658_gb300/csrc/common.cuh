@@ -59,24 +59,29 @@ const float2* twiddles32(int logm);
 // Opaque operator object of the C ABI.
 struct frac_op {
   frac_problem prob;
-  int64_t N;         // intervals per axis
-  int64_t n;         // interior points per axis
-  int64_t M;         // FFT length per axis
+  int64_t N;         // intervals per axis of the generator cube [0, L]^d, L = N h = the largest extent
+  int64_t n;         // interior points, FFT length, log2 and M/2 + 1 of axis 0 (x^(1), fastest);
+  int64_t M;         //   the same on every axis of a square grid
   int logm;
-  int64_t K;         // M / 2 + 1
-  int64_t nd;        // n^d grid values
+  int64_t K;
+  int64_t na[3];     // per axis i < d: interior points n_i (1 for i >= d)
+  int64_t Ma[3];     // FFT length M_i = nextpow2(2 n_i - 1), >= 2 (1 for i >= d)
+  int64_t Ka[3];     // M_i / 2 + 1 (1 for i >= d)
+  int logma[3];      // log2 M_i (0 for i >= d)
+  int square;        // n_i equal on every axis
+  int64_t nd;        // prod n_i grid values
   int64_t ngen;      // (N + 1)^d generator entries
-  int64_t nsym;      // K^d symbol entries
+  int64_t nsym;      // prod K_i symbol entries, axis 0 fastest
   double c;          // c_{d,alpha}
   double a0;
   double far_field;
   double norm_bound;
   double* a;         // device, (N+1)^d FP64 generator
-  double* lam64;     // device, K^d FP64 scaled symbol
-  float* lam32;      // device, K^d FP32 scaled symbol
-  double* pinv64;    // device, K^d FP64 symbol of the tau preconditioner (0 where k_i is 0 or M/2)
-  float* pinv32;     // device, K^d FP32 copy
-  int precond_ok;    // n <= M/2 - 1 and the symbol is positive: the tau preconditioner applies
+  double* lam64;     // device, prod K_i FP64 scaled symbol
+  float* lam32;      // device, prod K_i FP32 scaled symbol
+  double* pinv64;    // device, prod K_i FP64 symbol of the tau preconditioner (0 where some k_i is 0 or M_i/2)
+  float* pinv32;     // device, prod K_i FP32 copy
+  int precond_ok;    // n_i <= M_i/2 - 1 on every axis and the symbol is positive: the tau preconditioner applies
   size_t device_bytes;
   int device;
 };

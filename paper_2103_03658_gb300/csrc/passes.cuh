@@ -28,8 +28,8 @@ namespace frac {
 
 template <typename T> __host__ __device__ constexpr int blk() { return 32 / (int)sizeof(cplx_t<T>); }
 
-// column-blocked layout, slabs of n rows, KB = ceil(K / B) blocks per slab:
-// entry (row, k) at rowbase(row) + (k / B) n B + k % B
+// column-blocked layout, slabs of n rows (n: the extent of the next axis),
+// KB = ceil(K / B) blocks per slab: entry (row, k) at rowbase(row) + (k / B) n B + k % B
 template <int B>
 __device__ __forceinline__ int64_t wrow(int64_t row, int n, int KB) {
   const int64_t slab = row / n, r = row - slab * n;
@@ -64,7 +64,7 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
 template <typename T, int LOGM, bool ODD = false, typename In>
 __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t nrows, int KB,
                                              const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
-                                             int tl) {
+                                             int tl, int ns = 0) {
   using C = cplx_t<T>;
   using namespace fft;
   constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), B = blk<T>();
@@ -105,11 +105,12 @@ __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t
 #pragma unroll
   for (int e = E / 2; e < E; ++e) buf[pidx(tl + e * TPL)] = v[e];
   __syncthreads();
-  C* W0 = W + wrow<B>(h0 ? r0 : 0, n, KB);
-  C* W1 = W + wrow<B>(h1 ? r1 : 0, n, KB);
+  if (ns <= 0) ns = n;  // rows per slab of W (the next axis' extent; n on square grids)
+  C* W0 = W + wrow<B>(h0 ? r0 : 0, ns, KB);
+  C* W1 = W + wrow<B>(h1 ? r1 : 0, ns, KB);
   auto emit = [&](int k, C z, C zc) {
     const C s = cadd(z, zc), dd = csub(z, zc);
-    const int64_t kc = wcol<B>(k, n);
+    const int64_t kc = wcol<B>(k, ns);
     if (h0) W0[kc] = s;
     if (h1) W1[kc] = C{dd.y, -dd.x};
   };
@@ -129,21 +130,22 @@ __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t
 template <typename T, int LOGM, bool ODD = false, typename Out>
 __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t nrows, int KB,
                                              const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
-                                             int tl, Out out) {
+                                             int tl, Out out, int ns = 0) {
   using C = cplx_t<T>;
   using namespace fft;
   constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), B = blk<T>();
   const int64_t r0 = 2 * pair, r1 = r0 + 1;
   const bool h0 = r0 < nrows, h1 = r1 < nrows;
   C v[E];
-  const C* W0 = W + wrow<B>(h0 ? r0 : 0, n, KB);
-  const C* W1 = W + wrow<B>(h1 ? r1 : 0, n, KB);
+  if (ns <= 0) ns = n;  // rows per slab of W
+  const C* W0 = W + wrow<B>(h0 ? r0 : 0, ns, KB);
+  const C* W1 = W + wrow<B>(h1 ? r1 : 0, ns, KB);
   // line z = W0 + i W1 extended Hermitian-wise: z[x] = W0[x] + i W1[x] and
   // z[M-x] = conj(W0[x]) + i conj(W1[x]) for x in [0, M/2], so each half
   // spectrum entry is read once; the thread that reads W[x] leaves z[M-x] in
   // the line buffer for its owner
   auto load = [&](int x, C& lo, C& hi) {
-    const int64_t kc = wcol<B>(x, n);
+    const int64_t kc = wcol<B>(x, ns);
     const C v0 = h0 ? W0[kc] : C{0, 0};
     const C v1 = h1 ? W1[kc] : C{0, 0};
     lo = C{v0.x - v1.y, v0.y + v1.x};  // v0 + i v1
@@ -206,9 +208,11 @@ __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t 
 enum ColMode { SYM2 = 0, YFWD = 1, ZSYM = 2, YINV = 3 };
 
 struct ColArgs {
-  int n, K, KB;      // interior points, symbol extent M/2+1, column blocks per W1 slab
+  int n, K, KB;      // interior points along this pass's axis, k1 extent K_1 = M_1/2+1, column blocks per slab
   int64_t tiles;     // column tiles per slab
   int64_t nb;        // batch (fields)
+  int nz = 0;        // d = 3: z extent n_3 (slabs (b, j3) of W1; rows j3 of a W2 column block)
+  int My = 0, Ky = 0;  // d = 3: y FFT length M_2 and its symbol extent K_2 = M_2/2+1
 };
 
 template <typename T, int LOGM, int MODE, bool ODD = false>
@@ -220,8 +224,9 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
   constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride_tile(LOGM), B = blk<T>();
   C* buf = sm + cl * LS;
   const int n = A.n, K = A.K, KB = A.KB, Kp = KB * B;
-  const int64_t nB = (int64_t)n * B;
-  const int64_t W2slab = (int64_t)M * KB * nB;  // one field of W2
+  const int64_t nB = (int64_t)n * B;              // W1 slab rows (SYM2, YFWD, YINV: j2) / W2 rows (ZSYM: j3)
+  const int64_t zB = (int64_t)A.nz * B;           // W2 rows per column block (j3)
+  const int64_t W2slab = (int64_t)A.My * KB * zB;  // one field of W2
   C v[E];
   // ---- column identity and load
   int k1 = 0, k2r = 0;
@@ -233,16 +238,16 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
     const int64_t c = tile * B + cl;
     const int k2 = (int)(c / Kp);
     k1 = (int)(c % Kp);
-    k2r = k2 <= M / 2 ? k2 : M - k2;
+    k2r = k2 <= A.My / 2 ? k2 : A.My - k2;
     live = k1 < K;
   }
   if (MODE == YINV) {
-    const int64_t b = o / n, j3 = o % n;
-    const C* src = in + b * W2slab + tile * nB + j3 * B + cl;
+    const int64_t b = o / A.nz, j3 = o % A.nz;
+    const C* src = in + b * W2slab + tile * zB + j3 * B + cl;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k2 = tl + e * TPL;
-      v[e] = live ? src[(int64_t)k2 * KB * nB] : C{0, 0};
+      v[e] = live ? src[(int64_t)k2 * KB * zB] : C{0, 0};
     }
   } else if constexpr (!ODD) {
     const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl : in + (o * KB + tile) * nB + cl;
@@ -270,7 +275,7 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
   if (MODE != YINV) fft_reg<C, LOGM, false, !ODD, false>(v, buf, tl, tw);
   if (MODE == SYM2 || MODE == ZSYM) {
     const T* lrow = (MODE == SYM2) ? lam + k1 : lam + (int64_t)k2r * K + k1;
-    const int64_t kstride = (MODE == SYM2) ? K : (int64_t)K * K;
+    const int64_t kstride = (MODE == SYM2) ? K : (int64_t)A.Ky * K;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = tl + e * TPL;
@@ -282,12 +287,12 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
   // ---- store
   if (!live) return;
   if (MODE == YFWD) {
-    const int64_t b = o / n, j3 = o % n;
-    C* dst = out + b * W2slab + tile * nB + j3 * B + cl;
+    const int64_t b = o / A.nz, j3 = o % A.nz;
+    C* dst = out + b * W2slab + tile * zB + j3 * B + cl;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k2 = tl + e * TPL;
-      dst[(int64_t)k2 * KB * nB] = v[e];
+      dst[(int64_t)k2 * KB * zB] = v[e];
     }
   } else {
     C* dst = (MODE == ZSYM) ? out + o * W2slab + tile * nB + cl

@@ -38,10 +38,13 @@ def test_invalid_problems_rejected_before_any_device_work(lib):
         out = ctypes.c_void_p()
         assert lib.frac_coeffs(ctypes.byref(prob), ctypes.byref(out), None) == 1, b
         assert not out.value
-    # unequal extents in 2D
-    prob = nat.Problem(2, 1, 1.0, 0.25, (ctypes.c_int64 * 3)(7, 5, 1), 0.0)
-    out = ctypes.c_void_p()
-    assert lib.frac_coeffs(ctypes.byref(prob), ctypes.byref(out), None) == 1
+    # rectangular grids (unequal extents) are valid; a bad extent on any axis is not: an
+    # empty second axis, and an odd N_2 with the quadratic basis
+    for n3, degree in (((7, 0, 1), 1), ((7, 6, 1), 2), ((5, 5, 0), 0)):
+        prob = nat.Problem(2 if n3[2] == 1 else 3, degree, 1.0, 0.25, (ctypes.c_int64 * 3)(*n3), 0.0)
+        out = ctypes.c_void_p()
+        assert lib.frac_coeffs(ctypes.byref(prob), ctypes.byref(out), None) == 1, n3
+        assert not out.value
 
 
 def test_null_arguments(lib):
