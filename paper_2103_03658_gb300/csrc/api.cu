@@ -1,6 +1,7 @@
 // C ABI entry points (include/frac.h): argument validation, operator
 // lifecycle, staging of host buffers, dispatch to the device kernels.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -218,6 +219,110 @@ int frac_op_generator(const frac_op* op, double* a, size_t count) {
 
 }  // extern "C"
 
+// Library streams per device for the host-buffer pipeline below.
+constexpr int kCopyStreams = 3;
+static int copy_streams(cudaStream_t* out) {
+  static std::mutex mu;
+  static std::vector<std::vector<cudaStream_t>> per_dev;
+  int dev = 0;
+  FRAC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1);
+  if (per_dev[dev].empty()) {
+    for (int i = 0; i < kCopyStreams; ++i) {
+      cudaStream_t s;
+      FRAC_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      per_dev[dev].push_back(s);
+    }
+  }
+  for (int i = 0; i < kCopyStreams; ++i) out[i] = per_dev[dev][i];
+  return FRAC_OK;
+}
+
+static int run_apply(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* ws, bool precond,
+                     cudaStream_t st) {
+  if (precond)
+    return dtype == FRAC_F64 ? precond_t<double>(op, (const double*)u, (double*)y, batch, ws, st)
+                             : precond_t<float>(op, (const float*)u, (float*)y, batch, ws, st);
+  return dtype == FRAC_F64 ? apply_t<double>(op, (const double*)u, (double*)y, batch, ws, st)
+                           : apply_t<float>(op, (const float*)u, (float*)y, batch, ws, st);
+}
+
+// Host input and output, several fields: chunks of fields go round-robin to the
+// library's copy streams, each doing host-to-device copy, apply and device-to-host
+// copy of its chunk, so that the copies of one chunk overlap the other chunks' copies
+// (the two directions use separate copy engines) and compute.  Chunks of at least
+// kPipeChunkBytes keep the copies and the passes efficient (28 MB: the best of a sweep from 12 to
+// 70 MB on the 65-field 1023^2 FP32 apply, 29.3 GDOF/s end to end against 18.6 unpipelined).  Returns after the last
+// copy has landed.
+constexpr size_t kPipeChunkBytes = 28u << 20;
+static size_t pipe_chunk_bytes() {  // FRAC_PIPE_CHUNK_MB overrides the chunk size (tuning), read once
+  static const size_t v = [] {
+    const char* e = std::getenv("FRAC_PIPE_CHUNK_MB");
+    const long long mb = e ? std::atoll(e) : 0;
+    return mb > 0 ? (size_t)mb << 20 : kPipeChunkBytes;
+  }();
+  return v;
+}
+static int apply_host_pipelined(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, bool precond,
+                                cudaStream_t st) {
+  const size_t es = dtype == FRAC_F64 ? sizeof(double) : sizeof(float);
+  const size_t fb = (size_t)op->nd * es;
+  int64_t nch = std::min<int64_t>(batch, std::max<int64_t>(1, (int64_t)((batch * fb) / pipe_chunk_bytes())));
+  nch = std::min<int64_t>(nch, 16);
+  const int64_t per = (batch + nch - 1) / nch;
+  nch = (batch + per - 1) / per;
+  cudaStream_t ss[kCopyStreams];
+  FRAC_TRY(copy_streams(ss));
+  const int ns = (int)std::min<int64_t>(kCopyStreams, nch);
+  cudaEvent_t fork = nullptr, join[kCopyStreams] = {};
+  struct EvFree {
+    cudaEvent_t* f;
+    cudaEvent_t* j;
+    ~EvFree() {
+      if (*f) cudaEventDestroy(*f);
+      for (int i = 0; i < kCopyStreams; ++i)
+        if (j[i]) cudaEventDestroy(j[i]);
+    }
+  } evf{&fork, join};
+  FRAC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  FRAC_CUDA_TRY(cudaEventRecord(fork, st));
+  // per stream: device input, output and workspace for one chunk
+  void* bufs[kCopyStreams][3] = {};
+  const size_t wsb = apply_workspace_bytes(op, dtype, per);
+  int s = FRAC_OK;
+  for (int i = 0; i < ns && s == FRAC_OK; ++i) {
+    if (cudaStreamWaitEvent(ss[i], fork, 0) != cudaSuccess ||
+        cudaMallocAsync(&bufs[i][0], per * fb, ss[i]) != cudaSuccess ||
+        cudaMallocAsync(&bufs[i][1], per * fb, ss[i]) != cudaSuccess ||
+        (wsb && cudaMallocAsync(&bufs[i][2], wsb, ss[i]) != cudaSuccess))
+      s = FRAC_ENOMEM;
+  }
+  for (int64_t c = 0; c < nch && s == FRAC_OK; ++c) {
+    const int i = (int)(c % ns);
+    const int64_t b0 = c * per, nb = std::min<int64_t>(per, batch - b0);
+    const char* src = (const char*)u + b0 * fb;
+    char* dst = (char*)y + b0 * fb;
+    if (cudaMemcpyAsync(bufs[i][0], src, nb * fb, cudaMemcpyHostToDevice, ss[i]) != cudaSuccess) {
+      s = FRAC_ECUDA;
+      break;
+    }
+    s = run_apply(op, bufs[i][0], bufs[i][1], dtype, nb, bufs[i][2], precond, ss[i]);
+    if (s == FRAC_OK && cudaMemcpyAsync(dst, bufs[i][1], nb * fb, cudaMemcpyDeviceToHost, ss[i]) != cudaSuccess)
+      s = FRAC_ECUDA;
+  }
+  for (int i = 0; i < ns; ++i) {
+    for (int k = 0; k < 3; ++k)
+      if (bufs[i][k]) cudaFreeAsync(bufs[i][k], ss[i]);
+    if (cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventRecord(join[i], ss[i]) == cudaSuccess)
+      cudaStreamWaitEvent(st, join[i], 0);
+  }
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (s == FRAC_OK && e != cudaSuccess) s = FRAC_ECUDA;
+  return s;
+}
+
 // frac_apply (precond = false) and frac_precond (precond = true): device or host buffers.
 static int apply_entry(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* stream,
                        bool precond) {
@@ -230,6 +335,8 @@ static int apply_entry(const frac_op* op, const void* u, void* y, int dtype, int
   const size_t bytes = (size_t)batch * op->nd * es;
   const bool du = is_device_ptr(u), dy = is_device_ptr(y);
   if ((du && ((uintptr_t)u % es)) || (dy && ((uintptr_t)y % es))) return FRAC_EINVAL;
+  if (!du && !dy && batch >= 2 && bytes >= 2 * pipe_chunk_bytes())
+    return apply_host_pipelined(op, u, y, dtype, batch, precond, st);
   void* ws = nullptr;
   const size_t wsb = apply_workspace_bytes(op, dtype, batch);
   if (wsb) FRAC_CUDA_TRY(cudaMallocAsync(&ws, wsb, st));
