@@ -8,7 +8,7 @@
  * T(a) the symmetric multilevel Toeplitz matrix with generator a_k,
  * k in {0..N}^d, built from the weight integrals omega_k^p of Lagrange
  * bases of degree p (Eq. (wi-1D), Eq. (2D-scheme0)), splitting parameter
- * gamma = 2.
+ * gamma in (alpha, 2] (default 2).
  *
  * Conventions for every entry point:
  *   - Grid vectors are C-ordered arrays of shape [n3][n2][n1] (d = 3),
@@ -65,6 +65,8 @@ typedef struct frac_problem {
                        Unequal extents (a rectangular domain, Sec. 2.2) are allowed:
                        the generator covers [0, L]^d with L = max_i N_i h        */
   double lambda;    /* tempering: kernel e^{-lambda |xi|} (Remark 2.2); 0 = (-Delta)^{alpha/2} */
+  double gamma;     /* splitting parameter of Eq. (eq0) in (alpha, 2]; 0 means 2 (the default and
+                       the most accurate, Sec. 3.1); below 2 the origin term drops (zeta = 0) */
 } frac_problem;
 
 typedef struct frac_op frac_op;  /* opaque, immutable after frac_coeffs, shareable across streams */
@@ -91,7 +93,7 @@ typedef struct frac_op_info_t {
  * Lambda = -c_{d,alpha} DFT_M(circulant embedding of a) (real, even), kept in
  * FP64 and FP32.  *out receives a new op (release with frac_op_free).
  * Errors: FRAC_EINVAL (d not in 1..3, alpha not in (0,2), degree not in 0..2,
- * n_i < 1, an odd N_i with degree 2, h <= 0 or non-finite,
+ * n_i < 1, an odd N_i with degree 2, h <= 0 or non-finite, gamma not 0 and not in (alpha, 2],
  * lambda < 0 or non-finite, out == NULL), FRAC_ENOTSUP (M beyond the FFT
  * sizes of this build, per axis: M_i <= 8192 for d = 1, <= 2048 for d = 2,
  * <= 512 for d = 3), FRAC_ENOMEM, FRAC_ECUDA.  Synchronises `stream` before returning.

@@ -4,8 +4,9 @@ tempered form on uniform grids of (-1, 1)^d, d = 1, 2, 3.
 TEST INFRASTRUCTURE ONLY (see the package docstring): the product never
 imports this module.
 
-Notation follows Section 2 of the paper.  gamma = 2 (the splitting parameter
-used in all of Section 3), so zeta = floor(gamma / 2) = 1.  N intervals per
+Notation follows Section 2 of the paper.  The splitting parameter gamma in
+(alpha, 2] defaults to 2 (used in all of Section 3), zeta = floor(gamma / 2):
+1 at gamma = 2, 0 below (Eq. (gamma2)).  N intervals per
 axis, h = L / N, n = N - 1 interior points per axis; arrays of grid values
 have shape (n,) * d.  The operator is symmetric under permutations of the
 axes (the weights are, and so is every rule below), so the axis order of an
@@ -36,7 +37,9 @@ import math
 import numpy as np
 from scipy import integrate, linalg, special
 
-ZETA = 1  # floor(gamma / 2) with gamma = 2
+def zeta(gamma: float) -> int:
+    """zeta = floor(gamma / 2) (after Eq. (L1h)): 1 for gamma = 2, 0 for gamma in (alpha, 2)."""
+    return int(math.floor(gamma / 2.0))
 
 
 # ---------------------------------------------------------------------------
@@ -144,24 +147,24 @@ def _eval_local(loc, x):
     return np.array(out)
 
 
-def _origin_block(d, alpha, lam, H, loc, qs=24):
-    """int over [0, H]^d of prod_i phi_{l_i}(xi_i) |xi|^{2-d-alpha} exp(-lambda |xi|),
+def _origin_block(d, alpha, lam, H, loc, qs=24, gamma=2.0):
+    """int over [0, H]^d of prod_i phi_{l_i}(xi_i) |xi|^{gamma-d-alpha} exp(-lambda |xi|),
     for every choice (l_1..l_d) of local basis functions on the origin element.
 
     Duffy split into the d pyramids {xi_i = max_j xi_j}: xi = r (s with s_i = 1),
     Jacobian r^{d-1}, |xi| = r c(s), c = sqrt(1 + |s|^2); the radial factor is
-    r^{1-alpha} times a polynomial in r times exp(-lambda c r), integrated
+    r^{gamma-1-alpha} times a polynomial in r times exp(-lambda c r), integrated
     exactly (incomplete gamma); the s-integral uses Gauss-Legendre.
     """
     nloc = len(loc)
     polys = [scale * np.poly(np.array(roots, dtype=np.float64))[::-1] if roots else np.array([scale])
              for _, roots, scale in loc]  # ascending monomial coefficients in xi
-    beta = d + alpha - 2.0
+    beta = d + alpha - gamma
     out = np.zeros((nloc,) * d)
     if d == 1:
         for l in range(nloc):
             for m, cm in enumerate(polys[l]):
-                out[l] += cm * _radial_moment(2.0 - alpha + m, np.array([lam]), H)[0]
+                out[l] += cm * _radial_moment(gamma - alpha + m, np.array([lam]), H)[0]
         return out
     xs, ws = special.roots_legendre(qs)
     s1, w1 = 0.5 * (xs + 1.0), 0.5 * ws
@@ -170,7 +173,7 @@ def _origin_block(d, alpha, lam, H, loc, qs=24):
     Wq = np.prod(np.meshgrid(*([w1] * (d - 1)), indexing="ij"), axis=0).reshape(-1)
     cs = np.sqrt(1.0 + np.sum(S * S, axis=1))
     maxdeg = sum(len(pl) - 1 for pl in polys[:1]) * d
-    R = np.stack([_radial_moment(2.0 - alpha + m, lam * cs, H) for m in range(maxdeg + 1)], axis=1)
+    R = np.stack([_radial_moment(gamma - alpha + m, lam * cs, H) for m in range(maxdeg + 1)], axis=1)
     base = Wq * cs ** (-beta)                                          # (Q,)
     for i in range(d):                                                 # pyramid: axis i is the largest
         coords = []
@@ -200,11 +203,12 @@ def _gauss_points(lo, hi, q):
     return 0.5 * (hi - lo) * xs + 0.5 * (hi + lo), 0.5 * (hi - lo) * ws
 
 
-def weights(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0, q: int = 20) -> np.ndarray:
+def weights(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0, q: int = 20,
+            gamma: float = 2.0) -> np.ndarray:
     """omega_k^p for every k in {0..N}^d (Eq. (wi-1D); Eq. (2D-scheme0); Remark 2.2 for lambda > 0).
 
     omega_k = int over [0, L]^d of prod_i phi_{k_i}(xi_i) mu(xi) dxi with
-    mu(xi) = |xi|^{2-d-alpha} exp(-lambda |xi|), summed element by element:
+    mu(xi) = |xi|^{gamma-d-alpha} exp(-lambda |xi|) (mu_gamma of Eq. (eq0)), summed element by element:
     the origin element by ``_origin_block``; every other element, where the
     integrand is smooth, by a q^d-point tensor Gauss-Legendre rule.
     """
@@ -235,11 +239,11 @@ def weights(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0, q:
         shape = [ne] + [1] * (d - 1) + [q]
         r2 = r2 + (X ** 2).reshape(shape)
         r = np.sqrt(r2)
-        Mu = r ** (2.0 - d - alpha) * np.exp(-lam * r)
+        Mu = r ** (gamma - d - alpha) * np.exp(-lam * r)
         ops = [WB[e] for e in outer] + [WB, Mu]
         C = np.einsum(spec, *ops)                                     # (ne, nloc.., nloc)
         if all(e == 0 for e in outer):
-            C[0] = _origin_block(d, alpha, lam, H0, els[0][2])
+            C[0] = _origin_block(d, alpha, lam, H0, els[0][2], gamma=gamma)
         idx = []
         for i, e in enumerate(outer):
             shape = [1] * (d + 1)
@@ -252,7 +256,8 @@ def weights(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0, q:
     return omega
 
 
-def weights_at(d: int, N: int, h: float, alpha: float, p: int, lam: float, nodes, q: int = 20) -> np.ndarray:
+def weights_at(d: int, N: int, h: float, alpha: float, p: int, lam: float, nodes, q: int = 20,
+               gamma: float = 2.0) -> np.ndarray:
     """omega_k^p for the multi-indices in ``nodes`` only (same integrals as
     ``weights``: origin element by ``_origin_block``, the others by tensor
     Gauss-Legendre), for sizes where the whole generator is out of reach."""
@@ -261,7 +266,7 @@ def weights_at(d: int, N: int, h: float, alpha: float, p: int, lam: float, nodes
     for e, (_, _, loc) in enumerate(els):
         for l, (nd, _, _) in enumerate(loc):
             owner[nd].append((e, l))
-    origin = _origin_block(d, alpha, lam, els[0][1], els[0][2])
+    origin = _origin_block(d, alpha, lam, els[0][1], els[0][2], gamma=gamma)
     xs, ws = special.roots_legendre(q)
     out = np.empty(len(nodes))
     for t, k in enumerate(nodes):
@@ -283,19 +288,19 @@ def weights_at(d: int, N: int, h: float, alpha: float, p: int, lam: float, nodes
                 r2 = r2 + (x * x).reshape(shape)
                 wb = wb * w.reshape(shape)
             r = np.sqrt(r2)
-            tot += float(np.sum(wb * r ** (2.0 - d - alpha) * np.exp(-lam * r)))
+            tot += float(np.sum(wb * r ** (gamma - d - alpha) * np.exp(-lam * r)))
         out[t] = tot
     return out
 
 
-def weights_1d_appendix(N: int, h: float, alpha: float, p: int) -> np.ndarray:
-    """Closed forms of the Appendix for omega_k^p, 1D, lambda = 0, gamma = 2.
+def weights_1d_appendix(N: int, h: float, alpha: float, p: int, gamma: float = 2.0) -> np.ndarray:
+    """Closed forms of the Appendix for omega_k^p, 1D, lambda = 0, sigma_0 = gamma - alpha.
 
     p = 2, even 0 < k < N and k = N: uses xi_{k-3/2}, xi_{k+3/2} and
     xi_{N-3/2} where the paper prints xi_{k-1/2}, xi_{k+1/2}, xi_{N-3/4}
     (the printed forms disagree with Eq. (wi-1D); the corrected ones agree).
     """
-    s0 = 2.0 - alpha
+    s0 = gamma - alpha
     s1, s2 = s0 + 1.0, s0 + 2.0
     xi = lambda t: t * h  # noqa: E731
     w = np.zeros(N + 1)
@@ -341,32 +346,35 @@ ORIGIN_RULE = {0: (1.0,), 1: (1.0,), 2: (4.0 / 3.0, -1.0 / 3.0)}
 
 
 def stencil(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0,
-            omega: np.ndarray | None = None, q: int = 20) -> np.ndarray:
+            omega: np.ndarray | None = None, q: int = 20, gamma: float = 2.0) -> np.ndarray:
     """Generator a_k, k in {0..N}^d, of the scheme; a[(0,)*d] holds a_0.
 
-    * k != 0: a_k = 2^{z(k)} omega_k / |xi_k|^2, z(k) = number of zero entries
+    * k != 0: a_k = 2^{z(k)} omega_k / |xi_k|^gamma, z(k) = number of zero entries
       of k (each distinct neighbour x + s o xi_k appears 2^{z(k)} times in the
       sum over m in varkappa_1 of Eq. (eq0)).
     * origin term: zeta omega_0 Phi(x, xi_0) ~ zeta omega_0 (1/d) sum_i sum_j
       e_j Phi(x, j h e_i), which adds 2^{d-1} zeta e_j omega_0 / (d (j h)^2)
-      to a_{j e_i}.
+      to a_{j e_i} (gamma = 2 only: zeta = 0 below, Eq. (gamma2)).
     * a_0 = -sum_{k != 0} 2^{d-z(k)} a_k - 2^d F_d  (Eq. (1D-scheme): a_0;
       Eq. (2D-scheme): a_00).
     """
     if omega is None:
-        omega = weights(d, N, h, alpha, p, lam, q=q)
+        omega = weights(d, N, h, alpha, p, lam, q=q, gamma=gamma)
     K = np.indices((N + 1,) * d)
     k2 = np.sum(K * K, axis=0)
     z = np.sum(K == 0, axis=0)
     nz = k2 > 0
     a = np.zeros_like(omega)
-    a[nz] = 2.0 ** z[nz] * omega[nz] / (h * h * k2[nz])
+    if gamma == 2.0:
+        a[nz] = 2.0 ** z[nz] * omega[nz] / (h * h * k2[nz])
+    else:
+        a[nz] = 2.0 ** z[nz] * omega[nz] / (h * np.sqrt(k2[nz])) ** gamma
     o0 = omega[(0,) * d]
     for i in range(d):
         for j, ej in enumerate(ORIGIN_RULE[p], start=1):
             idx = [0] * d
             idx[i] = j
-            a[tuple(idx)] += 2.0 ** (d - 1) * ZETA * ej * o0 / (d * (j * h) ** 2)
+            a[tuple(idx)] += 2.0 ** (d - 1) * zeta(gamma) * ej * o0 / (d * (j * h) ** 2)
     mult = 2.0 ** (d - z)
     a[(0,) * d] = -math.fsum((mult * a)[nz].ravel()) - 2.0 ** d * far_field(d, alpha, N * h, lam)
     return a

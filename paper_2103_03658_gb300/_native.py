@@ -30,7 +30,8 @@ class FracError(RuntimeError):
 
 class Problem(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("degree", ctypes.c_int32), ("alpha", ctypes.c_double),
-                ("h", ctypes.c_double), ("n", ctypes.c_int64 * 3), ("lam", ctypes.c_double)]
+                ("h", ctypes.c_double), ("n", ctypes.c_int64 * 3), ("lam", ctypes.c_double),
+                ("gamma", ctypes.c_double)]
 
 
 class OpInfo(ctypes.Structure):
@@ -202,21 +203,22 @@ class FracOp:
     """Discretized (-Delta)^{alpha/2} (tempered when lam > 0) on a box with n interior points
     per axis: n an int (the cube (-1, 1)^d) or a sequence (n_1, .., n_d) of per-axis counts,
     axis 1 = x^(1) the fastest-varying (arrays have shape (n_d, .., n_1)).  h = 2 / (max n_i + 1)
-    unless given (the longest axis spans (-1, 1)); built on the current CUDA device."""
+    unless given (the longest axis spans (-1, 1)); gamma the splitting parameter in (alpha, 2]
+    (Eq. (eq0)); built on the current CUDA device."""
 
     def __init__(self, d: int, n, alpha: float, degree: int = 1, lam: float = 0.0,
-                 h: float | None = None, stream=None):
+                 h: float | None = None, stream=None, gamma: float = 2.0):
         lib = load()
         self._lib = lib
         ns = tuple(int(v) for v in n) if isinstance(n, (tuple, list)) else (int(n),) * d
         if len(ns) != d:
             raise ValueError(f"n has {len(ns)} entries for d = {d}")
-        self.d, self.alpha, self.degree, self.lam = d, alpha, degree, lam
+        self.d, self.alpha, self.degree, self.lam, self.gamma = d, alpha, degree, lam, gamma
         self.n = ns[0] if len(set(ns)) == 1 else ns
         self.ns = ns
         self.nd = int(np.prod(ns))
         self.h = 2.0 / (max(ns) + 1) if h is None else h
-        self._prob = Problem(d, degree, alpha, self.h, (ctypes.c_int64 * 3)(*(ns + (1,) * (3 - d))), lam)
+        self._prob = Problem(d, degree, alpha, self.h, (ctypes.c_int64 * 3)(*(ns + (1,) * (3 - d))), lam, gamma)
         handle = ctypes.c_void_p()
         s = lib.frac_coeffs(ctypes.byref(self._prob), ctypes.byref(handle), _stream(stream))
         if s != 0:

@@ -69,6 +69,7 @@ static int validate(const frac_problem* p) {
   if (p->degree < 0 || p->degree > 2) return FRAC_EINVAL;
   if (!(p->h > 0.0) || !std::isfinite(p->h)) return FRAC_EINVAL;
   if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return FRAC_EINVAL;
+  if (p->gamma != 0.0 && !(p->gamma > p->alpha && p->gamma <= 2.0)) return FRAC_EINVAL;
   for (int i = 0; i < p->d; ++i) {
     if (p->n[i] < 1) return FRAC_EINVAL;
     if (p->degree == 2 && ((p->n[i] + 1) % 2) != 0) return FRAC_EINVAL;

@@ -255,7 +255,8 @@ __global__ void k_far_terms(int d, double alpha, double lambda, double L, double
 struct WParams {
   int d, p;
   int64_t N;
-  double h, alpha, lambda, beta;  // beta = d + alpha - 2
+  double h, alpha, lambda, beta;  // beta = d + alpha - gamma: mu_gamma = |xi|^{-beta} e^{-lambda |xi|}
+  double gamma;                   // splitting parameter in (alpha, 2] (Eq. (eq0))
 };
 
 struct AxisEl {
@@ -353,7 +354,7 @@ __device__ double origin_element_1d(const WParams& P, int l, double H) {
   origin_poly(P.p, l, cf);
   const double ih = 1.0 / P.h;
   double s = 0.0, scale = 1.0;
-  for (int m = 0; m <= P.p; ++m, scale *= ih) s += cf[m] * scale * radial_moment(2.0 - P.alpha + m, P.lambda, H);
+  for (int m = 0; m <= P.p; ++m, scale *= ih) s += cf[m] * scale * radial_moment(P.gamma - P.alpha + m, P.lambda, H);
   return s;
 }
 
@@ -383,7 +384,7 @@ __device__ void duffy_angle(const WParams& P, int a, double H, DuffyAngle& A) {
     ws *= 0.5 * c_gl_w[off + ib];
   }
   const double cs = sqrt(1.0 + A.s[0] * A.s[0] + A.s[1] * A.s[1]);
-  for (int m = 0; m <= P.p * d && CHK(m, 7); ++m) A.R[m] = radial_moment(2.0 - P.alpha + m, P.lambda * cs, H);
+  for (int m = 0; m <= P.p * d && CHK(m, 7); ++m) A.R[m] = radial_moment(P.gamma - P.alpha + m, P.lambda * cs, H);
   A.base = ws * pow(cs, -P.beta);
 }
 
@@ -755,8 +756,10 @@ __global__ void k_stencil(WParams P, const double* __restrict__ omega, double* _
       if (k[i] == 0) ++z; else nzaxis = i;
       k2 += (double)k[i] * (double)k[i];
     }
-    double v = CHK(idx, count) ? ldexp(omega[idx], z) / (P.h * P.h * k2) : 0.0;
-    if (z == d - 1) {  // on an axis: k = j e_i
+    // a_k = 2^{z(k)} omega_k / |xi_k|^gamma; the origin rule (zeta = floor(gamma / 2)) only at gamma = 2
+    const double xi2 = P.h * P.h * k2;
+    double v = CHK(idx, count) ? ldexp(omega[idx], z) / (P.gamma == 2.0 ? xi2 : pow(xi2, 0.5 * P.gamma)) : 0.0;
+    if (z == d - 1 && P.gamma == 2.0) {  // on an axis: k = j e_i
       const int64_t j = k[nzaxis];
       double e = 0.0;
       if (P.p <= 1) e = (j == 1) ? 1.0 : 0.0;
@@ -982,7 +985,8 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   P.h = pr.h;
   P.alpha = pr.alpha;
   P.lambda = pr.lambda;
-  P.beta = pr.d + pr.alpha - 2.0;
+  P.gamma = pr.gamma > 0.0 ? pr.gamma : 2.0;
+  P.beta = pr.d + pr.alpha - P.gamma;
   const int d = pr.d;
   const int64_t ngen = op->ngen;
   const double L = op->N * pr.h;

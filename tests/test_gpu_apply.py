@@ -100,6 +100,32 @@ def test_generator_3d_full_size_sampled(alpha):
     op.close()
 
 
+@pytest.mark.parametrize("n,p,alpha,lam", [(127, 2, 0.9, 1.5), (255, 0, 1.7, 0.6)])
+def test_generator_3d_tempered_sampled(n, p, alpha, lam):
+    """Tempered 3D generators, sampled far and near nodes (the far elements' kernel comes from
+    a per-element Taylor series on the device): a_k from the oracle's weights at those nodes,
+    origin rule e = (1) (p <= 1) or (4/3, -1/3) (p = 2) on the axes."""
+    d = 3
+    N = n + 1
+    h = 2.0 / N
+    op = _op(d, n, p, alpha, lam)
+    a_gpu = op.generator()
+    rng = np.random.default_rng(31)
+    nodes = [(1, 0, 0), (2, 0, 0), (0, 2, 0), (1, 1, 1), (N, N, N), (N, 1, 0), (N // 2, 3, N - 2), (40, 41, 42)]
+    nodes += [tuple(int(v) for v in rng.integers(0, N + 1, size=3)) for _ in range(24)]
+    w = O.weights_at(d, N, h, alpha, p, lam, nodes + [(0, 0, 0)])
+    w0 = w[-1]
+    e = (1.0,) if p <= 1 else (4.0 / 3.0, -1.0 / 3.0)
+    for k, wk in zip(nodes, w[:-1]):
+        z = sum(1 for t in k if t == 0)
+        ak = 2.0 ** z * wk / (h * h * sum(t * t for t in k))
+        if z == d - 1 and max(k) <= len(e):
+            j = max(k)
+            ak += 2.0 ** (d - 1) * e[j - 1] * w0 / (d * (j * h) ** 2)
+        assert abs(a_gpu[k[2], k[1], k[0]] - ak) <= 1e-13 * abs(ak) + 1e-16 * abs(a_gpu).max(), k
+    op.close()
+
+
 # ---------------------------------------------------------------------------
 # apply
 # ---------------------------------------------------------------------------

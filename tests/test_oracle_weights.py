@@ -347,7 +347,7 @@ def test_definition_level_sum(d, N, p):
             for j, ej in enumerate(O.ORIGIN_RULE[p], start=1):
                 off = [0] * d
                 off[ax] = j
-                acc += O.ZETA * w[(0,) * d] * ej * Phi(i, tuple(off)) / d
+                acc += O.zeta(2.0) * w[(0,) * d] * ej * Phi(i, tuple(off)) / d
         acc += -(2 ** d) * F * val(i)
         y[ii] = -c * acc
     assert np.allclose(y, O.apply_dense(a, c, u), rtol=0, atol=1e-12 * np.max(np.abs(y)))
