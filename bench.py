@@ -55,15 +55,20 @@ def config(parallelism: str) -> dict:
 # CPU oracle leg (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-def oracle_rows_rate(seconds: float = 15.0, fields: np.ndarray | None = None) -> dict:
-    """Time the FP64 oracle on a bounded sample of the workload: build its
-    generator, then dense rows of the fields until ``seconds`` have elapsed."""
+def oracle_generator() -> tuple:
+    """The oracle's generator and c_{d,alpha} for the workload, and the seconds the build took."""
     from oracle import frac_oracle as O
     N = NSIDE + 1
     t0 = time.perf_counter()
     a = O.stencil(D, N, 2.0 / N, ALPHA, DEGREE)
-    c = O.c_dalpha(D, ALPHA)
-    t_gen = time.perf_counter() - t0
+    return a, O.c_dalpha(D, ALPHA), time.perf_counter() - t0
+
+
+def oracle_rows_rate(seconds: float = 15.0, fields: np.ndarray | None = None, gen: tuple | None = None) -> dict:
+    """Time the FP64 oracle on a bounded sample of the workload: dense rows of the
+    fields until ``seconds`` have elapsed (the generator built first unless given)."""
+    from oracle import frac_oracle as O
+    a, c, t_gen = gen if gen is not None else oracle_generator()
     if fields is None:
         fields = np.stack([synth.ball_power(D, NSIDE, 1 + ALPHA / 2), synth.smooth_field(D, NSIDE, synth.BASE_SEED)])
     rng = np.random.default_rng(1)
@@ -86,11 +91,12 @@ def run_reference(args) -> None:
     if rank != 0:
         return
     fields = np.stack([synth.ball_power(D, NSIDE, 1 + ALPHA / 2), synth.smooth_field(D, NSIDE, synth.BASE_SEED)])
+    gen = oracle_generator()
     per_step = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
     for _ in range(args.warmup):
-        oracle_rows_rate(min(per_step, 2.0), fields)
+        oracle_rows_rate(min(per_step, 2.0), fields, gen)
     t0 = time.perf_counter()
-    vals = [oracle_rows_rate(per_step, fields) for _ in range(args.steps)]
+    vals = [oracle_rows_rate(per_step, fields, gen) for _ in range(args.steps)]
     wall = time.perf_counter() - t0
     v = statistics.median(x["value"] for x in vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": args.gpus,
