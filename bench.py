@@ -226,9 +226,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # the next pass reads it, so at 65 fields the traffic per field is somewhat
 # higher.  Remove an entry when its kernel changes.
 DRAM_TRAFFIC_PER_FIELD = {
-    "cols_sym2_f32_M2048": (172.527360e6 + 110.699264e6) / 20,
-    "rows_fwd_f32_M2048": (84.182528e6 + 114.387200e6) / 20,
-    "rows_inv_f32_M2048": (168.299008e6 + 54.121216e6) / 20,
+    "cols_sym2_f32_M2048": (172.519424e6 + 110.782464e6) / 20,
+    "rows_fwd_f32_M2048": (84.167936e6 + 114.912768e6) / 20,
+    "rows_inv_f32_M2048": (168.301824e6 + 53.662464e6) / 20,
 }
 
 
