@@ -176,7 +176,9 @@ typedef struct frac_solve_opts {
   int32_t precision;    /* FRAC_PLAIN_F64 or FRAC_MIXED_IR                                  */
   int32_t use_x0;       /* nonzero: u holds the initial guess on entry                      */
   int32_t precond;      /* FRAC_PRECOND_TAU (0, the default) or FRAC_PRECOND_NONE           */
-  double inner_tol;     /* MIXED_IR: relative residual reduction of each FP32 inner solve   */
+  double inner_tol;     /* MIXED_IR: relative residual reduction of each FP32 inner solve;
+                           0 = automatic: max(1e-6, sqrt(rtol)/10) when the symbol's max/min
+                           ratio is below 50, else 1e-4                                      */
 } frac_solve_opts;
 
 typedef struct frac_solve_info {

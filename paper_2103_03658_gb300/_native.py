@@ -292,7 +292,7 @@ class FracOp:
 
     # -- solve --
     def solve(self, f, u=None, rtol: float = 1e-10, max_iter: int = 200000, precision: str = "mixed",
-              inner_tol: float = 1e-4, stream=None, precond: str = "tau"):
+              inner_tol: float = 0.0, stream=None, precond: str = "tau"):
         """Solve A u = f (g = 0); returns (u, info dict).  f, u float64."""
         if _dtype_code(f) != F64:
             raise TypeError("solve takes float64 data")
@@ -322,7 +322,7 @@ def _opts(rtol, max_iter, precision, use_x0, inner_tol, precond) -> "SolveOpts":
 
 
 def solve_batch(ops, fs, us, rtol: float = 1e-10, max_iter: int = 200000, precision: str = "mixed",
-                inner_tol: float = 1e-4, stream=None, precond: str = "tau"):
+                inner_tol: float = 0.0, stream=None, precond: str = "tau"):
     """Solve ops[i] u[i] = f[i] for all i (device tensors); returns a list of info dicts."""
     lib = load()
     cnt = len(ops)
@@ -373,7 +373,7 @@ class Engine:
         self._keep = {}
 
     def submit(self, op: "FracOp", f, u=None, rtol: float = 1e-10, max_iter: int = 200000,
-               precision: str = "mixed", inner_tol: float = 1e-4, use_x0: bool = False,
+               precision: str = "mixed", inner_tol: float = 0.0, use_x0: bool = False,
                precond: str = "tau") -> tuple:
         """Queue op u = f; the solution goes to `u` (a new buffer if None), whose
         contents are the initial guess only when use_x0 is set.  Returns (job id, u)."""

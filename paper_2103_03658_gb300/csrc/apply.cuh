@@ -1,6 +1,8 @@
 // Internal interfaces between the translation units of the library.
 #pragma once
 
+#include <cmath>
+
 #include <vector>
 
 #include "common.cuh"

@@ -527,7 +527,7 @@ B2Prob make_prob(const frac_op* op, const double* f, double* u, const frac_solve
   p.max_iter = o->max_iter;
   p.use_x0 = o->use_x0 ? 1 : 0;
   p.rtol = o->rtol;
-  p.inner_tol = o->inner_tol > 0.0 ? o->inner_tol : 1e-4;
+  p.inner_tol = o->inner_tol > 0.0 ? o->inner_tol : auto_inner_tol(op, o->rtol);
   return p;
 }
 

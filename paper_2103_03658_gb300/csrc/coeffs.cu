@@ -622,13 +622,19 @@ __global__ void __launch_bounds__(256) k_elements(WParams P, int64_t ne, const d
         c2 += cen[i] * cen[i];
         hi2 += ax[i][0].hi * ax[i][0].hi;
       }
-      const double dmax = fmax((c2 - lo2) / c2, (hi2 - c2) / c2);
+      const double inv_c2 = 1.0 / c2;
+      const double dmax = fmax(c2 - lo2, hi2 - c2) * inv_c2;
       int deg = 0;
-      double hser[kSeriesMax + 1], muc = 1.0, inv_c2 = 1.0 / c2;
+      double hser[kSeriesMax + 1], muc = 1.0;
       const double c = sqrt(c2);
       if (D == 3 && dmax > 0.0 && dmax <= 0.15) {  // (2D elements have too few points to pay for the setup)
-        int k1 = (int)ceil(log(1e-17) / log(dmax)), k2 = 0;
-        for (double t = 1.0, x = P.lambda * c * dmax; t > 1e-17 && k2 <= kSeriesMax; t *= x / k2) ++k2;
+        // k1 >= log(1e-17) / log(dmax) without a log: dmax = m 2^e, m in [1, 2), and
+        // log2(m) <= (m - 1) / ln 2, so -log2(dmax) >= -e - (m - 1) / ln 2; 1e-17 > 2^-56.5
+        int e2;
+        const double m2 = 2.0 * frexp(dmax, &e2);
+        const int k1 = (int)ceil(56.5 / (double)(1 - e2 - (m2 - 1.0) * 1.4426950408889634));
+        int k2 = 0;
+        for (double t = 1.0, x = P.lambda * c * dmax; t > 1e-17 && k2 < kSeriesMax; t *= x * c_inv[k2]) ++k2;
         deg = (k1 > k2 ? k1 : k2) + 4;
         if (deg > kSeriesMax) deg = 0;
       }
@@ -1138,6 +1144,8 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   bool fits = true;
   for (int i = 0; i < d; ++i) fits = fits && op->na[i] <= op->Ma[i] / 2 - 1;
   op->precond_ok = fits && mn > 0.0 ? 1 : 0;
+  // condition estimate: largest over smallest symbol entry (the scaled symbol is m |scale| at most)
+  op->kappa_est = mn > 0.0 ? m * std::fabs(scale) / mn : INFINITY;
   return FRAC_OK;
 }
 

@@ -1,6 +1,8 @@
 // Shared definitions for the sm_103a fractional-Laplacian library.
 #pragma once
 
+#include <cmath>
+
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -76,6 +78,7 @@ struct frac_op {
   double a0;
   double far_field;
   double norm_bound;
+  double kappa_est;  // max / min of the symbol: an estimate of the condition number of A
   double* a;         // device, (N+1)^d FP64 generator
   double* lam64;     // device, prod K_i FP64 scaled symbol
   float* lam32;      // device, prod K_i FP32 scaled symbol
@@ -85,3 +88,16 @@ struct frac_op {
   size_t device_bytes;
   int device;
 };
+
+// Inner tolerance of the mixed-precision refinement when the caller leaves it at 0:
+// a well-conditioned operator (kappa_est < 50, so FP32 CG resolves a 1e-6 reduction)
+// gets max(1e-6, sqrt(rtol) / 10), two refinement steps for rtol = 1e-10; otherwise
+// 1e-4, since FP32 limits each step to about kappa eps_32 anyway.
+inline double auto_inner_tol(const frac_op* op, double rtol) {
+  if (op->kappa_est < 50.0) {
+    const double t = 0.1 * std::sqrt(rtol);
+    return t > 1e-6 ? t : 1e-6;
+  }
+  return 1e-4;
+}
+

@@ -508,7 +508,7 @@ int solve_device(const frac_op* op, const double* f, double* u, const frac_solve
     FRAC_TRY(ws.get(&q32, nd * sizeof(float)));
     if (pcg) FRAC_TRY(ws.get(&z32, nd * sizeof(float)));
     FRAC_TRY(ws.get(&ws32, apply_workspace_bytes(op, FRAC_F32, 1)));
-    const double inner = opts->inner_tol > 0.0 ? opts->inner_tol : 1e-4;
+    const double inner = opts->inner_tol > 0.0 ? opts->inner_tol : auto_inner_tol(op, opts->rtol);
     int outer = 0;
     while (rnorm > rtol * fnorm && iters < opts->max_iter && outer < 100) {
       // inner FP32 CG on A d = r / ||r||
@@ -665,7 +665,7 @@ int start_cg(Job* j) {
   const unsigned gb = (unsigned)nb;
   const int left = j->opts.max_iter - j->iters;
   if (j->opts.precision == FRAC_MIXED_IR) {
-    const double inner = j->opts.inner_tol > 0.0 ? j->opts.inner_tol : 1e-4;
+    const double inner = j->opts.inner_tol > 0.0 ? j->opts.inner_tol : auto_inner_tol(j->op, j->opts.rtol);
     k_ir_scale_down<<<gb, kTB, 0, j->s>>>(j->r64, j->scal + 1, j->r32, j->p32, j->x32, nd);
     k_dot<float><<<gb, kTB, 0, j->s>>>(j->r32, j->r32, nd, j->partial, nullptr);
     k_cg_start<<<1, kTB, 0, j->s>>>(j->partial, nb, j->st, inner, -1.0, left, j->pcg ? 1 : 0);

@@ -21,7 +21,7 @@ struct Solve1dTask {
 inline Solve1dTask make_task1d(const frac_op* op, const double* f, double* u, frac_solve_info* info,
                                const frac_solve_opts* o) {
   return Solve1dTask{f, u, op->lam32, op->lam64, op->pinv32, op->pinv64, info, o->rtol,
-                     o->inner_tol > 0.0 ? o->inner_tol : 1e-4, (int)op->n, o->max_iter, o->use_x0 ? 1 : 0,
+                     o->inner_tol > 0.0 ? o->inner_tol : auto_inner_tol(op, o->rtol), (int)op->n, o->max_iter, o->use_x0 ? 1 : 0,
                      (o->precond == FRAC_PRECOND_TAU && op->precond_ok) ? 1 : 0};
 }
 
