@@ -232,6 +232,22 @@ DRAM_TRAFFIC_PER_FIELD = {
 }
 
 
+def max_over_ranks(x: float, dist, device: str = "cuda") -> float:
+    """The largest x over the ranks (the slowest rank's time); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Replicas: every rank processes units_per_rank; the job rate is all units over the
+    slowest rank's time (weak scaling, no collective on the data path)."""
+    return world * units_per_rank / seconds
+
+
 def run_ours(args) -> None:
     import torch
 
@@ -272,13 +288,9 @@ def run_ours(args) -> None:
         barrier()
     lib.frac_profile_enable(0)
     prof = profile_read(lib)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist)
     dof = NFIELDS * NSIDE * NSIDE
-    value = world * dof / (ms * 1e-3) / 1e9
+    value = whole_job_rate(dof, world, ms * 1e-3) / 1e9
     launches = sum(v[0] for v in prof.values())
 
     # roofline of the dominant kernel (largest total device time in the timed region)
@@ -333,12 +345,8 @@ def run_ours(args) -> None:
     for _ in range(e2e_steps):
         op.apply(hu, out=hy)
     barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * dof / e2e_s / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": host.nbytes,
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist)
+    e2e = {"value": whole_job_rate(dof, world, e2e_s) / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": host.nbytes,
            "d2h_bytes_per_step": host.nbytes}
 
     extra = {}
