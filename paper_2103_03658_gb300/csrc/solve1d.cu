@@ -37,31 +37,29 @@ __device__ __forceinline__ double block_allsum(double v, double* red) {
   return s;
 }
 
-// (A v) for one real vector, FFT in precision T on the line `buf`; the result
-// is left in the real parts of buf (read with buf[pidx(x)].x).  `load(x)`
-// gives v at grid point x < n.
+// (A v) for one real vector with the register-interface FFT: v is zero beyond n
+// <= M/2 (the first pass skips that half) and only entries below n are kept (the
+// last pass skips the other half).  `load(e, x)` gives v at grid point x = tl + e TPL
+// (e < E/2); on return y[e].x holds (A v) at x = tl + e TPL for e < E/2.
 template <typename T, int LOGM, typename Load>
-__device__ __forceinline__ void conv_line(cplx_t<T>* buf, int n, const T* __restrict__ lam,
-                                          const cplx_t<T>* __restrict__ tw, Load load) {
+__device__ __forceinline__ void conv_line(cplx_t<T> (&y)[elems(LOGM)], cplx_t<T>* buf, int n,
+                                          const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, Load load) {
   using C = cplx_t<T>;
   constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM);
   const int tl = threadIdx.x;
-  __syncthreads();
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int x = tl + e * TPL;
-    buf[pidx(x)] = C{x < n ? load(e, x) : T(0), T(0)};
+    y[e] = C{(e < E / 2 && x < n) ? load(e, x) : T(0), T(0)};
   }
-  __syncthreads();
-  run<C, LOGM, false>(buf, tl, tw);
+  fft_reg<C, LOGM, false, true, false>(y, buf, tl, tw);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int k = tl + e * TPL;
     const int kr = k <= M / 2 ? k : M - k;
-    buf[pidx(k)] = cscale(buf[pidx(k)], lam[kr]);
+    y[e] = cscale(y[e], lam[kr]);
   }
-  __syncthreads();
-  run<C, LOGM, true>(buf, tl, tw);
+  fft_reg<C, LOGM, true, false, true>(y, buf, tl, tw);
 }
 
 // z = P r with the tau preconditioner on the line `buf`: the odd extension of
@@ -73,7 +71,7 @@ __device__ __forceinline__ void precond_line(cplx_t<T>* buf, int n, const T* __r
   using C = cplx_t<T>;
   constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM);
   const int tl = threadIdx.x;
-  __syncthreads();
+  __syncthreads();  // earlier readers of buf are done
 #pragma unroll
   for (int e = 0; e < E; ++e) buf[pidx(tl + e * TPL)] = C{T(0), T(0)};
   __syncthreads();
@@ -87,15 +85,21 @@ __device__ __forceinline__ void precond_line(cplx_t<T>* buf, int n, const T* __r
     }
   }
   __syncthreads();
-  run<C, LOGM, false>(buf, tl, tw);
+  C v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = buf[pidx(tl + e * TPL)];
+  fft_reg<C, LOGM, false, false, false>(v, buf, tl, tw);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int k = tl + e * TPL;
     const int kr = k <= M / 2 ? k : M - k;
-    buf[pidx(k)] = cscale(buf[pidx(k)], pinv[kr]);
+    v[e] = cscale(v[e], pinv[kr]);
   }
+  fft_reg<C, LOGM, true, false, false>(v, buf, tl, tw);
+  __syncthreads();  // the last pass's reads of buf are done
+#pragma unroll
+  for (int e = 0; e < E; ++e) buf[pidx(tl + e * TPL)] = v[e];
   __syncthreads();
-  run<C, LOGM, true>(buf, tl, tw);
 }
 
 }  // namespace
@@ -133,13 +137,14 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
 
   int iters = 0, outer = 0, status = FRAC_OK;
   // r64 = f - A64 u into r (registers), returns ||r||^2
+  double2 y64[E];
   auto residual = [&](double (&r)[E]) {
-    conv_line<double, LOGM>(buf64, n, T.lam64, tw64, [&](int, int x) { return U[x]; });
+    conv_line<double, LOGM>(y64, buf64, n, T.lam64, tw64, [&](int, int x) { return U[x]; });
     double s = 0.0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int x = tl + e * TPL;
-      r[e] = x < n ? F[x] - buf64[pidx(x)].x : 0.0;
+      r[e] = (e < E / 2 && x < n) ? F[x] - y64[e].x : 0.0;
       s += r[e] * r[e];
     }
     return block_allsum<TPL>(s, red);
@@ -174,10 +179,10 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
       }
       double rr = rn2;
       while (rr > tol2 && iters < T.max_iter) {
-        conv_line<double, LOGM>(buf64, n, T.lam64, tw64, [&](int e, int) { return p[e]; });
+        conv_line<double, LOGM>(y64, buf64, n, T.lam64, tw64, [&](int e, int) { return p[e]; });
         double pq = 0.0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) pq += p[e] * buf64[pidx(tl + e * TPL)].x;  // p = 0 beyond n
+        for (int e = 0; e < E / 2; ++e) pq += p[e] * y64[e].x;  // p = 0 beyond n
         pq = block_allsum<TPL>(pq, red);
         if (!(pq > 0.0) || !isfinite(pq)) {
           status = FRAC_EBREAKDOWN;
@@ -188,9 +193,9 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           const int x = tl + e * TPL;
-          if (x < n) {  // the convolution is nonzero beyond n; r and p stay zero there
+          if (e < E / 2 && x < n) {  // the convolution is nonzero beyond n; r and p stay zero there
             U[x] += al * p[e];
-            r[e] -= al * buf64[pidx(x)].x;
+            r[e] -= al * y64[e].x;
           }
           rr1 += r[e] * r[e];
         }
@@ -252,19 +257,20 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
       }
       const double stop = inner2 * rr;
       while (rr > stop && iters < T.max_iter) {
-        conv_line<float, LOGM>(buf32, n, T.lam32, tw32, [&](int e, int) { return p[e]; });
+        float2 y32[E];
+        conv_line<float, LOGM>(y32, buf32, n, T.lam32, tw32, [&](int e, int) { return p[e]; });
         float pqf = 0.0f;
 #pragma unroll
-        for (int e = 0; e < E; ++e) pqf += p[e] * buf32[pidx(tl + e * TPL)].x;
+        for (int e = 0; e < E / 2; ++e) pqf += p[e] * y32[e].x;
         const double pq = block_allsum<TPL>((double)pqf, red);
         if (!(pq > 0.0) || !isfinite(pq)) break;  // inner breakdown: refine from here
         const float al = (float)(rz / pq);
         float rr1f = 0.0f;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          if (tl + e * TPL < n) {  // r and p stay zero beyond n
+          if (e < E / 2 && tl + e * TPL < n) {  // r and p stay zero beyond n
             x[e] += al * p[e];
-            r[e] -= al * buf32[pidx(tl + e * TPL)].x;
+            r[e] -= al * y32[e].x;
           }
           rr1f += r[e] * r[e];
         }
