@@ -559,9 +559,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fields", type=int, default=65,
                     help="fields per apply (65 = the benchmark workload; fewer only for profiler captures)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the 256-problem batch measurement and print its JSON (profiler captures)")
     args = ap.parse_args()
     global NFIELDS
     NFIELDS = args.fields
+    if args.batch_only:
+        import torch
+        import paper_2103_03658_gb300 as fg
+        print(json.dumps(batch_measurement(fg, torch, torch.cuda.synchronize)), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
