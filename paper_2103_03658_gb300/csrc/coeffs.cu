@@ -569,14 +569,52 @@ __global__ void __launch_bounds__(256) k_near_elements(WParams P, int E, double*
   }
 }
 
+// The integrand mu(|xi|) prod_i phi_{l_i}(xi_i) is symmetric under permutations of the
+// axes (mu is radial and every axis carries the same basis), so the integrals of a
+// permuted element are those of the sorted one with the local indices permuted: only
+// the elements with e_0 <= e_1 (<= e_2) are integrated, numbered by
+// canon_index(e) = T3(e_2) + T2(e_1) + e_0 (3D) or T2(e_1) + e_0 (2D), with the
+// tetrahedral T3(m) = m (m+1) (m+2) / 6 and triangular T2(m) = m (m+1) / 2 numbers.
+__host__ __device__ __forceinline__ int64_t tri2(int64_t m) { return m * (m + 1) / 2; }
+__host__ __device__ __forceinline__ int64_t tri3(int64_t m) { return m * (m + 1) * (m + 2) / 6; }
+__host__ __device__ __forceinline__ int64_t canon_count(int d, int64_t ne) { return d == 2 ? tri2(ne) : tri3(ne); }
+
+// the largest m with f(m) <= t for an increasing f, from an estimate (corrected both ways)
+template <typename F>
+__device__ __forceinline__ int64_t inv_increasing(int64_t t, int64_t guess, F f) {
+  int64_t m = guess < 0 ? 0 : guess;
+  while (m > 0 && f(m) > t) --m;
+  while (f(m + 1) <= t) ++m;
+  return m;
+}
+
+// canonical element number t -> (e_0 <= e_1 [<= e_2])
+template <int D>
+__device__ __forceinline__ void canon_element(int64_t t, int* el) {
+  if (D == 2) {
+    const int64_t e1 = inv_increasing(t, (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5), tri2);
+    el[1] = (int)e1;
+    el[0] = (int)(t - tri2(e1));
+    el[2] = 0;
+  } else {
+    const int64_t e2 = inv_increasing(t, (int64_t)cbrt(6.0 * (double)t) - 1, tri3);
+    const int64_t rem = t - tri3(e2);
+    const int64_t e1 = inv_increasing(rem, (int64_t)((sqrt(8.0 * (double)rem + 1.0) - 1.0) * 0.5), tri2);
+    el[2] = (int)e2;
+    el[1] = (int)e1;
+    el[0] = (int)(rem - tri2(e1));
+  }
+}
+
 template <int D, int PD>
 __global__ void __launch_bounds__(256) k_elements(WParams P, int64_t ne, const double* __restrict__ near, int E,
                                                   double* __restrict__ eint) {
   constexpr int N1 = PD + 1, NL = (D == 2) ? N1 * N1 : N1 * N1 * N1, NW = (D == 2) ? N1 : N1 * N1;
-  const int64_t total = (D == 2) ? ne * ne : ne * ne * ne;
+  const int64_t total = canon_count(D, ne);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= total) return;
-  const int el[3] = {(int)(t % ne), (int)((t / ne) % ne), D == 3 ? (int)(t / (ne * ne)) : 0};
+  int el[3];
+  canon_element<D>(t, el);
   double acc[NL];
 #pragma unroll
   for (int c = 0; c < NL; ++c) acc[c] = 0.0;
@@ -726,13 +764,25 @@ __global__ void k_gather(WParams P, int64_t ne, const double* __restrict__ eint,
       }
     }
   }
-  const int64_t total = (D == 2) ? ne * ne : ne * ne * ne;
+  const int64_t total = canon_count(D, ne);
   double tot = 0.0;
   for (int a = 0; a < nc[0]; ++a)
     for (int b = 0; b < nc[1]; ++b)
       for (int cc = 0; cc < (D == 3 ? nc[2] : 1); ++cc) {
-        const int64_t e = ee[0][a] + ne * (ee[1][b] + (D == 3 ? ne * ee[2][cc] : 0));
-        const int lc = ll[0][a] + nl1 * (ll[1][b] + (D == 3 ? nl1 * ll[2][cc] : 0));
+        // sort (element, local index) pairs by element: the canonical element and its local product
+        int64_t es[3] = {ee[0][a], ee[1][b], D == 3 ? ee[2][cc] : 0};
+        int ls[3] = {ll[0][a], ll[1][b], D == 3 ? ll[2][cc] : 0};
+        for (int i = 1; i < D; ++i)
+          for (int j = i; j > 0 && es[j - 1] > es[j]; --j) {
+            const int64_t te = es[j];
+            es[j] = es[j - 1];
+            es[j - 1] = te;
+            const int tl = ls[j];
+            ls[j] = ls[j - 1];
+            ls[j - 1] = tl;
+          }
+        const int64_t e = D == 2 ? tri2(es[1]) + es[0] : tri3(es[2]) + tri2(es[1]) + es[0];
+        const int lc = ls[0] + nl1 * (ls[1] + (D == 3 ? nl1 * ls[2] : 0));
         if (CHK(e, total) && CHK(lc, nloc)) tot += eint[e * nloc + lc];
       }
   omega[idx] = tot;
@@ -1008,11 +1058,9 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
     // near-origin elements [0, E)^d first, spread over kNearSplit blocks each
     const int64_t ne_axis = pr.degree == 0 ? op->N + 1 : (pr.degree == 1 ? op->N : op->N / 2);
     const int E = (int)std::min<int64_t>(kNearE[d], ne_axis);
-    int64_t nnear = 1, nel = 1;
-    for (int i = 0; i < d; ++i) {
-      nnear *= E;
-      nel *= ne_axis;
-    }
+    int64_t nnear = 1;
+    for (int i = 0; i < d; ++i) nnear *= E;
+    const int64_t nel = canon_count(d, ne_axis);  // elements up to a permutation of the axes
     const int nl1 = pr.degree + 1;
     const int nloc = d == 2 ? nl1 * nl1 : nl1 * nl1 * nl1;
     FRAC_CUDA_TRY(cudaMallocAsync(&near, (size_t)nnear * kNearSplit * nloc * sizeof(double), st));
