@@ -423,9 +423,36 @@ def extra_measurements(fg, torch, u32, op, barrier) -> dict:
         solves[f"3d_n255_p1_alpha{alpha}"] = res
         op3.close()
     out["solves"] = solves
+    out["applies"] = apply_measurement(fg, torch, barrier)
     out["operator_builds"] = build_measurement(fg, barrier)
     out["batch"] = batch_measurement(fg, torch, barrier)
     out["served"] = served_measurement(fg, torch, barrier)
+    return out
+
+
+def apply_measurement(fg, torch, barrier) -> dict:
+    """Single-vector applies of the other configurations: 1D n = 1023 (p = 1, alpha = 1.5) in
+    FP64 and FP32 (microseconds per apply, a latency: one small convolution), and 3D 255^3
+    (p = 1, alpha = 1.6) in FP32 and FP64 (milliseconds per apply); CUDA events over 20 applies."""
+    out = {}
+    for name, (d, n, p, alpha), dtypes, scale in (("1d_n1023", (1, 1023, 1, 1.5), (torch.float64, torch.float32), 1e3),
+                                                  ("3d_n255", (3, 255, 1, 1.6), (torch.float32, torch.float64), 1.0)):
+        op = fg.FracOp(d, n, alpha, degree=p)
+        for dt in dtypes:
+            u = torch.tensor(synth.ball_power(d, n, 1 + alpha / 2), dtype=dt, device="cuda")
+            y = torch.empty_like(u)
+            for _ in range(3):
+                op.apply(u, out=y)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                op.apply(u, out=y)
+            e1.record()
+            barrier()
+            unit = "us" if scale == 1e3 else "ms"
+            out[f"{name}_{'f64' if dt == torch.float64 else 'f32'}_{unit}"] = e0.elapsed_time(e1) / 20 * scale
+        op.close()
     return out
 
 
