@@ -588,9 +588,16 @@ def main():
                     help="fields per apply (65 = the benchmark workload; fewer only for profiler captures)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the 256-problem batch measurement and print its JSON (profiler captures)")
+    ap.add_argument("--applies-only", action="store_true",
+                    help="run only the 1D and 3D single-vector apply timings and print their JSON (profiler captures)")
     args = ap.parse_args()
     global NFIELDS
     NFIELDS = args.fields
+    if args.applies_only:
+        import torch
+        import paper_2103_03658_gb300 as fg
+        print(json.dumps(apply_measurement(fg, torch, torch.cuda.synchronize)), flush=True)
+        return
     if args.batch_only:
         import torch
         import paper_2103_03658_gb300 as fg
