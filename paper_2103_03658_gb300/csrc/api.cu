@@ -249,14 +249,17 @@ static int run_apply(const frac_op* op, const void* u, void* y, int dtype, int64
                            : apply_t<float>(op, (const float*)u, (float*)y, batch, ws, st);
 }
 
-// Host input and output, several fields: chunks of fields go round-robin to the
-// library's copy streams, each doing host-to-device copy, apply and device-to-host
-// copy of its chunk, so that the copies of one chunk overlap the other chunks' copies
-// (the two directions use separate copy engines) and compute.  Chunks of at least
-// kPipeChunkBytes keep the copies and the passes efficient (28 MB: the best of a sweep from 12 to
-// 70 MB on the 65-field 1023^2 FP32 apply, 29.3 GDOF/s end to end against 18.6 unpipelined).  Returns after the last
-// copy has landed.
+// Host input and output, several fields: a three-stage pipeline over chunks of
+// fields on the library's three streams, host-to-device copies on the first, the
+// applies on the second, device-to-host copies on the third, through a ring of
+// pipe_slots() device input and output buffers.  Events order a chunk's three
+// stages and the reuse of a slot: a chunk's input copy waits for the apply that
+// last read its input buffer, its apply for the output copy that last read its
+// output buffer.  The two copy directions run on separate copy engines, so each
+// stays busy while the applies (one stream, one workspace) fit in between.
+// Returns after the last copy has landed.
 constexpr size_t kPipeChunkBytes = 28u << 20;
+constexpr int kPipeSlots = 3;
 static size_t pipe_chunk_bytes() {  // FRAC_PIPE_CHUNK_MB overrides the chunk size (tuning), read once
   static const size_t v = [] {
     const char* e = std::getenv("FRAC_PIPE_CHUNK_MB");
@@ -265,62 +268,94 @@ static size_t pipe_chunk_bytes() {  // FRAC_PIPE_CHUNK_MB overrides the chunk si
   }();
   return v;
 }
+static int pipe_slots() {  // FRAC_PIPE_SLOTS overrides the ring size (tuning, 2..8), read once
+  static const int v = [] {
+    const char* e = std::getenv("FRAC_PIPE_SLOTS");
+    const int k = e ? std::atoi(e) : 0;
+    return k >= 2 && k <= 8 ? k : kPipeSlots;
+  }();
+  return v;
+}
 static int apply_host_pipelined(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, bool precond,
                                 cudaStream_t st) {
+  constexpr int kMaxSlots = 8;
   const size_t es = dtype == FRAC_F64 ? sizeof(double) : sizeof(float);
   const size_t fb = (size_t)op->nd * es;
   int64_t nch = std::min<int64_t>(batch, std::max<int64_t>(1, (int64_t)((batch * fb) / pipe_chunk_bytes())));
-  nch = std::min<int64_t>(nch, 16);
+  nch = std::min<int64_t>(nch, 256);
   const int64_t per = (batch + nch - 1) / nch;
   nch = (batch + per - 1) / per;
   cudaStream_t ss[kCopyStreams];
   FRAC_TRY(copy_streams(ss));
-  const int ns = (int)std::min<int64_t>(kCopyStreams, nch);
-  cudaEvent_t fork = nullptr, join[kCopyStreams] = {};
-  struct EvFree {
-    cudaEvent_t* f;
-    cudaEvent_t* j;
-    ~EvFree() {
-      if (*f) cudaEventDestroy(*f);
-      for (int i = 0; i < kCopyStreams; ++i)
-        if (j[i]) cudaEventDestroy(j[i]);
-    }
-  } evf{&fork, join};
-  FRAC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-  FRAC_CUDA_TRY(cudaEventRecord(fork, st));
-  // per stream: device input, output and workspace for one chunk
-  void* bufs[kCopyStreams][3] = {};
-  const size_t wsb = apply_workspace_bytes(op, dtype, per);
+  cudaStream_t s_in = ss[0], s_cmp = ss[1], s_out = ss[2];
+  const int K = (int)std::min<int64_t>(pipe_slots(), nch);
+  // device buffers (allocated on the caller's stream, freed there after the join)
+  void* in[kMaxSlots] = {};
+  void* out[kMaxSlots] = {};
+  void* ws = nullptr;
+  cudaEvent_t ev[3][kMaxSlots] = {};  // input landed, apply done, output landed
+  cudaEvent_t fork = nullptr, join[3] = {};
   int s = FRAC_OK;
-  for (int i = 0; i < ns && s == FRAC_OK; ++i) {
-    if (cudaStreamWaitEvent(ss[i], fork, 0) != cudaSuccess ||
-        cudaMallocAsync(&bufs[i][0], per * fb, ss[i]) != cudaSuccess ||
-        cudaMallocAsync(&bufs[i][1], per * fb, ss[i]) != cudaSuccess ||
-        (wsb && cudaMallocAsync(&bufs[i][2], wsb, ss[i]) != cudaSuccess))
+  const size_t wsb = apply_workspace_bytes(op, dtype, per);
+  for (int k = 0; k < K && s == FRAC_OK; ++k)
+    if (cudaMallocAsync(&in[k], per * fb, st) != cudaSuccess || cudaMallocAsync(&out[k], per * fb, st) != cudaSuccess)
       s = FRAC_ENOMEM;
-  }
+  if (s == FRAC_OK && wsb && cudaMallocAsync(&ws, wsb, st) != cudaSuccess) s = FRAC_ENOMEM;
+  for (int i = 0; i < 3 && s == FRAC_OK; ++i)
+    for (int k = 0; k < K && s == FRAC_OK; ++k)
+      if (cudaEventCreateWithFlags(&ev[i][k], cudaEventDisableTiming) != cudaSuccess) s = FRAC_ECUDA;
+  if (s == FRAC_OK && (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventRecord(fork, st) != cudaSuccess || cudaStreamWaitEvent(s_in, fork, 0) != cudaSuccess ||
+                       cudaStreamWaitEvent(s_cmp, fork, 0) != cudaSuccess ||
+                       cudaStreamWaitEvent(s_out, fork, 0) != cudaSuccess))
+    s = FRAC_ECUDA;
   for (int64_t c = 0; c < nch && s == FRAC_OK; ++c) {
-    const int i = (int)(c % ns);
+    const int k = (int)(c % K);
     const int64_t b0 = c * per, nb = std::min<int64_t>(per, batch - b0);
     const char* src = (const char*)u + b0 * fb;
     char* dst = (char*)y + b0 * fb;
-    if (cudaMemcpyAsync(bufs[i][0], src, nb * fb, cudaMemcpyHostToDevice, ss[i]) != cudaSuccess) {
+    // stage 1: the slot's input buffer is free once the apply of chunk c - K has read it
+    if ((c >= K && cudaStreamWaitEvent(s_in, ev[1][k], 0) != cudaSuccess) ||
+        cudaMemcpyAsync(in[k], src, nb * fb, cudaMemcpyHostToDevice, s_in) != cudaSuccess ||
+        cudaEventRecord(ev[0][k], s_in) != cudaSuccess) {
       s = FRAC_ECUDA;
       break;
     }
-    s = run_apply(op, bufs[i][0], bufs[i][1], dtype, nb, bufs[i][2], precond, ss[i]);
-    if (s == FRAC_OK && cudaMemcpyAsync(dst, bufs[i][1], nb * fb, cudaMemcpyDeviceToHost, ss[i]) != cudaSuccess)
+    // stage 2: after the input landed and the output copy of chunk c - K has read the output buffer
+    if (cudaStreamWaitEvent(s_cmp, ev[0][k], 0) != cudaSuccess ||
+        (c >= K && cudaStreamWaitEvent(s_cmp, ev[2][k], 0) != cudaSuccess)) {
+      s = FRAC_ECUDA;
+      break;
+    }
+    s = run_apply(op, in[k], out[k], dtype, nb, ws, precond, s_cmp);
+    if (s != FRAC_OK) break;
+    // stage 3
+    if (cudaEventRecord(ev[1][k], s_cmp) != cudaSuccess || cudaStreamWaitEvent(s_out, ev[1][k], 0) != cudaSuccess ||
+        cudaMemcpyAsync(dst, out[k], nb * fb, cudaMemcpyDeviceToHost, s_out) != cudaSuccess ||
+        cudaEventRecord(ev[2][k], s_out) != cudaSuccess)
       s = FRAC_ECUDA;
   }
-  for (int i = 0; i < ns; ++i) {
-    for (int k = 0; k < 3; ++k)
-      if (bufs[i][k]) cudaFreeAsync(bufs[i][k], ss[i]);
-    if (cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess &&
-        cudaEventRecord(join[i], ss[i]) == cudaSuccess)
-      cudaStreamWaitEvent(st, join[i], 0);
+  // join the three streams into the caller's stream, then free there
+  if (fork) {
+    const cudaStream_t three[3] = {s_in, s_cmp, s_out};
+    for (int i = 0; i < 3; ++i)
+      if (cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess &&
+          cudaEventRecord(join[i], three[i]) == cudaSuccess)
+        cudaStreamWaitEvent(st, join[i], 0);
   }
+  for (int k = 0; k < K; ++k) {
+    if (in[k]) cudaFreeAsync(in[k], st);
+    if (out[k]) cudaFreeAsync(out[k], st);
+  }
+  if (ws) cudaFreeAsync(ws, st);
   const cudaError_t e = cudaStreamSynchronize(st);
   if (s == FRAC_OK && e != cudaSuccess) s = FRAC_ECUDA;
+  for (int i = 0; i < 3; ++i) {
+    for (int k = 0; k < K; ++k)
+      if (ev[i][k]) cudaEventDestroy(ev[i][k]);
+    if (join[i]) cudaEventDestroy(join[i]);
+  }
+  if (fork) cudaEventDestroy(fork);
   return s;
 }
 

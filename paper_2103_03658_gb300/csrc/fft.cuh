@@ -5,7 +5,9 @@
 // i + i/16 (breaks the power-of-two strides of the butterfly writes into
 // distinct banks) and a line stride LS = line_stride(M) (odd, so that the same
 // element of consecutive lines falls in different banks when a tile of
-// columns is loaded with one lane per line).
+// columns is loaded with one lane per line).  Column tiles (lanes of 4 or 2
+// lines interleaved) pad every 2^tile_shift(M) entries instead, with their own
+// stride line_stride_tile(M).
 //
 // Pass p of radix R = 2^b with sub-transform length Ns (product of the
 // earlier radices): butterfly j in [0, M/R) reads x[j + r M/R], multiplies
@@ -34,14 +36,24 @@ __host__ __device__ constexpr int tpl(int logm) { return (1 << logm) / elems(log
 __host__ __device__ constexpr int line_stride(int logm) {
   return (1 << logm) + ((1 << logm) >> 4) + 1;
 }
+// Padding shift of the lines of a column tile: one pad entry every 2^SH entries.
+// SH = 4 unless the first pass has radix 8 or less (M = 32, 64, 512): its
+// butterflies then write R-entry runs at j R, and with a pad every 16 entries
+// two lanes of a half-warp land on the same bank slot; one pad per R entries
+// (SH = log2 R) spreads them.
+__host__ __device__ constexpr int tile_shift(int logm) {
+  return npasses(logm) > 1 && pass_bits(logm, 0) < 4 ? pass_bits(logm, 0) : 4;
+}
 // Line stride for tiles whose lanes interleave 4 (FP32) or 2 (FP64) lines with the
 // line index fastest: a stride of 4 mod 16 puts the 16 lanes of a half-warp
 // (4 lines x 4 consecutive entries) in 16 distinct 8-byte bank slots.
 __host__ __device__ constexpr int line_stride_tile(int logm) {
-  return (1 << logm) + ((1 << logm) >> 4) + ((4 - (((1 << logm) + ((1 << logm) >> 4)) & 15)) & 15);
+  return (1 << logm) + ((1 << logm) >> tile_shift(logm)) +
+         ((4 - (((1 << logm) + ((1 << logm) >> tile_shift(logm))) & 15)) & 15);
 }
 
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+template <int SH = 4>
+__device__ __forceinline__ int pidx(int i) { return i + (i >> SH); }
 
 // cos(2 pi k / 16) for k in [0, 16)
 __host__ __device__ constexpr double cos16_0_8(int k) {
@@ -189,7 +201,7 @@ __device__ __forceinline__ void pass(C* __restrict__ buf, int tl, const C* __res
 // skip the butterflies' dead halves.
 // ---------------------------------------------------------------------------
 
-template <typename C, int LOGM, int P, bool INV, bool ZIN, bool ZOUT>
+template <typename C, int LOGM, int P, bool INV, bool ZIN, bool ZOUT, int SH>
 __device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
   constexpr int M = 1 << LOGM;
   constexpr int NP = npasses(LOGM);
@@ -202,6 +214,7 @@ __device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ bu
   constexpr int NB = E / R;
   constexpr int TWS = M / (Ns * R);
   constexpr bool FIRST = (P == 0), LAST = (P == NP - 1);
+  constexpr int Q = 1 << SH;  // pad block: pidx<SH>(i) = i + i / Q
   C w[E];
   if constexpr (FIRST) {
     // butterfly j < M/R reads j + r M/R, which lies in the zero half iff r >= R/2
@@ -213,13 +226,13 @@ __device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ bu
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = tl + b * TPL;
-      if constexpr ((M / R) % 16 == 0) {  // pidx(j + c) = pidx(j) + pidx(c) for c a multiple of 16
-        const C* src = buf + pidx(j);
+      if constexpr ((M / R) % Q == 0) {  // pidx(j + c) = pidx(j) + pidx(c) for c a multiple of Q
+        const C* src = buf + pidx<SH>(j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) w[b * R + r] = src[r * (M / R) + ((r * (M / R)) >> 4)];
+        for (int r = 0; r < R; ++r) w[b * R + r] = src[r * (M / R) + ((r * (M / R)) >> SH)];
       } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) w[b * R + r] = buf[pidx(j + r * (M / R))];
+        for (int r = 0; r < R; ++r) w[b * R + r] = buf[pidx<SH>(j + r * (M / R))];
       }
     }
     if constexpr (!LAST) __syncthreads();  // every read of this pass done before its writes
@@ -257,37 +270,38 @@ __device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ bu
       for (int r = 0; r < (ZOUT ? R / 2 : R); ++r) v[b + r * NB] = w[b * R + r];
     } else {
       const int base = ((j >> NSB) << (NSB + RB)) + k;
-      if constexpr (Ns % 16 == 0) {
-        C* dst = buf + pidx(base);
+      if constexpr (Ns % Q == 0) {
+        C* dst = buf + pidx<SH>(base);
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[r * Ns + ((r * Ns) >> 4)] = w[b * R + r];
-      } else if constexpr (Ns == 1 && 16 % R == 0) {  // base = j R: base + r stays in one 16-block
-        C* dst = buf + pidx(base);
+        for (int r = 0; r < R; ++r) dst[r * Ns + ((r * Ns) >> SH)] = w[b * R + r];
+      } else if constexpr (Ns == 1 && Q % R == 0) {  // base = j R: base + r stays in one Q-block
+        C* dst = buf + pidx<SH>(base);
 #pragma unroll
         for (int r = 0; r < R; ++r) dst[r] = w[b * R + r];
       } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[pidx(base + r * Ns)] = w[b * R + r];
+        for (int r = 0; r < R; ++r) buf[pidx<SH>(base + r * Ns)] = w[b * R + r];
       }
     }
   }
   if constexpr (!LAST) __syncthreads();  // writes visible to the next pass
 }
 
-template <typename C, int LOGM, bool INV, bool ZIN, bool ZOUT, int P = 0>
+template <typename C, int LOGM, bool INV, bool ZIN, bool ZOUT, int SH, int P = 0>
 __device__ __forceinline__ void reg_passes(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
   if constexpr (P < npasses(LOGM)) {
-    reg_pass<C, LOGM, P, INV, ZIN, ZOUT>(v, buf, tl, tw);
-    reg_passes<C, LOGM, INV, ZIN, ZOUT, P + 1>(v, buf, tl, tw);
+    reg_pass<C, LOGM, P, INV, ZIN, ZOUT, SH>(v, buf, tl, tw);
+    reg_passes<C, LOGM, INV, ZIN, ZOUT, SH, P + 1>(v, buf, tl, tw);
   }
 }
 
 // FFT of the line held in registers (see above); `buf` is the line's shared
-// buffer (line_stride(LOGM) entries), used only when there is more than one pass.
-template <typename C, int LOGM, bool INV, bool ZIN = false, bool ZOUT = false>
+// buffer, used only when there is more than one pass: line_stride(LOGM)
+// entries with SH = 4, line_stride_tile(LOGM) with SH = tile_shift(LOGM).
+template <typename C, int LOGM, bool INV, bool ZIN = false, bool ZOUT = false, int SH = 4>
 __device__ __forceinline__ void fft_reg(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
   if constexpr (npasses(LOGM) > 1) __syncthreads();  // earlier users of buf are done
-  reg_passes<C, LOGM, INV, ZIN, ZOUT>(v, buf, tl, tw);
+  reg_passes<C, LOGM, INV, ZIN, ZOUT, SH>(v, buf, tl, tw);
 }
 
 template <typename C, int LOGM, bool INV, int P = 0>

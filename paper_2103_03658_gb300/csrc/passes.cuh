@@ -272,7 +272,8 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
     }
   }
   // ---- transforms
-  if (MODE != YINV) fft_reg<C, LOGM, false, !ODD, false>(v, buf, tl, tw);
+  constexpr int SH = tile_shift(LOGM);
+  if (MODE != YINV) fft_reg<C, LOGM, false, !ODD, false, SH>(v, buf, tl, tw);
   if (MODE == SYM2 || MODE == ZSYM) {
     const T* lrow = (MODE == SYM2) ? lam + k1 : lam + (int64_t)k2r * K + k1;
     const int64_t kstride = (MODE == SYM2) ? K : (int64_t)A.Ky * K;
@@ -283,7 +284,7 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
       v[e] = cscale(v[e], live ? lrow[kr * kstride] : T(0));
     }
   }
-  if (MODE != YFWD) fft_reg<C, LOGM, true, false, !ODD>(v, buf, tl, tw);  // keeps j < n (ODD: 1..n) only
+  if (MODE != YFWD) fft_reg<C, LOGM, true, false, !ODD, SH>(v, buf, tl, tw);  // keeps j < n (ODD: 1..n) only
   // ---- store
   if (!live) return;
   if (MODE == YFWD) {

@@ -200,7 +200,7 @@ def test_apply_batch_equals_single_and_host_buffers():
 @pytest.mark.parametrize("dtype,batch", [("f32", 29), ("f64", 13)])
 def test_apply_host_buffers_pipelined_equals_device(dtype, batch):
     """Large host batches (twice the 28 MB chunk or more; here >= 96 MB) go through the chunked
-    copy/compute pipeline of the library (several streams); every field must match the device-buffer
+    copy/apply/copy pipeline of the library (three streams, a ring of device buffers); every field must match the device-buffer
     apply of the whole batch, from pageable and from pinned host memory.  Rows are
     paired two per complex FFT across the batch, so a chunk boundary changes which rows
     share a transform: equal up to the FFT's rounding (normwise 1e-6 FP32, 1e-14 FP64)."""
