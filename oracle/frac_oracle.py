@@ -433,36 +433,45 @@ def norm_bound(a: np.ndarray, c: float, n) -> float:
 # Boundary vector b  (Eq. (1D-scheme): b_i; Eq. (2D-scheme): b_ij)
 # ---------------------------------------------------------------------------
 
-def boundary_vector(d: int, N: int, h: float, alpha: float, a: np.ndarray, c: float, g,
-                    lam: float = 0.0, lo: float = -1.0, nq: int = 96) -> np.ndarray:
-    """-c b_i for every interior point: b_i is the near-field sum of a_{|o|} g
-    over the exterior grid points x_i + o h (o in [-N, N]^d) plus the far field
-    sum_{m in varkappa_1} int over Upsilon_+^c of g(x_i + (-1)^m o xi)
-    |xi|^{-d-alpha} exp(-lambda |xi|) dxi  (Eq. (L2)).
-
-    ``g`` maps an array (..., d) of points to values.  The far-field integral
-    uses xi = rho (1, s) with rho = L / t: rho^{-1-alpha} d rho = L^{-alpha}
-    t^{alpha-1} dt, integrated by Gauss-Jacobi in t and Gauss-Legendre in s.
-    """
-    n = N - 1
-    L = N * h
-    # near field over exterior points, index range [1-N, 2N-1] per axis (paper indexing)
+def extended_samples(d: int, N: int, h: float, g, lo: float = -1.0) -> np.ndarray:
+    """g at the extended grid points lo + e h, e in [1-N, 2N-1]^d (axis i of the
+    array = coordinate i), zero at the interior points e in [1, N-1]^d (there the
+    unknown u, not g, enters the scheme).  Shape (3N-1,)*d."""
     ext = np.arange(1 - N, 2 * N)
     grids = np.meshgrid(*([lo + ext * h] * d), indexing="ij")
-    P = np.stack(grids, axis=-1)
-    G = g(P)
+    G = g(np.stack(grids, axis=-1))
     inside = np.ones(G.shape, dtype=bool)
     for i in range(d):
         shape = [1] * d
         shape[i] = len(ext)
         inside = inside & ((ext >= 1) & (ext <= N - 1)).reshape(shape)
-    G = np.where(inside, 0.0, G)
+    return np.where(inside, 0.0, G)
+
+
+def boundary_near(a: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """Near-field part of Eq. (L2) at every interior point: sum over o in [-N, N]^d
+    of a_{|o|} G[x_i + o h], G the extended samples (``extended_samples``; zero
+    inside, so only exterior points count).  Shape (N-1,)*d."""
+    d = G.ndim
+    N = (G.shape[0] + 1) // 3
+    n = N - 1
     near = np.zeros((n,) * d)
     for o in itertools.product(range(-N, N + 1), repeat=d):
         coef = a[tuple(abs(t) for t in o)]
         sl = tuple(slice(N + t, N + t + n) for t in o)   # interior index i+1 -> ext offset (i+1)-(1-N)
         near += coef * G[sl]
-    # far field
+    return near
+
+
+def boundary_far(d: int, N: int, h: float, alpha: float, g, lam: float = 0.0, lo: float = -1.0,
+                 nq: int = 96) -> np.ndarray:
+    """Far-field part of Eq. (L2) at every interior point:
+    sum_{m in varkappa_1} int over Upsilon_+^c of g(x_i + (-1)^m o xi)
+    |xi|^{-d-alpha} exp(-lambda |xi|) dxi.  xi = rho (1, s) with rho = L / t:
+    rho^{-1-alpha} d rho = L^{-alpha} t^{alpha-1} dt, integrated by Gauss-Jacobi
+    in t and Gauss-Legendre in s.  Shape (N-1,)*d."""
+    n = N - 1
+    L = N * h
     xt, wt = special.roots_jacobi(nq, 0.0, alpha - 1.0)     # weight (1+x)^{alpha-1} on [-1, 1]
     t = 0.5 * (xt + 1.0)
     wt = wt * 0.5 ** alpha                                   # int_0^1 t^{alpha-1} f(t) dt
@@ -489,6 +498,17 @@ def boundary_vector(d: int, N: int, h: float, alpha: float, a: np.ndarray, c: fl
                     pts = X[..., None, :] + rho[ti] * sd            # (n..,Q,d)
                     wq = WS * cs ** (-d - alpha) * np.exp(-lam * rho[ti] * cs)
                     far += L ** (-alpha) * wt[ti] * np.sum(wq * g(pts), axis=-1)
+    return far
+
+
+def boundary_vector(d: int, N: int, h: float, alpha: float, a: np.ndarray, c: float, g,
+                    lam: float = 0.0, lo: float = -1.0, nq: int = 96) -> np.ndarray:
+    """-c b_i for every interior point: b_i is the near-field sum of a_{|o|} g
+    over the exterior grid points x_i + o h (o in [-N, N]^d, ``boundary_near``)
+    plus the far field (``boundary_far``), Eq. (L2).  ``g`` maps an array
+    (..., d) of points to values."""
+    near = boundary_near(a, extended_samples(d, N, h, g, lo))
+    far = boundary_far(d, N, h, alpha, g, lam, lo, nq)
     return -c * (near + far)
 
 
