@@ -190,17 +190,43 @@ typedef struct frac_solve_info {
 } frac_solve_info;
 
 /*
- * frac_solve -- solve A u = f for one right-hand side (the fractional Poisson
- * problem Eq. (Poisson)-(BC) with g = 0; Example 3.2.3 asks for an FFT-based
+ * frac_boundary -- boundary vector of nonhomogeneous exterior data g (Eq. (L2),
+ * the b of the schemes' matrix forms in 1D and 2D):
+ *   b_i = -c (near_i + far_i),  near_i = sum over o in [-N, N]^d of
+ *   a_{|o|} g(x_i + o h) over the points x_i + o h outside the domain,
+ * far_i the integrals of g over the far region (the sum over the 2^d
+ * reflections of int over Upsilon_+^c of g(x_i + s xi) |xi|^{-d-alpha}
+ * e^{-lambda |xi|} dxi), which depend on g beyond every grid point and are the
+ * caller's.  Then A u = f - b is the discrete problem with u = g outside
+ * (frac_solve takes b as its g argument).
+ *   g_ext: (3N - 1)^d doubles, g at the grid points x_0 + e h (x_0 the domain's
+ *          lower corner), e in [1 - N, 2N - 1] per axis, axis 0 fastest as in u;
+ *          the interior points are e in [1, N - 1]^d and their values are not read.
+ *   far:   prod(n_i) doubles, or NULL for zero (g of compact support within
+ *          reach of the grid).
+ *   b:     prod(n_i) doubles, written.
+ * Device or host pointers (host buffers are staged).  The near field is a
+ * convolution on a circulant of side nextpow2(3N - 1) in FP64 (d = 2, 3: a
+ * transient (nextpow2(3N - 1))^d complex array, 17 GB at 3D N = 257) or a direct
+ * sum (d = 1).  Synchronises `stream`.  Errors: FRAC_EINVAL (NULL op/g_ext/b),
+ * FRAC_ENOTSUP (unequal extents), FRAC_ENOMEM, FRAC_ECUDA (including a failed
+ * device bounds check, named by frac_error_detail).
+ */
+int frac_boundary(const frac_op* op, const double* g_ext, const double* far, double* b, void* stream);
+
+/*
+ * frac_solve -- solve A u = f - g for one right-hand side (the fractional
+ * Poisson problem Eq. (Poisson)-(BC); Example 3.2.3 asks for an FFT-based
  * fast solver without naming one).  A is symmetric positive
  * definite, so the solver is conjugate gradients with the FFT apply, either in
  * FP64 or as FP32 CG inside FP64 iterative refinement.  f and u hold prod(n_i)
- * doubles (device or host).  g must be NULL (nonhomogeneous data:
- * FRAC_ENOTSUP).  `info` is a host pointer filled before return (the call
- * synchronises `stream`).  Errors: FRAC_EINVAL (NULL op/f/u/opts/info, rtol
- * <= 0, max_iter < 1, unknown precision, non-finite f), FRAC_ENOTSUP,
- * FRAC_ENOCONV / FRAC_EBREAKDOWN (u holds the last iterate, info filled),
- * FRAC_ENOMEM, FRAC_ECUDA.
+ * doubles (device or host).  g is NULL (homogeneous exterior data) or the
+ * boundary vector b of frac_boundary (prod(n_i) doubles, device or host); the
+ * residual of info->rel_resid is then relative to ||f - g||.  `info` is a host
+ * pointer filled before return (the call synchronises `stream`).  Errors:
+ * FRAC_EINVAL (NULL op/f/u/opts/info, rtol <= 0, max_iter < 1, unknown
+ * precision, non-finite host f or g), FRAC_ENOCONV / FRAC_EBREAKDOWN (u holds
+ * the last iterate, info filled), FRAC_ENOMEM, FRAC_ECUDA.
  */
 int frac_solve(const frac_op* op, const double* f, const double* g, double* u,
                const frac_solve_opts* opts, frac_solve_info* info, void* stream);

@@ -96,6 +96,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.frac_precond.restype = i32
     lib.frac_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.frac_solve.restype = i32
+    lib.frac_boundary.argtypes = [vp, vp, vp, vp, vp]
+    lib.frac_boundary.restype = i32
     lib.frac_solve_batch.argtypes = [i64, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
     lib.frac_solve_batch.restype = i32
@@ -290,19 +292,43 @@ class FracOp:
             raise FracError(s, "frac_precond")
         return z
 
+    # -- boundary vector of exterior data --
+    def boundary(self, g_ext, far=None, out=None, stream=None):
+        """b = -c (near + far) (frac_boundary): g_ext holds g at the (3N-1)^d grid
+        points e in [1-N, 2N-1]^d (shape (3N-1,)*d, float64; interior values unread),
+        far the caller's far-field integrals (shape of u) or None."""
+        if _dtype_code(g_ext) != F64 or (far is not None and _dtype_code(far) != F64):
+            raise TypeError("boundary takes float64 data")
+        E = 3 * (max(self.ns) + 1) - 1
+        numel = g_ext.size if isinstance(g_ext, np.ndarray) else g_ext.numel()
+        if numel != E ** self.d:
+            raise ValueError(f"g_ext has {numel} values, expected (3N-1)^d = {E ** self.d}")
+        if out is None:
+            if isinstance(g_ext, np.ndarray):
+                out = np.empty(self.shape, dtype=np.float64)
+            else:
+                import torch
+                out = torch.empty(self.shape, dtype=torch.float64, device=g_ext.device)
+        s = self._lib.frac_boundary(self._h, _ptr(g_ext), None if far is None else _ptr(far), _ptr(out),
+                                    _stream(stream))
+        if s != 0:
+            raise FracError(s, "frac_boundary")
+        return out
+
     # -- solve --
     def solve(self, f, u=None, rtol: float = 1e-10, max_iter: int = 200000, precision: str = "mixed",
-              inner_tol: float = 0.0, stream=None, precond: str = "tau"):
-        """Solve A u = f (g = 0); returns (u, info dict).  f, u float64."""
-        if _dtype_code(f) != F64:
+              inner_tol: float = 0.0, stream=None, precond: str = "tau", g=None):
+        """Solve A u = f - g (g: None, or the boundary vector of ``boundary``); returns
+        (u, info dict).  f, u, g float64."""
+        if _dtype_code(f) != F64 or (g is not None and _dtype_code(g) != F64):
             raise TypeError("solve takes float64 data")
         use_x0 = u is not None
         if u is None:
             u = _empty_like(f)
         opts = _opts(rtol, max_iter, precision, use_x0, inner_tol, precond)
         info = SolveInfo()
-        s = self._lib.frac_solve(self._h, _ptr(f), None, _ptr(u), ctypes.byref(opts), ctypes.byref(info),
-                                 _stream(stream))
+        s = self._lib.frac_solve(self._h, _ptr(f), None if g is None else _ptr(g), _ptr(u), ctypes.byref(opts),
+                                 ctypes.byref(info), _stream(stream))
         out = {k: getattr(info, k) for k, _ in SolveInfo._fields_}
         if s not in (0, 4):
             raise FracError(s, "frac_solve")

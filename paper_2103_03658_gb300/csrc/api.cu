@@ -417,24 +417,77 @@ int frac_precond(const frac_op* op, const void* r, void* z, int dtype, int64_t b
   return apply_entry(op, r, z, dtype, batch, stream, true);
 }
 
+int frac_boundary(const frac_op* op, const double* g_ext, const double* far, double* b, void* stream) {
+  if (!op || !g_ext || !b) return FRAC_EINVAL;
+  if (!op->square) return FRAC_ENOTSUP;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int d = op->prob.d;
+  int64_t ne = 1;
+  for (int i = 0; i < d; ++i) ne *= 3 * op->N - 1;
+  const size_t gbytes = ne * sizeof(double), bbytes = op->nd * sizeof(double);
+  const bool dgx = is_device_ptr(g_ext), dfar = far && is_device_ptr(far), db = is_device_ptr(b);
+  double *tg = nullptr, *tfar = nullptr, *tb = nullptr;
+  int s = FRAC_OK;
+  if (!dgx && cudaMallocAsync(&tg, gbytes, st) == cudaSuccess)
+    s = cudaMemcpyAsync(tg, g_ext, gbytes, cudaMemcpyHostToDevice, st) == cudaSuccess ? FRAC_OK : FRAC_ECUDA;
+  else if (!dgx)
+    s = FRAC_ENOMEM;
+  if (s == FRAC_OK && far && !dfar) {
+    if (cudaMallocAsync(&tfar, bbytes, st) != cudaSuccess)
+      s = FRAC_ENOMEM;
+    else if (cudaMemcpyAsync(tfar, far, bbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      s = FRAC_ECUDA;
+  }
+  if (s == FRAC_OK && !db && cudaMallocAsync(&tb, bbytes, st) != cudaSuccess) s = FRAC_ENOMEM;
+  if (s == FRAC_OK)
+    s = boundary_device(op, dgx ? g_ext : tg, far ? (dfar ? far : tfar) : nullptr, db ? b : tb, st);
+  if (s == FRAC_OK && !db && cudaMemcpyAsync(b, tb, bbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    s = FRAC_ECUDA;
+  if (tg) cudaFreeAsync(tg, st);
+  if (tfar) cudaFreeAsync(tfar, st);
+  if (tb) cudaFreeAsync(tb, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (s == FRAC_OK && e != cudaSuccess) s = FRAC_ECUDA;
+  return s;
+}
+
 int frac_solve(const frac_op* op, const double* f, const double* g, double* u, const frac_solve_opts* opts,
                frac_solve_info* info, void* stream) {
   if (!op || !f || !u || !opts || !info) return FRAC_EINVAL;
-  if (g) return FRAC_ENOTSUP;
   if (!(opts->rtol > 0.0) || opts->max_iter < 1) return FRAC_EINVAL;
   if (opts->precision != FRAC_PLAIN_F64 && opts->precision != FRAC_MIXED_IR) return FRAC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = op->nd * sizeof(double);
-  const bool df = is_device_ptr(f), du = is_device_ptr(u);
+  const bool df = is_device_ptr(f), du = is_device_ptr(u), dg = g && is_device_ptr(g);
   const double* fd = f;
   double* ud = u;
-  double *tf = nullptr, *tu = nullptr;
+  double *tf = nullptr, *tu = nullptr, *tg = nullptr;
   if (!df) {
     for (int64_t i = 0; i < op->nd; ++i)
       if (!std::isfinite(f[i])) return FRAC_EINVAL;
+  }
+  if (g && !dg) {
+    for (int64_t i = 0; i < op->nd; ++i)
+      if (!std::isfinite(g[i])) return FRAC_EINVAL;
+  }
+  if (!df || g) {  // device right-hand side: f, or f - g
     FRAC_CUDA_TRY(cudaMallocAsync(&tf, bytes, st));
-    FRAC_CUDA_TRY(cudaMemcpyAsync(tf, f, bytes, cudaMemcpyHostToDevice, st));
+    if (!df) FRAC_CUDA_TRY(cudaMemcpyAsync(tf, f, bytes, cudaMemcpyHostToDevice, st));
     fd = tf;
+  }
+  if (g) {
+    const double* gd = g;
+    if (!dg) {
+      FRAC_CUDA_TRY(cudaMallocAsync(&tg, bytes, st));
+      FRAC_CUDA_TRY(cudaMemcpyAsync(tg, g, bytes, cudaMemcpyHostToDevice, st));
+      gd = tg;
+    }
+    const int s0 = subtract_device(df ? f : tf, gd, tf, op->nd, st);
+    if (tg) cudaFreeAsync(tg, st);
+    if (s0 != FRAC_OK) {
+      cudaFreeAsync(tf, st);
+      return s0;
+    }
   }
   if (!du) {
     FRAC_CUDA_TRY(cudaMallocAsync(&tu, bytes, st));

@@ -34,6 +34,12 @@ struct CGState {
 // coeffs.cu
 int prepare_twiddles(int logm);
 int build_coefficients(frac_op* op, cudaStream_t st);
+int generator_symbol_cube(const frac_op* op, int logm, double* out, double* tmp, cudaStream_t st);
+int take_coeff_fault();
+
+// boundary.cu: b = -c (near + far) on device buffers (frac_boundary), and r = f - g.
+int boundary_device(const frac_op* op, const double* g_ext, const double* far, double* b, cudaStream_t st);
+int subtract_device(const double* f, const double* g, double* r, int64_t count, cudaStream_t st);
 
 // apply.cu: y = A u for `batch` vectors on device buffers; ws holds
 // apply_workspace_bytes(op, dtype, batch) bytes (unused for d = 1).

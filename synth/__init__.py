@@ -25,6 +25,16 @@ def interior_grid(n: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     return lo + h * np.arange(1, n + 1)
 
 
+def extended_points(d: int, n: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """The grid points lo + e h, e in [1-N, 2N-1] per axis (N = n + 1, h = (hi - lo) / N):
+    the interior grid and the exterior points within N h of it, where nonhomogeneous
+    exterior data g is sampled.  Shape (3N-1,)*d + (d,), indexing "ij"."""
+    N = n + 1
+    h = (hi - lo) / N
+    e = lo + h * np.arange(1 - N, 2 * N)
+    return np.stack(np.meshgrid(*([e] * d), indexing="ij"), axis=-1)
+
+
 def radius2(d: int, n: int) -> np.ndarray:
     x = interior_grid(n)
     grids = np.meshgrid(*([x] * d), indexing="ij")

@@ -1,0 +1,163 @@
+"""GPU parity, the boundary vector of nonhomogeneous exterior data (frac_boundary,
+Eq. (L2)) and solves with it (frac_solve's g).
+
+Bars: the near field against the oracle's (``boundary_near`` with the oracle's
+generator) entrywise within 1e-12 c sum|a| max|G| plus the generator difference
+c sum|a_gpu - a_oracle| max|G| (both sides sum the same products; the GPU by an
+FP64 FFT of side nextpow2(3N-1), error ~ eps log2 M' sum|a| max|G|); the far
+input passes through as -c far; constants are annihilated at full size; and the
+paper's own examples with exterior data (Tables 3-1-3, 3-2-2) are reproduced with
+the GPU's near field and solve (the far integrals of g, which depend on g off the
+grid, from the oracle).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import frac_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _op(d, n, p, alpha, lam=0.0):
+    import paper_2103_03658_gb300 as fg
+    return fg.FracOp(d, n, alpha, degree=p, lam=lam)
+
+
+def _unit(v):
+    return 10.0 ** (math.floor(math.log10(abs(v))) - 4)
+
+
+def _random_ext(d, N, seed):
+    return np.random.default_rng(seed).standard_normal((3 * N - 1,) * d)
+
+
+# sizes span one and several FFT tiles, ragged M' (3N-1 just above and below a power of two), all kinds
+CASES = [(1, 1, 1, 1.2, 0.0), (1, 15, 2, 0.5, 0.0), (1, 341, 1, 1.7, 0.8), (1, 2047, 0, 1.1, 0.0),
+         (2, 1, 1, 1.0, 0.0), (2, 2, 1, 0.6, 0.0), (2, 9, 2, 1.5, 0.0), (2, 21, 0, 0.9, 1.1), (2, 42, 1, 1.9, 0.0),
+         (2, 63, 2, 0.3, 0.0), (3, 1, 1, 1.4, 0.0), (3, 3, 2, 0.8, 0.0), (3, 6, 1, 1.2, 0.5), (3, 11, 1, 1.6, 0.0)]
+
+
+@pytest.mark.parametrize("d,n,p,alpha,lam", CASES)
+def test_near_field_matches_oracle(d, n, p, alpha, lam):
+    N = n + 1
+    h = 2.0 / N
+    a = O.stencil(d, N, h, alpha, p, lam, q=20 if d < 3 else 12)
+    c = O.c_dalpha(d, alpha)
+    G = _random_ext(d, N, 7 * n + d)
+    G_in = G.copy()
+    ext = np.arange(1 - N, 2 * N)
+    inside = np.ones(G.shape, dtype=bool)
+    for i in range(d):
+        shape = [1] * d
+        shape[i] = len(ext)
+        inside = inside & ((ext >= 1) & (ext <= N - 1)).reshape(shape)
+    G_in[inside] = 1e300                           # interior samples must not be read
+    G[inside] = 0.0
+    ref = -c * O.boundary_near(a, G)
+    op = _op(d, n, p, alpha, lam)
+    b = op.boundary(torch.tensor(G_in, device="cuda")).cpu().numpy()
+    da = np.abs(op.generator() - a)
+    gmax = np.max(np.abs(G))
+    K = np.indices(a.shape)
+    mult = 2.0 ** np.sum(K > 0, axis=0)              # each a_k stands for 2^{#nonzero k_i} offsets
+    tol = c * gmax * (1e-12 * np.sum(mult * np.abs(a)) + np.sum(mult * da))
+    assert b.shape == (n,) * d
+    assert np.max(np.abs(b - ref)) <= tol, (np.max(np.abs(b - ref)), tol)
+    # host buffers give the same
+    bh = op.boundary(G_in)
+    assert np.array_equal(bh, b)
+    op.close()
+
+
+@pytest.mark.parametrize("d,n", [(1, 100), (2, 30), (3, 9)])
+def test_far_input_adds_minus_c_far(d, n):
+    N = n + 1
+    op = _op(d, n, 1, 1.3)
+    c = op.info()["c_dalpha"]
+    G = torch.tensor(_random_ext(d, N, 3), device="cuda")
+    F = torch.tensor(np.random.default_rng(4).standard_normal((n,) * d), device="cuda")
+    b0 = op.boundary(G)
+    b1 = op.boundary(G, far=F)
+    assert torch.allclose(b1, b0 - c * F, rtol=1e-14, atol=1e-14 * float(F.abs().max()) * c)
+    op.close()
+
+
+@pytest.mark.parametrize("d,n,p,alpha", [(1, 4095, 1, 1.5), (2, 1023, 2, 1.2), (3, 255, 1, 1.6)])
+def test_constant_is_annihilated_at_full_size(d, n, p, alpha):
+    """u = 1 inside and g = 1 outside: A 1 + b(1) = 0 when far = 2^d F_d (the far
+    integrals of a constant), whatever the size (a_0 completes the generator sum)."""
+    N = n + 1
+    op = _op(d, n, p, alpha)
+    inf = op.info()
+    G = torch.ones((3 * N - 1,) * d, dtype=torch.float64, device="cuda")
+    far = torch.full((n,) * d, 2.0 ** d * inf["far_field"], dtype=torch.float64, device="cuda")
+    b = op.boundary(G, far=far)
+    one = torch.ones((n,) * d, dtype=torch.float64, device="cuda")
+    r = op.apply(one) + b
+    scale = inf["norm_bound"]                        # c max|symbol| >= c |a_0|, the size of the terms
+    assert float(r.abs().max()) <= 1e-11 * scale, (float(r.abs().max()), scale)
+    op.close()
+
+
+def _table(name):
+    with open(os.path.join(GOLD, name + ".json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("al,p,hh", [(0.5, 1, 0.0625), (1.7, 2, 0.015625), (1.0, 0, 0.03125)])
+def test_table_3_1_3_with_gpu_near_field(al, p, hh):
+    """1D, u = 1/(1+x^2) on (-1, 1) with g = u outside: max |A u + b - f| against the printed error."""
+    G = _table("table_3_1_3")
+    ref = G["entries"][str(al)][str(p)][G["h"].index(hh)]
+    N = int(round(2 / hh))
+    n = N - 1
+    h = 2.0 / N
+    g = lambda P: 1.0 / (1.0 + P[..., 0] ** 2)  # noqa: E731
+    far = O.boundary_far(1, N, h, al, g)
+    op = _op(1, n, p, al)
+    b = op.boundary(g(synth.extended_points(1, n)), far=far)
+    x = synth.interior_grid(n)
+    Au = op.apply(torch.tensor(1.0 / (1.0 + x * x), device="cuda")).cpu().numpy()
+    err = np.max(np.abs(Au + b - O.fl_lorentzian_1d(al, x)))
+    floor = max(8 * np.finfo(np.float64).eps * op.info()["norm_bound"], 5e-13)
+    assert abs(err - ref) <= 0.51 * _unit(ref) + floor, (err, ref)
+    op.close()
+
+
+@pytest.mark.parametrize("al", [0.7, 1.9])
+@pytest.mark.parametrize("hh", [0.125, 0.03125])
+def test_table_3_2_2_with_gpu_boundary_and_solve(al, hh):
+    """2D, p = 1, g = exp(-|x|^2) outside: frac_boundary (GPU near field, far from the
+    oracle) then frac_solve with g = b; the error against exp(-|x|^2) is the printed one."""
+    G = _table("table_3_2_2")
+    ref = G["entries"][str(al)][G["h"].index(hh)]
+    N = int(round(2 / hh))
+    n = N - 1
+    h = 2.0 / N
+    g = lambda P: np.exp(-np.sum(P * P, axis=-1))  # noqa: E731
+    far = O.boundary_far(2, N, h, al, g)
+    op = _op(2, n, 1, al)
+    b = op.boundary(torch.tensor(g(synth.extended_points(2, n)), device="cuda"),
+                    far=torch.tensor(far, device="cuda"))
+    r2 = synth.radius2(2, n)
+    f = torch.tensor(O.fl_gaussian(2, al, r2), device="cuda")
+    u, info = op.solve(f, rtol=1e-12, precision="mixed", g=b)
+    assert info["status"] == 0 and info["rel_resid"] <= 1e-12
+    err = np.max(np.abs(u.cpu().numpy() - np.exp(-r2)))
+    assert abs(err - ref) <= 0.51 * _unit(ref), (err, ref)
+    op.close()
