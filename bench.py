@@ -425,6 +425,7 @@ def extra_measurements(fg, torch, u32, op, barrier) -> dict:
     out["solves"] = solves
     out["applies"] = apply_measurement(fg, torch, barrier)
     out["operator_builds"] = build_measurement(fg, barrier)
+    out["boundary"] = boundary_measurement(fg, torch, barrier)
     out["batch"] = batch_measurement(fg, torch, barrier)
     out["served"] = served_measurement(fg, torch, barrier)
     return out
@@ -453,6 +454,40 @@ def apply_measurement(fg, torch, barrier) -> dict:
             unit = "us" if scale == 1e3 else "ms"
             out[f"{name}_{'f64' if dt == torch.float64 else 'f32'}_{unit}"] = e0.elapsed_time(e1) / 20 * scale
         op.close()
+    return out
+
+
+def boundary_measurement(fg, torch, barrier) -> dict:
+    """frac_boundary (near field of exterior data g = exp(-|x|^2), device buffers) at the largest
+    grid of each dimension: ms per call (3 calls after one warm-up; the call synchronises) and the
+    nominal FP64 rate of its line FFTs (5 M' log2 M' flops per line, M' = nextpow2(3N - 1), the
+    lines each pass transforms); d = 1 is a direct sum (2N + 1 products per point)."""
+    out = {}
+    for name, (d, n, p, alpha) in (("1d_n4095", (1, 4095, 1, 1.5)), ("2d_n1023", (2, 1023, 2, 1.2)),
+                                   ("3d_n255", (3, 255, 1, 1.6))):
+        op = fg.FracOp(d, n, alpha, degree=p)
+        P = synth.extended_points(d, n)
+        G = torch.tensor(np.exp(-np.sum(P * P, axis=-1)), device="cuda")
+        del P
+        b = torch.empty((n,) * d, dtype=torch.float64, device="cuda")
+        op.boundary(G, out=b)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            op.boundary(G, out=b)
+        barrier()
+        ms = (time.perf_counter() - t0) / 3 * 1e3
+        N = n + 1
+        E = 3 * N - 1
+        Mp = 1 << (E - 1).bit_length()
+        if d == 1:
+            flops = 2.0 * n * (2 * N + 1)
+        else:
+            lines = E + 2 * Mp + n if d == 2 else E * E + Mp * E + 2 * Mp * Mp + Mp * n + n * n
+            flops = lines * 5.0 * Mp * math.log2(Mp)
+        out[name] = {"ms": ms, "fft_side": Mp if d > 1 else None, "nominal_fp64_gflops": flops / (ms * 1e-3) / 1e9}
+        op.close()
+        del G, b
     return out
 
 
@@ -588,6 +623,8 @@ def main():
                     help="fields per apply (65 = the benchmark workload; fewer only for profiler captures)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the 256-problem batch measurement and print its JSON (profiler captures)")
+    ap.add_argument("--boundary-only", action="store_true",
+                    help="run only the frac_boundary timings and print their JSON (profiler captures)")
     ap.add_argument("--applies-only", action="store_true",
                     help="run only the 1D and 3D single-vector apply timings and print their JSON (profiler captures)")
     args = ap.parse_args()
@@ -597,6 +634,11 @@ def main():
         import torch
         import paper_2103_03658_gb300 as fg
         print(json.dumps(apply_measurement(fg, torch, torch.cuda.synchronize)), flush=True)
+        return
+    if args.boundary_only:
+        import torch
+        import paper_2103_03658_gb300 as fg
+        print(json.dumps(boundary_measurement(fg, torch, torch.cuda.synchronize)), flush=True)
         return
     if args.batch_only:
         import torch
