@@ -56,6 +56,7 @@ def test_null_arguments(lib):
     opts = nat.SolveOpts(1e-10, 10, 0, 0, 0, 1e-4)
     info = nat.SolveInfo()
     assert lib.frac_solve(None, None, None, None, ctypes.byref(opts), ctypes.byref(info), None) == 1
+    assert lib.frac_boundary(None, None, None, None, None) == 1
     assert lib.frac_solve_batch(-1, None, None, None, None, None, None) == 1
     assert lib.frac_solve_batch(0, None, None, None, None, None, None) == 0
 
