@@ -461,7 +461,8 @@ def boundary_measurement(fg, torch, barrier) -> dict:
     """frac_boundary (near field of exterior data g = exp(-|x|^2), device buffers) at the largest
     grid of each dimension: ms per call (3 calls after one warm-up; the call synchronises) and the
     nominal FP64 rate of its line FFTs (5 M' log2 M' flops per line, M' = nextpow2(3N - 1), the
-    lines each pass transforms); d = 1 is a direct sum (2N + 1 products per point)."""
+    lines each pass transforms, M'/2 + 1 along axis 0 after the first); d = 1 is a direct sum
+    (2N + 1 products per point)."""
     out = {}
     for name, (d, n, p, alpha) in (("1d_n4095", (1, 4095, 1, 1.5)), ("2d_n1023", (2, 1023, 2, 1.2)),
                                    ("3d_n255", (3, 255, 1, 1.6))):
@@ -483,7 +484,8 @@ def boundary_measurement(fg, torch, barrier) -> dict:
         if d == 1:
             flops = 2.0 * n * (2 * N + 1)
         else:
-            lines = E + 2 * Mp + n if d == 2 else E * E + Mp * E + 2 * Mp * Mp + Mp * n + n * n
+            Kp = Mp // 2 + 1
+            lines = E + 2 * Kp + n if d == 2 else E * E + Kp * E + 2 * Kp * Mp + Kp * n + n * n
             flops = lines * 5.0 * Mp * math.log2(Mp)
         out[name] = {"ms": ms, "fft_side": Mp if d > 1 else None, "nominal_fp64_gflops": flops / (ms * 1e-3) / 1e9}
         op.close()

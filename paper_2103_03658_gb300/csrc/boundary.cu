@@ -13,9 +13,10 @@
 // generator at side M' (generator_symbol_cube).  d >= 2: FP64 line FFTs along each
 // axis of an M'^d complex array, the first reading G, the last writing b on the
 // interior window only.  Lines that are still all zero (a coordinate at or beyond
-// 3N - 1 on an axis not yet transformed) are skipped on the way in, and lines whose
-// results the window does not use on the way out.  d = 1: the N + 2 terms per
-// point summed directly (one warp per point).
+// 3N - 1 on an axis not yet transformed) are skipped on the way in, lines whose
+// results the window does not use on the way out, and, G being real, the upper
+// half of the axis-0 spectrum, which the last pass rebuilds by conjugate symmetry.
+// d = 1: the N + 2 terms per point summed directly (one warp per point).
 #include <algorithm>
 
 #include "apply.cuh"
@@ -111,6 +112,20 @@ k_nf_lines(double2* X, const double* __restrict__ G, const double* __restrict__ 
         if (BCHK(idx, mul)) x = G[idx];
       }
       v[e] = C{x, 0.0};
+    }
+  } else if (KIND == NF_INV && A.extract) {
+    // axis 0 of a real result: only k0 < M'/2 + 1 was carried through the other
+    // axes; the rest is the conjugate, X[M' - k0]
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = tl + e * TPL;
+      const bool lo_half = j < A.Kp;
+      C x{0.0, 0.0};
+      if (live) {
+        const int64_t idx = base + (lo_half ? j : M - j) * stride;
+        if (BCHK(idx, A.total)) x = X[idx];
+      }
+      v[e] = lo_half ? x : C{x.x, -x.y};
     }
   } else {
 #pragma unroll
@@ -321,20 +336,22 @@ int boundary_device(const frac_op* op, const double* g_ext, const double* far, d
     P.extract = extract;
     return nf_pass(logm, kind, P, X, g_ext, S, far, b, st);
   };
-  // other-axis ranges: [0, E) where G has samples, [0, M') everywhere, [N, 2N-1) the interior window
+  // other-axis ranges: [0, E) where G has samples, [0, M') everywhere, [N, 2N-1) the interior
+  // window; along axis 0 after its forward transform only k0 < K' = M'/2 + 1 (G is real: the
+  // rest is conjugate-symmetric and the last pass rebuilds it)
   const int64_t z = 0, w = N, n = N - 1;
   if (d == 2) {
     const int64_t lo0[3] = {z, z, z}, cnt0[3] = {0, E, 1};    // axis 0 from G: rows y < E
-    const int64_t lo1[3] = {z, z, z}, cnt1[3] = {Mp, 0, 1};   // axis 1 with the symbol: every column
+    const int64_t lo1[3] = {z, z, z}, cnt1[3] = {Kp, 0, 1};   // axis 1 with the symbol: columns k0 < K'
     const int64_t lo2[3] = {z, w, z}, cnt2[3] = {0, n, 1};    // axis 0 inverse: rows in the window
     FRAC_TRY(pass(NF_FWD, 0, lo0, cnt0, 1, 0));
     FRAC_TRY(pass(NF_SYM, 1, lo1, cnt1, 0, 0));
     FRAC_TRY(pass(NF_INV, 0, lo2, cnt2, 0, 1));
   } else {
     const int64_t lo0[3] = {z, z, z}, cnt0[3] = {0, E, E};    // axis 0 from G
-    const int64_t lo1[3] = {z, z, z}, cnt1[3] = {Mp, 0, E};   // axis 1: planes z < E
-    const int64_t lo2[3] = {z, z, z}, cnt2[3] = {Mp, Mp, 0};  // axis 2 with the symbol
-    const int64_t lo3[3] = {z, z, w}, cnt3[3] = {Mp, 0, n};   // axis 1 inverse: planes in the window
+    const int64_t lo1[3] = {z, z, z}, cnt1[3] = {Kp, 0, E};   // axis 1: k0 < K', planes z < E
+    const int64_t lo2[3] = {z, z, z}, cnt2[3] = {Kp, Mp, 0};  // axis 2 with the symbol
+    const int64_t lo3[3] = {z, z, w}, cnt3[3] = {Kp, 0, n};   // axis 1 inverse: planes in the window
     const int64_t lo4[3] = {z, w, w}, cnt4[3] = {0, n, n};    // axis 0 inverse to b
     FRAC_TRY(pass(NF_FWD, 0, lo0, cnt0, 1, 0));
     FRAC_TRY(pass(NF_FWD, 1, lo1, cnt1, 0, 0));
