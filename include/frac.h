@@ -206,8 +206,8 @@ typedef struct frac_solve_info {
  *          reach of the grid).
  *   b:     prod(n_i) doubles, written.
  * Device or host pointers (host buffers are staged).  The near field is a
- * convolution on a circulant of side nextpow2(3N - 1) in FP64 (d = 2, 3: a
- * transient (nextpow2(3N - 1))^d complex array, 17 GB at 3D N = 257) or a direct
+ * convolution on a circulant of side M' = nextpow2(3N - 1) in FP64 (d = 2, 3: a
+ * transient complex array of (M'/2 + 1) M'^(d-1) entries, 8.6 GB at 3D N = 257) or a direct
  * sum (d = 1).  Synchronises `stream`.  Errors: FRAC_EINVAL (NULL op/g_ext/b),
  * FRAC_ENOTSUP (unequal extents), FRAC_ENOMEM, FRAC_ECUDA (including a failed
  * device bounds check, named by frac_error_detail).

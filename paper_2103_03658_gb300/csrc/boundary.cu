@@ -11,8 +11,9 @@
 // magnitude N+1 .. 2N-2 never reach the kernel's support modulo M'), so
 // near = IFFT(FFT(G) * Lambda') on the interior window, Lambda' the symbol of the
 // generator at side M' (generator_symbol_cube).  d >= 2: FP64 line FFTs along each
-// axis of an M'^d complex array, the first reading G, the last writing b on the
-// interior window only.  Lines that are still all zero (a coordinate at or beyond
+// axis of a complex array (M'/2 + 1 entries along axis 0, M' along the others), the
+// first reading G, the last writing b on the interior window only.  Lines that are
+// still all zero (a coordinate at or beyond
 // 3N - 1 on an axis not yet transformed) are skipped on the way in, lines whose
 // results the window does not use on the way out, and, G being real, the upper
 // half of the axis-0 spectrum, which the last pass rebuilds by conjugate symmetry.
@@ -49,7 +50,9 @@ int take_bnd_fault() {
 
 enum NfKind { NF_FWD = 0, NF_SYM = 1, NF_INV = 2 };
 
-// One pass of line FFTs along `axis` of the M'^d array X (axis 0 fastest).  The
+// One pass of line FFTs along `axis` of the array X (axis 0 fastest, extent ext0 =
+// M'/2 + 1 along axis 0: the first pass keeps only those frequencies of the real
+// samples, M' along the others).  The
 // lines transformed are those whose other coordinates lie in [lo, lo + cnt) on
 // each other axis; `fast` is the other axis of smallest stride (the tile axis: L
 // adjacent lines per block), `slow` the remaining one (d = 3).
@@ -59,7 +62,8 @@ struct NfArgs {
   int64_t E, N;        // extended samples per axis (3N - 1); generator intervals
   int64_t lo[3], cnt[3];
   int64_t ntf;         // tiles along `fast`
-  int64_t total;       // M'^d
+  int64_t ext0;        // extent of X along axis 0 (M'/2 + 1)
+  int64_t total;       // ext0 M'^(d-1) entries of X
   int fill;            // NF_FWD: read G (E^d doubles) instead of X
   int extract;         // NF_INV along axis 0: write b on the interior window instead of X
   double negc;         // -c
@@ -86,9 +90,9 @@ k_nf_lines(double2* X, const double* __restrict__ G, const double* __restrict__ 
   int64_t c[3] = {0, 0, 0};
   c[A.fast] = A.lo[A.fast] + off;
   if (A.d == 3) c[A.slow] = A.lo[A.slow] + sidx;
-  int64_t stride = 1;
-  for (int i = 0; i < A.axis; ++i) stride *= M;
-  const int64_t base = (c[2] * M + c[1]) * M + c[0];  // c[axis] = 0
+  const int64_t s1 = A.ext0, s2 = A.ext0 * M;                        // strides of axes 1, 2
+  const int64_t stride = A.axis == 0 ? 1 : (A.axis == 1 ? s1 : s2);
+  const int64_t base = c[2] * s2 + c[1] * s1 + c[0];                  // c[axis] = 0
   const int64_t N = A.N, wlo = N, whi = 2 * N - 2;     // interior window of p
   C v[E];
   if (KIND == NF_FWD && A.fill) {
@@ -184,6 +188,7 @@ k_nf_lines(double2* X, const double* __restrict__ G, const double* __restrict__ 
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = tl + e * TPL;
+      if (A.axis == 0 && j >= A.ext0) continue;  // the conjugate half is not stored
       const int64_t idx = base + j * stride;
       if (BCHK(idx, A.total)) X[idx] = v[e];
     }
@@ -287,10 +292,12 @@ int boundary_device(const frac_op* op, const double* g_ext, const double* far, d
   const int logm = ilog2(E);
   if (logm < kNfMinLog || logm > kNfMaxLog) return FRAC_ENOTSUP;
   const int64_t Mp = int64_t(1) << logm, Kp = Mp / 2 + 1;
-  int64_t total = 1, nsym = 1;
-  for (int i = 0; i < d; ++i) {
+  int64_t total = Kp, nsym = Kp;  // X: K' x M'^(d-1); symbol: K'^d
+  double full = (double)Mp;       // M'^d, the normalisation of the inverse transforms
+  for (int i = 1; i < d; ++i) {
     total *= Mp;
     nsym *= Kp;
+    full *= (double)Mp;
   }
   FRAC_TRY(prepare_twiddles(logm));
   double2* X = nullptr;
@@ -320,9 +327,10 @@ int boundary_device(const frac_op* op, const double* g_ext, const double* far, d
   A.Kp = Kp;
   A.E = E;
   A.N = N;
+  A.ext0 = Kp;
   A.total = total;
   A.negc = negc;
-  A.inv_norm = 1.0 / (double)total;
+  A.inv_norm = 1.0 / full;
   auto pass = [&](int kind, int axis, const int64_t lo[3], const int64_t cnt[3], int fill, int extract) {
     NfArgs P = A;
     P.axis = axis;
