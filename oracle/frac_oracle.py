@@ -433,52 +433,56 @@ def norm_bound(a: np.ndarray, c: float, n) -> float:
 # Boundary vector b  (Eq. (1D-scheme): b_i; Eq. (2D-scheme): b_ij)
 # ---------------------------------------------------------------------------
 
-def extended_samples(d: int, N: int, h: float, g, lo: float = -1.0) -> np.ndarray:
-    """g at the extended grid points lo + e h, e in [1-N, 2N-1]^d (axis i of the
-    array = coordinate i), zero at the interior points e in [1, N-1]^d (there the
-    unknown u, not g, enters the scheme).  Shape (3N-1,)*d."""
-    ext = np.arange(1 - N, 2 * N)
-    grids = np.meshgrid(*([lo + ext * h] * d), indexing="ij")
+def extended_samples(d: int, N: int, h: float, g, lo: float = -1.0, shape=None) -> np.ndarray:
+    """g at the extended grid points lo + e h, e in [1-N, n_i+N] on array axis i (axis i
+    of the array = coordinate i; n_i = shape[i], default N - 1 on every axis: the square
+    grid), zero at the interior points e in [1, n_i] (there the unknown u, not g,
+    enters the scheme).  The generator reaches N points on every axis (its cube has
+    side L = N h, Sec. 2.2 for N_2 < N_1).  Shape (n_i + 2N)_i."""
+    shape = (N - 1,) * d if shape is None else tuple(int(v) for v in shape)
+    exts = [np.arange(1 - N, m + N + 1) for m in shape]
+    grids = np.meshgrid(*[lo + e * h for e in exts], indexing="ij")
     G = g(np.stack(grids, axis=-1))
     inside = np.ones(G.shape, dtype=bool)
-    for i in range(d):
-        shape = [1] * d
-        shape[i] = len(ext)
-        inside = inside & ((ext >= 1) & (ext <= N - 1)).reshape(shape)
+    for i, (e, m) in enumerate(zip(exts, shape)):
+        sh = [1] * d
+        sh[i] = len(e)
+        inside = inside & ((e >= 1) & (e <= m)).reshape(sh)
     return np.where(inside, 0.0, G)
 
 
 def boundary_near(a: np.ndarray, G: np.ndarray) -> np.ndarray:
     """Near-field part of Eq. (L2) at every interior point: sum over o in [-N, N]^d
     of a_{|o|} G[x_i + o h], G the extended samples (``extended_samples``; zero
-    inside, so only exterior points count).  Shape (N-1,)*d."""
+    inside, so only exterior points count), N + 1 = the generator's extent and
+    n_i = G.shape[i] - 2N.  Shape (n_i)_i."""
     d = G.ndim
-    N = (G.shape[0] + 1) // 3
-    n = N - 1
-    near = np.zeros((n,) * d)
+    N = a.shape[0] - 1
+    shape = tuple(m - 2 * N for m in G.shape)
+    near = np.zeros(shape)
     for o in itertools.product(range(-N, N + 1), repeat=d):
         coef = a[tuple(abs(t) for t in o)]
-        sl = tuple(slice(N + t, N + t + n) for t in o)   # interior index i+1 -> ext offset (i+1)-(1-N)
+        sl = tuple(slice(N + t, N + t + m) for t, m in zip(o, shape))  # interior index i+1 -> ext offset (i+1)-(1-N)
         near += coef * G[sl]
     return near
 
 
 def boundary_far(d: int, N: int, h: float, alpha: float, g, lam: float = 0.0, lo: float = -1.0,
-                 nq: int = 96) -> np.ndarray:
+                 nq: int = 96, shape=None) -> np.ndarray:
     """Far-field part of Eq. (L2) at every interior point:
     sum_{m in varkappa_1} int over Upsilon_+^c of g(x_i + (-1)^m o xi)
     |xi|^{-d-alpha} exp(-lambda |xi|) dxi.  xi = rho (1, s) with rho = L / t:
     rho^{-1-alpha} d rho = L^{-alpha} t^{alpha-1} dt, integrated by Gauss-Jacobi
-    in t and Gauss-Legendre in s.  Shape (N-1,)*d."""
-    n = N - 1
+    in t and Gauss-Legendre in s; L = N h, the side of the generator's cube.
+    Shape ``shape`` (default (N-1,)*d)."""
+    shape = (N - 1,) * d if shape is None else tuple(int(v) for v in shape)
     L = N * h
     xt, wt = special.roots_jacobi(nq, 0.0, alpha - 1.0)     # weight (1+x)^{alpha-1} on [-1, 1]
     t = 0.5 * (xt + 1.0)
     wt = wt * 0.5 ** alpha                                   # int_0^1 t^{alpha-1} f(t) dt
     rho = L / t
-    interior = lo + (np.arange(n) + 1) * h
-    X = np.stack(np.meshgrid(*([interior] * d), indexing="ij"), axis=-1)  # (n,)*d + (d,)
-    far = np.zeros((n,) * d)
+    X = np.stack(np.meshgrid(*[lo + (np.arange(m) + 1) * h for m in shape], indexing="ij"), axis=-1)
+    far = np.zeros(shape)
     if d == 1:
         for sgn in (-1.0, 1.0):
             vals = g(X[..., None, :] + sgn * rho[:, None])          # (n, nq)
@@ -502,13 +506,13 @@ def boundary_far(d: int, N: int, h: float, alpha: float, g, lam: float = 0.0, lo
 
 
 def boundary_vector(d: int, N: int, h: float, alpha: float, a: np.ndarray, c: float, g,
-                    lam: float = 0.0, lo: float = -1.0, nq: int = 96) -> np.ndarray:
+                    lam: float = 0.0, lo: float = -1.0, nq: int = 96, shape=None) -> np.ndarray:
     """-c b_i for every interior point: b_i is the near-field sum of a_{|o|} g
     over the exterior grid points x_i + o h (o in [-N, N]^d, ``boundary_near``)
     plus the far field (``boundary_far``), Eq. (L2).  ``g`` maps an array
     (..., d) of points to values."""
-    near = boundary_near(a, extended_samples(d, N, h, g, lo))
-    far = boundary_far(d, N, h, alpha, g, lam, lo, nq)
+    near = boundary_near(a, extended_samples(d, N, h, g, lo, shape))
+    far = boundary_far(d, N, h, alpha, g, lam, lo, nq, shape)
     return -c * (near + far)
 
 

@@ -78,3 +78,44 @@ def test_boundary_vector_is_minus_c_near_plus_far():
     near = O.boundary_near(a, O.extended_samples(d, N, h, g))
     far = O.boundary_far(d, N, h, alpha, g)
     assert np.allclose(b, -c * (near + far), rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("d,shape,p,alpha", [(2, (7, 3), 1, 1.2), (2, (4, 9), 0, 0.7), (3, (5, 2, 3), 1, 1.5)])
+def test_rectangular_near_field_completes_the_generator_sum(d, shape, p, alpha):
+    """Rectangular grids (N_2 < N_1): the generator's cube has side N h with N = max n_i + 1,
+    so g is sampled on [1-N, n_i+N] per axis; constants are still annihilated."""
+    N = max(shape) + 1
+    h = 2.0 / N
+    a = O.stencil(d, N, h, alpha, p, q=12)
+    G = O.extended_samples(d, N, h, lambda P: np.ones(P.shape[:-1]), shape=shape)
+    assert G.shape == tuple(m + 2 * N for m in shape)
+    near = O.boundary_near(a, G)
+    T1 = (O.toeplitz_matrix(a, shape) @ np.ones(int(np.prod(shape)))).reshape(shape)
+    F = O.far_field(d, alpha, N * h)
+    assert np.allclose(T1 + near, -(2.0 ** d) * F, rtol=0, atol=1e-12 * np.abs(a).sum())
+    far = O.boundary_far(d, N, h, alpha, lambda P: np.ones(P.shape[:-1]), nq=48, shape=shape)
+    assert np.allclose(far, (2.0 ** d) * F, rtol=1e-9, atol=0)
+
+
+def test_rectangular_near_field_equals_brute_force():
+    d, shape = 2, (4, 2)
+    N = max(shape) + 1
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((N + 1,) * d)
+    G = rng.standard_normal(tuple(m + 2 * N for m in shape))
+    exts = [np.arange(1 - N, m + N + 1) for m in shape]
+    for e in itertools.product(*[range(len(x)) for x in exts]):
+        if all(1 <= exts[t][e[t]] <= shape[t] for t in range(d)):
+            G[e] = 0.0
+    ref = np.zeros(shape)
+    for i in itertools.product(*[range(1, m + 1) for m in shape]):
+        s = 0.0
+        for e in itertools.product(*[range(len(x)) for x in exts]):
+            x = tuple(int(exts[t][e[t]]) for t in range(d))
+            if all(1 <= x[t] <= shape[t] for t in range(d)):
+                continue
+            o = tuple(abs(x[t] - i[t]) for t in range(d))
+            if max(o) <= N:
+                s += a[o] * G[e]
+        ref[tuple(t - 1 for t in i)] = s
+    assert np.allclose(O.boundary_near(a, G), ref, rtol=1e-13, atol=1e-13)
