@@ -199,18 +199,20 @@ typedef struct frac_solve_info {
  * e^{-lambda |xi|} dxi), which depend on g beyond every grid point and are the
  * caller's.  Then A u = f - b is the discrete problem with u = g outside
  * (frac_solve takes b as its g argument).
- *   g_ext: (3N - 1)^d doubles, g at the grid points x_0 + e h (x_0 the domain's
- *          lower corner), e in [1 - N, 2N - 1] per axis, axis 0 fastest as in u;
- *          the interior points are e in [1, N - 1]^d and their values are not read.
+ *   g_ext: prod_i (n_i + 2N) doubles, N = max_i n_i + 1 (the generator's cube
+ *          spans the longest axis, so its reach is N points on every axis): g at
+ *          the grid points x_0 + e h (x_0 the domain's lower corner), e in
+ *          [1 - N, n_i + N] on axis i, axis 0 fastest as in u; the interior
+ *          points are e in [1, n_i] on every axis and their values are not read.
  *   far:   prod(n_i) doubles, or NULL for zero (g of compact support within
  *          reach of the grid).
  *   b:     prod(n_i) doubles, written.
  * Device or host pointers (host buffers are staged).  The near field is a
- * convolution on a circulant of side M' = nextpow2(3N - 1) in FP64 (d = 2, 3: a
- * transient complex array of (M'/2 + 1) M'^(d-1) entries, 8.6 GB at 3D N = 257) or a direct
- * sum (d = 1).  Synchronises `stream`.  Errors: FRAC_EINVAL (NULL op/g_ext/b),
- * FRAC_ENOTSUP (unequal extents), FRAC_ENOMEM, FRAC_ECUDA (including a failed
- * device bounds check, named by frac_error_detail).
+ * convolution on a circulant of sides M'_i = nextpow2(n_i + 2N) in FP64 (d = 2, 3:
+ * a transient complex array of (M'_0/2 + 1) prod_{i>0} M'_i entries, 8.6 GB at 3D
+ * n = 256) or a direct sum (d = 1).  Synchronises `stream`.  Errors: FRAC_EINVAL
+ * (NULL op/g_ext/b), FRAC_ENOTSUP (M'_i beyond 4096), FRAC_ENOMEM, FRAC_ECUDA
+ * (including a failed device bounds check, named by frac_error_detail).
  */
 int frac_boundary(const frac_op* op, const double* g_ext, const double* far, double* b, void* stream);
 

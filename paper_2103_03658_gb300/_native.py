@@ -293,16 +293,22 @@ class FracOp:
         return z
 
     # -- boundary vector of exterior data --
+    @property
+    def ext_shape(self) -> tuple:
+        """Array shape of the extended samples of ``boundary``: n_i + 2N per axis, N = max n_i + 1."""
+        N = max(self.ns) + 1
+        return tuple(m + 2 * N for m in self.shape)
+
     def boundary(self, g_ext, far=None, out=None, stream=None):
-        """b = -c (near + far) (frac_boundary): g_ext holds g at the (3N-1)^d grid
-        points e in [1-N, 2N-1]^d (shape (3N-1,)*d, float64; interior values unread),
+        """b = -c (near + far) (frac_boundary): g_ext holds g at the grid points e in
+        [1-N, n_i+N] per axis (shape ``ext_shape``, float64; interior values unread),
         far the caller's far-field integrals (shape of u) or None."""
         if _dtype_code(g_ext) != F64 or (far is not None and _dtype_code(far) != F64):
             raise TypeError("boundary takes float64 data")
-        E = 3 * (max(self.ns) + 1) - 1
+        want = int(np.prod(self.ext_shape))
         numel = g_ext.size if isinstance(g_ext, np.ndarray) else g_ext.numel()
-        if numel != E ** self.d:
-            raise ValueError(f"g_ext has {numel} values, expected (3N-1)^d = {E ** self.d}")
+        if numel != want:
+            raise ValueError(f"g_ext has {numel} values, expected prod(n_i + 2N) = {want}")
         if out is None:
             if isinstance(g_ext, np.ndarray):
                 out = np.empty(self.shape, dtype=np.float64)

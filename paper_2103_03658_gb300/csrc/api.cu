@@ -419,11 +419,10 @@ int frac_precond(const frac_op* op, const void* r, void* z, int dtype, int64_t b
 
 int frac_boundary(const frac_op* op, const double* g_ext, const double* far, double* b, void* stream) {
   if (!op || !g_ext || !b) return FRAC_EINVAL;
-  if (!op->square) return FRAC_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
   const int d = op->prob.d;
   int64_t ne = 1;
-  for (int i = 0; i < d; ++i) ne *= 3 * op->N - 1;
+  for (int i = 0; i < d; ++i) ne *= op->na[i] + 2 * op->N;
   const size_t gbytes = ne * sizeof(double), bbytes = op->nd * sizeof(double);
   const bool dgx = is_device_ptr(g_ext), dfar = far && is_device_ptr(far), db = is_device_ptr(b);
   double *tg = nullptr, *tfar = nullptr, *tb = nullptr;

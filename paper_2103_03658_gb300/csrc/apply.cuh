@@ -34,7 +34,7 @@ struct CGState {
 // coeffs.cu
 int prepare_twiddles(int logm);
 int build_coefficients(frac_op* op, cudaStream_t st);
-int generator_symbol_cube(const frac_op* op, int logm, double* out, double* tmp, cudaStream_t st);
+int generator_symbol_axes(const frac_op* op, const int* logm, double* out, double* tmp, cudaStream_t st);
 int take_coeff_fault();
 
 // boundary.cu: b = -c (near + far) on device buffers (frac_boundary), and r = f - g.

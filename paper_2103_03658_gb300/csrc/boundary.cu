@@ -3,21 +3,22 @@
 // exterior grid points x_i + o h, o in [-N, N]^d, of a_{|o|} g(x_i + o h) and far_i
 // the far-field integrals of g, which the caller supplies.
 //
-// The near field is a convolution of the extended samples G (g on the grid
-// points e in [1-N, 2N-1]^d, zero at the interior ones) with the even generator:
-// in the shifted index p = e + N - 1 in [0, 3N-2], near_i = sum_o a_{|o|} G[p_i + o]
-// with p_i = i + N - 1.  On a circulant of side M' >= 3N - 1 that sum has no
-// wrap-around for any p_i (every p_i + o stays in [0, 3N-2], and offsets of
-// magnitude N+1 .. 2N-2 never reach the kernel's support modulo M'), so
-// near = IFFT(FFT(G) * Lambda') on the interior window, Lambda' the symbol of the
-// generator at side M' (generator_symbol_cube).  d >= 2: FP64 line FFTs along each
-// axis of a complex array (M'/2 + 1 entries along axis 0, M' along the others), the
-// first reading G, the last writing b on the interior window only.  Lines that are
-// still all zero (a coordinate at or beyond
-// 3N - 1 on an axis not yet transformed) are skipped on the way in, lines whose
-// results the window does not use on the way out, and, G being real, the upper
-// half of the axis-0 spectrum, which the last pass rebuilds by conjugate symmetry.
-// d = 1: the N + 2 terms per point summed directly (one warp per point).
+// The near field is a convolution of the extended samples G (g on the grid points
+// e in [1-N, n_i+N] per axis, zero at the interior ones; N + 1 the generator's extent,
+// its cube spanning the longest axis) with the even generator: in the shifted index
+// p = e + N - 1 in [0, E_i - 1], E_i = n_i + 2N, near_i = sum_o a_{|o|} G[p_i + o] with
+// p_i = i + N - 1.  On a circulant of side M'_i >= E_i per axis that sum has no
+// wrap-around for any p_i (every p_i + o stays in [0, E_i - 1], and |p - q| <= N + n_i - 1
+// for output p and input q, so offsets beyond N never reach the kernel's support
+// modulo M'_i), so near = IFFT(FFT(G) * Lambda') on the interior window, Lambda' the
+// symbol of the generator at sides M'_i (generator_symbol_axes).  d >= 2: FP64 line
+// FFTs along each axis of a complex array (M'_0/2 + 1 entries along axis 0, M'_i along
+// the others), the first reading G, the last writing b on the interior window only.
+// Lines that are still all zero (a coordinate at or beyond E_i on an axis not yet
+// transformed) are skipped on the way in, lines whose results the window does not use
+// on the way out, and, G being real, the upper half of the axis-0 spectrum, which the
+// last pass rebuilds by conjugate symmetry.  d = 1: the N + 2 terms per point summed
+// directly (one warp per point).
 #include <algorithm>
 
 #include "apply.cuh"
@@ -50,24 +51,28 @@ int take_bnd_fault() {
 
 enum NfKind { NF_FWD = 0, NF_SYM = 1, NF_INV = 2 };
 
-// One pass of line FFTs along `axis` of the array X (axis 0 fastest, extent ext0 =
-// M'/2 + 1 along axis 0: the first pass keeps only those frequencies of the real
-// samples, M' along the others).  The
-// lines transformed are those whose other coordinates lie in [lo, lo + cnt) on
-// each other axis; `fast` is the other axis of smallest stride (the tile axis: L
-// adjacent lines per block), `slow` the remaining one (d = 3).
+// One pass of line FFTs along `axis` of the array X (axis 0 fastest; extent K'_0 =
+// M'_0/2 + 1 along axis 0, where the first pass keeps only those frequencies of the
+// real samples, M'_i along the others).  The lines transformed are those whose
+// other coordinates lie in [lo, lo + cnt) on each other axis; `fast` is the other
+// axis of smallest stride (the tile axis: L adjacent lines per block), `slow` the
+// remaining one (d = 3).  Per axis i: n_i interior points, E_i = n_i + 2N samples
+// (p = e + N - 1 for e in [1-N, n_i+N]; the interior window p in [N, N+n_i-1]),
+// circulant side M'_i = nextpow2(E_i), symbol extent K'_i = M'_i/2 + 1.
 struct NfArgs {
   int d, axis, fast, slow;
-  int64_t Mp, Kp;      // M' and M'/2 + 1
-  int64_t E, N;        // extended samples per axis (3N - 1); generator intervals
+  int64_t N;                     // generator intervals (its cube has side N h)
+  int64_t n[3], E[3], Mp[3], Kp[3];
   int64_t lo[3], cnt[3];
-  int64_t ntf;         // tiles along `fast`
-  int64_t ext0;        // extent of X along axis 0 (M'/2 + 1)
-  int64_t total;       // ext0 M'^(d-1) entries of X
-  int fill;            // NF_FWD: read G (E^d doubles) instead of X
-  int extract;         // NF_INV along axis 0: write b on the interior window instead of X
-  double negc;         // -c
-  double inv_norm;     // 1 / M'^d (unnormalised inverse transforms)
+  int64_t ntf;                   // tiles along `fast`
+  int64_t total;                 // K'_0 M'_1 M'_2 entries of X (M'_2 = 1 for d = 2)
+  int64_t nG;                    // prod E_i samples
+  int64_t nS;                    // prod K'_i symbol entries
+  int64_t nb;                    // prod n_i outputs
+  int fill;                      // NF_FWD: read G instead of X
+  int extract;                   // NF_INV along axis 0: write b on the interior window instead of X
+  double negc;                   // -c
+  double inv_norm;               // 1 / prod M'_i (unnormalised inverse transforms)
 };
 
 template <int LOGM>
@@ -90,10 +95,10 @@ k_nf_lines(double2* X, const double* __restrict__ G, const double* __restrict__ 
   int64_t c[3] = {0, 0, 0};
   c[A.fast] = A.lo[A.fast] + off;
   if (A.d == 3) c[A.slow] = A.lo[A.slow] + sidx;
-  const int64_t s1 = A.ext0, s2 = A.ext0 * M;                        // strides of axes 1, 2
+  const int64_t s1 = A.Kp[0], s2 = A.Kp[0] * A.Mp[1];                  // strides of axes 1, 2 in X
   const int64_t stride = A.axis == 0 ? 1 : (A.axis == 1 ? s1 : s2);
-  const int64_t base = c[2] * s2 + c[1] * s1 + c[0];                  // c[axis] = 0
-  const int64_t N = A.N, wlo = N, whi = 2 * N - 2;     // interior window of p
+  const int64_t base = c[2] * s2 + c[1] * s1 + c[0];                    // c[axis] = 0
+  const int64_t N = A.N;
   C v[E];
   if (KIND == NF_FWD && A.fill) {
     bool others_in = true;
@@ -103,27 +108,28 @@ k_nf_lines(double2* X, const double* __restrict__ G, const double* __restrict__ 
         gstride = mul;
       } else {
         gbase += c[i] * mul;
-        others_in = others_in && c[i] >= wlo && c[i] <= whi;
+        others_in = others_in && c[i] >= N && c[i] < N + A.n[i];
       }
-      mul *= A.E;
+      mul *= A.E[i];
     }
+    const int64_t Ea = A.E[A.axis], na = A.n[A.axis];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = tl + e * TPL;
       double x = 0.0;
-      if (live && j < A.E && !(others_in && j >= wlo && j <= whi)) {
+      if (live && j < Ea && !(others_in && j >= N && j < N + na)) {
         const int64_t idx = gbase + j * gstride;
-        if (BCHK(idx, mul)) x = G[idx];
+        if (BCHK(idx, A.nG)) x = G[idx];
       }
       v[e] = C{x, 0.0};
     }
   } else if (KIND == NF_INV && A.extract) {
-    // axis 0 of a real result: only k0 < M'/2 + 1 was carried through the other
-    // axes; the rest is the conjugate, X[M' - k0]
+    // axis 0 of a real result: only k0 < K'_0 was carried through the other axes;
+    // the rest is the conjugate, X[M'_0 - k0]
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = tl + e * TPL;
-      const bool lo_half = j < A.Kp;
+      const bool lo_half = j < A.Kp[0];
       C x{0.0, 0.0};
       if (live) {
         const int64_t idx = base + (lo_half ? j : M - j) * stride;
@@ -150,45 +156,41 @@ k_nf_lines(double2* X, const double* __restrict__ G, const double* __restrict__ 
       if (i == A.axis) {
         sstride = mul;
       } else {
-        const int64_t k = c[i], kr = k <= M / 2 ? k : M - k;
+        const int64_t k = c[i], kr = k <= A.Mp[i] / 2 ? k : A.Mp[i] - k;
         sb += kr * mul;
       }
-      mul *= A.Kp;
+      mul *= A.Kp[i];
     }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = tl + e * TPL, jr = j <= M / 2 ? j : M - j;
-      double s = 0.0;
+      double sv = 0.0;
       if (live) {
         const int64_t idx = sb + jr * sstride;
-        if (BCHK(idx, mul)) s = S[idx];
+        if (BCHK(idx, A.nS)) sv = S[idx];
       }
-      v[e] = cscale(v[e], s);
+      v[e] = cscale(v[e], sv);
     }
   }
   if (KIND != NF_FWD) fft_reg<C, LOGM, true, false, false, SH>(v, buf, tl, tw);
   if (!live) return;
   if (KIND == NF_INV && A.extract) {  // axis 0; the other coordinates lie in the window (launch range)
-    const int64_t n = N - 1;
-    int64_t ob = 0, cnt = n;
-    for (int i = A.d - 1; i >= 1; --i) {
-      ob = ob * n + (c[i] - wlo);
-      cnt *= n;
-    }
-    ob *= n;
+    int64_t ob = 0;
+    for (int i = A.d - 1; i >= 1; --i) ob = ob * A.n[i] + (c[i] - N);
+    ob *= A.n[0];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = tl + e * TPL;
-      if (j >= wlo && j <= whi) {
-        const int64_t o = ob + (j - wlo);
-        if (BCHK(o, cnt)) b[o] = A.negc * (v[e].x * A.inv_norm + (far ? far[o] : 0.0));
+      if (j >= N && j < N + A.n[0]) {
+        const int64_t o = ob + (j - N);
+        if (BCHK(o, A.nb)) b[o] = A.negc * (v[e].x * A.inv_norm + (far ? far[o] : 0.0));
       }
     }
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = tl + e * TPL;
-      if (A.axis == 0 && j >= A.ext0) continue;  // the conjugate half is not stored
+      if (A.axis == 0 && j >= A.Kp[0]) continue;  // the conjugate half is not stored
       const int64_t idx = base + j * stride;
       if (BCHK(idx, A.total)) X[idx] = v[e];
     }
@@ -275,31 +277,45 @@ int subtract_device(const double* f, const double* g, double* r, int64_t count, 
   return FRAC_OK;
 }
 
-// Square grids (N intervals per axis, n = N - 1 interior points); g_ext, far and b
-// on the device, (3N - 1)^d, n^d (or NULL) and n^d doubles, axis 0 fastest.
+// g_ext, far and b on the device: prod_i (n_i + 2N), prod n_i (or NULL) and prod n_i
+// doubles, axis 0 fastest; N = op->N (the generator's cube, N = max n_i + 1).
 int boundary_device(const frac_op* op, const double* g_ext, const double* far, double* b, cudaStream_t st) {
   const int d = op->prob.d;
-  const int64_t N = op->N, E = 3 * N - 1;
+  const int64_t N = op->N;
   const double negc = -op->c;
   if (N < 2) return FRAC_EINVAL;
   if (d == 1) {
+    if (op->na[0] != N - 1) return FRAC_EINVAL;
     const int64_t threads = (N - 1) * 32;
     k_nf_direct_1d<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(op->a, g_ext, far, b, N, negc);
     FRAC_CUDA_TRY(cudaGetLastError());
     FRAC_CUDA_TRY(cudaStreamSynchronize(st));
     return take_bnd_fault();
   }
-  const int logm = ilog2(E);
-  if (logm < kNfMinLog || logm > kNfMaxLog) return FRAC_ENOTSUP;
-  const int64_t Mp = int64_t(1) << logm, Kp = Mp / 2 + 1;
-  int64_t total = Kp, nsym = Kp;  // X: K' x M'^(d-1); symbol: K'^d
-  double full = (double)Mp;       // M'^d, the normalisation of the inverse transforms
-  for (int i = 1; i < d; ++i) {
-    total *= Mp;
-    nsym *= Kp;
-    full *= (double)Mp;
+  NfArgs A{};
+  A.d = d;
+  A.N = N;
+  int logm[3] = {0, 0, 0};
+  double full = 1.0;
+  A.nG = A.nS = A.nb = 1;
+  for (int i = 0; i < 3; ++i) {
+    A.n[i] = A.E[i] = A.Mp[i] = A.Kp[i] = 1;
+    if (i >= d) continue;
+    A.n[i] = op->na[i];
+    A.E[i] = op->na[i] + 2 * N;
+    logm[i] = ilog2(A.E[i]);
+    if (logm[i] < kNfMinLog || logm[i] > kNfMaxLog) return FRAC_ENOTSUP;
+    A.Mp[i] = int64_t(1) << logm[i];
+    A.Kp[i] = A.Mp[i] / 2 + 1;
+    full *= (double)A.Mp[i];
+    A.nG *= A.E[i];
+    A.nS *= A.Kp[i];
+    A.nb *= A.n[i];
   }
-  FRAC_TRY(prepare_twiddles(logm));
+  A.total = A.Kp[0] * A.Mp[1] * A.Mp[2];
+  A.negc = negc;
+  A.inv_norm = 1.0 / full;
+  for (int i = 0; i < d; ++i) FRAC_TRY(prepare_twiddles(logm[i]));
   double2* X = nullptr;
   double *S = nullptr, *tmp = nullptr;
   struct Free {
@@ -313,24 +329,14 @@ int boundary_device(const frac_op* op, const double* g_ext, const double* far, d
       if (*t) cudaFreeAsync(*t, st);
     }
   } fr{&X, &S, &tmp, st};
-  FRAC_CUDA_TRY(cudaMallocAsync(&S, nsym * sizeof(double), st));
-  FRAC_CUDA_TRY(cudaMallocAsync(&tmp, nsym * sizeof(double), st));
-  FRAC_TRY(generator_symbol_cube(op, logm, S, tmp, st));
+  FRAC_CUDA_TRY(cudaMallocAsync(&S, A.nS * sizeof(double), st));
+  FRAC_CUDA_TRY(cudaMallocAsync(&tmp, A.nS * sizeof(double), st));
+  FRAC_TRY(generator_symbol_axes(op, logm, S, tmp, st));
   FRAC_CUDA_TRY(cudaFreeAsync(tmp, st));
   tmp = nullptr;
-  FRAC_CUDA_TRY(cudaMallocAsync(&X, total * sizeof(double2), st));
-  FRAC_CUDA_TRY(cudaMemsetAsync(X, 0, total * sizeof(double2), st));
+  FRAC_CUDA_TRY(cudaMallocAsync(&X, A.total * sizeof(double2), st));
+  FRAC_CUDA_TRY(cudaMemsetAsync(X, 0, A.total * sizeof(double2), st));
 
-  NfArgs A{};
-  A.d = d;
-  A.Mp = Mp;
-  A.Kp = Kp;
-  A.E = E;
-  A.N = N;
-  A.ext0 = Kp;
-  A.total = total;
-  A.negc = negc;
-  A.inv_norm = 1.0 / full;
   auto pass = [&](int kind, int axis, const int64_t lo[3], const int64_t cnt[3], int fill, int extract) {
     NfArgs P = A;
     P.axis = axis;
@@ -342,25 +348,25 @@ int boundary_device(const frac_op* op, const double* g_ext, const double* far, d
     }
     P.fill = fill;
     P.extract = extract;
-    return nf_pass(logm, kind, P, X, g_ext, S, far, b, st);
+    return nf_pass(logm[axis], kind, P, X, g_ext, S, far, b, st);
   };
-  // other-axis ranges: [0, E) where G has samples, [0, M') everywhere, [N, 2N-1) the interior
-  // window; along axis 0 after its forward transform only k0 < K' = M'/2 + 1 (G is real: the
+  // other-axis ranges: [0, E_i) where G has samples, [0, M'_i) everywhere, [N, N + n_i) the
+  // interior window; along axis 0 after its forward transform only k0 < K'_0 (G is real: the
   // rest is conjugate-symmetric and the last pass rebuilds it)
-  const int64_t z = 0, w = N, n = N - 1;
+  const int64_t z = 0, w = N;
   if (d == 2) {
-    const int64_t lo0[3] = {z, z, z}, cnt0[3] = {0, E, 1};    // axis 0 from G: rows y < E
-    const int64_t lo1[3] = {z, z, z}, cnt1[3] = {Kp, 0, 1};   // axis 1 with the symbol: columns k0 < K'
-    const int64_t lo2[3] = {z, w, z}, cnt2[3] = {0, n, 1};    // axis 0 inverse: rows in the window
+    const int64_t lo0[3] = {z, z, z}, cnt0[3] = {0, A.E[1], 1};      // axis 0 from G: rows y < E_1
+    const int64_t lo1[3] = {z, z, z}, cnt1[3] = {A.Kp[0], 0, 1};     // axis 1 with the symbol
+    const int64_t lo2[3] = {z, w, z}, cnt2[3] = {0, A.n[1], 1};      // axis 0 inverse: window rows
     FRAC_TRY(pass(NF_FWD, 0, lo0, cnt0, 1, 0));
     FRAC_TRY(pass(NF_SYM, 1, lo1, cnt1, 0, 0));
     FRAC_TRY(pass(NF_INV, 0, lo2, cnt2, 0, 1));
   } else {
-    const int64_t lo0[3] = {z, z, z}, cnt0[3] = {0, E, E};    // axis 0 from G
-    const int64_t lo1[3] = {z, z, z}, cnt1[3] = {Kp, 0, E};   // axis 1: k0 < K', planes z < E
-    const int64_t lo2[3] = {z, z, z}, cnt2[3] = {Kp, Mp, 0};  // axis 2 with the symbol
-    const int64_t lo3[3] = {z, z, w}, cnt3[3] = {Kp, 0, n};   // axis 1 inverse: planes in the window
-    const int64_t lo4[3] = {z, w, w}, cnt4[3] = {0, n, n};    // axis 0 inverse to b
+    const int64_t lo0[3] = {z, z, z}, cnt0[3] = {0, A.E[1], A.E[2]};        // axis 0 from G
+    const int64_t lo1[3] = {z, z, z}, cnt1[3] = {A.Kp[0], 0, A.E[2]};       // axis 1: planes z < E_2
+    const int64_t lo2[3] = {z, z, z}, cnt2[3] = {A.Kp[0], A.Mp[1], 0};      // axis 2 with the symbol
+    const int64_t lo3[3] = {z, z, w}, cnt3[3] = {A.Kp[0], 0, A.n[2]};       // axis 1 inverse: window planes
+    const int64_t lo4[3] = {z, w, w}, cnt4[3] = {0, A.n[1], A.n[2]};        // axis 0 inverse to b
     FRAC_TRY(pass(NF_FWD, 0, lo0, cnt0, 1, 0));
     FRAC_TRY(pass(NF_FWD, 1, lo1, cnt1, 0, 0));
     FRAC_TRY(pass(NF_SYM, 2, lo2, cnt2, 0, 0));

@@ -1198,28 +1198,31 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
 }
 
 
-// Symbol of the generator on a cube of side M' = 2^logm: the unnormalised DFT of
-// a_{|o|} placed at o mod M' for o in [-N, N]^d, on k in [0, M'/2 + 1)^d (axis 0
-// fastest; the rest follows by k -> M' - k per axis).  The even extension of each
-// axis needs N + 1 <= M'/2.  Axis by axis with k_sym_fft, ping-ponging between
-// `tmp` and `out` so that the last axis writes `out` (both (M'/2 + 1)^d doubles).
-int generator_symbol_cube(const frac_op* op, int logm, double* out, double* tmp, cudaStream_t st) {
+// Symbol of the generator on a box of sides M'_i = 2^logm[i]: the unnormalised DFT
+// of a_{|o|} placed at o mod M'_i (per axis) for o in [-N, N]^d, on k in
+// prod_i [0, M'_i/2 + 1) (axis 0 fastest; the rest follows by k_i -> M'_i - k_i).
+// The even extension of each axis needs N + 1 <= M'_i/2.  Axis by axis with
+// k_sym_fft, ping-ponging between `tmp` and `out` so that the last axis writes
+// `out` (both prod_i (M'_i/2 + 1) doubles).
+int generator_symbol_axes(const frac_op* op, const int* logm, double* out, double* tmp, cudaStream_t st) {
   const int d = op->prob.d;
-  const int64_t n1 = op->N + 1, M = int64_t(1) << logm, K = M / 2 + 1;
-  if (2 * n1 > M) return FRAC_EINVAL;
-  const int LB = (int)std::max<int64_t>(1, std::min<int64_t>(8, 4096 / M));
-  const size_t fsm = (size_t)M * LB * sizeof(double2);
-  if (fsm > (size_t)kSymFftMaxSmem) return FRAC_ENOTSUP;
-  FRAC_TRY(ensure_twiddles(logm));
+  const int64_t n1 = op->N + 1;
   FRAC_CUDA_TRY(cudaFuncSetAttribute(k_sym_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, kSymFftMaxSmem));
   double* bufs[2] = {(d % 2) ? out : tmp, (d % 2) ? tmp : out};
   const double* src = op->a;  // the whole (N + 1)^d generator, axis 0 fastest
   int64_t B = 1;
   for (int i = 0; i < d; ++i) {
+    const int64_t M = int64_t(1) << logm[i], K = M / 2 + 1;
+    if (2 * n1 > M) return FRAC_EINVAL;
+    const int LB = (int)std::max<int64_t>(1, std::min<int64_t>(8, 4096 / M));
+    const size_t fsm = (size_t)M * LB * sizeof(double2);
+    if (fsm > (size_t)kSymFftMaxSmem) return FRAC_ENOTSUP;
+    FRAC_TRY(ensure_twiddles(logm[i]));
     int64_t A = 1;
     for (int j = i + 1; j < d; ++j) A *= n1;
     double* dst = bufs[i % 2];
-    k_sym_fft<<<(unsigned)ceil_div(A * B, 2 * LB), 256, fsm, st>>>(src, dst, A, n1, B, K, logm, LB, twiddles64(logm));
+    k_sym_fft<<<(unsigned)ceil_div(A * B, 2 * LB), 256, fsm, st>>>(src, dst, A, n1, B, K, logm[i], LB,
+                                                                     twiddles64(logm[i]));
     FRAC_CUDA_TRY(cudaGetLastError());
     src = dst;
     B *= K;

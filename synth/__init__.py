@@ -25,14 +25,16 @@ def interior_grid(n: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     return lo + h * np.arange(1, n + 1)
 
 
-def extended_points(d: int, n: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
-    """The grid points lo + e h, e in [1-N, 2N-1] per axis (N = n + 1, h = (hi - lo) / N):
-    the interior grid and the exterior points within N h of it, where nonhomogeneous
-    exterior data g is sampled.  Shape (3N-1,)*d + (d,), indexing "ij"."""
-    N = n + 1
+def extended_points(d: int, n, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """The grid points lo + e h, e in [1-N, n_i+N] on array axis i (n an int: n_i = n on
+    every axis, else one extent per array axis; N = max n_i + 1, h = (hi - lo) / N): the
+    interior grid and the exterior points within N h of it, where nonhomogeneous exterior
+    data g is sampled.  Shape (n_i + 2N)_i + (d,), indexing "ij"."""
+    shape = (int(n),) * d if np.isscalar(n) else tuple(int(v) for v in n)
+    N = max(shape) + 1
     h = (hi - lo) / N
-    e = lo + h * np.arange(1 - N, 2 * N)
-    return np.stack(np.meshgrid(*([e] * d), indexing="ij"), axis=-1)
+    axes = [lo + h * np.arange(1 - N, m + N + 1) for m in shape]
+    return np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1)
 
 
 def radius2(d: int, n: int) -> np.ndarray:

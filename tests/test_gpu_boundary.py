@@ -97,17 +97,53 @@ def test_far_input_adds_minus_c_far(d, n):
     op.close()
 
 
-@pytest.mark.parametrize("d,n,p,alpha", [(1, 4095, 1, 1.5), (2, 1023, 2, 1.2), (3, 255, 1, 1.6)])
+RECT = [(2, (7, 3), 1, 1.2, 0.0), (2, (20, 45), 0, 0.8, 0.5), (2, (63, 11), 2, 1.5, 0.0), (2, (1, 30), 1, 0.6, 0.0),
+        (3, (5, 2, 3), 1, 1.4, 0.0), (3, (9, 4, 7), 1, 0.9, 0.3), (3, (3, 11, 5), 2, 1.1, 0.0)]
+
+
+@pytest.mark.parametrize("d,ns,p,alpha,lam", RECT)
+def test_rectangular_near_field_matches_oracle(d, ns, p, alpha, lam):
+    """Rectangular grids: g sampled on [1-N, n_i+N] per axis (N = max n_i + 1, the generator's
+    cube spanning the longest axis), one circulant side per axis."""
+    import paper_2103_03658_gb300 as fg
+    N = max(ns) + 1
+    h = 2.0 / N
+    a = O.stencil(d, N, h, alpha, p, lam, q=20 if d < 3 else 12)
+    c = O.c_dalpha(d, alpha)
+    op = fg.FracOp(d, ns, alpha, degree=p, lam=lam)
+    shape = op.shape
+    G = np.random.default_rng(sum(ns)).standard_normal(op.ext_shape)
+    exts = [np.arange(1 - N, m + N + 1) for m in shape]
+    inside = np.ones(G.shape, dtype=bool)
+    for i, (e, m) in enumerate(zip(exts, shape)):
+        sh = [1] * d
+        sh[i] = len(e)
+        inside = inside & ((e >= 1) & (e <= m)).reshape(sh)
+    G_in = G.copy()
+    G_in[inside] = 1e300
+    G[inside] = 0.0
+    ref = -c * O.boundary_near(a, G)
+    b = op.boundary(torch.tensor(G_in, device="cuda")).cpu().numpy()
+    da = np.abs(op.generator() - a)
+    K = np.indices(a.shape)
+    mult = 2.0 ** np.sum(K > 0, axis=0)
+    tol = c * np.max(np.abs(G)) * (1e-12 * np.sum(mult * np.abs(a)) + np.sum(mult * da))
+    assert b.shape == shape
+    assert np.max(np.abs(b - ref)) <= tol, (np.max(np.abs(b - ref)), tol)
+    op.close()
+
+
+@pytest.mark.parametrize("d,n,p,alpha", [(1, 4095, 1, 1.5), (2, 1023, 2, 1.2), (3, 255, 1, 1.6),
+                                         (2, (1023, 300), 1, 0.9), (3, (255, 100, 64), 1, 1.3)])
 def test_constant_is_annihilated_at_full_size(d, n, p, alpha):
     """u = 1 inside and g = 1 outside: A 1 + b(1) = 0 when far = 2^d F_d (the far
     integrals of a constant), whatever the size (a_0 completes the generator sum)."""
-    N = n + 1
     op = _op(d, n, p, alpha)
     inf = op.info()
-    G = torch.ones((3 * N - 1,) * d, dtype=torch.float64, device="cuda")
-    far = torch.full((n,) * d, 2.0 ** d * inf["far_field"], dtype=torch.float64, device="cuda")
+    G = torch.ones(op.ext_shape, dtype=torch.float64, device="cuda")
+    far = torch.full(op.shape, 2.0 ** d * inf["far_field"], dtype=torch.float64, device="cuda")
     b = op.boundary(G, far=far)
-    one = torch.ones((n,) * d, dtype=torch.float64, device="cuda")
+    one = torch.ones(op.shape, dtype=torch.float64, device="cuda")
     r = op.apply(one) + b
     scale = inf["norm_bound"]                        # c max|symbol| >= c |a_0|, the size of the terms
     assert float(r.abs().max()) <= 1e-11 * scale, (float(r.abs().max()), scale)
