@@ -113,16 +113,18 @@ def axis_elements(N: int, h: float, p: int):
     basis function of ``node`` is scale * prod(xi - root for root in roots).
       p = 0: indicator of [xi_{k-1/2}, xi_{k+1/2}] cut to [0, L];
       p = 1: hat functions on the cells [j h, (j+1) h];
-      p = 2: quadratic Lagrange polynomials on [2m h, (2m+2) h] (N even).
+      p = 2: quadratic Lagrange polynomials on [2m h, (2m+2) h] (N even);
+      p = 3, 4: Lagrange polynomials of degree p on [p m h, (p m + p) h] (N a
+             multiple of p; the higher degrees the paper says raise the accuracy further).
     """
     L = N * h
     els = []
     if p == 0:
         for k in range(N + 1):
             els.append((max(0.0, (k - 0.5) * h), min(L, (k + 0.5) * h), [(k, (), 1.0)]))
-    elif p in (1, 2):
-        if p == 2 and N % 2:
-            raise ValueError("p = 2 needs an even number of intervals N")
+    elif p in (1, 2, 3, 4):
+        if N % p:
+            raise ValueError(f"p = {p} needs a number of intervals N divisible by {p}")
         for m in range(N // p):
             pts = [(p * m + t) * h for t in range(p + 1)]
             loc = []
@@ -132,7 +134,7 @@ def axis_elements(N: int, h: float, p: int):
                 loc.append((p * m + t, others, scale))
             els.append((pts[0], pts[-1], loc))
     else:
-        raise ValueError("p must be 0, 1 or 2")
+        raise ValueError("p must be 0, 1, 2, 3 or 4")
     return els
 
 
@@ -342,7 +344,13 @@ def weights_1d_appendix(N: int, h: float, alpha: float, p: int, gamma: float = 2
 # Stencil a_k and the multilevel Toeplitz operator  (Eq. (1D-scheme), Eq. (2D-scheme))
 # ---------------------------------------------------------------------------
 
-ORIGIN_RULE = {0: (1.0,), 1: (1.0,), 2: (4.0 / 3.0, -1.0 / 3.0)}
+# Weights e_j of the origin rule Phi(x, xi_0) ~ sum_j e_j Phi(x, j h) (per axis): the
+# second difference (p <= 1), the fourth-order combination (p = 2: sum e_j = 1,
+# sum e_j j^2 = 0) and, for p = 3, the sixth-order one (also sum e_j j^4 = 0), so that
+# the origin value is no less accurate than the cubic interpolation around it; p = 4 the
+# eighth-order one (sum e_j j^6 = 0 as well).
+ORIGIN_RULE = {0: (1.0,), 1: (1.0,), 2: (4.0 / 3.0, -1.0 / 3.0), 3: (1.5, -0.6, 0.1),
+               4: (1.6, -0.8, 8.0 / 35.0, -1.0 / 35.0)}
 
 
 def stencil(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0,
