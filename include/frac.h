@@ -58,7 +58,8 @@ enum frac_precision {
 typedef struct frac_problem {
   int32_t d;        /* dimension, 1..3                                             */
   int32_t degree;   /* Lagrange basis degree p: 0 (constant), 1 (linear), 2 (quadratic);
-                       p = 2 needs an even number of intervals N_i = n_i + 1       */
+                       3 and 4 for d = 1 (higher degrees: origin rules of order 6, 8);
+                       p >= 2 needs N_i = n_i + 1 divisible by p                     */
   double alpha;     /* fractional power, 0 < alpha < 2                             */
   double h;         /* mesh size, > 0                                              */
   int64_t n[3];     /* interior points per axis (N_i - 1); entries i >= d ignored.
@@ -92,8 +93,9 @@ typedef struct frac_op_info_t {
  * coefficient a_0 = -sum_{k!=0} 2^{d-z(k)} a_k - 2^d F_d, and the symbol
  * Lambda = -c_{d,alpha} DFT_M(circulant embedding of a) (real, even), kept in
  * FP64 and FP32.  *out receives a new op (release with frac_op_free).
- * Errors: FRAC_EINVAL (d not in 1..3, alpha not in (0,2), degree not in 0..2,
- * n_i < 1, an odd N_i with degree 2, h <= 0 or non-finite, gamma not 0 and not in (alpha, 2],
+ * Errors: FRAC_EINVAL (d not in 1..3, alpha not in (0,2), degree not in 0..2
+ * (0..4 for d = 1), n_i < 1, N_i not divisible by a degree >= 2, h <= 0 or
+ * non-finite, gamma not 0 and not in (alpha, 2],
  * lambda < 0 or non-finite, out == NULL), FRAC_ENOTSUP (M beyond the FFT
  * sizes of this build, per axis: M_i <= 8192 for d = 1, <= 2048 for d = 2,
  * <= 512 for d = 3), FRAC_ENOMEM, FRAC_ECUDA.  Synchronises `stream` before returning.

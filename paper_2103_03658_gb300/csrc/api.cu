@@ -66,13 +66,13 @@ static int validate(const frac_problem* p) {
   if (!p) return FRAC_EINVAL;
   if (p->d < 1 || p->d > 3) return FRAC_EINVAL;
   if (!(p->alpha > 0.0 && p->alpha < 2.0)) return FRAC_EINVAL;
-  if (p->degree < 0 || p->degree > 2) return FRAC_EINVAL;
+  if (p->degree < 0 || p->degree > 4 || (p->degree > 2 && p->d != 1)) return FRAC_EINVAL;
   if (!(p->h > 0.0) || !std::isfinite(p->h)) return FRAC_EINVAL;
   if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return FRAC_EINVAL;
   if (p->gamma != 0.0 && !(p->gamma > p->alpha && p->gamma <= 2.0)) return FRAC_EINVAL;
   for (int i = 0; i < p->d; ++i) {
     if (p->n[i] < 1) return FRAC_EINVAL;
-    if (p->degree == 2 && ((p->n[i] + 1) % 2) != 0) return FRAC_EINVAL;
+    if (p->degree >= 2 && ((p->n[i] + 1) % p->degree) != 0) return FRAC_EINVAL;
   }
   return FRAC_OK;
 }

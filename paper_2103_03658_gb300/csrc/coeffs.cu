@@ -261,10 +261,11 @@ struct WParams {
 
 struct AxisEl {
   double lo, hi;     // element interval
-  double r0, r1;     // roots of the local basis function (product form)
+  double r0, r1;     // roots of the local basis function (product form; p <= 2)
   double scale;
   int nroots;
   int origin_l;      // local index on the origin element, or -1 if lo > 0
+  double r2, r3;     // further roots (p = 3, 4; d = 1 only)
 };
 
 // Elements of the support of the 1D basis function of node k (at most 2).
@@ -280,12 +281,27 @@ __device__ int axis_elements(const WParams& P, int64_t k, AxisEl* el) {
   } else if (P.p == 1) {
     if (k >= 1 && CHK(ne, 2)) el[ne++] = AxisEl{(k - 1) * h, k * h, (k - 1) * h, 0, 1.0 / h, 1, k == 1 ? 1 : -1};
     if (k < N && CHK(ne, 2)) el[ne++] = AxisEl{k * h, (k + 1) * h, (k + 1) * h, 0, -1.0 / h, 1, k == 0 ? 0 : -1};
-  } else {
+  } else if (P.p == 2) {
     if (k & 1) {
       if (CHK(ne, 2)) el[ne++] = AxisEl{(k - 1) * h, (k + 1) * h, (k - 1) * h, (k + 1) * h, -1.0 / (h * h), 2, k == 1 ? 1 : -1};
     } else {
       if (k >= 2 && CHK(ne, 2)) el[ne++] = AxisEl{(k - 2) * h, k * h, (k - 2) * h, (k - 1) * h, 0.5 / (h * h), 2, k == 2 ? 2 : -1};
       if (k <= N - 2 && CHK(ne, 2)) el[ne++] = AxisEl{k * h, (k + 2) * h, (k + 1) * h, (k + 2) * h, 0.5 / (h * h), 2, k == 0 ? 0 : -1};
+    }
+  } else {  // p = 3, 4 (d = 1): Lagrange polynomial of node k on the elements [p m h, (p m + p) h]
+    const int p = P.p;
+    const int64_t m_lo = (k % p == 0) ? k / p - 1 : k / p, m_hi = k / p;
+    for (int64_t m = m_lo; m <= m_hi; ++m) {
+      if (m < 0 || (m + 1) * p > N || !CHK(ne, 2)) continue;
+      const int t = (int)(k - p * m);  // local index
+      double roots[4] = {0, 0, 0, 0}, scale = 1.0;
+      int nr = 0;
+      for (int s2 = 0; s2 <= p; ++s2) {
+        if (s2 == t) continue;
+        if (CHK(nr, 4)) roots[nr++] = (p * m + s2) * h;
+        scale /= (double)(t - s2) * h;
+      }
+      el[ne++] = AxisEl{p * m * h, (p * m + p) * h, roots[0], roots[1], scale, nr, m == 0 ? t : -1, roots[2], roots[3]};
     }
   }
   return ne;
@@ -295,6 +311,8 @@ __device__ __forceinline__ double basis_val(const AxisEl& e, double x) {
   double v = e.scale;
   if (e.nroots >= 1) v *= (x - e.r0);
   if (e.nroots >= 2) v *= (x - e.r1);
+  if (e.nroots >= 3) v *= (x - e.r2);
+  if (e.nroots >= 4) v *= (x - e.r3);
   return v;
 }
 
@@ -347,11 +365,30 @@ __device__ double radial_moment(double a, double b, double H) {
   return Ha * sum;
 }
 
+// Monomial coefficients (in t = xi / h, ascending) of the Lagrange basis of local
+// node l on the nodes t = 0..p, any p <= 4: prod_{s != l} (t - s) / (l - s).
+__device__ void origin_poly_lagrange(int p, int l, double* c) {
+  for (int m = 0; m <= 4; ++m) c[m] = m == 0 ? 1.0 : 0.0;
+  int deg = 0;
+  for (int s = 0; s <= p; ++s) {
+    if (s == l) continue;
+    const double inv = 1.0 / (double)(l - s);
+    for (int m = deg + 1; m >= 1; --m)
+      if (CHK(m, 5)) c[m] = (c[m - 1] - s * c[m]) * inv;
+    c[0] = -s * c[0] * inv;
+    ++deg;
+  }
+}
+
 // int_0^H phi_l(xi) mu(xi) dxi on the 1D origin element: exact radial moments of the
 // monomials of the local basis.
 __device__ double origin_element_1d(const WParams& P, int l, double H) {
-  double cf[3];
-  origin_poly(P.p, l, cf);
+  double cf[5];
+  if (P.p <= 2) {
+    origin_poly(P.p, l, cf);
+  } else {
+    origin_poly_lagrange(P.p, l, cf);
+  }
   const double ih = 1.0 / P.h;
   double s = 0.0, scale = 1.0;
   for (int m = 0; m <= P.p; ++m, scale *= ih) s += cf[m] * scale * radial_moment(P.gamma - P.alpha + m, P.lambda, H);
@@ -430,7 +467,10 @@ __global__ void k_weights_1d(WParams P, double* __restrict__ omega, int64_t coun
       total += origin_element_1d(P, E.origin_l, E.hi - E.lo);
       continue;
     }
-    const int rule = pick_rule(sqrt(E.lo * E.lo) / (E.hi - E.lo));
+    // p = 3, 4: a degree-p basis leaves 2q - p orders of the kernel's Taylor series to the
+    // rule, so the distance-chosen q (tuned for p <= 2) falls short far out; 20 points on
+    // every element (1D weights are a few per node)
+    const int rule = P.p >= 3 ? 7 : pick_rule(sqrt(E.lo * E.lo) / (E.hi - E.lo));
     if (!CHK(rule, kNumRules)) continue;
     const int q = rule_q(rule), off = rule_off(rule);
     if (!CHK(off + q - 1, kRuleTotal)) continue;
@@ -817,9 +857,12 @@ __global__ void k_stencil(WParams P, const double* __restrict__ omega, double* _
     double v = CHK(idx, count) ? ldexp(omega[idx], z) / (P.gamma == 2.0 ? xi2 : pow(xi2, 0.5 * P.gamma)) : 0.0;
     if (z == d - 1 && P.gamma == 2.0) {  // on an axis: k = j e_i
       const int64_t j = k[nzaxis];
+      // origin rule: second differences combined to order 2 (p <= 1), 4 (p = 2), 6 (p = 3), 8 (p = 4)
       double e = 0.0;
       if (P.p <= 1) e = (j == 1) ? 1.0 : 0.0;
-      else e = (j == 1) ? 4.0 / 3.0 : (j == 2 ? -1.0 / 3.0 : 0.0);
+      else if (P.p == 2) e = (j == 1) ? 4.0 / 3.0 : (j == 2 ? -1.0 / 3.0 : 0.0);
+      else if (P.p == 3) e = (j == 1) ? 1.5 : (j == 2 ? -0.6 : (j == 3 ? 0.1 : 0.0));
+      else e = (j == 1) ? 1.6 : (j == 2 ? -0.8 : (j == 3 ? 8.0 / 35.0 : (j == 4 ? -1.0 / 35.0 : 0.0)));
       if (e != 0.0) v += ldexp(1.0, d - 1) * e * omega[0] / (d * (j * P.h) * (j * P.h));
     }
     if (CHK(idx, count)) a[idx] = v;
