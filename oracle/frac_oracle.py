@@ -28,6 +28,11 @@ Readings of the paper that this oracle takes (each pinned by a test):
   * Tempered kernel (Remark 2.2): mu -> |xi|^{2-d-alpha} exp(-lambda |xi|),
     with the normalisation c_bar_{d,alpha} := c_{d,alpha} so that lambda = 0
     is the fractional Laplacian (Example 3.2.2).
+  * Degrees p = 3, 4 (the paper only says higher degrees raise the accuracy):
+    Lagrange bases on elements of p intervals, origin rules of order 6 and 8.
+  * Boundary vector (Eq. (L2)): g on every exterior grid point within the
+    generator's reach N (per axis, also on rectangles, where the generator's
+    cube spans the longest axis), the far field integrated along rays.
 """
 from __future__ import annotations
 
