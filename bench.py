@@ -467,9 +467,13 @@ def boundary_measurement(fg, torch, barrier) -> dict:
     for name, (d, n, p, alpha) in (("1d_n4095", (1, 4095, 1, 1.5)), ("2d_n1023", (2, 1023, 2, 1.2)),
                                    ("3d_n255", (3, 255, 1, 1.6))):
         op = fg.FracOp(d, n, alpha, degree=p)
-        P = synth.extended_points(d, n)
-        G = torch.tensor(np.exp(-np.sum(P * P, axis=-1)), device="cuda")
-        del P
+        # g = exp(-|x|^2) on the extended grid, formed on the device from the axis coordinates
+        x = torch.tensor(synth.extended_points(1, n)[..., 0], dtype=torch.float64, device="cuda")
+        r2 = x * x
+        for _ in range(d - 1):
+            r2 = r2.unsqueeze(-1) + (x * x)
+        G = torch.exp(-r2).contiguous()
+        del x, r2
         b = torch.empty((n,) * d, dtype=torch.float64, device="cuda")
         op.boundary(G, out=b)
         barrier()
