@@ -73,3 +73,23 @@ def test_p4_beats_p2_at_equal_grid():
         b = O.boundary_vector(1, N, h, alpha, a, c, g)
         err[p] = np.max(np.abs(O.apply_dense(a, c, 1.0 / (1.0 + x * x)) + b - O.fl_lorentzian_1d(alpha, x)))
     assert err[4] < 1e-2 * err[2], err
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_weights_integrate_tensor_monomials_2d(p):
+    """sum_k omega_k xi_1^a xi_2^b = int over [0, L]^2 of xi_1^a xi_2^b |xi|^{-alpha} for
+    a, b <= p (the tensor Lagrange interpolation reproduces them); reference by a polar
+    integral, r in closed form and theta by adaptive quadrature."""
+    alpha, N = 0.7, 2 * p if p > 1 else 3
+    h = 2.0 / N
+    L = N * h
+    w = O.weights(2, N, h, alpha, p, q=16)
+    K = np.indices(w.shape) * h
+    for a, b in {(0, 0), (1, 0), (p, 1), (p, p), (0, p)}:
+        def f(t, a=a, b=b):
+            R = L / max(math.cos(t), math.sin(t))
+            return math.cos(t) ** a * math.sin(t) ** b * R ** (a + b + 2 - alpha) / (a + b + 2 - alpha)
+        exact = sum(integrate.quad(f, lo, hi, epsabs=0, epsrel=1e-13, limit=200)[0]
+                    for lo, hi in ((0.0, math.pi / 4), (math.pi / 4, math.pi / 2)))
+        got = float(np.sum(w * K[0] ** a * K[1] ** b))
+        assert abs(got - exact) <= 1e-10 * exact, (p, a, b, got, exact)
