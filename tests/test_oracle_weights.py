@@ -351,3 +351,48 @@ def test_definition_level_sum(d, N, p):
         acc += -(2 ** d) * F * val(i)
         y[ii] = -c * acc
     assert np.allclose(y, O.apply_dense(a, c, u), rtol=0, atol=1e-12 * np.max(np.abs(y)))
+
+
+# ---------------------------------------------------------------------------
+# Degrees 3 and 4: moments up to degree p in every d, and the stencil identity
+# one even degree up (the origin rules of order 6 and 8 give Phi(0, 0) exactly).
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,p,alpha", [(1, 3, 0.4), (1, 4, 1.6), (2, 3, 1.1), (2, 4, 0.4), (3, 3, 1.6), (3, 4, 1.1)])
+def test_weight_moments_high_degree(d, p, alpha):
+    N = p
+    L, h = 2.0, 2.0 / N
+    w = O.weights(d, N, h, alpha, p, q=16 if d < 3 else 12)
+    X = _nodes(N, h, d)
+    tol = 1e-11 if d < 3 else 1e-9
+    for k in range(p + 1):
+        ref = cube_moment(d, alpha, 0.0, L, lambda v, k=k: v[0] ** k, k)
+        assert abs(np.sum(w * X[0] ** k) - ref) <= tol * ref, k
+    if d >= 2:
+        ref = cube_moment(d, alpha, 0.0, L, lambda v: v[0] ** p * v[1] ** (p - 1), 2 * p - 1)
+        assert abs(np.sum(w * X[0] ** p * X[1] ** (p - 1)) - ref) <= tol * ref
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_stencil_sextic_exactness_p4(d):
+    """u = |x|^6 at x = 0: Phi(0, xi) = 2^d |xi|^4, reproduced by quartic interpolation; the
+    eighth-order origin rule gives Phi(0, 0) = 0 exactly (sum e_j j^4 = 0)."""
+    N, alpha = 4, 0.8
+    h = 2.0 / N
+    a = O.stencil(d, N, h, alpha, 4, q=16 if d < 3 else 12)
+    lhs = _offset_sum(a, N, h, lambda r2: r2 ** 3)
+    ref = 2 ** d * cube_moment(d, alpha, 0.0, 2.0, lambda v: float(np.sum(v * v)) ** 2, 4)
+    assert abs(lhs - ref) <= 2e-9 * ref
+
+
+def test_planted_origin_rule_mistake_is_caught_p4(monkeypatch):
+    """Plant the fourth-order rule of p = 2 for p = 4: the sextic identity must fail (it
+    needs sum e_j j^4 = 0; the eighth-order condition sum e_j j^6 = 0 is pinned by the
+    moment conditions of the rules)."""
+    monkeypatch.setitem(O.ORIGIN_RULE, 4, O.ORIGIN_RULE[2] + (0.0, 0.0))
+    N, alpha, d = 4, 0.8, 1
+    h = 2.0 / N
+    a = O.stencil(d, N, h, alpha, 4)
+    lhs = _offset_sum(a, N, h, lambda r2: r2 ** 3)
+    ref = 2 ** d * cube_moment(d, alpha, 0.0, 2.0, lambda v: float(np.sum(v * v)) ** 2, 4)
+    assert abs(lhs - ref) > 1e-6 * ref
