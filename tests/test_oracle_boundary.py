@@ -119,3 +119,21 @@ def test_rectangular_near_field_equals_brute_force():
                 s += a[o] * G[e]
         ref[tuple(t - 1 for t in i)] = s
     assert np.allclose(O.boundary_near(a, G), ref, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("d,shape", [(1, (5,)), (2, (4, 4)), (2, (6, 3)), (3, (2, 4, 3))])
+def test_synth_extended_points_match_the_oracle_samples(d, shape):
+    """The inputs' extended grid (synth) and the oracle's sampling points are the same points:
+    g = sum of the coordinates weighted per axis, sampled both ways, agrees off the interior."""
+    import synth
+    N = max(shape) + 1
+    h = 2.0 / N
+    wts = np.arange(1, d + 1, dtype=float) ** 2
+    g = lambda P: np.sum(P * wts, axis=-1) + 10.0  # noqa: E731
+    G = O.extended_samples(d, N, h, g, shape=shape)
+    P = synth.extended_points(d, shape if d > 1 else shape[0])
+    S = g(P)
+    mask = G != 0.0
+    assert S.shape == G.shape
+    assert np.allclose(S[mask], G[mask], rtol=0, atol=1e-13)
+    assert np.count_nonzero(~mask) == int(np.prod(shape))      # exactly the interior is zeroed
