@@ -124,12 +124,12 @@ def test_rectangular_near_field_equals_brute_force():
 @pytest.mark.parametrize("d,shape", [(1, (5,)), (2, (4, 4)), (2, (6, 3)), (3, (2, 4, 3))])
 def test_synth_extended_points_match_the_oracle_samples(d, shape):
     """The inputs' extended grid (synth) and the oracle's sampling points are the same points:
-    g = sum of the coordinates weighted per axis, sampled both ways, agrees off the interior."""
+    a positive g that tells the axes apart, sampled both ways, agrees off the interior."""
     import synth
     N = max(shape) + 1
     h = 2.0 / N
     wts = np.arange(1, d + 1, dtype=float) ** 2
-    g = lambda P: np.sum(P * wts, axis=-1) + 10.0  # noqa: E731
+    g = lambda P: np.sum(P * P * wts, axis=-1) + 1.0 + 0.1 * P[..., 0]  # noqa: E731  (positive)
     G = O.extended_samples(d, N, h, g, shape=shape)
     P = synth.extended_points(d, shape if d > 1 else shape[0])
     S = g(P)
