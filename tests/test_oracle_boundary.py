@@ -13,6 +13,7 @@ far-field part (integrals of g over the far region).
   reach of each interior point (not over offsets).
 """
 import itertools
+import math
 
 import numpy as np
 import pytest
@@ -137,3 +138,22 @@ def test_synth_extended_points_match_the_oracle_samples(d, shape):
     assert S.shape == G.shape
     assert np.allclose(S[mask], G[mask], rtol=0, atol=1e-13)
     assert np.count_nonzero(~mask) == int(np.prod(shape))      # exactly the interior is zeroed
+
+
+@pytest.mark.parametrize("alpha,lam", [(0.5, 0.0), (1.5, 0.0), (1.2, 0.8)])
+def test_far_part_1d_against_adaptive_quadrature(alpha, lam):
+    """1D: far_i = sum over s = +-1 of int_L^inf g(x_i + s rho) rho^{-1-alpha} e^{-lam rho} d rho,
+    by QUADPACK on the half line (independent of the oracle's t = L / rho substitution)."""
+    from scipy import integrate
+    N = 8
+    h = 2.0 / N
+    L = N * h
+    g = lambda P: 1.0 / (1.0 + P[..., 0] ** 2)  # noqa: E731
+    far = O.boundary_far(1, N, h, alpha, g, lam)
+    x = -1.0 + h * np.arange(1, N)
+    for i, xi in enumerate(x):
+        ref = 0.0
+        for s in (-1.0, 1.0):
+            f = lambda r, s=s, xi=xi: r ** (-1.0 - alpha) * math.exp(-lam * r) / (1.0 + (xi + s * r) ** 2)  # noqa: E731
+            ref += integrate.quad(f, L, np.inf, epsabs=0, epsrel=1e-12, limit=400)[0]
+        assert abs(far[i] - ref) <= 1e-10 * ref, (i, far[i], ref)
