@@ -255,9 +255,10 @@ static int run_apply(const frac_op* op, const void* u, void* y, int dtype, int64
 // pipe_slots() device input and output buffers.  Events order a chunk's three
 // stages and the reuse of a slot: a chunk's input copy waits for the apply that
 // last read its input buffer, its apply for the output copy that last read its
-// output buffer.  The two copy directions run on separate copy engines, so each
-// stays busy while the applies (one stream, one workspace) fit in between.
-// Returns after the last copy has landed.
+// output buffer.  The two copy directions run on separate copy engines and the
+// applies (one stream, one workspace) overlap them; the host link bounds the whole
+// (the same pipeline with no applies at all takes as long).  Returns after the
+// last copy has landed.
 constexpr size_t kPipeChunkBytes = 28u << 20;
 constexpr int kPipeSlots = 3;
 static size_t pipe_chunk_bytes() {  // FRAC_PIPE_CHUNK_MB overrides the chunk size (tuning), read once
