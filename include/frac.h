@@ -25,6 +25,11 @@
  *     and the scratch it allocates (stream-ordered, cudaMallocAsync).
  *   - Return value: FRAC_OK or one of the error codes below; frac_strerror()
  *     names it.  On error no output is written unless stated.
+ *   - Devices: an operator's tables live on the device that was current when
+ *     frac_coeffs built it.  frac_apply, frac_apply_static, frac_precond,
+ *     frac_boundary and frac_solve return FRAC_EINVAL (frac_error_detail says
+ *     why) when that device is not the current one, or when a buffer is device
+ *     memory of another device.
  */
 #ifndef FRAC_H
 #define FRAC_H

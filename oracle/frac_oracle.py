@@ -211,13 +211,18 @@ def _gauss_points(lo, hi, q):
 
 
 def weights(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0, q: int = 20,
-            gamma: float = 2.0) -> np.ndarray:
+            gamma: float = 2.0, first=None) -> np.ndarray:
     """omega_k^p for every k in {0..N}^d (Eq. (wi-1D); Eq. (2D-scheme0); Remark 2.2 for lambda > 0).
 
     omega_k = int over [0, L]^d of prod_i phi_{k_i}(xi_i) mu(xi) dxi with
     mu(xi) = |xi|^{gamma-d-alpha} exp(-lambda |xi|) (mu_gamma of Eq. (eq0)), summed element by element:
     the origin element by ``_origin_block``; every other element, where the
     integrand is smooth, by a q^d-point tensor Gauss-Legendre rule.
+
+    ``first`` (d >= 2): a range of element indices along the first array axis;
+    only the elements in that range are summed (the sum over all ranges of a
+    partition is the whole array; a test driver uses this to spread the 3D
+    generator of the largest grids over processes).
     """
     els = axis_elements(N, h, p)
     ne = len(els)
@@ -237,7 +242,10 @@ def weights(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0, q:
     qlet = "pqr"[: d - 1]
     spec = ",".join(f"{letters[i]}{qlet[i]}" for i in range(d - 1))
     spec = (spec + "," if spec else "") + "elz," + "e" + "".join(qlet) + "z->e" + letters + "l"
-    for outer in itertools.product(range(ne), repeat=d - 1):
+    ranges = [range(ne)] * (d - 1)
+    if first is not None and d > 1:
+        ranges[0] = first
+    for outer in itertools.product(*ranges):
         r2 = np.zeros((ne,) + (q,) * d)
         for i, e in enumerate(outer):
             shape = [1] * (d + 1)
@@ -246,9 +254,11 @@ def weights(d: int, N: int, h: float, alpha: float, p: int, lam: float = 0.0, q:
         shape = [ne] + [1] * (d - 1) + [q]
         r2 = r2 + (X ** 2).reshape(shape)
         r = np.sqrt(r2)
-        Mu = r ** (gamma - d - alpha) * np.exp(-lam * r)
+        Mu = r ** (gamma - d - alpha)
+        if lam != 0.0:
+            Mu = Mu * np.exp(-lam * r)
         ops = [WB[e] for e in outer] + [WB, Mu]
-        C = np.einsum(spec, *ops)                                     # (ne, nloc.., nloc)
+        C = np.einsum(spec, *ops, optimize=True)                      # (ne, nloc.., nloc)
         if all(e == 0 for e in outer):
             C[0] = _origin_block(d, alpha, lam, H0, els[0][2], gamma=gamma)
         idx = []
@@ -430,6 +440,27 @@ def apply_rows(a: np.ndarray, c: float, u: np.ndarray, rows: np.ndarray) -> np.n
         D = tuple(np.abs(J[i] - r[i]) for i in range(d))
         out[t] = -c * math.fsum(a[D] * uf)
     return out
+
+
+def spectral_bound(a: np.ndarray, c: float, n) -> float:
+    """max |eigenvalue| of the circulant of side 2 n_i per axis whose leading block is
+    A = -c T(a) on the grid of shape grid_shape(a, n) (first column a_{min(j, M_i - j)}
+    for min(j, M_i - j) < n_i, zero elsewhere).  A is a principal submatrix of that
+    symmetric circulant, so this bounds ||A||_2 from above, and it is the largest
+    |Lambda| of an embedding of A; the eigenvalues are the DFT of the first column
+    (numpy's FFT as the library primitive).  Used to scale apply errors."""
+    shp = grid_shape(a, n)
+    C = np.zeros(tuple(2 * v for v in shp))
+    idx = []
+    for v in shp:
+        j = np.arange(2 * v)
+        m = np.minimum(j, 2 * v - j)
+        idx.append(np.where(m < v, m, -1))
+    grids = np.meshgrid(*idx, indexing="ij")
+    live = np.all([g >= 0 for g in grids], axis=0)
+    C[live] = a[tuple(g[live] for g in grids)]
+    lam = -c * np.real(np.fft.fftn(C))
+    return float(np.max(np.abs(lam)))
 
 
 def norm_bound(a: np.ndarray, c: float, n) -> float:

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <initializer_list>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -51,13 +52,21 @@ static int side_stream(cudaStream_t* out) {
   return FRAC_OK;
 }
 
-static bool is_device_ptr(const void* p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
+static bool is_device_ptr(const void* p) { return ptr_kind(p) == PTR_DEVICE; }
+
+// FRAC_EINVAL (with a detail) unless op was built on the current device and none of
+// the given pointers is device memory of another device.
+static int check_placement(const frac_op* op, const char* who, std::initializer_list<const void*> ptrs) {
+  if (!op_on_current_device(op)) {
+    record_detail("%s: the operator was built on device %d, which is not the current device", who, op->device);
+    return FRAC_EINVAL;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  for (const void* p : ptrs)
+    if (p && ptr_kind(p) == PTR_OTHER_DEVICE) {
+      record_detail("%s: a buffer lives on another device than the current one", who);
+      return FRAC_EINVAL;
+    }
+  return FRAC_OK;
 }
 
 static int max_logm(int d) { return d == 1 ? 13 : (d == 2 ? 11 : 9); }
@@ -367,6 +376,7 @@ static int apply_entry(const frac_op* op, const void* u, void* y, int dtype, int
   if (precond && !op->precond_ok) return FRAC_ENOTSUP;
   if (batch == 0) return FRAC_OK;
   if (!u || !y || u == y) return FRAC_EINVAL;
+  FRAC_TRY(check_placement(op, precond ? "frac_precond" : "frac_apply", {u, y}));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t es = dtype == FRAC_F64 ? sizeof(double) : sizeof(float);
   const size_t bytes = (size_t)batch * op->nd * es;
@@ -420,6 +430,7 @@ int frac_precond(const frac_op* op, const void* r, void* z, int dtype, int64_t b
 
 int frac_boundary(const frac_op* op, const double* g_ext, const double* far, double* b, void* stream) {
   if (!op || !g_ext || !b) return FRAC_EINVAL;
+  FRAC_TRY(check_placement(op, "frac_boundary", {g_ext, far, b}));
   cudaStream_t st = (cudaStream_t)stream;
   const int d = op->prob.d;
   int64_t ne = 1;
@@ -456,6 +467,7 @@ int frac_solve(const frac_op* op, const double* f, const double* g, double* u, c
   if (!op || !f || !u || !opts || !info) return FRAC_EINVAL;
   if (!(opts->rtol > 0.0) || opts->max_iter < 1) return FRAC_EINVAL;
   if (opts->precision != FRAC_PLAIN_F64 && opts->precision != FRAC_MIXED_IR) return FRAC_EINVAL;
+  FRAC_TRY(check_placement(op, "frac_solve", {f, g, u}));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = op->nd * sizeof(double);
   const bool df = is_device_ptr(f), du = is_device_ptr(u), dg = g && is_device_ptr(g);

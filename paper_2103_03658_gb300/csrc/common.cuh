@@ -45,6 +45,27 @@ void record_detail(const char* fmt, ...);
     if (s_ != FRAC_OK) return s_; \
   } while (0)
 
+// Where a caller's pointer lives: host memory (pageable, pinned or unknown to
+// CUDA), device memory of the current device (or managed memory), or device
+// memory of another device, which the library's kernels on the current device
+// must not be given.
+enum PtrKind { PTR_HOST = 0, PTR_DEVICE = 1, PTR_OTHER_DEVICE = 2 };
+inline PtrKind ptr_kind(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return PTR_HOST;
+  }
+  if (at.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+  if (at.type != cudaMemoryTypeDevice) return PTR_HOST;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return PTR_OTHER_DEVICE;
+  }
+  return at.device == dev ? PTR_DEVICE : PTR_OTHER_DEVICE;
+}
+
 inline int ilog2(int64_t m) {
   int l = 0;
   while ((int64_t(1) << l) < m) ++l;
@@ -88,6 +109,17 @@ struct frac_op {
   size_t device_bytes;
   int device;
 };
+
+// The operator's tables live on the device that was current when it was built:
+// every call that launches work with it must run with that device current.
+inline bool op_on_current_device(const frac_op* op) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return dev == op->device;
+}
 
 // Inner tolerance of the mixed-precision refinement when the caller leaves it at 0:
 // a well-conditioned operator (kappa_est < 50, so FP32 CG resolves a 1e-6 reduction)

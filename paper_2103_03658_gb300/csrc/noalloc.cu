@@ -43,14 +43,8 @@ int static_scratch(void** out) {
   return FRAC_OK;
 }
 
-bool on_device(const void* p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
+// device (or managed) memory that the current device's kernels may use
+bool on_device(const void* p) { return ptr_kind(p) == PTR_DEVICE; }
 
 }  // namespace
 }  // namespace frac
@@ -63,8 +57,17 @@ extern "C" int frac_apply_static(const frac_op* op, const void* u, void* y, int 
   if (batch == 0) return FRAC_OK;
   if (!u || !y || u == y) return FRAC_EINVAL;
   const size_t es = dtype == FRAC_F64 ? sizeof(double) : sizeof(float);
-  // host buffers would need staging allocations: device memory only here
-  if (!on_device(u) || !on_device(y)) return FRAC_EINVAL;
+  // host buffers would need staging allocations: device memory of the current device only,
+  // and the operator's tables must live there too
+  if (!op_on_current_device(op)) {
+    record_detail("frac_apply_static: the operator was built on device %d, which is not the current device",
+                  op->device);
+    return FRAC_EINVAL;
+  }
+  if (!on_device(u) || !on_device(y)) {
+    record_detail("frac_apply_static: u and y must be device buffers of the current device");
+    return FRAC_EINVAL;
+  }
   if (((uintptr_t)u % es) || ((uintptr_t)y % es)) return FRAC_EINVAL;
   const size_t need = apply_workspace_bytes(op, dtype, batch);
   if (need > kStaticScratchBytes) {

@@ -219,26 +219,89 @@ def test_apply_host_buffers_pipelined_equals_device(dtype, batch):
     op.close()
 
 
-def test_apply_2d_full_size_sampled_rows():
-    """The bench workload: 1023^2 grid, alpha = 1.2, p = 2, 65 FP32 fields
-    (u_exact and 64 smooth random fields) in one call; sampled rows of every
-    field against the oracle."""
+def _check_sampled(got, ref, uu, nrm, rho, tol, nrows, what):
+    """Sampled-row checks of one field: the normwise error (the row error scaled by
+    sqrt(rows / points) to a whole-vector estimate) against tol ||A|| ||u|| with the
+    row-sum bound, and the plain relative error ||y - y_ref|| / ||y_ref|| over the rows
+    against tol kappa_y, kappa_y = rho ||u|| / ||A u|| with rho the circulant bound of
+    ||A||_2 (the tighter of the two).  Returns (relative error, kappa_y)."""
+    scale = np.sqrt(nrows / uu.size)
+    e = np.linalg.norm(got - ref)
+    assert e <= tol * nrm * np.linalg.norm(uu) * scale, (what, e / (nrm * np.linalg.norm(uu) * scale))
+    rel = e / np.linalg.norm(ref)
+    kappa_y = rho * np.linalg.norm(uu) * scale / np.linalg.norm(ref)
+    assert rel <= tol * kappa_y, (what, rel, kappa_y)
+    return rel, kappa_y
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_apply_2d_full_size_sampled_rows(dtype):
+    """The bench workload: 1023^2 grid, alpha = 1.2, p = 2, 65 fields (u_exact and 64
+    smooth random fields) in one call, FP32 (the bench's precision) and FP64; sampled
+    rows of four fields against the oracle, normwise and plain relative errors."""
     d, n, p, alpha = 2, 1023, 2, 1.2
     a, c = oracle_operator(d, n, p, alpha, 0.0)
     nrm = O.norm_bound(a, c, n)
+    rho = O.spectral_bound(a, c, n)
     op = _op(d, n, p, alpha, 0.0)
     fields = np.concatenate([synth.ball_power(d, n, 1 + alpha / 2)[None], synth.smooth_fields(d, n, 64)])
-    u_dev = torch.tensor(fields, dtype=torch.float32, device="cuda")
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    u_dev = torch.tensor(fields, dtype=tdt, device="cuda")
     y = op.apply(u_dev).double().cpu().numpy()
+    tol = 1e-5 if dtype == "f32" else 1e-12
     rng = np.random.default_rng(3)
     for b in (0, 1, 31, 64):
-        rows = np.array([[0, 0], [n - 1, n - 1], [511, 511]] + [list(rng.integers(0, n, 2)) for _ in range(13)])
-        uu = fields[b].astype(np.float32).astype(np.float64)
+        rows = np.array([[0, 0], [n - 1, n - 1], [511, 511], [0, n - 1]] + [list(rng.integers(0, n, 2)) for _ in range(28)])
+        uu = fields[b].astype(np.float32).astype(np.float64) if dtype == "f32" else fields[b]
         ref = O.apply_rows(a, c, uu, rows)
         got = y[b][tuple(rows.T)]
-        err = np.max(np.abs(got - ref)) / (nrm * np.sqrt(np.mean(uu * uu)))
-        assert err <= 1e-5, (b, err)
+        rel, kap = _check_sampled(got, ref, uu, nrm, rho, tol, len(rows), (dtype, b))
+        print(f"2D 1023^2 {dtype} field {b}: rel {rel:.2e}, kappa_y {kap:.1f}")
     op.close()
+
+
+_GEN3D = {}
+
+
+def _oracle_generator_3d(n, p, alpha):
+    """The oracle's whole 3D generator for the 255^3 grid (N = 256), its weights summed
+    by a pool of host processes (about a minute on 16 cores)."""
+    import _oracle_pool as P
+    key = (n, p, alpha)
+    if key not in _GEN3D:
+        a, c = P.stencil(3, n + 1, alpha, p, 0.0, q=12)
+        _GEN3D[key] = (a, c, O.norm_bound(a, c, n), O.spectral_bound(a, c, n))
+    return _GEN3D[key]
+
+
+_ROWS3D = {}
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_apply_3d_full_size_sampled_rows(dtype):
+    """The 3D configuration at full size: 255^3 grid on a 512^3 FFT grid, alpha = 1.6,
+    p = 1, one seeded smooth-plus-noise field (rounded to FP32, so that both precisions
+    apply the same vector); 256 seeded rows (corners, faces, centre and random points)
+    against the oracle's dense rows built from its own whole generator."""
+    import _oracle_pool as P
+    d, n, p, alpha = 3, 255, 1, 1.6
+    a, c, nrm, rho = _oracle_generator_3d(n, p, alpha)
+    rng = np.random.default_rng(255)
+    U = (synth.smooth_field(d, n, 4242) + 0.1 * rng.standard_normal((n,) * d)).astype(np.float32).astype(np.float64)
+    corners = [[i, j, k] for i in (0, n - 1) for j in (0, n - 1) for k in (0, n - 1)]
+    rows = np.array(corners + [[n // 2] * 3, [0, n // 2, n // 2], [n - 1, 1, 128]] +
+                    [list(rng.integers(0, n, 3)) for _ in range(256 - 11)])
+    op = _op(d, n, p, alpha, 0.0)
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    y = op.apply(torch.tensor(U, dtype=tdt, device="cuda")).double().cpu().numpy()
+    op.close()
+    if "ref" not in _ROWS3D:
+        _ROWS3D["ref"] = P.apply_rows(a, c, U, rows)
+    ref = _ROWS3D["ref"]
+    got = y[tuple(rows.T)]
+    tol = 1e-5 if dtype == "f32" else 1e-12
+    rel, kap = _check_sampled(got, ref, U, nrm, rho, tol, len(rows), dtype)
+    print(f"3D 255^3 {dtype}: rel {rel:.2e}, kappa_y {kap:.1f}")
 
 
 def test_apply_3d_full_size_properties():

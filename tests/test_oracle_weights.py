@@ -396,3 +396,58 @@ def test_planted_origin_rule_mistake_is_caught_p4(monkeypatch):
     lhs = _offset_sum(a, N, h, lambda r2: r2 ** 3)
     ref = 2 ** d * cube_moment(d, alpha, 0.0, 2.0, lambda v: float(np.sum(v * v)) ** 2, 4)
     assert abs(lhs - ref) > 1e-6 * ref
+
+
+# ---------------------------------------------------------------------------
+# The origin element by an independent rule (spherical / polar coordinates with
+# QUADPACK, not the Duffy split of the oracle), in 2D and 3D
+# ---------------------------------------------------------------------------
+
+def _lagrange_1d(p, h, j):
+    """Ascending coefficients of the Lagrange polynomial of node j h on the nodes
+    0, h, .., p h (degree p)."""
+    c = np.array([1.0])
+    for t in range(p + 1):
+        if t != j:
+            c = np.convolve(c, np.array([-t * h, 1.0])) / ((j - t) * h)
+    return c
+
+
+def _origin_node_polar(d, N, alpha, lam, p, k):
+    """omega_k for a node k that only the origin element [0, max(p, 1) h]^d supports,
+    as sum over total degrees m of int P_m(xi) |xi|^{2-d-alpha} e^{-lam |xi|} with P_m
+    the degree-m part of the basis product (cube_moment: radial part exact or adaptive,
+    angles by QUADPACK)."""
+    h = 2.0 / N
+    pe = max(p, 1)
+    polys = [_lagrange_1d(pe, h, int(ki)) for ki in k]
+    coef = {}
+    for mono in itertools.product(*[range(len(c)) for c in polys]):
+        coef[mono] = np.prod([polys[i][m] for i, m in enumerate(mono)])
+    tot = 0.0
+    for deg in range(sum(len(c) - 1 for c in polys) + 1):
+        terms = [(m, v) for m, v in coef.items() if sum(m) == deg and v != 0.0]
+        if not terms:
+            continue
+
+        def P(dv, terms=terms):
+            return sum(v * np.prod(dv ** np.array(m)) for m, v in terms)
+        tot += cube_moment(d, alpha, lam, pe * h, P, deg)
+    return tot
+
+
+@pytest.mark.parametrize("d,p,alpha,lam,k", [
+    (3, 1, 1.3, 0.0, (0, 0, 0)), (3, 1, 0.4, 0.0, (0, 0, 0)),
+    (3, 2, 1.6, 0.0, (0, 0, 0)), (3, 2, 0.7, 0.0, (1, 0, 0)), (3, 2, 1.2, 0.0, (1, 1, 0)),
+    (3, 2, 1.9, 0.0, (1, 1, 1)),
+    (2, 2, 1.2, 0.0, (0, 0)), (2, 2, 0.5, 0.8, (1, 0)), (2, 2, 1.8, 1.5, (1, 1)),
+    (2, 1, 0.9, 0.6, (0, 0)),
+])
+def test_origin_element_against_polar_quadrature(d, p, alpha, lam, k):
+    """The nodes that only the origin element supports (k = 0 for p <= 1, k_i in {0, 1}
+    for p = 2): the oracle's Duffy-split weights against spherical (3D) / polar (2D)
+    coordinates integrated by QUADPACK, to 1e-12 relative (they agree to ~1e-15)."""
+    N = 8
+    w = O.weights(d, N, 2.0 / N, alpha, p, lam)
+    ref = _origin_node_polar(d, N, alpha, lam, p, k)
+    assert abs(w[tuple(k)] - ref) <= 1e-12 * abs(ref), (w[tuple(k)], ref)
