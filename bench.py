@@ -64,26 +64,64 @@ def oracle_generator() -> tuple:
     return a, O.c_dalpha(D, ALPHA), time.perf_counter() - t0
 
 
-def oracle_rows_rate(seconds: float = 15.0, fields: np.ndarray | None = None, gen: tuple | None = None) -> dict:
-    """Time the FP64 oracle on a bounded sample of the workload: dense rows of the
-    fields until ``seconds`` have elapsed (the generator built first unless given)."""
+def _pool_init(a, c, fields):
+    global _POOL_STATE
+    _POOL_STATE = (a, c, fields)
+
+
+def _pool_rows(args):
+    """One worker's share of the CPU baseline: oracle rows of seeded fields and points
+    until `seconds` have elapsed; returns (rows, seconds)."""
     from oracle import frac_oracle as O
-    a, c, t_gen = gen if gen is not None else oracle_generator()
-    if fields is None:
-        fields = np.stack([synth.ball_power(D, NSIDE, 1 + ALPHA / 2), synth.smooth_field(D, NSIDE, synth.BASE_SEED)])
-    rng = np.random.default_rng(1)
+    seed, seconds = args
+    a, c, fields = _POOL_STATE
+    rng = np.random.default_rng(seed)
     rows = 0
     t1 = time.perf_counter()
     while time.perf_counter() - t1 < seconds:
         b = rows % len(fields)
-        r = rng.integers(0, NSIDE, size=(1, 2))
-        O.apply_rows(a, c, fields[b].astype(np.float64), r)
+        O.apply_rows(a, c, fields[b], rng.integers(0, NSIDE, size=(1, 2)))
         rows += 1
-    t_rows = time.perf_counter() - t1
-    rate = rows / t_rows / 1e9
-    return {"value": rate, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
-            "sample": f"{rows} output rows of the 1023^2 FP64 dense sum (generator build {t_gen:.1f} s excluded), "
-                      f"single-threaded numpy"}
+    return rows, time.perf_counter() - t1
+
+
+class OraclePool:
+    """The FP64 oracle on every host core: a pool of `spawn` workers (the parent may
+    already hold a CUDA context), each evaluating dense rows of the workload with
+    oracle.apply_rows (a math.fsum over the 1023^2 products of one output point)."""
+
+    def __init__(self, gen: tuple, fields: np.ndarray, workers: int | None = None):
+        import multiprocessing as mp
+        self.a, self.c, self.t_gen = gen
+        self.workers = workers or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_pool_init,
+                                                 initargs=(self.a, self.c, fields))
+        self.pool.map(_pool_rows, [(w, 0.05) for w in range(self.workers)])  # workers up and warm
+        self.calls = 0
+
+    def rate(self, seconds: float) -> dict:
+        self.calls += 1
+        t0 = time.perf_counter()
+        res = self.pool.map(_pool_rows, [(1000 * self.calls + w, seconds) for w in range(self.workers)])
+        wall = time.perf_counter() - t0
+        rows = sum(r for r, _ in res)
+        return {"value": rows / wall / 1e9, "unit": "GDOF/s", "cores": self.workers, "kind": "oracle",
+                "sample": f"{rows} output points of the 1023^2 FP64 dense sum (oracle.apply_rows, math.fsum over "
+                          f"1023^2 products each) on {self.workers} worker processes for {wall:.1f} s; generator "
+                          f"build {self.t_gen:.1f} s excluded"}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_rows_rate(seconds: float = 15.0) -> dict:
+    fields = np.stack([synth.ball_power(D, NSIDE, 1 + ALPHA / 2), synth.smooth_field(D, NSIDE, synth.BASE_SEED)])
+    pool = OraclePool(oracle_generator(), fields)
+    try:
+        return pool.rate(seconds)
+    finally:
+        pool.close()
 
 
 def run_reference(args) -> None:
@@ -91,13 +129,14 @@ def run_reference(args) -> None:
     if rank != 0:
         return
     fields = np.stack([synth.ball_power(D, NSIDE, 1 + ALPHA / 2), synth.smooth_field(D, NSIDE, synth.BASE_SEED)])
-    gen = oracle_generator()
-    per_step = max(2.0, 60.0 / max(args.steps + args.warmup, 1))
+    pool = OraclePool(oracle_generator(), fields)
+    per_step = max(0.25, min(10.0, 60.0 / max(args.steps + args.warmup, 1)))  # about a minute in all
     for _ in range(args.warmup):
-        oracle_rows_rate(min(per_step, 2.0), fields, gen)
+        pool.rate(min(per_step, 1.0))
     t0 = time.perf_counter()
-    vals = [oracle_rows_rate(per_step, fields, gen) for _ in range(args.steps)]
+    vals = [pool.rate(per_step) for _ in range(args.steps)]
     wall = time.perf_counter() - t0
+    pool.close()
     v = statistics.median(x["value"] for x in vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GDOF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
@@ -216,20 +255,11 @@ def apply_model_bytes(fields: int) -> float:
     return fields * (2 * n * n * 4 + 4 * n * K * 8) + K * K * 4
 
 
-# FP32 FMA peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-
 # DRAM bytes per field (dram__bytes_read.sum + dram__bytes_write.sum of one
-# launch / fields in it) of the kernels as they stand, from one ncu --set full
-# capture of a 20-field apply, scaled to a launch by the fields it processes.
-# With 20 fields part of the 168 MB half spectrum is still in the 129 MB L2 when
-# the next pass reads it, so at 65 fields the traffic per field is somewhat
-# higher.  Remove an entry when its kernel changes.
-DRAM_TRAFFIC_PER_FIELD = {
-    "cols_sym2_f32_M2048": (172.519424e6 + 110.782464e6) / 20,
-    "rows_fwd_f32_M2048": (84.167936e6 + 114.912768e6) / 20,
-    "rows_inv_f32_M2048": (168.301824e6 + 53.662464e6) / 20,
-}
+# launch / fields in it) of the kernels as they stand, from one ncu capture of
+# the 65-field apply (profiles/apply2d_1023_65fields_dram.md), scaled to a launch
+# by the fields it processes.  Remove an entry when its kernel changes.
+DRAM_TRAFFIC_PER_FIELD = {}
 
 
 def max_over_ranks(x: float, dist, device: str = "cuda") -> float:
@@ -268,6 +298,7 @@ def run_ours(args) -> None:
             dist.barrier()
         torch.cuda.synchronize()
 
+    alu_peaks = {k: nat.alu_peak_tflops(k) for k in ("f32", "f64", "f32x2")}
     op = fg.FracOp(D, NSIDE, ALPHA, degree=DEGREE)
     host = workload_fields()
     u = torch.from_numpy(host).cuda()
@@ -293,20 +324,19 @@ def run_ours(args) -> None:
     value = whole_job_rate(dof, world, ms * 1e-3) / 1e9
     launches = sum(v[0] for v in prof.values())
 
-    # roofline of the dominant kernel (largest total device time in the timed region)
+    # roofline of the dominant kernel (largest total device time in the timed region):
+    # algorithmic bytes of one launch over its CUDA-event duration against the measured
+    # HBM copy rate; its FFT arithmetic against the FP32 rate measured in this run
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs")
-    peak_note = "measured" if peak else "fallback"
+    peak_note = "measured (STREAM-style copy)" if peak else "fallback 6800 GB/s"
     peak = peak or 6800.0
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roof = None
     if dom:
         name, (nl, tot) = dom
-        # the 2D apply runs its passes on chunks of fields (one launch per pass and
-        # chunk): per-launch figures are the step's totals over its launches
         lps = nl / args.steps
         per_launch_ms = tot / nl
-        step_ms = tot / args.steps
         ab = algorithmic_bytes(name, NFIELDS, lps) / lps
         fl = nominal_flops(name, NFIELDS) / lps
         hbm = ab / (per_launch_ms * 1e-3) / 1e9
@@ -315,25 +345,18 @@ def run_ours(args) -> None:
         if tr is not None:
             tr = tr * NFIELDS / lps
         bm = apply_model_bytes(NFIELDS)
-        # the symbol pass is issue bound (FP32 FFT arithmetic, DRAM well below
-        # peak in the capture); the row passes are closer to the HBM bound
-        alu_bound = name.startswith("cols")
-        roof = {"bound": "alu" if alu_bound else "hbm", "kernel": name,
-                "achieved": alu if alu_bound else hbm,
-                "peak": FP32_PEAK_TFLOPS if alu_bound else peak,
-                "unit": "TFLOP/s" if alu_bound else "GB/s",
-                "frac": (alu / FP32_PEAK_TFLOPS) if alu_bound else (hbm / peak),
-                "peak_source": ("FP32 FMA peak from unit counts and clocks (152 SMs x 128 lanes x 2 x 2.07 GHz)"
-                                if alu_bound else peak_note),
-                "traffic": tr,
-                "algorithmic_bytes": ab, "nominal_flops": fl, "ms_per_launch": per_launch_ms,
-                "launches_per_step": lps, "fields_per_launch": NFIELDS / lps, "kernel_ms_per_step": step_ms,
-                "hbm_view": {"achieved_gbs": hbm, "peak_gbs": peak, "frac": hbm / peak, "peak_source": peak_note},
-                "alu_view": {"achieved_tflops": alu, "peak_tflops": FP32_PEAK_TFLOPS, "frac": alu / FP32_PEAK_TFLOPS},
+        total_ms = sum(v[1] for v in prof.values())
+        roof = {"bound": "hbm", "kernel": name, "achieved": hbm, "peak": peak, "unit": "GB/s", "frac": hbm / peak,
+                "peak_source": peak_note, "traffic": tr,
+                "algorithmic_bytes": ab, "ms_per_launch": per_launch_ms, "launches_per_step": lps,
+                "fields_per_launch": NFIELDS / lps, "kernel_ms_per_step": tot / args.steps,
                 "apply_model": {"bytes": bm, "ms": ms, "achieved_gbs": bm / (ms * 1e-3) / 1e9,
                                 "frac_of_hbm_peak": bm / (ms * 1e-3) / 1e9 / peak},
+                "alu_view": {"nominal_flops": fl, "achieved_tflops": alu, "peak_tflops": alu_peaks["f32"],
+                             "frac": alu / alu_peaks["f32"], "peak_source": "fma.rn.f32 rate measured in this run",
+                             "peak_f32x2_tflops": alu_peaks["f32x2"]},
                 "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1),
-                                "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-12)} for k, v in prof.items()}}
+                                "share": v[1] / max(total_ms, 1e-12)} for k, v in prof.items()}}
 
     # end to end through the public API with pinned host buffers (copies inside the timed region)
     hu = torch.from_numpy(host).pin_memory()
@@ -349,9 +372,10 @@ def run_ours(args) -> None:
     e2e = {"value": whole_job_rate(dof, world, e2e_s) / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": host.nbytes,
            "d2h_bytes_per_step": host.nbytes}
 
-    extra = {}
+    extra = {"alu_peaks_tflops": alu_peaks, "apply_f64": apply_f64_measurement(lib, torch, u, op, barrier,
+                                                                                  alu_peaks["f64"], peak)}
     if not args.no_extra:
-        extra = extra_measurements(fg, torch, u, op, barrier)
+        extra.update(extra_measurements(fg, torch, u, op, barrier))
 
     if rank != 0:
         op.close()
@@ -373,23 +397,47 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def apply_f64_measurement(lib, torch, u32, op, barrier, f64_peak: float, hbm_peak: float, steps: int = 10) -> dict:
+    """The same 65-field apply in FP64 (BASELINE config 2's FP64 arm): CUDA events over
+    `steps` applies after a warm-up, per-kernel times from the library's profiler, and
+    the FP64 ALU roofline (nominal FFT flops against the fma.rn.f64 rate measured in
+    this run: FP64 runs at a small fraction of the FP32 rate on this part, so these
+    passes are bound by FP64 arithmetic, not by HBM) beside the HBM view of the byte
+    model (every FP32 byte doubled)."""
+    u64 = u32.double()
+    y64 = torch.empty_like(u64)
+    for _ in range(2):
+        op.apply(u64, out=y64)
+    barrier()
+    lib.frac_profile_enable(1)
+    profile_read(lib)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        op.apply(u64, out=y64)
+    e1.record()
+    barrier()
+    lib.frac_profile_enable(0)
+    prof = profile_read(lib)
+    ms = e0.elapsed_time(e1) / steps
+    fl = sum(nominal_flops(k, NFIELDS) for k in prof)
+    bm = 2 * apply_model_bytes(NFIELDS)
+    del u64, y64
+    return {"value": NFIELDS * NSIDE * NSIDE / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "ms_per_step": ms,
+            "alu_roofline": {"bound": "alu", "nominal_flops": fl, "achieved_tflops": fl / (ms * 1e-3) / 1e12,
+                             "peak_tflops": f64_peak, "frac": fl / (ms * 1e-3) / 1e12 / f64_peak,
+                             "peak_source": "fma.rn.f64 rate measured in this run"},
+            "hbm_view": {"bytes": bm, "achieved_gbs": bm / (ms * 1e-3) / 1e9,
+                         "frac": bm / (ms * 1e-3) / 1e9 / hbm_peak},
+            "kernels": {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1)} for k, v in prof.items()}}
+
+
 def extra_measurements(fg, torch, u32, op, barrier) -> dict:
     """FP64 apply of the same workload, and solves at a 1e-10 relative residual:
     1D (n = 1023, p = 1, alpha in {0.5, 1, 1.5}) mixed and plain FP64, the 3D
     solve (255^3, p = 1) mixed at alpha in {0.4, 1.6} and plain FP64 at 0.4, the
     256-problem batch and the served stream."""
     out = {}
-    u64 = u32.double()
-    y64 = torch.empty_like(u64)
-    op.apply(u64, out=y64)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(3):
-        op.apply(u64, out=y64)
-    barrier()
-    t = (time.perf_counter() - t0) / 3
-    out["apply_f64"] = {"value": NFIELDS * NSIDE * NSIDE / t / 1e9, "unit": "GDOF/s", "ms_per_step": 1e3 * t}
-    del u64, y64
     solves = {}
     for alpha in (0.5, 1.0, 1.5):
         op1 = fg.FracOp(1, 1023, alpha, degree=1)
@@ -620,7 +668,7 @@ def served_measurement(fg, torch, barrier, seconds: float = 2.0) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true")

@@ -308,6 +308,19 @@ int frac_profile_enable(int on);
 int frac_profile_read(frac_kernel_stat* out, int cap, int* count, int reset);
 
 /*
+ * frac_profile_alu_peak -- measures the arithmetic rate of the current GPU for
+ * the rooflines of the library's ALU-bound kernels (a measurement aid, not
+ * part of the paper's method): a grid of 8 blocks of 256 threads per SM runs 8
+ * independent fused multiply-add chains per thread; `kind` 0 = FP32 (fma.rn.f32),
+ * 1 = FP64 (fma.rn.f64), 2 = FP32 in pairs (fma.rn.f32x2, two FMAs per
+ * instruction).  *tflops receives 2 flops per FMA over the best of three timed
+ * launches (CUDA events on `stream`); the call synchronises `stream` and
+ * allocates (and frees) a small result buffer.  Errors: FRAC_EINVAL (kind
+ * unknown, NULL tflops), FRAC_ENOMEM, FRAC_ECUDA.
+ */
+int frac_profile_alu_peak(int kind, double* tflops, void* stream);
+
+/*
  * Solve engine: many solves in flight at once (continuous batching).  Each
  * submitted job advances through its own stream from a fixed pool: d = 1 as
  * one whole-solve block, d >= 2 as FP32 CG chunks (replayed CUDA graphs) and

@@ -123,6 +123,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.frac_profile_enable.restype = i32
     lib.frac_profile_read.argtypes = [ctypes.c_void_p, i32, ctypes.POINTER(ctypes.c_int), i32]
     lib.frac_profile_read.restype = i32
+    lib.frac_profile_alu_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
+    lib.frac_profile_alu_peak.restype = i32
     _lib = lib
     return lib
 
@@ -139,6 +141,17 @@ def _detail() -> str:
         return load().frac_error_detail().decode()
     except Exception:
         return ""
+
+
+def alu_peak_tflops(kind: str, stream=None) -> float:
+    """Measured arithmetic rate of the current GPU (frac_profile_alu_peak): kind "f32"
+    (fma.rn.f32), "f64" (fma.rn.f64) or "f32x2" (paired FP32 FMAs), in TFLOP/s."""
+    code = {"f32": 0, "f64": 1, "f32x2": 2}[kind]
+    v = ctypes.c_double()
+    s = load().frac_profile_alu_peak(code, ctypes.byref(v), _stream(stream))
+    if s != 0:
+        raise FracError(s, "frac_profile_alu_peak")
+    return v.value
 
 
 def declared_entry_points() -> list[str]:
