@@ -62,8 +62,8 @@ enum frac_precision {
 /* One discretized problem on Omega = prod_i (lo_i, lo_i + (n_i + 1) h). */
 typedef struct frac_problem {
   int32_t d;        /* dimension, 1..3                                             */
-  int32_t degree;   /* Lagrange basis degree p: 0 (constant), 1 (linear), 2 (quadratic);
-                       3 and 4 for d = 1 (higher degrees: origin rules of order 6, 8);
+  int32_t degree;   /* Lagrange basis degree p: 0 (constant), 1 (linear), 2 (quadratic),
+                       3 and 4 (higher degrees: origin rules of order 6, 8), any d;
                        p >= 2 needs N_i = n_i + 1 divisible by p                     */
   double alpha;     /* fractional power, 0 < alpha < 2                             */
   double h;         /* mesh size, > 0                                              */
@@ -98,8 +98,7 @@ typedef struct frac_op_info_t {
  * coefficient a_0 = -sum_{k!=0} 2^{d-z(k)} a_k - 2^d F_d, and the symbol
  * Lambda = -c_{d,alpha} DFT_M(circulant embedding of a) (real, even), kept in
  * FP64 and FP32.  *out receives a new op (release with frac_op_free).
- * Errors: FRAC_EINVAL (d not in 1..3, alpha not in (0,2), degree not in 0..2
- * (0..4 for d = 1), n_i < 1, N_i not divisible by a degree >= 2, h <= 0 or
+ * Errors: FRAC_EINVAL (d not in 1..3, alpha not in (0,2), degree not in 0..4, n_i < 1, N_i not divisible by a degree >= 2, h <= 0 or
  * non-finite, gamma not 0 and not in (alpha, 2],
  * lambda < 0 or non-finite, out == NULL), FRAC_ENOTSUP (M beyond the FFT
  * sizes of this build, per axis: M_i <= 8192 for d = 1, <= 2048 for d = 2,
@@ -224,6 +223,46 @@ typedef struct frac_solve_info {
 int frac_boundary(const frac_op* op, const double* g_ext, const double* far, double* b, void* stream);
 
 /*
+ * Far field of exterior data g (the far_i of frac_boundary: the second integral of
+ * Eq. (L2), over Upsilon_+^c, summed over the 2^d reflections), on the device.  The
+ * C ABI cannot carry the function g, so the caller evaluates it between two calls
+ * (reverse communication): frac_far_points lists the points at which g is needed,
+ * the caller writes g there into a device buffer, frac_far_sum forms the weighted
+ * sums.  The rule is the same for every grid point: Q nodes xi_q in R_+^d outside
+ * [0, L]^d and weights w_q with
+ *     far_i ~ sum_{m in {0,1}^d} sum_q w_q g(x_i + s(m) o xi_q),  s(m)_k = -1 if bit k of m is set,
+ * from the split of the region into the d pyramids where coordinate k is the largest,
+ * xi = rho (1, s) (coordinate k first), rho = L / t with t by an nr-point Gauss-Jacobi
+ * rule for the weight t^{alpha-1} and each s_j by an ns-point Gauss-Legendre rule on
+ * [0, 1]; w_q carries L^{-alpha}, |(1, s)|^{-d-alpha} and e^{-lambda rho |(1, s)|}.
+ * Q = d ns^{d-1} nr.  The error falls quickly with nr and ns for g smooth and bounded
+ * outside the domain (96 and 48 give about 1e-14 for the paper's exterior data).
+ *
+ * frac_far_nodes (host only, no device work): the rule for dimension d, power alpha,
+ * tempering lambda and cube side L = N h (N = max_i n_i + 1, the side of the
+ * generator's cube): *count = Q; xi (Q*d doubles, node-major, coordinate k along
+ * axis x^(k+1)) and w (Q doubles) are filled when not NULL.  Errors: FRAC_EINVAL (d
+ * not in 1..3, alpha not in (0,2), lambda < 0 or not finite, L <= 0, nr or ns not in
+ * 1..512, NULL count), FRAC_ECUDA (an eigenvalue iteration that did not converge).
+ *
+ * frac_far_points: for the `count` grid points first..first+count-1 (flat index,
+ * axis x^(1) fastest as in u), writes the points x_i + s(m) o xi_q to pts (device,
+ * count * 2^d * nq * d doubles, ordered (point, m, q, coordinate)); x_i has coordinate
+ * lo[k] + (j_k + 1) h along axis x^(k+1), lo (host, d doubles) the domain's lower
+ * corner.  xi: the nq nodes of frac_far_nodes in a device buffer.
+ * frac_far_sum: far[p] = sum_m sum_q w[q] g[(p 2^d + m) nq + q] for p < count
+ * (device buffers; far receives count doubles, in the order of the points).
+ * Both are stream-ordered on `stream`.  Errors: FRAC_EINVAL (NULL pointers, nq < 1,
+ * points outside the grid, host buffers or buffers of another device).
+ */
+int frac_far_nodes(int32_t d, double alpha, double lambda, double L, int32_t nr, int32_t ns, double* xi,
+                   double* w, int64_t* count);
+int frac_far_points(const frac_op* op, const double* lo, const double* xi, int64_t nq, int64_t first,
+                    int64_t count, double* pts, void* stream);
+int frac_far_sum(const frac_op* op, const double* w, int64_t nq, const double* g, int64_t count, double* far,
+                 void* stream);
+
+/*
  * frac_solve -- solve A u = f - g for one right-hand side (the fractional
  * Poisson problem Eq. (Poisson)-(BC); Example 3.2.3 asks for an FFT-based
  * fast solver without naming one).  A is symmetric positive
@@ -252,6 +291,9 @@ int frac_solve(const frac_op* op, const double* f, const double* g, double* u,
  *     block each, as chosen by an autotuner that times each FFT length once
  *     per device (the first batch with a new length pays for that timing);
  *   - the others share a solve engine (frac_engine_*) on several streams.
+ * The 1D and 2D launches (with their uploads) are captured into one CUDA graph
+ * and launched once on `stream`; the autotuner's first timings run before the
+ * capture.  `stream` must not be capturing when this is called.
  * Errors as frac_solve, per problem in info[i].status; the return value is the
  * first nonzero status or FRAC_OK.  Synchronizes `stream` before returning.
  */

@@ -125,6 +125,13 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.frac_profile_read.restype = i32
     lib.frac_profile_alu_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
     lib.frac_profile_alu_peak.restype = i32
+    lib.frac_far_nodes.argtypes = [i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, i32, i32, vp, vp,
+                                   ctypes.POINTER(ctypes.c_int64)]
+    lib.frac_far_nodes.restype = i32
+    lib.frac_far_points.argtypes = [vp, vp, vp, i64, i64, i64, vp, vp]
+    lib.frac_far_points.restype = i32
+    lib.frac_far_sum.argtypes = [vp, vp, i64, vp, i64, vp, vp]
+    lib.frac_far_sum.restype = i32
     _lib = lib
     return lib
 
@@ -141,6 +148,22 @@ def _detail() -> str:
         return load().frac_error_detail().decode()
     except Exception:
         return ""
+
+
+def far_nodes(d: int, alpha: float, lam: float, L: float, nr: int = 96, ns: int = 48):
+    """The library's far-field rule (frac_far_nodes, host only): nodes xi (Q, d), column k
+    along axis x^(k+1), and weights w (Q,)."""
+    lib = load()
+    cnt = ctypes.c_int64()
+    s = lib.frac_far_nodes(d, alpha, lam, L, nr, ns, None, None, ctypes.byref(cnt))
+    if s != 0:
+        raise FracError(s, "frac_far_nodes")
+    xi = np.empty((cnt.value, d))
+    w = np.empty(cnt.value)
+    s = lib.frac_far_nodes(d, alpha, lam, L, nr, ns, xi.ctypes.data, w.ctypes.data, ctypes.byref(cnt))
+    if s != 0:
+        raise FracError(s, "frac_far_nodes")
+    return xi, w
 
 
 def alu_peak_tflops(kind: str, stream=None) -> float:
@@ -311,6 +334,41 @@ class FracOp:
         """Array shape of the extended samples of ``boundary``: n_i + 2N per axis, N = max n_i + 1."""
         N = max(self.ns) + 1
         return tuple(m + 2 * N for m in self.shape)
+
+    def far_field(self, g, lo=-1.0, nr: int = 96, ns: int = 48, max_values: int = 1 << 25, stream=None):
+        """The far part of the boundary vector for exterior data g (frac_far_points and
+        frac_far_sum): g is called on float64 device tensors of shape (P, d) whose column k
+        is the coordinate along array axis k (the last array axis is x^(1)) and returns P
+        values; lo is the domain's lower corner (a number or one value per array axis).
+        Grid points are taken in chunks of at most max_values evaluation points.  Returns
+        a float64 device tensor of the grid's shape."""
+        import torch
+        d = self.d
+        los = [float(lo)] * d if np.isscalar(lo) else [float(v) for v in lo]
+        L = (max(self.ns) + 1) * self.h
+        xi_h, w_h = far_nodes(d, self.alpha, self.lam, L, nr, ns)
+        nq = len(w_h)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        xi = torch.tensor(xi_h, device=dev)
+        w = torch.tensor(w_h, device=dev)
+        far = torch.empty(self.shape, dtype=torch.float64, device=dev)
+        per = (1 << d) * nq
+        chunk = max(1, max_values // per)
+        lo_c = (ctypes.c_double * 3)(*(list(reversed(los)) + [0.0] * (3 - d)))  # per axis x^(k+1)
+        st = _stream(stream)
+        flat = far.view(-1)
+        for first in range(0, self.nd, chunk):
+            cnt = min(chunk, self.nd - first)
+            pts = torch.empty((cnt * per, d), dtype=torch.float64, device=dev)
+            s = self._lib.frac_far_points(self._h, lo_c, xi.data_ptr(), nq, first, cnt, pts.data_ptr(), st)
+            if s != 0:
+                raise FracError(s, "frac_far_points")
+            gv = g(pts.flip(1)).to(torch.float64).contiguous()  # columns in array-axis order
+            s = self._lib.frac_far_sum(self._h, w.data_ptr(), nq, gv.data_ptr(), cnt, flat[first:].data_ptr(), st)
+            if s != 0:
+                raise FracError(s, "frac_far_sum")
+            del pts, gv
+        return far
 
     def boundary(self, g_ext, far=None, out=None, stream=None):
         """b = -c (near + far) (frac_boundary): g_ext holds g at the grid points e in

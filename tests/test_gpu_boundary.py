@@ -197,3 +197,87 @@ def test_table_3_2_2_with_gpu_boundary_and_solve(al, hh):
     err = np.max(np.abs(u.cpu().numpy() - np.exp(-r2)))
     assert abs(err - ref) <= 0.51 * _unit(ref), (err, ref)
     op.close()
+
+
+# ---------------------------------------------------------------------------
+# The far field on the device (frac_far_points / frac_far_sum): the caller only
+# evaluates g at the listed points.
+# ---------------------------------------------------------------------------
+
+def _g_pair(kind):
+    """(numpy g for the oracle, torch g for the library); column k = array axis k."""
+    if kind == "lorentz":
+        return (lambda P: 1.0 / (1.0 + np.sum(P * P, axis=-1)),
+                lambda P: 1.0 / (1.0 + (P * P).sum(dim=1)))
+    if kind == "gauss":
+        return (lambda P: np.exp(-np.sum(P * P, axis=-1)),
+                lambda P: torch.exp(-(P * P).sum(dim=1)))
+    # not symmetric in the axes: shows that coordinates reach g in array-axis order
+    if kind == "skew1":
+        return (lambda P: np.exp(-0.5 * P[..., 0] ** 2) * (1.0 + 0.3 * np.sin(P[..., 0])),
+                lambda P: torch.exp(-0.5 * P[:, 0] ** 2) * (1.0 + 0.3 * torch.sin(P[:, 0])))
+    return (lambda P: np.exp(-P[..., 0] ** 2 - 2.0 * P[..., 1] ** 2) * (1.0 + 0.3 * P[..., 0]),
+            lambda P: torch.exp(-P[:, 0] ** 2 - 2.0 * P[:, 1] ** 2) * (1.0 + 0.3 * P[:, 0]))
+
+
+@pytest.mark.parametrize("d,ns,alpha,lam,kind", [
+    (1, (63,), 0.5, 0.0, "lorentz"), (1, (255,), 1.5, 0.0, "skew1"), (1, (31,), 1.1, 0.7, "lorentz"),
+    (2, (15, 15), 1.9, 0.0, "gauss"), (2, (31, 31), 0.7, 0.0, "skew2"), (2, (15, 23), 1.2, 0.4, "skew2"),
+])
+def test_far_field_matches_oracle(d, ns, alpha, lam, kind):
+    """Element by element against the oracle's far field (its own loops over reflections,
+    pyramids and nodes) to 1e-12 of the largest value; rectangular grids, tempered kernels
+    and exterior data that distinguish the axes included."""
+    import paper_2103_03658_gb300 as fg
+    g_np, g_t = _g_pair(kind)
+    op = fg.FracOp(d, ns if d > 1 else ns[0], alpha, degree=1, lam=lam)
+    far = op.far_field(g_t).cpu().numpy()
+    N = max(ns) + 1
+    shape = tuple(reversed(ns))
+    ref = O.boundary_far(d, N, 2.0 / N, alpha, g_np, lam, shape=shape)
+    assert np.max(np.abs(far - ref)) <= 1e-12 * np.max(np.abs(ref)), np.max(np.abs(far - ref))
+    op.close()
+
+
+@pytest.mark.parametrize("al,p,hh", [(0.5, 1, 0.0625), (1.7, 2, 0.015625), (1.0, 0, 0.03125), (1.0, 2, 0.00390625)])
+def test_table_3_1_3_all_on_gpu(al, p, hh):
+    """Table 3-1-3 with no oracle input: near and far field of g = 1/(1+x^2) and the apply
+    all from the library (the exact (-Delta)^{alpha/2} u is the comparison value)."""
+    G = _table("table_3_1_3")
+    ref = G["entries"][str(al)][str(p)][G["h"].index(hh)]
+    N = int(round(2 / hh))
+    n = N - 1
+    op = _op(1, n, p, al)
+    _, g_t = _g_pair("lorentz")
+    far = op.far_field(g_t)
+    ext = torch.tensor(synth.extended_points(1, n), device="cuda")
+    b = op.boundary(g_t(ext.reshape(-1, 1)).reshape(ext.shape[:-1]).contiguous(), far=far).cpu().numpy()
+    x = synth.interior_grid(n)
+    Au = op.apply(torch.tensor(1.0 / (1.0 + x * x), device="cuda")).cpu().numpy()
+    err = np.max(np.abs(Au + b - O.fl_lorentzian_1d(al, x)))
+    floor = max(8 * np.finfo(np.float64).eps * op.info()["norm_bound"], 5e-13)
+    assert abs(err - ref) <= 0.51 * _unit(ref) + floor, (err, ref)
+    op.close()
+
+
+@pytest.mark.parametrize("al", [0.7, 1.9])
+@pytest.mark.parametrize("hh", [0.125, 0.03125])
+def test_table_3_2_2_all_on_gpu(al, hh):
+    """Table 3-2-2 with no oracle input in the solve path: g = exp(-|x|^2) near and far
+    field, boundary vector and mixed-precision solve all from the library."""
+    G = _table("table_3_2_2")
+    ref = G["entries"][str(al)][G["h"].index(hh)]
+    N = int(round(2 / hh))
+    n = N - 1
+    op = _op(2, n, 1, al)
+    _, g_t = _g_pair("gauss")
+    ext = torch.tensor(synth.extended_points(2, n), device="cuda")
+    gext = g_t(ext.reshape(-1, 2)).reshape(ext.shape[:-1]).contiguous()
+    b = op.boundary(gext, far=op.far_field(g_t))
+    r2 = synth.radius2(2, n)
+    f = torch.tensor(O.fl_gaussian(2, al, r2), device="cuda")
+    u, info = op.solve(f, rtol=1e-12, precision="mixed", g=b)
+    assert info["status"] == 0 and info["rel_resid"] <= 1e-12
+    err = np.max(np.abs(u.cpu().numpy() - np.exp(-r2)))
+    assert abs(err - ref) <= 0.51 * _unit(ref), (err, ref)
+    op.close()
