@@ -451,3 +451,58 @@ def test_origin_element_against_polar_quadrature(d, p, alpha, lam, k):
     w = O.weights(d, N, 2.0 / N, alpha, p, lam)
     ref = _origin_node_polar(d, N, alpha, lam, p, k)
     assert abs(w[tuple(k)] - ref) <= 1e-12 * abs(ref), (w[tuple(k)], ref)
+
+
+def _origin_node_mp(d, N, alpha, p, k, dps=34):
+    """omega_k for a node of the origin element of degree p (gamma = 2, lambda = 0) in dps-digit
+    arithmetic: the Duffy split of [0, p h]^d with the radial integral of every monomial in
+    closed form and the angles by mpmath quadrature (the monomial expansion cancels by up to
+    p^{p d} relative, harmless at 34 digits)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = dps
+    h = mpmath.mpf(2) / N
+    H, al = p * h, mpmath.mpf(alpha)
+
+    def lag(j):
+        c = [mpmath.mpf(1)]
+        for t in range(p + 1):
+            if t != j:
+                nc = [mpmath.mpf(0)] * (len(c) + 1)
+                for i, v in enumerate(c):
+                    nc[i] += v * (-t * h)
+                    nc[i + 1] += v
+                c = [v / ((j - t) * h) for v in nc]
+        return c
+
+    polys = [lag(int(ki)) for ki in k]
+    tot = mpmath.mpf(0)
+    for lead in range(d):
+        def f(*s, lead=lead):
+            it = iter(s)
+            coords = [mpmath.mpf(1) if j == lead else next(it) for j in range(d)]
+            P = [mpmath.mpf(1)]
+            for j in range(d):
+                pj = [polys[j][m] * coords[j] ** m for m in range(p + 1)]
+                nP = [mpmath.mpf(0)] * (len(P) + p)
+                for a_, va in enumerate(P):
+                    for b_, vb in enumerate(pj):
+                        nP[a_ + b_] += va * vb
+                P = nP
+            rad = sum(v * H ** (2 - al + m) / (2 - al + m) for m, v in enumerate(P))
+            return rad * mpmath.sqrt(1 + sum(x * x for x in s)) ** (-(d + al - 2))
+        tot += mpmath.quad(f, *([[0, 1]] * (d - 1)))
+    return float(tot)
+
+
+@pytest.mark.parametrize("d,p,alpha,k,tol", [
+    (2, 3, 0.6, (2, 1), 1e-14), (2, 4, 1.3, (3, 1), 1e-14), (2, 4, 1.9, (0, 0), 1e-14), (3, 4, 0.7, (3, 2, 1), 1e-13),
+])
+def test_origin_element_high_degree_against_high_precision(d, p, alpha, k, tol):
+    """Degrees 3, 4: the origin element's weights (the oracle cuts it into cells of side h
+    and integrates the one at the origin by the Duffy split) against the Duffy split of the
+    whole element carried out in 34-digit arithmetic; in FP64 that whole-element expansion
+    loses up to 6e-11 to cancellation, the cell split does not."""
+    N = 4 * p
+    w = O.weights(d, N, 2.0 / N, alpha, p)
+    ref = _origin_node_mp(d, N, alpha, p, k)
+    assert abs(w[k] - ref) <= tol * abs(ref), (w[k], ref)
