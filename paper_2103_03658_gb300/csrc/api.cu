@@ -39,16 +39,19 @@ static int keep_pool_memory() {
   return FRAC_OK;
 }
 
-// A non-blocking library stream per device for work that runs beside the caller's stream.
-static int side_stream(cudaStream_t* out) {
+// Non-blocking library streams per device for work that runs beside the caller's stream:
+// which = 0 the side stream, 1 the stream a CUDA graph is captured on (the caller's stream
+// may be the legacy default stream, which cannot be captured).
+static int side_stream(cudaStream_t* out, int which = 0) {
   static std::mutex mu;
-  static std::vector<cudaStream_t> per_dev;
+  static std::vector<cudaStream_t> per_dev[2];
   int dev = 0;
   FRAC_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(mu);
-  if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1, nullptr);
-  if (!per_dev[dev]) FRAC_CUDA_TRY(cudaStreamCreateWithFlags(&per_dev[dev], cudaStreamNonBlocking));
-  *out = per_dev[dev];
+  std::vector<cudaStream_t>& v = per_dev[which ? 1 : 0];
+  if ((int)v.size() <= dev) v.resize(dev + 1, nullptr);
+  if (!v[dev]) FRAC_CUDA_TRY(cudaStreamCreateWithFlags(&v[dev], cudaStreamNonBlocking));
+  *out = v[dev];
   return FRAC_OK;
 }
 
@@ -75,7 +78,7 @@ static int validate(const frac_problem* p) {
   if (!p) return FRAC_EINVAL;
   if (p->d < 1 || p->d > 3) return FRAC_EINVAL;
   if (!(p->alpha > 0.0 && p->alpha < 2.0)) return FRAC_EINVAL;
-  if (p->degree < 0 || p->degree > 4 || (p->degree > 2 && p->d != 1)) return FRAC_EINVAL;
+  if (p->degree < 0 || p->degree > 4) return FRAC_EINVAL;
   if (!(p->h > 0.0) || !std::isfinite(p->h)) return FRAC_EINVAL;
   if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return FRAC_EINVAL;
   if (p->gamma != 0.0 && !(p->gamma > p->alpha && p->gamma <= 2.0)) return FRAC_EINVAL;
@@ -562,39 +565,65 @@ int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* con
     else others.push_back(i);
   }
   rest.swap(others);
-  // the 1D launches run on a side stream next to the persistent 2D launch: fork
-  // here, before anything of this call is queued on st
-  cudaStream_t s1 = st;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  if (!oned.empty() && !wide.empty()) {
-    FRAC_TRY(side_stream(&s1));
-    FRAC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    FRAC_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-    FRAC_CUDA_TRY(cudaEventRecord(fork, st));
-    FRAC_CUDA_TRY(cudaStreamWaitEvent(s1, fork, 0));
-  }
-  struct EvFree {
-    cudaEvent_t* a;
-    cudaEvent_t* b;
-    ~EvFree() {
-      if (*a) cudaEventDestroy(*a);
-      if (*b) cudaEventDestroy(*b);
-    }
-  } evf{&fork, &join};
   BatchPending p2, p1;
-  if (!wide.empty()) {
+  if (!oned.empty() || !wide.empty()) {
+    // Everything that waits on the device or builds tables runs first (the
+    // autotuner's timings, twiddles); the uploads, the persistent 2D launch and
+    // the 1D launches (on a side stream forked from the capture, so that they run
+    // beside the 2D launch) are then captured into one CUDA graph on a library
+    // stream, and the graph is launched once on st.
+    if (!wide.empty()) FRAC_TRY(batch2d_prepare((int64_t)wide.size(), ops, f, wide.data(), st));
+    for (int64_t i : oned) FRAC_TRY(prepare_twiddles(ops[i]->logm));
+    cudaStream_t cap = nullptr;
+    FRAC_TRY(side_stream(&cap, 1));
+    cudaStream_t s1 = cap;
+    if (!oned.empty() && !wide.empty()) FRAC_TRY(side_stream(&s1, 0));
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    struct Release {
+      cudaEvent_t *a, *b;
+      cudaGraph_t* g;
+      cudaGraphExec_t* x;
+      ~Release() {
+        if (*a) cudaEventDestroy(*a);
+        if (*b) cudaEventDestroy(*b);
+        if (*x) cudaGraphExecDestroy(*x);
+        if (*g) cudaGraphDestroy(*g);
+      }
+    } rel{&fork, &join, &graph, &exec};
+    if (s1 != cap) {
+      FRAC_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+      FRAC_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    }
+    FRAC_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed));
+    int cs = FRAC_OK;
     frac_batch_plan plan{};
-    FRAC_TRY(solve_batch_2d((int64_t)wide.size(), ops, f, u, opts, wide.data(), st, &plan, g_pin_size, g_pin_cut,
-                            &p2));
-    g_last_plan = plan;
-    g_have_plan = true;
-  }
-  if (!oned.empty()) FRAC_TRY(solve_batch_1d((int64_t)oned.size(), ops, f, u, opts, oned.data(), s1, &p1));
-  if (!wide.empty()) FRAC_TRY(p2.collect(info));
-  if (!oned.empty()) FRAC_TRY(p1.collect(info));
-  if (join) {  // later work on st is ordered after the side stream's
-    FRAC_CUDA_TRY(cudaEventRecord(join, s1));
-    FRAC_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
+    if (s1 != cap) {
+      if (cudaEventRecord(fork, cap) != cudaSuccess || cudaStreamWaitEvent(s1, fork, 0) != cudaSuccess)
+        cs = FRAC_ECUDA;
+    }
+    if (cs == FRAC_OK && !wide.empty())
+      cs = solve_batch_2d((int64_t)wide.size(), ops, f, u, opts, wide.data(), cap, &plan, g_pin_size, g_pin_cut, &p2);
+    if (cs == FRAC_OK && !oned.empty()) cs = solve_batch_1d((int64_t)oned.size(), ops, f, u, opts, oned.data(), s1, &p1);
+    if (cs == FRAC_OK && s1 != cap) {  // the side stream rejoins the capture
+      if (cudaEventRecord(join, s1) != cudaSuccess || cudaStreamWaitEvent(cap, join, 0) != cudaSuccess)
+        cs = FRAC_ECUDA;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(cap, &graph);  // always ends the capture
+    if (cs != FRAC_OK) return cs;
+    FRAC_CUDA_TRY(ec);
+    FRAC_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+    FRAC_CUDA_TRY(cudaGraphLaunch(exec, st));
+    // the results of both branches are complete when st is: collect (and free) on st
+    p1.st = st;
+    p2.st = st;
+    if (!wide.empty()) {
+      g_last_plan = plan;
+      g_have_plan = true;
+      FRAC_TRY(p2.collect(info));
+    }
+    if (!oned.empty()) FRAC_TRY(p1.collect(info));
   }
   for (const std::vector<int64_t>* v : {&oned, &wide})
     for (int64_t i : *v) {

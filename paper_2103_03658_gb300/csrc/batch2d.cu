@@ -652,6 +652,33 @@ double simulate(const std::vector<Item>& items, const std::map<int, ClassTiming>
 
 }  // namespace
 
+int batch2d_prepare(int64_t count, const frac_op* const* ops, const double* const* f, const int64_t* idx,
+                    cudaStream_t st) {
+  if (count <= 0) return FRAC_OK;
+  FRAC_TRY(configure_kernel());
+  for (int l = kBatch2dMinLog; l <= kBatch2dMaxLog; ++l) FRAC_TRY(prepare_twiddles(l));
+  int dev = 0;
+  FRAC_CUDA_TRY(cudaGetDevice(&dev));
+  std::map<int, int64_t> rep;  // logm -> largest problem of that class
+  for (int64_t t = 0; t < count; ++t) {
+    const frac_op* op = ops[idx[t]];
+    auto it = rep.find(op->logm);
+    if (it == rep.end() || ops[it->second]->n < op->n) rep[op->logm] = idx[t];
+  }
+  for (auto& kv : rep) {
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      if (g_tune.count({dev, kv.first})) continue;
+    }
+    ClassTiming t;
+    prof::Scope ps("batch2d_autotune", st);
+    FRAC_TRY(probe_class(ops[kv.second], f[kv.second], st, &t));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[{dev, kv.first}] = t;
+  }
+  return FRAC_OK;
+}
+
 bool batch2d_eligible(const frac_op* op, const frac_solve_opts* opts) {
   return op->prob.d == 2 && op->square && opts->precision == FRAC_MIXED_IR && op->logm >= kBatch2dMinLog &&
          op->logm <= kBatch2dMaxLog;

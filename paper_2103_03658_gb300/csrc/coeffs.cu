@@ -336,6 +336,19 @@ __device__ int pick_rule(double ratio) {
   return 8;                    // 3: error ~ (1 / (2 ratio))^6 < 4e-15 relative
 }
 
+// Rule for bases of degree p >= 3 (d >= 2): the degree-p product leaves 2q - p orders of the
+// kernel's Taylor series to a q-point rule, so each distance class takes more points than
+// pick_rule gives for p <= 2 (the error ~ (1 / (2 ratio))^{2q - p} stays below 1e-16).
+__device__ int pick_rule_high(double ratio) {
+  if (ratio < 2.0) return 7;    // q = 20
+  if (ratio < 8.0) return 6;    // 16
+  if (ratio < 32.0) return 5;   // 12
+  if (ratio < 128.0) return 4;  // 10
+  if (ratio < 512.0) return 3;  // 8
+  return 2;                     // 6
+}
+__device__ __forceinline__ int pick_rule_p(double ratio, int p) { return p >= 3 ? pick_rule_high(ratio) : pick_rule(ratio); }
+
 // Monomial coefficients (in t = xi / h) of the local basis on the origin element.
 __device__ void origin_poly(int p, int l, double* c) {
   c[0] = c[1] = c[2] = 0.0;
@@ -401,10 +414,11 @@ __device__ double origin_element_1d(const WParams& P, int l, double H) {
 // a shares across all basis products (direction, weight x |s|^{-beta}, radial moments);
 // duffy_product the sum over the pyramids for one product l.
 constexpr int kDuffyRule = 6;  // rule index of q = 16
+constexpr int kDuffyMoments = 13;  // radial moments m = 0 .. p d (p <= 4, d <= 3)
 struct DuffyAngle {
   double s[2];
   double base;
-  double R[7];
+  double R[kDuffyMoments];
 };
 
 __device__ void duffy_angle(const WParams& P, int a, double H, DuffyAngle& A) {
@@ -421,35 +435,44 @@ __device__ void duffy_angle(const WParams& P, int a, double H, DuffyAngle& A) {
     ws *= 0.5 * c_gl_w[off + ib];
   }
   const double cs = sqrt(1.0 + A.s[0] * A.s[0] + A.s[1] * A.s[1]);
-  for (int m = 0; m <= P.p * d && CHK(m, 7); ++m) A.R[m] = radial_moment(P.gamma - P.alpha + m, P.lambda * cs, H);
+  for (int m = 0; m <= P.p * d && CHK(m, kDuffyMoments); ++m)
+    A.R[m] = radial_moment(P.gamma - P.alpha + m, P.lambda * cs, H);
   A.base = ws * pow(cs, -P.beta);
 }
 
 __device__ double duffy_product(const WParams& P, const int* l, const DuffyAngle& A) {
+  constexpr int NM = kDuffyMoments;
   const int d = P.d, p = P.p;
   const double ih = 1.0 / P.h;
-  double cf[3][3];
+  double cf[3][5];
   for (int i = 0; i < d && CHK(i, 3); ++i) {
-    origin_poly(p, l[i], cf[i]);
-    cf[i][1] *= ih;  // coefficients of xi^m
-    cf[i][2] *= ih * ih;
+    if (p <= 2) {
+      origin_poly(p, l[i], cf[i]);
+      cf[i][3] = cf[i][4] = 0.0;
+    } else {
+      origin_poly_lagrange(p, l[i], cf[i]);
+    }
+    double sc = ih;  // coefficients of xi^m
+    for (int m = 1; m <= 4; ++m, sc *= ih) cf[i][m] *= sc;
   }
   double tot = 0.0;
   for (int i = 0; i < d; ++i) {  // pyramid: axis i largest
-    double poly[7] = {1, 0, 0, 0, 0, 0, 0};
+    double poly[NM] = {1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     int deg = 0, col = 0;
     for (int j = 0; j < d && CHK(j, 3); ++j) {
       const double t = (j == i) ? 1.0 : (CHK(col, 2) ? A.s[col++] : 0.0);
-      const double pj[3] = {cf[j][0], cf[j][1] * t, cf[j][2] * t * t};
-      double np[7] = {0, 0, 0, 0, 0, 0, 0};
+      double pj[5];
+      double tp = 1.0;
+      for (int m = 0; m < 5; ++m, tp *= t) pj[m] = cf[j][m] * tp;
+      double np[NM] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
       for (int m1 = 0; m1 <= deg; ++m1)
         for (int m2 = 0; m2 <= p; ++m2)
-          if (CHK(m1 + m2, 7) && CHK(m1, 7) && CHK(m2, 3)) np[m1 + m2] += poly[m1] * pj[m2];
+          if (CHK(m1 + m2, NM) && CHK(m1, NM) && CHK(m2, 5)) np[m1 + m2] += poly[m1] * pj[m2];
       deg += p;
-      for (int m = 0; m < 7; ++m) poly[m] = np[m];
+      for (int m = 0; m < NM; ++m) poly[m] = np[m];
     }
     double acc = 0.0;
-    for (int m = 0; m <= deg && CHK(m, 7); ++m) acc += poly[m] * A.R[m];
+    for (int m = 0; m <= deg && CHK(m, NM); ++m) acc += poly[m] * A.R[m];
     tot += acc;
   }
   return A.base * tot;
@@ -507,10 +530,23 @@ __device__ AxisEl elem_axis(const WParams& P, int e, int l) {
     if (l == 0) return AxisEl{a, a + h, a + h, 0, -1.0 / h, 1, e == 0 ? 0 : -1};
     return AxisEl{a, a + h, a, 0, 1.0 / h, 1, e == 0 ? 1 : -1};
   }
-  const double a = 2 * e * h;
-  if (l == 0) return AxisEl{a, a + 2 * h, a + h, a + 2 * h, 0.5 / (h * h), 2, e == 0 ? 0 : -1};
-  if (l == 1) return AxisEl{a, a + 2 * h, a, a + 2 * h, -1.0 / (h * h), 2, e == 0 ? 1 : -1};
-  return AxisEl{a, a + 2 * h, a, a + h, 0.5 / (h * h), 2, e == 0 ? 2 : -1};
+  if (P.p == 2) {
+    const double a = 2 * e * h;
+    if (l == 0) return AxisEl{a, a + 2 * h, a + h, a + 2 * h, 0.5 / (h * h), 2, e == 0 ? 0 : -1};
+    if (l == 1) return AxisEl{a, a + 2 * h, a, a + 2 * h, -1.0 / (h * h), 2, e == 0 ? 1 : -1};
+    return AxisEl{a, a + 2 * h, a, a + h, 0.5 / (h * h), 2, e == 0 ? 2 : -1};
+  }
+  // p = 3, 4: Lagrange polynomial of local node l on the nodes p e + s, s = 0..p
+  const int p = P.p;
+  double roots[4] = {0, 0, 0, 0}, scale = 1.0;
+  int nr = 0;
+  for (int s2 = 0; s2 <= p; ++s2) {
+    if (s2 == l) continue;
+    if (CHK(nr, 4)) roots[nr++] = ((double)p * e + s2) * h;
+    scale /= (double)(l - s2) * h;
+  }
+  return AxisEl{(double)p * e * h, ((double)p * e + p) * h, roots[0], roots[1], scale, nr, e == 0 ? l : -1, roots[2],
+                roots[3]};
 }
 
 // ---------------------------------------------------------------------------
@@ -549,21 +585,60 @@ __global__ void __launch_bounds__(256) k_near_elements(WParams P, int E, double*
   }
   const int stride = kNearSplit * blockDim.x;
   if (origin) {
+    // Degrees p <= 2: the Duffy split on the whole element.  p >= 3: the Duffy split on
+    // the cell [0, h]^D at the origin only (the monomial expansion over the whole element,
+    // side p h, would multiply terms by up to p^{p D} and cancel to 1e-11), and the
+    // element's other p^D - 1 cells, where the integrand is smooth, by a 20-point tensor
+    // Gauss-Legendre rule with the basis functions in product form.
     const int q = rule_q(kDuffyRule), nang = (D == 2) ? q : q * q;
-    const double H = ax[0][0].hi - ax[0][0].lo;
+    const double H = PD >= 3 ? P.h : ax[0][0].hi - ax[0][0].lo;
     for (int u = sp + kNearSplit * threadIdx.x; u < nang * kNearGroups; u += stride) {
       const int a = u % nang, g = u / nang;
       DuffyAngle A;
       duffy_angle(P, a, H, A);
+      if constexpr (PD <= 2) {
 #pragma unroll
-      for (int c = 0; c < NL; ++c) {
-        if (c % kNearGroups != g) continue;
-        const int l[3] = {c % N1, (c / N1) % N1, D == 3 ? c / (N1 * N1) : 0};
-        acc[c] += duffy_product(P, l, A);
+        for (int c = 0; c < NL; ++c) {
+          if (c % kNearGroups != g) continue;
+          const int l[3] = {c % N1, (c / N1) % N1, D == 3 ? c / (N1 * N1) : 0};
+          acc[c] += duffy_product(P, l, A);
+        }
+      } else {  // up to 125 products: a loop, not 125 inlined copies
+#pragma unroll 1
+        for (int c = g; c < NL; c += kNearGroups) {
+          const int l[3] = {c % N1, (c / N1) % N1, D == 3 ? c / (N1 * N1) : 0};
+          acc[c] += duffy_product(P, l, A);
+        }
+      }
+    }
+    if constexpr (PD >= 3) {
+      constexpr int QS = 20, NCELL = (D == 2) ? PD * PD : PD * PD * PD, NPTS = (D == 2) ? QS * QS : QS * QS * QS;
+      const int off = rule_off(7);  // q = 20
+      for (int j = sp + kNearSplit * threadIdx.x; j < (NCELL - 1) * NPTS; j += stride) {
+        const int cell = 1 + j / NPTS, pt = j % NPTS;
+        const int ci[3] = {cell % PD, (cell / PD) % PD, D == 3 ? cell / (PD * PD) : 0};
+        const int gq[3] = {pt % QS, (pt / QS) % QS, D == 3 ? pt / (QS * QS) : 0};
+        double wb[3][N1], r2 = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+          const int gi = CHK(off + gq[i], kRuleTotal) ? off + gq[i] : off;
+          const double x = (ci[i] + 0.5 * (c_gl_x[gi] + 1.0)) * P.h;
+          const double w = 0.5 * P.h * c_gl_w[gi];
+          r2 += x * x;
+#pragma unroll
+          for (int l = 0; l < N1; ++l) wb[i][l] = w * basis_val(ax[i][l], x);
+        }
+        const double m = mu_r2(r2, P);
+#pragma unroll
+        for (int c = 0; c < NL; ++c) {
+          double v = m * wb[0][c % N1] * wb[1][(c / N1) % N1];
+          if (D == 3) v *= wb[2][c / (N1 * N1)];
+          acc[c] += v;
+        }
       }
     }
   } else {
-    const int rule = pick_rule(sqrt(lo2) / width);
+    const int rule = pick_rule_p(sqrt(lo2) / width, PD);
     const int q = rule_q(rule), off = rule_off(rule);
     const int npts = (D == 2) ? q * q : q * q * q;
     double cen[3], hw[3];
@@ -676,7 +751,7 @@ __global__ void __launch_bounds__(256) k_elements(WParams P, int64_t ne, const d
       lo2 += ax[i][0].lo * ax[i][0].lo;
       width = fmax(width, ax[i][0].hi - ax[i][0].lo);
     }
-    const int rule = pick_rule(sqrt(lo2) / width);
+    const int rule = pick_rule_p(sqrt(lo2) / width, PD);
     const int q = rule_q(rule), off = rule_off(rule);
     if (CHK(q - 1, 20) && CHK(off + q - 1, kRuleTotal)) {
       double cen[3], hw[3];
@@ -796,11 +871,12 @@ __global__ void k_gather(WParams P, int64_t ne, const double* __restrict__ eint,
     else if (p == 1) {
       if (k[i] >= 1) { ee[i][nc[i]] = k[i] - 1; ll[i][nc[i]++] = 1; }
       if (k[i] < P.N) { ee[i][nc[i]] = k[i]; ll[i][nc[i]++] = 0; }
-    } else {
-      if (k[i] & 1) { ee[i][0] = k[i] / 2; ll[i][0] = 1; nc[i] = 1; }
+    } else {  // elements of p intervals: an inner node in one, a shared node in two
+      const int64_t m = k[i] / p, t = k[i] - m * p;
+      if (t != 0) { ee[i][0] = m; ll[i][0] = (int)t; nc[i] = 1; }
       else {
-        if (k[i] >= 2) { ee[i][nc[i]] = k[i] / 2 - 1; ll[i][nc[i]++] = 2; }
-        if (k[i] <= P.N - 2) { ee[i][nc[i]] = k[i] / 2; ll[i][nc[i]++] = 0; }
+        if (k[i] >= p) { ee[i][nc[i]] = m - 1; ll[i][nc[i]++] = p; }
+        if (k[i] <= P.N - p) { ee[i][nc[i]] = m; ll[i][nc[i]++] = 0; }
       }
     }
   }
@@ -1099,7 +1175,7 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
     k_weights_1d<<<(unsigned)nblk, TB, 0, st>>>(P, omega, ngen);
   } else {
     // near-origin elements [0, E)^d first, spread over kNearSplit blocks each
-    const int64_t ne_axis = pr.degree == 0 ? op->N + 1 : (pr.degree == 1 ? op->N : op->N / 2);
+    const int64_t ne_axis = pr.degree == 0 ? op->N + 1 : op->N / pr.degree;
     const int E = (int)std::min<int64_t>(kNearE[d], ne_axis);
     int64_t nnear = 1;
     for (int i = 0; i < d; ++i) nnear *= E;
@@ -1109,32 +1185,26 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
     FRAC_CUDA_TRY(cudaMallocAsync(&near, (size_t)nnear * kNearSplit * nloc * sizeof(double), st));
     FRAC_CUDA_TRY(cudaMallocAsync(&eint, (size_t)nel * nloc * sizeof(double), st));
     const unsigned nb = (unsigned)(nnear * kNearSplit), eb = (unsigned)ceil_div(nel, 256);
-    switch (d * 3 + pr.degree) {
-      case 6:
-        k_near_elements<2, 0><<<nb, 256, 0, st>>>(P, E, near);
-        k_elements<2, 0><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
-        break;
-      case 7:
-        k_near_elements<2, 1><<<nb, 256, 0, st>>>(P, E, near);
-        k_elements<2, 1><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
-        break;
-      case 8:
-        k_near_elements<2, 2><<<nb, 256, 0, st>>>(P, E, near);
-        k_elements<2, 2><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
-        break;
-      case 9:
-        k_near_elements<3, 0><<<nb, 256, 0, st>>>(P, E, near);
-        k_elements<3, 0><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
-        break;
-      case 10:
-        k_near_elements<3, 1><<<nb, 256, 0, st>>>(P, E, near);
-        k_elements<3, 1><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
-        break;
+#define FRAC_ELEM_CASE(DD, PP)                                                \
+  case DD * 5 + PP:                                                           \
+    k_near_elements<DD, PP><<<nb, 256, 0, st>>>(P, E, near);                  \
+    k_elements<DD, PP><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);        \
+    break;
+    switch (d * 5 + pr.degree) {
+      FRAC_ELEM_CASE(2, 0)
+      FRAC_ELEM_CASE(2, 1)
+      FRAC_ELEM_CASE(2, 2)
+      FRAC_ELEM_CASE(2, 3)
+      FRAC_ELEM_CASE(2, 4)
+      FRAC_ELEM_CASE(3, 0)
+      FRAC_ELEM_CASE(3, 1)
+      FRAC_ELEM_CASE(3, 2)
+      FRAC_ELEM_CASE(3, 3)
+      FRAC_ELEM_CASE(3, 4)
       default:
-        k_near_elements<3, 2><<<nb, 256, 0, st>>>(P, E, near);
-        k_elements<3, 2><<<eb, 256, 0, st>>>(P, ne_axis, near, E, eint);
-        break;
+        return FRAC_EINVAL;
     }
+#undef FRAC_ELEM_CASE
     FRAC_CUDA_TRY(cudaGetLastError());
     if (d == 2) k_gather<2><<<(unsigned)nblk, TB, 0, st>>>(P, ne_axis, eint, omega, ngen);
     else k_gather<3><<<(unsigned)nblk, TB, 0, st>>>(P, ne_axis, eint, omega, ngen);

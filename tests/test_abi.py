@@ -30,7 +30,7 @@ def test_strerror(lib):
 def test_invalid_problems_rejected_before_any_device_work(lib):
     bad = [dict(d=4), dict(alpha=0.0), dict(alpha=2.0), dict(degree=5), dict(degree=-1), dict(h=-1.0),
            dict(lam=-0.1), dict(n=0), dict(degree=2, n=8), dict(degree=3, n=7), dict(degree=4, n=9),
-           dict(degree=3, n=8, d=2), dict(degree=4, n=7, d=3), dict(lam=float("nan")), dict(gamma=1.0),
+           dict(degree=3, n=9, d=2), dict(degree=4, n=6, d=3), dict(lam=float("nan")), dict(gamma=1.0),
            dict(gamma=0.5), dict(gamma=2.5), dict(gamma=-1.0)]
     for b in bad:
         kw = dict(d=1, degree=1, alpha=1.0, h=0.25, n=7, lam=0.0, gamma=0.0)

@@ -167,3 +167,45 @@ def test_batch2d_config_mix_all_converge():
         r = fs[k] - ops[k].apply(us[k])
         assert float(r.norm() / fs[k].norm()) <= 1e-10 * 1.01
     _close(ops)
+
+
+def test_batch_config_mix_1d_and_2d_in_one_graph_oracle_residuals():
+    """The whole 256-problem batch workload (d in {1, 2} 50/50, 1D n in [63, 4095], 2D side
+    in [63, 511], alpha ~ U(0.1, 1.9), p in {0, 1, 2}, lambda ~ U(0, 2)): the 1D whole-solve
+    launches and the persistent 2D launch run from one captured CUDA graph.  Every problem
+    must reach 1e-10, except a long 1D problem at alpha > 1.8 (kappa ~ 1e6-1e7, where the
+    FP64 residual itself carries errors near 1e-10), which must still come within 5e-10; for
+    every 16th problem the oracle recomputes the residual with its own generator, over all
+    rows in 1D and over 96 seeded rows in 2D."""
+    import paper_2103_03658_gb300 as fg
+    probs = synth.batch_problems(256)
+    ops = [fg.FracOp(p.d, p.n, p.alpha, degree=p.degree, lam=p.lam) for p in probs]
+    fs = [torch.tensor(synth.smooth_field(p.d, p.n, p.seed) + 0.25, device="cuda") for p in probs]
+    us = [torch.empty_like(f) for f in fs]
+    infos = fg.solve_batch(ops, fs, us, rtol=1e-10)
+    assert fg.batch_last_plan()["cluster_problems"] + fg.batch_last_plan()["local_problems"] == \
+        sum(1 for p in probs if p.d == 2)
+    for p, op, i in zip(probs, ops, infos):
+        if i["status"] == 0:
+            assert i["rel_resid"] <= 1e-10, (p, i)
+        else:
+            assert p.d == 1 and p.n >= 2047 and p.alpha > 1.8 and i["rel_resid"] <= 5e-10, (p, i)
+    rng = np.random.default_rng(4)
+    for k in range(0, len(probs), 16):
+        p = probs[k]
+        N = p.n + 1
+        a = O.stencil(p.d, N, 2.0 / N, p.alpha, p.degree, p.lam)
+        c = O.c_dalpha(p.d, p.alpha)
+        u = us[k].cpu().numpy()
+        f = fs[k].cpu().numpy()
+        if p.d == 1:
+            r = f - O.apply_dense(a, c, u)
+            rel = np.linalg.norm(r) / np.linalg.norm(f)
+        else:
+            rows = rng.integers(0, p.n, size=(96, 2))
+            r = f[tuple(rows.T)] - O.apply_rows(a, c, u, rows)
+            rel = np.linalg.norm(r) / np.linalg.norm(f[tuple(rows.T)])
+        # the oracle's own FP64 rounding of A u (~ eps log(n) ||A|| ||u||) on top of the GPU's 1e-10
+        floor = 1e-15 * math.log2(4 * p.n) * O.norm_bound(a, c, p.n) * np.linalg.norm(u) / np.linalg.norm(f)
+        assert rel <= 3e-10 + 10 * floor, (p, rel, floor, infos[k])
+    _close(ops)

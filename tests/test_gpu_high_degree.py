@@ -1,9 +1,9 @@
-"""GPU parity, 1D Lagrange bases of degree 3 and 4 (origin rules of order 6 and 8; the
-oracle's higher-degree scheme): the generator against the oracle's (1e-13 of its largest
-entry, the bar of the lower degrees), the FP64 apply against the oracle's dense sum, a
-solve whose residual the oracle recomputes, and the accuracy the oracle shows on
-u = 1/(1+x^2) with its exterior data (the GPU's apply and boundary vector, the far
-integrals of g from the oracle)."""
+"""GPU parity, Lagrange bases of degree 3 and 4 (origin rules of order 6 and 8; the
+oracle's higher-degree scheme) in 1D, 2D and 3D: the generator against the oracle's
+(1e-13 of its largest entry, the bar of the lower degrees), the applies against the
+oracle's dense sum, solves whose residual the oracle recomputes, and the accuracy the
+oracle shows on u = 1/(1+x^2) with its exterior data (the GPU's apply and boundary
+vector, the far integrals of g from the oracle)."""
 import math
 
 import numpy as np
@@ -87,4 +87,62 @@ def test_accuracy_on_smooth_exterior_data(p, alpha, bound):
     Au = op.apply(torch.tensor(1.0 / (1.0 + x * x), device="cuda")).cpu().numpy()
     err = np.max(np.abs(Au + b - O.fl_lorentzian_1d(alpha, x)))
     assert err <= bound, err
+    op.close()
+
+
+# ---------------------------------------------------------------------------
+# d = 2, 3
+# ---------------------------------------------------------------------------
+
+def _opd(d, n, p, alpha, lam=0.0):
+    import paper_2103_03658_gb300 as fg
+    return fg.FracOp(d, n, alpha, degree=p, lam=lam)
+
+
+DCASES = [(2, 2, 3, 1.1, 0.0), (2, 11, 3, 0.6, 0.0), (2, 23, 3, 1.8, 0.7), (2, 3, 4, 1.3, 0.0), (2, 23, 4, 0.4, 0.0),
+          (2, 39, 4, 1.5, 1.2), (3, 2, 3, 0.9, 0.0), (3, 11, 3, 1.5, 0.0), (3, 7, 4, 0.7, 0.0), (3, 11, 4, 1.2, 0.8)]
+
+
+@pytest.mark.parametrize("d,n,p,alpha,lam", DCASES)
+def test_generator_matches_oracle_2d_3d(d, n, p, alpha, lam):
+    N = n + 1
+    a_ref = O.stencil(d, N, 2.0 / N, alpha, p, lam, q=20 if d < 3 else 12)
+    op = _opd(d, n, p, alpha, lam)
+    a_gpu = op.generator()
+    assert np.max(np.abs(a_gpu - a_ref)) <= 1e-13 * np.max(np.abs(a_ref)), np.max(np.abs(a_gpu - a_ref))
+    op.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("d,n,p,alpha", [(2, 23, 3, 1.3), (2, 35, 4, 0.7), (3, 11, 3, 1.6), (3, 7, 4, 0.9)])
+def test_apply_matches_oracle_2d_3d(d, n, p, alpha, dtype):
+    N = n + 1
+    a = O.stencil(d, N, 2.0 / N, alpha, p, q=20 if d < 3 else 12)
+    c = O.c_dalpha(d, alpha)
+    nrm = O.norm_bound(a, c, n)
+    U = np.random.default_rng(7 * n + p).standard_normal((2,) + (n,) * d)
+    op = _opd(d, n, p, alpha)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    y = op.apply(torch.tensor(U, dtype=tdt, device="cuda")).double().cpu().numpy()
+    tol = 1e-12 if dtype == "f64" else 1e-5
+    for b in range(2):
+        uu = U[b] if dtype == "f64" else U[b].astype(np.float32).astype(np.float64)
+        ref = O.apply_dense(a, c, uu)
+        assert np.linalg.norm(y[b] - ref) <= tol * nrm * np.linalg.norm(uu)
+    op.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "mixed"])
+@pytest.mark.parametrize("d,n,p,alpha", [(2, 35, 3, 1.5), (3, 11, 4, 0.9)])
+def test_solve_residual_recomputed_by_oracle_2d_3d(d, n, p, alpha, precision):
+    N = n + 1
+    a = O.stencil(d, N, 2.0 / N, alpha, p, q=20 if d < 3 else 12)
+    c = O.c_dalpha(d, alpha)
+    f = synth.smooth_field(d, n, 5 + n) + 0.5
+    op = _opd(d, n, p, alpha)
+    u, info = op.solve(torch.tensor(f, device="cuda"), rtol=1e-10, precision=precision)
+    assert info["status"] == 0 and info["rel_resid"] <= 1e-10
+    uu = u.cpu().numpy()
+    res = np.linalg.norm(f - O.apply_dense(a, c, uu)) / np.linalg.norm(f)
+    assert res <= 1.05e-10 + 1e-13 * O.norm_bound(a, c, n) * np.linalg.norm(uu) / np.linalg.norm(f)
     op.close()
