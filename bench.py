@@ -165,7 +165,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -259,7 +259,11 @@ def apply_model_bytes(fields: int) -> float:
 # launch / fields in it) of the kernels as they stand, from one ncu capture of
 # the 65-field apply (profiles/apply2d_1023_65fields_dram.md), scaled to a launch
 # by the fields it processes.  Remove an entry when its kernel changes.
-DRAM_TRAFFIC_PER_FIELD = {}
+DRAM_TRAFFIC_PER_FIELD = {
+    "cols_sym2_f32_M2048": (551.107584e6 + 492.779264e6) / 65,
+    "rows_fwd_f32_M2048": (274.032384e6 + 493.253120e6) / 65,
+    "rows_inv_f32_M2048": (546.925568e6 + 242.039552e6) / 65,
+}
 
 
 def max_over_ranks(x: float, dist, device: str = "cuda") -> float:
@@ -625,6 +629,46 @@ def _serve(fg, reqs, barrier, realtime=True, precision="mixed") -> tuple:
     return res, wall, srv
 
 
+def _oracle_residual(args):
+    """The oracle's relative residual ||f - A u|| / ||f|| of one served result, A built
+    from the oracle's own generator: over every row in 1D, over 64 seeded rows otherwise."""
+    from oracle import frac_oracle as O
+    d, n, alpha, degree, lam, f, u = args
+    N = n + 1
+    a = O.stencil(d, N, 2.0 / N, alpha, degree, lam, q=20 if d < 3 else 12)
+    c = O.c_dalpha(d, alpha)
+    if d == 1:
+        r = f - O.apply_dense(a, c, u)
+        return float(np.linalg.norm(r) / np.linalg.norm(f))
+    rows = np.random.default_rng(n).integers(0, n, size=(64, d))
+    fr = f[tuple(rows.T)]
+    return float(np.linalg.norm(fr - O.apply_rows(a, c, u, rows)) / np.linalg.norm(fr))
+
+
+def oracle_sample(reqs, res, every: int = 50, max_nd: int = 63 ** 3) -> dict:
+    """Every `every`-th served request (the next one whose oracle generator takes seconds,
+    n^d <= 63^3, when the due one is larger) checked by the oracle on the host cores."""
+    import multiprocessing as mp
+    byid = {r.rid: r for r in res}
+    picks, due = [], 0
+    for q in reqs:
+        if q.rid >= due and q.n ** q.d <= max_nd and q.rid in byid:
+            picks.append(q)
+            due = q.rid + every
+    jobs = [(q.d, q.n, q.alpha, q.degree, q.lam, np.asarray(q.f, dtype=np.float64),
+             np.asarray(byid[q.rid].u, dtype=np.float64)) for q in picks]
+    if not jobs:
+        return {"checked": 0}
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        errs = pool.map(_oracle_residual, jobs)
+    by_d = {}
+    for q, e in zip(picks, errs):
+        by_d.setdefault(str(q.d), []).append(e)
+    return {"checked": len(jobs), "every": every, "max_rel_resid": max(errs), "median_rel_resid": float(np.median(errs)),
+            "max_rel_resid_by_d": {k: max(v) for k, v in sorted(by_d.items())},
+            "rows": "all rows (1D), 64 seeded rows (2D, 3D)"}
+
+
 def served_measurement(fg, torch, barrier, seconds: float = 2.0) -> dict:
     """Poisson arrivals at 200 req/s for `seconds`: d in {1, 2, 3} (0.4/0.4/0.2),
     1D/2D sizes as in the batch mix, 3D side in {63, 127, 255}, alpha ~ U(0.1, 1.9),
@@ -647,7 +691,9 @@ def served_measurement(fg, torch, barrier, seconds: float = 2.0) -> dict:
         for r, q in zip(res, reqs):
             by_d.setdefault(q.d, []).append(r.latency_s)
         rate_done = len(res) / wall
+        check = oracle_sample(reqs, res)
         out[name] = {"requests": len(reqs), "window_s": seconds, "rate_per_s": 200.0, "converged": ok,
+                     "oracle_check": check,
                      "solves_per_s": rate_done, "wall_s": wall,
                      "rho": (200.0 / rate_done) if wall > 1.2 * seconds else None,
                      "p50_ms": 1e3 * serve.percentile(lat, 50), "p99_ms": 1e3 * serve.percentile(lat, 99),
@@ -668,7 +714,7 @@ def served_measurement(fg, torch, barrier, seconds: float = 2.0) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true")
@@ -679,6 +725,10 @@ def main():
                     help="run only the 256-problem batch measurement and print its JSON (profiler captures)")
     ap.add_argument("--boundary-only", action="store_true",
                     help="run only the frac_boundary timings and print their JSON (profiler captures)")
+    ap.add_argument("--served-only", action="store_true",
+                    help="run only the served-stream measurement and print its JSON")
+    ap.add_argument("--served-seconds", type=float, default=2.0,
+                    help="arrival window of the served stream (the configured stream is 60 s)")
     ap.add_argument("--applies-only", action="store_true",
                     help="run only the 1D and 3D single-vector apply timings and print their JSON (profiler captures)")
     args = ap.parse_args()
@@ -693,6 +743,11 @@ def main():
         import torch
         import paper_2103_03658_gb300 as fg
         print(json.dumps(boundary_measurement(fg, torch, torch.cuda.synchronize)), flush=True)
+        return
+    if args.served_only:
+        import torch
+        import paper_2103_03658_gb300 as fg
+        print(json.dumps(served_measurement(fg, torch, torch.cuda.synchronize, args.served_seconds)), flush=True)
         return
     if args.batch_only:
         import torch

@@ -90,3 +90,42 @@ def test_served_stream_each_result_same_as_alone():
         u1 = u1.cpu().numpy()
         assert np.linalg.norm(np.asarray(r.u) - u1) <= 1e-8 * np.linalg.norm(u1)
         op.close()
+
+
+def test_served_results_checked_by_oracle():
+    """Served results against the oracle: a stream of mixed requests (1D up to n = 4095,
+    2D sides up to 255, 3D sides 15 and 31) through the serving loop, and for every other
+    request the oracle's relative residual ||f - A u|| / ||f|| with its own generator (all
+    rows in 1D and for n^d <= 4096, 64 seeded rows otherwise) within the solve tolerance
+    plus the oracle's own FP64 rounding of A u."""
+    import math
+
+    from paper_2103_03658_gb300 import serve
+    from oracle import frac_oracle as O
+    probs = synth.served_problems(20, seed=29, sides3d=(15, 31))
+    reqs = []
+    for i, pb in enumerate(probs):
+        n = min(pb.n, 255) if pb.d == 2 else pb.n
+        if pb.degree == 2 and n % 2 == 0:
+            n += 1
+        reqs.append(serve.Request(i, pb.d, n, pb.alpha, pb.degree, pb.lam,
+                                  synth.smooth_field(pb.d, n, pb.seed) + 0.2, 0.0))
+    srv = serve.Server(hbm_budget=20e9, nstreams=8)
+    res = srv.run(reqs, realtime=False)
+    srv.close()
+    rng = np.random.default_rng(3)
+    for r, q in list(zip(res, reqs))[::2]:
+        assert r.info["status"] == 0 and r.info["rel_resid"] <= 1e-10
+        N = q.n + 1
+        a = O.stencil(q.d, N, 2.0 / N, q.alpha, q.degree, q.lam, q=20 if q.d < 3 else 12)
+        c = O.c_dalpha(q.d, q.alpha)
+        u = np.asarray(r.u, dtype=np.float64)
+        f = q.f
+        if q.d == 1 or q.n ** q.d <= 4096:
+            rel = np.linalg.norm(f - O.apply_dense(a, c, u)) / np.linalg.norm(f)
+        else:
+            rows = rng.integers(0, q.n, size=(64, q.d))
+            fr = f[tuple(rows.T)]
+            rel = np.linalg.norm(fr - O.apply_rows(a, c, u, rows)) / np.linalg.norm(fr)
+        floor = 1e-15 * math.log2(4 * q.n) * O.norm_bound(a, c, q.n) * np.linalg.norm(u) / np.linalg.norm(f)
+        assert rel <= 3e-10 + 10 * floor, (q.d, q.n, q.alpha, q.degree, q.lam, rel, floor)
