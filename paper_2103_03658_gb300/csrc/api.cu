@@ -177,13 +177,14 @@ int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
   }
   op->c = c_dalpha(d, prob->alpha);
   cudaGetDevice(&op->device);
-  op->device_bytes = op->ngen * sizeof(double) + 2 * op->nsym * (sizeof(double) + sizeof(float));
+  op->nsym_alloc = d == 2 ? (op->Ka[0] + 3) / 4 * 4 * op->Ka[1] : op->nsym;
+  op->device_bytes = op->ngen * sizeof(double) + 2 * op->nsym_alloc * (sizeof(double) + sizeof(float));
   int s = FRAC_OK;
   if (cudaMalloc(&op->a, op->ngen * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&op->lam64, op->nsym * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&op->lam32, op->nsym * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&op->pinv64, op->nsym * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&op->pinv32, op->nsym * sizeof(float)) != cudaSuccess) {
+      cudaMalloc(&op->lam64, op->nsym_alloc * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&op->lam32, op->nsym_alloc * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&op->pinv64, op->nsym_alloc * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&op->pinv32, op->nsym_alloc * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     s = FRAC_ENOMEM;
   }

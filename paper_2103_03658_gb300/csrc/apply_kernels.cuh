@@ -444,7 +444,7 @@ static int pipeline(const frac_op* op, const T* lam, const void* in, void* out, 
   if (d == 2) {
     const int64_t nrows = batch * n2;
     FRAC_TRY((rows_fwd_any<T, FK>(op->logma[0], in, W1, n1, n2, nrows, (int)KB, st, fwd)));
-    ColArgs A{(int)n2, (int)K1, (int)KB, KB, batch};
+    ColArgs A{(int)n2, (int)K1, (int)KB, KB, batch, 0, 0, (int)op->Ka[1]};
     FRAC_TRY((cols_any<T, SYM2, ODD>(op->logma[1], W1, W1, A, batch, lam, st, cgst)));
     FRAC_TRY((rows_inv_any<T, IK>(op->logma[0], W1, out, n1, n2, nrows, (int)KB, st, inv)));
     return FRAC_OK;

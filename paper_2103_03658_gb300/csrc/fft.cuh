@@ -146,7 +146,7 @@ __device__ __forceinline__ void dft_zin(C* x) {
 
 // One Stockham pass on this thread's line; tl = thread index within the line.
 template <typename C, int LOGM, int P, bool INV>
-__device__ __forceinline__ void pass(C* __restrict__ buf, int tl, const C* __restrict__ tw) {
+__device__ __forceinline__ void pass(C* buf, int tl, const C* __restrict__ tw) {
   constexpr int M = 1 << LOGM;
   constexpr int RB = pass_bits(LOGM, P);
   constexpr int R = 1 << RB;
@@ -194,6 +194,12 @@ __device__ __forceinline__ void pass(C* __restrict__ buf, int tl, const C* __res
 // either end.  The caller must not touch `buf` between the entry __syncthreads
 // and the return.
 //
+// The line buffer `buf` is shared memory that other threads write between the
+// barriers of a pass; it must not be declared __restrict__: a restrict-qualified
+// pointer lets the compiler assume that the barrier does not change what it points
+// to and move accesses across it (inlined into the persistent batch kernel, that
+// produced wrong transforms for M = 32).
+//
 // Zero-padded transforms: ZIN states that entries M/2 .. M-1 of the input are
 // zero (v[e] for e >= E/2 is not read); ZOUT that only outputs 0 .. M/2-1 are
 // wanted (v[e] for e >= E/2 is left undefined).  A convolution of n <= M/2
@@ -202,7 +208,7 @@ __device__ __forceinline__ void pass(C* __restrict__ buf, int tl, const C* __res
 // ---------------------------------------------------------------------------
 
 template <typename C, int LOGM, int P, bool INV, bool ZIN, bool ZOUT, int SH>
-__device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
+__device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* buf, int tl, const C* __restrict__ tw) {
   constexpr int M = 1 << LOGM;
   constexpr int NP = npasses(LOGM);
   constexpr int RB = pass_bits(LOGM, P);
@@ -288,7 +294,7 @@ __device__ __forceinline__ void reg_pass(C (&v)[elems(LOGM)], C* __restrict__ bu
 }
 
 template <typename C, int LOGM, bool INV, bool ZIN, bool ZOUT, int SH, int P = 0>
-__device__ __forceinline__ void reg_passes(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
+__device__ __forceinline__ void reg_passes(C (&v)[elems(LOGM)], C* buf, int tl, const C* __restrict__ tw) {
   if constexpr (P < npasses(LOGM)) {
     reg_pass<C, LOGM, P, INV, ZIN, ZOUT, SH>(v, buf, tl, tw);
     reg_passes<C, LOGM, INV, ZIN, ZOUT, SH, P + 1>(v, buf, tl, tw);
@@ -299,13 +305,13 @@ __device__ __forceinline__ void reg_passes(C (&v)[elems(LOGM)], C* __restrict__ 
 // buffer, used only when there is more than one pass: line_stride(LOGM)
 // entries with SH = 4, line_stride_tile(LOGM) with SH = tile_shift(LOGM).
 template <typename C, int LOGM, bool INV, bool ZIN = false, bool ZOUT = false, int SH = 4>
-__device__ __forceinline__ void fft_reg(C (&v)[elems(LOGM)], C* __restrict__ buf, int tl, const C* __restrict__ tw) {
+__device__ __forceinline__ void fft_reg(C (&v)[elems(LOGM)], C* buf, int tl, const C* __restrict__ tw) {
   if constexpr (npasses(LOGM) > 1) __syncthreads();  // earlier users of buf are done
   reg_passes<C, LOGM, INV, ZIN, ZOUT, SH>(v, buf, tl, tw);
 }
 
 template <typename C, int LOGM, bool INV, int P = 0>
-__device__ __forceinline__ void run(C* __restrict__ buf, int tl, const C* __restrict__ tw) {
+__device__ __forceinline__ void run(C* buf, int tl, const C* __restrict__ tw) {
   if constexpr (P < npasses(LOGM)) {
     pass<C, LOGM, P, INV>(buf, tl, tw);
     run<C, LOGM, INV, P + 1>(buf, tl, tw);

@@ -212,7 +212,8 @@ struct ColArgs {
   int64_t tiles;     // column tiles per slab
   int64_t nb;        // batch (fields)
   int nz = 0;        // d = 3: z extent n_3 (slabs (b, j3) of W1; rows j3 of a W2 column block)
-  int My = 0, Ky = 0;  // d = 3: y FFT length M_2 and its symbol extent K_2 = M_2/2+1
+  int My = 0, Ky = 0;  // d = 3: y FFT length M_2 and its symbol extent K_2 = M_2/2+1;
+                       // SYM2: Ky = K_2, the symbol's rows (the symbol is stored in column tiles)
 };
 
 template <typename T, int LOGM, int MODE, bool ODD = false>
@@ -275,8 +276,10 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
   constexpr int SH = tile_shift(LOGM);
   if (MODE != YINV) fft_reg<C, LOGM, false, !ODD, false, SH>(v, buf, tl, tw);
   if (MODE == SYM2 || MODE == ZSYM) {
-    const T* lrow = (MODE == SYM2) ? lam + k1 : lam + (int64_t)k2r * K + k1;
-    const int64_t kstride = (MODE == SYM2) ? K : (int64_t)A.Ky * K;
+    // SYM2: the d = 2 symbol in column tiles, entry (kr, k1) at (k1 / B) K_2 B + kr B + k1 % B, so
+    // that the B lanes of a row read one contiguous run; ZSYM: entry (k3r, k2r, k1) plain
+    const T* lrow = (MODE == SYM2) ? lam + (int64_t)tile * A.Ky * B + cl : lam + (int64_t)k2r * K + k1;
+    const int64_t kstride = (MODE == SYM2) ? B : (int64_t)A.Ky * K;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = tl + e * TPL;
