@@ -102,10 +102,11 @@ __device__ double group_sum(double v, const Group& g, double* red, double* slots
 
 // One problem on one group (cluster or CTA).  The three steps of the
 // refinement are separate (non-inlined) functions, so the FP32 CG loop gets
-// its own register allocation instead of sharing one with the FP64 passes;
-// and inlined into the kernel, the 2^5-point instantiation computed a wrong
-// inverse row pass (the same source as a separate function, or in a separate
-// kernel, is exact), so nothing of it is inlined there.
+// its own register allocation instead of sharing one with the FP64 passes.
+// (Inlined, they once computed a wrong inverse row pass at M = 32: the FFT's
+// shared line buffer was a __restrict__ parameter, which let the compiler move
+// its accesses across the block barriers; the buffer is no longer restrict and
+// the inlined build is exact.)
 struct Ctx {
   const B2Prob* P;
   const B2Slot* S;
@@ -152,16 +153,21 @@ struct Solver {
     return group_sum(v, c.g, c.red, c.slots, c.parity);
   }
 
-  // ||f||^2, and u = 0 unless it is the initial guess
+  // ||f||^2, and u = 0 unless it is the initial guess; with u = 0 the first residual is f
+  // itself (R64 = F), which spares an FP64 apply
   static __device__ __noinline__ double start(Ctx& c) {
     const double* F = c.P->f;
     double* U = c.P->u;
+    double* R64 = c.S->r64;
     const bool zero = !c.P->use_x0;
     double ff = 0.0;
     for_own(c, [&](int64_t k) {
       const double fv = F[k];
       ff += fv * fv;
-      if (zero) U[k] = 0.0;
+      if (zero) {
+        U[k] = 0.0;
+        R64[k] = fv;
+      }
     });
     return gsum(c, ff);
   }
@@ -179,7 +185,7 @@ struct Solver {
                                  pair_of(c, i), rb, tl);
     c.g.sync();
     {
-      const ColArgs A{n, K, KB64, KB64, 1};
+      const ColArgs A{n, K, KB64, KB64, 1, 0, 0, K};
       const int ts = tid / (2 * TPL), w = tid % (2 * TPL);
       const int cr = (KB64 + c.g.G * TPR64 - 1) / (c.g.G * TPR64);
       for (int i = 0; i < cr; ++i)
@@ -212,7 +218,7 @@ struct Solver {
                                       pair_of(c, i), rb, tl);
     c.g.sync();
     {
-      const ColArgs A{n, K, KB32, KB32, 1};
+      const ColArgs A{n, K, KB32, KB32, 1, 0, 0, K};
       const int ts = tid / (4 * TPL), w = tid % (4 * TPL);
       const int cr = (KB32 + c.g.G * TPR32 - 1) / (c.g.G * TPR32);
       for (int i = 0; i < cr; ++i)
@@ -243,7 +249,7 @@ struct Solver {
     float* Q = c.S->q;
     float2* W = static_cast<float2*>(c.S->W);
     float2* rb = reinterpret_cast<float2*>(c.smem) + (tid / TPL) * LS;
-    const ColArgs A{n, K, KB32, KB32, 1};
+    const ColArgs A{n, K, KB32, KB32, 1, 0, 0, K};
     const int ts = tid / (4 * TPL), w = tid % (4 * TPL);
     const int cr = (KB32 + c.g.G * TPR32 - 1) / (c.g.G * TPR32);
     const double sc = 1.0 / sqrt(rn2);
@@ -313,7 +319,7 @@ struct Solver {
     int iters = 0, outer = 0, status = FRAC_OK;
     double rn2 = 0.0;
     if (fn2 != 0.0) {
-      rn2 = residual(c);
+      rn2 = c.P->use_x0 ? residual(c) : fn2;  // u = 0: R64 = f, set by start()
       double prev = INFINITY;
       while (rn2 > tol2 && iters < c.P->max_iter && outer < 100) {
         iters = inner(c, rn2, iters);

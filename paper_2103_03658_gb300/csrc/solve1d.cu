@@ -149,6 +149,15 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
     }
     return block_allsum<TPL>(s, red);
   };
+  // the first residual when u starts at 0: f itself (no FP64 convolution)
+  auto from_f = [&](double (&r)[E]) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int x = tl + e * TPL;
+      r[e] = (e < E / 2 && x < n) ? F[x] : 0.0;
+    }
+    return fn2;
+  };
   const double tol2 = T.rtol * T.rtol * fn2;
   double rn2 = 0.0;
 
@@ -158,7 +167,7 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
     // FP64 CG (preconditioned when T.pcg), restarted from the true residual if
     // the recursive one drifts
     double r[E], p[E];
-    rn2 = residual(r);
+    rn2 = T.use_x0 ? residual(r) : from_f(r);
     // rz = r.z with z = P r (pcg) or z = r; the new direction p = z + beta p
     auto precond_rz = [&]() -> double {
       precond_line<double, LOGM>(buf64, n, T.pinv64, tw64, [&](int e, int) { return r[e]; });
@@ -221,15 +230,15 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
     const double inner2 = T.inner_tol * T.inner_tol;
     float x[E], r[E], p[E];
     // residual in FP64, then scaled to unit norm in FP32 for the next inner solve
-    auto refresh = [&]() {
+    auto refresh = [&](bool zero_u) {
       double r64[E];
-      const double nn = residual(r64);
+      const double nn = zero_u ? from_f(r64) : residual(r64);
       const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
 #pragma unroll
       for (int e = 0; e < E; ++e) r[e] = (float)(r64[e] * sc);
       return nn;
     };
-    rn2 = refresh();
+    rn2 = refresh(!T.use_x0);
     double prev = INFINITY;
     auto precond_rz = [&]() -> double {
       precond_line<float, LOGM>(buf32, n, T.pinv32, tw32, [&](int e, int) { return r[e]; });
@@ -294,7 +303,7 @@ k_solve1d(const Solve1dTask* __restrict__ tasks, int ntasks, const float2* __res
         const int xx = tl + e * TPL;
         if (xx < n) U[xx] += sc * (double)x[e];
       }
-      rn2 = refresh();
+      rn2 = refresh(false);
       ++outer;
       if (!(rn2 < prev) && outer > 3) break;  // refinement stagnated
       prev = rn2;
