@@ -130,7 +130,8 @@ class Server:
     loop keeps admitting and polling while coefficients are computed."""
 
     def __init__(self, hbm_budget: float = 150e9, nstreams: int = 16, precision: str = "mixed",
-                 rtol: float = 1e-10, op_cache_bytes: float = 8e9, build_workers: int = 2):
+                 rtol: float = 1e-10, op_cache_bytes: float = 8e9, build_workers: int = 2,
+                 max_builds: int = 8):
         from concurrent.futures import ThreadPoolExecutor
         self.engine = Engine(nstreams)
         self.cache = OpCache(int(op_cache_bytes))
@@ -140,6 +141,9 @@ class Server:
         self.pool = PinnedPool()
         self.builder = ThreadPoolExecutor(max_workers=build_workers) if build_workers else None
         self.building = {}
+        # operators built ahead of admission hold device memory outside the cache: at most
+        # max_builds of them (queued, running or finished) at a time
+        self.max_builds = max_builds
 
     def close(self):
         if self.builder:
@@ -167,7 +171,8 @@ class Server:
             return self.cache.get(r.d, r.n, r.alpha, r.degree, r.lam, in_use)
         fut = self.building.get(key)
         if fut is None:
-            self.building[key] = self.builder.submit(self._build, key)
+            if len(self.building) < self.max_builds:
+                self.building[key] = self.builder.submit(self._build, key)
             return None
         if not fut.done():
             return None

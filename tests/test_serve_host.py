@@ -116,3 +116,36 @@ def test_background_operator_builds(fakes, monkeypatch):
     srv.close()
     assert [r.rid for r in res] == list(range(16))
     assert srv.cache.misses == 3 and srv.cache.hits == 13
+
+
+def test_operators_built_ahead_are_bounded(fakes, monkeypatch):
+    """A backlog of requests with distinct operators must not build all of them ahead of
+    admission (each built operator holds device memory outside the cache): at most
+    max_builds are pending or finished-but-unadmitted at any time, and every request is
+    still served once."""
+    import threading
+    import time as _t
+    live = {"now": 0, "peak": 0}
+    lock = threading.Lock()
+
+    class CountingOp(FakeOp):
+        def __init__(self, *a, **k):
+            _t.sleep(0.002)
+            super().__init__(*a, **k)
+
+    orig_build = serve.Server._build
+
+    def counting_build(self, key):
+        with lock:
+            live["now"] = len(self.building)
+            live["peak"] = max(live["peak"], live["now"])
+        return orig_build(self, key)
+
+    monkeypatch.setattr(serve, "FracOp", CountingOp)
+    monkeypatch.setattr(serve.Server, "_build", counting_build)
+    srv = serve.Server(hbm_budget=1e12, nstreams=4, op_cache_bytes=1e9, build_workers=2, max_builds=3)
+    reqs = _reqs(40, distinct=20)
+    res = srv.run(reqs, realtime=False, device_inputs=True)
+    srv.close()
+    assert [r.rid for r in res] == list(range(40))
+    assert live["peak"] <= 3
