@@ -177,7 +177,7 @@ int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
   }
   op->c = c_dalpha(d, prob->alpha);
   cudaGetDevice(&op->device);
-  op->nsym_alloc = d == 2 ? (op->Ka[0] + 3) / 4 * 4 * op->Ka[1] : op->nsym;
+  op->nsym_alloc = d == 1 ? op->nsym : (op->Ka[0] + 3) / 4 * 4 * op->Ka[1] * (d == 3 ? op->Ka[2] : 1);
   op->device_bytes = op->ngen * sizeof(double) + 2 * op->nsym_alloc * (sizeof(double) + sizeof(float));
   int s = FRAC_OK;
   if (cudaMalloc(&op->a, op->ngen * sizeof(double)) != cudaSuccess ||

@@ -1110,15 +1110,24 @@ __global__ void k_scale_symbol(const double* __restrict__ raw, double* __restric
 // 1 / (stored * s2) with s2 = M^2 (d = 1) or (2 M^d)^2.  Zero where some k_i is
 // 0 or M/2 (the odd extension has no spectrum there); per-block minimum of the
 // stored symbol over the other entries for the positivity check.
-// d = 2: symbol from the plain layout (k2, k1) -> column tiles of B, entry (k2, k1) at
-// (k1 / B) K2 B + k2 B + k1 % B; padding columns k1 >= K1 get 0.
+// Symbols from the plain layout (axis 0 = k1 fastest) -> the column tiles the column
+// passes read, B entries of k1 side by side and the column axis next:
+//   d = 2: entry (k2, k1) at (k1 / B) K2 B + k2 B + k1 % B;
+//   d = 3: entry (k3, k2, k1) at ((k2 KB + k1 / B) K3 + k3) B + k1 % B, KB = ceil(K1 / B).
+// Padding columns k1 >= K1 get 0.  K3 = 1 for d = 2 (then k2 is the column axis).
 template <typename T, int B>
 __global__ void k_tile_symbol(const T* __restrict__ plain, T* __restrict__ tiled, int64_t K1, int64_t K2,
-                              int64_t count) {
+                              int64_t K3, int d, int64_t count) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= count) return;
-  const int64_t c = idx % B, k2 = (idx / B) % K2, t = idx / (B * K2), k1 = t * B + c;
-  tiled[idx] = k1 < K1 ? plain[k2 * K1 + k1] : T(0);
+  const int64_t KB = (K1 + B - 1) / B, c = idx % B;
+  if (d == 2) {
+    const int64_t k2 = (idx / B) % K2, t = idx / (B * K2), k1 = t * B + c;
+    tiled[idx] = k1 < K1 ? plain[k2 * K1 + k1] : T(0);
+  } else {
+    const int64_t k3 = (idx / B) % K3, t = (idx / (B * K3)) % KB, k2 = idx / (B * K3 * KB), k1 = t * B + c;
+    tiled[idx] = k1 < K1 ? plain[(k3 * K2 + k2) * K1 + k1] : T(0);
+  }
 }
 
 __global__ void k_precond_symbol(const double* __restrict__ l64, double* __restrict__ p64, float* __restrict__ p32,
@@ -1287,16 +1296,16 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   std::vector<double> hmin(nb2);
   FRAC_CUDA_TRY(cudaMemcpyAsync(hmin.data(), pmin, nb2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   FRAC_CUDA_TRY(cudaFreeAsync(pmin, st));
-  if (d == 2) {  // the column pass reads the symbols in column tiles (one run per tile row)
-    const int64_t K1 = op->Ka[0], K2 = op->Ka[1];
+  if (d >= 2) {  // the column passes read the symbols in column tiles (one run per tile row)
+    const int64_t K1 = op->Ka[0], K2 = op->Ka[1], K3 = d == 3 ? op->Ka[2] : 1;
     void* tmp = nullptr;
     FRAC_CUDA_TRY(cudaMallocAsync(&tmp, ns * sizeof(double), st));
     auto tile = [&](auto* arr, auto bconst) -> int {
       using T = std::remove_pointer_t<decltype(arr)>;
       constexpr int B = decltype(bconst)::value;
-      const int64_t cnt = (K1 + B - 1) / B * B * K2;
+      const int64_t cnt = (K1 + B - 1) / B * B * K2 * K3;
       FRAC_CUDA_TRY(cudaMemcpyAsync(tmp, arr, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
-      k_tile_symbol<T, B><<<(unsigned)ceil_div(cnt, TB), TB, 0, st>>>((const T*)tmp, arr, K1, K2, cnt);
+      k_tile_symbol<T, B><<<(unsigned)ceil_div(cnt, TB), TB, 0, st>>>((const T*)tmp, arr, K1, K2, K3, d, cnt);
       FRAC_CUDA_TRY(cudaGetLastError());
       return FRAC_OK;
     };

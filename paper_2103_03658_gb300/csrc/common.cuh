@@ -94,10 +94,12 @@ struct frac_op {
   int square;        // n_i equal on every axis
   int64_t nd;        // prod n_i grid values
   int64_t ngen;      // (N + 1)^d generator entries
-  int64_t nsym;      // prod K_i symbol entries, axis 0 fastest (d = 2: stored in column tiles, below)
-  int64_t nsym_alloc;  // entries allocated per symbol array: nsym, or for d = 2 the column tiles
-                       // ceil(K_1 / 4) 4 K_2 (entry (k2, k1) at (k1 / B) K_2 B + k2 B + k1 % B, B = 4 for
-                       // the FP32 arrays and 2 for the FP64 ones; the padding columns hold zeros)
+  int64_t nsym;      // prod K_i symbol entries (d >= 2: stored in column tiles, below)
+  int64_t nsym_alloc;  // entries allocated per symbol array: nsym (d = 1), or the column tiles
+                       // ceil(K_1 / 4) 4 prod_{i>0} K_i: d = 2 entry (k2, k1) at (k1 / B) K_2 B + k2 B +
+                       // k1 % B, d = 3 entry (k3, k2, k1) at ((k2 KB + k1 / B) K_3 + k3) B + k1 % B
+                       // (B = 4 for the FP32 arrays and 2 for the FP64 ones, KB = ceil(K_1 / B);
+                       // the padding columns hold zeros)
   double c;          // c_{d,alpha}
   double a0;
   double far_field;

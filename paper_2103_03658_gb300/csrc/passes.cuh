@@ -276,10 +276,12 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
   constexpr int SH = tile_shift(LOGM);
   if (MODE != YINV) fft_reg<C, LOGM, false, !ODD, false, SH>(v, buf, tl, tw);
   if (MODE == SYM2 || MODE == ZSYM) {
-    // SYM2: the d = 2 symbol in column tiles, entry (kr, k1) at (k1 / B) K_2 B + kr B + k1 % B, so
-    // that the B lanes of a row read one contiguous run; ZSYM: entry (k3r, k2r, k1) plain
-    const T* lrow = (MODE == SYM2) ? lam + (int64_t)tile * A.Ky * B + cl : lam + (int64_t)k2r * K + k1;
-    const int64_t kstride = (MODE == SYM2) ? B : (int64_t)A.Ky * K;
+    // the symbol in column tiles, so that the B lanes of a row read one contiguous run:
+    // SYM2 entry (kr, k1) at (k1 / B) K_2 B + kr B + k1 % B; ZSYM entry (k3r, k2r, k1) at
+    // ((k2r KB + k1 / B) K_3 + k3r) B + k1 % B with K_3 = M / 2 + 1 (this pass's axis)
+    const T* lrow = (MODE == SYM2) ? lam + (int64_t)tile * A.Ky * B + cl
+                                   : lam + ((int64_t)k2r * KB + k1 / B) * (M / 2 + 1) * B + (k1 % B);
+    const int64_t kstride = B;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int k = tl + e * TPL;
