@@ -260,9 +260,9 @@ def apply_model_bytes(fields: int) -> float:
 # the 65-field apply (profiles/apply2d_1023_65fields_dram.md), scaled to a launch
 # by the fields it processes.  Remove an entry when its kernel changes.
 DRAM_TRAFFIC_PER_FIELD = {
-    "rows_fwd_f32_M2048": (274.029824e6 + 492.920576e6) / 65,
-    "cols_sym2_f32_M2048": (551.571456e6 + 487.584768e6) / 65,
-    "rows_inv_f32_M2048": (546.946816e6 + 242.094336e6) / 65,
+    "rows_fwd_f32_M2048": (274.020864e6 + 493.092608e6) / 65,
+    "cols_sym2_f32_M2048": (551.746048e6 + 487.677952e6) / 65,
+    "rows_inv_f32_M2048": (546.918656e6 + 243.917056e6) / 65,
 }
 
 

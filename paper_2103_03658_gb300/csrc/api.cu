@@ -100,7 +100,7 @@ int record_cuda_error(cudaError_t e, const char* file, int line, const char* exp
     if (*c == '/') base = c + 1;
   std::snprintf(g_detail, sizeof(g_detail), "%s:%d %s -> %s (%s)", base, line, expr, cudaGetErrorName(e),
                 cudaGetErrorString(e));
-  return e == cudaErrorMemoryAllocation ? FRAC_ENOMEM : FRAC_ECUDA;
+  return settle(e == cudaErrorMemoryAllocation ? FRAC_ENOMEM : FRAC_ECUDA);
 }
 
 void record_detail(const char* fmt, ...) {
@@ -370,8 +370,30 @@ static int apply_host_pipelined(const frac_op* op, const void* u, void* y, int d
     if (join[i]) cudaEventDestroy(join[i]);
   }
   if (fork) cudaEventDestroy(fork);
-  return s;
+  return settle(s);
 }
+
+// Stream-ordered temporaries of one call, freed on its stream on every return
+// path; a call that has queued copies from or to the caller's host memory (host_io)
+// also waits for its stream before it returns, on an error path too.
+struct Temps {
+  cudaStream_t st;
+  void* p[4] = {};
+  int n = 0;
+  bool host_io = false;
+  template <typename P>
+  int get(P** out, size_t bytes) {
+    void* q = nullptr;
+    FRAC_CUDA_TRY(cudaMallocAsync(&q, bytes, st));
+    p[n++] = q;
+    *out = static_cast<P*>(q);
+    return FRAC_OK;
+  }
+  ~Temps() {
+    for (int i = 0; i < n; ++i) cudaFreeAsync(p[i], st);
+    if (host_io && cudaStreamSynchronize(st) != cudaSuccess) (void)cudaGetLastError();
+  }
+};
 
 // frac_apply (precond = false) and frac_precond (precond = true): device or host buffers.
 static int apply_entry(const frac_op* op, const void* u, void* y, int dtype, int64_t batch, void* stream,
@@ -388,21 +410,20 @@ static int apply_entry(const frac_op* op, const void* u, void* y, int dtype, int
   if ((du && ((uintptr_t)u % es)) || (dy && ((uintptr_t)y % es))) return FRAC_EINVAL;
   if (!du && !dy && batch >= 2 && bytes >= 2 * pipe_chunk_bytes())
     return apply_host_pipelined(op, u, y, dtype, batch, precond, st);
+  Temps tmp{st};
+  tmp.host_io = !du || !dy;
   void* ws = nullptr;
   const size_t wsb = apply_workspace_bytes(op, dtype, batch);
-  if (wsb) FRAC_CUDA_TRY(cudaMallocAsync(&ws, wsb, st));
+  if (wsb) FRAC_TRY(tmp.get(&ws, wsb));
   const void* ud = u;
   void* yd = y;
-  void *tmp_u = nullptr, *tmp_y = nullptr;
   if (!du) {
-    FRAC_CUDA_TRY(cudaMallocAsync(&tmp_u, bytes, st));
-    FRAC_CUDA_TRY(cudaMemcpyAsync(tmp_u, u, bytes, cudaMemcpyHostToDevice, st));
-    ud = tmp_u;
+    void* tu = nullptr;
+    FRAC_TRY(tmp.get(&tu, bytes));
+    FRAC_CUDA_TRY(cudaMemcpyAsync(tu, u, bytes, cudaMemcpyHostToDevice, st));
+    ud = tu;
   }
-  if (!dy) {
-    FRAC_CUDA_TRY(cudaMallocAsync(&tmp_y, bytes, st));
-    yd = tmp_y;
-  }
+  if (!dy) FRAC_TRY(tmp.get(&yd, bytes));
   int s;
   if (precond)
     s = dtype == FRAC_F64 ? precond_t<double>(op, (const double*)ud, (double*)yd, batch, ws, st)
@@ -410,16 +431,15 @@ static int apply_entry(const frac_op* op, const void* u, void* y, int dtype, int
   else
     s = dtype == FRAC_F64 ? apply_t<double>(op, (const double*)ud, (double*)yd, batch, ws, st)
                           : apply_t<float>(op, (const float*)ud, (float*)yd, batch, ws, st);
-  if (s == FRAC_OK && !dy)
-    if (cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = FRAC_ECUDA;
-  if (ws) cudaFreeAsync(ws, st);
-  if (tmp_u) cudaFreeAsync(tmp_u, st);
-  if (tmp_y) cudaFreeAsync(tmp_y, st);
-  if (!du || !dy) {
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (s == FRAC_OK && e != cudaSuccess) s = FRAC_ECUDA;
+  if (s == FRAC_OK && !dy) {
+    const cudaError_t e = cudaMemcpyAsync(y, yd, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = record_cuda_error(e, __FILE__, __LINE__, "cudaMemcpyAsync");
   }
-  return s;
+  if (!du || !dy) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (s == FRAC_OK && e != cudaSuccess) s = record_cuda_error(e, __FILE__, __LINE__, "cudaStreamSynchronize");
+  }
+  return settle(s);
 }
 
 extern "C" {
@@ -441,29 +461,31 @@ int frac_boundary(const frac_op* op, const double* g_ext, const double* far, dou
   for (int i = 0; i < d; ++i) ne *= op->na[i] + 2 * op->N;
   const size_t gbytes = ne * sizeof(double), bbytes = op->nd * sizeof(double);
   const bool dgx = is_device_ptr(g_ext), dfar = far && is_device_ptr(far), db = is_device_ptr(b);
-  double *tg = nullptr, *tfar = nullptr, *tb = nullptr;
-  int s = FRAC_OK;
-  if (!dgx && cudaMallocAsync(&tg, gbytes, st) == cudaSuccess)
-    s = cudaMemcpyAsync(tg, g_ext, gbytes, cudaMemcpyHostToDevice, st) == cudaSuccess ? FRAC_OK : FRAC_ECUDA;
-  else if (!dgx)
-    s = FRAC_ENOMEM;
-  if (s == FRAC_OK && far && !dfar) {
-    if (cudaMallocAsync(&tfar, bbytes, st) != cudaSuccess)
-      s = FRAC_ENOMEM;
-    else if (cudaMemcpyAsync(tfar, far, bbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-      s = FRAC_ECUDA;
+  Temps tmp{st};
+  tmp.host_io = !dgx || (far && !dfar) || !db;
+  const double *gd = g_ext, *fard = far;
+  double* bd = b;
+  if (!dgx) {
+    double* t = nullptr;
+    FRAC_TRY(tmp.get(&t, gbytes));
+    FRAC_CUDA_TRY(cudaMemcpyAsync(t, g_ext, gbytes, cudaMemcpyHostToDevice, st));
+    gd = t;
   }
-  if (s == FRAC_OK && !db && cudaMallocAsync(&tb, bbytes, st) != cudaSuccess) s = FRAC_ENOMEM;
-  if (s == FRAC_OK)
-    s = boundary_device(op, dgx ? g_ext : tg, far ? (dfar ? far : tfar) : nullptr, db ? b : tb, st);
-  if (s == FRAC_OK && !db && cudaMemcpyAsync(b, tb, bbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    s = FRAC_ECUDA;
-  if (tg) cudaFreeAsync(tg, st);
-  if (tfar) cudaFreeAsync(tfar, st);
-  if (tb) cudaFreeAsync(tb, st);
+  if (far && !dfar) {
+    double* t = nullptr;
+    FRAC_TRY(tmp.get(&t, bbytes));
+    FRAC_CUDA_TRY(cudaMemcpyAsync(t, far, bbytes, cudaMemcpyHostToDevice, st));
+    fard = t;
+  }
+  if (!db) FRAC_TRY(tmp.get(&bd, bbytes));
+  int s = boundary_device(op, gd, fard, bd, st);
+  if (s == FRAC_OK && !db) {
+    const cudaError_t e = cudaMemcpyAsync(b, bd, bbytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = record_cuda_error(e, __FILE__, __LINE__, "cudaMemcpyAsync");
+  }
   const cudaError_t e = cudaStreamSynchronize(st);
-  if (s == FRAC_OK && e != cudaSuccess) s = FRAC_ECUDA;
-  return s;
+  if (s == FRAC_OK && e != cudaSuccess) s = record_cuda_error(e, __FILE__, __LINE__, "cudaStreamSynchronize");
+  return settle(s);
 }
 
 int frac_solve(const frac_op* op, const double* f, const double* g, double* u, const frac_solve_opts* opts,
@@ -477,7 +499,6 @@ int frac_solve(const frac_op* op, const double* f, const double* g, double* u, c
   const bool df = is_device_ptr(f), du = is_device_ptr(u), dg = g && is_device_ptr(g);
   const double* fd = f;
   double* ud = u;
-  double *tf = nullptr, *tu = nullptr, *tg = nullptr;
   if (!df) {
     for (int64_t i = 0; i < op->nd; ++i)
       if (!std::isfinite(f[i])) return FRAC_EINVAL;
@@ -486,43 +507,41 @@ int frac_solve(const frac_op* op, const double* f, const double* g, double* u, c
     for (int64_t i = 0; i < op->nd; ++i)
       if (!std::isfinite(g[i])) return FRAC_EINVAL;
   }
+  Temps tmp{st};
+  tmp.host_io = !df || (g && !dg) || !du;
   if (!df || g) {  // device right-hand side: f, or f - g
-    FRAC_CUDA_TRY(cudaMallocAsync(&tf, bytes, st));
+    double* tf = nullptr;
+    FRAC_TRY(tmp.get(&tf, bytes));
     if (!df) FRAC_CUDA_TRY(cudaMemcpyAsync(tf, f, bytes, cudaMemcpyHostToDevice, st));
+    if (g) {
+      const double* gd = g;
+      if (!dg) {
+        double* tg = nullptr;
+        FRAC_TRY(tmp.get(&tg, bytes));
+        FRAC_CUDA_TRY(cudaMemcpyAsync(tg, g, bytes, cudaMemcpyHostToDevice, st));
+        gd = tg;
+      }
+      FRAC_TRY(subtract_device(df ? f : tf, gd, tf, op->nd, st));
+    }
     fd = tf;
   }
-  if (g) {
-    const double* gd = g;
-    if (!dg) {
-      FRAC_CUDA_TRY(cudaMallocAsync(&tg, bytes, st));
-      FRAC_CUDA_TRY(cudaMemcpyAsync(tg, g, bytes, cudaMemcpyHostToDevice, st));
-      gd = tg;
-    }
-    const int s0 = subtract_device(df ? f : tf, gd, tf, op->nd, st);
-    if (tg) cudaFreeAsync(tg, st);
-    if (s0 != FRAC_OK) {
-      cudaFreeAsync(tf, st);
-      return s0;
-    }
-  }
   if (!du) {
-    FRAC_CUDA_TRY(cudaMallocAsync(&tu, bytes, st));
-    if (opts->use_x0) FRAC_CUDA_TRY(cudaMemcpyAsync(tu, u, bytes, cudaMemcpyHostToDevice, st));
-    ud = tu;
+    FRAC_TRY(tmp.get(&ud, bytes));
+    if (opts->use_x0) FRAC_CUDA_TRY(cudaMemcpyAsync(ud, u, bytes, cudaMemcpyHostToDevice, st));
   }
   int s = solve_device(op, fd, ud, opts, info, st);
-  if (s == FRAC_OK && !du)
-    if (cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) s = FRAC_ECUDA;
-  if (tf) cudaFreeAsync(tf, st);
-  if (tu) cudaFreeAsync(tu, st);
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (s == FRAC_OK && e != cudaSuccess) s = FRAC_ECUDA;
-  if (s == FRAC_OK && std::isnan(info->rel_resid)) {
+  if (s == FRAC_OK && !du) {
+    const cudaError_t e = cudaMemcpyAsync(u, ud, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = record_cuda_error(e, __FILE__, __LINE__, "cudaMemcpyAsync");
+  }
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (s == FRAC_OK && e != cudaSuccess) s = record_cuda_error(e, __FILE__, __LINE__, "cudaStreamSynchronize");
+  if (s != FRAC_OK) return settle(s);
+  if (std::isnan(info->rel_resid)) {
     info->status = FRAC_EINVAL;  // non-finite data in f
     return FRAC_EINVAL;
   }
-  if (s == FRAC_OK) s = info->status;
-  return s;
+  return info->status;
 }
 
 int frac_batch_pin_plan(int32_t cluster_size, int32_t first_cluster_logm) {
@@ -612,7 +631,7 @@ int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* con
         cs = FRAC_ECUDA;
     }
     const cudaError_t ec = cudaStreamEndCapture(cap, &graph);  // always ends the capture
-    if (cs != FRAC_OK) return cs;
+    if (cs != FRAC_OK) return settle(cs);
     FRAC_CUDA_TRY(ec);
     FRAC_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
     FRAC_CUDA_TRY(cudaGraphLaunch(exec, st));
@@ -664,7 +683,7 @@ int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* con
     for (int64_t i : rest)
       if (info[i].status != FRAC_OK && first == FRAC_OK) first = info[i].status;
   }
-  return first;
+  return settle(first);
 }
 
 }  // extern "C"

@@ -87,7 +87,7 @@ struct BatchPending {
   int alloc(P** out, size_t bytes) {
     void* p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, st);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FRAC_ENOMEM : FRAC_ECUDA;
+    if (e != cudaSuccess) return record_cuda_error(e, __FILE__, __LINE__, "cudaMallocAsync");
     bufs.push_back(p);
     *out = static_cast<P*>(p);
     return FRAC_OK;

@@ -442,7 +442,7 @@ struct DevBuf {
   int get(P** out, size_t bytes) {
     void* p = nullptr;
     cudaError_t e = cudaMallocAsync(&p, bytes ? bytes : 16, st);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FRAC_ENOMEM : FRAC_ECUDA;
+    if (e != cudaSuccess) return record_cuda_error(e, __FILE__, __LINE__, "cudaMallocAsync");
     ptrs.push_back(p);
     *out = static_cast<P*>(p);
     return FRAC_OK;
@@ -598,7 +598,7 @@ int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return rc;
+  return settle(rc);
 }
 
 // Relative cost model of one problem: plain CG iterations ~ n^(alpha/2)

@@ -25,7 +25,8 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
 template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
 template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return C{a.x * s, a.y * s}; }
 
-// Records the text of a failed CUDA call for frac_error_detail(); returns the status.
+// Records the text of a failed CUDA call for frac_error_detail() and consumes the
+// thread's last CUDA error (see settle()); returns the status.
 int record_cuda_error(cudaError_t e, const char* file, int line, const char* expr);
 // Records a failed device-side bounds check (file:line, index); returns FRAC_ECUDA.
 int record_check_failure(const char* file, int line, long long index);
@@ -38,6 +39,16 @@ void record_detail(const char* fmt, ...);
     cudaError_t e_ = (expr);                                                  \
     if (e_ != cudaSuccess) return record_cuda_error(e_, __FILE__, __LINE__, #expr); \
   } while (0)
+
+// A failed runtime call (an allocation above all) leaves its error behind as the
+// thread's last CUDA error, where the cudaGetLastError() that follows the next
+// launch of this library would report it again, in a later call that did not
+// fail. An entry point that fails with a CUDA status consumes it before it
+// returns. (A sticky error, one that ends the context, stays reported.)
+inline int settle(int s) {
+  if (s == FRAC_ENOMEM || s == FRAC_ECUDA) (void)cudaGetLastError();
+  return s;
+}
 
 #define FRAC_TRY(expr)            \
   do {                            \

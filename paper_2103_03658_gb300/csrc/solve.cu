@@ -204,7 +204,7 @@ struct Ws {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMallocAsync(&p, bytes, st);
-    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? FRAC_ENOMEM : FRAC_ECUDA;
+    if (e != cudaSuccess) return record_cuda_error(e, __FILE__, __LINE__, "cudaMallocAsync");
     ptrs.push_back(p);
     *out = (P*)p;
     return FRAC_OK;
@@ -905,7 +905,7 @@ extern "C" int frac_engine_submit(frac_engine* e, const frac_op* op, const doubl
   if (s != FRAC_OK) {
     cudaStreamSynchronize(j->s);
     release_job(e, j);
-    return s;
+    return settle(s);
   }
   e->jobs.push_back(j);
   *job = j->id;
