@@ -73,7 +73,20 @@ typedef struct frac_problem {
   double lambda;    /* tempering: kernel e^{-lambda |xi|} (Remark 2.2); 0 = (-Delta)^{alpha/2} */
   double gamma;     /* splitting parameter of Eq. (eq0) in (alpha, 2]; 0 means 2 (the default and
                        the most accurate, Sec. 3.1); below 2 the origin term drops (zeta = 0) */
+  int32_t fft_lengths; /* circulant embedding lengths M_i (Sec. 2.1 needs M_i >= 2 n_i - 1):
+                       FRAC_FFT_POW2 (0, the default): the next power of two >= 2 n_i - 1;
+                       FRAC_FFT_SMOOTH (1): the smallest 2^a 3^b 5^c 7^d >= 2 n_i + 2 with a >= 4
+                       (mixed-radix FFTs; less padding, and M_i/2 - 1 >= n_i keeps the tau
+                       preconditioner for every n_i); FRAC_FFT_AUTO (2): the cheaper of the
+                       two by a pass-count model (frac_fft_length).  Axes whose M_i is a power of two run
+                       the power-of-two kernels either way; the others the mixed-radix
+                       kernels, whose passes all go through shared memory.  Limits as for
+                       powers of two: M_i <= 8192 (d = 1), 2048 (d = 2), 512 (d = 3).  The
+                       persistent 2D batch launch of frac_solve_batch takes power-of-two
+                       problems only; mixed-length ones run through the solve engine. */
 } frac_problem;
+
+enum frac_fft_lengths { FRAC_FFT_POW2 = 0, FRAC_FFT_SMOOTH = 1, FRAC_FFT_AUTO = 2 };
 
 typedef struct frac_op frac_op;  /* opaque, immutable after frac_coeffs, shareable across streams */
 
@@ -82,7 +95,7 @@ typedef struct frac_op_info_t {
   double a0;              /* centre coefficient a_0 (Eq. (1D-scheme), a_00 of Eq. (2D-scheme)) */
   double far_field;       /* F_d = int over R_+^d \ [0,L]^d of |xi|^{-d-alpha} e^{-lambda|xi|} */
   double norm_bound;      /* max_k |Lambda_k| = ||A||_2 (from the FP64 symbol)    */
-  int64_t fft_len;        /* M_1: circulant embedding length of axis 1 (power of two >= 2 n_1 - 1) */
+  int64_t fft_len;        /* M_1: circulant embedding length of axis 1 (see frac_problem.fft_lengths) */
   int64_t n_gen;          /* N + 1: generator entries per axis, N = the largest N_i */
   size_t device_bytes;    /* device memory owned by the op                         */
   int32_t precond_ok;     /* 1: the tau preconditioner applies (n_i <= M_i/2 - 1, positive symbol) */
@@ -99,12 +112,26 @@ typedef struct frac_op_info_t {
  * Lambda = -c_{d,alpha} DFT_M(circulant embedding of a) (real, even), kept in
  * FP64 and FP32.  *out receives a new op (release with frac_op_free).
  * Errors: FRAC_EINVAL (d not in 1..3, alpha not in (0,2), degree not in 0..4, n_i < 1, N_i not divisible by a degree >= 2, h <= 0 or
- * non-finite, gamma not 0 and not in (alpha, 2],
+ * non-finite, gamma not 0 and not in (alpha, 2], fft_lengths not a frac_fft_lengths value,
  * lambda < 0 or non-finite, out == NULL), FRAC_ENOTSUP (M beyond the FFT
  * sizes of this build, per axis: M_i <= 8192 for d = 1, <= 2048 for d = 2,
  * <= 512 for d = 3), FRAC_ENOMEM, FRAC_ECUDA.  Synchronises `stream` before returning.
  */
 int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream);
+
+/*
+ * frac_fft_length -- the circulant embedding length M that frac_coeffs gives an
+ * axis of n interior points in dimension d under the policy fft_lengths (see
+ * frac_problem.fft_lengths), written to *M.  Host only (no device work).
+ * FRAC_FFT_AUTO compares M times the transform's passes through shared memory:
+ * ceil(log2 M / 4) for a power of two (register-interface radix-16 passes), the
+ * plan's passes plus one for a mixed length (plus two for d = 1), over the power
+ * of two (if M/2 - 1 >= n) and every mixed length from 2 n + 2 up to it (up to
+ * twice it when it does not hold the tau system); ties keep the power of two.
+ * Errors: FRAC_EINVAL (n < 1, d not in 1..3, unknown policy, M == NULL),
+ * FRAC_ENOTSUP (the length is beyond this build's limit for d).
+ */
+int frac_fft_length(int64_t n, int32_t d, int32_t fft_lengths, int64_t* M);
 
 /* Release an op (NULL is ignored).  The caller must ensure no work using it is in flight. */
 void frac_op_free(frac_op* op);

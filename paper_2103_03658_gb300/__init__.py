@@ -4,4 +4,5 @@ arXiv 2103.03658): coefficients, FFT Toeplitz apply and CG / mixed-precision
 iterative-refinement solves, behind the C ABI of include/frac.h.
 """
 from ._native import (F32, F64, MIXED_IR, PLAIN_F64, Engine, FracError, FracOp, batch_last_plan,  # noqa: F401
-                      batch_pin_plan, declared_entry_points, far_nodes, library_path, load, solve_batch)
+                      batch_pin_plan, declared_entry_points, far_nodes, fft_length, library_path, load,
+                      solve_batch)

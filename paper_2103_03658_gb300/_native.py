@@ -31,7 +31,10 @@ class FracError(RuntimeError):
 class Problem(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("degree", ctypes.c_int32), ("alpha", ctypes.c_double),
                 ("h", ctypes.c_double), ("n", ctypes.c_int64 * 3), ("lam", ctypes.c_double),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("fft_lengths", ctypes.c_int32)]
+
+
+FFT_LENGTHS = {"pow2": 0, "smooth": 1, "auto": 2}
 
 
 class OpInfo(ctypes.Structure):
@@ -131,6 +134,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.frac_far_points.argtypes = [vp, vp, vp, i64, i64, i64, vp, vp]
     lib.frac_far_points.restype = i32
     lib.frac_far_sum.argtypes = [vp, vp, i64, vp, i64, vp, vp]
+    lib.frac_fft_length.restype = i32
+    lib.frac_fft_length.argtypes = [i64, i32, i32, ctypes.POINTER(ctypes.c_int64)]
     lib.frac_far_sum.restype = i32
     _lib = lib
     return lib
@@ -164,6 +169,16 @@ def far_nodes(d: int, alpha: float, lam: float, L: float, nr: int = 96, ns: int 
     if s != 0:
         raise FracError(s, "frac_far_nodes")
     return xi, w
+
+
+def fft_length(n: int, d: int, fft: str = "pow2") -> int:
+    """The circulant embedding length frac_coeffs gives an axis of n points (frac_fft_length,
+    host only): fft "pow2" or "smooth" as in FracOp."""
+    m = ctypes.c_int64()
+    s = load().frac_fft_length(int(n), int(d), FFT_LENGTHS[fft], ctypes.byref(m))
+    if s != 0:
+        raise FracError(s, "frac_fft_length")
+    return m.value
 
 
 def alu_peak_tflops(kind: str, stream=None) -> float:
@@ -242,21 +257,27 @@ class FracOp:
     per axis: n an int (the cube (-1, 1)^d) or a sequence (n_1, .., n_d) of per-axis counts,
     axis 1 = x^(1) the fastest-varying (arrays have shape (n_d, .., n_1)).  h = 2 / (max n_i + 1)
     unless given (the longest axis spans (-1, 1)); gamma the splitting parameter in (alpha, 2]
-    (Eq. (eq0)); built on the current CUDA device."""
+    (Eq. (eq0)); fft the circulant embedding lengths: "pow2" (the next power of two) or
+    "smooth" (the smallest 2^a 3^b 5^c 7^d >= 2 n_i + 2, a >= 4, on mixed-radix FFTs) or "auto"
+    (the cheaper of the two by frac_fft_length's pass-count model);
+    built on the current CUDA device."""
 
     def __init__(self, d: int, n, alpha: float, degree: int = 1, lam: float = 0.0,
-                 h: float | None = None, stream=None, gamma: float = 2.0):
+                 h: float | None = None, stream=None, gamma: float = 2.0, fft: str = "pow2"):
+        if fft not in FFT_LENGTHS:
+            raise ValueError(f"fft must be one of {sorted(FFT_LENGTHS)}, not {fft!r}")
         lib = load()
         self._lib = lib
         ns = tuple(int(v) for v in n) if isinstance(n, (tuple, list)) else (int(n),) * d
         if len(ns) != d:
             raise ValueError(f"n has {len(ns)} entries for d = {d}")
-        self.d, self.alpha, self.degree, self.lam, self.gamma = d, alpha, degree, lam, gamma
+        self.d, self.alpha, self.degree, self.lam, self.gamma, self.fft = d, alpha, degree, lam, gamma, fft
         self.n = ns[0] if len(set(ns)) == 1 else ns
         self.ns = ns
         self.nd = int(np.prod(ns))
         self.h = 2.0 / (max(ns) + 1) if h is None else h
-        self._prob = Problem(d, degree, alpha, self.h, (ctypes.c_int64 * 3)(*(ns + (1,) * (3 - d))), lam, gamma)
+        self._prob = Problem(d, degree, alpha, self.h, (ctypes.c_int64 * 3)(*(ns + (1,) * (3 - d))), lam, gamma,
+                             FFT_LENGTHS[fft])
         handle = ctypes.c_void_p()
         s = lib.frac_coeffs(ctypes.byref(self._prob), ctypes.byref(handle), _stream(stream))
         if s != 0:

@@ -82,6 +82,7 @@ static int validate(const frac_problem* p) {
   if (!(p->h > 0.0) || !std::isfinite(p->h)) return FRAC_EINVAL;
   if (!(p->lambda >= 0.0) || !std::isfinite(p->lambda)) return FRAC_EINVAL;
   if (p->gamma != 0.0 && !(p->gamma > p->alpha && p->gamma <= 2.0)) return FRAC_EINVAL;
+  if (p->fft_lengths < FRAC_FFT_POW2 || p->fft_lengths > FRAC_FFT_AUTO) return FRAC_EINVAL;
   for (int i = 0; i < p->d; ++i) {
     if (p->n[i] < 1) return FRAC_EINVAL;
     if (p->degree >= 2 && ((p->n[i] + 1) % p->degree) != 0) return FRAC_EINVAL;
@@ -137,6 +138,52 @@ const char* frac_strerror(int s) {
   }
 }
 
+// Relative cost of one transform of length M, by the passes it makes through shared
+// memory: a power of two takes ceil(log2 M / 4) radix-16 passes on the register
+// interface; a mixed length its np passes plus one (the odd passes leave part of
+// the threads idle), plus two in 1D (the whole-solve kernel keeps its CG vectors in
+// registers across the out-of-line passes).  Calibrated on GB300 FP32 applies:
+// 2D 1280 and 640 beat 2048 and 1024, 1440 and 2016 lose to 2048, 3D 432 and 224
+// lose to 512 and 256, 1D 6048 and 2240 lose to 8192 and 4096 in the solve.
+static double fft_cost(int64_t M, int d) {
+  MxPlan p;
+  if ((M & (M - 1)) == 0) return (double)M * ((ilog2(M) + 3) / 4);
+  if (!mx_plan(M, &p)) return INFINITY;
+  return (double)M * (p.np + (d == 1 ? 2 : 1));
+}
+
+int frac_fft_length(int64_t n, int32_t d, int32_t fft_lengths, int64_t* M) {
+  if (!M || n < 1 || d < 1 || d > 3) return FRAC_EINVAL;
+  if (fft_lengths != FRAC_FFT_POW2 && fft_lengths != FRAC_FFT_SMOOTH && fft_lengths != FRAC_FFT_AUTO)
+    return FRAC_EINVAL;
+  int64_t m = 2;
+  while (m < 2 * n - 1) m *= 2;
+  const int64_t cap = int64_t(1) << max_logm(d);
+  if (fft_lengths == FRAC_FFT_SMOOTH) {
+    // the smallest 7-smooth length with a >= 4 that keeps M/2 - 1 >= n (the tau
+    // system); the power of two when that one is beyond the limit
+    const int64_t ms = mx_length_at_least(2 * n + 2);
+    if (ms <= cap) m = ms;
+  } else if (fft_lengths == FRAC_FFT_AUTO) {
+    // the cheapest by fft_cost among the power of two (when it holds the tau system)
+    // and the 7-smooth lengths >= 2 n + 2 below twice the power of two
+    const bool p2_tau = m / 2 - 1 >= n;
+    double best = p2_tau ? fft_cost(m, d) : INFINITY;
+    int64_t pick = m;
+    for (int64_t c = (2 * n + 2 + 15) / 16 * 16; c <= std::min(cap, p2_tau ? m : 2 * m); c += 16) {
+      const double cost = fft_cost(c, d);
+      if (cost < best) {
+        best = cost;
+        pick = c;
+      }
+    }
+    m = pick;
+  }
+  if (m > cap) return FRAC_ENOTSUP;
+  *M = m;
+  return FRAC_OK;
+}
+
 int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
   if (!out) return FRAC_EINVAL;
   *out = nullptr;
@@ -144,11 +191,10 @@ int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int d = prob->d;
   int64_t Ma[3] = {1, 1, 1}, nmax = 0;
+  MxPlan plans[3];
   for (int i = 0; i < d; ++i) {
-    int64_t M = 2;
-    while (M < 2 * prob->n[i] - 1) M *= 2;
-    if (ilog2(M) > max_logm(d)) return FRAC_ENOTSUP;
-    Ma[i] = M;
+    FRAC_TRY(frac_fft_length(prob->n[i], d, prob->fft_lengths, &Ma[i]));
+    if ((Ma[i] & (Ma[i] - 1)) != 0 && !mx_plan(Ma[i], &plans[i])) return FRAC_ENOTSUP;
     nmax = std::max<int64_t>(nmax, prob->n[i]);
   }
   FRAC_TRY(keep_pool_memory());
@@ -161,7 +207,8 @@ int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
     op->na[i] = i < d ? prob->n[i] : 1;
     op->Ma[i] = Ma[i];
     op->Ka[i] = i < d ? Ma[i] / 2 + 1 : 1;
-    op->logma[i] = i < d ? ilog2(Ma[i]) : 0;
+    op->plan[i] = plans[i];
+    op->logma[i] = i >= d ? 0 : (plans[i].m ? -1 : ilog2(Ma[i]));
     if (i < d && prob->n[i] != prob->n[0]) op->square = 0;
   }
   op->N = nmax + 1;  // the generator covers [0, L]^d with L the largest extent
@@ -188,7 +235,7 @@ int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
     cudaGetLastError();
     s = FRAC_ENOMEM;
   }
-  for (int i = 0; i < d && s == FRAC_OK; ++i) s = prepare_twiddles(op->logma[i]);
+  for (int i = 0; i < d && s == FRAC_OK; ++i) s = prepare_twiddles_len(op->Ma[i]);
   if (s == FRAC_OK) s = build_coefficients(op, st);
   if (s != FRAC_OK) {
     frac_op_free(op);
@@ -593,7 +640,7 @@ int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* con
     // beside the 2D launch) are then captured into one CUDA graph on a library
     // stream, and the graph is launched once on st.
     if (!wide.empty()) FRAC_TRY(batch2d_prepare((int64_t)wide.size(), ops, f, wide.data(), st));
-    for (int64_t i : oned) FRAC_TRY(prepare_twiddles(ops[i]->logm));
+    for (int64_t i : oned) FRAC_TRY(prepare_twiddles_len(ops[i]->M));
     cudaStream_t cap = nullptr;
     FRAC_TRY(side_stream(&cap, 1));
     cudaStream_t s1 = cap;

@@ -17,7 +17,7 @@ size_t apply_workspace_bytes(const frac_op* op, int dtype, int64_t batch) {
 template <typename T>
 int apply_t(const frac_op* op, const T* u, T* y, int64_t batch, void* ws, cudaStream_t st) {
   if (batch <= 0) return FRAC_OK;
-  if (op->prob.d == 1) return conv1d_any<T, false>(op->logm, u, y, op->n, batch, sym_table<T>(op), st);
+  if (op->prob.d == 1) return conv1d_op<T, false>(op, u, y, batch, sym_table<T>(op), st);
   return pipeline<T, RF_PLAIN, RI_PLAIN, false>(op, sym_table<T>(op), u, y, batch, ws, CgArgs{}, CgArgs{}, nullptr,
                                                 st);
 }
@@ -28,7 +28,7 @@ template int apply_t<double>(const frac_op*, const double*, double*, int64_t, vo
 size_t apply_cg_partials(const frac_op* op) {
   int64_t nrows = 1;  // rows of one field: the extents of the axes after the row axis
   for (int i = 1; i < op->prob.d; ++i) nrows *= op->na[i];
-  const int64_t a = rows_grid_any<float>(op->logm, nrows), b = rows_grid_any<double>(op->logm, nrows);
+  const int64_t a = rows_grid_op<float>(op, nrows), b = rows_grid_op<double>(op, nrows);
   return (size_t)(a > b ? a : b);
 }
 

@@ -16,6 +16,7 @@
 //        extract; in place) -> y-columns (iFFT, extract) -> rows.
 #pragma once
 
+#include <algorithm>
 #include <cstdio>
 
 #include "apply.cuh"
@@ -45,22 +46,27 @@ template <typename T> __host__ __device__ constexpr int minb_cols(int nt) {
   return sizeof(T) == 4 ? minb_rows<T>(nt) : minb<T>(nt);
 }
 
+// the mixed-length kernels: blocks per SM asked of the compiler for a block of nt
+// threads, so that FP32 kernels fit 64 registers a thread (as the power-of-two
+// ones) and FP64 kernels 128
+template <typename T> __host__ __device__ constexpr int mx_minb(int nt) {
+  return clamp_blocks(65536 / (nt * ((int)sizeof(T) == 4 ? 64 : 128)));
+}
+
 // ---------------------------------------------------------------------------
 // d = 1: whole convolution per line (two vectors per complex line)
 // ---------------------------------------------------------------------------
 
 // ODD: the tau preconditioner (odd extension, entries 1..n kept, lam = its symbol).
-template <typename T, int LOGM, int LINES, bool ODD = false>
-__global__ void __launch_bounds__(LINES * tpl(LOGM), minb<T>(LINES * tpl(LOGM)))
-k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const T* __restrict__ lam,
-         const cplx_t<T>* __restrict__ tw) {
+// One complex line (vectors va, va + 1) on the thread group of tl; ln: the line policy.
+template <typename T, typename LN, bool ODD>
+__device__ __forceinline__ void conv1d_pair(const LN& ln, const T* __restrict__ u, T* __restrict__ y, int n,
+                                            int64_t batch, const T* __restrict__ lam,
+                                            const cplx_t<T>* __restrict__ tw, int64_t va, cplx_t<T>* buf, int tl) {
   using C = cplx_t<T>;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride(LOGM);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
-  C* buf = sm + line * LS;
-  const int64_t va = 2 * ((int64_t)blockIdx.x * LINES + line), vb = va + 1;
+  constexpr int E = LN::E;
+  const int M = ln.m(), TPL = ln.tpl();
+  const int64_t vb = va + 1;
   const bool ha = va < batch, hb = vb < batch;
   C v[E];
   if constexpr (!ODD) {
@@ -73,7 +79,7 @@ k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const
       T im = (x < n && hb) ? u[vb * n + x] : T(0);
       v[e] = C{re, im};
     }
-    fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);
+    ln.template fft<false, true, false>(v, buf, tl, tw);
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -88,7 +94,7 @@ k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const
       }
       v[e] = C{re, im};
     }
-    fft_reg<C, LOGM, false, false, false>(v, buf, tl, tw);
+    ln.template fft<false, false, false>(v, buf, tl, tw);
   }
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -96,7 +102,7 @@ k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const
     v[e] = cscale(v[e], lam[k <= M / 2 ? k : M - k]);
   }
   if constexpr (!ODD) {
-    fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);
+    ln.template fft<true, false, true>(v, buf, tl, tw);
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {
       const int x = tl + e * TPL;
@@ -106,7 +112,7 @@ k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const
       }
     }
   } else {
-    fft_reg<C, LOGM, true, false, false>(v, buf, tl, tw);
+    ln.template fft<true, false, false>(v, buf, tl, tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int x = tl + e * TPL;
@@ -117,6 +123,36 @@ k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const
     }
   }
 }
+
+template <typename T, int LOGM, int LINES, bool ODD = false>
+__global__ void __launch_bounds__(LINES * tpl(LOGM), minb<T>(LINES * tpl(LOGM)))
+k_conv1d(const T* __restrict__ u, T* __restrict__ y, int n, int64_t batch, const T* __restrict__ lam,
+         const cplx_t<T>* __restrict__ tw) {
+  using C = cplx_t<T>;
+  constexpr int TPL = tpl(LOGM), LS = line_stride(LOGM);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
+  conv1d_pair<T, P2Line<LOGM>, ODD>(P2Line<LOGM>{}, u, y, n, batch, lam, tw, 2 * ((int64_t)blockIdx.x * LINES + line),
+                                    sm + line * LS, tl);
+}
+
+#ifdef FRAC_MX_TU
+// Mixed lengths: blockDim.x / ln.tpl() lines per block.
+template <typename T, bool ODD, int NTMAX>
+__global__ void __launch_bounds__(NTMAX, mx_minb<T>(NTMAX)) k_conv1d_mx(MxLine ln, const T* __restrict__ u, T* __restrict__ y, int n,
+                                                   int64_t batch, const T* __restrict__ lam,
+                                                   const cplx_t<T>* __restrict__ tw) {
+  using C = cplx_t<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int TPL = ln.tpl(), lines = blockDim.x / TPL;
+  const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
+  conv1d_pair<T, MxLine, ODD>(ln, u, y, n, batch, lam, tw, 2 * ((int64_t)blockIdx.x * lines + line),
+                              sm + line * ln.stride(), tl);
+}
+
+#endif  // FRAC_MX_TU
 
 // Every block stores its total in partials[blockIdx.x]; the last block to
 // arrive (counter) sums all of them in index order and calls fin(sum) in
@@ -155,6 +191,28 @@ __device__ __forceinline__ void last_block_reduce(double total, double* partials
 // block sets st->beta and st->rz).  CG kinds return at once when st->done.
 enum RowKind { RF_PLAIN = 0, RF_CG = 1, RF_ODD = 2, RI_PLAIN = 0, RI_CG = 1, RI_ODD = 2, RI_ODD_CG = 3 };
 
+// One row pair of the forward row pass (kind KIND) on the thread group of tl.
+template <typename T, int KIND, typename LN>
+__device__ __forceinline__ void rows_fwd_unit(const LN& ln, const T* u, cplx_t<T>* W, int n, int ns, int64_t nrows,
+                                              int KB, const cplx_t<T>* __restrict__ tw, const T* __restrict__ r,
+                                              const CGState* st, int64_t pair, cplx_t<T>* buf, int tl) {
+  if constexpr (KIND == RF_CG) {
+    const T be = (T)st->beta;
+    T* p = const_cast<T*>(u);
+    row_fwd_pair_l<T, LN>(
+        ln,
+        [&](int64_t row, int x) {
+          const T v = r[row * n + x] + be * p[row * n + x];
+          p[row * n + x] = v;
+          return v;
+        },
+        W, n, nrows, KB, tw, pair, buf, tl, ns);
+  } else {
+    row_fwd_pair_l<T, LN, KIND == RF_ODD>(ln, [&](int64_t row, int x) { return u[row * n + x]; }, W, n, nrows, KB, tw,
+                                          pair, buf, tl, ns);
+  }
+}
+
 template <typename T, int LOGM, int LINES, int KIND>
 __global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
 k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int ns, int64_t nrows, int KB,
@@ -165,43 +223,46 @@ k_rows_fwd(const T* u, cplx_t<T>* __restrict__ W, int n, int ns, int64_t nrows, 
   if (KIND == RF_CG && st->done) return;
   C* sm = reinterpret_cast<C*>(smem_raw);
   const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
-  const int64_t pair = (int64_t)blockIdx.x * LINES + line;
-  if constexpr (KIND == RF_CG) {
-    const T be = (T)st->beta;
-    T* p = const_cast<T*>(u);
-    row_fwd_pair<T, LOGM>(
-        [&](int64_t row, int x) {
-          const T v = r[row * n + x] + be * p[row * n + x];
-          p[row * n + x] = v;
-          return v;
-        },
-        W, n, nrows, KB, tw, pair, sm + line * LS, tl, ns);
-  } else {
-    row_fwd_pair<T, LOGM, KIND == RF_ODD>([&](int64_t row, int x) { return u[row * n + x]; }, W, n, nrows, KB, tw,
-                                          pair, sm + line * LS, tl, ns);
-  }
+  rows_fwd_unit<T, KIND>(P2Line<LOGM>{}, u, W, n, ns, nrows, KB, tw, r, st, (int64_t)blockIdx.x * LINES + line,
+                         sm + line * LS, tl);
 }
 
-template <typename T, int LOGM, int LINES, int KIND>
-__global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
-k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int ns, int64_t nrows, int KB,
-           const cplx_t<T>* __restrict__ tw, const T* __restrict__ p, CGState* st, double* partials) {
+#ifdef FRAC_MX_TU
+template <typename T, int KIND>
+__global__ void __launch_bounds__(256, mx_minb<T>(256)) k_rows_fwd_mx(MxLine ln, const T* u, cplx_t<T>* __restrict__ W, int n, int ns,
+                                                     int64_t nrows, int KB, const cplx_t<T>* __restrict__ tw,
+                                                     const T* __restrict__ r, const CGState* st) {
   using C = cplx_t<T>;
-  constexpr int TPL = tpl(LOGM), LS = line_stride(LOGM);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (KIND == RF_CG && st->done) return;
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int TPL = ln.tpl(), lines = blockDim.x / TPL, line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
+  rows_fwd_unit<T, KIND>(ln, u, W, n, ns, nrows, KB, tw, r, st, (int64_t)blockIdx.x * lines + line,
+                         sm + line * ln.stride(), tl);
+}
+
+#endif  // FRAC_MX_TU
+
+// One row pair of the inverse row pass; returns this thread's part of the CG dot product.
+template <typename T, int KIND, typename LN>
+__device__ __forceinline__ T rows_inv_unit(const LN& ln, const cplx_t<T>* W, T* __restrict__ y, int n, int ns,
+                                           int64_t nrows, int KB, const cplx_t<T>* __restrict__ tw,
+                                           const T* __restrict__ p, int64_t pair, cplx_t<T>* buf, int tl) {
   constexpr bool CG = KIND == RI_CG || KIND == RI_ODD_CG;
   constexpr bool ODD = KIND == RI_ODD || KIND == RI_ODD_CG;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (CG && st->done) return;
-  C* sm = reinterpret_cast<C*>(smem_raw);
-  const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
-  const int64_t pair = (int64_t)blockIdx.x * LINES + line;
   T dot = T(0);
-  row_inv_pair<T, LOGM, ODD>(W, n, nrows, KB, tw, pair, sm + line * LS, tl, [&](int64_t row, int x, T v) {
+  row_inv_pair_l<T, LN, ODD>(ln, W, n, nrows, KB, tw, pair, buf, tl, [&](int64_t row, int x, T v) {
     y[row * n + x] = v;
     if (CG) dot += v * p[row * n + x];
   }, ns);
+  return dot;
+}
+
+// The CG kinds' reduction at the end of the inverse row pass (red: the block's
+// dynamic shared memory, free once the FFT lines are done).
+template <int KIND>
+__device__ __forceinline__ void rows_inv_finish(double dot, CGState* st, double* partials, double* red) {
   if constexpr (KIND == RI_CG) {
-    double* red = reinterpret_cast<double*>(smem_raw);  // the FFT lines are no longer needed
     const double total = block_sum_all(dot, red);
     last_block_reduce(total, partials, &st->count_pq, red, [&](double pq) {
       st->pq = pq;
@@ -213,7 +274,6 @@ k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int ns, in
       }
     });
   } else if constexpr (KIND == RI_ODD_CG) {
-    double* red = reinterpret_cast<double*>(smem_raw);
     const double total = block_sum_all(dot, red);
     last_block_reduce(total, partials, &st->count_rz, red, [&](double rz) {
       if (!(rz > 0.0) || !isfinite(rz)) {  // P is SPD: r.z > 0 unless r = 0
@@ -226,6 +286,41 @@ k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int ns, in
     });
   }
 }
+
+template <typename T, int LOGM, int LINES, int KIND>
+__global__ void __launch_bounds__(LINES * tpl(LOGM), minb_rows<T>(LINES * tpl(LOGM)))
+k_rows_inv(const cplx_t<T>* __restrict__ W, T* __restrict__ y, int n, int ns, int64_t nrows, int KB,
+           const cplx_t<T>* __restrict__ tw, const T* __restrict__ p, CGState* st, double* partials) {
+  using C = cplx_t<T>;
+  constexpr int TPL = tpl(LOGM), LS = line_stride(LOGM);
+  constexpr bool CG = KIND == RI_CG || KIND == RI_ODD_CG;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (CG && st->done) return;
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
+  const T dot = rows_inv_unit<T, KIND>(P2Line<LOGM>{}, W, y, n, ns, nrows, KB, tw, p,
+                                       (int64_t)blockIdx.x * LINES + line, sm + line * LS, tl);
+  rows_inv_finish<KIND>(dot, st, partials, reinterpret_cast<double*>(smem_raw));
+}
+
+#ifdef FRAC_MX_TU
+template <typename T, int KIND>
+__global__ void __launch_bounds__(256, mx_minb<T>(256)) k_rows_inv_mx(MxLine ln, const cplx_t<T>* __restrict__ W, T* __restrict__ y,
+                                                     int n, int ns, int64_t nrows, int KB,
+                                                     const cplx_t<T>* __restrict__ tw, const T* __restrict__ p,
+                                                     CGState* st, double* partials) {
+  using C = cplx_t<T>;
+  constexpr bool CG = KIND == RI_CG || KIND == RI_ODD_CG;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (CG && st->done) return;
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  const int TPL = ln.tpl(), lines = blockDim.x / TPL, line = threadIdx.x / TPL, tl = threadIdx.x % TPL;
+  const T dot = rows_inv_unit<T, KIND>(ln, W, y, n, ns, nrows, KB, tw, p, (int64_t)blockIdx.x * lines + line,
+                                       sm + line * ln.stride(), tl);
+  rows_inv_finish<KIND>(dot, st, partials, reinterpret_cast<double*>(smem_raw));
+}
+
+#endif  // FRAC_MX_TU
 
 // Columns: one tile of B adjacent columns per block (see col_tile).
 template <typename T, int LOGM, int MODE, bool ODD>
@@ -240,6 +335,22 @@ k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam
   const int64_t o = blockIdx.x / A.tiles, tile = blockIdx.x % A.tiles;
   col_tile<T, LOGM, MODE, ODD>(in, out, A, lam, tw, o, tile, reinterpret_cast<C*>(smem_raw), cl, tl);
 }
+
+#ifdef FRAC_MX_TU
+template <typename T, int MODE, bool ODD, int NTMAX>
+__global__ void __launch_bounds__(NTMAX, mx_minb<T>(NTMAX)) k_cols_mx(MxLine ln, const cplx_t<T>* in, cplx_t<T>* out, ColArgs A,
+                                                  const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw,
+                                                  const CGState* st) {
+  using C = cplx_t<T>;
+  constexpr int B = blk<T>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (st && st->done) return;
+  const int cl = threadIdx.x % B, tl = threadIdx.x / B;
+  const int64_t o = blockIdx.x / A.tiles, tile = blockIdx.x % A.tiles;
+  col_tile_l<T, MxLine, MODE, ODD>(ln, in, out, A, lam, tw, o, tile, reinterpret_cast<C*>(smem_raw), cl, tl);
+}
+
+#endif  // FRAC_MX_TU
 
 // ---------------------------------------------------------------------------
 // Launch helpers
@@ -416,6 +527,146 @@ static int cols_any(int logm, const void* in, void* out, const ColArgs& A, int64
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed lengths (op->plan[axis].m set): the same passes on MxLine, runtime M.
+// ---------------------------------------------------------------------------
+
+template <typename T> inline const cplx_t<T>* tw_len(int64_t M);
+template <> inline const float2* tw_len<float>(int64_t M) { return twiddles32_len(M); }
+template <> inline const double2* tw_len<double>(int64_t M) { return twiddles64_len(M); }
+
+template <typename T>
+static const char* kname_mx(char* buf, const char* what, int M) {
+  std::snprintf(buf, 48, "%s_%s_M%d", what, sizeof(T) == 8 ? "f64" : "f32", M);
+  return buf;
+}
+
+// lines per block of the mixed row and 1D kernels: as many as fit 128 threads and
+// 48 KB of shared memory, at least one
+template <typename T>
+static int mx_lines(const MxLine& ln) {
+  const int by_threads = 128 / ln.tpl();
+  const int by_smem = (int)(48 * 1024 / ((size_t)ln.stride() * sizeof(cplx_t<T>)));
+  return std::max(1, std::min(by_threads, by_smem));
+}
+
+// Launchers of the mixed-length kernels (defined and instantiated in apply_mx_f32.cu and
+// apply_mx_f64.cu, so that the mixed kernels compile apart from the power-of-two ones).
+template <typename T, bool ODD>
+int launch_conv1d_mx(const MxLine& ln, const T* u, T* y, int64_t n, int64_t batch, const T* lam, cudaStream_t st);
+template <typename T, int KIND>
+int launch_rows_fwd_mx(const MxLine& ln, const void* in, void* out, int64_t n, int64_t ns, int64_t nrows, int KB,
+                       const CgArgs& cg, cudaStream_t st);
+template <typename T, int KIND>
+int launch_rows_inv_mx(const MxLine& ln, const void* in, void* out, int64_t n, int64_t ns, int64_t nrows, int KB,
+                       const CgArgs& cg, cudaStream_t st);
+template <typename T, int MODE, bool ODD>
+int launch_cols_mx(const MxLine& ln, const void* in, void* out, const ColArgs& A, int64_t nouter, const T* lam,
+                   const CGState* cgst, cudaStream_t st);
+
+#ifdef FRAC_MX_TU
+template <typename T, bool ODD>
+int launch_conv1d_mx(const MxLine& ln, const T* u, T* y, int64_t n, int64_t batch, const T* lam,
+                            cudaStream_t st) {
+  const int L = mx_lines<T>(ln);
+  const size_t sm = (size_t)L * ln.stride() * sizeof(cplx_t<T>);
+  // blocks of up to 256 threads get up to 255 registers a thread; longer lines take 512
+  auto kern = L * ln.tpl() <= 256 ? k_conv1d_mx<T, ODD, 256> : k_conv1d_mx<T, ODD, 512>;
+  FRAC_TRY(set_smem(kern, sm));
+  char nb[48];
+  prof::Scope ps(kname_mx<T>(nb, ODD ? "conv1d_tau" : "conv1d", ln.m()), st);
+  kern<<<(unsigned)cdiv(cdiv(batch, 2), L), L * ln.tpl(), sm, st>>>(ln, u, y, (int)n, batch, lam, tw_len<T>(ln.m()));
+  FRAC_CUDA_TRY(cudaGetLastError());
+  return FRAC_OK;
+}
+
+template <typename T, int KIND>
+int launch_rows_fwd_mx(const MxLine& ln, const void* in, void* out, int64_t n, int64_t ns, int64_t nrows,
+                              int KB, const CgArgs& cg, cudaStream_t st) {
+  using C = cplx_t<T>;
+  const int L = mx_lines<T>(ln);
+  const size_t sm = (size_t)L * ln.stride() * sizeof(C);
+  static const char* names[3] = {"rows_fwd", "rows_fwd_cg", "rows_fwd_tau"};
+  char nb[48];
+  prof::Scope ps(kname_mx<T>(nb, names[KIND], ln.m()), st);
+  auto kern = k_rows_fwd_mx<T, KIND>;
+  FRAC_TRY(set_smem(kern, sm));
+  kern<<<(unsigned)cdiv(cdiv(nrows, 2), L), L * ln.tpl(), sm, st>>>(ln, (const T*)in, (C*)out, (int)n, (int)ns, nrows,
+                                                                     KB, tw_len<T>(ln.m()), (const T*)cg.r, cg.st);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  return FRAC_OK;
+}
+
+template <typename T, int KIND>
+int launch_rows_inv_mx(const MxLine& ln, const void* in, void* out, int64_t n, int64_t ns, int64_t nrows,
+                              int KB, const CgArgs& cg, cudaStream_t st) {
+  using C = cplx_t<T>;
+  const int L = mx_lines<T>(ln);
+  const size_t sm = std::max<size_t>((size_t)L * ln.stride() * sizeof(C), 32 * sizeof(double));
+  static const char* names[4] = {"rows_inv", "rows_inv_cg", "rows_inv_tau", "rows_inv_tau_cg"};
+  char nb[48];
+  prof::Scope ps(kname_mx<T>(nb, names[KIND], ln.m()), st);
+  auto kern = k_rows_inv_mx<T, KIND>;
+  FRAC_TRY(set_smem(kern, sm));
+  kern<<<(unsigned)cdiv(cdiv(nrows, 2), L), L * ln.tpl(), sm, st>>>(ln, (const C*)in, (T*)out, (int)n, (int)ns, nrows,
+                                                                     KB, tw_len<T>(ln.m()), (const T*)cg.p, cg.st,
+                                                                     cg.partials);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  return FRAC_OK;
+}
+
+template <typename T, int MODE, bool ODD>
+int launch_cols_mx(const MxLine& ln, const void* in, void* out, const ColArgs& A, int64_t nouter, const T* lam,
+                          const CGState* cgst, cudaStream_t st) {
+  using C = cplx_t<T>;
+  constexpr int B = blk<T>();
+  const size_t sm = (size_t)B * ln.stride_tile() * sizeof(C);
+  auto kern = B * ln.tpl() <= 256 ? k_cols_mx<T, MODE, ODD, 256> : k_cols_mx<T, MODE, ODD, 512>;
+  FRAC_TRY(set_smem(kern, sm));
+  static const char* names[2][4] = {{"cols_sym2", "cols_yfwd", "cols_zsym", "cols_yinv"},
+                                    {"cols_sym2_tau", "cols_yfwd_tau", "cols_zsym_tau", "cols_yinv_tau"}};
+  char nb[48];
+  prof::Scope ps(kname_mx<T>(nb, names[ODD ? 1 : 0][MODE], ln.m()), st);
+  kern<<<(unsigned)(nouter * A.tiles), B * ln.tpl(), sm, st>>>(ln, (const C*)in, (C*)out, A, lam, tw_len<T>(ln.m()),
+                                                                cgst);
+  FRAC_CUDA_TRY(cudaGetLastError());
+  return FRAC_OK;
+}
+
+#endif  // FRAC_MX_TU
+
+// Per-axis dispatch: the power-of-two kernels, or the mixed ones where plan[axis].m is set.
+template <typename T, bool ODD>
+static int conv1d_op(const frac_op* op, const T* u, T* y, int64_t batch, const T* lam, cudaStream_t st) {
+  if (op->plan[0].m) return launch_conv1d_mx<T, ODD>(MxLine(op->plan[0]), u, y, op->n, batch, lam, st);
+  return conv1d_any<T, ODD>(op->logm, u, y, op->n, batch, lam, st);
+}
+template <typename T, int KIND>
+static int rows_fwd_op(const frac_op* op, const void* in, void* out, int64_t n, int64_t ns, int64_t nrows, int KB,
+                       cudaStream_t st, const CgArgs& cg) {
+  if (op->plan[0].m) return launch_rows_fwd_mx<T, KIND>(MxLine(op->plan[0]), in, out, n, ns, nrows, KB, cg, st);
+  return rows_fwd_any<T, KIND>(op->logma[0], in, out, n, ns, nrows, KB, st, cg);
+}
+template <typename T, int KIND>
+static int rows_inv_op(const frac_op* op, const void* in, void* out, int64_t n, int64_t ns, int64_t nrows, int KB,
+                       cudaStream_t st, const CgArgs& cg) {
+  if (op->plan[0].m) return launch_rows_inv_mx<T, KIND>(MxLine(op->plan[0]), in, out, n, ns, nrows, KB, cg, st);
+  return rows_inv_any<T, KIND>(op->logma[0], in, out, n, ns, nrows, KB, st, cg);
+}
+template <typename T, int MODE, bool ODD>
+static int cols_op(const frac_op* op, int axis, const void* in, void* out, const ColArgs& A, int64_t nouter,
+                   const T* lam, cudaStream_t st, const CGState* cgst) {
+  if (op->plan[axis].m)
+    return launch_cols_mx<T, MODE, ODD>(MxLine(op->plan[axis]), in, out, A, nouter, lam, cgst, st);
+  return cols_any<T, MODE, ODD>(op->logma[axis], in, out, A, nouter, lam, st, cgst);
+}
+// blocks of one launch of the row kernels over nrows rows (the partial sums of the CG kinds)
+template <typename T>
+static int64_t rows_grid_op(const frac_op* op, int64_t nrows) {
+  if (op->plan[0].m) return cdiv(cdiv(nrows, 2), mx_lines<T>(MxLine(op->plan[0])));
+  return rows_grid_any<T>(op->logm, nrows);
+}
+
 // Spectrum layout for d >= 2 (axis i: n_i points, FFT length M_i, K_i = M_i/2 + 1;
 // axis 0 = x^(1) is the row axis): W1 holds the rows' half spectra column-blocked,
 // slabs of n_2 rows (KB = ceil(K_1 / B) blocks); d = 3: W2 holds the y transform,
@@ -445,21 +696,21 @@ static int pipeline(const frac_op* op, const T* lam, const void* in, void* out, 
   C* W1 = (C*)ws;
   if (d == 2) {
     const int64_t nrows = batch * n2;
-    FRAC_TRY((rows_fwd_any<T, FK>(op->logma[0], in, W1, n1, n2, nrows, (int)KB, st, fwd)));
+    FRAC_TRY((rows_fwd_op<T, FK>(op, in, W1, n1, n2, nrows, (int)KB, st, fwd)));
     ColArgs A{(int)n2, (int)K1, (int)KB, KB, batch, 0, 0, (int)op->Ka[1]};
-    FRAC_TRY((cols_any<T, SYM2, ODD>(op->logma[1], W1, W1, A, batch, lam, st, cgst)));
-    FRAC_TRY((rows_inv_any<T, IK>(op->logma[0], W1, out, n1, n2, nrows, (int)KB, st, inv)));
+    FRAC_TRY((cols_op<T, SYM2, ODD>(op, 1, W1, W1, A, batch, lam, st, cgst)));
+    FRAC_TRY((rows_inv_op<T, IK>(op, W1, out, n1, n2, nrows, (int)KB, st, inv)));
     return FRAC_OK;
   }
   C* W2 = W1 + w1;
   const int64_t nrows = batch * n3 * n2;
-  FRAC_TRY((rows_fwd_any<T, FK>(op->logma[0], in, W1, n1, n2, nrows, (int)KB, st, fwd)));
+  FRAC_TRY((rows_fwd_op<T, FK>(op, in, W1, n1, n2, nrows, (int)KB, st, fwd)));
   ColArgs Ay{(int)n2, (int)K1, (int)KB, KB, batch, (int)n3, (int)op->Ma[1], (int)op->Ka[1]};
-  FRAC_TRY((cols_any<T, YFWD, ODD>(op->logma[1], W1, W2, Ay, batch * n3, lam, st, cgst)));
+  FRAC_TRY((cols_op<T, YFWD, ODD>(op, 1, W1, W2, Ay, batch * n3, lam, st, cgst)));
   ColArgs Az{(int)n3, (int)K1, (int)KB, op->Ma[1] * KB, batch, (int)n3, (int)op->Ma[1], (int)op->Ka[1]};
-  FRAC_TRY((cols_any<T, ZSYM, ODD>(op->logma[2], W2, W2, Az, batch, lam, st, cgst)));
-  FRAC_TRY((cols_any<T, YINV, ODD>(op->logma[1], W2, W1, Ay, batch * n3, lam, st, cgst)));
-  FRAC_TRY((rows_inv_any<T, IK>(op->logma[0], W1, out, n1, n2, nrows, (int)KB, st, inv)));
+  FRAC_TRY((cols_op<T, ZSYM, ODD>(op, 2, W2, W2, Az, batch, lam, st, cgst)));
+  FRAC_TRY((cols_op<T, YINV, ODD>(op, 1, W2, W1, Ay, batch * n3, lam, st, cgst)));
+  FRAC_TRY((rows_inv_op<T, IK>(op, W1, out, n1, n2, nrows, (int)KB, st, inv)));
   return FRAC_OK;
 }
 

@@ -4,11 +4,13 @@
 //   coefficient a_0, far field F_d (host), and the symbol of the circulant
 //   embedding (separable cosine sums, each axis by an FP64 FFT).
 #include <cmath>
+#include <map>
 #include <mutex>
 #include <type_traits>
 #include <vector>
 
 #include "common.cuh"
+#include "fft_mixed.cuh"
 
 namespace frac {
 
@@ -186,6 +188,50 @@ static int ensure_twiddles(int logm) {
 }
 
 int prepare_twiddles(int logm) { return ensure_twiddles(logm); }
+
+// Tables of the mixed lengths, keyed by (device, M).
+struct TwLenTables {
+  std::mutex mu;
+  std::map<std::pair<int, int64_t>, std::pair<double2*, float2*>> t;
+};
+static TwLenTables g_twl;
+
+int prepare_twiddles_len(int64_t M) {
+  if (M >= 2 && (M & (M - 1)) == 0) return ensure_twiddles(ilog2(M));
+  int dev = 0;
+  FRAC_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_twl.mu);
+  if (g_twl.t.count({dev, M})) return FRAC_OK;
+  std::vector<double2> h;
+  host_twiddles(M, h);
+  std::vector<float2> hf(M);
+  for (int64_t t = 0; t < M; ++t) hf[t] = float2{(float)h[t].x, (float)h[t].y};
+  double2* d64 = nullptr;
+  float2* d32 = nullptr;
+  FRAC_CUDA_TRY(cudaMalloc(&d64, M * sizeof(double2)));
+  FRAC_CUDA_TRY(cudaMalloc(&d32, M * sizeof(float2)));
+  FRAC_CUDA_TRY(cudaMemcpy(d64, h.data(), M * sizeof(double2), cudaMemcpyHostToDevice));
+  FRAC_CUDA_TRY(cudaMemcpy(d32, hf.data(), M * sizeof(float2), cudaMemcpyHostToDevice));
+  g_twl.t[{dev, M}] = {d64, d32};
+  return FRAC_OK;
+}
+
+const double2* twiddles64_len(int64_t M) {
+  if (M >= 2 && (M & (M - 1)) == 0) return twiddles64(ilog2(M));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_twl.mu);
+  auto it = g_twl.t.find({dev, M});
+  return it == g_twl.t.end() ? nullptr : it->second.first;
+}
+const float2* twiddles32_len(int64_t M) {
+  if (M >= 2 && (M & (M - 1)) == 0) return twiddles32(ilog2(M));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_twl.mu);
+  auto it = g_twl.t.find({dev, M});
+  return it == g_twl.t.end() ? nullptr : it->second.second;
+}
 
 const double2* twiddles64(int logm) {
   int dev = 0;
@@ -1080,6 +1126,75 @@ __global__ void __launch_bounds__(256) k_sym_fft(const double* __restrict__ in, 
   }
 }
 
+// The same for an axis of mixed length M (a 7-smooth M that is not a power of two):
+// thread group g of ln.tpl() threads transforms lines 2 q and 2 q + 1 (q = blockIdx.x G
+// + g) as the real and imaginary parts of one complex line with the mixed-radix FFT.
+__global__ void __launch_bounds__(512, 1) k_sym_fft_mx(const double* __restrict__ in, double* __restrict__ out, int64_t A, int64_t n,
+                             int64_t B, int64_t K, fft::MxLine ln, const double2* __restrict__ tw) {
+  extern __shared__ __align__(16) double2 sxm[];
+  const int TPL = ln.tpl(), M = ln.m(), G = blockDim.x / TPL;
+  const int g = threadIdx.x / TPL, tl = threadIdx.x % TPL;
+  const int64_t lines = A * B, L0 = 2 * ((int64_t)blockIdx.x * G + g);
+  double2 v[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const int j = tl + e * TPL, jj = j <= M - j ? j : M - j;
+    double re = 0.0, im = 0.0;
+    if (jj < n) {
+      if (L0 < lines) {
+        const int64_t src = ((L0 / B) * n + jj) * B + L0 % B;
+        if (CHK(src, lines * n)) re = in[src];
+      }
+      if (L0 + 1 < lines) {
+        const int64_t src = (((L0 + 1) / B) * n + jj) * B + (L0 + 1) % B;
+        if (CHK(src, lines * n)) im = in[src];
+      }
+    }
+    v[e] = double2{re, im};
+  }
+  ln.fft<false, false, false>(v, sxm + g * ln.stride(), tl, tw);
+#pragma unroll
+  for (int e = 0; e <= 8; ++e) {
+    const int64_t k = tl + e * TPL;
+    if (k >= K) continue;
+    if (L0 < lines) {
+      const int64_t dst = ((L0 / B) * K + k) * B + L0 % B;
+      if (CHK(dst, lines * K)) out[dst] = v[e].x;
+    }
+    if (L0 + 1 < lines) {
+      const int64_t dst = (((L0 + 1) / B) * K + k) * B + (L0 + 1) % B;
+      if (CHK(dst, lines * K)) out[dst] = v[e].y;
+    }
+  }
+}
+
+// Launches one axis of the symbol (k_sym_fft, or k_sym_fft_mx when plan.m is set).
+static int sym_axis(const double* src, double* dst, int64_t A, int64_t n, int64_t B, int64_t K, int64_t M,
+                    const MxPlan& plan, cudaStream_t st) {
+  if (plan.m == 0) {
+    const int logm = ilog2(M);
+    // 2 LB lines per block, M x LB complex slots (64 KB; one 128 KB line at M = 8192)
+    const int LB = (int)std::max<int64_t>(1, std::min<int64_t>(8, 4096 / M));
+    const size_t fsm = (size_t)M * LB * sizeof(double2);
+    if (fsm > (size_t)kSymFftMaxSmem) return FRAC_ENOTSUP;
+    FRAC_TRY(ensure_twiddles(logm));
+    k_sym_fft<<<(unsigned)((A * B + 2 * LB - 1) / (2 * LB)), 256, fsm, st>>>(src, dst, A, n, B, K, logm, LB,
+                                                                            twiddles64(logm));
+  } else {
+    const fft::MxLine ln(plan);
+    const int G = std::max(1, 256 / ln.tpl());
+    const size_t fsm = (size_t)G * ln.stride() * sizeof(double2);
+    if (fsm > 200 * 1024) return FRAC_ENOTSUP;
+    FRAC_TRY(prepare_twiddles_len(M));
+    FRAC_CUDA_TRY(cudaFuncSetAttribute(k_sym_fft_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    const int64_t pairs = (A * B + 1) / 2;
+    k_sym_fft_mx<<<(unsigned)((pairs + G - 1) / G), G * ln.tpl(), fsm, st>>>(src, dst, A, n, B, K, ln,
+                                                                             twiddles64_len(M));
+  }
+  FRAC_CUDA_TRY(cudaGetLastError());
+  return FRAC_OK;
+}
+
 __global__ void k_scale_symbol(const double* __restrict__ raw, double* __restrict__ l64, float* __restrict__ l32,
                                double scale, int64_t count, double* __restrict__ partial_max) {
   __shared__ double sh[32];
@@ -1172,7 +1287,7 @@ static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int build_coefficients(frac_op* op, cudaStream_t st) {
   FRAC_TRY(upload_rules());
-  for (int i = 0; i < op->prob.d; ++i) FRAC_TRY(ensure_twiddles(op->logma[i]));
+  for (int i = 0; i < op->prob.d; ++i) FRAC_TRY(prepare_twiddles_len(op->Ma[i]));
   const frac_problem& pr = op->prob;
   WParams P;
   P.d = pr.d;
@@ -1265,13 +1380,7 @@ int build_coefficients(frac_op* op, cudaStream_t st) {
   for (int i = 0; i < d; ++i) {
     int64_t A = 1;
     for (int j = i + 1; j < d; ++j) A *= op->na[j];
-    const int64_t Mi = op->Ma[i];
-    // 2 LB lines per block, M x LB complex slots (64 KB; one 128 KB line at M = 8192)
-    const int LB = (int)std::max<int64_t>(1, std::min<int64_t>(8, 4096 / Mi));
-    const size_t fsm = (size_t)Mi * LB * sizeof(double2);
-    k_sym_fft<<<(unsigned)ceil_div(A * B, 2 * LB), 256, fsm, st>>>(bufA, bufB, A, op->na[i], B, op->Ka[i],
-                                                                     op->logma[i], LB, twiddles64(op->logma[i]));
-    FRAC_CUDA_TRY(cudaGetLastError());
+    FRAC_TRY(sym_axis(bufA, bufB, A, op->na[i], B, op->Ka[i], op->Ma[i], op->plan[i], st));
     std::swap(bufA, bufB);
     B *= op->Ka[i];
   }

@@ -84,9 +84,75 @@ inline int ilog2(int64_t m) {
 }
 
 // Twiddle tables exp(-2 pi i t / M), t in [0, M), FP64 and FP32, per M (device-resident,
-// built once per M and device, never freed).
+// built once per M and device, never freed): by log2 M for powers of two, by M for
+// the mixed lengths below (prepare_twiddles_len builds them).
 const double2* twiddles64(int logm);
 const float2* twiddles32(int logm);
+const double2* twiddles64_len(int64_t M);
+const float2* twiddles32_len(int64_t M);
+int prepare_twiddles_len(int64_t M);
+
+// Pass plan of a mixed-radix FFT length M = 2^a 3^b 5^c 7^d, a >= 4 (fft_mixed.cuh):
+// the power-of-two factor in ceil(a / 4) passes of radix up to 16 (bits split as
+// evenly as in fft.cuh, larger first) and one pass per odd factor, executed as: the
+// first power-of-two pass (`first`, from registers), the odd passes (3s, 5s, 7s),
+// the other power-of-two passes but the smallest, and that smallest one (`last`, to
+// registers; 0 when a <= 4 leaves a single power-of-two pass).  count[] holds the
+// middle passes per radix in the order 3, 5, 7, 16, 8, 4, 2; radix[] lists all np
+// passes in execution order.  m = 0: the axis has a power-of-two length (fft.cuh).
+constexpr int kMxMaxPasses = 12;
+struct MxPlan {
+  int m = 0;
+  int np = 0;
+  int8_t radix[kMxMaxPasses] = {};
+  int8_t count[7] = {};
+  int8_t first = 0, last = 0;
+};
+
+// The plan of M; false unless M = 2^a 3^b 5^c 7^d with a >= 4.
+inline bool mx_plan(int64_t M, MxPlan* p) {
+  if (M < 16 || M > (int64_t(1) << 24)) return false;
+  int64_t m = M;
+  int a = 0;
+  while (m % 2 == 0) {
+    m /= 2;
+    ++a;
+  }
+  int odd[kMxMaxPasses], no = 0;
+  for (int q : {3, 5, 7})
+    while (m % q == 0 && no < kMxMaxPasses) {
+      m /= q;
+      odd[no++] = q;
+    }
+  const int np2 = (a + 3) / 4;
+  if (m != 1 || a < 4 || np2 + no > kMxMaxPasses) return false;
+  int p2[4];
+  for (int i = 0; i < np2; ++i) p2[i] = 1 << (a / np2 + (i < a % np2 ? 1 : 0));
+  p->m = (int)M;
+  p->np = 0;
+  for (int c = 0; c < 7; ++c) p->count[c] = 0;
+  p->first = (int8_t)p2[0];
+  p->last = (int8_t)(np2 > 1 ? p2[np2 - 1] : 0);
+  p->radix[p->np++] = p->first;
+  for (int i = 0; i < no; ++i) {  // odd[] is sorted: 3s, then 5s, then 7s
+    p->radix[p->np++] = (int8_t)odd[i];
+    p->count[odd[i] == 3 ? 0 : (odd[i] == 5 ? 1 : 2)] += 1;
+  }
+  for (int i = 1; i + 1 < np2; ++i) {
+    p->radix[p->np++] = (int8_t)p2[i];
+    p->count[p2[i] == 16 ? 3 : (p2[i] == 8 ? 4 : (p2[i] == 4 ? 5 : 6))] += 1;
+  }
+  if (np2 > 1) p->radix[p->np++] = p->last;
+  return true;
+}
+
+// The smallest M >= lo of that form.
+inline int64_t mx_length_at_least(int64_t lo) {
+  for (int64_t M = lo < 16 ? 16 : (lo + 15) / 16 * 16;; M += 16) {
+    MxPlan p;
+    if (mx_plan(M, &p)) return M;
+  }
+}
 
 }  // namespace frac
 
@@ -99,9 +165,11 @@ struct frac_op {
   int logm;
   int64_t K;
   int64_t na[3];     // per axis i < d: interior points n_i (1 for i >= d)
-  int64_t Ma[3];     // FFT length M_i = nextpow2(2 n_i - 1), >= 2 (1 for i >= d)
+  int64_t Ma[3];     // FFT length M_i: nextpow2(2 n_i - 1), >= 2, or (FRAC_FFT_SMOOTH) the smallest
+                     // 2^a 3^b 5^c 7^d >= 2 n_i + 2 with a >= 4 (1 for i >= d)
   int64_t Ka[3];     // M_i / 2 + 1 (1 for i >= d)
-  int logma[3];      // log2 M_i (0 for i >= d)
+  int logma[3];      // log2 M_i (0 for i >= d; -1 where M_i is not a power of two)
+  frac::MxPlan plan[3];  // the pass plan of a 7-smooth M_i that is not a power of two (m = 0 otherwise)
   int square;        // n_i equal on every axis
   int64_t nd;        // prod n_i grid values
   int64_t ngen;      // (N + 1)^d generator entries

@@ -23,6 +23,7 @@
 #pragma once
 
 #include "fft.cuh"
+#include "fft_mixed.cuh"
 
 namespace frac {
 
@@ -58,16 +59,19 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
 // complex FFT -> two half spectra U0 = Z[k] + conj Z[M-k], U1 = -i (Z[k] -
 // conj Z[M-k]), k in [0, M/2] (stored without the 1/2 of the separation; the
 // symbol carries it).  in(row, x) gives the real input at x < n of a row < nrows
-// (called once per such point).  buf: this group's line buffer
-// (line_stride(LOGM) entries); tl: thread index within the group of tpl(LOGM).
+// (called once per such point).  ln: the line policy (fft_mixed.cuh: P2Line for
+// M = 2^LOGM, MxLine for a 7-smooth M); buf: this group's line buffer
+// (ln.stride() entries); tl: thread index within the group of ln.tpl().  The
+// LOGM form is the power-of-two line.
 // ---------------------------------------------------------------------------
-template <typename T, int LOGM, bool ODD = false, typename In>
-__device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t nrows, int KB,
-                                             const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
-                                             int tl, int ns = 0) {
+template <typename T, typename LN, bool ODD = false, typename In>
+__device__ __forceinline__ void row_fwd_pair_l(const LN& ln, In in, cplx_t<T>* W, int n, int64_t nrows, int KB,
+                                               const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
+                                               int tl, int ns = 0) {
   using C = cplx_t<T>;
   using namespace fft;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), B = blk<T>();
+  constexpr int E = LN::E, B = blk<T>();
+  const int M = ln.m(), TPL = ln.tpl();
   const int64_t r0 = 2 * pair, r1 = r0 + 1;
   const bool h0 = r0 < nrows, h1 = r1 < nrows;
   C v[E];
@@ -79,7 +83,7 @@ __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t
       const T im = (x < n && h1) ? in(r1, x) : T(0);
       v[e] = C{re, im};
     }
-    fft_reg<C, LOGM, false, true, false>(v, buf, tl, tw);  // upper half is zero padding
+    ln.template fft<false, true, false>(v, buf, tl, tw);  // upper half is zero padding
   } else {
     // odd extension (n <= M/2 - 1): entry j at x = j + 1, -entry j at x = M - 1 - j,
     // zero at x = 0, M/2 and between; in() is called twice per point here
@@ -96,14 +100,14 @@ __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t
       }
       v[e] = C{re, im};
     }
-    fft_reg<C, LOGM, false, false, false>(v, buf, tl, tw);
+    ln.template fft<false, false, false>(v, buf, tl, tw);
   }
   // separation needs Z[k] and Z[M-k] for k in [0, M/2]: each thread keeps its
   // lower-half Z[k] in registers and reads the mirror from the upper half,
   // which alone goes through the line buffer
   __syncthreads();
 #pragma unroll
-  for (int e = E / 2; e < E; ++e) buf[pidx(tl + e * TPL)] = v[e];
+  for (int e = E / 2; e < E; ++e) buf[ln.pad(tl + e * TPL)] = v[e];
   __syncthreads();
   if (ns <= 0) ns = n;  // rows per slab of W (the next axis' extent; n on square grids)
   C* W0 = W + wrow<B>(h0 ? r0 : 0, ns, KB);
@@ -117,9 +121,15 @@ __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t
 #pragma unroll
   for (int e = 0; e < E / 2; ++e) {
     const int k = tl + e * TPL;  // k < M/2; M - k is in the upper half unless k = 0
-    emit(k, v[e], cconj(k == 0 ? v[e] : buf[pidx(M - k)]));
+    emit(k, v[e], cconj(k == 0 ? v[e] : buf[ln.pad(M - k)]));
   }
   if (tl == 0) emit(M / 2, v[E / 2], cconj(v[E / 2]));
+}
+template <typename T, int LOGM, bool ODD = false, typename In>
+__device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t nrows, int KB,
+                                             const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
+                                             int tl, int ns = 0) {
+  row_fwd_pair_l<T, fft::P2Line<LOGM>, ODD>(fft::P2Line<LOGM>{}, in, W, n, nrows, KB, tw, pair, buf, tl, ns);
 }
 
 // ---------------------------------------------------------------------------
@@ -127,13 +137,14 @@ __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t
 // -> iFFT -> two real rows; out(row, x, value) receives the first n entries
 // of each row < nrows (ODD: entries 1..n, as x = 0..n-1).
 // ---------------------------------------------------------------------------
-template <typename T, int LOGM, bool ODD = false, typename Out>
-__device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t nrows, int KB,
-                                             const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
-                                             int tl, Out out, int ns = 0) {
+template <typename T, typename LN, bool ODD = false, typename Out>
+__device__ __forceinline__ void row_inv_pair_l(const LN& ln, const cplx_t<T>* W, int n, int64_t nrows, int KB,
+                                               const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
+                                               int tl, Out out, int ns = 0) {
   using C = cplx_t<T>;
   using namespace fft;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), B = blk<T>();
+  constexpr int E = LN::E, B = blk<T>();
+  const int M = ln.m(), TPL = ln.tpl();
   const int64_t r0 = 2 * pair, r1 = r0 + 1;
   const bool h0 = r0 < nrows, h1 = r1 < nrows;
   C v[E];
@@ -157,18 +168,18 @@ __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t 
     const int x = tl + e * TPL;  // x < M/2
     C hi;
     load(x, v[e], hi);
-    if (x > 0) buf[pidx(M - x)] = hi;
+    if (x > 0) buf[ln.pad(M - x)] = hi;
   }
   if (tl == 0) {
     C lo, hi;
     load(M / 2, lo, hi);
-    buf[pidx(M / 2)] = lo;
+    buf[ln.pad(M / 2)] = lo;
   }
   __syncthreads();
 #pragma unroll
-  for (int e = E / 2; e < E; ++e) v[e] = buf[pidx(tl + e * TPL)];
+  for (int e = E / 2; e < E; ++e) v[e] = buf[ln.pad(tl + e * TPL)];
   if constexpr (!ODD) {
-    fft_reg<C, LOGM, true, false, true>(v, buf, tl, tw);  // only x < n <= M/2 is kept
+    ln.template fft<true, false, true>(v, buf, tl, tw);  // only x < n <= M/2 is kept
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {
       const int x = tl + e * TPL;
@@ -178,7 +189,7 @@ __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t 
       }
     }
   } else {
-    fft_reg<C, LOGM, true, false, false>(v, buf, tl, tw);  // odd extension: entries 1..n are kept
+    ln.template fft<true, false, false>(v, buf, tl, tw);  // odd extension: entries 1..n are kept
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int x = tl + e * TPL;
@@ -188,6 +199,12 @@ __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t 
       }
     }
   }
+}
+template <typename T, int LOGM, bool ODD = false, typename Out>
+__device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t nrows, int KB,
+                                             const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
+                                             int tl, Out out, int ns = 0) {
+  row_inv_pair_l<T, fft::P2Line<LOGM>, ODD>(fft::P2Line<LOGM>{}, W, n, nrows, KB, tw, pair, buf, tl, out, ns);
 }
 
 // ---------------------------------------------------------------------------
@@ -200,7 +217,7 @@ __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t 
 //                 iFFT, keep n; in place.
 //   YINV (d = 3): slab o = (b, j3): M entries k2 of W2 columns k1, iFFT, first n (j2) to W1.
 // A tile whose column k1 >= K is empty.  sm: the tile's B line buffers of
-// line_stride_tile(LOGM) entries each.  ODD: the odd extension of the n
+// ln.stride_tile() entries each (line_stride_tile(LOGM) for M = 2^LOGM).  ODD: the odd extension of the n
 // entries (the sine-transform embedding of the tau preconditioner) instead of
 // zero padding, and entries 1..n kept.
 // ---------------------------------------------------------------------------
@@ -216,13 +233,14 @@ struct ColArgs {
                        // SYM2: Ky = K_2, the symbol's rows (the symbol is stored in column tiles)
 };
 
-template <typename T, int LOGM, int MODE, bool ODD = false>
-__device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, const ColArgs& A,
-                                         const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, int64_t o,
-                                         int64_t tile, cplx_t<T>* sm, int cl, int tl) {
+template <typename T, typename LN, int MODE, bool ODD = false>
+__device__ __forceinline__ void col_tile_l(const LN& ln, const cplx_t<T>* in, cplx_t<T>* out, const ColArgs& A,
+                                           const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, int64_t o,
+                                           int64_t tile, cplx_t<T>* sm, int cl, int tl) {
   using C = cplx_t<T>;
   using namespace fft;
-  constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LS = line_stride_tile(LOGM), B = blk<T>();
+  constexpr int E = LN::E, B = blk<T>();
+  const int M = ln.m(), TPL = ln.tpl(), LS = ln.stride_tile();
   C* buf = sm + cl * LS;
   const int n = A.n, K = A.K, KB = A.KB, Kp = KB * B;
   const int64_t nB = (int64_t)n * B;              // W1 slab rows (SYM2, YFWD, YINV: j2) / W2 rows (ZSYM: j3)
@@ -273,8 +291,7 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
     }
   }
   // ---- transforms
-  constexpr int SH = tile_shift(LOGM);
-  if (MODE != YINV) fft_reg<C, LOGM, false, !ODD, false, SH>(v, buf, tl, tw);
+  if (MODE != YINV) ln.template fft<false, !ODD, false>(v, buf, tl, tw);
   if (MODE == SYM2 || MODE == ZSYM) {
     // the symbol in column tiles, so that the B lanes of a row read one contiguous run:
     // SYM2 entry (kr, k1) at (k1 / B) K_2 B + kr B + k1 % B; ZSYM entry (k3r, k2r, k1) at
@@ -289,7 +306,7 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
       v[e] = cscale(v[e], live ? lrow[kr * kstride] : T(0));
     }
   }
-  if (MODE != YFWD) fft_reg<C, LOGM, true, false, !ODD, SH>(v, buf, tl, tw);  // keeps j < n (ODD: 1..n) only
+  if (MODE != YFWD) ln.template fft<true, false, !ODD>(v, buf, tl, tw);  // keeps j < n (ODD: 1..n) only
   // ---- store
   if (!live) return;
   if (MODE == YFWD) {
@@ -317,6 +334,13 @@ __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, co
       }
     }
   }
+}
+template <typename T, int LOGM, int MODE, bool ODD = false>
+__device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, const ColArgs& A,
+                                         const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, int64_t o,
+                                         int64_t tile, cplx_t<T>* sm, int cl, int tl) {
+  using LN = fft::P2Line<LOGM, fft::tile_shift(LOGM)>;
+  col_tile_l<T, LN, MODE, ODD>(LN{}, in, out, A, lam, tw, o, tile, sm, cl, tl);
 }
 
 }  // namespace frac

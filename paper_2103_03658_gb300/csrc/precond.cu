@@ -14,7 +14,7 @@ template <typename T>
 int precond_t(const frac_op* op, const T* r, T* z, int64_t batch, void* ws, cudaStream_t st) {
   if (!op->precond_ok) return FRAC_ENOTSUP;
   if (batch <= 0) return FRAC_OK;
-  if (op->prob.d == 1) return conv1d_any<T, true>(op->logm, r, z, op->n, batch, pinv_table<T>(op), st);
+  if (op->prob.d == 1) return conv1d_op<T, true>(op, r, z, batch, pinv_table<T>(op), st);
   return pipeline<T, RF_ODD, RI_ODD, true>(op, pinv_table<T>(op), r, z, batch, ws, CgArgs{}, CgArgs{}, nullptr, st);
 }
 

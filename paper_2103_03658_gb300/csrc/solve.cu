@@ -18,6 +18,7 @@
 #include <mutex>
 #include <new>
 #include <thread>
+#include <map>
 #include <vector>
 
 #include "apply.cuh"
@@ -342,7 +343,7 @@ static int solve_1d(const frac_op* op, const double* f, double* u, const frac_so
   FRAC_TRY(ws.get(&di, sizeof(frac_solve_info)));
   Solve1dTask t = make_task1d(op, f, u, di, opts);
   FRAC_CUDA_TRY(cudaMemcpyAsync(dt, &t, sizeof(t), cudaMemcpyHostToDevice, st));
-  FRAC_TRY(solve1d_launch(op->logm, opts->precision == FRAC_MIXED_IR, dt, 1, st));
+  FRAC_TRY(solve1d_launch(op->M, opts->precision == FRAC_MIXED_IR, dt, 1, st));
   FRAC_CUDA_TRY(cudaMemcpyAsync(info, di, sizeof(frac_solve_info), cudaMemcpyDeviceToHost, st));
   FRAC_CUDA_TRY(cudaStreamSynchronize(st));
   if (info->status == FRAC_EINVAL) {  // non-finite data: report through rel_resid as the other paths do
@@ -382,17 +383,16 @@ int solve_batch_1d(int64_t count, const frac_op* const* ops, const double* const
                    const frac_solve_opts* opts, const int64_t* idx, cudaStream_t st, BatchPending* pend) {
   // group the listed problems by FFT length; one launch per group, largest first
   pend->st = st;
-  std::vector<std::vector<int64_t>> groups(14);
-  for (int64_t t = 0; t < count; ++t) groups[ops[idx[t]]->logm].push_back(idx[t]);
+  std::map<int64_t, std::vector<int64_t>> groups;  // M -> problems
+  for (int64_t t = 0; t < count; ++t) groups[ops[idx[t]]->M].push_back(idx[t]);
   Solve1dTask* dt;
   FRAC_TRY(pend->alloc(&pend->dinfo, count * sizeof(frac_solve_info)));
   FRAC_TRY(pend->alloc(&dt, count * sizeof(Solve1dTask)));
   std::vector<Solve1dTask> tasks;
-  std::vector<std::pair<int, int64_t>> launches;  // (logm, first task)
-  for (int lg = 13; lg >= 1; --lg) {
-    if (groups[lg].empty()) continue;
-    launches.emplace_back(lg, (int64_t)tasks.size());
-    for (int64_t i : groups[lg]) {
+  std::vector<std::pair<int64_t, int64_t>> launches;  // (M, first task)
+  for (auto g = groups.rbegin(); g != groups.rend(); ++g) {
+    launches.emplace_back(g->first, (int64_t)tasks.size());
+    for (int64_t i : g->second) {
       const frac_op* op = ops[i];
       tasks.push_back(make_task1d(op, f[i], u[i], pend->dinfo + tasks.size(), opts));
       pend->order.push_back(i);
@@ -844,7 +844,7 @@ static int submit_impl(frac_engine* e, Job* j, const double* f, double* u) {
     FRAC_TRY(jalloc(j, &j->dtask, sizeof(Solve1dTask)));
     j->hm->task = make_task1d(op, j->f, j->u, j->dinfo, &j->opts);
     FRAC_CUDA_TRY(cudaMemcpyAsync(j->dtask, &j->hm->task, sizeof(Solve1dTask), cudaMemcpyHostToDevice, j->s));
-    FRAC_TRY(solve1d_launch(op->logm, j->opts.precision == FRAC_MIXED_IR, j->dtask, 1, j->s));
+    FRAC_TRY(solve1d_launch(op->M, j->opts.precision == FRAC_MIXED_IR, j->dtask, 1, j->s));
     FRAC_CUDA_TRY(cudaMemcpyAsync(&j->hm->info, j->dinfo, sizeof(frac_solve_info), cudaMemcpyDeviceToHost, j->s));
     FRAC_CUDA_TRY(cudaEventRecord(j->ev, j->s));
     j->phase = PH_WHOLE1D;

@@ -25,7 +25,10 @@ inline Solve1dTask make_task1d(const frac_op* op, const double* f, double* u, fr
                      (o->precond == FRAC_PRECOND_TAU && op->precond_ok) ? 1 : 0};
 }
 
-// Launch one block per task; all tasks share FFT length 2^logm (<= 8192).
-int solve1d_launch(int logm, bool mixed, const Solve1dTask* d_tasks, int ntasks, cudaStream_t st);
+// Launch one block per task; all tasks share FFT length M (a power of two or a
+// 7-smooth mixed length, <= 8192).
+int solve1d_launch(int64_t M, bool mixed, const Solve1dTask* d_tasks, int ntasks, cudaStream_t st);
+// The same for a mixed length (solve1d_mx.cu).
+int solve1d_launch_mx(int64_t M, bool mixed, const Solve1dTask* d_tasks, int ntasks, cudaStream_t st);
 
 }  // namespace frac

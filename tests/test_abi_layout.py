@@ -20,7 +20,8 @@ class KernelStat(ctypes.Structure):  # as bench.py reads frac_profile_read
 # C struct name -> (ctypes class, [(C field, ctypes field)])
 STRUCTS = {
     "frac_problem": (nat.Problem, [("d", "d"), ("degree", "degree"), ("alpha", "alpha"), ("h", "h"), ("n", "n"),
-                                   ("lambda", "lam"), ("gamma", "gamma")]),
+                                   ("lambda", "lam"), ("gamma", "gamma"),
+                                   ("fft_lengths", "fft_lengths")]),
     "frac_op_info_t": (nat.OpInfo, [(f, f) for f, _ in nat.OpInfo._fields_]),
     "frac_solve_opts": (nat.SolveOpts, [(f, f) for f, _ in nat.SolveOpts._fields_]),
     "frac_solve_info": (nat.SolveInfo, [(f, f) for f, _ in nat.SolveInfo._fields_]),
