@@ -479,7 +479,49 @@ def extra_measurements(fg, torch, u32, op, barrier) -> dict:
     out["operator_builds"] = build_measurement(fg, barrier)
     out["boundary"] = boundary_measurement(fg, torch, barrier)
     out["batch"] = batch_measurement(fg, torch, barrier)
+    out["batch_fft_auto"] = batch_measurement(fg, torch, barrier, fft="auto")
+    out["mixed_radix"] = mixed_radix_measurement(fg, torch, barrier)
     out["served"] = served_measurement(fg, torch, barrier)
+    return out
+
+
+def mixed_radix_measurement(fg, torch, barrier) -> dict:
+    """The same problems on power-of-two and on mixed-radix (7-smooth) FFT lengths: FP32
+    and FP64 applies (CUDA events over 10 applies of a batch of fields, alpha = 1.3,
+    p = 1) and a mixed-precision solve to 1e-10; the length "auto" picks is reported."""
+    out = {}
+    for d, n, batch in ((1, 1100, 512), (2, 300, 64), (2, 600, 64), (2, 700, 16), (3, 200, 2)):
+        row = {"auto_picks": fg.fft_length(n, d, "auto")}
+        for fft in ("pow2", "smooth"):
+            op = fg.FracOp(d, n, 1.3, degree=1, fft=fft)
+            rec = {"fft_len": op.info()["fft_lens"][0]}
+            g = torch.Generator(device="cuda").manual_seed(d * 1000 + n)
+            u32 = torch.randn((batch,) + (n,) * d, device="cuda", generator=g)
+            for dt, key in ((torch.float32, "apply_f32_ms"), (torch.float64, "apply_f64_ms")):
+                u = u32.to(dt)
+                y = torch.empty_like(u)
+                for _ in range(2):
+                    op.apply(u, out=y)
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(10):
+                    op.apply(u, out=y)
+                e1.record()
+                barrier()
+                rec[key] = e0.elapsed_time(e1) / 10
+            f = u32[0].double()
+            op.solve(f, rtol=1e-10)
+            barrier()
+            t0 = time.perf_counter()
+            _, info = op.solve(f, rtol=1e-10)
+            barrier()
+            rec["solve_mixed_ms"] = 1e3 * (time.perf_counter() - t0)
+            rec["solve_iters"] = info["iters"]
+            rec["solve_rel_resid"] = info["rel_resid"]
+            row[fft] = rec
+            op.close()
+        out[f"{d}d_n{n}_b{batch}"] = row
     return out
 
 
@@ -569,16 +611,18 @@ def build_measurement(fg, barrier) -> dict:
     return out
 
 
-def batch_measurement(fg, torch, barrier) -> dict:
+def batch_measurement(fg, torch, barrier, fft: str = "pow2") -> dict:
     """256 mixed problems (d in {1, 2}, 1D n in [63, 4095], 2D side in [63, 511],
     alpha ~ U(0.1, 1.9), p in {0, 1, 2}, lambda ~ U(0, 2), smooth random right-hand
     sides) solved by one frac_solve_batch call, FP32 CG in FP64 refinement to 1e-10:
-    1D problems one block each (one launch per FFT length), 2D problems in one
-    persistent cluster launch.  The warm-up batch holds one problem of every FFT
-    length, so the autotuner's one-time timings fall outside the timed call."""
+    1D problems one block each (one launch per FFT length), 2D problems of
+    power-of-two lengths in one persistent cluster launch (mixed lengths, with fft
+    "auto" or "smooth", through the solve engine).  The warm-up batch holds one
+    problem of every FFT length, so the autotuner's one-time timings fall outside the
+    timed call."""
     probs = synth.batch_problems(256)
     t0 = time.perf_counter()
-    ops = [fg.FracOp(p.d, p.n, p.alpha, degree=p.degree, lam=p.lam) for p in probs]
+    ops = [fg.FracOp(p.d, p.n, p.alpha, degree=p.degree, lam=p.lam, fft=fft) for p in probs]
     barrier()
     t_coeff = time.perf_counter() - t0
     fs = [torch.tensor(synth.smooth_field(p.d, p.n, p.seed) + 0.25, device="cuda") for p in probs]
@@ -598,9 +642,11 @@ def batch_measurement(fg, torch, barrier) -> dict:
     plan = fg.batch_last_plan()
     dof = sum(p.n ** p.d for p in probs)
     ok = sum(1 for i in infos if i["status"] == 0 and i["rel_resid"] <= 1e-10)
+    mixed = sum(1 for op in ops if any(m & (m - 1) for m in op.info()["fft_lens"]))
     for op in ops:
         op.close()
-    return {"problems": len(probs), "converged": ok, "solves_per_s": len(probs) / dt, "ms": 1e3 * dt,
+    return {"problems": len(probs), "fft_lengths": fft, "mixed_length_problems": mixed, "converged": ok,
+            "solves_per_s": len(probs) / dt, "ms": 1e3 * dt,
             "dof_total": dof, "iters_total": int(sum(i["iters"] for i in infos)),
             "coefficient_build_ms_all_ops": 1e3 * t_coeff, "warmup_incl_autotune_ms": 1e3 * t_warm,
             "persistent_2d_plan": plan}

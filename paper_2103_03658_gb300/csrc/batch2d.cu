@@ -27,371 +27,18 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
-#include "apply.cuh"
-#include "batch2d.cuh"
-#include "passes.cuh"
+#include "batch2d_kernel.cuh"
 #include "prof.cuh"
 
 namespace frac {
 namespace {
 
+using namespace b2;
 using namespace fft;
-
-constexpr int kThreads = 512;
-
-struct B2Prob {
-  const double* f;
-  double* u;
-  const float* lam32;
-  const double* lam64;
-  const float* pinv32;  // tau preconditioner symbol (pcg)
-  int n, logm, max_iter, use_x0, pcg;
-  double rtol, inner_tol;
-};
-
-// Scratch of one worker (a cluster or a CTA), sized for its largest problem.
-struct B2Slot {
-  void* W;  // spectrum, FP64 layout n ceil(K/2) 2 complex doubles; the FP32 passes use its front
-  float *x, *r, *p, *q;
-  double* r64;
-};
-
-struct B2Args {
-  const B2Prob* probs;
-  frac_solve_info* info;  // per problem
-  int n_cluster, n_local; // probs[0, n_cluster) cluster-wide, then n_local CTA-local
-  unsigned int* next;     // queue heads: [0] cluster, [1] local
-  const B2Slot* cslots;   // per cluster
-  const B2Slot* lslots;   // per CTA
-  const float2* tw32[kBatch2dMaxLog + 1];
-  const double2* tw64[kBatch2dMaxLog + 1];
-};
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-struct Group {
-  int G, rank;  // CTAs on the problem, this CTA's rank among them
-  __device__ __forceinline__ void sync() const {
-    if (G > 1)
-      cluster_sync_all();
-    else
-      __syncthreads();
-  }
-};
-
-// Sum over the group, identical in every thread of every CTA of the group:
-// block sum, then (cluster) each CTA's total from the shared memory of ranks
-// 0..G-1 in order.  Two slots alternate, so a slot is rewritten only after
-// the next reduction's barrier, when every reader is done with it.
-__device__ double group_sum(double v, const Group& g, double* red, double* slots, int& parity) {
-  const double s = block_sum_all(v, red);
-  if (g.G == 1) return s;
-  double* slot = slots + parity;
-  parity ^= 1;
-  if (threadIdx.x == 0) *slot = s;
-  cluster_sync_all();
-  double t = 0.0;
-  for (int r = 0; r < g.G; ++r) t += *static_cast<volatile double*>(__cluster_map_shared_rank((void*)slot, r));
-  return t;
-}
-
-// One problem on one group (cluster or CTA).  The three steps of the
-// refinement are separate (non-inlined) functions, so the FP32 CG loop gets
-// its own register allocation instead of sharing one with the FP64 passes.
-// (Inlined, they once computed a wrong inverse row pass at M = 32: the FFT's
-// shared line buffer was a __restrict__ parameter, which let the compiler move
-// its accesses across the block barriers; the buffer is no longer restrict and
-// the inlined build is exact.)
-struct Ctx {
-  const B2Prob* P;
-  const B2Slot* S;
-  Group g;
-  const float2* tw32;
-  const double2* tw64;
-  unsigned char* smem;
-  double* red;
-  double* slots;
-  int parity;
-};
-
-template <int LOGM>
-struct Solver {
-  static constexpr int M = 1 << LOGM, E = elems(LOGM), TPL = tpl(LOGM), LINES = kThreads / TPL;
-  static constexpr int LS = line_stride(LOGM), LST = line_stride_tile(LOGM);
-  static constexpr int K = M / 2 + 1, KB32 = (K + 3) / 4, KB64 = (K + 1) / 2;
-  static constexpr int TPR32 = kThreads / (4 * TPL), TPR64 = kThreads / (2 * TPL);  // column tiles per CTA round
-
-  static __device__ __forceinline__ int rrounds(const Ctx& c) {
-    const int npairs = (c.P->n + 1) / 2;
-    return (npairs + c.g.G * LINES - 1) / (c.g.G * LINES);
-  }
-  static __device__ __forceinline__ int64_t pair_of(const Ctx& c, int i) {
-    return ((int64_t)i * c.g.G + c.g.rank) * LINES + threadIdx.x / TPL;
-  }
-  // the points of this thread: those its row passes read and write
-  template <typename Fn>
-  static __device__ __forceinline__ void for_own(const Ctx& c, Fn fn) {
-    const int n = c.P->n, tl = threadIdx.x % TPL, rr = rrounds(c);
-    for (int i = 0; i < rr; ++i) {
-      const int64_t r0 = 2 * pair_of(c, i);
-#pragma unroll
-      for (int e = 0; e < E / 2; ++e) {
-        const int x = tl + e * TPL;
-        if (x < n) {
-          if (r0 < n) fn(r0 * n + x);
-          if (r0 + 1 < n) fn((r0 + 1) * n + x);
-        }
-      }
-    }
-  }
-  static __device__ __forceinline__ double gsum(Ctx& c, double v) {
-    return group_sum(v, c.g, c.red, c.slots, c.parity);
-  }
-
-  // ||f||^2, and u = 0 unless it is the initial guess; with u = 0 the first residual is f
-  // itself (R64 = F), which spares an FP64 apply
-  static __device__ __noinline__ double start(Ctx& c) {
-    const double* F = c.P->f;
-    double* U = c.P->u;
-    double* R64 = c.S->r64;
-    const bool zero = !c.P->use_x0;
-    double ff = 0.0;
-    for_own(c, [&](int64_t k) {
-      const double fv = F[k];
-      ff += fv * fv;
-      if (zero) {
-        U[k] = 0.0;
-        R64[k] = fv;
-      }
-    });
-    return gsum(c, ff);
-  }
-
-  // R64 = F - A64 U (FP64 passes); returns ||R64||^2
-  static __device__ __noinline__ double residual(Ctx& c) {
-    const int n = c.P->n, tid = threadIdx.x, tl = tid % TPL, rr = rrounds(c);
-    const double* F = c.P->f;
-    const double* U = c.P->u;
-    double* R64 = c.S->r64;
-    double2* W = static_cast<double2*>(c.S->W);
-    double2* rb = reinterpret_cast<double2*>(c.smem) + (tid / TPL) * LS;
-    for (int i = 0; i < rr; ++i)
-      row_fwd_pair<double, LOGM>([&](int64_t row, int x) { return U[row * n + x]; }, W, n, n, KB64, c.tw64,
-                                 pair_of(c, i), rb, tl);
-    c.g.sync();
-    {
-      const ColArgs A{n, K, KB64, KB64, 1, 0, 0, K};
-      const int ts = tid / (2 * TPL), w = tid % (2 * TPL);
-      const int cr = (KB64 + c.g.G * TPR64 - 1) / (c.g.G * TPR64);
-      for (int i = 0; i < cr; ++i)
-        col_tile<double, LOGM, SYM2>(W, W, A, c.P->lam64, c.tw64, 0, ((int64_t)i * c.g.G + c.g.rank) * TPR64 + ts,
-                                     reinterpret_cast<double2*>(c.smem) + ts * 2 * LST, w % 2, w / 2);
-    }
-    c.g.sync();
-    double part = 0.0;
-    for (int i = 0; i < rr; ++i)
-      row_inv_pair<double, LOGM>(W, n, n, KB64, c.tw64, pair_of(c, i), rb, tl, [&](int64_t row, int x, double v) {
-        const double rv = F[row * n + x] - v;
-        R64[row * n + x] = rv;
-        part += rv * rv;
-      });
-    return gsum(c, part);
-  }
-
-  // Z = P R (tau preconditioner, FP32 passes on the odd extension; Z in the
-  // storage of Q, which is dead once R is updated); returns the group sum of
-  // R.Z.  The odd passes read entries that other threads of the CTA own; the
-  // block barriers of the group sums before and after order those accesses.
-  static __device__ __forceinline__ double precond(Ctx& c) {
-    const int n = c.P->n, tid = threadIdx.x, tl = tid % TPL, rr = rrounds(c);
-    const float* R = c.S->r;
-    float* Z = c.S->q;
-    float2* W = static_cast<float2*>(c.S->W);
-    float2* rb = reinterpret_cast<float2*>(c.smem) + (tid / TPL) * LS;
-    for (int i = 0; i < rr; ++i)
-      row_fwd_pair<float, LOGM, true>([&](int64_t row, int x) { return R[row * n + x]; }, W, n, n, KB32, c.tw32,
-                                      pair_of(c, i), rb, tl);
-    c.g.sync();
-    {
-      const ColArgs A{n, K, KB32, KB32, 1, 0, 0, K};
-      const int ts = tid / (4 * TPL), w = tid % (4 * TPL);
-      const int cr = (KB32 + c.g.G * TPR32 - 1) / (c.g.G * TPR32);
-      for (int i = 0; i < cr; ++i)
-        col_tile<float, LOGM, SYM2, true>(W, W, A, c.P->pinv32, c.tw32, 0,
-                                          ((int64_t)i * c.g.G + c.g.rank) * TPR32 + ts,
-                                          reinterpret_cast<float2*>(c.smem) + ts * 4 * LST, w % 4, w / 4);
-    }
-    c.g.sync();
-    float s = 0.0f;
-    for (int i = 0; i < rr; ++i)
-      row_inv_pair<float, LOGM, true>(W, n, n, KB32, c.tw32, pair_of(c, i), rb, tl, [&](int64_t row, int x, float v) {
-        Z[row * n + x] = v;
-        s += v * R[row * n + x];
-      });
-    return gsum(c, s);
-  }
-
-  // FP32 CG (preconditioned when pcg) on A d = R64 / ||R64|| (||R64||^2 = rn2)
-  // to a relative reduction inner_tol, then U += ||R64|| d.  Returns the
-  // iteration count after it.
-  static __device__ __noinline__ int inner(Ctx& c, double rn2, int iters) {
-    const int n = c.P->n, tid = threadIdx.x, tl = tid % TPL, rr = rrounds(c), max_iter = c.P->max_iter;
-    const double* R64 = c.S->r64;
-    double* U = c.P->u;
-    float* X = c.S->x;
-    float* R = c.S->r;
-    float* Pv = c.S->p;
-    float* Q = c.S->q;
-    float2* W = static_cast<float2*>(c.S->W);
-    float2* rb = reinterpret_cast<float2*>(c.smem) + (tid / TPL) * LS;
-    const ColArgs A{n, K, KB32, KB32, 1, 0, 0, K};
-    const int ts = tid / (4 * TPL), w = tid % (4 * TPL);
-    const int cr = (KB32 + c.g.G * TPR32 - 1) / (c.g.G * TPR32);
-    const double sc = 1.0 / sqrt(rn2);
-    float rf = 0.0f;
-    for_own(c, [&](int64_t k) {
-      const float rv = (float)(R64[k] * sc);
-      R[k] = rv;
-      X[k] = 0.0f;
-      rf += rv * rv;
-    });
-    double rrv = gsum(c, rf);
-    const double stop = c.P->inner_tol * c.P->inner_tol * rrv;
-    const bool pcg = c.P->pcg;
-    const float* Zs = pcg ? Q : R;  // the vector the direction is built from
-    double rz = (pcg && rrv > stop) ? precond(c) : rrv;
-    bool first = true;
-    float be = 0.0f;
-    while (rrv > stop && iters < max_iter) {
-      for (int i = 0; i < rr; ++i)
-        row_fwd_pair<float, LOGM>(
-            [&](int64_t row, int x) {
-              const int64_t k = row * n + x;
-              const float v = first ? Zs[k] : Zs[k] + be * Pv[k];
-              Pv[k] = v;
-              return v;
-            },
-            W, n, n, KB32, c.tw32, pair_of(c, i), rb, tl);
-      c.g.sync();
-      for (int i = 0; i < cr; ++i)
-        col_tile<float, LOGM, SYM2>(W, W, A, c.P->lam32, c.tw32, 0, ((int64_t)i * c.g.G + c.g.rank) * TPR32 + ts,
-                                    reinterpret_cast<float2*>(c.smem) + ts * 4 * LST, w % 4, w / 4);
-      c.g.sync();
-      float pqf = 0.0f;
-      for (int i = 0; i < rr; ++i)
-        row_inv_pair<float, LOGM>(W, n, n, KB32, c.tw32, pair_of(c, i), rb, tl, [&](int64_t row, int x, float v) {
-          const int64_t k = row * n + x;
-          Q[k] = v;
-          pqf += v * Pv[k];
-        });
-      const double pq = gsum(c, pqf);
-      if (!(pq > 0.0) || !isfinite(pq)) break;  // inner breakdown: refine from here
-      const float al = (float)(rz / pq);
-      float rf1 = 0.0f;
-      for_own(c, [&](int64_t k) {
-        X[k] += al * Pv[k];
-        const float rv = R[k] - al * Q[k];
-        R[k] = rv;
-        rf1 += rv * rv;
-      });
-      rrv = gsum(c, rf1);
-      first = false;
-      ++iters;
-      if (!(rrv > stop)) break;
-      const double rz1 = pcg ? precond(c) : rrv;
-      be = (float)(rz1 / rz);
-      rz = rz1;
-    }
-    const double s = sqrt(rn2);
-    for_own(c, [&](int64_t k) { U[k] += s * (double)X[k]; });
-    return iters;
-  }
-
-  // mixed-precision refinement to ||f - A u|| <= rtol ||f||
-  static __device__ __noinline__ void solve(Ctx& c, frac_solve_info* info) {
-    const double fn2 = start(c);
-    const double tol2 = c.P->rtol * c.P->rtol * fn2;
-    int iters = 0, outer = 0, status = FRAC_OK;
-    double rn2 = 0.0;
-    if (fn2 != 0.0) {
-      rn2 = c.P->use_x0 ? residual(c) : fn2;  // u = 0: R64 = f, set by start()
-      double prev = INFINITY;
-      while (rn2 > tol2 && iters < c.P->max_iter && outer < 100) {
-        iters = inner(c, rn2, iters);
-        rn2 = residual(c);
-        ++outer;
-        if (!(rn2 < prev) && outer > 3) break;  // refinement stagnated
-        prev = rn2;
-      }
-    }
-    if (c.g.rank == 0 && threadIdx.x == 0) {
-      frac_solve_info out;
-      out.iters = iters;
-      out.outer = outer;
-      out.precond = c.P->pcg;
-      out.rel_resid = fn2 > 0.0 ? sqrt(rn2 / fn2) : (fn2 == 0.0 ? 0.0 : NAN);  // NaN: non-finite f
-      if (status == FRAC_OK && !(out.rel_resid <= c.P->rtol)) status = FRAC_ENOCONV;
-      if (!isfinite(out.rel_resid)) status = FRAC_EINVAL;
-      out.status = status;
-      *info = out;
-    }
-  }
-};
-
-__device__ void solve_any(const B2Args& A, int item, const B2Slot& S, const Group g, unsigned char* smem,
-                          double* red, double* slots) {
-  const B2Prob& P = A.probs[item];
-  frac_solve_info* info = A.info + item;
-  Ctx c{&P, &S, g, nullptr, nullptr, smem, red, slots, 0};
-  switch (P.logm) {  // uniform over the group
-#define FRAC_B2_CASE(L)       \
-  case L:                     \
-    c.tw32 = A.tw32[L];       \
-    c.tw64 = A.tw64[L];       \
-    Solver<L>::solve(c, info); \
-    break;
-    FRAC_B2_CASE(5)
-    FRAC_B2_CASE(6)
-    FRAC_B2_CASE(7)
-    FRAC_B2_CASE(8)
-    FRAC_B2_CASE(9)
-    FRAC_B2_CASE(10)
-#undef FRAC_B2_CASE
-    default: break;
-  }
-}
-
-__global__ void __launch_bounds__(kThreads, 1) k_batch2d(B2Args A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32];
-  __shared__ double slots[2];
-  __shared__ unsigned int s_item;
-  const int C = (int)__clusterSizeInBlocks(), rank = (int)__clusterRelativeBlockRank();
-  const int cid = (int)(blockIdx.x / C);
-  // cluster-wide problems: rank 0 takes the next one, every CTA reads it from rank 0
-  while (true) {
-    if (rank == 0 && threadIdx.x == 0) s_item = atomicAdd(A.next, 1u);
-    cluster_sync_all();
-    const unsigned int item = *static_cast<volatile unsigned int*>(__cluster_map_shared_rank((void*)&s_item, 0));
-    cluster_sync_all();  // every read of rank 0's slot is done before it changes or its CTA moves on
-    if (item >= (unsigned int)A.n_cluster) break;
-    solve_any(A, (int)item, A.cslots[cid], Group{C, rank}, smem, red, slots);
-  }
-  // then one problem per CTA
-  while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(A.next + 1, 1u);
-    __syncthreads();
-    const unsigned int item = s_item;
-    __syncthreads();
-    if (item >= (unsigned int)A.n_local) break;
-    solve_any(A, A.n_cluster + (int)item, A.lslots[blockIdx.x], Group{1, 0}, smem, red, slots);
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -401,21 +48,38 @@ constexpr int kProbeIters = 24;
 constexpr int kClusterSizes[] = {1, 2, 4, 8, 16};
 constexpr int kNumSizes = 5;
 
-size_t smem_bytes(int logm) {
-  const int tplv = tpl(logm), lines = kThreads / tplv;
-  const size_t rows = (size_t)lines * line_stride(logm) * sizeof(double2);
-  const size_t cols = (size_t)(kThreads / tplv) * line_stride_tile(logm) * sizeof(double2);
+// Problem classes are FFT lengths M (a power of two 2^5 .. 2^10 or a mixed length up
+// to 2^10); lvl(M) = ceil(log2 M) orders them against the cluster cut-over.
+bool is_pow2(int64_t M) { return (M & (M - 1)) == 0; }
+int lvl(int64_t M) { return ilog2(M); }
+
+// Dynamic shared memory of one CTA for a class: the row lines or the column tiles of
+// its FP64 passes (FP32 ones take half); a mixed length adds the spare line and tile.
+size_t smem_bytes(int64_t M) {  // M: a power of two or a length with a plan
+  if (is_pow2(M)) {
+    const int logm = ilog2(M);
+    const int tplv = tpl(logm), lines = kThreads / tplv;
+    const size_t rows = (size_t)lines * line_stride(logm) * sizeof(double2);
+    const size_t cols = (size_t)(kThreads / tplv) * line_stride_tile(logm) * sizeof(double2);
+    return std::max(rows, cols);
+  }
+  MxPlan plan;
+  mx_plan(M, &plan);
+  const MxLine ln(plan);
+  const int lines = kThreads / ln.tpl(), tpr64 = kThreads / (2 * ln.tpl());
+  const size_t rows = (size_t)(lines + 1) * ln.stride() * sizeof(double2);
+  const size_t cols = (size_t)(tpr64 + 1) * 2 * ln.stride_tile() * sizeof(double2);
   return std::max(rows, cols);
 }
 
-size_t slot_bytes(int n, int logm) {
-  const int64_t K = (int64_t(1) << logm) / 2 + 1, KB64 = (K + 1) / 2, nn = (int64_t)n * n;
+size_t slot_bytes(int n, int64_t M) {
+  const int64_t K = M / 2 + 1, KB64 = (K + 1) / 2, nn = (int64_t)n * n;
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   return al((size_t)n * KB64 * 2 * sizeof(double2)) + 4 * al(nn * sizeof(float)) + al(nn * sizeof(double));
 }
 
-B2Slot carve(unsigned char* base, int n, int logm) {
-  const int64_t K = (int64_t(1) << logm) / 2 + 1, KB64 = (K + 1) / 2, nn = (int64_t)n * n;
+B2Slot carve(unsigned char* base, int n, int64_t M) {
+  const int64_t K = M / 2 + 1, KB64 = (K + 1) / 2, nn = (int64_t)n * n;
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   B2Slot s;
   s.W = base;
@@ -457,58 +121,27 @@ int configure_kernel() {
   std::lock_guard<std::mutex> lk(mu);
   if ((int)done.size() <= dev) done.resize(dev + 1, 0);
   if (!done[dev]) {
+    // the largest over every length the kernel takes (powers of two and mixed lengths)
     size_t mx = 0;
-    for (int l = kBatch2dMinLog; l <= kBatch2dMaxLog; ++l) mx = std::max(mx, smem_bytes(l));
-    FRAC_CUDA_TRY(cudaFuncSetAttribute(k_batch2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
-    FRAC_CUDA_TRY(cudaFuncSetAttribute(k_batch2d, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    for (int64_t M = 1 << kBatch2dMinLog; M <= (1 << kBatch2dMaxLog); M += 16) {
+      MxPlan plan;
+      if (is_pow2(M) || mx_plan(M, &plan)) mx = std::max(mx, smem_bytes(M));
+    }
+    FRAC_TRY(kernel_attrs<false>(mx));
+    FRAC_TRY(mx_kernel_attrs(mx));
     done[dev] = 1;
   }
   return FRAC_OK;
 }
 
-// Clusters of size C that can be resident at once (0: C not launchable).
-int active_clusters(int C, size_t smem) {
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = C;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(C);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  int num = 0;
-  if (cudaOccupancyMaxActiveClusters(&num, k_batch2d, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return num;
+// Clusters of size C that can be resident at once, and the launch, of the kernel
+// instance without (mx = false) or with the mixed-length solver.
+int active_clusters(int C, size_t smem, bool mx) {
+  return mx ? mx_kernel_active_clusters(C, smem) : kernel_active_clusters<false>(C, smem);
 }
 
-int launch(const B2Args& a, int C, int grid, size_t smem, cudaStream_t st) {
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = C;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  FRAC_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_batch2d, a));
-  return FRAC_OK;
-}
-
-void fill_twiddles(B2Args& a) {
-  for (int l = 0; l <= kBatch2dMaxLog; ++l) {
-    a.tw32[l] = l >= kBatch2dMinLog ? twiddles32(l) : nullptr;
-    a.tw64[l] = l >= kBatch2dMinLog ? twiddles64(l) : nullptr;
-  }
+int launch(const B2Args& a, int C, int grid, size_t smem, bool mx, cudaStream_t st) {
+  return mx ? mx_kernel_launch(a, C, grid, smem, st) : kernel_launch<false>(a, C, grid, smem, st);
 }
 
 // Autotuner timings: microseconds per CG iteration of a class's probe problem
@@ -518,7 +151,7 @@ struct ClassTiming {
   double t[kNumSizes] = {-1, -1, -1, -1, -1};
 };
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, ClassTiming> g_tune;  // (device, logm)
+std::map<std::pair<int, int64_t>, ClassTiming> g_tune;  // (device, FFT length M)
 
 B2Prob make_prob(const frac_op* op, const double* f, double* u, const frac_solve_opts* o) {
   B2Prob p;
@@ -528,6 +161,9 @@ B2Prob make_prob(const frac_op* op, const double* f, double* u, const frac_solve
   p.lam64 = op->lam64;
   p.pinv32 = op->pinv32;
   p.pcg = (o->precond == FRAC_PRECOND_TAU && op->precond_ok) ? 1 : 0;
+  p.tw32 = twiddles32_len(op->M);
+  p.tw64 = twiddles64_len(op->M);
+  p.plan = op->plan[0];
   p.n = (int)op->n;
   p.logm = op->logm;
   p.max_iter = o->max_iter;
@@ -540,8 +176,10 @@ B2Prob make_prob(const frac_op* op, const double* f, double* u, const frac_solve
 // Times kProbeIters CG iterations of (op, f) alone, on one CTA and on one
 // cluster of each launchable size; the solution goes to scratch.
 int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming* out) {
-  const int logm = op->logm, n = (int)op->n;
-  const size_t smem = smem_bytes(logm);
+  const int64_t M = op->M;
+  const int n = (int)op->n;
+  const size_t smem = smem_bytes(M);
+  const bool mx = !is_pow2(M);
   DevBuf b{st, {}};
   double* u;
   B2Prob* dp;
@@ -554,10 +192,10 @@ int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming
   FRAC_TRY(b.get(&ds, sizeof(B2Slot)));
   FRAC_TRY(b.get(&di, sizeof(frac_solve_info)));
   FRAC_TRY(b.get(&next, 2 * sizeof(unsigned int)));
-  FRAC_TRY(b.get(&scratch, slot_bytes(n, logm)));
+  FRAC_TRY(b.get(&scratch, slot_bytes(n, M)));
   frac_solve_opts o{0.0, kProbeIters, FRAC_MIXED_IR, 0, FRAC_PRECOND_TAU, 1e-30};  // exactly kProbeIters iterations
   B2Prob hp = make_prob(op, f, u, &o);
-  B2Slot hs = carve(scratch, n, logm);
+  B2Slot hs = carve(scratch, n, M);
   FRAC_CUDA_TRY(cudaMemcpyAsync(dp, &hp, sizeof(hp), cudaMemcpyHostToDevice, st));
   FRAC_CUDA_TRY(cudaMemcpyAsync(ds, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
   cudaEvent_t e0, e1;
@@ -567,7 +205,7 @@ int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming
   out->n_probe = n;
   for (int i = 0; i < kNumSizes && rc == FRAC_OK; ++i) {
     const int C = kClusterSizes[i];
-    if (active_clusters(C, smem) < 1) continue;
+    if (active_clusters(C, smem, mx) < 1) continue;
     B2Args a = {};
     a.probs = dp;
     a.info = di;
@@ -576,7 +214,6 @@ int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming
     a.next = next;
     a.cslots = ds;
     a.lslots = ds;
-    fill_twiddles(a);
     float best = 1e30f;
     for (int rep = 0; rep < 2 && rc == FRAC_OK; ++rep) {  // the first run also loads the code
       if (cudaMemsetAsync(next, 0, 2 * sizeof(unsigned int), st) != cudaSuccess ||
@@ -584,7 +221,7 @@ int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming
         rc = FRAC_ECUDA;
         break;
       }
-      rc = launch(a, C, C, smem, st);
+      rc = launch(a, C, C, smem, mx, st);
       if (rc != FRAC_OK) break;
       float ms = 0.0f;
       if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -611,20 +248,21 @@ double est_iters(int n, double alpha, bool pcg) {
 
 struct Item {
   int64_t idx;  // problem index in the caller's arrays
-  int logm, n;
+  int64_t M;    // class: the FFT length
+  int n;
   double alpha;
   bool pcg;
 };
 
-// Makespan of the two queues on `ncl` clusters of C CTAs, classes with logm >= cut cluster-wide.
-double simulate(const std::vector<Item>& items, const std::map<int, ClassTiming>& tm, int si, int ncl, int cut,
+// Makespan of the two queues on `ncl` clusters of C CTAs, classes with lvl(M) >= cut cluster-wide.
+double simulate(const std::vector<Item>& items, const std::map<int64_t, ClassTiming>& tm, int si, int ncl, int cut,
                 std::vector<const Item*>* cl_out, std::vector<const Item*>* lo_out) {
   const int C = kClusterSizes[si];
   std::vector<std::pair<double, const Item*>> cl, lo;
   for (const Item& it : items) {
-    const ClassTiming& t = tm.at(it.logm);
+    const ClassTiming& t = tm.at(it.M);
     const double scale = 0.5 + 0.5 * (double)it.n / t.n_probe;
-    const bool wide = C > 1 && it.logm >= cut && t.t[si] > 0;
+    const bool wide = C > 1 && lvl(it.M) >= cut && t.t[si] > 0;
     const double per = wide ? t.t[si] : t.t[0];
     (wide ? cl : lo).emplace_back(est_iters(it.n, it.alpha, it.pcg) * per * scale, &it);
   }
@@ -662,15 +300,15 @@ int batch2d_prepare(int64_t count, const frac_op* const* ops, const double* cons
                     cudaStream_t st) {
   if (count <= 0) return FRAC_OK;
   FRAC_TRY(configure_kernel());
-  for (int l = kBatch2dMinLog; l <= kBatch2dMaxLog; ++l) FRAC_TRY(prepare_twiddles(l));
   int dev = 0;
   FRAC_CUDA_TRY(cudaGetDevice(&dev));
-  std::map<int, int64_t> rep;  // logm -> largest problem of that class
+  std::map<int64_t, int64_t> rep;  // M -> largest problem of that class
   for (int64_t t = 0; t < count; ++t) {
     const frac_op* op = ops[idx[t]];
-    auto it = rep.find(op->logm);
-    if (it == rep.end() || ops[it->second]->n < op->n) rep[op->logm] = idx[t];
+    auto it = rep.find(op->M);
+    if (it == rep.end() || ops[it->second]->n < op->n) rep[op->M] = idx[t];
   }
+  for (auto& kv : rep) FRAC_TRY(prepare_twiddles_len(kv.first));
   for (auto& kv : rep) {
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -686,8 +324,8 @@ int batch2d_prepare(int64_t count, const frac_op* const* ops, const double* cons
 }
 
 bool batch2d_eligible(const frac_op* op, const frac_solve_opts* opts) {
-  return op->prob.d == 2 && op->square && opts->precision == FRAC_MIXED_IR && op->logm >= kBatch2dMinLog &&
-         op->logm <= kBatch2dMaxLog;
+  return op->prob.d == 2 && op->square && opts->precision == FRAC_MIXED_IR && op->M >= (1 << kBatch2dMinLog) &&
+         op->M <= (1 << kBatch2dMaxLog);
 }
 
 int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const* f, double* const* u,
@@ -698,17 +336,17 @@ int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const
   int dev = 0;
   FRAC_CUDA_TRY(cudaGetDevice(&dev));
   std::vector<Item> items;
-  std::map<int, int64_t> rep;  // logm -> largest problem of that class
+  std::map<int64_t, int64_t> rep;  // M -> largest problem of that class
   for (int64_t t = 0; t < count; ++t) {
     const frac_op* op = ops[idx[t]];
-    items.push_back(Item{idx[t], op->logm, (int)op->n, op->prob.alpha,
+    items.push_back(Item{idx[t], op->M, (int)op->n, op->prob.alpha,
                          opts->precond == FRAC_PRECOND_TAU && op->precond_ok != 0});
-    auto it = rep.find(op->logm);
-    if (it == rep.end() || ops[it->second]->n < op->n) rep[op->logm] = idx[t];
+    auto it = rep.find(op->M);
+    if (it == rep.end() || ops[it->second]->n < op->n) rep[op->M] = idx[t];
   }
-  for (int l = kBatch2dMinLog; l <= kBatch2dMaxLog; ++l) FRAC_TRY(prepare_twiddles(l));
+  for (auto& kv : rep) FRAC_TRY(prepare_twiddles_len(kv.first));
   // timings of every class present (measured once per device and FFT length)
-  std::map<int, ClassTiming> tm;
+  std::map<int64_t, ClassTiming> tm;
   for (auto& kv : rep) {
     ClassTiming t;
     bool have = false;
@@ -731,13 +369,17 @@ int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const
   }
   // plan: cluster size and the first cluster-wide FFT length, by simulated makespan
   size_t smem = 0;
-  for (auto& kv : rep) smem = std::max(smem, smem_bytes(kv.first));
+  bool mx = false;
+  for (auto& kv : rep) {
+    smem = std::max(smem, smem_bytes(kv.first));
+    mx = mx || !is_pow2(kv.first);
+  }
   int best_si = 0, best_cut = kBatch2dMaxLog + 1, best_ncl = 0;
   double best = INFINITY;
   for (int si = 0; si < kNumSizes; ++si) {
     const int C = kClusterSizes[si];
     if (pin_size > 0 && C != pin_size) continue;
-    const int ncl = active_clusters(C, smem);
+    const int ncl = active_clusters(C, smem, mx);
     if (ncl < 1) continue;
     for (int cut = kBatch2dMinLog; cut <= kBatch2dMaxLog + 1; ++cut) {
       if (C == 1 && cut <= kBatch2dMaxLog) continue;
@@ -766,11 +408,12 @@ int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const
 
   // device records: problems in queue order, scratch per cluster and per CTA
   const int grid = best_ncl * C;
-  int ncl_max = 0, nlo_max = 0, lcl = kBatch2dMinLog, llo = kBatch2dMinLog;
+  int ncl_max = 0, nlo_max = 0;
+  int64_t lcl = 1 << kBatch2dMinLog, llo = 1 << kBatch2dMinLog;
   for (const Item* it : cl)
-    if (it->n > ncl_max) ncl_max = it->n, lcl = it->logm;
+    if (it->n > ncl_max) ncl_max = it->n, lcl = it->M;
   for (const Item* it : lo)
-    if (it->n > nlo_max) nlo_max = it->n, llo = it->logm;
+    if (it->n > nlo_max) nlo_max = it->n, llo = it->M;
   const size_t cslot = cl.empty() ? 0 : slot_bytes(ncl_max, lcl), lslot = lo.empty() ? 0 : slot_bytes(nlo_max, llo);
   const int n_cslots = cl.empty() ? 0 : best_ncl, n_lslots = lo.empty() ? 0 : grid;
   pend->st = st;
@@ -815,9 +458,8 @@ int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const
   a.next = next;
   a.cslots = ds;
   a.lslots = ds + n_cslots;
-  fill_twiddles(a);
   prof::Scope ps("batch2d", st);
-  return launch(a, C, grid, smem, st);
+  return launch(a, C, grid, smem, mx, st);
 }
 
 }  // namespace frac

@@ -5,10 +5,11 @@
 
 namespace frac {
 
-// FFT lengths handled by the persistent kernel: 2^5 .. 2^10 (n = 9 .. 511).
+// FFT lengths handled by the persistent kernel: 2^5 .. 2^10 (n = 9 .. 511) and the
+// mixed (7-smooth) lengths between.
 constexpr int kBatch2dMinLog = 5, kBatch2dMaxLog = 10;
 
-// True when a problem can go to the persistent kernel (d = 2, mixed precision,
+// True when a problem can go to the persistent kernel (square d = 2, mixed precision,
 // FFT length in range); f and u must also be device pointers.
 bool batch2d_eligible(const frac_op* op, const frac_solve_opts* opts);
 
