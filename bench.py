@@ -485,12 +485,14 @@ def extra_measurements(fg, torch, u32, op, barrier) -> dict:
     return out
 
 
-def mixed_radix_measurement(fg, torch, barrier) -> dict:
+def mixed_radix_measurement(fg, torch, barrier, cases=None) -> dict:
     """The same problems on power-of-two and on mixed-radix (7-smooth) FFT lengths: FP32
     and FP64 applies (CUDA events over 10 applies of a batch of fields, alpha = 1.3,
     p = 1) and a mixed-precision solve to 1e-10; the length "auto" picks is reported."""
     out = {}
     for d, n, batch in ((1, 1100, 512), (2, 300, 64), (2, 600, 64), (2, 700, 16), (3, 200, 2)):
+        if cases is not None and f"{d}d_n{n}_b{batch}" not in cases:
+            continue
         row = {"auto_picks": fg.fft_length(n, d, "auto")}
         for fft in ("pow2", "smooth"):
             op = fg.FracOp(d, n, 1.3, degree=1, fft=fft)
@@ -777,6 +779,11 @@ def main():
                     help="arrival window of the served stream (the configured stream is 60 s)")
     ap.add_argument("--applies-only", action="store_true",
                     help="run only the 1D and 3D single-vector apply timings and print their JSON (profiler captures)")
+    ap.add_argument("--mixed-only", default=None, metavar="CASES",
+                    help="run only the mixed-radix comparison for the listed cases (comma-separated, e.g. "
+                         "2d_n600_b64; 'all' for every case) and print its JSON (profiler captures)")
+    ap.add_argument("--batch-fft", default="pow2", choices=["pow2", "smooth", "auto"],
+                    help="FFT-length policy of the operators of --batch-only")
     args = ap.parse_args()
     global NFIELDS
     NFIELDS = args.fields
@@ -798,7 +805,13 @@ def main():
     if args.batch_only:
         import torch
         import paper_2103_03658_gb300 as fg
-        print(json.dumps(batch_measurement(fg, torch, torch.cuda.synchronize)), flush=True)
+        print(json.dumps(batch_measurement(fg, torch, torch.cuda.synchronize, fft=args.batch_fft)), flush=True)
+        return
+    if args.mixed_only:
+        import torch
+        import paper_2103_03658_gb300 as fg
+        cases = None if args.mixed_only == "all" else set(args.mixed_only.split(","))
+        print(json.dumps(mixed_radix_measurement(fg, torch, torch.cuda.synchronize, cases)), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -41,14 +41,16 @@ def _static(lib, op, u, y, dtype):
     return lib.frac_apply_static(op.handle, u.data_ptr(), y.data_ptr(), code, u.shape[0], stream)
 
 
-@pytest.mark.parametrize("d,n,p,alpha,batch,dtype", [
-    (2, 1023, 2, 1.2, 3, torch.float32),
-    (3, 63, 1, 0.6, 2, torch.float64),
-    (1, 1023, 1, 1.5, 5, torch.float32),
+@pytest.mark.parametrize("d,n,p,alpha,batch,dtype,fft", [
+    (2, 1023, 2, 1.2, 3, torch.float32, "pow2"),
+    (3, 63, 1, 0.6, 2, torch.float64, "pow2"),
+    (1, 1023, 1, 1.5, 5, torch.float32, "pow2"),
+    (2, 599, 1, 1.1, 3, torch.float32, "smooth"),  # mixed-radix length 1200
+    (3, 39, 2, 0.8, 2, torch.float64, "smooth"),  # 80
 ])
-def test_static_scratch_apply_equals_frac_apply_twice(lib, d, n, p, alpha, batch, dtype):
+def test_static_scratch_apply_equals_frac_apply_twice(lib, d, n, p, alpha, batch, dtype, fft):
     import paper_2103_03658_gb300 as fg
-    op = fg.FracOp(d, n, alpha, degree=p)
+    op = fg.FracOp(d, n, alpha, degree=p, fft=fft)
     for call in range(2):
         u = torch.tensor(synth.smooth_fields(d, n, batch, 300 + 10 * call), dtype=dtype, device="cuda")
         y_static = torch.full_like(u, float("nan"))
