@@ -695,6 +695,9 @@ int frac_solve_batch(int64_t count, const frac_op* const* ops, const double* con
   for (const std::vector<int64_t>* v : {&oned, &wide})
     for (int64_t i : *v) {
       if (std::isnan(info[i].rel_resid)) info[i].status = FRAC_EINVAL;
+      if (info[i].status == FRAC_ECUDA)
+        record_detail("persistent batch: problem %lld failed the kernel's scratch and shared-memory check",
+                      (long long)i);
       if (info[i].status != FRAC_OK && first == FRAC_OK) first = info[i].status;
     }
   if (!rest.empty()) {

@@ -72,26 +72,38 @@ size_t smem_bytes(int64_t M) {  // M: a power of two or a length with a plan
   return std::max(rows, cols);
 }
 
-size_t slot_bytes(int n, int64_t M) {
-  const int64_t K = M / 2 + 1, KB64 = (K + 1) / 2, nn = (int64_t)n * n;
-  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-  return al((size_t)n * KB64 * 2 * sizeof(double2)) + 4 * al(nn * sizeof(float)) + al(nn * sizeof(double));
+// Scratch of a worker for the problems it may take: the FP64 spectrum layout
+// (n ceil(K/2) 2 complex doubles, the largest over the problems: with mixed
+// lengths the largest n need not have the largest M) and five vectors of the
+// largest n^2.
+struct SlotSize {
+  size_t w = 0;   // bytes of the spectrum
+  int64_t nn = 0; // entries of a vector
+  void add(int n, int64_t M) {
+    const int64_t K = M / 2 + 1, KB64 = (K + 1) / 2;
+    w = std::max(w, (size_t)n * KB64 * 2 * sizeof(double2));
+    nn = std::max(nn, (int64_t)n * n);
+  }
+};
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+size_t slot_bytes(const SlotSize& z) {
+  return al256(z.w) + 4 * al256(z.nn * sizeof(float)) + al256(z.nn * sizeof(double));
 }
 
-B2Slot carve(unsigned char* base, int n, int64_t M) {
-  const int64_t K = M / 2 + 1, KB64 = (K + 1) / 2, nn = (int64_t)n * n;
-  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+B2Slot carve(unsigned char* base, const SlotSize& z) {
   B2Slot s;
   s.W = base;
-  base += al((size_t)n * KB64 * 2 * sizeof(double2));
+  s.w_bytes = z.w;
+  s.nn = z.nn;
+  base += al256(z.w);
   s.x = reinterpret_cast<float*>(base);
-  base += al(nn * sizeof(float));
+  base += al256(z.nn * sizeof(float));
   s.r = reinterpret_cast<float*>(base);
-  base += al(nn * sizeof(float));
+  base += al256(z.nn * sizeof(float));
   s.p = reinterpret_cast<float*>(base);
-  base += al(nn * sizeof(float));
+  base += al256(z.nn * sizeof(float));
   s.q = reinterpret_cast<float*>(base);
-  base += al(nn * sizeof(float));
+  base += al256(z.nn * sizeof(float));
   s.r64 = reinterpret_cast<double*>(base);
   return s;
 }
@@ -192,10 +204,12 @@ int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming
   FRAC_TRY(b.get(&ds, sizeof(B2Slot)));
   FRAC_TRY(b.get(&di, sizeof(frac_solve_info)));
   FRAC_TRY(b.get(&next, 2 * sizeof(unsigned int)));
-  FRAC_TRY(b.get(&scratch, slot_bytes(n, M)));
+  SlotSize z;
+  z.add(n, M);
+  FRAC_TRY(b.get(&scratch, slot_bytes(z)));
   frac_solve_opts o{0.0, kProbeIters, FRAC_MIXED_IR, 0, FRAC_PRECOND_TAU, 1e-30};  // exactly kProbeIters iterations
   B2Prob hp = make_prob(op, f, u, &o);
-  B2Slot hs = carve(scratch, n, M);
+  B2Slot hs = carve(scratch, z);
   FRAC_CUDA_TRY(cudaMemcpyAsync(dp, &hp, sizeof(hp), cudaMemcpyHostToDevice, st));
   FRAC_CUDA_TRY(cudaMemcpyAsync(ds, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
   cudaEvent_t e0, e1;
@@ -408,13 +422,10 @@ int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const
 
   // device records: problems in queue order, scratch per cluster and per CTA
   const int grid = best_ncl * C;
-  int ncl_max = 0, nlo_max = 0;
-  int64_t lcl = 1 << kBatch2dMinLog, llo = 1 << kBatch2dMinLog;
-  for (const Item* it : cl)
-    if (it->n > ncl_max) ncl_max = it->n, lcl = it->M;
-  for (const Item* it : lo)
-    if (it->n > nlo_max) nlo_max = it->n, llo = it->M;
-  const size_t cslot = cl.empty() ? 0 : slot_bytes(ncl_max, lcl), lslot = lo.empty() ? 0 : slot_bytes(nlo_max, llo);
+  SlotSize zcl, zlo;
+  for (const Item* it : cl) zcl.add(it->n, it->M);
+  for (const Item* it : lo) zlo.add(it->n, it->M);
+  const size_t cslot = cl.empty() ? 0 : slot_bytes(zcl), lslot = lo.empty() ? 0 : slot_bytes(zlo);
   const int n_cslots = cl.empty() ? 0 : best_ncl, n_lslots = lo.empty() ? 0 : grid;
   pend->st = st;
   B2Prob* dp;
@@ -436,9 +447,8 @@ int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const
     pend->order.push_back(it->idx);
   }
   std::vector<B2Slot> hs;
-  for (int i = 0; i < n_cslots; ++i) hs.push_back(carve(scratch + (size_t)i * cslot, ncl_max, lcl));
-  for (int i = 0; i < n_lslots; ++i)
-    hs.push_back(carve(scratch + (size_t)n_cslots * cslot + (size_t)i * lslot, nlo_max, llo));
+  for (int i = 0; i < n_cslots; ++i) hs.push_back(carve(scratch + (size_t)i * cslot, zcl));
+  for (int i = 0; i < n_lslots; ++i) hs.push_back(carve(scratch + (size_t)n_cslots * cslot + (size_t)i * lslot, zlo));
   if (hs.empty()) hs.push_back(B2Slot{});
   // pinned staging kept until collect(), so the uploads do not wait for the stream
   const size_t hb = hp.size() * sizeof(B2Prob), sb = hs.size() * sizeof(B2Slot);

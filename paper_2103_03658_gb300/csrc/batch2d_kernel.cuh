@@ -35,6 +35,8 @@ struct B2Slot {
   void* W;  // spectrum, FP64 layout n ceil(K/2) 2 complex doubles; the FP32 passes use its front
   float *x, *r, *p, *q;
   double* r64;
+  size_t w_bytes;  // capacity of W
+  int64_t nn;      // capacity of each vector (entries)
 };
 
 struct B2Args {
@@ -44,6 +46,7 @@ struct B2Args {
   unsigned int* next;     // queue heads: [0] cluster, [1] local
   const B2Slot* cslots;   // per cluster
   const B2Slot* lslots;   // per CTA
+  size_t smem;            // dynamic shared memory of each CTA (bytes)
 };
 
 __device__ __forceinline__ void cluster_sync_all() {
@@ -90,6 +93,7 @@ struct Ctx {
   const float2* tw32;
   const double2* tw64;
   unsigned char* smem;
+  size_t smem_bytes;
   double* red;
   double* slots;
   int parity;
@@ -333,7 +337,26 @@ struct Solver {
   }
 
   // mixed-precision refinement to ||f - A u|| <= rtol ||f||
+  // Geometry guard: the problem's spectrum and vectors fit its worker's slot, and its row
+  // lines and column tiles (spare ones included) fit the CTA's shared memory.  The
+  // same in every thread of the group; a problem that fails it is not touched and
+  // reports FRAC_ECUDA.
+  static __device__ bool fits(const Ctx& c) {
+    const int n = c.P->n, TPL = tpl(c);
+    const size_t w = (size_t)n * kb64(c) * 2 * sizeof(double2);
+    const int sr = lines(c) * TPL < kThreads, s64 = tpr64(c) * 2 * TPL < kThreads, s32 = tpr32(c) * 4 * TPL < kThreads;
+    const size_t rows = (size_t)(lines(c) + sr) * ln(c).stride() * sizeof(double2);
+    const size_t t64 = (size_t)(tpr64(c) + s64) * 2 * lnt(c).stride_tile() * sizeof(double2);
+    const size_t t32 = (size_t)(tpr32(c) + s32) * 4 * lnt(c).stride_tile() * sizeof(float2);
+    return w <= c.S->w_bytes && (int64_t)n * n <= c.S->nn && rows <= c.smem_bytes && t64 <= c.smem_bytes &&
+           t32 <= c.smem_bytes;
+  }
+
   static __device__ __noinline__ void solve(Ctx& c, frac_solve_info* info) {
+    if (!fits(c)) {
+      if (c.g.rank == 0 && threadIdx.x == 0) *info = frac_solve_info{FRAC_ECUDA, 0, 0, c.P->pcg, INFINITY};
+      return;
+    }
     const double fn2 = start(c);
     const double tol2 = c.P->rtol * c.P->rtol * fn2;
     int iters = 0, outer = 0, status = FRAC_OK;
@@ -372,7 +395,7 @@ __device__ inline void solve_any(const B2Args& A, int item, const B2Slot& S, con
                           double* red, double* slots) {
   const B2Prob& P = A.probs[item];
   frac_solve_info* info = A.info + item;
-  Ctx c{&P, &S, g, P.tw32, P.tw64, smem, red, slots, 0};
+  Ctx c{&P, &S, g, P.tw32, P.tw64, smem, A.smem, red, slots, 0};
   if constexpr (MX) {
     if (P.plan.m) {  // a mixed length (uniform over the group)
       Solver<MxLine>::solve(c, info);
@@ -457,7 +480,9 @@ int kernel_active_clusters(int C, size_t smem) {
 }
 
 template <bool MX>
-int kernel_launch(const B2Args& a, int C, int grid, size_t smem, cudaStream_t st) {
+int kernel_launch(const B2Args& args, int C, int grid, size_t smem, cudaStream_t st) {
+  B2Args a = args;
+  a.smem = smem;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;

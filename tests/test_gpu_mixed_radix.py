@@ -246,3 +246,29 @@ def test_mixed_apply_is_deterministic_and_host_buffers_match():
     yh = op.apply(torch.tensor(u))  # host buffers through the C ABI
     assert torch.equal(yh, y1.cpu())
     op.close()
+
+
+def test_batch_slots_hold_the_largest_spectrum_not_the_largest_n():
+    """With per-operator FFT lengths the largest n of a queue need not have the largest
+    spectrum (n = 310 on 640 points against n = 300 on 1024): the persistent batch sizes
+    each worker's scratch by the largest spectrum and the largest n separately.  Every
+    result equals its single solve."""
+    import paper_2103_03658_gb300 as fg
+    probs = [(310, "smooth"), (300, "pow2"), (305, "pow2"), (200, "smooth"), (250, "pow2"), (311, "smooth")]
+    ops = [_op(2, n, 1, 1.2, fft=ff) for n, ff in probs]
+    lens = [op.info()["fft_len"] for op in ops]
+    assert lens[0] == 640 and lens[1] == 1024
+    rng = np.random.default_rng(8)
+    fs = [torch.tensor(rng.standard_normal((n, n)) * 0.1 + 0.5, device="cuda") for n, _ in probs]
+    us = [torch.empty_like(f) for f in fs]
+    for size in (0, 1):  # the autotuner's choice, then every problem on a CTA of its own
+        fg.batch_pin_plan(size)
+        infos = fg.solve_batch(ops, fs, us, rtol=1e-10)
+        fg.batch_pin_plan(0)
+        for i, (op, f, u, inf) in enumerate(zip(ops, fs, us, infos)):
+            assert inf["status"] == 0 and inf["rel_resid"] <= 1e-10, (size, i, inf)
+            u1, _ = op.solve(f, rtol=1e-10)
+            kappa = op.info()["norm_bound"] * float(u1.norm()) / float(f.norm())
+            assert float((u - u1).norm() / u1.norm()) <= 4e-10 * max(kappa, 1.0), (size, i)
+    for op in ops:
+        op.close()
