@@ -272,3 +272,15 @@ def test_batch_slots_hold_the_largest_spectrum_not_the_largest_n():
             assert float((u - u1).norm() / u1.norm()) <= 4e-10 * max(kappa, 1.0), (size, i)
     for op in ops:
         op.close()
+
+
+def test_boundary_vector_does_not_depend_on_the_fft_length():
+    """frac_boundary convolves the exterior samples on a circulant of its own (power-of-two)
+    side, so the boundary vector of an operator on mixed lengths is the one on powers of two."""
+    for d, n in ((1, 99), (2, 39)):
+        op_m, op_p = _op(d, n, 1, 1.3), _op(d, n, 1, 1.3, fft="pow2")
+        rng = np.random.default_rng(d)
+        g = torch.tensor(rng.standard_normal(op_p.ext_shape), device="cuda")
+        assert torch.equal(op_m.boundary(g), op_p.boundary(g))
+        op_m.close()
+        op_p.close()
