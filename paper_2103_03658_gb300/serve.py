@@ -43,15 +43,17 @@ class Result:
     op_cache_hit: bool
 
 
-def job_bytes(d: int, n: int, precision: str = "mixed") -> int:
+def job_bytes(d: int, n: int, precision: str = "mixed", M: int | None = None) -> int:
     """Device bytes of one solve job (vectors, FFT scratch, partial sums), as the
-    library allocates them; d = 1 jobs hold only a few small records."""
+    library allocates them; d = 1 jobs hold only a few small records.  M: the
+    operator's FFT length (default: the power of two)."""
     nd = n ** d
     if d == 1:
         return 4096 + 16 * nd
-    M = 2
-    while M < 2 * n - 1:
-        M *= 2
+    if M is None:
+        M = 2
+        while M < 2 * n - 1:
+            M *= 2
     K = M // 2 + 1
 
     def ws(cs, B):
@@ -71,6 +73,7 @@ class OpCache:
     """Operators keyed by (d, n, alpha, h, degree, lambda), least recently used
     evicted first when the cache's device bytes exceed `capacity`."""
     capacity: int
+    fft: str = "pow2"   # FFT-length policy of the operators it builds
     ops: "collections.OrderedDict" = field(default_factory=collections.OrderedDict)
     bytes: int = 0
     hits: int = 0
@@ -101,7 +104,7 @@ class OpCache:
             self.ops.move_to_end(key)
             self.hits += 1
             return self.ops[key], True
-        op = FracOp(d, n, alpha, degree=degree, lam=lam)
+        op = FracOp(d, n, alpha, degree=degree, lam=lam, fft=self.fft)
         self.misses += 1
         self.ops[key] = op
         self.bytes += op.info()["device_bytes"]
@@ -131,10 +134,11 @@ class Server:
 
     def __init__(self, hbm_budget: float = 150e9, nstreams: int = 16, precision: str = "mixed",
                  rtol: float = 1e-10, op_cache_bytes: float = 8e9, build_workers: int = 2,
-                 max_builds: int = 8):
+                 max_builds: int = 8, fft: str = "pow2"):
         from concurrent.futures import ThreadPoolExecutor
         self.engine = Engine(nstreams)
-        self.cache = OpCache(int(op_cache_bytes))
+        self.fft = fft  # FFT-length policy of the operators (FracOp's fft)
+        self.cache = OpCache(int(op_cache_bytes), fft)
         self.budget = int(hbm_budget)
         self.precision = precision
         self.rtol = rtol
@@ -157,12 +161,19 @@ class Server:
         import torch
         d, n, alpha, h, degree, lam = key
         if not torch.cuda.is_available():
-            return FracOp(d, n, alpha, degree=degree, lam=lam)
+            return FracOp(d, n, alpha, degree=degree, lam=lam, fft=self.fft)
         st = torch.cuda.Stream()
         with torch.cuda.stream(st):
-            op = FracOp(d, n, alpha, degree=degree, lam=lam, stream=st.cuda_stream)
+            op = FracOp(d, n, alpha, degree=degree, lam=lam, stream=st.cuda_stream, fft=self.fft)
         st.synchronize()
         return op
+
+    def _fft_len(self, d, n):
+        """The FFT length of the server's operators for (d, n); None: the power of two."""
+        if self.fft == "pow2":
+            return None
+        from ._native import fft_length
+        return fft_length(n, d, self.fft)
 
     def _op_ready(self, r, in_use):
         """The request's operator if it is available now (cache hit or finished build), else None."""
@@ -197,7 +208,7 @@ class Server:
             blocked = []
             while waiting:
                 r = waiting[0]
-                need = job_bytes(r.d, r.n, self.precision)
+                need = job_bytes(r.d, r.n, self.precision, self._fft_len(r.d, r.n))
                 if active and held + need + self.cache.bytes > self.budget:
                     break
                 in_use = [a[1] for a in active.values()]

@@ -11,8 +11,11 @@ import paper_2103_03658_gb300.serve as serve
 class FakeOp:
     built = 0
 
-    def __init__(self, d, n, alpha, degree=1, lam=0.0):
+    ffts = []
+
+    def __init__(self, d, n, alpha, degree=1, lam=0.0, fft="pow2"):
         FakeOp.built += 1
+        FakeOp.ffts.append(fft)
         self.key = (d, n, alpha, degree, lam)
         self.closed = False
 
@@ -149,3 +152,18 @@ def test_operators_built_ahead_are_bounded(fakes, monkeypatch):
     srv.close()
     assert [r.rid for r in res] == list(range(40))
     assert live["peak"] <= 3
+
+
+def test_fft_policy_reaches_the_operators_and_the_admission_estimate(fakes):
+    """Server(fft=...) builds its operators with that FFT-length policy, and sizes each job
+    by the length the policy gives (a power of two n gets a longer smooth length: 2 n + 2)."""
+    import paper_2103_03658_gb300 as fg
+    FakeOp.ffts = []
+    srv = serve.Server(hbm_budget=1e12, nstreams=4, op_cache_bytes=1e9, build_workers=0, fft="smooth")
+    srv.run(_reqs(4, distinct=2), realtime=False, device_inputs=True)
+    assert FakeOp.ffts and set(FakeOp.ffts) == {"smooth"}
+    m = fg.fft_length(64, 2, "smooth")
+    assert m == 144 and srv._fft_len(2, 64) == 144
+    assert serve.job_bytes(2, 64, "mixed", m) > serve.job_bytes(2, 64, "mixed")
+    assert serve.Server(build_workers=0)._fft_len(2, 64) is None
+
