@@ -101,12 +101,21 @@ __device__ __forceinline__ void mx_pass(C* buf, int tl, int TPL, int M, int Ns, 
   const int nbf = M / R, tws = M / (Ns * R);
   const unsigned inv = 0xffffffffu / (unsigned)Ns + 1u;
   C w[NB * R];
+  // for an odd R, nbf = M / R is a multiple of 16 (as M is), so pad(j + r nbf) =
+  // pad(j) + r (nbf + nbf / 16): one address per butterfly
+  const int rstep = nbf + (nbf >> 4);
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int j = tl + b * TPL;
     if (NB * R == 16 || j < nbf) {
+      if constexpr (R % 2 == 1) {
+        const C* src = buf + mx_pad(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) w[b * R + r] = buf[mx_pad(j + r * nbf)];
+        for (int r = 0; r < R; ++r) w[b * R + r] = src[r * rstep];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) w[b * R + r] = buf[mx_pad(j + r * nbf)];
+      }
     }
   }
   __syncthreads();  // every read of this pass done before its writes
