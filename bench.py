@@ -248,6 +248,20 @@ def nominal_flops(kernel: str, fields: int) -> float:
     raise KeyError(kernel)
 
 
+def apply3d_alu_view(applies: dict, alu_peaks: dict) -> dict:
+    """Nominal FFT arithmetic of the 3D 255^3 apply (M = 512 on every axis, K = 257) against
+    the measured FMA rates: rows ceil(n/2) n line FFTs forward and inverse, the y passes
+    n K forward and inverse, the z (symbol) pass M K forward and inverse; 5 M log2 M each."""
+    n, M, K = 255, 512, 257
+    per = 5.0 * M * math.log2(M)
+    flops = 2 * per * (((n + 1) // 2) * n + n * K + M * K)
+    out = {"nominal_flops": flops}
+    for dt, key in (("f32", "3d_n255_f32_ms"), ("f64", "3d_n255_f64_ms")):
+        tf = flops / (applies[key] * 1e-3) / 1e12
+        out[dt] = {"achieved_tflops": tf, "frac_of_measured_fma_rate": tf / alu_peaks[dt]}
+    return out
+
+
 def apply_model_bytes(fields: int) -> float:
     """Whole-apply byte model B_model: read u, write y, read the symbol once,
     and the half spectrum W written and read twice (rows -> columns -> rows)."""
@@ -380,6 +394,7 @@ def run_ours(args) -> None:
                                                                                   alu_peaks["f64"], peak)}
     if not args.no_extra:
         extra.update(extra_measurements(fg, torch, u, op, barrier))
+        extra["applies"]["3d_n255_alu_view"] = apply3d_alu_view(extra["applies"], alu_peaks)
 
     if rank != 0:
         op.close()
