@@ -156,14 +156,18 @@ int frac_fft_length(int64_t n, int32_t d, int32_t fft_lengths, int64_t* M) {
   if (!M || n < 1 || d < 1 || d > 3) return FRAC_EINVAL;
   if (fft_lengths != FRAC_FFT_POW2 && fft_lengths != FRAC_FFT_SMOOTH && fft_lengths != FRAC_FFT_AUTO)
     return FRAC_EINVAL;
+  const int64_t cap = int64_t(1) << max_logm(d);
+  if (n > cap) return FRAC_ENOTSUP;  // M >= 2 n - 1 > cap (and no overflow below)
   int64_t m = 2;
   while (m < 2 * n - 1) m *= 2;
-  const int64_t cap = int64_t(1) << max_logm(d);
+  if (m > cap) return FRAC_ENOTSUP;  // (also keeps the searches below within the limit)
   if (fft_lengths == FRAC_FFT_SMOOTH) {
     // the smallest 7-smooth length with a >= 4 that keeps M/2 - 1 >= n (the tau
     // system); the power of two when that one is beyond the limit
-    const int64_t ms = mx_length_at_least(2 * n + 2);
-    if (ms <= cap) m = ms;
+    if (2 * n + 2 <= cap) {
+      const int64_t ms = mx_length_at_least(2 * n + 2);
+      if (ms <= cap) m = ms;
+    }
   } else if (fft_lengths == FRAC_FFT_AUTO) {
     // the cheapest by fft_cost among the power of two (when it holds the tau system)
     // and the 7-smooth lengths >= 2 n + 2 below twice the power of two

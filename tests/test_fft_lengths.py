@@ -59,6 +59,19 @@ def test_smooth_lengths_are_shorter_and_keep_the_tau_system():
         assert m // 2 - 1 >= n and m <= fg.fft_length(n, 1, "pow2") * 2
 
 
+def test_huge_sizes_are_refused_at_once():
+    """Sizes far beyond every limit return FRAC_ENOTSUP without searching for a length."""
+    import time
+    fg.load()
+    t0 = time.perf_counter()
+    for fft in ("pow2", "smooth", "auto"):
+        for n in (10 ** 6, 10 ** 9, 2 ** 40):
+            with pytest.raises(fg.FracError) as e:
+                fg.fft_length(n, 1, fft)
+            assert e.value.status == 3
+    assert time.perf_counter() - t0 < 1.0
+
+
 def test_invalid_arguments():
     lib = nat.load()
     import ctypes
