@@ -133,6 +133,20 @@ int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream);
  */
 int frac_fft_length(int64_t n, int32_t d, int32_t fft_lengths, int64_t* M);
 
+/*
+ * frac_apply_3d_passes -- schedule of the 3D FP32 apply (frac_apply, frac_precond and
+ * the FP32 CG of the solvers) for this process: fused != 0 runs the x and y transforms
+ * of each z-plane fused on a thread-block cluster of 8 CTAs, the plane's x spectra kept
+ * in distributed shared memory (three passes over device memory: xy forward, z with the
+ * symbol, xy inverse); 0 (the default) runs five pencil passes (x, y, z, y, x), which
+ * measured faster on GB300 (255^3: 0.49 against 0.82 ms).  Both run the same device
+ * functions and agree to FP32 rounding.  The fused schedule applies to operators with
+ * equal power-of-two x and y FFT lengths 32..512 on a device that can hold a cluster of
+ * 8 CTAs of the pass's shared memory; others always take the five passes.  Host only,
+ * returns FRAC_OK.
+ */
+int frac_apply_3d_passes(int32_t fused);
+
 /* Release an op (NULL is ignored).  The caller must ensure no work using it is in flight. */
 void frac_op_free(frac_op* op);
 

@@ -134,6 +134,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.frac_far_points.argtypes = [vp, vp, vp, i64, i64, i64, vp, vp]
     lib.frac_far_points.restype = i32
     lib.frac_far_sum.argtypes = [vp, vp, i64, vp, i64, vp, vp]
+    lib.frac_apply_3d_passes.restype = i32
+    lib.frac_apply_3d_passes.argtypes = [i32]
     lib.frac_fft_length.restype = i32
     lib.frac_fft_length.argtypes = [i64, i32, i32, ctypes.POINTER(ctypes.c_int64)]
     lib.frac_far_sum.restype = i32
@@ -169,6 +171,13 @@ def far_nodes(d: int, alpha: float, lam: float, L: float, nr: int = 96, ns: int 
     if s != 0:
         raise FracError(s, "frac_far_nodes")
     return xi, w
+
+
+def apply_3d_passes(fused: bool) -> None:
+    """Schedule of the 3D FP32 apply (frac_apply_3d_passes): fused xy passes on thread-block
+    clusters (True) or five pencil passes (False, the default, faster on GB300); the results
+    agree to FP32 rounding."""
+    load().frac_apply_3d_passes(1 if fused else 0)
 
 
 def fft_length(n: int, d: int, fft: str = "pow2") -> int:

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libfrac.so")
 OBJ_DIR = os.path.join(HERE, "_build")
-SOURCES = ["coeffs.cu", "apply.cu", "precond.cu", "apply_mx_f32.cu", "apply_mx_f64.cu", "solve.cu", "solve1d.cu",
+SOURCES = ["coeffs.cu", "apply.cu", "precond.cu", "apply_mx_f32.cu", "apply_mx_f64.cu", "apply_xy.cu", "solve.cu", "solve1d.cu",
            "solve1d_mx.cu", "batch2d.cu", "batch2d_mx.cu", "api.cu", "prof.cu", "noalloc.cu", "boundary.cu", "far.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]

@@ -241,6 +241,7 @@ int frac_coeffs(const frac_problem* prob, frac_op** out, void* stream) {
   }
   for (int i = 0; i < d && s == FRAC_OK; ++i) s = prepare_twiddles_len(op->Ma[i]);
   if (s == FRAC_OK) s = build_coefficients(op, st);
+  if (s == FRAC_OK) s = xy_prepare(op);
   if (s != FRAC_OK) {
     frac_op_free(op);
     return s;

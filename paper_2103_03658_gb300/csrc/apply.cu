@@ -29,7 +29,8 @@ size_t apply_cg_partials(const frac_op* op) {
   int64_t nrows = 1;  // rows of one field: the extents of the axes after the row axis
   for (int i = 1; i < op->prob.d; ++i) nrows *= op->na[i];
   const int64_t a = rows_grid_op<float>(op, nrows), b = rows_grid_op<double>(op, nrows);
-  return (size_t)(a > b ? a : b);
+  const int64_t c = xy_grid_blocks(op, 1);  // the fused 3D inverse pass (0 when it does not apply)
+  return (size_t)std::max(a, std::max(b, c));
 }
 
 template <typename T>

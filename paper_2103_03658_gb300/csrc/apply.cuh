@@ -41,6 +41,11 @@ int take_coeff_fault();
 int boundary_device(const frac_op* op, const double* g_ext, const double* far, double* b, cudaStream_t st);
 int subtract_device(const double* f, const double* g, double* r, int64_t count, cudaStream_t st);
 
+// apply_xy.cu: decides op->xy_fused for a 3D operator when it is built (equal
+// power-of-two x and y FFT lengths 32..512, a cluster launch that fits the device) and
+// sets the fused kernels' attributes; outside any stream capture.
+int xy_prepare(frac_op* op);
+
 // apply.cu: y = A u for `batch` vectors on device buffers; ws holds
 // apply_workspace_bytes(op, dtype, batch) bytes (unused for d = 1).
 size_t apply_workspace_bytes(const frac_op* op, int dtype, int64_t batch);

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "apply.cuh"
 #include "fft.cuh"
@@ -667,6 +668,20 @@ static int64_t rows_grid_op(const frac_op* op, int64_t nrows) {
   return rows_grid_any<T>(op->logm, nrows);
 }
 
+// Fused xy passes of the 3D FP32 apply (xy_cluster.cuh, instantiated in apply_xy.cu):
+// forward rows + y (kind FK, ODD as the column pass) into W2, and inverse y + rows
+// (kind IK) out of it.  xy_enabled: the operator takes them (op->xy_fused, set when it
+// was built) and frac_apply_3d_passes has not switched them off.
+template <int FK, bool ODD>
+int xy_fwd(const frac_op* op, const void* in, void* W2, int64_t batch, const float* lam, const CgArgs& cg,
+           const CGState* cgst, cudaStream_t st);
+template <int IK, bool ODD>
+int xy_inv(const frac_op* op, const void* W2, void* out, int64_t batch, const CgArgs& cg, cudaStream_t st);
+bool xy_enabled(const frac_op* op);
+// Blocks of one fused launch over `batch` fields (0 when the operator does not take the
+// fused passes): the per-block partial sums of the CG epilogues need that many entries.
+int64_t xy_grid_blocks(const frac_op* op, int64_t batch);
+
 // Spectrum layout for d >= 2 (axis i: n_i points, FFT length M_i, K_i = M_i/2 + 1;
 // axis 0 = x^(1) is the row axis): W1 holds the rows' half spectra column-blocked,
 // slabs of n_2 rows (KB = ceil(K_1 / B) blocks); d = 3: W2 holds the y transform,
@@ -703,6 +718,15 @@ static int pipeline(const frac_op* op, const T* lam, const void* in, void* out, 
     return FRAC_OK;
   }
   C* W2 = W1 + w1;
+  if constexpr (std::is_same<T, float>::value) {
+    if (xy_enabled(op)) {  // three passes over HBM: xy forward, z (symbol), xy inverse
+      FRAC_TRY((xy_fwd<FK, ODD>(op, in, W2, batch, lam, fwd, cgst, st)));
+      ColArgs Az{(int)n3, (int)K1, (int)KB, op->Ma[1] * KB, batch, (int)n3, (int)op->Ma[1], (int)op->Ka[1]};
+      FRAC_TRY((cols_op<T, ZSYM, ODD>(op, 2, W2, W2, Az, batch, lam, st, cgst)));
+      FRAC_TRY((xy_inv<IK, ODD>(op, W2, out, batch, inv, st)));
+      return FRAC_OK;
+    }
+  }
   const int64_t nrows = batch * n3 * n2;
   FRAC_TRY((rows_fwd_op<T, FK>(op, in, W1, n1, n2, nrows, (int)KB, st, fwd)));
   ColArgs Ay{(int)n2, (int)K1, (int)KB, KB, batch, (int)n3, (int)op->Ma[1], (int)op->Ka[1]};

@@ -190,6 +190,7 @@ struct frac_op {
   double* pinv64;    // device, prod K_i FP64 symbol of the tau preconditioner (0 where some k_i is 0 or M_i/2)
   float* pinv32;     // device, prod K_i FP32 copy
   int precond_ok;    // n_i <= M_i/2 - 1 on every axis and the symbol is positive: the tau preconditioner applies
+  int xy_fused;      // d = 3: the FP32 apply may run its xy passes fused on thread-block clusters (xy_cluster.cuh)
   size_t device_bytes;
   int device;
 };

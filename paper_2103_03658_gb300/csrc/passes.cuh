@@ -64,13 +64,16 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
 // (ln.stride() entries); tl: thread index within the group of ln.tpl().  The
 // LOGM form is the power-of-two line.
 // ---------------------------------------------------------------------------
-template <typename T, typename LN, bool ODD = false, typename In>
-__device__ __forceinline__ void row_fwd_pair_l(const LN& ln, In in, cplx_t<T>* W, int n, int64_t nrows, int KB,
+// The same with the half spectra handed to sink(which, k, value) (which = 0 for row
+// r0, 1 for r1, k in [0, M/2]) instead of stored into W; sink is called only for
+// rows below nrows.
+template <typename T, typename LN, bool ODD = false, typename In, typename Sink>
+__device__ __forceinline__ void row_fwd_pair_s(const LN& ln, In in, Sink sink, int n, int64_t nrows,
                                                const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
-                                               int tl, int ns = 0) {
+                                               int tl) {
   using C = cplx_t<T>;
   using namespace fft;
-  constexpr int E = LN::E, B = blk<T>();
+  constexpr int E = LN::E;
   const int M = ln.m(), TPL = ln.tpl();
   const int64_t r0 = 2 * pair, r1 = r0 + 1;
   const bool h0 = r0 < nrows, h1 = r1 < nrows;
@@ -109,14 +112,10 @@ __device__ __forceinline__ void row_fwd_pair_l(const LN& ln, In in, cplx_t<T>* W
 #pragma unroll
   for (int e = E / 2; e < E; ++e) buf[ln.pad(tl + e * TPL)] = v[e];
   __syncthreads();
-  if (ns <= 0) ns = n;  // rows per slab of W (the next axis' extent; n on square grids)
-  C* W0 = W + wrow<B>(h0 ? r0 : 0, ns, KB);
-  C* W1 = W + wrow<B>(h1 ? r1 : 0, ns, KB);
   auto emit = [&](int k, C z, C zc) {
     const C s = cadd(z, zc), dd = csub(z, zc);
-    const int64_t kc = wcol<B>(k, ns);
-    if (h0) W0[kc] = s;
-    if (h1) W1[kc] = C{dd.y, -dd.x};
+    if (h0) sink(0, k, s);
+    if (h1) sink(1, k, C{dd.y, -dd.x});
   };
 #pragma unroll
   for (int e = 0; e < E / 2; ++e) {
@@ -124,6 +123,25 @@ __device__ __forceinline__ void row_fwd_pair_l(const LN& ln, In in, cplx_t<T>* W
     emit(k, v[e], cconj(k == 0 ? v[e] : buf[ln.pad(M - k)]));
   }
   if (tl == 0) emit(M / 2, v[E / 2], cconj(v[E / 2]));
+}
+
+template <typename T, typename LN, bool ODD = false, typename In>
+__device__ __forceinline__ void row_fwd_pair_l(const LN& ln, In in, cplx_t<T>* W, int n, int64_t nrows, int KB,
+                                               const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
+                                               int tl, int ns = 0) {
+  using C = cplx_t<T>;
+  constexpr int B = blk<T>();
+  const int64_t r0 = 2 * pair, r1 = r0 + 1;
+  if (ns <= 0) ns = n;  // rows per slab of W (the next axis' extent; n on square grids)
+  C* W0 = W + wrow<B>(r0 < nrows ? r0 : 0, ns, KB);
+  C* W1 = W + wrow<B>(r1 < nrows ? r1 : 0, ns, KB);
+  row_fwd_pair_s<T, LN, ODD>(
+      ln, in,
+      [&](int which, int k, C z) {
+        const int64_t kc = wcol<B>(k, ns);
+        (which ? W1 : W0)[kc] = z;
+      },
+      n, nrows, tw, pair, buf, tl);
 }
 template <typename T, int LOGM, bool ODD = false, typename In>
 __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t nrows, int KB,
@@ -137,28 +155,26 @@ __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t
 // -> iFFT -> two real rows; out(row, x, value) receives the first n entries
 // of each row < nrows (ODD: entries 1..n, as x = 0..n-1).
 // ---------------------------------------------------------------------------
-template <typename T, typename LN, bool ODD = false, typename Out>
-__device__ __forceinline__ void row_inv_pair_l(const LN& ln, const cplx_t<T>* W, int n, int64_t nrows, int KB,
+// The same with the half spectra read through src(which, x) (which = 0 for row r0, 1
+// for r1, x in [0, M/2]) instead of from W; src is called only for rows below nrows.
+template <typename T, typename LN, bool ODD = false, typename Src, typename Out>
+__device__ __forceinline__ void row_inv_pair_s(const LN& ln, Src src, int n, int64_t nrows,
                                                const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
-                                               int tl, Out out, int ns = 0) {
+                                               int tl, Out out) {
   using C = cplx_t<T>;
   using namespace fft;
-  constexpr int E = LN::E, B = blk<T>();
+  constexpr int E = LN::E;
   const int M = ln.m(), TPL = ln.tpl();
   const int64_t r0 = 2 * pair, r1 = r0 + 1;
   const bool h0 = r0 < nrows, h1 = r1 < nrows;
   C v[E];
-  if (ns <= 0) ns = n;  // rows per slab of W
-  const C* W0 = W + wrow<B>(h0 ? r0 : 0, ns, KB);
-  const C* W1 = W + wrow<B>(h1 ? r1 : 0, ns, KB);
   // line z = W0 + i W1 extended Hermitian-wise: z[x] = W0[x] + i W1[x] and
   // z[M-x] = conj(W0[x]) + i conj(W1[x]) for x in [0, M/2], so each half
   // spectrum entry is read once; the thread that reads W[x] leaves z[M-x] in
   // the line buffer for its owner
   auto load = [&](int x, C& lo, C& hi) {
-    const int64_t kc = wcol<B>(x, ns);
-    const C v0 = h0 ? W0[kc] : C{0, 0};
-    const C v1 = h1 ? W1[kc] : C{0, 0};
+    const C v0 = h0 ? src(0, x) : C{0, 0};
+    const C v1 = h1 ? src(1, x) : C{0, 0};
     lo = C{v0.x - v1.y, v0.y + v1.x};  // v0 + i v1
     hi = C{v0.x + v1.y, v1.x - v0.y};  // conj(v0) + i conj(v1)
   };
@@ -200,6 +216,19 @@ __device__ __forceinline__ void row_inv_pair_l(const LN& ln, const cplx_t<T>* W,
     }
   }
 }
+template <typename T, typename LN, bool ODD = false, typename Out>
+__device__ __forceinline__ void row_inv_pair_l(const LN& ln, const cplx_t<T>* W, int n, int64_t nrows, int KB,
+                                               const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
+                                               int tl, Out out, int ns = 0) {
+  using C = cplx_t<T>;
+  constexpr int B = blk<T>();
+  const int64_t r0 = 2 * pair, r1 = r0 + 1;
+  if (ns <= 0) ns = n;  // rows per slab of W
+  const C* W0 = W + wrow<B>(r0 < nrows ? r0 : 0, ns, KB);
+  const C* W1 = W + wrow<B>(r1 < nrows ? r1 : 0, ns, KB);
+  row_inv_pair_s<T, LN, ODD>(
+      ln, [&](int which, int x) { return (which ? W1 : W0)[wcol<B>(x, ns)]; }, n, nrows, tw, pair, buf, tl, out);
+}
 template <typename T, int LOGM, bool ODD = false, typename Out>
 __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t nrows, int KB,
                                              const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
@@ -233,10 +262,14 @@ struct ColArgs {
                        // SYM2: Ky = K_2, the symbol's rows (the symbol is stored in column tiles)
 };
 
+// src_tile (YFWD) / dst_tile (YINV): when given, the tile's n rows of B lanes are read
+// from / written to there (row j at j B) instead of the W1 slab in global memory (the
+// fused xy passes keep that slab in distributed shared memory).
 template <typename T, typename LN, int MODE, bool ODD = false>
 __device__ __forceinline__ void col_tile_l(const LN& ln, const cplx_t<T>* in, cplx_t<T>* out, const ColArgs& A,
                                            const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, int64_t o,
-                                           int64_t tile, cplx_t<T>* sm, int cl, int tl) {
+                                           int64_t tile, cplx_t<T>* sm, int cl, int tl,
+                                           const cplx_t<T>* src_tile = nullptr, cplx_t<T>* dst_tile = nullptr) {
   using C = cplx_t<T>;
   using namespace fft;
   constexpr int E = LN::E, B = blk<T>();
@@ -269,14 +302,18 @@ __device__ __forceinline__ void col_tile_l(const LN& ln, const cplx_t<T>* in, cp
       v[e] = live ? src[(int64_t)k2 * KB * zB] : C{0, 0};
     }
   } else if constexpr (!ODD) {
-    const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl : in + (o * KB + tile) * nB + cl;
+    const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl
+                 : src_tile       ? src_tile + cl
+                                  : in + (o * KB + tile) * nB + cl;
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {  // j < n <= M/2; the rest is zero padding
       const int j = tl + e * TPL;
       v[e] = (live && j < n) ? src[(int64_t)j * B] : C{0, 0};
     }
   } else {  // odd extension: row j at j + 1, its negative at M - 1 - j
-    const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl : in + (o * KB + tile) * nB + cl;
+    const C* src = (MODE == ZSYM) ? in + o * W2slab + tile * nB + cl
+                 : src_tile       ? src_tile + cl
+                                  : in + (o * KB + tile) * nB + cl;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = tl + e * TPL;
@@ -319,7 +356,8 @@ __device__ __forceinline__ void col_tile_l(const LN& ln, const cplx_t<T>* in, cp
     }
   } else {
     C* dst = (MODE == ZSYM) ? out + o * W2slab + tile * nB + cl
-                            : out + (o * KB + tile) * nB + cl;  // SYM2 in place; YINV to W1 slab o
+             : dst_tile       ? dst_tile + cl
+                              : out + (o * KB + tile) * nB + cl;  // SYM2 in place; YINV to W1 slab o
     if constexpr (!ODD) {
 #pragma unroll
       for (int e = 0; e < E / 2; ++e) {
