@@ -11,7 +11,10 @@
 // run the inverse row FFTs (as k_rows_inv).  The x-spectrum slab W1 of the five-pass
 // schedule never reaches global memory: per FP32 apply the passes move u, W2 (three
 // times), the symbol and y instead of also W1 four times.  The arithmetic is that of
-// the five-pass kernels (the same device functions), so the results are the same.
+// the five-pass kernels (the same device functions); the compiler may fuse multiplies
+// and adds differently in these kernels, so the two agree to FP32 rounding.  Measured
+// slower than the five passes on GB300 (W1 largely stays in L2 between those passes,
+// and these kernels hold one CTA per SM), so frac_apply_3d_passes selects them.
 //
 // Waits: two cluster barriers per kernel (forward: at the start, so that every CTA
 // has started before remote writes, and after the row phase; inverse: after the
