@@ -64,11 +64,12 @@ __device__ __forceinline__ double block_sum_all(double v, double* red) {
 // (ln.stride() entries); tl: thread index within the group of ln.tpl().  The
 // LOGM form is the power-of-two line.
 // ---------------------------------------------------------------------------
-// The same with the half spectra handed to sink(which, k, value) (which = 0 for row
-// r0, 1 for r1, k in [0, M/2]) instead of stored into W; sink is called only for
-// rows below nrows.
-template <typename T, typename LN, bool ODD = false, typename In, typename Sink>
-__device__ __forceinline__ void row_fwd_pair_s(const LN& ln, In in, Sink sink, int n, int64_t nrows,
+// The same with the half spectra handed to a sink(k, U0, U1, h0, h1) (the entries k in
+// [0, M/2] of rows r0 and r1; h0, h1: whether r0, r1 are rows below nrows, whose entry
+// the sink stores) instead of stored into W.  make_sink() gives the sink once the
+// transform is done (so that its addressing is not live across the FFT).
+template <typename T, typename LN, bool ODD = false, typename In, typename MakeSink>
+__device__ __forceinline__ void row_fwd_pair_s(const LN& ln, In in, MakeSink make_sink, int n, int64_t nrows,
                                                const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
                                                int tl) {
   using C = cplx_t<T>;
@@ -112,10 +113,10 @@ __device__ __forceinline__ void row_fwd_pair_s(const LN& ln, In in, Sink sink, i
 #pragma unroll
   for (int e = E / 2; e < E; ++e) buf[ln.pad(tl + e * TPL)] = v[e];
   __syncthreads();
+  auto sink = make_sink();
   auto emit = [&](int k, C z, C zc) {
     const C s = cadd(z, zc), dd = csub(z, zc);
-    if (h0) sink(0, k, s);
-    if (h1) sink(1, k, C{dd.y, -dd.x});
+    sink(k, s, C{dd.y, -dd.x}, h0, h1);
   };
 #pragma unroll
   for (int e = 0; e < E / 2; ++e) {
@@ -133,13 +134,16 @@ __device__ __forceinline__ void row_fwd_pair_l(const LN& ln, In in, cplx_t<T>* W
   constexpr int B = blk<T>();
   const int64_t r0 = 2 * pair, r1 = r0 + 1;
   if (ns <= 0) ns = n;  // rows per slab of W (the next axis' extent; n on square grids)
-  C* W0 = W + wrow<B>(r0 < nrows ? r0 : 0, ns, KB);
-  C* W1 = W + wrow<B>(r1 < nrows ? r1 : 0, ns, KB);
   row_fwd_pair_s<T, LN, ODD>(
       ln, in,
-      [&](int which, int k, C z) {
-        const int64_t kc = wcol<B>(k, ns);
-        (which ? W1 : W0)[kc] = z;
+      [&]() {
+        C* W0 = W + wrow<B>(r0 < nrows ? r0 : 0, ns, KB);
+        C* W1 = W + wrow<B>(r1 < nrows ? r1 : 0, ns, KB);
+        return [=](int k, C z0, C z1, bool h0, bool h1) {
+          const int64_t kc = wcol<B>(k, ns);
+          if (h0) W0[kc] = z0;
+          if (h1) W1[kc] = z1;
+        };
       },
       n, nrows, tw, pair, buf, tl);
 }
@@ -155,8 +159,9 @@ __device__ __forceinline__ void row_fwd_pair(In in, cplx_t<T>* W, int n, int64_t
 // -> iFFT -> two real rows; out(row, x, value) receives the first n entries
 // of each row < nrows (ODD: entries 1..n, as x = 0..n-1).
 // ---------------------------------------------------------------------------
-// The same with the half spectra read through src(which, x) (which = 0 for row r0, 1
-// for r1, x in [0, M/2]) instead of from W; src is called only for rows below nrows.
+// The same with the half spectra read through src(x, v0, v1, h0, h1) (sets v0, v1 to the
+// entries x in [0, M/2] of rows r0, r1, zero for a row not below nrows: h0, h1 false)
+// instead of from W.
 template <typename T, typename LN, bool ODD = false, typename Src, typename Out>
 __device__ __forceinline__ void row_inv_pair_s(const LN& ln, Src src, int n, int64_t nrows,
                                                const cplx_t<T>* __restrict__ tw, int64_t pair, cplx_t<T>* buf,
@@ -173,8 +178,8 @@ __device__ __forceinline__ void row_inv_pair_s(const LN& ln, Src src, int n, int
   // spectrum entry is read once; the thread that reads W[x] leaves z[M-x] in
   // the line buffer for its owner
   auto load = [&](int x, C& lo, C& hi) {
-    const C v0 = h0 ? src(0, x) : C{0, 0};
-    const C v1 = h1 ? src(1, x) : C{0, 0};
+    C v0, v1;
+    src(x, v0, v1, h0, h1);
     lo = C{v0.x - v1.y, v0.y + v1.x};  // v0 + i v1
     hi = C{v0.x + v1.y, v1.x - v0.y};  // conj(v0) + i conj(v1)
   };
@@ -227,7 +232,13 @@ __device__ __forceinline__ void row_inv_pair_l(const LN& ln, const cplx_t<T>* W,
   const C* W0 = W + wrow<B>(r0 < nrows ? r0 : 0, ns, KB);
   const C* W1 = W + wrow<B>(r1 < nrows ? r1 : 0, ns, KB);
   row_inv_pair_s<T, LN, ODD>(
-      ln, [&](int which, int x) { return (which ? W1 : W0)[wcol<B>(x, ns)]; }, n, nrows, tw, pair, buf, tl, out);
+      ln,
+      [&](int x, C& v0, C& v1, bool h0, bool h1) {
+        const int64_t kc = wcol<B>(x, ns);
+        v0 = h0 ? W0[kc] : C{0, 0};
+        v1 = h1 ? W1[kc] : C{0, 0};
+      },
+      n, nrows, tw, pair, buf, tl, out);
 }
 template <typename T, int LOGM, bool ODD = false, typename Out>
 __device__ __forceinline__ void row_inv_pair(const cplx_t<T>* W, int n, int64_t nrows, int KB,

@@ -76,10 +76,13 @@ k_xy_fwd(const float* u, float2* __restrict__ W2, XyArgs X, const float* __restr
   for (int i = 0; i < rounds; ++i) {
     const int64_t pair = ((int64_t)i * kXyC + rank) * LINES + line;
     const int64_t r0 = 2 * pair;
-    auto sink = [&](int which, int k, C z) {
-      const int kb = k / B, owner = kb % kXyC, lk = kb / kXyC;
-      C* dst = static_cast<C*>(__cluster_map_shared_rank((void*)S, owner));
-      dst[((int64_t)lk * n2 + r0 + which) * B + (k % B)] = z;
+    auto sink = [&]() {
+      return [&](int k, C z0, C z1, bool h0, bool h1) {
+        const int kb = k / B, owner = kb % kXyC, lk = kb / kXyC;
+        C* dst = static_cast<C*>(__cluster_map_shared_rank((void*)S, owner)) + ((int64_t)lk * n2 + r0) * B + (k % B);
+        if (h0) dst[0] = z0;
+        if (h1) dst[B] = z1;
+      };
     };
     if constexpr (FK == RF_CG) {
       const float be = (float)st->beta;
@@ -153,10 +156,12 @@ k_xy_inv(const float2* __restrict__ W2, float* __restrict__ y, XyArgs X, const f
   for (int i = 0; i < rounds; ++i) {
     const int64_t pair = ((int64_t)i * kXyC + rank) * LINES + line;
     const int64_t r0 = 2 * pair;
-    auto src = [&](int which, int x) {
+    auto src = [&](int x, C& v0, C& v1, bool h0, bool h1) {
       const int kb = x / B, owner = kb % kXyC, lk = kb / kXyC;
-      const C* from = static_cast<const C*>(__cluster_map_shared_rank((void*)S, owner));
-      return from[((int64_t)lk * n2 + r0 + which) * B + (x % B)];
+      const C* from =
+          static_cast<const C*>(__cluster_map_shared_rank((void*)S, owner)) + ((int64_t)lk * n2 + r0) * B + (x % B);
+      v0 = h0 ? from[0] : C{0.0f, 0.0f};
+      v1 = h1 ? from[B] : C{0.0f, 0.0f};
     };
     row_inv_pair_s<float, LN, RODD>(LN{}, src, n1, n2, tw, pair, work + line * LN::stride(), tl,
                                     [&](int64_t row, int x, float v) {
