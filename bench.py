@@ -271,12 +271,12 @@ def apply_model_bytes(fields: int) -> float:
 
 # DRAM bytes per field (dram__bytes_read.sum + dram__bytes_write.sum of one
 # launch / fields in it) of the kernels as they stand, from one ncu capture of
-# the 65-field apply (profiles/apply2d_1023_65fields_dram.md), scaled to a launch
+# the 65-field apply (profiles/apply2d_1023_65fields_ncu_full.md), scaled to a launch
 # by the fields it processes.  Remove an entry when its kernel changes.
 DRAM_TRAFFIC_PER_FIELD = {
-    "rows_fwd_f32_M2048": (274.020864e6 + 493.092608e6) / 65,
-    "cols_sym2_f32_M2048": (551.746048e6 + 487.677952e6) / 65,
-    "rows_inv_f32_M2048": (546.918656e6 + 243.917056e6) / 65,
+    "rows_fwd_f32_M2048": (274.043136e6 + 492.188672e6) / 65,
+    "cols_sym2_f32_M2048": (551.528960e6 + 484.491520e6) / 65,
+    "rows_inv_f32_M2048": (546.940672e6 + 239.797760e6) / 65,
 }
 
 
