@@ -156,11 +156,13 @@ int launch(const B2Args& a, int C, int grid, size_t smem, bool mx, cudaStream_t 
   return mx ? mx_kernel_launch(a, C, grid, smem, st) : kernel_launch<false>(a, C, grid, smem, st);
 }
 
-// Autotuner timings: microseconds per CG iteration of a class's probe problem
-// (size n_probe) with one CTA, and with one cluster of each size.
+// Autotuner timings of a class's probe problem (size n_probe) with one CTA, and with
+// one cluster of each size: microseconds per FP32 CG iteration (t) and per
+// refinement residual, the FP64 apply with the solve's fixed costs (t64).
 struct ClassTiming {
   int n_probe = 0;
   double t[kNumSizes] = {-1, -1, -1, -1, -1};
+  double t64[kNumSizes] = {0, 0, 0, 0, 0};
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int64_t>, ClassTiming> g_tune;  // (device, FFT length M)
@@ -185,8 +187,10 @@ B2Prob make_prob(const frac_op* op, const double* f, double* u, const frac_solve
   return p;
 }
 
-// Times kProbeIters CG iterations of (op, f) alone, on one CTA and on one
-// cluster of each launchable size; the solution goes to scratch.
+// Times (op, f) alone, on one CTA and on one cluster of each launchable size, as
+// solves of exactly kProbeIters and 2 kProbeIters FP32 CG iterations (each followed by
+// one FP64 residual); their difference gives the time of an iteration, the rest that
+// of the residual.  The solution goes to scratch.
 int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming* out) {
   const int64_t M = op->M;
   const int n = (int)op->n;
@@ -207,10 +211,12 @@ int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming
   SlotSize z;
   z.add(n, M);
   FRAC_TRY(b.get(&scratch, slot_bytes(z)));
-  frac_solve_opts o{0.0, kProbeIters, FRAC_MIXED_IR, 0, FRAC_PRECOND_TAU, 1e-30};  // exactly kProbeIters iterations
-  B2Prob hp = make_prob(op, f, u, &o);
+  // rtol 0 and an unreachable inner tolerance: exactly max_iter iterations, then one residual
+  frac_solve_opts o1{0.0, kProbeIters, FRAC_MIXED_IR, 0, FRAC_PRECOND_TAU, 1e-30};
+  frac_solve_opts o2 = o1;
+  o2.max_iter = 2 * kProbeIters;
+  const B2Prob hp[2] = {make_prob(op, f, u, &o1), make_prob(op, f, u, &o2)};
   B2Slot hs = carve(scratch, z);
-  FRAC_CUDA_TRY(cudaMemcpyAsync(dp, &hp, sizeof(hp), cudaMemcpyHostToDevice, st));
   FRAC_CUDA_TRY(cudaMemcpyAsync(ds, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
   cudaEvent_t e0, e1;
   FRAC_CUDA_TRY(cudaEventCreate(&e0));
@@ -228,36 +234,57 @@ int probe_class(const frac_op* op, const double* f, cudaStream_t st, ClassTiming
     a.next = next;
     a.cslots = ds;
     a.lslots = ds;
-    float best = 1e30f;
-    for (int rep = 0; rep < 2 && rc == FRAC_OK; ++rep) {  // the first run also loads the code
-      if (cudaMemsetAsync(next, 0, 2 * sizeof(unsigned int), st) != cudaSuccess ||
-          cudaEventRecord(e0, st) != cudaSuccess) {
+    float best[2] = {1e30f, 1e30f};
+    for (int k = 0; k < 2 && rc == FRAC_OK; ++k) {
+      if (cudaMemcpyAsync(dp, &hp[k], sizeof(B2Prob), cudaMemcpyHostToDevice, st) != cudaSuccess) {
         rc = FRAC_ECUDA;
         break;
       }
-      rc = launch(a, C, C, smem, mx, st);
-      if (rc != FRAC_OK) break;
-      float ms = 0.0f;
-      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        rc = FRAC_ECUDA;
-        break;
+      for (int rep = 0; rep < 2 - k && rc == FRAC_OK; ++rep) {  // the first run also loads the code
+        if (cudaMemsetAsync(next, 0, 2 * sizeof(unsigned int), st) != cudaSuccess ||
+            cudaEventRecord(e0, st) != cudaSuccess) {
+          rc = FRAC_ECUDA;
+          break;
+        }
+        rc = launch(a, C, C, smem, mx, st);
+        if (rc != FRAC_OK) break;
+        float ms = 0.0f;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          rc = FRAC_ECUDA;
+          break;
+        }
+        best[k] = std::min(best[k], ms);
       }
-      best = std::min(best, ms);
     }
-    if (rc == FRAC_OK) out->t[i] = 1e3 * best / kProbeIters;
+    if (rc == FRAC_OK) {
+      // the second solve's extra kProbeIters iterations; at least a tenth of the first
+      // solve's mean (timing noise), the residual what is left of the first solve
+      const double it = std::max(1e3 * (best[1] - best[0]), 0.1 * 1e3 * best[0]) / kProbeIters;
+      out->t[i] = it;
+      out->t64[i] = std::max(0.0, 1e3 * best[0] - kProbeIters * it);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return settle(rc);
 }
 
-// Relative cost model of one problem: plain CG iterations ~ n^(alpha/2)
-// (condition number ~ n^alpha); with the tau preconditioner they hardly grow
-// (about 5-15 to 1e-10 in 2D); per-iteration time of its class measured at
-// n_probe, half of it proportional to the number of rows.
-double est_iters(int n, double alpha, bool pcg) {
-  return pcg ? 10.0 + std::log2((double)n) : 20.0 + 6.0 * std::pow((double)n, 0.5 * alpha);
+// Cost model of one problem: `outer` refinement steps, each an FP32 CG solve to the
+// inner tolerance and an FP64 residual; the CG iterations of a step grow like
+// alpha log n with the tau preconditioner (about 2 + alpha log2 n per step in the 2D
+// mixes measured) and like n^(alpha/2) without it (condition number ~ n^alpha).
+// Per-iteration and per-residual times of its class measured at n_probe, scaled by the
+// number of line transforms (the columns' share is the same for every n of a class).
+double est_iters(int n, double alpha, bool pcg, int outer) {
+  return pcg ? outer * (2.0 + alpha * std::log2((double)n)) : 20.0 + 6.0 * std::pow((double)n, 0.5 * alpha);
+}
+
+// Refinement steps to rtol when each gains a factor inner_tol (the last residual
+// included), at least one.
+int est_outer(double rtol, double inner_tol) {
+  if (!(rtol > 0.0 && rtol < 1.0 && inner_tol > 0.0 && inner_tol < 1.0)) return 1;
+  return std::max(1, (int)std::ceil(std::log(rtol) / std::log(inner_tol) - 1e-9));
 }
 
 struct Item {
@@ -266,6 +293,7 @@ struct Item {
   int n;
   double alpha;
   bool pcg;
+  int outer;  // estimated refinement steps
 };
 
 // Makespan of the two queues on `ncl` clusters of C CTAs, classes with lvl(M) >= cut cluster-wide.
@@ -275,10 +303,14 @@ double simulate(const std::vector<Item>& items, const std::map<int64_t, ClassTim
   std::vector<std::pair<double, const Item*>> cl, lo;
   for (const Item& it : items) {
     const ClassTiming& t = tm.at(it.M);
-    const double scale = 0.5 + 0.5 * (double)it.n / t.n_probe;
+    // line transforms of a refinement pass: n row lines (n / 2 pairs, forward and
+    // inverse) and 2 K columns of the half spectrum, K = M / 2 + 1 for the whole class
+    const double K = (double)(it.M / 2 + 1);
+    const double scale = (2.0 * K + it.n) / (2.0 * K + t.n_probe);
     const bool wide = C > 1 && lvl(it.M) >= cut && t.t[si] > 0;
-    const double per = wide ? t.t[si] : t.t[0];
-    (wide ? cl : lo).emplace_back(est_iters(it.n, it.alpha, it.pcg) * per * scale, &it);
+    const int k = wide ? si : 0;
+    const double cost = est_iters(it.n, it.alpha, it.pcg, it.outer) * t.t[k] + it.outer * t.t64[k];
+    (wide ? cl : lo).emplace_back(cost * scale, &it);
   }
   auto desc = [](const std::pair<double, const Item*>& a, const std::pair<double, const Item*>& b) {
     return a.first > b.first;
@@ -353,8 +385,9 @@ int solve_batch_2d(int64_t count, const frac_op* const* ops, const double* const
   std::map<int64_t, int64_t> rep;  // M -> largest problem of that class
   for (int64_t t = 0; t < count; ++t) {
     const frac_op* op = ops[idx[t]];
+    const double itol = opts->inner_tol > 0.0 ? opts->inner_tol : auto_inner_tol(op, opts->rtol);
     items.push_back(Item{idx[t], op->M, (int)op->n, op->prob.alpha,
-                         opts->precond == FRAC_PRECOND_TAU && op->precond_ok != 0});
+                         opts->precond == FRAC_PRECOND_TAU && op->precond_ok != 0, est_outer(opts->rtol, itol)});
     auto it = rep.find(op->M);
     if (it == rep.end() || ops[it->second]->n < op->n) rep[op->M] = idx[t];
   }
