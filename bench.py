@@ -480,6 +480,7 @@ def extra_measurements(fg, torch, u32, op, barrier) -> dict:
         f3 = torch.tensor(synth.ball_power_rhs(3, 255, alpha), device="cuda")
         res = {}
         for prec in precs:
+            op3.solve(f3, rtol=1e-10, precision=prec)  # warm-up: kernel loading, graph instantiation
             barrier()
             t0 = time.perf_counter()
             _, info = op3.solve(f3, rtol=1e-10, precision=prec)
