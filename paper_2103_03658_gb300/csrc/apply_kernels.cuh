@@ -337,6 +337,22 @@ k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam
   col_tile<T, LOGM, MODE, ODD>(in, out, A, lam, tw, o, tile, reinterpret_cast<C*>(smem_raw), cl, tl);
 }
 
+// Columns of the 2D tau preconditioner two to a transform (col_pair_tau_l): B lines per
+// block, line q = unit B + cl of slab o.
+template <typename T, int LOGM>
+__global__ void __launch_bounds__(blk<T>() * tpl(LOGM), minb_cols<T>(blk<T>() * tpl(LOGM)))
+k_cols_tau_pairs(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, int64_t qtiles, const T* __restrict__ lam,
+                 const cplx_t<T>* __restrict__ tw, const CGState* st) {
+  using C = cplx_t<T>;
+  constexpr int B = blk<T>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (st && st->done) return;
+  const int cl = threadIdx.x % B, tl = threadIdx.x / B;
+  const int64_t o = blockIdx.x / qtiles, q = (blockIdx.x % qtiles) * B + cl;
+  using LN = P2Line<LOGM, tile_shift(LOGM)>;
+  col_pair_tau_l<T, LN>(LN{}, in, out, A, lam, tw, o, q, reinterpret_cast<C*>(smem_raw), cl, tl);
+}
+
 #ifdef FRAC_MX_TU
 template <typename T, int MODE, bool ODD, int NTMAX>
 __global__ void __launch_bounds__(NTMAX, mx_minb<T>(NTMAX)) k_cols_mx(MxLine ln, const cplx_t<T>* in, cplx_t<T>* out, ColArgs A,
@@ -455,13 +471,22 @@ static int launch_cols(const void* in, void* out, const ColArgs& A, int64_t nout
   using C = cplx_t<T>;
   constexpr int B = blk<T>();
   const size_t sm = (size_t)B * line_stride_tile(LOGM) * sizeof(C);
-  auto kern = k_cols<T, LOGM, MODE, ODD>;
-  FRAC_TRY(set_smem(kern, sm));
-  const int64_t blocks = nouter * A.tiles;
   static const char* names[2][4] = {{"cols_sym2", "cols_yfwd", "cols_zsym", "cols_yinv"},
                                     {"cols_sym2_tau", "cols_yfwd_tau", "cols_zsym_tau", "cols_yinv_tau"}};
   char nb[48];
   prof::Scope ps(kname<T>(nb, names[ODD ? 1 : 0][MODE], LOGM), st);
+  if constexpr (MODE == SYM2 && ODD) {  // the 2D tau preconditioner: two columns a transform
+    auto kp = k_cols_tau_pairs<T, LOGM>;
+    FRAC_TRY(set_smem(kp, sm));
+    const int64_t qtiles = cdiv(cdiv(A.K, 2), B);
+    kp<<<(unsigned)(nouter * qtiles), B * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, qtiles, lam,
+                                                              tw_table<T>(LOGM), cgst);
+    FRAC_CUDA_TRY(cudaGetLastError());
+    return FRAC_OK;
+  }
+  auto kern = k_cols<T, LOGM, MODE, ODD>;
+  FRAC_TRY(set_smem(kern, sm));
+  const int64_t blocks = nouter * A.tiles;
   kern<<<(unsigned)blocks, B * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, lam, tw_table<T>(LOGM), cgst);
   FRAC_CUDA_TRY(cudaGetLastError());
   return FRAC_OK;

@@ -384,6 +384,82 @@ __device__ __forceinline__ void col_tile_l(const LN& ln, const cplx_t<T>* in, cp
     }
   }
 }
+// Columns of the tau preconditioner (SYM2 on the odd extension), two per transform.
+// After the odd-extension row pass every entry of W is purely imaginary, i s(j, k1)
+// with s real, so the full-width pass would spend a complex transform on one real
+// column.  Here line q carries columns c = 2q and c + 1 (one tile, B even) as
+// z(j) = s(j, c) + i s(j, c + 1): with the odd extension along this axis the transform
+// of each real part is purely imaginary, so after the forward transform the imaginary
+// part belongs to column c and the real part to c + 1; each is scaled by its own
+// symbol entry, and the inverse transform returns s'(j, c) + i s'(j, c + 1), stored
+// back as i s'.  The result equals the full-width pass's up to rounding (which leaves
+// a rounding-size real part there); a column c + 1 >= K is empty.  sm: the block's B
+// line buffers (ln.stride_tile() entries each); cl: this lane's line in the block.
+// The imaginary parts of p[0] and p[1] (two adjacent complex entries, 2-entry aligned),
+// in one vector load for FP32.
+template <typename T>
+__device__ __forceinline__ cplx_t<T> im_pair(const cplx_t<T>* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    return cplx_t<T>{q.y, q.w};
+  } else {
+    return cplx_t<T>{p[0].y, p[1].y};
+  }
+}
+
+template <typename T, typename LN>
+__device__ __forceinline__ void col_pair_tau_l(const LN& ln, const cplx_t<T>* in, cplx_t<T>* out, const ColArgs& A,
+                                               const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, int64_t o,
+                                               int64_t q, cplx_t<T>* sm, int cl, int tl) {
+  using C = cplx_t<T>;
+  constexpr int E = LN::E, B = blk<T>();
+  static_assert(B % 2 == 0, "a column pair lies in one tile");
+  const int M = ln.m(), TPL = ln.tpl(), LS = ln.stride_tile();
+  C* buf = sm + cl * LS;
+  const int n = A.n, K = A.K, KB = A.KB;
+  const int64_t nB = (int64_t)n * B;
+  const int64_t c = 2 * q, tile = c / B;
+  const int lt = (int)(c % B);
+  const bool la = c < K, lb = c + 1 < K;
+  const C* src = in + (o * KB + (la ? tile : 0)) * nB + lt;
+  C v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {  // odd extension: row j at j + 1, its negative at M - 1 - j
+    const int j = tl + e * TPL;
+    const bool pos = j >= 1 && j <= n, neg = !pos && j >= M - n;
+    C w = C{0, 0};
+    if (la && (pos || neg)) {
+      const C im = im_pair<T>(src + (int64_t)(pos ? j - 1 : M - 1 - j) * B);
+      const T sg = pos ? T(1) : T(-1);
+      w = C{sg * im.x, lb ? sg * im.y : T(0)};
+    }
+    v[e] = w;
+  }
+  ln.template fft<false, false, false>(v, buf, tl, tw);
+  // symbol entry (kr, k1) at (k1 / B) K_2 B + kr B + k1 % B: columns c, c + 1 adjacent
+  const T* lrow = lam + tile * A.Ky * B + lt;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int k = tl + e * TPL;
+    const int kr = k <= M / 2 ? k : M - k;
+    // both entries in one aligned load (c even; the tiles are padded to B columns, so
+    // entry c + 1 exists even past K, and an empty column's factor is zero)
+    const C s2 = la ? *reinterpret_cast<const C*>(lrow + (int64_t)kr * B) : C{0, 0};
+    v[e] = C{v[e].x * (lb ? s2.y : T(0)), v[e].y * s2.x};
+  }
+  ln.template fft<true, false, false>(v, buf, tl, tw);
+  if (!la) return;
+  C* dst = out + (o * KB + tile) * nB + lt;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = tl + e * TPL;
+    if (j >= 1 && j <= n) {
+      dst[(int64_t)(j - 1) * B] = C{T(0), v[e].x};
+      if (lb) dst[(int64_t)(j - 1) * B + 1] = C{T(0), v[e].y};
+    }
+  }
+}
+
 template <typename T, int LOGM, int MODE, bool ODD = false>
 __device__ __forceinline__ void col_tile(const cplx_t<T>* in, cplx_t<T>* out, const ColArgs& A,
                                          const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, int64_t o,
