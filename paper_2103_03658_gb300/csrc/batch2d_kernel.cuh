@@ -241,12 +241,14 @@ struct Solver {
                                       c.tw32, pair_of(c, i), rb, tl);
     c.g.sync();
     {
+      // two real columns per transform (col_pair_tau_l): QT groups of 4 column pairs
       const ColArgs A{n, K, KB32, KB32, 1, 0, 0, K};
       const int ts = tid / (4 * TPL), w = tid % (4 * TPL);
-      const int cr = (KB32 + c.g.G * TPR32 - 1) / (c.g.G * TPR32);
+      const int QT = ((K + 1) / 2 + 3) / 4;
+      const int cr = (QT + c.g.G * TPR32 - 1) / (c.g.G * TPR32);
       for (int i = 0; i < cr; ++i)
-        col_tile_l<float, LNT, SYM2, true>(lnt(c), W, W, A, c.P->pinv32, c.tw32, 0, tile_of(c, i, ts, TPR32, KB32),
-                                           reinterpret_cast<float2*>(c.smem) + min(ts, TPR32) * 4 * LST, w % 4, w / 4);
+        col_pair_tau_l<float, LNT>(lnt(c), W, W, A, c.P->pinv32, c.tw32, 0, tile_of(c, i, ts, TPR32, QT) * 4 + w % 4,
+                                   reinterpret_cast<float2*>(c.smem) + min(ts, TPR32) * 4 * LST, w % 4, w / 4);
     }
     c.g.sync();
     float s = 0.0f;
