@@ -247,7 +247,7 @@ struct Solver {
       const int QT = ((K + 1) / 2 + 3) / 4;
       const int cr = (QT + c.g.G * TPR32 - 1) / (c.g.G * TPR32);
       for (int i = 0; i < cr; ++i)
-        col_pair_tau_l<float, LNT>(lnt(c), W, W, A, c.P->pinv32, c.tw32, 0, tile_of(c, i, ts, TPR32, QT) * 4 + w % 4,
+        col_pair_tau_l<float, LNT, SYM2>(lnt(c), W, W, A, c.P->pinv32, c.tw32, 0, tile_of(c, i, ts, TPR32, QT) * 4 + w % 4,
                                    reinterpret_cast<float2*>(c.smem) + min(ts, TPR32) * 4 * LST, w % 4, w / 4);
     }
     c.g.sync();

@@ -384,35 +384,38 @@ __device__ __forceinline__ void col_tile_l(const LN& ln, const cplx_t<T>* in, cp
     }
   }
 }
-// Columns of the tau preconditioner (SYM2 on the odd extension), two per transform.
-// After the odd-extension row pass every entry of W is purely imaginary, i s(j, k1)
-// with s real, so the full-width pass would spend a complex transform on one real
-// column.  Here line q carries columns c = 2q and c + 1 (one tile, B even) as
-// z(j) = s(j, c) + i s(j, c + 1): with the odd extension along this axis the transform
-// of each real part is purely imaginary, so after the forward transform the imaginary
-// part belongs to column c and the real part to c + 1; each is scaled by its own
-// symbol entry, and the inverse transform returns s'(j, c) + i s'(j, c + 1), stored
-// back as i s'.  The result equals the full-width pass's up to rounding (which leaves
-// a rounding-size real part there); a column c + 1 >= K is empty.  sm: the block's B
-// line buffers (ln.stride_tile() entries each); cl: this lane's line in the block.
-// The imaginary parts of p[0] and p[1] (two adjacent complex entries, 2-entry aligned),
-// in one vector load for FP32.
-template <typename T>
-__device__ __forceinline__ cplx_t<T> im_pair(const cplx_t<T>* p) {
+// Columns of the tau preconditioner (SYM2, and ZSYM in 3D, on the odd extension), two
+// per transform.  After the odd-extension row pass every entry of the 2D spectrum W is
+// purely imaginary, i s(j, k1) with s real (in 3D the odd y pass leaves W2 purely real,
+// r(j3, c)), so the full-width pass would spend a complex transform on one real column.
+// Here line q carries columns c = 2q and c + 1 (one tile, B even) as z(j) = s(j, c) +
+// i s(j, c + 1): with the odd extension along this axis the transform of each real part
+// is purely imaginary, so after the forward transform the imaginary part belongs to
+// column c and the real part to c + 1; each is scaled by its own symbol entry, and the
+// inverse transform returns s'(j, c) + i s'(j, c + 1), stored back as i s' (SYM2) or s'
+// (ZSYM).  The result equals the full-width pass's up to rounding (which leaves a
+// rounding-size real (SYM2) or imaginary (ZSYM) part there); a column past the half
+// spectrum (k1 >= K) is empty.  sm: the block's B line buffers (ln.stride_tile()
+// entries each); cl: this lane's line in the block.
+template <typename T, bool IM>
+__device__ __forceinline__ cplx_t<T> part_pair(const cplx_t<T>* p) {
+  // the imaginary (IM) or real parts of p[0] and p[1], one vector load for FP32
   if constexpr (sizeof(T) == 4) {
     const float4 q = *reinterpret_cast<const float4*>(p);
-    return cplx_t<T>{q.y, q.w};
+    return IM ? cplx_t<T>{q.y, q.w} : cplx_t<T>{q.x, q.z};
   } else {
-    return cplx_t<T>{p[0].y, p[1].y};
+    return IM ? cplx_t<T>{p[0].y, p[1].y} : cplx_t<T>{p[0].x, p[1].x};
   }
 }
 
-template <typename T, typename LN>
+template <typename T, typename LN, int MODE>
 __device__ __forceinline__ void col_pair_tau_l(const LN& ln, const cplx_t<T>* in, cplx_t<T>* out, const ColArgs& A,
                                                const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, int64_t o,
                                                int64_t q, cplx_t<T>* sm, int cl, int tl) {
+  static_assert(MODE == SYM2 || MODE == ZSYM, "the symbol passes");
   using C = cplx_t<T>;
   constexpr int E = LN::E, B = blk<T>();
+  constexpr bool IM = MODE == SYM2;  // SYM2 columns are imaginary, ZSYM columns real
   static_assert(B % 2 == 0, "a column pair lies in one tile");
   const int M = ln.m(), TPL = ln.tpl(), LS = ln.stride_tile();
   C* buf = sm + cl * LS;
@@ -420,8 +423,20 @@ __device__ __forceinline__ void col_pair_tau_l(const LN& ln, const cplx_t<T>* in
   const int64_t nB = (int64_t)n * B;
   const int64_t c = 2 * q, tile = c / B;
   const int lt = (int)(c % B);
-  const bool la = c < K, lb = c + 1 < K;
-  const C* src = in + (o * KB + (la ? tile : 0)) * nB + lt;
+  int64_t k1 = c, base, sbase;  // first column's k1; slab of the pair; symbol of (k1 .. k1 + 1, kr = 0)
+  if constexpr (MODE == SYM2) {
+    base = (o * KB + tile) * nB;
+    sbase = tile * A.Ky * B + lt;  // entry (kr, k1) at (k1 / B) K_2 B + kr B + k1 % B
+  } else {  // W2 column c = k2 Kp + k1 (Kp = KB B) of field o, n = n_3 rows
+    const int64_t Kp = (int64_t)KB * B, k2 = c / Kp;
+    k1 = c % Kp;
+    const int64_t k2r = k2 <= A.My / 2 ? k2 : A.My - k2;
+    base = o * (int64_t)A.My * KB * ((int64_t)A.nz * B) + tile * nB;
+    // entry (k3r, k2r, k1) at ((k2r KB + k1 / B) K_3 + k3r) B + k1 % B, K_3 = M / 2 + 1
+    sbase = (k2r * KB + k1 / B) * (M / 2 + 1) * B + k1 % B;
+  }
+  const bool la = k1 < K, lb = k1 + 1 < K;
+  const C* src = in + (la ? base : 0) + lt;
   C v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {  // odd extension: row j at j + 1, its negative at M - 1 - j
@@ -429,33 +444,32 @@ __device__ __forceinline__ void col_pair_tau_l(const LN& ln, const cplx_t<T>* in
     const bool pos = j >= 1 && j <= n, neg = !pos && j >= M - n;
     C w = C{0, 0};
     if (la && (pos || neg)) {
-      const C im = im_pair<T>(src + (int64_t)(pos ? j - 1 : M - 1 - j) * B);
+      const C pr = part_pair<T, IM>(src + (int64_t)(pos ? j - 1 : M - 1 - j) * B);
       const T sg = pos ? T(1) : T(-1);
-      w = C{sg * im.x, lb ? sg * im.y : T(0)};
+      w = C{sg * pr.x, lb ? sg * pr.y : T(0)};
     }
     v[e] = w;
   }
   ln.template fft<false, false, false>(v, buf, tl, tw);
-  // symbol entry (kr, k1) at (k1 / B) K_2 B + kr B + k1 % B: columns c, c + 1 adjacent
-  const T* lrow = lam + tile * A.Ky * B + lt;
+  const T* lrow = lam + (la ? sbase : 0);
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int k = tl + e * TPL;
     const int kr = k <= M / 2 ? k : M - k;
-    // both entries in one aligned load (c even; the tiles are padded to B columns, so
-    // entry c + 1 exists even past K, and an empty column's factor is zero)
+    // both entries in one aligned load (k1 even; the tiles are padded to B columns, so
+    // entry k1 + 1 exists even past K, and an empty column's factor is zero)
     const C s2 = la ? *reinterpret_cast<const C*>(lrow + (int64_t)kr * B) : C{0, 0};
     v[e] = C{v[e].x * (lb ? s2.y : T(0)), v[e].y * s2.x};
   }
   ln.template fft<true, false, false>(v, buf, tl, tw);
   if (!la) return;
-  C* dst = out + (o * KB + tile) * nB + lt;
+  C* dst = out + base + lt;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int j = tl + e * TPL;
     if (j >= 1 && j <= n) {
-      dst[(int64_t)(j - 1) * B] = C{T(0), v[e].x};
-      if (lb) dst[(int64_t)(j - 1) * B + 1] = C{T(0), v[e].y};
+      dst[(int64_t)(j - 1) * B] = IM ? C{T(0), v[e].x} : C{v[e].x, T(0)};
+      if (lb) dst[(int64_t)(j - 1) * B + 1] = IM ? C{T(0), v[e].y} : C{v[e].y, T(0)};
     }
   }
 }
