@@ -337,8 +337,8 @@ k_cols(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, const T* __restrict__ lam
   col_tile<T, LOGM, MODE, ODD>(in, out, A, lam, tw, o, tile, reinterpret_cast<C*>(smem_raw), cl, tl);
 }
 
-// Columns of the tau preconditioner's symbol pass (2D SYM2, 3D ZSYM) two to a transform
-// (col_pair_tau_l): B lines per block, line q = unit B + cl of slab o.
+// Column passes of the tau preconditioner two columns to a transform (col_pair_tau_l):
+// B lines per block, line q = unit B + cl of slab o.
 template <typename T, int LOGM, int MODE>
 __global__ void __launch_bounds__(blk<T>() * tpl(LOGM), minb_cols<T>(blk<T>() * tpl(LOGM)))
 k_cols_tau_pairs(const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, int64_t qtiles, const T* __restrict__ lam,
@@ -475,11 +475,11 @@ static int launch_cols(const void* in, void* out, const ColArgs& A, int64_t nout
                                     {"cols_sym2_tau", "cols_yfwd_tau", "cols_zsym_tau", "cols_yinv_tau"}};
   char nb[48];
   prof::Scope ps(kname<T>(nb, names[ODD ? 1 : 0][MODE], LOGM), st);
-  if constexpr ((MODE == SYM2 || MODE == ZSYM) && ODD) {  // tau preconditioner: two columns a transform
+  if constexpr (ODD) {  // tau preconditioner: two columns a transform
     auto kp = k_cols_tau_pairs<T, LOGM, MODE>;
     FRAC_TRY(set_smem(kp, sm));
-    // column pairs of a slab: SYM2 ceil(K / 2), ZSYM the W2 blocks' (tiles x B) / 2
-    const int64_t qtiles = MODE == SYM2 ? cdiv(cdiv(A.K, 2), B) : cdiv(A.tiles * B / 2, B);
+    // column pairs of a slab: ceil(K / 2), or for ZSYM the W2 blocks' (tiles x B) / 2
+    const int64_t qtiles = MODE == ZSYM ? cdiv(A.tiles * B / 2, B) : cdiv(cdiv(A.K, 2), B);
     kp<<<(unsigned)(nouter * qtiles), B * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, qtiles, lam,
                                                               tw_table<T>(LOGM), cgst);
     FRAC_CUDA_TRY(cudaGetLastError());

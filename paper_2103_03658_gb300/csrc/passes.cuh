@@ -384,19 +384,27 @@ __device__ __forceinline__ void col_tile_l(const LN& ln, const cplx_t<T>* in, cp
     }
   }
 }
-// Columns of the tau preconditioner (SYM2, and ZSYM in 3D, on the odd extension), two
-// per transform.  After the odd-extension row pass every entry of the 2D spectrum W is
-// purely imaginary, i s(j, k1) with s real (in 3D the odd y pass leaves W2 purely real,
-// r(j3, c)), so the full-width pass would spend a complex transform on one real column.
-// Here line q carries columns c = 2q and c + 1 (one tile, B even) as z(j) = s(j, c) +
-// i s(j, c + 1): with the odd extension along this axis the transform of each real part
-// is purely imaginary, so after the forward transform the imaginary part belongs to
-// column c and the real part to c + 1; each is scaled by its own symbol entry, and the
-// inverse transform returns s'(j, c) + i s'(j, c + 1), stored back as i s' (SYM2) or s'
-// (ZSYM).  The result equals the full-width pass's up to rounding (which leaves a
-// rounding-size real (SYM2) or imaginary (ZSYM) part there); a column past the half
-// spectrum (k1 >= K) is empty.  sm: the block's B line buffers (ln.stride_tile()
-// entries each); cl: this lane's line in the block.
+// Column passes of the tau preconditioner (all on the odd extension), two columns per
+// transform.  The odd-extension spectra are purely imaginary or purely real: after the
+// row pass every entry of W (W1 in 3D) is i s(j, k1) with s real; the 3D y pass maps
+// such columns to purely real ones r(k2, c) of W2, the z pass keeps W2 real, and the
+// inverse y pass maps them back to imaginary ones.  So the full-width passes spend a
+// complex transform on one real column.  Here line q carries columns c = 2q and c + 1
+// (one tile, B even) as z = s(., c) + i s(., c + 1): with the odd extension the
+// transform of each real part is purely imaginary (an odd-symmetric real spectrum
+// transforms back to a purely imaginary one), so the two columns separate again into
+// the real and imaginary parts:
+//   SYM2, ZSYM: z(j) -> forward -> imaginary part column c, real part c + 1, each scaled
+//               by its own symbol entry -> inverse -> s'(j, c) + i s'(j, c + 1), stored
+//               back as i s' (SYM2) or s' (ZSYM);
+//   YFWD:       z(j2) from the imaginary parts of W1 -> forward -> the full-width pass's
+//               real outputs -Im (column c) and Re (c + 1), to W2 at every k2;
+//   YINV:       z(k2) from the real parts of W2 -> inverse -> i s''(c) - s''(c + 1), so
+//               Im to column c and -Re to c + 1 of W1 (as i s'').
+// The results equal the full-width passes' up to rounding (which leaves a rounding-size
+// second part there); a column past the half spectrum (k1 >= K) is empty.  sm: the
+// block's B line buffers (ln.stride_tile() entries each); cl: this lane's line in the
+// block; o: the slab (the field; (b, j3) for YFWD and YINV).
 template <typename T, bool IM>
 __device__ __forceinline__ cplx_t<T> part_pair(const cplx_t<T>* p) {
   // the imaginary (IM) or real parts of p[0] and p[1], one vector load for FP32
@@ -408,68 +416,115 @@ __device__ __forceinline__ cplx_t<T> part_pair(const cplx_t<T>* p) {
   }
 }
 
+// p[0] = a and, when both, p[1] = b (one vector store for FP32; p 2-entry aligned).
+template <typename T>
+__device__ __forceinline__ void store_pair(cplx_t<T>* p, cplx_t<T> a, cplx_t<T> b, bool both) {
+  if constexpr (sizeof(T) == 4) {
+    if (both)
+      *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+    else
+      p[0] = a;
+  } else {
+    p[0] = a;
+    if (both) p[1] = b;
+  }
+}
+
 template <typename T, typename LN, int MODE>
 __device__ __forceinline__ void col_pair_tau_l(const LN& ln, const cplx_t<T>* in, cplx_t<T>* out, const ColArgs& A,
                                                const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, int64_t o,
                                                int64_t q, cplx_t<T>* sm, int cl, int tl) {
-  static_assert(MODE == SYM2 || MODE == ZSYM, "the symbol passes");
   using C = cplx_t<T>;
   constexpr int E = LN::E, B = blk<T>();
-  constexpr bool IM = MODE == SYM2;  // SYM2 columns are imaginary, ZSYM columns real
+  constexpr bool IN_IM = MODE == SYM2 || MODE == YFWD;  // the input columns' nonzero part
   static_assert(B % 2 == 0, "a column pair lies in one tile");
   const int M = ln.m(), TPL = ln.tpl(), LS = ln.stride_tile();
   C* buf = sm + cl * LS;
   const int n = A.n, K = A.K, KB = A.KB;
-  const int64_t nB = (int64_t)n * B;
+  const int64_t nB = (int64_t)n * B, zB = (int64_t)A.nz * B, W2slab = (int64_t)A.My * KB * zB;
   const int64_t c = 2 * q, tile = c / B;
   const int lt = (int)(c % B);
-  int64_t k1 = c, base, sbase;  // first column's k1; slab of the pair; symbol of (k1 .. k1 + 1, kr = 0)
+  // k1 of the first column; W1 slab rows (SYM2, YFWD in, YINV out: j2) or W2 column
+  // (ZSYM: j3 rows; YFWD out, YINV in: k2 rows); the symbol's (k1, kr = 0) entry
+  int64_t k1 = c, w1 = (o * KB + tile) * nB, w2 = 0, sbase = 0;
   if constexpr (MODE == SYM2) {
-    base = (o * KB + tile) * nB;
     sbase = tile * A.Ky * B + lt;  // entry (kr, k1) at (k1 / B) K_2 B + kr B + k1 % B
-  } else {  // W2 column c = k2 Kp + k1 (Kp = KB B) of field o, n = n_3 rows
+  } else if constexpr (MODE == ZSYM) {  // W2 column c = k2 Kp + k1 (Kp = KB B) of field o
     const int64_t Kp = (int64_t)KB * B, k2 = c / Kp;
     k1 = c % Kp;
     const int64_t k2r = k2 <= A.My / 2 ? k2 : A.My - k2;
-    base = o * (int64_t)A.My * KB * ((int64_t)A.nz * B) + tile * nB;
+    w2 = o * W2slab + tile * nB;
     // entry (k3r, k2r, k1) at ((k2r KB + k1 / B) K_3 + k3r) B + k1 % B, K_3 = M / 2 + 1
     sbase = (k2r * KB + k1 / B) * (M / 2 + 1) * B + k1 % B;
+  } else {  // YFWD, YINV: slab o = (b, j3); W2 entry k2 of the tile's columns at k2 KB zB
+    w2 = (o / A.nz) * W2slab + tile * zB + (o % A.nz) * B;
   }
   const bool la = k1 < K, lb = k1 + 1 < K;
-  const C* src = in + (la ? base : 0) + lt;
   C v[E];
+  if constexpr (MODE == YINV) {
+    const C* src = in + (la ? w2 : 0) + lt;
 #pragma unroll
-  for (int e = 0; e < E; ++e) {  // odd extension: row j at j + 1, its negative at M - 1 - j
-    const int j = tl + e * TPL;
-    const bool pos = j >= 1 && j <= n, neg = !pos && j >= M - n;
-    C w = C{0, 0};
-    if (la && (pos || neg)) {
-      const C pr = part_pair<T, IM>(src + (int64_t)(pos ? j - 1 : M - 1 - j) * B);
-      const T sg = pos ? T(1) : T(-1);
-      w = C{sg * pr.x, lb ? sg * pr.y : T(0)};
+    for (int e = 0; e < E; ++e) {
+      const int k2 = tl + e * TPL;
+      const C pr = la ? part_pair<T, false>(src + (int64_t)k2 * KB * zB) : C{0, 0};
+      v[e] = C{pr.x, lb ? pr.y : T(0)};
     }
-    v[e] = w;
-  }
-  ln.template fft<false, false, false>(v, buf, tl, tw);
-  const T* lrow = lam + (la ? sbase : 0);
+  } else {
+    const C* src = in + (la ? (MODE == ZSYM ? w2 : w1) : 0) + lt;
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int k = tl + e * TPL;
-    const int kr = k <= M / 2 ? k : M - k;
-    // both entries in one aligned load (k1 even; the tiles are padded to B columns, so
-    // entry k1 + 1 exists even past K, and an empty column's factor is zero)
-    const C s2 = la ? *reinterpret_cast<const C*>(lrow + (int64_t)kr * B) : C{0, 0};
-    v[e] = C{v[e].x * (lb ? s2.y : T(0)), v[e].y * s2.x};
+    for (int e = 0; e < E; ++e) {  // odd extension: row j at j + 1, its negative at M - 1 - j
+      const int j = tl + e * TPL;
+      const bool pos = j >= 1 && j <= n, neg = !pos && j >= M - n;
+      C w = C{0, 0};
+      if (la && (pos || neg)) {
+        const C pr = part_pair<T, IN_IM>(src + (int64_t)(pos ? j - 1 : M - 1 - j) * B);
+        const T sg = pos ? T(1) : T(-1);
+        w = C{sg * pr.x, lb ? sg * pr.y : T(0)};
+      }
+      v[e] = w;
+    }
   }
-  ln.template fft<true, false, false>(v, buf, tl, tw);
+  if constexpr (MODE != YINV) ln.template fft<false, false, false>(v, buf, tl, tw);
+  if constexpr (MODE == SYM2 || MODE == ZSYM) {
+    const T* lrow = lam + (la ? sbase : 0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int k = tl + e * TPL;
+      const int kr = k <= M / 2 ? k : M - k;
+      // both entries in one aligned load (k1 even; the tiles are padded to B columns, so
+      // entry k1 + 1 exists even past K, and an empty column's factor is zero)
+      const C s2 = la ? *reinterpret_cast<const C*>(lrow + (int64_t)kr * B) : C{0, 0};
+      v[e] = C{v[e].x * (lb ? s2.y : T(0)), v[e].y * s2.x};
+    }
+  }
+  if constexpr (MODE != YFWD) ln.template fft<true, false, false>(v, buf, tl, tw);
   if (!la) return;
-  C* dst = out + base + lt;
+  if constexpr (MODE == YFWD) {
+    C* dst = out + w2 + lt;
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int j = tl + e * TPL;
-    if (j >= 1 && j <= n) {
-      dst[(int64_t)(j - 1) * B] = IM ? C{T(0), v[e].x} : C{v[e].x, T(0)};
-      if (lb) dst[(int64_t)(j - 1) * B + 1] = IM ? C{T(0), v[e].y} : C{v[e].y, T(0)};
+    for (int e = 0; e < E; ++e) {
+      const int64_t k2 = tl + e * TPL;
+      store_pair<T>(dst + k2 * KB * zB, C{-v[e].y, T(0)}, C{v[e].x, T(0)}, lb);
+    }
+  } else {
+    C* dst = out + (MODE == ZSYM ? w2 : w1) + lt;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = tl + e * TPL;
+      if (j >= 1 && j <= n) {
+        C a, b;
+        if constexpr (MODE == SYM2) {
+          a = C{T(0), v[e].x};
+          b = C{T(0), v[e].y};
+        } else if constexpr (MODE == ZSYM) {
+          a = C{v[e].x, T(0)};
+          b = C{v[e].y, T(0)};
+        } else {  // YINV
+          a = C{T(0), v[e].y};
+          b = C{T(0), -v[e].x};
+        }
+        store_pair<T>(dst + (int64_t)(j - 1) * B, a, b, lb);
+      }
     }
   }
 }

@@ -32,7 +32,9 @@ def _op(d, n, p, alpha, lam=0.0):
 # n = 2^k - 1 (tau system of exactly the problem's size) and other n (restricted)
 CASES = [(1, 3, 1, 1.2, 0.0, 1), (1, 7, 2, 0.4, 0.0, 3), (1, 100, 0, 1.5, 1.0, 2), (1, 1023, 1, 1.9, 0.0, 2),
          (2, 3, 1, 1.0, 0.0, 1), (2, 15, 2, 1.6, 0.3, 2), (2, 20, 0, 0.5, 1.5, 1), (2, 63, 1, 1.2, 0.0, 2),
-         (3, 3, 1, 0.7, 0.0, 1), (3, 9, 2, 1.6, 0.0, 2), (3, 15, 1, 0.4, 0.8, 1)]
+         (3, 3, 1, 0.7, 0.0, 1), (3, 9, 2, 1.6, 0.0, 2), (3, 15, 1, 0.4, 0.8, 1),
+         # several column tiles and slabs per pass, the last column pair half empty
+         (2, 127, 1, 0.9, 0.0, 3), (3, 31, 1, 0.4, 0.0, 2)]
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
