@@ -492,6 +492,7 @@ def extra_measurements(fg, torch, u32, op, barrier) -> dict:
         op3.close()
     out["solves"] = solves
     out["applies"] = apply_measurement(fg, torch, barrier)
+    out["precond"] = precond_measurement(fg, torch, barrier)
     out["operator_builds"] = build_measurement(fg, barrier)
     out["boundary"] = boundary_measurement(fg, torch, barrier)
     out["batch"] = batch_measurement(fg, torch, barrier)
@@ -565,6 +566,40 @@ def apply_measurement(fg, torch, barrier) -> dict:
             barrier()
             unit = "us" if scale == 1e3 else "ms"
             out[f"{name}_{'f64' if dt == torch.float64 else 'f32'}_{unit}"] = e0.elapsed_time(e1) / 20 * scale
+        op.close()
+    return out
+
+
+def precond_measurement(fg, torch, barrier, lib=None) -> dict:
+    """The tau preconditioner (frac_precond) of the benchmark operator (2D 1023^2, alpha = 1.2,
+    p = 2) on 65 seeded fields, FP32 and FP64, and of the 3D 255^3 operator (p = 1, alpha = 0.4)
+    on one field: ms per call (CUDA events over 10 calls, 3 for FP64, after 3 warm-up calls) and
+    the device time per call of each kernel (the library's profiler)."""
+    from paper_2103_03658_gb300 import _native
+    lib = lib or _native.load()
+    out = {}
+    for name, (d, n, p, alpha, fields) in (("2d_n1023_65fields", (2, 1023, 2, 1.2, 65)),
+                                           ("3d_n255", (3, 255, 1, 0.4, 1))):
+        op = fg.FracOp(d, n, alpha, degree=p)
+        g = torch.Generator(device="cuda").manual_seed(d * 100 + n)
+        for dt, reps in ((torch.float32, 10), (torch.float64, 3)):
+            r = torch.randn((fields,) + op.shape, dtype=dt, device="cuda", generator=g)
+            for _ in range(3):
+                op.precond(r)
+            barrier()
+            lib.frac_profile_enable(1)
+            profile_read(lib)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                op.precond(r)
+            e1.record()
+            barrier()
+            lib.frac_profile_enable(0)
+            prof = profile_read(lib)
+            out[f"{name}_{'f64' if dt == torch.float64 else 'f32'}"] = {
+                "ms": e0.elapsed_time(e1) / reps,
+                "kernels_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()}}
         op.close()
     return out
 
@@ -795,6 +830,8 @@ def main():
                     help="arrival window of the served stream (the configured stream is 60 s)")
     ap.add_argument("--applies-only", action="store_true",
                     help="run only the 1D and 3D single-vector apply timings and print their JSON (profiler captures)")
+    ap.add_argument("--precond-only", action="store_true",
+                    help="run only the tau preconditioner timings and print their JSON (profiler captures)")
     ap.add_argument("--mixed-only", default=None, metavar="CASES",
                     help="run only the mixed-radix comparison for the listed cases (comma-separated, e.g. "
                          "2d_n600_b64; 'all' for every case) and print its JSON (profiler captures)")
@@ -807,6 +844,11 @@ def main():
         import torch
         import paper_2103_03658_gb300 as fg
         print(json.dumps(apply_measurement(fg, torch, torch.cuda.synchronize)), flush=True)
+        return
+    if args.precond_only:
+        import torch
+        import paper_2103_03658_gb300 as fg
+        print(json.dumps(precond_measurement(fg, torch, torch.cuda.synchronize)), flush=True)
         return
     if args.boundary_only:
         import torch
