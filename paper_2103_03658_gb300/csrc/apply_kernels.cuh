@@ -367,6 +367,20 @@ __global__ void __launch_bounds__(NTMAX, mx_minb<T>(NTMAX)) k_cols_mx(MxLine ln,
   col_tile_l<T, MxLine, MODE, ODD>(ln, in, out, A, lam, tw, o, tile, reinterpret_cast<C*>(smem_raw), cl, tl);
 }
 
+// The tau preconditioner's column passes on a mixed length, two columns a transform.
+template <typename T, int MODE, int NTMAX>
+__global__ void __launch_bounds__(NTMAX, mx_minb<T>(NTMAX))
+    k_cols_tau_pairs_mx(MxLine ln, const cplx_t<T>* in, cplx_t<T>* out, ColArgs A, int64_t qtiles,
+                        const T* __restrict__ lam, const cplx_t<T>* __restrict__ tw, const CGState* st) {
+  using C = cplx_t<T>;
+  constexpr int B = blk<T>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (st && st->done) return;
+  const int cl = threadIdx.x % B, tl = threadIdx.x / B;
+  const int64_t o = blockIdx.x / qtiles, q = (blockIdx.x % qtiles) * B + cl;
+  col_pair_tau_l<T, MxLine, MODE>(ln, in, out, A, lam, tw, o, q, reinterpret_cast<C*>(smem_raw), cl, tl);
+}
+
 #endif  // FRAC_MX_TU
 
 // ---------------------------------------------------------------------------
@@ -482,13 +496,12 @@ static int launch_cols(const void* in, void* out, const ColArgs& A, int64_t nout
     const int64_t qtiles = MODE == ZSYM ? cdiv(A.tiles * B / 2, B) : cdiv(cdiv(A.K, 2), B);
     kp<<<(unsigned)(nouter * qtiles), B * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, qtiles, lam,
                                                               tw_table<T>(LOGM), cgst);
-    FRAC_CUDA_TRY(cudaGetLastError());
-    return FRAC_OK;
+  } else {  // (a discarded branch: the full-width kernel is not instantiated for ODD)
+    auto kern = k_cols<T, LOGM, MODE, ODD>;
+    FRAC_TRY(set_smem(kern, sm));
+    const int64_t blocks = nouter * A.tiles;
+    kern<<<(unsigned)blocks, B * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, lam, tw_table<T>(LOGM), cgst);
   }
-  auto kern = k_cols<T, LOGM, MODE, ODD>;
-  FRAC_TRY(set_smem(kern, sm));
-  const int64_t blocks = nouter * A.tiles;
-  kern<<<(unsigned)blocks, B * tpl(LOGM), sm, st>>>((const C*)in, (C*)out, A, lam, tw_table<T>(LOGM), cgst);
   FRAC_CUDA_TRY(cudaGetLastError());
   return FRAC_OK;
 }
@@ -648,14 +661,22 @@ int launch_cols_mx(const MxLine& ln, const void* in, void* out, const ColArgs& A
   using C = cplx_t<T>;
   constexpr int B = blk<T>();
   const size_t sm = (size_t)B * ln.stride_tile() * sizeof(C);
-  auto kern = B * ln.tpl() <= 256 ? k_cols_mx<T, MODE, ODD, 256> : k_cols_mx<T, MODE, ODD, 512>;
-  FRAC_TRY(set_smem(kern, sm));
   static const char* names[2][4] = {{"cols_sym2", "cols_yfwd", "cols_zsym", "cols_yinv"},
                                     {"cols_sym2_tau", "cols_yfwd_tau", "cols_zsym_tau", "cols_yinv_tau"}};
   char nb[48];
   prof::Scope ps(kname_mx<T>(nb, names[ODD ? 1 : 0][MODE], ln.m()), st);
-  kern<<<(unsigned)(nouter * A.tiles), B * ln.tpl(), sm, st>>>(ln, (const C*)in, (C*)out, A, lam, tw_len<T>(ln.m()),
-                                                                cgst);
+  if constexpr (ODD) {  // tau preconditioner: two columns a transform (as launch_cols)
+    auto kp = B * ln.tpl() <= 256 ? k_cols_tau_pairs_mx<T, MODE, 256> : k_cols_tau_pairs_mx<T, MODE, 512>;
+    FRAC_TRY(set_smem(kp, sm));
+    const int64_t qtiles = MODE == ZSYM ? cdiv(A.tiles * B / 2, B) : cdiv(cdiv(A.K, 2), B);
+    kp<<<(unsigned)(nouter * qtiles), B * ln.tpl(), sm, st>>>(ln, (const C*)in, (C*)out, A, qtiles, lam,
+                                                              tw_len<T>(ln.m()), cgst);
+  } else {  // (a discarded branch: the full-width kernel is not instantiated for ODD)
+    auto kern = B * ln.tpl() <= 256 ? k_cols_mx<T, MODE, ODD, 256> : k_cols_mx<T, MODE, ODD, 512>;
+    FRAC_TRY(set_smem(kern, sm));
+    kern<<<(unsigned)(nouter * A.tiles), B * ln.tpl(), sm, st>>>(ln, (const C*)in, (C*)out, A, lam,
+                                                                  tw_len<T>(ln.m()), cgst);
+  }
   FRAC_CUDA_TRY(cudaGetLastError());
   return FRAC_OK;
 }
